@@ -1,0 +1,20 @@
+"""Plain FP64 CPU oracle of the two-level BPJD eigensolver.
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product path may import, call, link
+or execute anything in this package: only the test-suite, the smoke check of
+``__graft_entry__`` and the CPU-baseline leg of ``bench.py`` use it.  It shares
+no code with the CUDA library: it has its own finite-element assembly, its own
+subdomain partition and coarse interpolation, and its own BPJD iteration,
+written in NumPy/SciPy double precision for readability rather than speed.
+
+Modules
+  fem        finite-element stiffness/mass assembly (Section 2.2, Section 6)
+  partition  overlapping box subdomains and colouring (Section 2.3, Assumption 2)
+  coarse     nodal interpolation from the coarse space V^H (Section 2.3)
+  bpjd       the two-level BPJD method (Section 3, Algorithm 3.1, Eq. (3.3))
+  metrics    gap between subspaces (Definition 2.1), residuals, clusters
+
+Every function cites the passage it follows.  Functions without an external
+pin are marked "parity unpinned" in their docstrings; at present every
+function is pinned by a test in ``tests/test_oracle_*.py``.
+"""

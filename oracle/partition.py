@@ -1,0 +1,64 @@
+"""Overlapping box subdomains, local dof lists and colouring.
+
+Oracle (test infrastructure only).  Section 2.3: the coarse partition J_H
+into subdomains Omega_l is enlarged layer by layer by whole fine elements into
+Omega_l'; delta measures the overlap; the local space V^(l) is the part of V^h
+that vanishes outside Omega_l' (zero trace on its boundary).  Assumption 2:
+the Omega_l' can be coloured so that same-coloured subdomains are disjoint.
+
+Rule used here (box subdomains on the uniform grid, in fine-node index units):
+  * subdomain (s_x, s_y[, s_z]) has id l = s_x + S_x (s_y + S_y s_z);
+  * along axis d with m = n_d / S_d elements per subdomain, Omega_l' spans the
+    open index interval (lo, hi) with lo = s_d m - delta (0 for s_d = 0) and
+    hi = (s_d + 1) m + delta (n_d for the last subdomain), clipped to [0, n_d];
+  * the local dofs are the grid nodes strictly inside Omega_l' (so the local
+    functions vanish on its boundary), which are interior nodes of Omega;
+  * they are listed in ascending global dof order;
+  * colour = sum_d (s_d mod 2) 2^d, valid (disjoint colour classes) while
+    2 delta <= m.
+"""
+
+from __future__ import annotations
+
+import itertools
+
+import numpy as np
+
+
+def axis_ranges(n: int, S: int, delta: int):
+    """Inclusive node-index ranges [a, b] strictly inside each subdomain along one axis."""
+    m = n // S
+    out = []
+    for s in range(S):
+        lo = 0 if s == 0 else max(s * m - delta, 0)
+        hi = n if s == S - 1 else min((s + 1) * m + delta, n)
+        out.append((lo + 1, hi - 1))
+    return out
+
+
+def box_partition(spec):
+    """Returns (sub_ptr int64[N+1], sub_dofs int32[sum n_l], sub_color int32[N], n_colors)."""
+    n, S, dim = spec.n, spec.nsub, spec.dim
+    ranges = [axis_ranges(n[d], S[d], spec.delta) for d in range(dim)]
+    inner = [m - 1 for m in n]                      # interior nodes per axis
+    ptr = [0]
+    dofs = []
+    colors = []
+    # subdomain id l = s_x + S_x (s_y + S_y s_z): iterate with x fastest
+    for sidx in itertools.product(*[range(S[d]) for d in reversed(range(dim))]):
+        s = tuple(reversed(sidx))                   # (s_x, s_y[, s_z])
+        axes = [np.arange(ranges[d][s[d]][0], ranges[d][s[d]][1] + 1) for d in range(dim)]
+        # global dof of interior node (i, j[, l]) = ((l-1) inner_y + (j-1)) inner_x + (i-1)
+        g = np.zeros([len(a) for a in reversed(axes)], dtype=np.int64)
+        stride = 1
+        for d in range(dim):
+            shape = [1] * dim
+            shape[dim - 1 - d] = len(axes[d])
+            g = g + (axes[d] - 1).reshape(shape) * stride
+            stride *= inner[d]
+        local = np.sort(g.ravel())
+        dofs.append(local)
+        ptr.append(ptr[-1] + len(local))
+        colors.append(sum((s[d] % 2) << d for d in range(dim)))
+    return (np.asarray(ptr, dtype=np.int64), np.concatenate(dofs).astype(np.int32),
+            np.asarray(colors, dtype=np.int32), 1 << dim)

@@ -1,0 +1,159 @@
+"""Pins of the oracle's finite-element assembly (Section 2.2, Section 6).
+
+Each test checks the oracle against something other than itself: eigenvalues
+printed in the paper, closed forms, or exact integrals of polynomials.
+"""
+
+import numpy as np
+import pytest
+import scipy.linalg as la
+import scipy.sparse.linalg as sla
+
+from conftest import golden
+from oracle import fem
+from workloads import ProblemSpec, config_table1_col1, config_table5
+
+
+def _lowest(K, M, k):
+    w = sla.eigsh(K.tocsc(), k, M.tocsc(), sigma=0.0, which="LM")[0]
+    return np.sort(w)
+
+
+def test_table1_first_column():
+    """Table 1 (Example 6.1), 16129 dofs: all 19 printed eigenvalues to 8 decimals."""
+    spec = config_table1_col1()
+    K, M = fem.assemble(spec)
+    assert K.shape == (16129, 16129)
+    want = np.array([r[0] for r in golden("table1_col1.txt")])
+    got = _lowest(K, M, 19)
+    np.testing.assert_allclose(got, want, rtol=0, atol=6e-9)
+
+
+@pytest.mark.parametrize("col,n", [(0, 16), (1, 32)])
+def test_table5_columns(col, n):
+    """Table 5 (Example 6.3), trilinear elements: 20 printed eigenvalues to 8 decimals."""
+    spec = config_table5(n)
+    K, M = fem.assemble(spec)
+    assert K.shape[0] == (n - 1) ** 3
+    want = np.array([r[col] for r in golden("table5.txt")])
+    got = _lowest(K, M, 20)
+    np.testing.assert_allclose(got, want, rtol=0, atol=6e-9)
+
+
+def test_q1_closed_form_spectrum():
+    """Trilinear elements on a uniform grid: the pencil separates, and every eigenvalue is
+    sum_d 6 (1 - cos t_d) / (h_d^2 (2 + cos t_d)), t_d = j_d pi / n_d (1-D linear elements)."""
+    n = (5, 6, 4)
+    L = (1.0, 1.3, 0.7)
+    spec = ProblemSpec("q1_3d", n, L, (1, 1, 1), 0, 1)
+    K, M = fem.q1_3d_interior(*n, *L)
+    w = la.eigh(K.toarray(), M.toarray(), eigvals_only=True)
+    mus = []
+    for m, Ld in zip(n, L):
+        h = Ld / m
+        t = np.arange(1, m) * np.pi / m
+        mus.append(6 * (1 - np.cos(t)) / (h * h * (2 + np.cos(t))))
+    closed = np.sort((mus[0][:, None, None] + mus[1][None, :, None] + mus[2][None, None, :]).ravel())
+    np.testing.assert_allclose(w, closed, rtol=1e-12)
+    assert spec.n_dofs == K.shape[0]
+
+
+def test_p1_2d_unit_kappa_is_five_point_laplacian():
+    """Right triangles with kappa = 1 and hx = hy: the stiffness matrix is the 5-point
+    Laplacian (couplings across the SW->NE diagonal vanish) and its spectrum is
+    4 - 2 cos(i pi/n) - 2 cos(j pi/n)."""
+    n = 9
+    spec = ProblemSpec("p1_2d", (n, n), (1.0, 1.0), (1, 1), 0, 1)
+    K, M = fem.assemble(spec)
+    Kd = K.toarray()
+    N = n - 1
+    for g in range(N * N):
+        i, j = g % N, g // N
+        assert Kd[g, g] == pytest.approx(4.0, abs=1e-14)
+        for di, dj, v in [(1, 0, -1), (-1, 0, -1), (0, 1, -1), (0, -1, -1), (1, 1, 0), (-1, -1, 0)]:
+            if 0 <= i + di < N and 0 <= j + dj < N:
+                assert Kd[g, (j + dj) * N + i + di] == pytest.approx(v, abs=1e-14)
+    t = np.arange(1, n) * np.pi / n
+    closed = np.sort((4 - 2 * np.cos(t)[:, None] - 2 * np.cos(t)[None, :]).ravel())
+    np.testing.assert_allclose(np.linalg.eigvalsh(Kd), closed, atol=1e-12)
+    # pattern: K and M share the element-connectivity pattern (7 per interior row)
+    assert (K.indptr == M.indptr).all() and (K.indices == M.indices).all()
+    assert np.diff(K.indptr).max() == 7
+
+
+def _poly_checks_2d(Kf, Mf, nx, ny, Lx, Ly, kap):
+    hx, hy = Lx / nx, Ly / ny
+    nodes = np.arange((nx + 1) * (ny + 1))
+    x = (nodes % (nx + 1)) * hx
+    y = (nodes // (nx + 1)) * hy
+    one = np.ones_like(x)
+    area = hx * hy / 2
+    # constants are in the kernel of the stiffness; the mass integrates to |Omega|
+    assert np.abs(Kf @ one).max() < 1e-12 * np.abs(Kf).max()
+    assert one @ (Mf @ one) == pytest.approx(Lx * Ly, rel=1e-13)
+    # a linear u is reproduced exactly: a(u,u) = sum_e kappa_e |e| |grad u|^2
+    for a, b in [(1.0, 0.0), (0.0, 1.0), (1.0, 2.0)]:
+        u = a * x + b * y
+        assert u @ (Kf @ u) == pytest.approx(kap.sum() * area * (a * a + b * b), rel=1e-12)
+    # b(x, x) = int x^2 = Lx^3 Ly / 3 and b(x, y) = Lx^2 Ly^2 / 4 exactly
+    assert x @ (Mf @ x) == pytest.approx(Lx ** 3 * Ly / 3, rel=1e-12)
+    assert x @ (Mf @ y) == pytest.approx(Lx ** 2 * Ly ** 2 / 4, rel=1e-12)
+
+
+def test_p1_2d_polynomial_invariants_random_kappa():
+    nx, ny, Lx, Ly = 7, 5, 1.3, 0.9
+    kap = np.random.default_rng(3).uniform(0.5, 2.0, size=(ny, nx, 2))
+    Kf, Mf = fem.p1_2d_full(nx, ny, Lx, Ly, kap)
+    _poly_checks_2d(Kf, Mf, nx, ny, Lx, Ly, kap)
+    # which triangle carries which kappa: u = x - y is constant along the diagonal
+    # direction, so only ... use u = x restricted: a(u,u) per triangle equals kappa |e|;
+    # perturbing one triangle's kappa must change a(x,x) by exactly that triangle's area.
+    kap2 = kap.copy()
+    kap2[2, 3, 1] += 1.0
+    Kf2, _ = fem.p1_2d_full(nx, ny, Lx, Ly, kap2)
+    hx, hy = Lx / nx, Ly / ny
+    nodes = np.arange((nx + 1) * (ny + 1))
+    x = (nodes % (nx + 1)) * hx
+    assert x @ ((Kf2 - Kf) @ x) == pytest.approx(hx * hy / 2, rel=1e-12)
+    # the perturbed triangle is (SW, NE, NW) of square (3, 2): only its nodes change
+    changed = np.unique((Kf2 - Kf).tocoo().row[np.abs((Kf2 - Kf).tocoo().data) > 1e-14])
+    sq = lambda i, j: j * (nx + 1) + i
+    assert set(changed) == {sq(3, 2), sq(4, 3), sq(3, 3)}
+
+
+def test_p1_3d_polynomial_invariants_random_kappa():
+    nx, ny, nz = 3, 4, 2
+    L = (1.1, 0.8, 0.6)
+    kap = np.random.default_rng(5).uniform(0.5, 2.0, size=(nz, ny, nx))
+    Kf, Mf = fem.p1_3d_full(nx, ny, nz, *L, kap)
+    h = [L[0] / nx, L[1] / ny, L[2] / nz]
+    nodes = np.arange((nx + 1) * (ny + 1) * (nz + 1))
+    x = (nodes % (nx + 1)) * h[0]
+    y = ((nodes // (nx + 1)) % (ny + 1)) * h[1]
+    z = (nodes // ((nx + 1) * (ny + 1))) * h[2]
+    one = np.ones_like(x)
+    vol = h[0] * h[1] * h[2]
+    assert np.abs(Kf @ one).max() < 1e-12 * np.abs(Kf).max()
+    assert one @ (Mf @ one) == pytest.approx(L[0] * L[1] * L[2], rel=1e-13)
+    for c in [(1, 0, 0), (0, 1, 0), (0, 0, 1), (1, -2, 3)]:
+        u = c[0] * x + c[1] * y + c[2] * z
+        assert u @ (Kf @ u) == pytest.approx(kap.sum() * vol * sum(q * q for q in c), rel=1e-12)
+    assert z @ (Mf @ z) == pytest.approx(L[2] ** 3 * L[0] * L[1] / 3, rel=1e-12)
+    assert x @ (Mf @ z) == pytest.approx(L[0] ** 2 * L[2] ** 2 * L[1] / 4, rel=1e-12)
+
+
+@pytest.mark.parametrize("kind", ["p1_2d", "p1_3d"])
+def test_upper_bounds_and_second_order_convergence(kind):
+    """Theorem 2.1 (Eq. (2.4)): 0 <= lambda^h - lambda <= C h^2 for conforming P1; the error of
+    the principal eigenvalue of the unit square/cube falls by ~4 per halving of h."""
+    dim = 2 if kind == "p1_2d" else 3
+    exact = dim * np.pi ** 2
+    errs = []
+    for n in ([8, 16, 32] if dim == 2 else [4, 8, 16]):
+        spec = ProblemSpec(kind, (n,) * dim, (1.0,) * dim, (1,) * dim, 0, 1)
+        K, M = fem.assemble(spec)
+        lam = _lowest(K, M, 1)[0]
+        assert lam >= exact
+        errs.append(lam - exact)
+    ratios = np.array(errs[:-1]) / np.array(errs[1:])
+    assert np.all(ratios > 3.3) and np.all(ratios < 4.5), ratios

@@ -1,0 +1,57 @@
+"""Seeded synthetic workload generators for the two-level BPJD eigensolver.
+
+This package only *describes* eigenproblems: mesh resolution, domain size,
+the coefficient field kappa sampled per element, the subdomain grid, the
+overlap width and the number k of wanted eigenpairs, plus the seeded request
+stream of the serving workload.  It holds none of the solver's arithmetic:
+no finite-element assembly, no partition rule, no coarse interpolation and no
+eigensolver step.  Both the CPU oracle (``oracle/``) and the CUDA library
+(``paper_2203_06327_gb300``) consume these descriptions and build everything
+else independently.
+
+Problem classes follow the model problems of the paper (Section 2.1, the
+Laplacian eigenproblem with Dirichlet data) discretised as in Section 2.2 and
+the experiments of Section 6:
+
+* ``p1_2d``   -- P1 Lagrange elements on a uniform grid of nx x ny squares,
+  each split along its SW->NE diagonal (Section 6, Example 6.1 uses a uniform
+  triangle partition).
+* ``p1_3d``   -- P1 Lagrange elements on the Kuhn (Freudenthal) split of a
+  uniform nx x ny x nz cube grid into six tetrahedra per cube.
+* ``q1_3d``   -- trilinear elements on a uniform cube grid (Section 6,
+  Example 6.3).
+
+Layout of the per-element coefficient array ``kappa`` (float64, C order):
+
+* p1_2d: shape (ny, nx, 2); [j, i, 0] is the triangle of square (i, j) below
+  the SW->NE diagonal (vertices SW, SE, NE), [j, i, 1] the one above it
+  (vertices SW, NE, NW).  The value is kappa at the triangle's centroid.
+* p1_3d / q1_3d: shape (nz, ny, nx); one value per cube (kappa at the cube
+  centre), shared by the cube's tetrahedra.
+"""
+
+from .specs import (
+    ProblemSpec,
+    kappa_field_2d,
+    config_c1,
+    config_c2,
+    config_c3,
+    config_small_2d,
+    config_small_3d,
+    config_table1_col1,
+    config_table5,
+    serving_stream,
+)
+
+__all__ = [
+    "ProblemSpec",
+    "kappa_field_2d",
+    "config_c1",
+    "config_c2",
+    "config_c3",
+    "config_small_2d",
+    "config_small_3d",
+    "config_table1_col1",
+    "config_table5",
+    "serving_stream",
+]
