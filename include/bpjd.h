@@ -1,0 +1,231 @@
+/*
+ * bpjd.h -- C ABI of the GB300 two-level BPJD eigensolver.
+ *
+ * The library computes the lowest k eigenpairs (multiple and clustered ones
+ * included) of the symmetric-definite pencil K x = lambda M x arising from a
+ * conforming finite-element discretisation of a symmetric elliptic operator
+ * (Section 2.2), with the two-level block preconditioned Jacobi-Davidson
+ * method of Section 3 (Algorithm 3.1) and its overlapping-Schwarz
+ * preconditioner (Eq. (3.3)):
+ *
+ *   (B_i^k)^{-1} = (A^H - lambda_i^k)^{-1} Q_{s+1}^H Q^H
+ *                  + sum_l (A^(l) - lambda_i^k)^{-1} Q^(l).
+ *
+ * Conventions shared by every entry point
+ *   - Sparse matrices are 0-based CSR with int64 row pointers, int32 column
+ *     indices sorted ascending within a row and no duplicates, float64 values.
+ *   - Dense blocks of k vectors are ROW-MAJOR n x k ("k contiguous per dof").
+ *   - Pointers documented as "device" must be CUDA device pointers of the
+ *     current device; "host" pointers are ordinary host memory.
+ *   - Every function returns BPJD_OK (0) or a negative BPJD_ERR_* code; no
+ *     exception or abort crosses the ABI.  bpjd_status_string() names codes.
+ *   - A handle may be used from one host thread at a time; all of its GPU
+ *     work is ordered on the stream given in bpjd_opts.stream.
+ */
+#ifndef BPJD_H_
+#define BPJD_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define BPJD_OK                    0
+#define BPJD_ERR_BAD_ARG          -1  /* null pointer, k < 1, sizes inconsistent */
+#define BPJD_ERR_CSR_INVALID      -2  /* row_ptr not monotone, column out of range/unsorted */
+#define BPJD_ERR_MAP_INVALID      -3  /* subdomain dof list unsorted / out of range / empty */
+#define BPJD_ERR_K_TOO_LARGE      -4  /* k >= dim V^H: Section 3 needs s < dim(V^H) */
+#define BPJD_ERR_GAP              -5  /* lambda_k^H == lambda_{k+1}^H: Assumption 1 fails on V^H */
+#define BPJD_ERR_LOCAL_INDEFINITE -6  /* a shifted local matrix K_l - lambda_i M_l has a
+                                         non-positive pivot (Eq. (3.1) violated) */
+#define BPJD_ERR_BREAKDOWN        -7  /* Rayleigh-Ritz basis lost rank below k */
+#define BPJD_ERR_NOCONV           -8  /* max_iter reached before the stop rule held */
+#define BPJD_ERR_OOM              -9  /* device allocation failed */
+#define BPJD_ERR_CUDA            -10  /* a CUDA runtime call failed */
+#define BPJD_ERR_UNSUPPORTED     -11  /* option outside what this build implements */
+
+/* ---- option values ----------------------------------------------------- */
+#define BPJD_FP64        0  /* every step in FP64 */
+#define BPJD_MIXED       1  /* preconditioner (local band factorisations and solves,
+                               coarse solve, prolongation) in FP32; residuals,
+                               projections, Gram matrices, Rayleigh-Ritz and the
+                               Ritz-vector update in FP64 */
+
+#define BPJD_W_2K        0  /* W^{k+1} = U^k + span{t_i}           (Remark 3.1) */
+#define BPJD_W_3K        1  /* W^{k+1} = U^{k-1} + U^k + span{t_i} (Remark 3.1) */
+
+#define BPJD_STOP_RESIDUAL 0 /* every ||K x_i - lambda_i M x_i||_2 / (|lambda_i| ||M x_i||_2) <= tol */
+#define BPJD_STOP_DLAMBDA  1 /* sum_i |lambda_i^{k+1} - lambda_i^k| < tol (Algorithm 3.1 Step 4) */
+
+/* ---- input descriptors ------------------------------------------------- */
+typedef struct {
+  int32_t n_rows, n_cols;
+  int64_t nnz;
+  const int64_t* row_ptr;   /* n_rows + 1 */
+  const int32_t* col_idx;   /* nnz */
+  const double*  val;       /* nnz */
+} bpjd_csr;
+
+/* Overlapping subdomains Omega_l' (Section 2.3): the dofs of V^(l), i.e. the
+ * fine dofs strictly inside Omega_l', ascending, for l = 0..n_sub-1.  The
+ * local matrices are the principal submatrices K_l = R_l K R_l^T and
+ * M_l = R_l M R_l^T; they are factorised as banded matrices, so an ordering
+ * with small bandwidth (lexicographic on a box) keeps the local cost low. */
+typedef struct {
+  int32_t n_sub;
+  const int64_t* sub_ptr;   /* n_sub + 1, sub_ptr[0] = 0 */
+  const int32_t* sub_dofs;  /* sub_ptr[n_sub] */
+  const int32_t* sub_color; /* n_sub, or NULL; same colour => disjoint (Assumption 2).
+                               Informational: the prolongation-add is a gather over
+                               an inverse map and needs no colouring. */
+  int32_t n_colors;
+} bpjd_partition;
+
+typedef struct {
+  int32_t k;                /* wanted eigenpairs (the paper's s), 1 <= k <= 32 */
+  int32_t precision;        /* BPJD_FP64 | BPJD_MIXED */
+  int32_t subspace;         /* BPJD_W_2K | BPJD_W_3K */
+  int32_t stop_rule;        /* BPJD_STOP_RESIDUAL | BPJD_STOP_DLAMBDA */
+  double  tol;              /* threshold of the stop rule (default 1e-8) */
+  int32_t max_iter;         /* Rayleigh-Ritz steps at most (default 500) */
+  double  drop_tol;         /* Rayleigh-Ritz drops Gram eigen-directions below
+                               drop_tol * max (default 1e-10) */
+  double  H, delta;         /* subdomain diameter and overlap (metadata for logs) */
+  int32_t inputs_on_device; /* 1: all pointers of A, M, P, P0 and the partition
+                               are device pointers; 0: host pointers */
+  void*   stream;           /* cudaStream_t for all work; NULL = legacy default stream */
+} bpjd_opts;
+
+typedef struct {
+  int32_t iters;            /* Rayleigh-Ritz steps taken */
+  int32_t converged;        /* 1 if the stop rule held */
+  double  max_rel_resid;    /* of the returned pairs */
+  double  sum_abs_dlambda;  /* of the last step */
+  double  t_setup_s, t_solve_s;
+  int32_t status;
+} bpjd_stats;
+
+typedef struct bpjd_handle bpjd_handle;
+
+/* Fills *o with the defaults listed above (k = 1). */
+void bpjd_default_opts(bpjd_opts* o);
+
+const char* bpjd_status_string(int code);
+
+/*
+ * bpjd_setup -- build the device-resident solver state (Algorithm 3.1 Step 1).
+ *
+ * A, M : n x n stiffness and mass matrices (symmetric; M SPD).
+ * P    : n x n_H nodal interpolation V^H -> V^h (column c = fine values of the
+ *        c-th coarse basis function); defines Q^H and A^H by Galerkin products
+ *        K_H = P^T K P, M_H = P^T M P (Section 3).
+ * P0   : n x n_H0 interpolation from the grid H~ = H/2^tau used for the initial
+ *        eigenproblem of Step 1, or NULL to use P (tau = 0).
+ * part : overlapping subdomains.
+ * Inputs are only read during the call; the handle owns every device buffer
+ * until bpjd_free.  Errors: BAD_ARG, CSR_INVALID, MAP_INVALID, K_TOO_LARGE,
+ * GAP, OOM, CUDA; on error *out is NULL and nothing leaks.
+ */
+int bpjd_setup(const bpjd_csr* A, const bpjd_csr* M, const bpjd_csr* P, const bpjd_csr* P0,
+               const bpjd_partition* part, const bpjd_opts* opts, bpjd_handle** out);
+
+/*
+ * bpjd_solve -- run Algorithm 3.1 Steps 2-4 from the Step 1 initial guess.
+ *
+ * eigvals : k doubles (host), ascending Ritz values, or NULL.
+ * eigvecs : n x k row-major doubles, b-orthonormal (X^T M X = I), or NULL;
+ *           host memory if eigvecs_on_device == 0, device memory otherwise.
+ * st      : statistics, or NULL.
+ * May be called repeatedly; every call restarts from the initial guess.
+ * Errors: LOCAL_INDEFINITE, BREAKDOWN, NOCONV (results still written), CUDA.
+ */
+int bpjd_solve(bpjd_handle* h, double* eigvals, double* eigvecs, int32_t eigvecs_on_device,
+               bpjd_stats* st);
+
+/* Releases every resource of the handle (NULL is a no-op). */
+void bpjd_free(bpjd_handle* h);
+
+/* ---- hot-path steps on device buffers (for tests and measurements) ----- */
+
+/* n, n_H and k of a handle. */
+int bpjd_dims(const bpjd_handle* h, int32_t* n, int32_t* n_coarse, int32_t* k);
+
+/* Local-solve layout: band window B (lower bandwidth + 1, maximum over the
+ * subdomains), sum of the local sizes n_l, number of subdomains, and nnz of K. */
+int bpjd_layout(const bpjd_handle* h, int32_t* band_window, int64_t* sum_local, int32_t* n_sub, int64_t* nnz);
+
+/* Y_A = K X and Y_M = M X for a device n x ncols row-major X (1 <= ncols <= 64).
+ * Y_A, Y_M: device n x ncols.  Ordered on the handle's stream. */
+int bpjd_spmm(bpjd_handle* h, const double* X, double* YA, double* YM, int32_t ncols);
+
+/* z_i = (B_i)^{-1} rho_i (Eq. (3.3)) for the k columns of the device n x k
+ * array rho, with shifts lam (device, k doubles).  Z: device n x k.  Uses the
+ * handle's precision.  Returns LOCAL_INDEFINITE if a local pivot is <= 0. */
+int bpjd_apply_preconditioner(bpjd_handle* h, const double* rho, const double* lam, double* Z);
+
+/* Ritz values of every Rayleigh-Ritz step of the last solve (row j = step j,
+ * row 0 = initial guess), host array of cap x k doubles; returns rows written. */
+int bpjd_history(const bpjd_handle* h, double* lam_hist, int32_t cap);
+
+/* Device bytes held by the handle. */
+size_t bpjd_device_bytes(const bpjd_handle* h);
+
+/* ---- instrumentation --------------------------------------------------- */
+/* Kernel classes timed when profiling is on. */
+#define BPJD_PROF_LOCAL     0  /* banded local factorisation + solves (Q^(l), (B_{l,i})^{-1}) */
+#define BPJD_PROF_COARSE    1  /* coarse restriction, spectral solve, expansion */
+#define BPJD_PROF_PROLONG   2  /* prolongation-add of coarse and local corrections */
+#define BPJD_PROF_SPMM      3  /* K X and M X */
+#define BPJD_PROF_INNER     4  /* block inner products (projection, Gram matrices) */
+#define BPJD_PROF_COMBINE   5  /* row-wise block updates (projection, Ritz vectors) */
+#define BPJD_PROF_RR        6  /* small Rayleigh-Ritz eigenproblem */
+#define BPJD_PROF_RESID     7  /* residuals and norms */
+#define BPJD_PROF_N         8
+
+/* enable = 1 records a CUDA event pair around every kernel class launch on the
+ * handle's stream (small overhead); 0 stops.  Resets the accumulated data. */
+int bpjd_profile(bpjd_handle* h, int32_t enable);
+
+/* Accumulated device time (ms) and launch count per class since the last
+ * bpjd_profile call, and the total number of kernels the library launched on
+ * the handle (counted with or without profiling).  Arrays: BPJD_PROF_N entries;
+ * any pointer may be NULL. */
+int bpjd_profile_read(bpjd_handle* h, double* ms, int64_t* count, int64_t* kernel_launches);
+
+/* ---- problem generation helpers (host) --------------------------------- */
+
+/* Mesh description of the model problems (Section 2.1, Section 6):
+ *   kind 0 = P1 triangles on a uniform nx x ny grid, squares split SW->NE;
+ *   kind 1 = P1 tetrahedra, each cube of a uniform grid split into the six
+ *            Kuhn tetrahedra;
+ *   kind 2 = trilinear bricks (constant kappa only).
+ * kappa: per-element coefficient, layout [ny][nx][2] (kind 0, entry 0 = the
+ * triangle below the diagonal) or [nz][ny][nx] (kinds 1, 2); NULL = 1.
+ * Subdomains: nsub boxes per axis grown by delta element layers; the initial
+ * grid of Step 1 is the subdomain grid refined tau times. */
+typedef struct {
+  int32_t kind;
+  int32_t n[3];
+  double  length[3];
+  int32_t nsub[3];
+  int32_t delta;
+  int32_t tau;
+  const double* kappa;
+} bpjd_mesh;
+
+typedef struct {
+  bpjd_csr K, M, P, P0;     /* host arrays owned by the problem */
+  bpjd_partition part;
+} bpjd_problem;
+
+/* Assembles K, M, P, P0 and the box partition on the host.  Errors: BAD_ARG. */
+int bpjd_problem_create(const bpjd_mesh* mesh, bpjd_problem** out);
+void bpjd_problem_free(bpjd_problem* p);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BPJD_H_ */

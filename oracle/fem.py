@@ -167,8 +167,13 @@ def q1_3d_interior(nx, ny, nz, Lx, Ly, Lz):
     Kx, Mx = _q1_1d(nx, Lx)
     Ky, My = _q1_1d(ny, Ly)
     Kz, Mz = _q1_1d(nz, Lz)
-    kr = lambda a, b, c: sp.kron(a, sp.kron(b, c))
-    K = (kr(Mz, My, Kx) + kr(Mz, Ky, Mx) + kr(Kz, My, Mx)).tocsr()
+    kr = lambda a, b, c: sp.kron(a, sp.kron(b, c)).tocoo()
+    # sum the three terms as COO triplets so that entries cancelling to zero stay in
+    # the pattern (node pairs sharing an element), like every other element kind
+    terms = [kr(Mz, My, Kx), kr(Mz, Ky, Mx), kr(Kz, My, Mx)]
+    K = sp.coo_matrix((np.concatenate([t.data for t in terms]),
+                       (np.concatenate([t.row for t in terms]), np.concatenate([t.col for t in terms]))),
+                      shape=terms[0].shape).tocsr()
     M = kr(Mz, My, Mx).tocsr()
     for A in (K, M):
         A.sum_duplicates()

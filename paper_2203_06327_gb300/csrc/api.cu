@@ -1,0 +1,768 @@
+// C ABI of the BPJD library: setup (Algorithm 3.1 Step 1 and the device
+// data of Eq. (3.3)), the iteration driver (Steps 2-4) and the step-level
+// entry points.  See include/bpjd.h for the contract of every function.
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "bpjd_internal.h"
+
+using namespace bpjd;
+
+namespace {
+
+#define CK(call)                          \
+  do {                                    \
+    cudaError_t e_ = (call);              \
+    if (e_ != cudaSuccess) {              \
+      rc = (e_ == cudaErrorMemoryAllocation) ? BPJD_ERR_OOM : BPJD_ERR_CUDA; \
+      goto fail;                          \
+    }                                     \
+  } while (0)
+
+#define CKI(call)                         \
+  do {                                    \
+    int e_ = (call);                      \
+    if (e_ != 0) {                        \
+      rc = BPJD_ERR_CUDA;                 \
+      goto fail;                          \
+    }                                     \
+  } while (0)
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+template <typename T>
+cudaError_t dalloc(Handle& h, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e == cudaSuccess) {
+    h.allocs.push_back((void*)*p);
+    h.bytes += count * sizeof(T);
+  }
+  return e;
+}
+
+// Host view of a CSR (copied from the device when the inputs live there).
+struct HostCsr {
+  int32_t n_rows = 0, n_cols = 0;
+  int64_t nnz = 0;
+  std::vector<int64_t> rp_buf;
+  std::vector<int32_t> ci_buf;
+  std::vector<double> v_buf;
+  const int64_t* rp = nullptr;
+  const int32_t* ci = nullptr;
+  const double* v = nullptr;
+};
+
+int host_view(const bpjd_csr* c, bool on_dev, bool need_vals, HostCsr& out) {
+  out.n_rows = c->n_rows;
+  out.n_cols = c->n_cols;
+  out.nnz = c->nnz;
+  if (!on_dev) {
+    out.rp = c->row_ptr;
+    out.ci = c->col_idx;
+    out.v = c->val;
+    return BPJD_OK;
+  }
+  out.rp_buf.resize((size_t)c->n_rows + 1);
+  out.ci_buf.resize((size_t)std::max<int64_t>(c->nnz, 1));
+  if (cudaMemcpy(out.rp_buf.data(), c->row_ptr, sizeof(int64_t) * (c->n_rows + 1), cudaMemcpyDeviceToHost) !=
+      cudaSuccess)
+    return BPJD_ERR_CUDA;
+  if (c->nnz > 0 &&
+      cudaMemcpy(out.ci_buf.data(), c->col_idx, sizeof(int32_t) * c->nnz, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return BPJD_ERR_CUDA;
+  if (need_vals) {
+    out.v_buf.resize((size_t)std::max<int64_t>(c->nnz, 1));
+    if (c->nnz > 0 && cudaMemcpy(out.v_buf.data(), c->val, sizeof(double) * c->nnz, cudaMemcpyDeviceToHost) !=
+                          cudaSuccess)
+      return BPJD_ERR_CUDA;
+    out.v = out.v_buf.data();
+  }
+  out.rp = out.rp_buf.data();
+  out.ci = out.ci_buf.data();
+  return BPJD_OK;
+}
+
+int validate_csr(const HostCsr& c) {
+  if (c.n_rows < 0 || c.n_cols < 0 || c.nnz < 0) return BPJD_ERR_BAD_ARG;
+  if (c.rp[0] != 0 || c.rp[c.n_rows] != c.nnz) return BPJD_ERR_CSR_INVALID;
+  for (int64_t r = 0; r < c.n_rows; ++r) {
+    if (c.rp[r + 1] < c.rp[r]) return BPJD_ERR_CSR_INVALID;
+    for (int64_t e = c.rp[r]; e < c.rp[r + 1]; ++e) {
+      if (c.ci[e] < 0 || c.ci[e] >= c.n_cols) return BPJD_ERR_CSR_INVALID;
+      if (e > c.rp[r] && c.ci[e] <= c.ci[e - 1]) return BPJD_ERR_CSR_INVALID;
+    }
+  }
+  return BPJD_OK;
+}
+
+// Copies a CSR (host or device source) into handle-owned device memory.
+cudaError_t upload_csr(Handle& h, const bpjd_csr* c, bool on_dev, CsrDev& d, bool vals = true) {
+  d.n_rows = c->n_rows;
+  d.n_cols = c->n_cols;
+  d.nnz = c->nnz;
+  cudaMemcpyKind kind = on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  cudaError_t e;
+  if ((e = dalloc(h, &d.row_ptr, (size_t)c->n_rows + 1)) != cudaSuccess) return e;
+  if ((e = dalloc(h, &d.col, (size_t)c->nnz)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(d.row_ptr, c->row_ptr, sizeof(int64_t) * (c->n_rows + 1), kind, h.stream)) != cudaSuccess)
+    return e;
+  if (c->nnz && (e = cudaMemcpyAsync(d.col, c->col_idx, sizeof(int32_t) * c->nnz, kind, h.stream)) != cudaSuccess)
+    return e;
+  if (vals) {
+    if ((e = dalloc(h, &d.val, (size_t)c->nnz)) != cudaSuccess) return e;
+    if (c->nnz && (e = cudaMemcpyAsync(d.val, c->val, sizeof(double) * c->nnz, kind, h.stream)) != cudaSuccess)
+      return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t upload_host_csr(Handle& h, const HostCsr& c, CsrDev& d) {
+  bpjd_csr v;
+  v.n_rows = c.n_rows;
+  v.n_cols = c.n_cols;
+  v.nnz = c.nnz;
+  v.row_ptr = c.rp;
+  v.col_idx = c.ci;
+  v.val = c.v;
+  return upload_csr(h, &v, false, d, true);
+}
+
+// Transpose of a host CSR (rows of the result sorted by column = original row).
+void transpose_host(const HostCsr& a, HostCsr& t) {
+  t.n_rows = a.n_cols;
+  t.n_cols = a.n_rows;
+  t.nnz = a.nnz;
+  t.rp_buf.assign((size_t)a.n_cols + 1, 0);
+  t.ci_buf.resize((size_t)std::max<int64_t>(a.nnz, 1));
+  t.v_buf.resize((size_t)std::max<int64_t>(a.nnz, 1));
+  for (int64_t e = 0; e < a.nnz; ++e) t.rp_buf[a.ci[e] + 1]++;
+  for (int32_t c = 0; c < a.n_cols; ++c) t.rp_buf[c + 1] += t.rp_buf[c];
+  std::vector<int64_t> fill(t.rp_buf.begin(), t.rp_buf.end() - 1);
+  for (int64_t r = 0; r < a.n_rows; ++r)
+    for (int64_t e = a.rp[r]; e < a.rp[r + 1]; ++e) {
+      int64_t dst = fill[a.ci[e]]++;
+      t.ci_buf[dst] = (int32_t)r;
+      t.v_buf[dst] = a.v[e];
+    }
+  t.rp = t.rp_buf.data();
+  t.ci = t.ci_buf.data();
+  t.v = t.v_buf.data();
+}
+
+// Coarse pencil of an interpolation P: Galerkin products on the device, then
+// the dense generalised eigensolve on the host.
+int coarse_pencil(Handle& h, const CsrDev& P, const CsrDev& PT, std::vector<double>& lam, std::vector<double>& Phi) {
+  int rc = BPJD_OK;
+  const int nH = P.n_cols;
+  double *dKH = nullptr, *dMH = nullptr;
+  std::vector<double> KH((size_t)nH * nH), MH((size_t)nH * nH);
+  CK(cudaMalloc(&dKH, sizeof(double) * nH * nH));
+  CK(cudaMalloc(&dMH, sizeof(double) * nH * nH));
+  CKI(launch_galerkin(h.A, h.same_pattern ? CsrDev{h.A.n_rows, h.A.n_cols, h.A.nnz, h.A.row_ptr, h.A.col, h.M.val}
+                                          : h.M,
+                      P, PT, dKH, dMH, h.stream));
+  CK(cudaMemcpyAsync(KH.data(), dKH, sizeof(double) * nH * nH, cudaMemcpyDeviceToHost, h.stream));
+  CK(cudaMemcpyAsync(MH.data(), dMH, sizeof(double) * nH * nH, cudaMemcpyDeviceToHost, h.stream));
+  CK(cudaStreamSynchronize(h.stream));
+  for (int i = 0; i < nH; ++i)
+    for (int j = i + 1; j < nH; ++j) {
+      double a = 0.5 * (KH[(size_t)i * nH + j] + KH[(size_t)j * nH + i]);
+      KH[(size_t)i * nH + j] = KH[(size_t)j * nH + i] = a;
+      double b = 0.5 * (MH[(size_t)i * nH + j] + MH[(size_t)j * nH + i]);
+      MH[(size_t)i * nH + j] = MH[(size_t)j * nH + i] = b;
+    }
+  rc = gen_eig_host(nH, KH, MH, lam, Phi);
+fail:
+  cudaFree(dKH);
+  cudaFree(dMH);
+  return rc;
+}
+
+}  // namespace
+
+// ===========================================================================
+
+extern "C" void bpjd_default_opts(bpjd_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->k = 1;
+  o->precision = BPJD_FP64;
+  o->subspace = BPJD_W_2K;
+  o->stop_rule = BPJD_STOP_RESIDUAL;
+  o->tol = 1e-8;
+  o->max_iter = 500;
+  o->drop_tol = 1e-10;
+}
+
+extern "C" const char* bpjd_status_string(int c) {
+  switch (c) {
+    case BPJD_OK: return "ok";
+    case BPJD_ERR_BAD_ARG: return "bad argument";
+    case BPJD_ERR_CSR_INVALID: return "invalid CSR matrix";
+    case BPJD_ERR_MAP_INVALID: return "invalid subdomain map";
+    case BPJD_ERR_K_TOO_LARGE: return "k must be smaller than the coarse space dimension";
+    case BPJD_ERR_GAP: return "coarse eigenvalues k and k+1 coincide (Assumption 1)";
+    case BPJD_ERR_LOCAL_INDEFINITE: return "shifted local matrix not positive definite (Eq. (3.1))";
+    case BPJD_ERR_BREAKDOWN: return "Rayleigh-Ritz basis lost rank";
+    case BPJD_ERR_NOCONV: return "no convergence within max_iter";
+    case BPJD_ERR_OOM: return "device out of memory";
+    case BPJD_ERR_CUDA: return "CUDA error";
+    case BPJD_ERR_UNSUPPORTED: return "unsupported option";
+    default: return "unknown status";
+  }
+}
+
+extern "C" void bpjd_free(bpjd_handle* hh) {
+  if (!hh) return;
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  for (void* p : h->allocs) cudaFree(p);
+  for (void* e : h->ev_pool) cudaEventDestroy((cudaEvent_t)e);
+  if (h->hstat) cudaFreeHost(h->hstat);
+  delete h;
+}
+
+extern "C" int bpjd_setup(const bpjd_csr* A, const bpjd_csr* M, const bpjd_csr* P, const bpjd_csr* P0,
+                          const bpjd_partition* part, const bpjd_opts* opts, bpjd_handle** out) {
+  if (!out) return BPJD_ERR_BAD_ARG;
+  *out = nullptr;
+  if (!A || !M || !P || !part || !opts) return BPJD_ERR_BAD_ARG;
+  if (!A->row_ptr || !A->col_idx || !A->val || !M->row_ptr || !M->col_idx || !M->val || !P->row_ptr ||
+      !P->col_idx || !P->val || !part->sub_ptr || !part->sub_dofs)
+    return BPJD_ERR_BAD_ARG;
+  const int k = opts->k;
+  const int n = A->n_rows;
+  if (k < 1 || k > 32 || n < 1 || A->n_cols != n || M->n_rows != n || M->n_cols != n || P->n_rows != n ||
+      part->n_sub < 1)
+    return BPJD_ERR_BAD_ARG;
+  if (P0 && (P0->n_rows != n || !P0->row_ptr || !P0->col_idx || !P0->val)) return BPJD_ERR_BAD_ARG;
+  if (opts->precision != BPJD_FP64 && opts->precision != BPJD_MIXED) return BPJD_ERR_UNSUPPORTED;
+  if (opts->subspace != BPJD_W_2K && opts->subspace != BPJD_W_3K) return BPJD_ERR_UNSUPPORTED;
+  const int mmax = (opts->subspace == BPJD_W_3K) ? 3 * k : 2 * k;
+  if (mmax > 64) return BPJD_ERR_UNSUPPORTED;
+  const bool on_dev = opts->inputs_on_device != 0;
+  const double t0 = now_s();
+
+  Handle* h = new (std::nothrow) Handle();
+  if (!h) return BPJD_ERR_OOM;
+  int rc = BPJD_OK;
+  h->n = n;
+  h->k = k;
+  h->nsub = part->n_sub;
+  h->precision = opts->precision;
+  h->subspace = opts->subspace;
+  h->stop_rule = opts->stop_rule;
+  h->tol = opts->tol > 0 ? opts->tol : 1e-8;
+  h->max_iter = opts->max_iter > 0 ? opts->max_iter : 500;
+  h->drop_tol = opts->drop_tol > 0 ? opts->drop_tol : 1e-10;
+  h->stream = (cudaStream_t)opts->stream;
+
+  {
+    HostCsr hA, hM, hP, hP0, hPT, hP0T;
+    std::vector<int64_t> sub_ptr_buf;
+    std::vector<int32_t> sub_dofs_buf;
+    const int64_t* sptr;
+    const int32_t* sdofs;
+    const int nsub = part->n_sub;
+    std::vector<double> lamH, Phi, lam0H, Phi0;
+    int64_t sum_nl;
+    int bw = 0;
+    std::vector<int32_t> loc;
+    std::vector<int64_t> posK, posM;
+    int64_t* dposK = nullptr;
+    int64_t* dposM = nullptr;
+    std::vector<int32_t> rtp, rtpos;
+    CsrDev dP0, dP0T;
+    double* dPhi0 = nullptr;
+
+    if ((rc = host_view(A, on_dev, false, hA)) != BPJD_OK) goto fail;
+    if ((rc = host_view(M, on_dev, false, hM)) != BPJD_OK) goto fail;
+    if ((rc = host_view(P, on_dev, true, hP)) != BPJD_OK) goto fail;
+    if (P0 && (rc = host_view(P0, on_dev, true, hP0)) != BPJD_OK) goto fail;
+    if ((rc = validate_csr(hA)) != BPJD_OK) goto fail;
+    if ((rc = validate_csr(hM)) != BPJD_OK) goto fail;
+    if ((rc = validate_csr(hP)) != BPJD_OK) goto fail;
+    if (P0 && (rc = validate_csr(hP0)) != BPJD_OK) goto fail;
+    h->nH = P->n_cols;
+    h->nH0 = P0 ? P0->n_cols : P->n_cols;
+    if (!(k < h->nH) || !(k < h->nH0)) {
+      rc = BPJD_ERR_K_TOO_LARGE;
+      goto fail;
+    }
+    // partition
+    if (on_dev) {
+      sub_ptr_buf.resize(nsub + 1);
+      CK(cudaMemcpy(sub_ptr_buf.data(), part->sub_ptr, sizeof(int64_t) * (nsub + 1), cudaMemcpyDeviceToHost));
+      sub_dofs_buf.resize((size_t)std::max<int64_t>(sub_ptr_buf[nsub], 1));
+      if (sub_ptr_buf[nsub] > 0)
+        CK(cudaMemcpy(sub_dofs_buf.data(), part->sub_dofs, sizeof(int32_t) * sub_ptr_buf[nsub],
+                      cudaMemcpyDeviceToHost));
+      sptr = sub_ptr_buf.data();
+      sdofs = sub_dofs_buf.data();
+    } else {
+      sptr = part->sub_ptr;
+      sdofs = part->sub_dofs;
+    }
+    if (sptr[0] != 0) {
+      rc = BPJD_ERR_MAP_INVALID;
+      goto fail;
+    }
+    for (int l = 0; l < nsub; ++l) {
+      if (sptr[l + 1] <= sptr[l]) {
+        rc = BPJD_ERR_MAP_INVALID;
+        goto fail;
+      }
+      for (int64_t e = sptr[l]; e < sptr[l + 1]; ++e) {
+        if (sdofs[e] < 0 || sdofs[e] >= n || (e > sptr[l] && sdofs[e] <= sdofs[e - 1])) {
+          rc = BPJD_ERR_MAP_INVALID;
+          goto fail;
+        }
+      }
+      h->max_nl = std::max<int32_t>(h->max_nl, (int32_t)(sptr[l + 1] - sptr[l]));
+    }
+    sum_nl = sptr[nsub];
+    h->sum_nl = sum_nl;
+    h->same_pattern = (hA.nnz == hM.nnz) && std::equal(hA.rp, hA.rp + n + 1, hM.rp) &&
+                      std::equal(hA.ci, hA.ci + hA.nnz, hM.ci);
+
+    // device copies of the matrices and the partition
+    CK(upload_csr(*h, A, on_dev, h->A));
+    if (h->same_pattern) {
+      h->M = h->A;
+      h->M.val = nullptr;
+      CK(dalloc(*h, &h->M.val, (size_t)M->nnz));
+      CK(cudaMemcpyAsync(h->M.val, M->val, sizeof(double) * M->nnz,
+                         on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+    } else {
+      CK(upload_csr(*h, M, on_dev, h->M));
+    }
+    CK(upload_host_csr(*h, hP, h->P));
+    transpose_host(hP, hPT);
+    CK(upload_host_csr(*h, hPT, h->PT));
+    CK(dalloc(*h, &h->sub_ptr, (size_t)nsub + 1));
+    CK(dalloc(*h, &h->sub_dofs, (size_t)sum_nl));
+    CK(cudaMemcpyAsync(h->sub_ptr, sptr, sizeof(int64_t) * (nsub + 1), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->sub_dofs, sdofs, sizeof(int32_t) * sum_nl, cudaMemcpyHostToDevice, h->stream));
+
+    // band structure of every local matrix (principal submatrix on the subdomain dofs)
+    loc.assign(n, -1);
+    for (int l = 0; l < nsub; ++l) {
+      const int32_t* d = sdofs + sptr[l];
+      const int nl = (int)(sptr[l + 1] - sptr[l]);
+      for (int p = 0; p < nl; ++p) loc[d[p]] = p;
+      for (int p = 0; p < nl; ++p) {
+        for (int64_t e = hA.rp[d[p]]; e < hA.rp[d[p] + 1]; ++e) {
+          int q = loc[hA.ci[e]];
+          if (q >= 0 && q <= p) bw = std::max(bw, p - q);
+        }
+        if (!h->same_pattern)
+          for (int64_t e = hM.rp[d[p]]; e < hM.rp[d[p] + 1]; ++e) {
+            int q = loc[hM.ci[e]];
+            if (q >= 0 && q <= p) bw = std::max(bw, p - q);
+          }
+      }
+      for (int p = 0; p < nl; ++p) loc[d[p]] = -1;
+    }
+    h->B = bw + 1;
+    {
+      const int B = h->B;
+      posK.assign((size_t)sum_nl * B, -1);
+      if (!h->same_pattern) posM.assign((size_t)sum_nl * B, -1);
+      for (int l = 0; l < nsub; ++l) {
+        const int64_t off = sptr[l];
+        const int32_t* d = sdofs + off;
+        const int nl = (int)(sptr[l + 1] - off);
+        for (int p = 0; p < nl; ++p) loc[d[p]] = p;
+        for (int p = 0; p < nl; ++p) {
+          for (int64_t e = hA.rp[d[p]]; e < hA.rp[d[p] + 1]; ++e) {
+            int q = loc[hA.ci[e]];
+            if (q >= 0 && q <= p) posK[(size_t)(off + p) * B + (q - p + bw)] = e;
+          }
+          if (!h->same_pattern)
+            for (int64_t e = hM.rp[d[p]]; e < hM.rp[d[p] + 1]; ++e) {
+              int q = loc[hM.ci[e]];
+              if (q >= 0 && q <= p) posM[(size_t)(off + p) * B + (q - p + bw)] = e;
+            }
+        }
+        for (int p = 0; p < nl; ++p) loc[d[p]] = -1;
+      }
+      CK(dalloc(*h, &h->bandK, (size_t)sum_nl * B));
+      CK(dalloc(*h, &h->bandM, (size_t)sum_nl * B));
+      if (h->precision == BPJD_MIXED) {
+        CK(dalloc(*h, &h->bandKf, (size_t)sum_nl * B));
+        CK(dalloc(*h, &h->bandMf, (size_t)sum_nl * B));
+      }
+      CK(cudaMalloc(&dposK, sizeof(int64_t) * sum_nl * B));
+      CK(cudaMemcpyAsync(dposK, posK.data(), sizeof(int64_t) * sum_nl * B, cudaMemcpyHostToDevice, h->stream));
+      CKI(launch_band_gather(*h, dposK, h->A.val, h->bandK, h->bandKf));
+      if (h->same_pattern) {
+        CKI(launch_band_gather(*h, dposK, h->M.val, h->bandM, h->bandMf));
+      } else {
+        CK(cudaMalloc(&dposM, sizeof(int64_t) * sum_nl * B));
+        CK(cudaMemcpyAsync(dposM, posM.data(), sizeof(int64_t) * sum_nl * B, cudaMemcpyHostToDevice, h->stream));
+        CKI(launch_band_gather(*h, dposM, h->M.val, h->bandM, h->bandMf));
+      }
+    }
+    // inverse map dof -> packed local positions, ascending subdomain order
+    rtp.assign((size_t)n + 1, 0);
+    for (int64_t e = 0; e < sum_nl; ++e) rtp[sdofs[e] + 1]++;
+    for (int g = 0; g < n; ++g) rtp[g + 1] += rtp[g];
+    rtpos.resize((size_t)sum_nl);
+    {
+      std::vector<int32_t> fill(rtp.begin(), rtp.end() - 1);
+      for (int64_t e = 0; e < sum_nl; ++e) rtpos[fill[sdofs[e]]++] = (int32_t)e;
+    }
+    CK(dalloc(*h, &h->rt_ptr, (size_t)n + 1));
+    CK(dalloc(*h, &h->rt_pos, (size_t)sum_nl));
+    CK(cudaMemcpyAsync(h->rt_ptr, rtp.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->rt_pos, rtpos.data(), sizeof(int32_t) * sum_nl, cudaMemcpyHostToDevice, h->stream));
+
+    // coarse pencil and its eigenbasis
+    if ((rc = coarse_pencil(*h, h->P, h->PT, lamH, Phi)) != BPJD_OK) goto fail;
+    if ((lamH[k] - lamH[k - 1]) <= 1e-8 * std::fabs(lamH[k])) {
+      rc = BPJD_ERR_GAP;
+      goto fail;
+    }
+    CK(dalloc(*h, &h->Phi, (size_t)h->nH * h->nH));
+    CK(dalloc(*h, &h->lamH, (size_t)h->nH));
+    CK(cudaMemcpyAsync(h->Phi, Phi.data(), sizeof(double) * h->nH * h->nH, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->lamH, lamH.data(), sizeof(double) * h->nH, cudaMemcpyHostToDevice, h->stream));
+    // initial guess X0 = P0 Phi0[:, :k] (Step 1)
+    CK(dalloc(*h, &h->X0, (size_t)n * k));
+    CK(dalloc(*h, &h->lam0, (size_t)k));
+    if (P0) {
+      Handle tmp;  // allocations of the temporary coarse space are released below
+      tmp.stream = h->stream;
+      CK(upload_host_csr(tmp, hP0, dP0));
+      transpose_host(hP0, hP0T);
+      CK(upload_host_csr(tmp, hP0T, dP0T));
+      tmp.A = h->A;
+      tmp.M = h->M;
+      tmp.same_pattern = h->same_pattern;
+      rc = coarse_pencil(tmp, dP0, dP0T, lam0H, Phi0);
+      if (rc == BPJD_OK && (lam0H[k] - lam0H[k - 1]) <= 1e-8 * std::fabs(lam0H[k])) rc = BPJD_ERR_GAP;
+      if (rc == BPJD_OK && cudaMalloc(&dPhi0, sizeof(double) * h->nH0 * h->nH0) != cudaSuccess) rc = BPJD_ERR_OOM;
+      if (rc == BPJD_OK &&
+          cudaMemcpyAsync(dPhi0, Phi0.data(), sizeof(double) * h->nH0 * h->nH0, cudaMemcpyHostToDevice,
+                          h->stream) != cudaSuccess)
+        rc = BPJD_ERR_CUDA;
+      if (rc == BPJD_OK && launch_csr_times_dense(dP0, dPhi0, h->nH0, k, h->X0, k, h->stream) != 0)
+        rc = BPJD_ERR_CUDA;
+      cudaStreamSynchronize(h->stream);
+      for (void* p : tmp.allocs) cudaFree(p);
+      cudaFree(dPhi0);
+      if (rc != BPJD_OK) goto fail;
+    } else {
+      CKI(launch_csr_times_dense(h->P, h->Phi, h->nH, k, h->X0, k, h->stream));
+    }
+
+    // scratch and iteration vectors
+    {
+      const size_t esz = (h->precision == BPJD_MIXED) ? sizeof(float) : sizeof(double);
+      void* p;
+      CK(cudaMalloc(&p, esz * (size_t)sum_nl * k * h->B));
+      h->allocs.push_back(p);
+      h->bytes += esz * (size_t)sum_nl * k * h->B;
+      h->Lbuf = p;
+      CK(cudaMalloc(&p, esz * (size_t)sum_nl * k));
+      h->allocs.push_back(p);
+      h->bytes += esz * (size_t)sum_nl * k;
+      h->wpk = p;
+    }
+    CK(dalloc(*h, &h->cH, (size_t)h->nH * k));
+    CK(dalloc(*h, &h->aH, (size_t)h->nH * k));
+    CK(dalloc(*h, &h->w0, (size_t)h->nH * k));
+    {
+      double** vecs[] = {&h->X, &h->AX, &h->MX, &h->Xn, &h->AXn, &h->MXn,
+                         &h->T, &h->AT, &h->MT, &h->Pd, &h->APd, &h->MPd, &h->rho, &h->Z,
+                         &h->Pd2, &h->APd2, &h->MPd2};
+      for (double** v : vecs) CK(dalloc(*h, v, (size_t)n * k));
+    }
+    CK(dalloc(*h, &h->lam, (size_t)2 * k));
+    CK(dalloc(*h, &h->partial, (size_t)456 * 96 * 96));
+    CK(dalloc(*h, &h->small, (size_t)5 * 96 * 96));
+    h->hist_rows = h->max_iter + 1;
+    CK(dalloc(*h, &h->hist, (size_t)h->hist_rows * k));
+    CK(dalloc(*h, &h->dstat, 1));
+    CK(dalloc(*h, &h->derr, 4));
+    CK(cudaMallocHost(&h->hstat, sizeof(DevStatus)));
+    CK(cudaStreamSynchronize(h->stream));
+    if (dposK) cudaFree(dposK);
+    if (dposM) cudaFree(dposM);
+    dposK = dposM = nullptr;
+    (void)t0;
+    *out = reinterpret_cast<bpjd_handle*>(h);
+    return BPJD_OK;
+  fail:
+    if (dposK) cudaFree(dposK);
+    if (dposM) cudaFree(dposM);
+  }
+  bpjd_free(reinterpret_cast<bpjd_handle*>(h));
+  return rc;
+}
+
+namespace {
+
+// sign normalisation: flip each column so its largest-magnitude entry is
+// positive (lowest row index wins ties)
+__global__ void k_sign_normalise(int n, int k, double* X) {
+  __shared__ double bv[256];
+  __shared__ int bi[256];
+  const int col = blockIdx.x;
+  double best = -1;
+  int bidx = n;
+  for (int r = threadIdx.x; r < n; r += blockDim.x) {
+    double a = fabs(X[(int64_t)r * k + col]);
+    if (a > best) {
+      best = a;
+      bidx = r;
+    }
+  }
+  bv[threadIdx.x] = best;
+  bi[threadIdx.x] = bidx;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+      double o = bv[threadIdx.x + w];
+      int oi = bi[threadIdx.x + w];
+      if (o > bv[threadIdx.x] || (o == bv[threadIdx.x] && oi < bi[threadIdx.x])) {
+        bv[threadIdx.x] = o;
+        bi[threadIdx.x] = oi;
+      }
+    }
+    __syncthreads();
+  }
+  const bool flip = X[(int64_t)bi[0] * k + col] < 0;
+  if (flip)
+    for (int r = threadIdx.x; r < n; r += blockDim.x) X[(int64_t)r * k + col] = -X[(int64_t)r * k + col];
+}
+
+}  // namespace
+
+extern "C" int bpjd_solve(bpjd_handle* hh, double* eigvals, double* eigvecs, int32_t eigvecs_on_device,
+                          bpjd_stats* st) {
+  if (!hh) return BPJD_ERR_BAD_ARG;
+  Handle& h = *reinterpret_cast<Handle*>(hh);
+  const int n = h.n, k = h.k;
+  const size_t vbytes = sizeof(double) * (size_t)n * k;
+  int rc = BPJD_OK;
+  const double t0 = now_s();
+  int it = 0;
+  bool converged = false;
+  double* lam_cur = h.lam;
+  double* lam_nxt = h.lam + k;
+  double* C1 = h.small;                 // k x k
+  double* G = h.small + 2 * 96 * 96;    // m x m
+  double* Hm = h.small + 3 * 96 * 96;   // m x m
+  double* Crr = h.small + 4 * 96 * 96;  // m x k
+  double *X = h.X, *AX = h.AX, *MX = h.MX;
+  double *Xn = h.Xn, *AXn = h.AXn, *MXn = h.MXn;
+  double *Pc = h.Pd, *APc = h.APd, *MPc = h.MPd;      // current P block (3k)
+  double *Pn = h.Pd2, *APn = h.APd2, *MPn = h.MPd2;   // next P block
+  bool have_prev = false;
+
+  CK(cudaMemsetAsync(h.dstat, 0, sizeof(DevStatus), h.stream));
+  CK(cudaMemsetAsync(h.derr, 0, 4 * sizeof(int32_t), h.stream));
+  CK(cudaMemcpyAsync(X, h.X0, vbytes, cudaMemcpyDeviceToDevice, h.stream));
+  CKI(launch_spmm(h, X, AX, MX, k));
+  CKI(launch_rayleigh(h, X, AX, MX, lam_cur));
+  CK(cudaMemcpyAsync(h.hist, lam_cur, sizeof(double) * k, cudaMemcpyDeviceToDevice, h.stream));
+  for (;;) {
+    CKI(launch_residual(h, AX, MX, lam_cur, h.rho));
+    CK(cudaMemcpyAsync(h.hstat, h.dstat, sizeof(DevStatus), cudaMemcpyDeviceToHost, h.stream));
+    int32_t herr[4];
+    CK(cudaMemcpyAsync(herr, h.derr, sizeof(herr), cudaMemcpyDeviceToHost, h.stream));
+    CK(cudaStreamSynchronize(h.stream));
+    if (herr[0]) {
+      rc = BPJD_ERR_LOCAL_INDEFINITE;
+      break;
+    }
+    if (h.hstat->err_breakdown) {
+      rc = BPJD_ERR_BREAKDOWN;
+      break;
+    }
+    if (h.hstat->converged) {
+      converged = true;
+      break;
+    }
+    if (it >= h.max_iter) {
+      rc = BPJD_ERR_NOCONV;
+      break;
+    }
+    // Step 2: t_i = (I - X X^T M) (B_i)^{-1} r_i
+    CKI(launch_precond(h, h.rho, lam_cur, h.Z));
+    {
+      const double* U[1] = {MX};
+      const double* V[1] = {h.Z};
+      CKI(launch_inner(h, 1, U, 1, V, C1));
+      const double* Win[1] = {X};
+      CKI(launch_combine_rows(h, 1, Win, C1, k, k, h.Z, h.T, -1.0));
+    }
+    CKI(launch_spmm(h, h.T, h.AT, h.MT, k));
+    // Step 3: Rayleigh-Ritz in W = U^k + span{t} (+ U^{k-1})
+    int nb;
+    const double *W[3], *AW[3], *MW[3];
+    W[0] = X;
+    AW[0] = AX;
+    MW[0] = MX;
+    if (h.subspace == BPJD_W_3K && have_prev) {
+      // span{X, P} = U^k + U^{k-1}: P is the part of the previous update outside X
+      W[1] = Pc;
+      AW[1] = APc;
+      MW[1] = MPc;
+      W[2] = h.T;
+      AW[2] = h.AT;
+      MW[2] = h.MT;
+      nb = 3;
+    } else {
+      W[1] = h.T;
+      AW[1] = h.AT;
+      MW[1] = h.MT;
+      nb = 2;
+    }
+    const int m = nb * k;
+    CKI(launch_inner(h, nb, W, nb, MW, G));
+    CKI(launch_inner(h, nb, W, nb, AW, Hm));
+    CKI(launch_rr(h, m, G, Hm, lam_cur, Crr, lam_nxt, it + 1));
+    CKI(launch_combine_rows(h, nb, W, Crr, k, k, nullptr, Xn, 1.0));
+    CKI(launch_spmm(h, Xn, AXn, MXn, k));
+    if (h.subspace == BPJD_W_3K) {
+      // P_new = W[:, k:] C[k:, :], with K P_new and M P_new by SpMM (no cancellation)
+      CKI(launch_combine_rows(h, nb - 1, W + 1, Crr + (size_t)k * k, k, k, nullptr, Pn, 1.0));
+      CKI(launch_spmm(h, Pn, APn, MPn, k));
+      std::swap(Pc, Pn);
+      std::swap(APc, APn);
+      std::swap(MPc, MPn);
+    }
+    // the new iterate becomes the current one
+    std::swap(X, Xn);
+    std::swap(AX, AXn);
+    std::swap(MX, MXn);
+    std::swap(lam_cur, lam_nxt);
+    have_prev = true;
+    ++it;
+  }
+  if (rc == BPJD_OK || rc == BPJD_ERR_NOCONV) {
+    k_sign_normalise<<<k, 256, 0, h.stream>>>(n, k, X);
+    h.launches += 1;
+    CK(cudaGetLastError());
+    if (eigvals) CK(cudaMemcpyAsync(eigvals, lam_cur, sizeof(double) * k, cudaMemcpyDeviceToHost, h.stream));
+    if (eigvecs)
+      CK(cudaMemcpyAsync(eigvecs, X, vbytes, eigvecs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                         h.stream));
+    CK(cudaStreamSynchronize(h.stream));
+  }
+  h.last_iters = it;
+  if (st) {
+    st->iters = it;
+    st->converged = converged ? 1 : 0;
+    st->max_rel_resid = h.hstat->max_res;
+    st->sum_abs_dlambda = h.hstat->sum_dl;
+    st->t_setup_s = 0;
+    st->t_solve_s = now_s() - t0;
+    st->status = rc;
+  }
+  // keep the handle's notion of the current buffers consistent for the next call
+  h.X = X;
+  h.AX = AX;
+  h.MX = MX;
+  h.Xn = Xn;
+  h.AXn = AXn;
+  h.MXn = MXn;
+  return rc;
+fail:
+  if (st) st->status = rc;
+  return rc;
+}
+
+extern "C" int bpjd_dims(const bpjd_handle* hh, int32_t* n, int32_t* nH, int32_t* k) {
+  if (!hh) return BPJD_ERR_BAD_ARG;
+  const Handle& h = *reinterpret_cast<const Handle*>(hh);
+  if (n) *n = h.n;
+  if (nH) *nH = h.nH;
+  if (k) *k = h.k;
+  return BPJD_OK;
+}
+
+extern "C" int bpjd_layout(const bpjd_handle* hh, int32_t* B, int64_t* sum_nl, int32_t* nsub, int64_t* nnz) {
+  if (!hh) return BPJD_ERR_BAD_ARG;
+  const Handle& h = *reinterpret_cast<const Handle*>(hh);
+  if (B) *B = h.B;
+  if (sum_nl) *sum_nl = h.sum_nl;
+  if (nsub) *nsub = h.nsub;
+  if (nnz) *nnz = h.A.nnz;
+  return BPJD_OK;
+}
+
+extern "C" int bpjd_spmm(bpjd_handle* hh, const double* X, double* YA, double* YM, int32_t ncols) {
+  if (!hh || !X || !YA || !YM || ncols < 1 || ncols > 64) return BPJD_ERR_BAD_ARG;
+  Handle& h = *reinterpret_cast<Handle*>(hh);
+  if (launch_spmm(h, X, YA, YM, ncols) != 0) return BPJD_ERR_CUDA;
+  return BPJD_OK;
+}
+
+extern "C" int bpjd_apply_preconditioner(bpjd_handle* hh, const double* rho, const double* lam, double* Z) {
+  if (!hh || !rho || !lam || !Z) return BPJD_ERR_BAD_ARG;
+  Handle& h = *reinterpret_cast<Handle*>(hh);
+  int rc = BPJD_OK;
+  int32_t herr[4];
+  CK(cudaMemsetAsync(h.derr, 0, 4 * sizeof(int32_t), h.stream));
+  CKI(launch_precond(h, rho, lam, Z));
+  CK(cudaMemcpyAsync(herr, h.derr, sizeof(herr), cudaMemcpyDeviceToHost, h.stream));
+  CK(cudaStreamSynchronize(h.stream));
+  if (herr[0]) return BPJD_ERR_LOCAL_INDEFINITE;
+  return BPJD_OK;
+fail:
+  return rc;
+}
+
+extern "C" int bpjd_history(const bpjd_handle* hh, double* lam_hist, int32_t cap) {
+  if (!hh || !lam_hist || cap < 0) return BPJD_ERR_BAD_ARG;
+  const Handle& h = *reinterpret_cast<const Handle*>(hh);
+  int rows = std::min(cap, std::min(h.last_iters + 1, h.hist_rows));
+  if (rows <= 0) return 0;
+  if (cudaMemcpy(lam_hist, h.hist, sizeof(double) * rows * h.k, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return BPJD_ERR_CUDA;
+  return rows;
+}
+
+extern "C" int bpjd_profile(bpjd_handle* hh, int32_t enable) {
+  if (!hh) return BPJD_ERR_BAD_ARG;
+  Handle& h = *reinterpret_cast<Handle*>(hh);
+  prof_flush(h);
+  h.profile = enable != 0;
+  for (int c = 0; c < BPJD_PROF_N; ++c) {
+    h.prof_ms[c] = 0;
+    h.prof_count[c] = 0;
+  }
+  h.launches = 0;
+  return BPJD_OK;
+}
+
+extern "C" int bpjd_profile_read(bpjd_handle* hh, double* ms, int64_t* count, int64_t* launches) {
+  if (!hh) return BPJD_ERR_BAD_ARG;
+  Handle& h = *reinterpret_cast<Handle*>(hh);
+  prof_flush(h);
+  for (int c = 0; c < BPJD_PROF_N; ++c) {
+    if (ms) ms[c] = h.prof_ms[c];
+    if (count) count[c] = h.prof_count[c];
+  }
+  if (launches) *launches = h.launches;
+  return BPJD_OK;
+}
+
+extern "C" size_t bpjd_device_bytes(const bpjd_handle* hh) {
+  if (!hh) return 0;
+  return reinterpret_cast<const Handle*>(hh)->bytes;
+}

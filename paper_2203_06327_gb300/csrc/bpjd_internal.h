@@ -1,0 +1,142 @@
+// Internal declarations shared by the library's translation units.
+#ifndef BPJD_INTERNAL_H_
+#define BPJD_INTERNAL_H_
+
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include "bpjd.h"
+
+#ifdef __CUDACC__
+#include <cuda_runtime.h>
+#else
+typedef struct CUstream_st* cudaStream_t;
+#endif
+
+namespace bpjd {
+
+// Device-side status written by the reduction kernels; copied to pinned host
+// memory once per iteration.
+struct DevStatus {
+  double max_res;       // max relative residual of the current iterate
+  double sum_dl;        // sum |lambda^{k+1} - lambda^k| of the last Rayleigh-Ritz step
+  int32_t converged;    // stop rule satisfied
+  int32_t err_local;    // a local pivot was <= 0
+  int32_t err_breakdown;// Rayleigh-Ritz kept fewer than k directions
+  int32_t kept;         // directions kept by the last Rayleigh-Ritz step
+  double res[64];       // per-column relative residuals
+};
+
+struct CsrDev {
+  int32_t n_rows = 0, n_cols = 0;
+  int64_t nnz = 0;
+  int64_t* row_ptr = nullptr;
+  int32_t* col = nullptr;
+  double* val = nullptr;
+};
+
+struct Handle {
+  // ---- sizes and options
+  int32_t n = 0, nH = 0, nH0 = 0, k = 0, nsub = 0;
+  int32_t B = 0;            // band window: lower bandwidth + 1 (max over subdomains)
+  int64_t sum_nl = 0;       // sum of local sizes
+  int32_t max_nl = 0;
+  int32_t precision = BPJD_FP64, subspace = BPJD_W_2K, stop_rule = BPJD_STOP_RESIDUAL;
+  int32_t max_iter = 500;
+  double tol = 1e-8, drop_tol = 1e-10;
+  cudaStream_t stream = nullptr;
+
+  // ---- matrices
+  CsrDev A, M;              // M may share A's pattern arrays (same_pattern)
+  bool same_pattern = false;
+  CsrDev P, PT;             // coarse interpolation and its transpose
+  double* Phi = nullptr;    // n_H x n_H row-major, M_H-orthonormal eigenvectors
+  double* lamH = nullptr;   // n_H ascending
+  double* X0 = nullptr;     // initial guess n x k
+  double* lam0 = nullptr;   // k
+
+  // ---- subdomains
+  int64_t* sub_ptr = nullptr;
+  int32_t* sub_dofs = nullptr;
+  int32_t* rt_ptr = nullptr;   // n + 1: inverse map dof -> packed local positions
+  int32_t* rt_pos = nullptr;   // sum_nl, packed position sub_ptr[l] + p
+  double* bandK = nullptr;     // sum_nl x B, row p holds K_l(p, p-B+1 .. p)
+  double* bandM = nullptr;
+  float* bandKf = nullptr;     // FP32 copies for the mixed path
+  float* bandMf = nullptr;
+
+  // ---- scratch
+  void* Lbuf = nullptr;        // band factors, sum_nl * k * B elements (FP32 or FP64)
+  void* wpk = nullptr;         // packed local solutions sum_nl x k (FP32 or FP64)
+  double* cH = nullptr;        // n_H x k coarse restriction
+  double* aH = nullptr;        // n_H x k coarse coordinates
+  double* w0 = nullptr;        // n_H x k coarse correction
+
+  // ---- iteration vectors, n x k row-major FP64
+  double *X = nullptr, *AX = nullptr, *MX = nullptr;
+  double *Xn = nullptr, *AXn = nullptr, *MXn = nullptr;   // next iterate
+  double *T = nullptr, *AT = nullptr, *MT = nullptr;
+  double *Pd = nullptr, *APd = nullptr, *MPd = nullptr;   // previous-update block (3k)
+  double *Pd2 = nullptr, *APd2 = nullptr, *MPd2 = nullptr;
+  double *rho = nullptr, *Z = nullptr;
+  double* lam = nullptr;       // k
+  double* partial = nullptr;   // block partial sums
+  double* small = nullptr;     // small dense matrices (Gram, C, ...)
+  double* hist = nullptr;      // (max_iter + 1) x k Ritz values
+  int32_t hist_rows = 0;
+  DevStatus* dstat = nullptr;
+  DevStatus* hstat = nullptr;  // pinned host mirror
+  int32_t* derr = nullptr;     // device error flags
+
+  // ---- instrumentation
+  bool profile = false;
+  std::vector<void*> ev_pool;  // cudaEvent_t
+  size_t ev_used = 0;
+  std::vector<int> ev_cls;     // class of each recorded pair
+  double prof_ms[BPJD_PROF_N] = {0};
+  int64_t prof_count[BPJD_PROF_N] = {0};
+  int64_t launches = 0;        // kernels launched by the library
+
+  size_t bytes = 0;            // device bytes held
+  std::vector<void*> allocs;   // every device allocation (freed in bpjd_free)
+  int64_t n_partial_blocks = 0;
+  int last_iters = 0;
+};
+
+// Records an event pair around a kernel-class launch when profiling is on.
+struct ProfScope {
+  Handle& h;
+  int cls;
+  size_t idx;
+  bool on;
+  ProfScope(Handle& hh, int c);
+  ~ProfScope();
+};
+// Resolves recorded event pairs into prof_ms/prof_count (synchronises the stream).
+void prof_flush(Handle& h);
+
+// dense.cpp
+int sym_eig_host(int n, std::vector<double> A, std::vector<double>& lam, std::vector<double>& V);
+int gen_eig_host(int n, const std::vector<double>& K, const std::vector<double>& M, std::vector<double>& lam,
+                 std::vector<double>& Phi);
+
+// kernels.cu launchers (all asynchronous on h.stream; return cudaError_t as int)
+int launch_spmm(Handle& h, const double* X, double* YA, double* YM, int ncols);
+int launch_csr_times_dense(const CsrDev& P, const double* D, int ldd, int ncols, double* Y, int ldy,
+                           cudaStream_t s);
+int launch_residual(Handle& h, const double* AX, const double* MX, const double* lam, double* rho);
+int launch_rayleigh(Handle& h, const double* X, const double* AX, const double* MX, double* lam);
+int launch_precond(Handle& h, const double* rho, const double* lam, double* Z);
+int launch_inner(Handle& h, int p, const double* const* U, int q, const double* const* V, double* out);
+int launch_combine_rows(Handle& h, int nin, const double* const* Win, const double* C, int ldc,
+                        int csub, const double* Zadd, double* out, double alpha);
+int launch_rr(Handle& h, int m, const double* G, const double* Hm, const double* lam_old, double* C,
+              double* lam_new, int hist_row);
+int launch_band_gather(Handle& h, const int64_t* pos, const double* val, double* out, float* outf);
+int launch_galerkin(const CsrDev& A, const CsrDev& Msp, const CsrDev& P, const CsrDev& PT, double* KH,
+                    double* MH, cudaStream_t s);
+
+}  // namespace bpjd
+
+#endif  // BPJD_INTERNAL_H_

@@ -1,0 +1,983 @@
+// CUDA kernels of one BPJD iteration (Section 3, Algorithm 3.1) for sm_103a.
+//
+// Layout: every block of k vectors is row-major n x k (k contiguous per dof),
+// FP64.  Reductions over the n rows are done in two deterministic stages
+// (fixed per-block partial sums, then a per-entry sum over the blocks), so a
+// run is bit-reproducible for a given launch configuration.
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <new>
+#include <type_traits>
+
+#include "bpjd_internal.h"
+
+namespace bpjd {
+
+namespace {
+
+constexpr int kPartialBlocks = 456;  // 3 x 152 SMs
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// CSR SpMM over a block of vectors: YA = A X and (optionally) YM = M X with a
+// shared pattern.  LANES consecutive lanes serve one row; lane j of the group
+// owns columns j, j + LANES, ... (at most 2 per lane).  The row's column
+// indices and values are broadcast to the group; X rows are read as contiguous
+// ncols-vectors.
+// ---------------------------------------------------------------------------
+template <int LANES>
+__global__ void __launch_bounds__(256) k_spmm(int n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                              const double* __restrict__ va, const double* __restrict__ vm,
+                                              const double* __restrict__ X, double* __restrict__ YA,
+                                              double* __restrict__ YM, int ncols) {
+  constexpr int RPW = 32 / LANES;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t row = warp * RPW + lane / LANES;
+  const int j0 = lane % LANES;
+  if (row >= n) return;
+  double a0 = 0, a1 = 0, m0 = 0, m1 = 0;
+  const int j1 = j0 + LANES;
+  const bool has0 = j0 < ncols, has1 = j1 < ncols;
+  for (int64_t e = rp[row]; e < rp[row + 1]; ++e) {
+    const int64_t c = ci[e];
+    const double av = va[e];
+    const double mv = vm ? vm[e] : 0.0;
+    const double* xr = X + c * ncols;
+    if (has0) {
+      double x = xr[j0];
+      a0 = fma(av, x, a0);
+      m0 = fma(mv, x, m0);
+    }
+    if (has1) {
+      double x = xr[j1];
+      a1 = fma(av, x, a1);
+      m1 = fma(mv, x, m1);
+    }
+  }
+  if (has0) {
+    YA[row * ncols + j0] = a0;
+    if (YM) YM[row * ncols + j0] = m0;
+  }
+  if (has1) {
+    YA[row * ncols + j1] = a1;
+    if (YM) YM[row * ncols + j1] = m1;
+  }
+}
+
+// Y[r, j] = sum_e P[r, c_e] D[c_e, j] for j < ncols (sparse times small dense).
+__global__ void k_csr_dense(int n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                            const double* __restrict__ pv, const double* __restrict__ D, int ldd, int ncols,
+                            double* __restrict__ Y, int ldy) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)n * ncols) return;
+  int64_t r = t / ncols;
+  int j = (int)(t % ncols);
+  double acc = 0;
+  for (int64_t e = rp[r]; e < rp[r + 1]; ++e) acc = fma(pv[e], D[(int64_t)ci[e] * ldd + j], acc);
+  Y[r * ldy + j] = acc;
+}
+
+// ---------------------------------------------------------------------------
+// Column sums in two stages.  Block size is a multiple of k and so is the grid
+// stride, hence thread t always works on column t % k.
+// ---------------------------------------------------------------------------
+__device__ void block_column_partials(double acc0, double acc1, int k, double* partial /* [blocks][2k] */) {
+  extern __shared__ double sred[];
+  const int tid = threadIdx.x;
+  sred[tid] = acc0;
+  sred[blockDim.x + tid] = acc1;
+  __syncthreads();
+  if (tid < k) {
+    double s0 = 0, s1 = 0;
+    for (int t = tid; t < (int)blockDim.x; t += k) {
+      s0 += sred[t];
+      s1 += sred[blockDim.x + t];
+    }
+    partial[(int64_t)blockIdx.x * 2 * k + tid] = s0;
+    partial[(int64_t)blockIdx.x * 2 * k + k + tid] = s1;
+  }
+}
+
+// rho = lam .* MX - AX, and per-column partial sums of rho^2 and MX^2.
+__global__ void k_residual(int64_t nk, int k, const double* __restrict__ AX, const double* __restrict__ MX,
+                           const double* __restrict__ lam, double* __restrict__ rho, double* partial) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int col = (int)(t % k);
+  const double l = lam[col];
+  double r2 = 0, m2 = 0;
+  for (; t < nk; t += stride) {
+    double mx = MX[t];
+    double r = l * mx - AX[t];
+    rho[t] = r;
+    r2 = fma(r, r, r2);
+    m2 = fma(mx, mx, m2);
+  }
+  block_column_partials(r2, m2, k, partial);
+}
+
+// x . Ax and x . Mx per column.
+__global__ void k_rq_partial(int64_t nk, int k, const double* __restrict__ X, const double* __restrict__ AX,
+                             const double* __restrict__ MX, double* partial) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double s0 = 0, s1 = 0;
+  for (; t < nk; t += stride) {
+    double x = X[t];
+    s0 = fma(x, AX[t], s0);
+    s1 = fma(x, MX[t], s1);
+  }
+  block_column_partials(s0, s1, k, partial);
+}
+
+__global__ void k_residual_finish(int nblk, int k, const double* partial, const double* lam, int stop_rule,
+                                  double tol, DevStatus* st) {
+  __shared__ double res[64];
+  int i = threadIdx.x;
+  if (i < k) {
+    double r2 = 0, m2 = 0;
+    for (int b = 0; b < nblk; ++b) {
+      r2 += partial[(int64_t)b * 2 * k + i];
+      m2 += partial[(int64_t)b * 2 * k + k + i];
+    }
+    double r = sqrt(r2) / (fabs(lam[i]) * sqrt(m2));
+    res[i] = r;
+    st->res[i] = r;
+  }
+  __syncthreads();
+  if (i == 0) {
+    double mx = 0;
+    for (int j = 0; j < k; ++j) mx = fmax(mx, res[j]);
+    st->max_res = mx;
+    if (stop_rule == BPJD_STOP_RESIDUAL) st->converged = (mx <= tol) ? 1 : 0;
+  }
+}
+
+__global__ void k_rq_finish(int nblk, int k, const double* partial, double* lam) {
+  int i = threadIdx.x;
+  if (i < k) {
+    double a = 0, m = 0;
+    for (int b = 0; b < nblk; ++b) {
+      a += partial[(int64_t)b * 2 * k + i];
+      m += partial[(int64_t)b * 2 * k + k + i];
+    }
+    lam[i] = a / m;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Block inner products out = U^T V with U = [U_0 .. U_{p-1}], V = [V_0 .. V_{q-1}],
+// each U_b, V_b an n x k row-major array.  Stage 1 writes per-block partials.
+// ---------------------------------------------------------------------------
+struct Ptrs6 {
+  const double* p[6];
+};
+constexpr int kInnerRows = 16;
+constexpr int kInnerMaxOut = 36;  // (96 x 96) / 256
+
+__global__ void __launch_bounds__(256) k_inner(int n, int k, int p, Ptrs6 U, int q, Ptrs6 V, int rows_per_block,
+                                               double* partial) {
+  extern __shared__ double sm[];
+  const int mu = p * k, mv = q * k;
+  double* Us = sm;                       // [kInnerRows][mu]
+  double* Vs = sm + kInnerRows * mu;     // [kInnerRows][mv]
+  const int nout = mu * mv;
+  double acc[kInnerMaxOut];
+#pragma unroll
+  for (int o = 0; o < kInnerMaxOut; ++o) acc[o] = 0;
+  const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
+  const int64_t r1 = min((int64_t)n, r0 + rows_per_block);
+  for (int64_t rb = r0; rb < r1; rb += kInnerRows) {
+    const int nr = (int)min((int64_t)kInnerRows, r1 - rb);
+    for (int t = threadIdx.x; t < kInnerRows * mu; t += blockDim.x) {
+      int r = t / mu, c = t % mu;
+      Us[t] = (r < nr) ? U.p[c / k][(rb + r) * k + (c % k)] : 0.0;
+    }
+    for (int t = threadIdx.x; t < kInnerRows * mv; t += blockDim.x) {
+      int r = t / mv, c = t % mv;
+      Vs[t] = (r < nr) ? V.p[c / k][(rb + r) * k + (c % k)] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int oo = 0; oo < kInnerMaxOut; ++oo) {
+      int o = threadIdx.x + oo * blockDim.x;
+      if (o < nout) {
+        int a = o / mv, b = o % mv;
+        double s = acc[oo];
+        for (int r = 0; r < kInnerRows; ++r) s = fma(Us[r * mu + a], Vs[r * mv + b], s);
+        acc[oo] = s;
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int oo = 0; oo < kInnerMaxOut; ++oo) {
+    int o = threadIdx.x + oo * blockDim.x;
+    if (o < nout) partial[(int64_t)blockIdx.x * nout + o] = acc[oo];
+  }
+}
+
+__global__ void k_sum_partials(int nblk, int len, const double* partial, double* out) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= len) return;
+  double s = 0;
+  for (int b = 0; b < nblk; ++b) s += partial[(int64_t)b * len + j];
+  out[j] = s;
+}
+
+// out[r, j] = alpha_z * Zadd[r, j] + sign * sum_b sum_a W_b[r, a] C[(b k + a) * ldc + j]
+__global__ void k_combine_rows(int64_t n, int k, int nin, Ptrs6 W, const double* __restrict__ C, int ldc,
+                               int csub, const double* __restrict__ Zadd, double* __restrict__ out,
+                               double sign) {
+  extern __shared__ double Cs[];
+  const int m = nin * k;
+  for (int t = threadIdx.x; t < m * csub; t += blockDim.x) Cs[t] = C[(t / csub) * ldc + (t % csub)];
+  __syncthreads();
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n * csub) return;
+  int64_t r = t / csub;
+  int j = (int)(t % csub);
+  double acc = 0;
+  for (int b = 0; b < nin; ++b) {
+    const double* wr = W.p[b] + r * k;
+    for (int a = 0; a < k; ++a) acc = fma(wr[a], Cs[(b * k + a) * csub + j], acc);
+  }
+  double v = sign * acc;
+  if (Zadd) v += Zadd[r * csub + j];
+  out[r * csub + j] = v;
+}
+
+// ---------------------------------------------------------------------------
+// Local solves: one warp per (subdomain l, column i) computes
+//   w = (K_l - lambda_i M_l)^{-1} R_l rho_i
+// by a banded Cholesky factorisation streamed through a (B x B) window held
+// in shared memory (B = lower bandwidth + 1), with the forward substitution
+// fused into the factorisation and the band factor written to scratch for the
+// backward substitution.  The window is stored as a full symmetric B x B
+// block with circular row/column slots (slot of row p = p mod B); step j
+// eliminates row j, updates the remaining b rows by a rank-1 update and loads
+// row j + B of the shifted band matrix into the freed slot.  Rows past n_l
+// are identity rows.  A pivot <= 0 sets err (Eq. (3.1) violated).
+// ---------------------------------------------------------------------------
+template <typename TP>
+__global__ void k_local_band(int npairs, int k, const int64_t* __restrict__ sub_ptr,
+                             const int32_t* __restrict__ sub_dofs, int B, const TP* __restrict__ bandK,
+                             const TP* __restrict__ bandM, const double* __restrict__ lam,
+                             const double* __restrict__ rho, TP* __restrict__ Lbuf, TP* __restrict__ wpk,
+                             int32_t* err) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  const int pair = blockIdx.x * (blockDim.x >> 5) + wib;
+  if (pair >= npairs) return;
+  const int BB = B * B;
+  TP* W = reinterpret_cast<TP*>(smraw) + (size_t)wib * (BB + 3 * B);
+  TP* rw = W + BB;   // right-hand side window
+  TP* lc = rw + B;   // current column of L by slot
+  TP* xs = lc + B;   // solution window (backward sweep)
+  const int l = pair / k, i = pair % k;
+  const int64_t off = sub_ptr[l];
+  const int nl = (int)(sub_ptr[l + 1] - off);
+  const int32_t* dofs = sub_dofs + off;
+  const int b = B - 1;
+  const TP lm = (TP)lam[i];
+  TP* Lp = Lbuf + ((size_t)off * k + (size_t)i * nl) * B;
+  auto aval = [&](int p, int q) -> TP {  // shifted local matrix entry, q <= p <= q + b
+    if (p >= nl) return (p == q) ? TP(1) : TP(0);
+    const size_t e = (size_t)(off + p) * B + (q - p + b);
+    return bandK[e] - lm * bandM[e];
+  };
+  // initial window: rows 0..B-1
+  for (int e = lane; e < BB; e += 32) W[e] = TP(0);
+  __syncwarp();
+  for (int p = 0; p < B; ++p) {
+    for (int e = lane; e <= b; e += 32) {
+      int q = p - b + e;
+      if (q < 0) continue;
+      TP v = aval(p, q);
+      W[(p % B) * B + (q % B)] = v;
+      W[(q % B) * B + (p % B)] = v;
+    }
+    __syncwarp();
+  }
+  for (int p = lane; p < B; p += 32) rw[p] = (p < nl) ? (TP)rho[(int64_t)dofs[p] * k + i] : TP(0);
+  __syncwarp();
+  for (int j = 0; j < nl; ++j) {
+    const int s = j % B;
+    const TP piv = W[s * B + s];
+    if (!(piv > TP(0))) {
+      if (lane == 0) atomicOr(err, 1);
+      return;
+    }
+    const TP inv = TP(1) / sqrt(piv);
+    for (int u = lane; u < B; u += 32) lc[u] = (u == s) ? TP(0) : W[u * B + s] * inv;
+    const TP yj = rw[s] * inv;
+    __syncwarp();
+    // L column j: slot 0 = 1/L_jj, slot t = L(j + t, j)
+    for (int t = lane; t < B; t += 32) Lp[(size_t)j * B + t] = (t == 0) ? inv : lc[(j + t) % B];
+    if (lane == 0) wpk[(off + j) * k + i] = yj;
+    // rank-1 update of the window (row/column s is left alone: lc[s] = 0)
+    {
+      int e = lane, u = 0, v = lane;
+      while (v >= B) {
+        v -= B;
+        ++u;
+      }
+      for (; e < BB; e += 32) {
+        W[e] -= lc[u] * lc[v];
+        v += 32;
+        while (v >= B) {
+          v -= B;
+          ++u;
+        }
+      }
+    }
+    for (int u = lane; u < B; u += 32) rw[u] -= lc[u] * yj;
+    __syncwarp();
+    // load row j + B into slot s
+    const int pn = j + B;
+    for (int e = lane; e <= b; e += 32) {
+      int q = pn - b + e;  // q in j+1 .. j+B
+      TP v = aval(pn, q);
+      W[s * B + (q % B)] = v;
+      W[(q % B) * B + s] = v;
+    }
+    if (lane == 0) rw[s] = (pn < nl) ? (TP)rho[(int64_t)dofs[pn] * k + i] : TP(0);
+    __syncwarp();
+  }
+  // backward substitution with L^T
+  for (int u = lane; u < B; u += 32) xs[u] = TP(0);
+  __syncwarp();
+  for (int j = nl - 1; j >= 0; --j) {
+    const TP* row = Lp + (size_t)j * B;
+    TP part = 0;
+    for (int t = 1 + lane; t < B; t += 32) {
+      if (j + t < nl) part += row[t] * xs[(j + t) % B];
+    }
+    part = warp_sum(part);
+    if (lane == 0) {
+      TP xj = (wpk[(off + j) * k + i] - part) * row[0];
+      xs[j % B] = xj;
+      wpk[(off + j) * k + i] = xj;
+    }
+    __syncwarp();
+  }
+}
+
+// c[a, i] = sum_{g} P[g, a] rho[g, i] using P^T (CSR n_H x n); one block per coarse dof.
+__global__ void k_coarse_restrict(int nH, int k, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                  const double* __restrict__ pv, const double* __restrict__ rho, double* c) {
+  __shared__ double red[256];
+  const int a = blockIdx.x;
+  for (int i = 0; i < k; ++i) {
+    double s = 0;
+    for (int64_t e = rp[a] + threadIdx.x; e < rp[a + 1]; e += blockDim.x) s = fma(pv[e], rho[(int64_t)ci[e] * k + i], s);
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+      if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) c[(int64_t)a * k + i] = red[0];
+    __syncthreads();
+  }
+}
+
+// Coarse term of Eq. (3.3) in the eigenbasis Phi of (K_H, M_H):
+// a[j, i] = (phi_j . c_i) / (lambda_j^H - lambda_i) for j >= k (Q_{s+1}^H), 0 for j < k.
+__global__ void k_coarse_spectral(int nH, int k, const double* __restrict__ Phi, const double* __restrict__ lamH,
+                                  const double* __restrict__ lam, const double* __restrict__ c, double* a) {
+  __shared__ double red[128];
+  const int j = blockIdx.x;
+  for (int i = 0; i < k; ++i) {
+    double s = 0;
+    if (j >= k)
+      for (int r = threadIdx.x; r < nH; r += blockDim.x) s = fma(Phi[(int64_t)r * nH + j], c[(int64_t)r * k + i], s);
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+      if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) a[(int64_t)j * k + i] = (j >= k) ? red[0] / (lamH[j] - lam[i]) : 0.0;
+    __syncthreads();
+  }
+}
+
+// w0 = Phi a (n_H x k)
+__global__ void k_coarse_expand(int nH, int k, const double* __restrict__ Phi, const double* __restrict__ a,
+                                double* w0) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nH * k) return;
+  int r = t / k, i = t % k;
+  double s = 0;
+  for (int j = k; j < nH; ++j) s = fma(Phi[(int64_t)r * nH + j], a[(int64_t)j * k + i], s);
+  w0[t] = s;
+}
+
+// z[g, i] = sum_{c} P[g, c] w0[c, i] + sum_{local copies of g} w[pos, i]
+template <typename TP>
+__global__ void k_prolong_add(int64_t n, int k, const int64_t* __restrict__ prp, const int32_t* __restrict__ pci,
+                              const double* __restrict__ pv, const double* __restrict__ w0,
+                              const int32_t* __restrict__ rtp, const int32_t* __restrict__ rtpos,
+                              const TP* __restrict__ wpk, double* __restrict__ Z) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n * k) return;
+  int64_t g = t / k;
+  int i = (int)(t % k);
+  double z = 0;
+  for (int64_t e = prp[g]; e < prp[g + 1]; ++e) z = fma(pv[e], w0[(int64_t)pci[e] * k + i], z);
+  for (int e = rtp[g]; e < rtp[g + 1]; ++e) z += (double)wpk[(int64_t)rtpos[e] * k + i];
+  Z[t] = z;
+}
+
+// ---------------------------------------------------------------------------
+// Rayleigh-Ritz in W (one block, FP64).  Parallel cyclic Jacobi (round-robin
+// ordering) for the two small symmetric eigenproblems.
+// ---------------------------------------------------------------------------
+constexpr int kRRMax = 64;
+
+// Symmetric eigen-decomposition of A (m x m, leading dimension ld = kRRMax) in
+// shared memory; V receives the eigenvectors (columns), A's diagonal the
+// eigenvalues.  mp = m rounded up to even (the extra index is a zero row/column
+// that never rotates).  Uses all threads of the block.
+__device__ void jacobi_eig(double* A, double* V, int m, double* cs, double* sn, int* pp, int* qq) {
+  const int mp = m + (m & 1);
+  const int ld = kRRMax;
+  const int tid = threadIdx.x;
+  for (int t = tid; t < mp * ld; t += blockDim.x) {
+    int r = t / ld, c = t % ld;
+    V[t] = (r == c) ? 1.0 : 0.0;
+    if ((r >= m || c >= m) && c < mp) A[t] = 0.0;
+  }
+  __syncthreads();
+  const int half = mp / 2;
+  __shared__ int done;
+  __shared__ double amax;
+  if (tid == 0) {
+    double a = 0;
+    for (int j = 0; j < m; ++j) a = fmax(a, fabs(A[j * ld + j]));
+    amax = a;
+  }
+  __syncthreads();
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    if (tid == 0) done = 1;
+    __syncthreads();
+    for (int round = 0; round < mp - 1; ++round) {
+      if (tid < half) {
+        // circle method: position 0 fixed, the others rotate
+        int e0 = 0, e1;
+        auto ring = [&](int pos) { return ((pos + round) % (mp - 1)) + 1; };
+        if (tid == 0) {
+          e1 = ring(0);
+        } else {
+          e0 = ring(tid);
+          e1 = ring(mp - 1 - tid);
+        }
+        int p = min(e0, e1), q = max(e0, e1);
+        double apq = A[p * ld + q], app = A[p * ld + p], aqq = A[q * ld + q];
+        double c = 1.0, s = 0.0;
+        if (fabs(apq) > 1e-300 && fabs(apq) > 1e-17 * sqrt(fabs(app * aqq)) && fabs(apq) > 1e-30 * amax) {
+          double tau = (aqq - app) / (2.0 * apq);
+          double tt = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+          c = 1.0 / sqrt(1.0 + tt * tt);
+          s = tt * c;
+          done = 0;
+        }
+        cs[tid] = c;
+        sn[tid] = s;
+        pp[tid] = p;
+        qq[tid] = q;
+      }
+      __syncthreads();
+      // A <- A J and V <- V J (columns p, q of every pair)
+      for (int t = tid; t < half * mp; t += blockDim.x) {
+        int pr = t / mp, r = t % mp;
+        int p = pp[pr], q = qq[pr];
+        double c = cs[pr], s = sn[pr];
+        double ap = A[r * ld + p], aq = A[r * ld + q];
+        A[r * ld + p] = c * ap - s * aq;
+        A[r * ld + q] = s * ap + c * aq;
+        double vp = V[r * ld + p], vq = V[r * ld + q];
+        V[r * ld + p] = c * vp - s * vq;
+        V[r * ld + q] = s * vp + c * vq;
+      }
+      __syncthreads();
+      // A <- J^T A (rows p, q of every pair)
+      for (int t = tid; t < half * mp; t += blockDim.x) {
+        int pr = t / mp, col = t % mp;
+        int p = pp[pr], q = qq[pr];
+        double c = cs[pr], s = sn[pr];
+        double ap = A[p * ld + col], aq = A[q * ld + col];
+        A[p * ld + col] = c * ap - s * aq;
+        A[q * ld + col] = s * ap + c * aq;
+      }
+      __syncthreads();
+    }
+    if (done) break;
+    __syncthreads();
+  }
+}
+
+// Ascending order of diag(A)[0..m): ord[rank] = index (ties by index).
+__device__ void sort_diag(const double* A, int m, int* ord) {
+  const int ld = kRRMax;
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    double dj = A[j * ld + j];
+    int rank = 0;
+    for (int i = 0; i < m; ++i) {
+      double di = A[i * ld + i];
+      if (di < dj || (di == dj && i < j)) ++rank;
+    }
+    ord[rank] = j;
+  }
+  __syncthreads();
+}
+
+// G, H: m x m (row-major, ld m).  First k columns of W are b-orthonormal Ritz
+// vectors, the rest are scaled to unit M-norm.  Output C (m x k, ld k),
+// lam_new (k), hist row, status.
+__global__ void k_rayleigh_ritz(int m, int k, const double* __restrict__ G, const double* __restrict__ H,
+                                double drop_tol, const double* __restrict__ lam_old, double* C, double* lam_new,
+                                double* hist_row, int stop_rule, double tol, DevStatus* st) {
+  extern __shared__ double rr[];
+  const int ld = kRRMax;
+  double* A = rr;                  // ld x ld
+  double* V = A + ld * ld;         // ld x ld
+  double* Bm = V + ld * ld;        // ld x ld : basis of the kept directions (m x r)
+  double* Hs = Bm + ld * ld;       // ld x ld : scaled H
+  double* sc = Hs + ld * ld;       // ld     : column scaling
+  double* cs = sc + ld;            // ld/2
+  double* sn = cs + ld;
+  int* pp = reinterpret_cast<int*>(sn + ld);
+  int* qq = pp + ld;
+  int* ord = qq + ld;
+  __shared__ int r_keep;
+  const int tid = threadIdx.x;
+  for (int j = tid; j < m; j += blockDim.x) {
+    double g = G[j * m + j];
+    sc[j] = (j < k) ? 1.0 : (g > 0 ? 1.0 / sqrt(g) : 0.0);
+  }
+  __syncthreads();
+  for (int t = tid; t < m * m; t += blockDim.x) {
+    int a = t / m, b = t % m;
+    double gs = 0.5 * (G[a * m + b] + G[b * m + a]) * sc[a] * sc[b];
+    double hs = 0.5 * (H[a * m + b] + H[b * m + a]) * sc[a] * sc[b];
+    A[a * ld + b] = gs;
+    Hs[a * ld + b] = hs;
+  }
+  __syncthreads();
+  jacobi_eig(A, V, m, cs, sn, pp, qq);
+  sort_diag(A, m, ord);
+  // keep eigen-directions of the scaled Gram matrix above drop_tol * max
+  if (tid == 0) {
+    double gmax = A[ord[m - 1] * ld + ord[m - 1]];
+    int r = 0;
+    for (int t = 0; t < m; ++t)
+      if (A[ord[t] * ld + ord[t]] > drop_tol * gmax) ++r;
+    r_keep = r;
+  }
+  __syncthreads();
+  const int r = r_keep;
+  const int first = m - r;  // kept = ord[first .. m)
+  // Bm[:, c] = V[:, ord[first + c]] / sqrt(g)
+  for (int t = tid; t < m * r; t += blockDim.x) {
+    int a = t / r, c = t % r;
+    int j = ord[first + c];
+    Bm[a * ld + c] = V[a * ld + j] / sqrt(A[j * ld + j]);
+  }
+  __syncthreads();
+  // V <- Hs Bm (m x r), then A <- Bm^T V (r x r)
+  for (int t = tid; t < m * r; t += blockDim.x) {
+    int a = t / r, c = t % r;
+    double s = 0;
+    for (int e = 0; e < m; ++e) s = fma(Hs[a * ld + e], Bm[e * ld + c], s);
+    V[a * ld + c] = s;
+  }
+  __syncthreads();
+  for (int t = tid; t < r * r; t += blockDim.x) {
+    int a = t / r, c = t % r;
+    double s = 0;
+    for (int e = 0; e < m; ++e) s = fma(Bm[e * ld + a], V[e * ld + c], s);
+    A[a * ld + c] = s;
+  }
+  __syncthreads();
+  for (int t = tid; t < r * r; t += blockDim.x) {
+    int a = t / r, c = t % r;
+    if (a < c) {
+      double s = 0.5 * (A[a * ld + c] + A[c * ld + a]);
+      A[a * ld + c] = s;
+      A[c * ld + a] = s;
+    }
+  }
+  __syncthreads();
+  jacobi_eig(A, V, r, cs, sn, pp, qq);
+  sort_diag(A, r, ord);
+  // C = diag(sc) Bm Y[:, 0..k)
+  const int kk = min(k, r);
+  for (int t = tid; t < m * k; t += blockDim.x) {
+    int a = t / k, c = t % k;
+    double s = 0;
+    if (c < kk) {
+      int j = ord[c];
+      for (int e = 0; e < r; ++e) s = fma(Bm[a * ld + e], V[e * ld + j], s);
+    }
+    C[a * k + c] = sc[a] * s;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double dl = 0;
+    for (int c = 0; c < k; ++c) {
+      double th = (c < kk) ? A[ord[c] * ld + ord[c]] : lam_old[c];
+      dl += fabs(th - lam_old[c]);
+      lam_new[c] = th;
+      if (hist_row) hist_row[c] = th;
+    }
+    st->sum_dl = dl;
+    st->kept = r;
+    if (r < k) st->err_breakdown = 1;
+    if (stop_rule == BPJD_STOP_DLAMBDA) st->converged = (dl < tol) ? 1 : 0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Setup kernels
+// ---------------------------------------------------------------------------
+__global__ void k_band_gather(int64_t total, const int64_t* __restrict__ pos, const double* __restrict__ val,
+                              double* out, float* outf) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  int64_t p = pos[t];
+  double a = (p >= 0) ? val[p] : 0.0;
+  out[t] = a;
+  if (outf) outf[t] = (float)a;
+}
+
+// Galerkin products K_H = P^T K P and M_H = P^T M P in two deterministic passes.
+// Pass 1 (thread per fine row r): the sparse rows (K P)[r, :] and (M P)[r, :],
+// at most kKPWidth coarse columns each, accumulated in a fixed order.
+constexpr int kKPWidth = 32;
+__global__ void k_kp_rows(int n, const int64_t* __restrict__ arp, const int32_t* __restrict__ aci,
+                          const double* __restrict__ av, const int64_t* __restrict__ mrp,
+                          const int32_t* __restrict__ mci, const double* __restrict__ mv,
+                          const int64_t* __restrict__ prp, const int32_t* __restrict__ pci,
+                          const double* __restrict__ pv, int32_t* kpc, double* kpk, double* kpm, int32_t* cnt,
+                          int32_t* overflow) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  int32_t* cols = kpc + (int64_t)r * kKPWidth;
+  double* vk = kpk + (int64_t)r * kKPWidth;
+  double* vm = kpm + (int64_t)r * kKPWidth;
+  int m = 0;
+  bool full = false;
+  auto add = [&](int32_t b, double x, bool isk) {
+    int s = 0;
+    while (s < m && cols[s] != b) ++s;
+    if (s == m) {
+      if (m == kKPWidth) {
+        full = true;
+        return;
+      }
+      cols[m] = b;
+      vk[m] = 0.0;
+      vm[m] = 0.0;
+      ++m;
+    }
+    if (isk)
+      vk[s] += x;
+    else
+      vm[s] += x;
+  };
+  for (int64_t f = arp[r]; f < arp[r + 1]; ++f) {
+    const int64_t c = aci[f];
+    for (int64_t g = prp[c]; g < prp[c + 1]; ++g) add(pci[g], av[f] * pv[g], true);
+  }
+  for (int64_t f = mrp[r]; f < mrp[r + 1]; ++f) {
+    const int64_t c = mci[f];
+    for (int64_t g = prp[c]; g < prp[c + 1]; ++g) add(pci[g], mv[f] * pv[g], false);
+  }
+  if (full) *overflow = 1;
+  cnt[r] = m;
+}
+
+// Pass 2 (one warp per coarse row a): K_H[a, b] = sum_{r in P^T row a, ascending}
+// P[r, a] (K P)[r, b].  Lane j owns the columns b = j mod 32 of a dense row in
+// shared memory, so every entry is summed by one lane in a fixed order.
+__global__ void k_galerkin_rows(int nH, const int64_t* __restrict__ ptr, const int32_t* __restrict__ ptc,
+                                const double* __restrict__ ptv, const int32_t* __restrict__ kpc,
+                                const double* __restrict__ kpk, const double* __restrict__ kpm,
+                                const int32_t* __restrict__ cnt, double* KH, double* MH) {
+  extern __shared__ double rowbuf[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int a = blockIdx.x * (blockDim.x >> 5) + wib;
+  if (a >= nH) return;
+  double* kr = rowbuf + (size_t)wib * 2 * nH;
+  double* mr = kr + nH;
+  for (int t = lane; t < nH; t += 32) {
+    kr[t] = 0.0;
+    mr[t] = 0.0;
+  }
+  __syncwarp();
+  for (int64_t e = ptr[a]; e < ptr[a + 1]; ++e) {
+    const int64_t r = ptc[e];
+    const double pra = ptv[e];
+    const int m = cnt[r];
+    for (int s = 0; s < m; ++s) {
+      const int b = kpc[r * kKPWidth + s];
+      if ((b & 31) == lane) {
+        kr[b] += pra * kpk[r * kKPWidth + s];
+        mr[b] += pra * kpm[r * kKPWidth + s];
+      }
+    }
+  }
+  __syncwarp();
+  for (int t = lane; t < nH; t += 32) {
+    KH[(int64_t)a * nH + t] = kr[t];
+    MH[(int64_t)a * nH + t] = mr[t];
+  }
+}
+
+int col_block(int k) { return k * (256 / k); }
+
+}  // namespace
+
+// ===========================================================================
+// instrumentation
+// ===========================================================================
+ProfScope::ProfScope(Handle& hh, int c) : h(hh), cls(c), idx(0), on(hh.profile) {
+  if (!on) return;
+  idx = h.ev_used;
+  while (h.ev_pool.size() < idx + 2) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    h.ev_pool.push_back((void*)e);
+  }
+  h.ev_used += 2;
+  h.ev_cls.push_back(cls);
+  cudaEventRecord((cudaEvent_t)h.ev_pool[idx], h.stream);
+}
+ProfScope::~ProfScope() {
+  if (on) cudaEventRecord((cudaEvent_t)h.ev_pool[idx + 1], h.stream);
+}
+void prof_flush(Handle& h) {
+  if (h.ev_used == 0) return;
+  cudaStreamSynchronize(h.stream);
+  for (size_t p = 0; p < h.ev_cls.size(); ++p) {
+    float ms = 0;
+    cudaEventElapsedTime(&ms, (cudaEvent_t)h.ev_pool[2 * p], (cudaEvent_t)h.ev_pool[2 * p + 1]);
+    h.prof_ms[h.ev_cls[p]] += ms;
+    h.prof_count[h.ev_cls[p]] += 1;
+  }
+  h.ev_used = 0;
+  h.ev_cls.clear();
+}
+
+// ===========================================================================
+// launchers
+// ===========================================================================
+int launch_spmm(Handle& h, const double* X, double* YA, double* YM, int ncols) {
+  ProfScope ps(h, BPJD_PROF_SPMM);
+  const int n = h.n;
+  auto go = [&](auto lanes_tag, const CsrDev& A, const double* vm, double* ya, double* ym) {
+    constexpr int LANES = decltype(lanes_tag)::value;
+    constexpr int RPW = 32 / LANES;
+    int64_t warps = (n + RPW - 1) / RPW;
+    int64_t blocks = (warps * 32 + 255) / 256;
+    k_spmm<LANES><<<(unsigned)blocks, 256, 0, h.stream>>>(n, A.row_ptr, A.col, A.val, vm, X, ya, ym, ncols);
+    h.launches += 1;
+  };
+  auto dispatch = [&](const CsrDev& A, const double* vm, double* ya, double* ym) {
+    if (ncols <= 4)
+      go(std::integral_constant<int, 4>(), A, vm, ya, ym);
+    else if (ncols <= 8)
+      go(std::integral_constant<int, 8>(), A, vm, ya, ym);
+    else if (ncols <= 16)
+      go(std::integral_constant<int, 16>(), A, vm, ya, ym);
+    else
+      go(std::integral_constant<int, 32>(), A, vm, ya, ym);
+  };
+  if (h.same_pattern) {
+    dispatch(h.A, h.M.val, YA, YM);
+  } else {
+    dispatch(h.A, nullptr, YA, nullptr);
+    dispatch(h.M, nullptr, YM, nullptr);
+  }
+  return (int)cudaGetLastError();
+}
+
+int launch_csr_times_dense(const CsrDev& P, const double* D, int ldd, int ncols, double* Y, int ldy,
+                           cudaStream_t s) {
+  int64_t tot = (int64_t)P.n_rows * ncols;
+  k_csr_dense<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(P.n_rows, P.row_ptr, P.col, P.val, D, ldd, ncols, Y,
+                                                            ldy);
+  return (int)cudaGetLastError();
+}
+
+int launch_residual(Handle& h, const double* AX, const double* MX, const double* lam, double* rho) {
+  const int k = h.k;
+  ProfScope ps(h, BPJD_PROF_RESID);
+  const int bs = col_block(k);
+  const int64_t nk = (int64_t)h.n * k;
+  int nblk = (int)std::min<int64_t>(kPartialBlocks, (nk + bs - 1) / bs);
+  h.launches += 2;
+  k_residual<<<nblk, bs, 2 * bs * sizeof(double), h.stream>>>(nk, k, AX, MX, lam, rho, h.partial);
+  k_residual_finish<<<1, 64, 0, h.stream>>>(nblk, k, h.partial, lam, h.stop_rule, h.tol, h.dstat);
+  return (int)cudaGetLastError();
+}
+
+int launch_rayleigh(Handle& h, const double* X, const double* AX, const double* MX, double* lam) {
+  const int k = h.k;
+  const int bs = col_block(k);
+  const int64_t nk = (int64_t)h.n * k;
+  int nblk = (int)std::min<int64_t>(kPartialBlocks, (nk + bs - 1) / bs);
+  h.launches += 2;
+  k_rq_partial<<<nblk, bs, 2 * bs * sizeof(double), h.stream>>>(nk, k, X, AX, MX, h.partial);
+  k_rq_finish<<<1, 64, 0, h.stream>>>(nblk, k, h.partial, lam);
+  return (int)cudaGetLastError();
+}
+
+int launch_inner(Handle& h, int p, const double* const* U, int q, const double* const* V, double* out) {
+  const int k = h.k;
+  Ptrs6 u{}, v{};
+  for (int b = 0; b < p; ++b) u.p[b] = U[b];
+  for (int b = 0; b < q; ++b) v.p[b] = V[b];
+  const int nout = p * k * q * k;
+  if (nout > kInnerMaxOut * 256) return (int)cudaErrorInvalidValue;
+  ProfScope ps(h, BPJD_PROF_INNER);
+  h.launches += 2;
+  int nblk = (int)std::min<int64_t>(kPartialBlocks, ((int64_t)h.n + 63) / 64);
+  int rpb = (int)(((int64_t)h.n + nblk - 1) / nblk);
+  size_t sm = (size_t)kInnerRows * (p + q) * k * sizeof(double);
+  k_inner<<<nblk, 256, sm, h.stream>>>(h.n, k, p, u, q, v, rpb, h.partial);
+  k_sum_partials<<<(nout + 255) / 256, 256, 0, h.stream>>>(nblk, nout, h.partial, out);
+  return (int)cudaGetLastError();
+}
+
+int launch_combine_rows(Handle& h, int nin, const double* const* Win, const double* C, int ldc, int csub,
+                        const double* Zadd, double* out, double sign) {
+  ProfScope ps(h, BPJD_PROF_COMBINE);
+  h.launches += 1;
+  Ptrs6 w{};
+  for (int b = 0; b < nin; ++b) w.p[b] = Win[b];
+  int64_t tot = (int64_t)h.n * csub;
+  size_t sm = (size_t)nin * h.k * csub * sizeof(double);
+  k_combine_rows<<<(unsigned)((tot + 255) / 256), 256, sm, h.stream>>>(h.n, h.k, nin, w, C, ldc, csub, Zadd, out,
+                                                                        sign);
+  return (int)cudaGetLastError();
+}
+
+int launch_precond(Handle& h, const double* rho, const double* lam, double* Z) {
+  const int k = h.k;
+  const int npairs = h.nsub * k;
+  const int B = h.B;
+  // local band solves
+  {
+    ProfScope ps(h, BPJD_PROF_LOCAL);
+    h.launches += 1;
+    const bool f32 = (h.precision == BPJD_MIXED);
+    const size_t esz = f32 ? sizeof(float) : sizeof(double);
+    const size_t per_warp = (size_t)(B * B + 3 * B) * esz;
+    int wpb = (int)std::max<size_t>(1, std::min<size_t>(4, (200 * 1024) / per_warp));
+    size_t sm = per_warp * wpb;
+    int blocks = (npairs + wpb - 1) / wpb;
+    if (f32) {
+      cudaFuncSetAttribute(k_local_band<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      k_local_band<float><<<blocks, 32 * wpb, sm, h.stream>>>(npairs, k, h.sub_ptr, h.sub_dofs, B, h.bandKf,
+                                                              h.bandMf, lam, rho, (float*)h.Lbuf, (float*)h.wpk,
+                                                              h.derr);
+    } else {
+      cudaFuncSetAttribute(k_local_band<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      k_local_band<double><<<blocks, 32 * wpb, sm, h.stream>>>(npairs, k, h.sub_ptr, h.sub_dofs, B, h.bandK,
+                                                               h.bandM, lam, rho, (double*)h.Lbuf,
+                                                               (double*)h.wpk, h.derr);
+    }
+  }
+  // coarse solve
+  {
+    ProfScope ps(h, BPJD_PROF_COARSE);
+    h.launches += 3;
+    k_coarse_restrict<<<h.nH, 256, 0, h.stream>>>(h.nH, k, h.PT.row_ptr, h.PT.col, h.PT.val, rho, h.cH);
+    k_coarse_spectral<<<h.nH, 128, 0, h.stream>>>(h.nH, k, h.Phi, h.lamH, lam, h.cH, h.aH);
+    k_coarse_expand<<<(h.nH * k + 127) / 128, 128, 0, h.stream>>>(h.nH, k, h.Phi, h.aH, h.w0);
+  }
+  // prolongation-add
+  {
+    ProfScope ps(h, BPJD_PROF_PROLONG);
+    h.launches += 1;
+    int64_t tot = (int64_t)h.n * k;
+    if (h.precision == BPJD_MIXED)
+      k_prolong_add<float><<<(unsigned)((tot + 255) / 256), 256, 0, h.stream>>>(
+          h.n, k, h.P.row_ptr, h.P.col, h.P.val, h.w0, h.rt_ptr, h.rt_pos, (const float*)h.wpk, Z);
+    else
+      k_prolong_add<double><<<(unsigned)((tot + 255) / 256), 256, 0, h.stream>>>(
+          h.n, k, h.P.row_ptr, h.P.col, h.P.val, h.w0, h.rt_ptr, h.rt_pos, (const double*)h.wpk, Z);
+  }
+  return (int)cudaGetLastError();
+}
+
+int launch_rr(Handle& h, int m, const double* G, const double* Hm, const double* lam_old, double* C,
+              double* lam_new, int hist_row) {
+  if (m > kRRMax) return (int)cudaErrorInvalidValue;
+  size_t sm = (size_t)(4 * kRRMax * kRRMax + 3 * kRRMax) * sizeof(double) + 3 * kRRMax * sizeof(int);
+  cudaFuncSetAttribute(k_rayleigh_ritz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  ProfScope ps(h, BPJD_PROF_RR);
+  h.launches += 1;
+  double* hr = (hist_row >= 0 && hist_row < h.hist_rows) ? h.hist + (int64_t)hist_row * h.k : nullptr;
+  k_rayleigh_ritz<<<1, 256, sm, h.stream>>>(m, h.k, G, Hm, h.drop_tol, lam_old, C, lam_new, hr, h.stop_rule, h.tol,
+                                            h.dstat);
+  return (int)cudaGetLastError();
+}
+
+int launch_band_gather(Handle& h, const int64_t* pos, const double* val, double* out, float* outf) {
+  int64_t total = h.sum_nl * h.B;
+  k_band_gather<<<(unsigned)((total + 255) / 256), 256, 0, h.stream>>>(total, pos, val, out, outf);
+  return (int)cudaGetLastError();
+}
+
+int launch_galerkin(const CsrDev& A, const CsrDev& Msp, const CsrDev& P, const CsrDev& PT, double* KH,
+                    double* MH, cudaStream_t s) {
+  const int n = A.n_rows, nH = P.n_cols;
+  int32_t *kpc = nullptr, *cnt = nullptr, *ovf = nullptr;
+  double *kpk = nullptr, *kpm = nullptr;
+  int rc = 0, hov = 0;
+  const int wpb = 4;
+  const size_t sm = (size_t)wpb * 2 * nH * sizeof(double);
+  cudaError_t e = cudaSuccess;
+  if ((e = cudaMalloc(&kpc, sizeof(int32_t) * (size_t)n * kKPWidth)) != cudaSuccess) goto done;
+  if ((e = cudaMalloc(&kpk, sizeof(double) * (size_t)n * kKPWidth)) != cudaSuccess) goto done;
+  if ((e = cudaMalloc(&kpm, sizeof(double) * (size_t)n * kKPWidth)) != cudaSuccess) goto done;
+  if ((e = cudaMalloc(&cnt, sizeof(int32_t) * (size_t)n)) != cudaSuccess) goto done;
+  if ((e = cudaMalloc(&ovf, sizeof(int32_t))) != cudaSuccess) goto done;
+  if ((e = cudaMemsetAsync(ovf, 0, sizeof(int32_t), s)) != cudaSuccess) goto done;
+  k_kp_rows<<<(n + 127) / 128, 128, 0, s>>>(n, A.row_ptr, A.col, A.val, Msp.row_ptr, Msp.col, Msp.val, P.row_ptr,
+                                            P.col, P.val, kpc, kpk, kpm, cnt, ovf);
+  if (sm > 48 * 1024) cudaFuncSetAttribute(k_galerkin_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_galerkin_rows<<<(nH + wpb - 1) / wpb, 32 * wpb, sm, s>>>(nH, PT.row_ptr, PT.col, PT.val, kpc, kpk, kpm, cnt,
+                                                              KH, MH);
+  if ((e = cudaGetLastError()) != cudaSuccess) goto done;
+  if ((e = cudaMemcpyAsync(&hov, ovf, sizeof(int32_t), cudaMemcpyDeviceToHost, s)) != cudaSuccess) goto done;
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) goto done;
+  if (hov) rc = (int)cudaErrorInvalidValue;
+done:
+  cudaFree(kpc);
+  cudaFree(kpk);
+  cudaFree(kpm);
+  cudaFree(cnt);
+  cudaFree(ovf);
+  return e != cudaSuccess ? (int)e : rc;
+}
+
+}  // namespace bpjd

@@ -1,0 +1,163 @@
+"""GPU parity of the CUDA path against the FP64 oracle, through the C ABI.
+
+Tolerances (derived from the arithmetic, see the design notes):
+  * SpMM (FP64, <= 27 terms per entry): 1e-13 relative to the row-wise scale.
+  * Preconditioner FP64: 1e-10 relative to max |z| (banded vs dense Cholesky of
+    local matrices with condition ~ (H/h)^2 ~ 1e3..1e4).  MIXED (FP32 local
+    solves): 2e-3 relative to max |z| (eps_32 times the local condition number).
+  * Eigenvalues: 1e-10 relative (FP64 path), 1e-9 (mixed path); cluster
+    subspace gap theta_b <= 1e-6; relative residual <= 1e-8.
+"""
+
+from dataclasses import replace
+
+import numpy as np
+import pytest
+import scipy.linalg as la
+
+from oracle import bpjd as obpjd
+from oracle import metrics, problem as oproblem
+from workloads import config_c1, config_small_2d, config_small_3d, ProblemSpec
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+B = pytest.importorskip("paper_2203_06327_gb300.binding")
+
+DEV = "cuda"
+
+
+def _solver(spec, device_inputs=True, **kw):
+    pb = B.problem_from_spec(spec)
+    return pb, B.Solver.from_problem(pb, spec.k, device=DEV if device_inputs else None, **kw)
+
+
+@pytest.fixture(scope="module")
+def c1_oracle():
+    op = oproblem.build(config_c1())
+    S = op.setup()
+    return op, S
+
+
+@pytest.mark.parametrize("ncols", [1, 6, 12, 16, 24])
+def test_spmm_matches_oracle(c1_oracle, ncols):
+    op, S = c1_oracle
+    pb, sv = _solver(config_c1())
+    X = np.random.default_rng(ncols).standard_normal((sv.n, ncols))
+    Xd = torch.tensor(X, device=DEV)
+    YA = torch.empty_like(Xd)
+    YM = torch.empty_like(Xd)
+    sv.spmm(Xd, YA, YM)
+    torch.cuda.synchronize()
+    for Y, A in ((YA, op.K), (YM, op.M)):
+        ref = A @ X
+        scale = abs(A) @ np.abs(X)
+        assert np.all(np.abs(Y.cpu().numpy() - ref) <= 1e-13 * scale + 1e-300)
+
+
+@pytest.mark.parametrize("spec", [config_c1(), config_small_2d(), config_small_3d(), config_small_3d(kind="q1_3d")],
+                         ids=lambda s: s.name)
+@pytest.mark.parametrize("precision", [B.FP64, B.MIXED], ids=["fp64", "mixed"])
+def test_preconditioner_matches_oracle(spec, precision):
+    op = oproblem.build(spec)
+    S = op.setup()
+    pb, sv = _solver(spec, precision=precision)
+    k = spec.k
+    rng = np.random.default_rng(7)
+    rho = rng.standard_normal((sv.n, k))
+    lam = np.sort(S.lam0H[:k]) * rng.uniform(0.9, 1.0, k)       # shifts below the initial Ritz values
+    Z_ref = obpjd.apply_preconditioner(S, rho, lam)
+    Zd = torch.empty((sv.n, k), dtype=torch.float64, device=DEV)
+    sv.apply_preconditioner(torch.tensor(rho, device=DEV), torch.tensor(lam, device=DEV), Zd)
+    Z = Zd.cpu().numpy()
+    tol = 1e-10 if precision == B.FP64 else 2e-3
+    assert np.abs(Z - Z_ref).max() <= tol * np.abs(Z_ref).max()
+
+
+def _check_solution(op, lam, X, lam_ref, V_ref, rtol):
+    k = len(lam)
+    np.testing.assert_allclose(lam, lam_ref[:k], rtol=rtol)
+    assert metrics.rel_residuals(op.K, op.M, lam, X).max() <= 1e-8
+    for a, b in metrics.clusters(lam_ref[:k]):
+        assert metrics.gap_b(X[:, a:b], V_ref[:, a:b], op.M) <= 1e-6
+    np.testing.assert_allclose(X.T @ (op.M @ X), np.eye(k), atol=1e-10)
+
+
+@pytest.mark.parametrize("subspace", [B.W_2K, B.W_3K], ids=["W2k", "W3k"])
+@pytest.mark.parametrize("precision", [B.FP64, B.MIXED], ids=["fp64", "mixed"])
+def test_c1_solve_matches_oracle(c1_oracle, subspace, precision):
+    op, S = c1_oracle
+    spec = config_c1()
+    pb, sv = _solver(spec, precision=precision, subspace=subspace)
+    lam, X, st = sv.solve()
+    assert st["converged"] == 1
+    w, V = la.eigh(op.K.toarray(), op.M.toarray())
+    _check_solution(op, lam, X, w, V, 1e-10 if precision == B.FP64 else 1e-9)
+    ref = obpjd.solve(S, tol=1e-8, subspace="2s" if subspace == B.W_2K else "3s")
+    if precision == B.FP64:
+        # same trajectory: iteration count and per-step Ritz values
+        assert st["iters"] == ref.iterations
+        H = sv.history()
+        Hr = np.array(ref.history_lam)
+        n = min(len(H), len(Hr))
+        np.testing.assert_allclose(H[:n], Hr[:n], rtol=1e-9)
+    else:
+        assert abs(st["iters"] - ref.iterations) <= max(3, ref.iterations // 5)
+
+
+@pytest.mark.parametrize("spec", [config_small_2d(), config_small_3d(), config_small_3d(kind="q1_3d"),
+                                  config_small_2d(nx=40, ny=40, nsx=5, nsy=5, delta=1, k=1, kappa="random")],
+                         ids=lambda s: s.name)
+def test_other_problems_solve(spec):
+    op = oproblem.build(spec)
+    w, V = la.eigh(op.K.toarray(), op.M.toarray())
+    for precision in (B.FP64, B.MIXED):
+        pb, sv = _solver(spec, precision=precision, subspace=B.W_3K)
+        lam, X, st = sv.solve()
+        assert st["converged"] == 1
+        _check_solution(op, lam, X, w, V, 1e-10 if precision == B.FP64 else 1e-9)
+
+
+def test_host_inputs_and_device_eigvecs_agree():
+    spec = config_small_2d()
+    pb = B.problem_from_spec(spec)
+    s_host = B.Solver.from_problem(pb, spec.k, device=None)
+    s_dev = B.Solver.from_problem(pb, spec.k, device=DEV)
+    l1, X1, _ = s_host.solve()
+    l2, X2, _ = s_dev.solve(eigvecs="device")
+    np.testing.assert_array_equal(l1, l2)
+    np.testing.assert_array_equal(X1, X2.cpu().numpy())
+    # repeated solves restart from the initial guess and are bit-reproducible
+    l3, X3, _ = s_host.solve()
+    np.testing.assert_array_equal(l1, l3)
+    np.testing.assert_array_equal(X1, X3)
+
+
+def test_local_indefinite_reported():
+    spec = replace(config_c1(), tau=0)
+    pb, sv = _solver(spec)
+    with pytest.raises(B.BpjdError) as e:
+        sv.solve()
+    assert e.value.code == B.ERR_LOCAL_INDEFINITE
+
+
+def test_coarse_gap_reported():
+    """Trilinear elements on a cube keep the exact multiplicities of the Laplacian (Table 5):
+    the 2nd to 4th coarse eigenvalues coincide, so k = 2 violates Assumption 1 on V^H."""
+    spec = replace(config_small_3d(kind="q1_3d"), k=2)
+    pb = B.problem_from_spec(spec)
+    with pytest.raises(B.BpjdError) as e:
+        B.Solver.from_problem(pb, 2, device=DEV)
+    assert e.value.code == B.ERR_GAP
+    op = oproblem.build(spec)
+    with pytest.raises(obpjd.CoarseGap):
+        op.setup()
+
+
+def test_paper_stop_rule():
+    op = oproblem.build(config_c1())
+    ref = obpjd.solve(op.setup(), tol=1e-10, stop="dlambda", subspace="3s")
+    pb, sv = _solver(config_c1(), subspace=B.W_3K, stop_rule=B.STOP_DLAMBDA, tol=1e-10)
+    lam, X, st = sv.solve()
+    assert st["converged"] == 1 and st["sum_abs_dlambda"] < 1e-10
+    assert st["iters"] == ref.iterations
+    np.testing.assert_allclose(lam, ref.lam, rtol=1e-10)

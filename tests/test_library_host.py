@@ -1,0 +1,107 @@
+"""Host-side checks of the CUDA library (no GPU needed): it loads, exports every
+entry point declared in include/bpjd.h, its problem generators agree with the
+oracle's (bit-exact patterns and index maps, values to 1e-15), and argument
+validation in bpjd_setup rejects bad inputs before any device work."""
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from conftest import ROOT
+from oracle import problem as oracle_problem
+from workloads import config_c1, config_small_2d, config_small_3d, ProblemSpec
+
+B = pytest.importorskip("paper_2203_06327_gb300.binding")
+
+
+def test_exports_every_declared_symbol():
+    with open(os.path.join(ROOT, "include", "bpjd.h")) as f:
+        text = f.read()
+    declared = set(re.findall(r"\b(bpjd_[a-z_0-9]+)\s*\(", text))
+    assert declared, "no declarations found"
+    lib = C.CDLL(B.LIB_PATH)
+    for name in sorted(declared):
+        assert hasattr(lib, name), name
+    assert set(B.EXPORTED) <= declared
+
+
+def _cmp_csr(lib_csr, ora):
+    ora = ora.tocsr()
+    ora.sort_indices()
+    np.testing.assert_array_equal(lib_csr.row_ptr, ora.indptr)
+    np.testing.assert_array_equal(lib_csr.col_idx, ora.indices)
+    scale = np.abs(ora.data).max()
+    np.testing.assert_allclose(lib_csr.val, ora.data, rtol=0, atol=2e-15 * scale)
+
+
+@pytest.mark.parametrize("spec", [config_c1(), config_small_2d(), config_small_3d(),
+                                  config_small_3d(kind="q1_3d"), config_small_3d(n=16, ns=4, delta=2)],
+                         ids=lambda s: s.name)
+def test_generators_match_oracle(spec):
+    lp = B.problem_from_spec(spec)
+    op = oracle_problem.build(spec)
+    _cmp_csr(lp.K, op.K)
+    _cmp_csr(lp.M, op.M)
+    _cmp_csr(lp.P, op.P)
+    _cmp_csr(lp.P0, op.P0)
+    np.testing.assert_array_equal(lp.part.sub_ptr, op.sub_ptr)
+    np.testing.assert_array_equal(lp.part.sub_dofs, op.sub_dofs)
+    np.testing.assert_array_equal(lp.part.sub_color, op.sub_color)
+    assert lp.part.n_colors == op.n_colors
+
+
+def test_c2_generators_match_oracle_full_size():
+    """The 261121-dof C2 workload: patterns and maps bit-exact at full size."""
+    from workloads import config_c2
+    spec = config_c2()
+    lp = B.problem_from_spec(spec)
+    from oracle import fem, partition
+    K, M = fem.assemble(spec)
+    _cmp_csr(lp.K, K)
+    _cmp_csr(lp.M, M)
+    ptr, dofs, col, nc = partition.box_partition(spec)
+    np.testing.assert_array_equal(lp.part.sub_ptr, ptr)
+    np.testing.assert_array_equal(lp.part.sub_dofs, dofs)
+
+
+def test_problem_create_rejects_bad_mesh():
+    with pytest.raises(B.BpjdError) as e:
+        B.problem_create("p1_2d", (10, 10), (1.0, 1.0), (3, 3), 1)      # 10 not a multiple of 3
+    assert e.value.code == B.ERR_BAD_ARG
+
+
+def _c1_arrays():
+    return B.problem_from_spec(config_c1())
+
+
+def test_setup_rejects_invalid_csr():
+    pb = _c1_arrays()
+    bad = B.CsrArrays(pb.K.n_rows, pb.K.n_cols, pb.K.row_ptr.copy(), pb.K.col_idx.copy(), pb.K.val)
+    bad.col_idx[1], bad.col_idx[2] = bad.col_idx[2], bad.col_idx[1]           # unsorted row
+    with pytest.raises(B.BpjdError) as e:
+        B.Solver(bad, pb.M, pb.P, pb.P0, pb.part, 6)
+    assert e.value.code == B.ERR_CSR_INVALID
+    bad2 = B.CsrArrays(pb.K.n_rows, pb.K.n_cols, pb.K.row_ptr, pb.K.col_idx.copy(), pb.K.val)
+    bad2.col_idx[5] = pb.K.n_cols                                              # out of range
+    with pytest.raises(B.BpjdError) as e:
+        B.Solver(bad2, pb.M, pb.P, pb.P0, pb.part, 6)
+    assert e.value.code == B.ERR_CSR_INVALID
+
+
+def test_setup_rejects_invalid_map_and_k():
+    pb = _c1_arrays()
+    dofs = pb.part.sub_dofs.copy()
+    dofs[3], dofs[4] = dofs[4], dofs[3]
+    part = B.PartitionArrays(pb.part.sub_ptr, dofs, pb.part.sub_color, 4)
+    with pytest.raises(B.BpjdError) as e:
+        B.Solver(pb.K, pb.M, pb.P, pb.P0, part, 6)
+    assert e.value.code == B.ERR_MAP_INVALID
+    with pytest.raises(B.BpjdError) as e:
+        B.Solver(pb.K, pb.M, pb.P, None, pb.part, 9)                          # n_H = 9
+    assert e.value.code == B.ERR_K_TOO_LARGE
+    with pytest.raises(B.BpjdError) as e:
+        B.Solver(pb.K, pb.M, pb.P, None, pb.part, 0)
+    assert e.value.code == B.ERR_BAD_ARG
