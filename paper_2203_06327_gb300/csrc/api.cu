@@ -375,6 +375,14 @@ extern "C" int bpjd_setup(const bpjd_csr* A, const bpjd_csr* M, const bpjd_csr* 
       for (int p = 0; p < nl; ++p) loc[d[p]] = -1;
     }
     h->B = bw + 1;
+    if (h->precision == BPJD_MIXED) {
+      static const int tiers[] = {16, 24, 32, 40, 48, 64};
+      for (int t : tiers)
+        if (h->B <= t) {
+          h->Bpad = t;
+          break;
+        }
+    }
     {
       const int B = h->B;
       posK.assign((size_t)sum_nl * B, -1);
@@ -400,8 +408,9 @@ extern "C" int bpjd_setup(const bpjd_csr* A, const bpjd_csr* M, const bpjd_csr* 
       CK(dalloc(*h, &h->bandK, (size_t)sum_nl * B));
       CK(dalloc(*h, &h->bandM, (size_t)sum_nl * B));
       if (h->precision == BPJD_MIXED) {
-        CK(dalloc(*h, &h->bandKf, (size_t)sum_nl * B));
-        CK(dalloc(*h, &h->bandMf, (size_t)sum_nl * B));
+        const size_t W = (size_t)std::max(h->B, h->Bpad);
+        CK(dalloc(*h, &h->bandKf, (size_t)sum_nl * W));
+        CK(dalloc(*h, &h->bandMf, (size_t)sum_nl * W));
       }
       CK(cudaMalloc(&dposK, sizeof(int64_t) * sum_nl * B));
       CK(cudaMemcpyAsync(dposK, posK.data(), sizeof(int64_t) * sum_nl * B, cudaMemcpyHostToDevice, h->stream));
@@ -470,10 +479,11 @@ extern "C" int bpjd_setup(const bpjd_csr* A, const bpjd_csr* M, const bpjd_csr* 
     // scratch and iteration vectors
     {
       const size_t esz = (h->precision == BPJD_MIXED) ? sizeof(float) : sizeof(double);
+      const size_t lw = (size_t)std::max(h->B, h->Bpad);
       void* p;
-      CK(cudaMalloc(&p, esz * (size_t)sum_nl * k * h->B));
+      CK(cudaMalloc(&p, esz * (size_t)sum_nl * k * lw));
       h->allocs.push_back(p);
-      h->bytes += esz * (size_t)sum_nl * k * h->B;
+      h->bytes += esz * (size_t)sum_nl * k * lw;
       h->Lbuf = p;
       CK(cudaMalloc(&p, esz * (size_t)sum_nl * k));
       h->allocs.push_back(p);

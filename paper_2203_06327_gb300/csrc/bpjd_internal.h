@@ -40,6 +40,7 @@ struct Handle {
   // ---- sizes and options
   int32_t n = 0, nH = 0, nH0 = 0, k = 0, nsub = 0;
   int32_t B = 0;            // band window: lower bandwidth + 1 (max over subdomains)
+  int32_t Bpad = 0;         // register-window size of the FP32 local kernel (0: shared-memory kernel)
   int64_t sum_nl = 0;       // sum of local sizes
   int32_t max_nl = 0;
   int32_t precision = BPJD_FP64, subspace = BPJD_W_2K, stop_rule = BPJD_STOP_RESIDUAL;

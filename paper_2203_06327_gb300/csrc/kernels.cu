@@ -377,6 +377,503 @@ __global__ void k_local_band(int npairs, int k, const int64_t* __restrict__ sub_
   }
 }
 
+// ---------------------------------------------------------------------------
+// Local solves, register-window variant (FP32): same banded Cholesky as
+// k_local_band, with the B x B symmetric window held in registers.  Window
+// size BMAX >= B (the band is zero-padded); lane v owns window columns v and
+// v + 32 (slot u of a column = row u mod BMAX).  Steps are unrolled in groups
+// of BMAX so that the pivot slot s = j mod BMAX is a compile-time index.  The
+// column of L at step j is broadcast through shared memory; the new band row
+// j + BMAX enters slot s (each lane loads its own entry, the owner of column
+// s gathers the full row from shared memory).
+// ---------------------------------------------------------------------------
+template <int BMAX>
+__global__ void __launch_bounds__(128, (BMAX <= 32) ? 4 : ((BMAX <= 40) ? 3 : 2)) k_local_band_reg(
+    int npairs, int k, const int64_t* __restrict__ sub_ptr, const int32_t* __restrict__ sub_dofs, int Bt,
+    const float* __restrict__ bandK, const float* __restrict__ bandM, const double* __restrict__ lam,
+    const double* __restrict__ rho, float* __restrict__ Lbuf, float* __restrict__ wpk, int32_t* err) {
+  constexpr int NC = (BMAX + 31) / 32;
+  constexpr int PD = (BMAX >= 40) ? 2 : 4;  // prefetch distance (steps) of the rows entering the window
+  static_assert(BMAX % PD == 0, "the prefetch ring index must be static within a window group");
+  constexpr unsigned FULL = 0xffffffffu;
+  __shared__ __align__(16) float shm[4][3][64];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int pair = blockIdx.x * (blockDim.x >> 5) + wib;
+  if (pair >= npairs) return;
+  float* sl = shm[wib][0];
+  float* sa = shm[wib][1];
+  float* xs = shm[wib][2];
+  const int l = pair / k, i = pair % k;
+  const int64_t off = sub_ptr[l];
+  const int nl = (int)(sub_ptr[l + 1] - off);
+  const int32_t* dofs = sub_dofs + off;
+  const int bt = Bt - 1;
+  const float lm = (float)lam[i];
+  float* Lp = Lbuf + ((size_t)off * k + (size_t)i * nl) * BMAX;
+  auto aval = [&](int p, int q) -> float {  // shifted entry (p, q), q <= p
+    if (p >= nl) return (p == q) ? 1.f : 0.f;
+    const int d = p - q;
+    if (d > bt || q < 0) return 0.f;
+    const size_t e = (size_t)(off + p) * Bt + (bt - d);
+    return bandK[e] - lm * bandM[e];
+  };
+  auto rhs = [&](int p) -> float { return (p < nl) ? (float)rho[(int64_t)dofs[p] * k + i] : 0.f; };
+  // entry of row j + BMAX that column v receives at step j (slot s = j mod BMAX)
+  auto incoming = [&](int j, int s, int v) -> float {
+    int t = v - s;
+    t += (t <= 0) ? BMAX : 0;
+    return aval(j + BMAX, j + t);
+  };
+  float w[NC][BMAX];
+  float rw[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    const int v = lane + 32 * c;
+#pragma unroll
+    for (int u = 0; u < BMAX; ++u) {
+      float x = 0.f;
+      if (v < BMAX) x = (u >= v) ? aval(u, v) : aval(v, u);
+      w[c][u] = x;
+    }
+    rw[c] = (v < BMAX) ? rhs(v) : 0.f;
+  }
+  // prefetch ring: pre[d] holds the incoming entries of step j when j mod PD == d
+  float pre[PD][NC];
+  float rpre[PD];
+#pragma unroll
+  for (int d = 0; d < PD; ++d) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const int v = lane + 32 * c;
+      pre[d][c] = (v < BMAX) ? incoming(d, d % BMAX, v) : 0.f;
+    }
+    rpre[d] = rhs(d + BMAX);
+  }
+  bool bad = false;
+  for (int j0 = 0; j0 < nl && !bad; j0 += BMAX) {
+    // an opaque zero keeps the per-slot lane offsets from being hoisted out of
+    // this loop (BMAX copies of them would otherwise occupy registers)
+    int zero;
+    asm volatile("mov.u32 %0, 0;" : "=r"(zero));
+    const int vl = lane + zero;
+#pragma unroll
+    for (int s = 0; s < BMAX; ++s) {
+      const int j = j0 + s;
+      if (j >= nl) break;
+      const int sc = s >> 5, so = s & 31;
+      const int pd = s % PD;  // ring slot of step j (j0 is a multiple of BMAX, hence of PD)
+      const float piv = __shfl_sync(FULL, w[sc][s], so);
+      if (!(piv > 0.f)) {
+        bad = true;
+        break;
+      }
+      const float inv = __frsqrt_rn(piv);
+      const float yj = __shfl_sync(FULL, rw[sc], so) * inv;
+      float lc[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const int v = vl + 32 * c;
+        lc[c] = (v < BMAX && v != s) ? w[c][s] * inv : 0.f;
+        if (v < BMAX) {
+          int t = v - s;
+          t += (t < 0) ? BMAX : 0;
+          Lp[(size_t)j * BMAX + t] = (t == 0) ? inv : lc[c];
+          sl[v] = lc[c];
+        }
+      }
+      if (lane == 0) wpk[(off + j) * k + i] = yj;
+      __syncwarp();
+#pragma unroll
+      for (int u4 = 0; u4 < BMAX; u4 += 4) {
+        const float4 q = *reinterpret_cast<const float4*>(sl + u4);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          w[c][u4 + 0] = fmaf(-q.x, lc[c], w[c][u4 + 0]);
+          w[c][u4 + 1] = fmaf(-q.y, lc[c], w[c][u4 + 1]);
+          w[c][u4 + 2] = fmaf(-q.z, lc[c], w[c][u4 + 2]);
+          w[c][u4 + 3] = fmaf(-q.w, lc[c], w[c][u4 + 3]);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < NC; ++c) rw[c] = fmaf(-lc[c], yj, rw[c]);
+      // row j + BMAX (prefetched PD steps ago) enters slot s
+      float anew[NC];
+      float rnew = 0.f;
+#pragma unroll
+      for (int d = 0; d < PD; ++d)
+        if (d == pd) {
+#pragma unroll
+          for (int c = 0; c < NC; ++c) anew[c] = pre[d][c];
+          rnew = rpre[d];
+        }
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const int v = vl + 32 * c;
+        if (v < BMAX) {
+          w[c][s] = anew[c];
+          sa[v] = anew[c];
+        }
+      }
+      // prefetch the entries for step j + PD into the freed ring slot
+      {
+        const int jn = j + PD;
+        const int sn = (s + PD) % BMAX;
+        float nv[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          const int v = vl + 32 * c;
+          nv[c] = (v < BMAX) ? incoming(jn, sn, v) : 0.f;
+        }
+        const float nr = rhs(jn + BMAX);
+#pragma unroll
+        for (int d = 0; d < PD; ++d)
+          if (d == pd) {
+#pragma unroll
+            for (int c = 0; c < NC; ++c) pre[d][c] = nv[c];
+            rpre[d] = nr;
+          }
+      }
+      __syncwarp();
+      if (lane == so) {
+#pragma unroll
+        for (int u4 = 0; u4 < BMAX; u4 += 4) {
+          const float4 q = *reinterpret_cast<const float4*>(sa + u4);
+          w[sc][u4 + 0] = q.x;
+          w[sc][u4 + 1] = q.y;
+          w[sc][u4 + 2] = q.z;
+          w[sc][u4 + 3] = q.w;
+        }
+        rw[sc] = rnew;
+      }
+      __syncwarp();
+    }
+  }
+  if (bad) {
+    if (lane == 0) atomicOr(err, 1);
+    return;
+  }
+  // backward substitution with L^T; x window in shared memory (slot = row mod BMAX),
+  // the L columns and right-hand sides of the next two rows are prefetched
+  for (int v = lane; v < BMAX; v += 32) xs[v] = 0.f;
+  __syncwarp();
+  float lrow[2][NC], yv[2], linv[2];
+  auto load_row = [&](int j, float* lr, float& y, float& li) {
+    if (j < 0) return;
+    const int s = j % BMAX;
+    const float* row = Lp + (size_t)j * BMAX;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const int v = lane + 32 * c;
+      int t = v - s;
+      t += (t < 0) ? BMAX : 0;
+      lr[c] = (v < BMAX && t > 0 && j + t < nl) ? row[t] : 0.f;
+    }
+    y = wpk[(off + j) * k + i];
+    li = row[0];
+  };
+  load_row(nl - 1, lrow[0], yv[0], linv[0]);
+  load_row(nl - 2, lrow[1], yv[1], linv[1]);
+  for (int j = nl - 1; j >= 0; --j) {
+    const int cur = (nl - 1 - j) & 1;
+    float lr[NC], y, li;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) lr[c] = cur ? lrow[1][c] : lrow[0][c];
+    y = cur ? yv[1] : yv[0];
+    li = cur ? linv[1] : linv[0];
+    if (cur)
+      load_row(j - 2, lrow[1], yv[1], linv[1]);
+    else
+      load_row(j - 2, lrow[0], yv[0], linv[0]);
+    float part = 0.f;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const int v = lane + 32 * c;
+      if (v < BMAX) part = fmaf(lr[c], xs[v], part);
+    }
+    part = warp_sum(part);
+    const float xj = (y - part) * li;
+    __syncwarp();
+    if (lane == 0) {
+      xs[j % BMAX] = xj;
+      wpk[(off + j) * k + i] = xj;
+    }
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Local solves, register window + TMA-streamed band (FP32).  One CTA of four
+// warps per (subdomain l, four shifts): the warps share the band rows of
+// K_l and M_l, which enter shared memory one window group (BMAX rows) ahead
+// through 1-D bulk tensor copies completing on an mbarrier; each warp runs the
+// banded factorisation of its own shift with the window in registers (lane v
+// owns window columns v and v + 32, slot u = row mod BMAX) and stores the
+// columns of L in slot order.  The FP32 band is stored with width BMAX (zero
+// padded on the left), so that window slot and band position map statically.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+// Bounded wait on an mbarrier phase; false after the iteration limit.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  for (int it = 0; it < (1 << 22); ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+constexpr int kLocalWarps = 4;
+
+template <int BMAX>
+__global__ void __launch_bounds__(128, (BMAX <= 32) ? 4 : ((BMAX <= 40) ? 3 : 2)) k_local_band_tma(
+    int nsub, int k, const int64_t* __restrict__ sub_ptr, const int32_t* __restrict__ sub_dofs,
+    const float* __restrict__ bandK, const float* __restrict__ bandM, const double* __restrict__ lam,
+    const double* __restrict__ rho, float* __restrict__ Lbuf, float* __restrict__ wpk, int32_t* err) {
+  constexpr int NC = (BMAX + 31) / 32;
+  constexpr unsigned FULL = 0xffffffffu;
+  constexpr uint32_t kChunkBytes = BMAX * BMAX * sizeof(float);
+  __shared__ __align__(128) float sK[2][BMAX * BMAX];
+  __shared__ __align__(128) float sM[2][BMAX * BMAX];
+  __shared__ __align__(16) float sw[kLocalWarps][4][64];
+  __shared__ __align__(8) uint64_t bars[2];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int groups_per_sub = (k + kLocalWarps - 1) / kLocalWarps;
+  const int l = blockIdx.x / groups_per_sub;
+  const int i = (blockIdx.x % groups_per_sub) * kLocalWarps + wib;
+  const bool active = (i < k);
+  const int ii = active ? i : 0;
+  float* sl = sw[wib][0];
+  float* sa = sw[wib][1];
+  float* xs = sw[wib][2];
+  float* sr = sw[wib][3];
+  const int64_t off = sub_ptr[l];
+  const int nl = (int)(sub_ptr[l + 1] - off);
+  const int32_t* dofs = sub_dofs + off;
+  const float lm = (float)lam[ii];
+  float* Lp = Lbuf + ((size_t)off * k + (size_t)ii * nl) * BMAX;
+  const float* gK = bandK + (size_t)off * BMAX;  // band row p at gK + p * BMAX, diagonal at BMAX - 1
+  const float* gM = bandM + (size_t)off * BMAX;
+  const int ngroups = (nl + BMAX - 1) / BMAX;
+  // chunk c = band rows [BMAX (c + 1), BMAX (c + 2)) ∩ [0, nl): the rows entering during group c
+  auto issue_chunk = [&](int c) {
+    const int r0 = BMAX * (c + 1);
+    if (r0 >= nl) return;
+    const int rows = min(BMAX, nl - r0);
+    const uint32_t bytes = (uint32_t)rows * BMAX * sizeof(float);
+    uint64_t* bar = &bars[c & 1];
+    mbar_expect_tx(bar, 2 * bytes);
+    bulk_load(sK[c & 1], gK + (size_t)r0 * BMAX, bytes, bar);
+    bulk_load(sM[c & 1], gM + (size_t)r0 * BMAX, bytes, bar);
+  };
+  if (threadIdx.x == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) issue_chunk(0);
+  (void)kChunkBytes;
+  // initial window rows 0..BMAX-1 straight from global memory
+  auto a0 = [&](int p, int q) -> float {  // q <= p < BMAX
+    if (p >= nl) return (p == q) ? 1.f : 0.f;
+    const int e = BMAX - 1 - (p - q);
+    return gK[(size_t)p * BMAX + e] - lm * gM[(size_t)p * BMAX + e];
+  };
+  auto rhs = [&](int p) -> float { return (p < nl) ? (float)rho[(int64_t)dofs[p] * k + ii] : 0.f; };
+  float w[NC][BMAX];
+  float rw[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    const int v = lane + 32 * c;
+#pragma unroll
+    for (int u = 0; u < BMAX; ++u) {
+      float x = 0.f;
+      if (v < BMAX) x = (u >= v) ? a0(u, v) : a0(v, u);
+      w[c][u] = x;
+    }
+    rw[c] = (v < BMAX) ? rhs(v) : 0.f;
+  }
+  // right-hand sides of the rows entering in group c are staged in sr[] at the
+  // start of group c; rn holds those of the next group (loaded one group ahead)
+  float rn[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    const int v = lane + 32 * c;
+    rn[c] = (v < BMAX) ? rhs(BMAX + v) : 0.f;
+  }
+  bool bad = false, timeout = false;
+  for (int g = 0; g < ngroups; ++g) {
+    const int j0 = g * BMAX;
+    __syncthreads();  // every warp is done with group g - 1: its buffer may be refilled
+    if (threadIdx.x == 0) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue_chunk(g + 1);
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const int v = lane + 32 * c;
+      if (v < BMAX) sr[v] = rn[c];
+      rn[c] = (v < BMAX) ? rhs(BMAX * (g + 2) + v) : 0.f;
+    }
+    const bool have_chunk = BMAX * (g + 1) < nl;
+    if (have_chunk && !mbar_wait_bounded(&bars[g & 1], (uint32_t)((g >> 1) & 1))) timeout = true;
+    __syncwarp();
+    const float* cK = sK[g & 1];
+    const float* cM = sM[g & 1];
+    int zero;
+    asm volatile("mov.u32 %0, 0;" : "=r"(zero));
+    const int vl = lane + zero;
+#pragma unroll
+    for (int s = 0; s < BMAX; ++s) {
+      const int j = j0 + s;
+      if (j >= nl) break;
+      const int sc = s >> 5, so = s & 31;
+      float piv = __shfl_sync(FULL, w[sc][s], so);
+      if (!(piv > 0.f)) {
+        bad = true;
+        piv = 1.f;
+      }
+      const float inv = rsqrtf(piv);
+      const float yj = __shfl_sync(FULL, rw[sc], so) * inv;
+      float lc[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const int v = vl + 32 * c;
+        lc[c] = (v != s) ? w[c][s] * inv : 0.f;
+        if (v < BMAX) {
+          if (active) Lp[(size_t)j * BMAX + v] = (v == s) ? inv : lc[c];
+          sl[v] = lc[c];
+        }
+      }
+      if (lane == 0 && active) wpk[(off + j) * k + ii] = yj;
+      __syncwarp();
+#pragma unroll
+      for (int u4 = 0; u4 < BMAX; u4 += 4) {
+        const float4 q = *reinterpret_cast<const float4*>(sl + u4);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          w[c][u4 + 0] = fmaf(-q.x, lc[c], w[c][u4 + 0]);
+          w[c][u4 + 1] = fmaf(-q.y, lc[c], w[c][u4 + 1]);
+          w[c][u4 + 2] = fmaf(-q.z, lc[c], w[c][u4 + 2]);
+          w[c][u4 + 3] = fmaf(-q.w, lc[c], w[c][u4 + 3]);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < NC; ++c) rw[c] = fmaf(-lc[c], yj, rw[c]);
+      // row pn = j + BMAX enters slot s; column v receives entry (pn, j + t),
+      // t = (v - s) mod BMAX in 1..BMAX, band position t - 1
+      const int pn = j + BMAX;
+      const bool real = pn < nl;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const int v = vl + 32 * c;
+        if (v < BMAX) {
+          int t = v - s;
+          t += (t <= 0) ? BMAX : 0;
+          float a;
+          if (real)
+            a = cK[s * BMAX + t - 1] - lm * cM[s * BMAX + t - 1];
+          else
+            a = (t == BMAX) ? 1.f : 0.f;
+          w[c][s] = a;
+          sa[v] = a;
+        }
+      }
+      __syncwarp();
+      if (lane == so) {
+#pragma unroll
+        for (int u4 = 0; u4 < BMAX; u4 += 4) {
+          const float4 q = *reinterpret_cast<const float4*>(sa + u4);
+          w[sc][u4 + 0] = q.x;
+          w[sc][u4 + 1] = q.y;
+          w[sc][u4 + 2] = q.z;
+          w[sc][u4 + 3] = q.w;
+        }
+        rw[sc] = sr[s];
+      }
+      __syncwarp();
+    }
+  }
+  if (bad || timeout) {
+    if (lane == 0 && active) atomicOr(err, timeout ? 2 : 1);
+  }
+  if (bad || timeout || !active) return;
+  // backward substitution with L^T: x window by slot in shared memory; row j of L
+  // holds 1/L_jj at slot j mod BMAX and L(row(v), j) at slot v.  A ring of PB
+  // rows is prefetched.
+  constexpr int PB = 4;
+  for (int v = lane; v < BMAX; v += 32) xs[v] = 0.f;
+  __syncwarp();
+  float lr[PB][NC], yv[PB];
+  auto load_row = [&](int j, int d) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const int v = lane + 32 * c;
+      lr[d][c] = (j >= 0 && v < BMAX) ? Lp[(size_t)j * BMAX + v] : 0.f;
+    }
+    yv[d] = (j >= 0) ? wpk[(off + j) * k + ii] : 0.f;
+  };
+#pragma unroll
+  for (int d = 0; d < PB; ++d) load_row(nl - 1 - d, d);
+  int j = nl - 1;
+  while (j >= 0) {
+#pragma unroll
+    for (int d = 0; d < PB; ++d) {
+      if (j >= 0) {
+        const int s = j % BMAX;
+        float part = 0.f;
+        float invj = 0.f;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          const int v = lane + 32 * c;
+          if (v < BMAX) {
+            if (v == s)
+              invj = lr[d][c];
+            else
+              part = fmaf(lr[d][c], xs[v], part);
+          }
+        }
+        const float y = yv[d];
+        load_row(j - PB, d);
+        part = warp_sum(part);
+        invj = warp_sum(invj);
+        const float xj = (y - part) * invj;
+        __syncwarp();
+        if (lane == 0) {
+          xs[s] = xj;
+          wpk[(off + j) * k + ii] = xj;
+        }
+        __syncwarp();
+        --j;
+      }
+    }
+  }
+}
+
 // c[a, i] = sum_{g} P[g, a] rho[g, i] using P^T (CSR n_H x n); one block per coarse dof.
 __global__ void k_coarse_restrict(int nH, int k, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
                                   const double* __restrict__ pv, const double* __restrict__ rho, double* c) {
@@ -550,10 +1047,9 @@ __device__ void sort_diag(const double* A, int m, int* ord) {
 // G, H: m x m (row-major, ld m).  First k columns of W are b-orthonormal Ritz
 // vectors, the rest are scaled to unit M-norm.  Output C (m x k, ld k),
 // lam_new (k), hist row, status.
-__global__ void k_rayleigh_ritz(int m, int k, const double* __restrict__ G, const double* __restrict__ H,
-                                double drop_tol, const double* __restrict__ lam_old, double* C, double* lam_new,
-                                double* hist_row, int stop_rule, double tol, DevStatus* st) {
-  extern __shared__ double rr[];
+__device__ void rayleigh_ritz_eig(int m, int k, const double* __restrict__ G, const double* __restrict__ H,
+                                  double drop_tol, const double* __restrict__ lam_old, double* C, double* lam_new,
+                                  double* hist_row, int stop_rule, double tol, DevStatus* st, double* rr) {
   const int ld = kRRMax;
   double* A = rr;                  // ld x ld
   double* V = A + ld * ld;         // ld x ld
@@ -653,17 +1149,249 @@ __global__ void k_rayleigh_ritz(int m, int k, const double* __restrict__ G, cons
   }
 }
 
+// Parallel cyclic Jacobi, one pass per round: with the round's disjoint
+// rotations J, A' = J^T A J is formed element-wise from the old A (4 terms per
+// entry, lower triangle mirrored) into a second buffer, and V' = V J.
+// A, A2, V, V2 have leading dimension kRRMax; returns (via the buffers that end
+// up holding the result) pointers in *Aout / *Vout.
+__device__ void jacobi_eig_sym(double* A, double* A2, double* V, double* V2, int m, double** Aout, double** Vout,
+                               double* fr, double* gr, int* partner) {
+  const int mp = m + (m & 1);
+  const int ld = kRRMax;
+  const int tid = threadIdx.x;
+  __shared__ int done;
+  for (int t = tid; t < mp * ld; t += blockDim.x) {
+    int r = t / ld, c = t % ld;
+    V[t] = (r == c) ? 1.0 : 0.0;
+    if ((r >= m || c >= m) && c < mp) A[t] = 0.0;
+  }
+  __syncthreads();
+  const int half = mp / 2;
+  // lower-triangle index list (r >= c)
+  __shared__ unsigned char tri_r[kRRMax * (kRRMax + 1) / 2], tri_c[kRRMax * (kRRMax + 1) / 2];
+  if (tid == 0) {
+    int t = 0;
+    for (int r = 0; r < mp; ++r)
+      for (int c = 0; c <= r; ++c) {
+        tri_r[t] = (unsigned char)r;
+        tri_c[t] = (unsigned char)c;
+        ++t;
+      }
+  }
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    if (tid == 0) done = 1;
+    __syncthreads();
+    for (int round = 0; round < mp - 1; ++round) {
+      if (tid < half) {
+        int e0 = 0, e1;
+        auto ring = [&](int pos) { return ((pos + round) % (mp - 1)) + 1; };
+        if (tid == 0) {
+          e1 = ring(0);
+        } else {
+          e0 = ring(tid);
+          e1 = ring(mp - 1 - tid);
+        }
+        const int p = min(e0, e1), q = max(e0, e1);
+        const double apq = A[p * ld + q], app = A[p * ld + p], aqq = A[q * ld + q];
+        double c = 1.0, s = 0.0;
+        if (fabs(apq) > 1e-300 && fabs(apq) > 1e-17 * sqrt(fabs(app * aqq))) {
+          const double tau = (aqq - app) / (2.0 * apq);
+          const double tt = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+          c = 1.0 / sqrt(1.0 + tt * tt);
+          s = tt * c;
+          done = 0;
+        }
+        // J[p][p] = c, J[q][p] = -s, J[p][q] = s, J[q][q] = c
+        fr[p] = c;
+        gr[p] = -s;
+        partner[p] = q;
+        fr[q] = c;
+        gr[q] = s;
+        partner[q] = p;
+      }
+      __syncthreads();
+      for (int t = tid; t < mp * (mp + 1) / 2; t += blockDim.x) {
+        const int r = tri_r[t], c = tri_c[t];
+        const int rb = partner[r], cb = partner[c];
+        const double v = fr[r] * (fr[c] * A[r * ld + c] + gr[c] * A[r * ld + cb]) +
+                         gr[r] * (fr[c] * A[rb * ld + c] + gr[c] * A[rb * ld + cb]);
+        A2[r * ld + c] = v;
+        A2[c * ld + r] = v;
+      }
+      for (int t = tid; t < mp * mp; t += blockDim.x) {
+        const int x = t / mp, r = t % mp;
+        V2[x * ld + r] = V[x * ld + r] * fr[r] + V[x * ld + partner[r]] * gr[r];
+      }
+      __syncthreads();
+      double* tA = A;
+      A = A2;
+      A2 = tA;
+      double* tV = V;
+      V = V2;
+      V2 = tV;
+    }
+    if (done) break;
+    __syncthreads();
+  }
+  *Aout = A;
+  *Vout = V;
+}
+
+// Rayleigh-Ritz (Eq. (3.6)) with a Cholesky orthonormalisation of the scaled
+// Gram matrix G' = L L^T.  When the lower bound 1 / ||L^{-1}||_F^2 of the
+// smallest eigenvalue of G' exceeds drop_tol * trace(G') >= drop_tol * lambda_max,
+// the eigen-based basis of k_rayleigh_ritz would keep every direction, so both
+// produce the Ritz pairs of the same space; the reduced matrix
+// H'' = L^{-1} H' L^{-T} is diagonalised by one symmetric Jacobi.  Otherwise the
+// eigen-based path with dropping runs.
+__global__ void k_rayleigh_ritz_chol(int m, int k, const double* __restrict__ G, const double* __restrict__ H,
+                                     double drop_tol, const double* __restrict__ lam_old, double* C,
+                                     double* lam_new, double* hist_row, int stop_rule, double tol, DevStatus* st) {
+  extern __shared__ double rr[];
+  const int ld = kRRMax;
+  const int LL = ld * ld;
+  double* B0 = rr;
+  double* B1 = B0 + LL;
+  double* B2 = B1 + LL;
+  double* B3 = B2 + LL;
+  double* B4 = B3 + LL;
+  double* sc = B4 + LL;
+  double* fr = sc + ld;
+  double* gr = fr + ld;
+  int* partner = reinterpret_cast<int*>(gr + ld);
+  int* ord = partner + ld;
+  __shared__ int ok;
+  __shared__ double crit_lhs, crit_rhs;
+  const int tid = threadIdx.x;
+  for (int j = tid; j < m; j += blockDim.x) {
+    const double g = G[j * m + j];
+    sc[j] = (j < k) ? 1.0 : (g > 0 ? 1.0 / sqrt(g) : 0.0);
+  }
+  if (tid == 0) ok = 1;
+  __syncthreads();
+  // B0 = G' (becomes L), B1 = H'
+  for (int t = tid; t < m * m; t += blockDim.x) {
+    const int a = t / m, b = t % m;
+    B0[a * ld + b] = 0.5 * (G[a * m + b] + G[b * m + a]) * sc[a] * sc[b];
+    B1[a * ld + b] = 0.5 * (H[a * m + b] + H[b * m + a]) * sc[a] * sc[b];
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double tr = 0;
+    for (int j = 0; j < m; ++j) tr += B0[j * ld + j];
+    crit_rhs = drop_tol * tr;
+  }
+  // right-looking Cholesky in place (lower triangle)
+  for (int j = 0; j < m; ++j) {
+    if (tid == 0) {
+      const double d = B0[j * ld + j];
+      if (!(d > 0.0)) ok = 0;
+      B0[j * ld + j] = (d > 0.0) ? sqrt(d) : 1.0;
+    }
+    __syncthreads();
+    const double ljj = B0[j * ld + j];
+    for (int i = j + 1 + tid; i < m; i += blockDim.x) B0[i * ld + j] /= ljj;
+    __syncthreads();
+    const int rem = m - j - 1;
+    for (int t = tid; t < rem * rem; t += blockDim.x) {
+      const int i = j + 1 + t / rem, c = j + 1 + t % rem;
+      if (c <= i) B0[i * ld + c] -= B0[i * ld + j] * B0[c * ld + j];
+    }
+    __syncthreads();
+  }
+  // B2 = L^{-1} (column c by forward substitution, one thread per column)
+  for (int c = tid; c < m; c += blockDim.x) {
+    for (int i = 0; i < m; ++i) {
+      if (i < c) {
+        B2[i * ld + c] = 0.0;
+        continue;
+      }
+      double s = (i == c) ? 1.0 : 0.0;
+      for (int t = c; t < i; ++t) s -= B0[i * ld + t] * B2[t * ld + c];
+      B2[i * ld + c] = s / B0[i * ld + i];
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double f = 0;
+    for (int i = 0; i < m; ++i)
+      for (int c = 0; c <= i; ++c) f += B2[i * ld + c] * B2[i * ld + c];
+    crit_lhs = 1.0 / f;
+    if (!(crit_lhs > crit_rhs)) ok = 0;
+  }
+  __syncthreads();
+  if (!ok) {
+    // ill-conditioned basis: eigen-based orthonormalisation with dropping
+    rayleigh_ritz_eig(m, k, G, H, drop_tol, lam_old, C, lam_new, hist_row, stop_rule, tol, st, rr);
+    return;
+  }
+  // B3 = H' L^{-T};  B4 = L^{-1} B3  (= H'')
+  for (int t = tid; t < m * m; t += blockDim.x) {
+    const int a = t / m, b = t % m;
+    double s = 0;
+    for (int c = 0; c <= b; ++c) s = fma(B1[a * ld + c], B2[b * ld + c], s);
+    B3[a * ld + b] = s;
+  }
+  __syncthreads();
+  for (int t = tid; t < m * m; t += blockDim.x) {
+    const int a = t / m, b = t % m;
+    if (a < b) continue;
+    double s = 0;
+    for (int c = 0; c <= a; ++c) s = fma(B2[a * ld + c], B3[c * ld + b], s);
+    B4[a * ld + b] = s;
+  }
+  __syncthreads();
+  for (int t = tid; t < m * m; t += blockDim.x) {
+    const int a = t / m, b = t % m;
+    if (a < b) B4[a * ld + b] = B4[b * ld + a];
+  }
+  __syncthreads();
+  // eigen-decomposition of H'' (A: B4/B0, V: B1/B3; B2 = L^{-1} is kept)
+  double *Ar, *Vr;
+  jacobi_eig_sym(B4, B0, B1, B3, m, &Ar, &Vr, fr, gr, partner);
+  sort_diag(Ar, m, ord);
+  // C = diag(sc) L^{-T} Y[:, 0..k)
+  for (int t = tid; t < m * k; t += blockDim.x) {
+    const int a = t / k, c = t % k;
+    const int j = ord[c];
+    double s = 0;
+    for (int b = a; b < m; ++b) s = fma(B2[b * ld + a], Vr[b * ld + j], s);
+    C[a * k + c] = sc[a] * s;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double dl = 0;
+    for (int c = 0; c < k; ++c) {
+      const double th = Ar[ord[c] * ld + ord[c]];
+      dl += fabs(th - lam_old[c]);
+      lam_new[c] = th;
+      if (hist_row) hist_row[c] = th;
+    }
+    st->sum_dl = dl;
+    st->kept = m;
+    if (stop_rule == BPJD_STOP_DLAMBDA) st->converged = (dl < tol) ? 1 : 0;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Setup kernels
 // ---------------------------------------------------------------------------
 __global__ void k_band_gather(int64_t total, const int64_t* __restrict__ pos, const double* __restrict__ val,
-                              double* out, float* outf) {
+                              double* out) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= total) return;
   int64_t p = pos[t];
-  double a = (p >= 0) ? val[p] : 0.0;
-  out[t] = a;
-  if (outf) outf[t] = (float)a;
+  out[t] = (p >= 0) ? val[p] : 0.0;
+}
+
+// FP32 copy of a band of width B into width W >= B, zero-padded on the left
+// (the diagonal stays in the last position of each row).
+__global__ void k_band_pad_f32(int64_t rows, int B, int W, const double* __restrict__ in, float* __restrict__ out) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= rows * W) return;
+  const int64_t r = t / W;
+  const int e = (int)(t % W) - (W - B);
+  out[t] = (e >= 0) ? (float)in[r * B + e] : 0.f;
 }
 
 // Galerkin products K_H = P^T K P and M_H = P^T M P in two deterministic passes.
@@ -888,21 +1616,46 @@ int launch_precond(Handle& h, const double* rho, const double* lam, double* Z) {
     ProfScope ps(h, BPJD_PROF_LOCAL);
     h.launches += 1;
     const bool f32 = (h.precision == BPJD_MIXED);
-    const size_t esz = f32 ? sizeof(float) : sizeof(double);
-    const size_t per_warp = (size_t)(B * B + 3 * B) * esz;
-    int wpb = (int)std::max<size_t>(1, std::min<size_t>(4, (200 * 1024) / per_warp));
-    size_t sm = per_warp * wpb;
-    int blocks = (npairs + wpb - 1) / wpb;
-    if (f32) {
-      cudaFuncSetAttribute(k_local_band<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      k_local_band<float><<<blocks, 32 * wpb, sm, h.stream>>>(npairs, k, h.sub_ptr, h.sub_dofs, B, h.bandKf,
-                                                              h.bandMf, lam, rho, (float*)h.Lbuf, (float*)h.wpk,
-                                                              h.derr);
+    if (f32 && h.Bpad > 0) {
+      const int blocks = h.nsub * ((k + kLocalWarps - 1) / kLocalWarps);
+#define BPJD_LOCAL_REG(BM)                                                                                   \
+  case BM:                                                                                                   \
+    k_local_band_tma<BM><<<blocks, 32 * kLocalWarps, 0, h.stream>>>(h.nsub, k, h.sub_ptr, h.sub_dofs,        \
+                                                                    h.bandKf, h.bandMf, lam, rho,            \
+                                                                    (float*)h.Lbuf, (float*)h.wpk, h.derr); \
+    break;
+      switch (h.Bpad) {
+        BPJD_LOCAL_REG(16)
+        BPJD_LOCAL_REG(24)
+        BPJD_LOCAL_REG(32)
+        BPJD_LOCAL_REG(40)
+        BPJD_LOCAL_REG(48)
+        case 64:
+          k_local_band_reg<64><<<(npairs + 3) / 4, 128, 0, h.stream>>>(npairs, k, h.sub_ptr, h.sub_dofs, 64,
+                                                                      h.bandKf, h.bandMf, lam, rho,
+                                                                      (float*)h.Lbuf, (float*)h.wpk, h.derr);
+          break;
+        default:
+          return (int)cudaErrorInvalidValue;
+      }
+#undef BPJD_LOCAL_REG
     } else {
-      cudaFuncSetAttribute(k_local_band<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      k_local_band<double><<<blocks, 32 * wpb, sm, h.stream>>>(npairs, k, h.sub_ptr, h.sub_dofs, B, h.bandK,
-                                                               h.bandM, lam, rho, (double*)h.Lbuf,
-                                                               (double*)h.wpk, h.derr);
+      const size_t esz = f32 ? sizeof(float) : sizeof(double);
+      const size_t per_warp = (size_t)(B * B + 3 * B) * esz;
+      int wpb = (int)std::max<size_t>(1, std::min<size_t>(4, (200 * 1024) / per_warp));
+      size_t sm = per_warp * wpb;
+      int blocks = (npairs + wpb - 1) / wpb;
+      if (f32) {
+        cudaFuncSetAttribute(k_local_band<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        k_local_band<float><<<blocks, 32 * wpb, sm, h.stream>>>(npairs, k, h.sub_ptr, h.sub_dofs, B, h.bandKf,
+                                                                h.bandMf, lam, rho, (float*)h.Lbuf, (float*)h.wpk,
+                                                                h.derr);
+      } else {
+        cudaFuncSetAttribute(k_local_band<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        k_local_band<double><<<blocks, 32 * wpb, sm, h.stream>>>(npairs, k, h.sub_ptr, h.sub_dofs, B, h.bandK,
+                                                                 h.bandM, lam, rho, (double*)h.Lbuf,
+                                                                 (double*)h.wpk, h.derr);
+      }
     }
   }
   // coarse solve
@@ -931,19 +1684,24 @@ int launch_precond(Handle& h, const double* rho, const double* lam, double* Z) {
 int launch_rr(Handle& h, int m, const double* G, const double* Hm, const double* lam_old, double* C,
               double* lam_new, int hist_row) {
   if (m > kRRMax) return (int)cudaErrorInvalidValue;
-  size_t sm = (size_t)(4 * kRRMax * kRRMax + 3 * kRRMax) * sizeof(double) + 3 * kRRMax * sizeof(int);
-  cudaFuncSetAttribute(k_rayleigh_ritz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  size_t sm = (size_t)(5 * kRRMax * kRRMax + 3 * kRRMax) * sizeof(double) + 3 * kRRMax * sizeof(int);
+  cudaFuncSetAttribute(k_rayleigh_ritz_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   ProfScope ps(h, BPJD_PROF_RR);
   h.launches += 1;
   double* hr = (hist_row >= 0 && hist_row < h.hist_rows) ? h.hist + (int64_t)hist_row * h.k : nullptr;
-  k_rayleigh_ritz<<<1, 256, sm, h.stream>>>(m, h.k, G, Hm, h.drop_tol, lam_old, C, lam_new, hr, h.stop_rule, h.tol,
-                                            h.dstat);
+  k_rayleigh_ritz_chol<<<1, 256, sm, h.stream>>>(m, h.k, G, Hm, h.drop_tol, lam_old, C, lam_new, hr, h.stop_rule,
+                                                 h.tol, h.dstat);
   return (int)cudaGetLastError();
 }
 
 int launch_band_gather(Handle& h, const int64_t* pos, const double* val, double* out, float* outf) {
   int64_t total = h.sum_nl * h.B;
-  k_band_gather<<<(unsigned)((total + 255) / 256), 256, 0, h.stream>>>(total, pos, val, out, outf);
+  k_band_gather<<<(unsigned)((total + 255) / 256), 256, 0, h.stream>>>(total, pos, val, out);
+  if (outf) {
+    const int W = std::max(h.B, h.Bpad);
+    const int64_t tw = h.sum_nl * W;
+    k_band_pad_f32<<<(unsigned)((tw + 255) / 256), 256, 0, h.stream>>>(h.sum_nl, h.B, W, out, outf);
+  }
   return (int)cudaGetLastError();
 }
 
