@@ -7,7 +7,11 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <string>
+#include <future>
 #include <new>
 #include <vector>
 
@@ -38,6 +42,34 @@ namespace {
 double now_s() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
+
+// BPJD_TRACE=1 in the environment: JSON lines on stderr for setup phases and
+// iterations.
+bool trace_on() {
+  static const bool on = [] {
+    const char* e = std::getenv("BPJD_TRACE");
+    return e && e[0] && e[0] != '0';
+  }();
+  return on;
+}
+
+struct PhaseTimer {
+  double t;
+  std::string buf;
+  PhaseTimer() : t(now_s()) {}
+  void mark(const char* name, cudaStream_t s) {
+    if (!trace_on()) return;
+    cudaStreamSynchronize(s);
+    const double u = now_s();
+    char tmp[96];
+    std::snprintf(tmp, sizeof(tmp), "%s\"%s\": %.3f", buf.empty() ? "" : ", ", name, 1e3 * (u - t));
+    buf += tmp;
+    t = u;
+  }
+  void emit() {
+    if (trace_on()) std::fprintf(stderr, "{\"bpjd_setup_ms\": {%s}}\n", buf.c_str());
+  }
+};
 
 template <typename T>
 cudaError_t dalloc(Handle& h, T** p, size_t count) {
@@ -160,13 +192,14 @@ void transpose_host(const HostCsr& a, HostCsr& t) {
   t.v = t.v_buf.data();
 }
 
-// Coarse pencil of an interpolation P: Galerkin products on the device, then
-// the dense generalised eigensolve on the host.
-int coarse_pencil(Handle& h, const CsrDev& P, const CsrDev& PT, std::vector<double>& lam, std::vector<double>& Phi) {
+// Galerkin products K_H = P^T K P and M_H = P^T M P on the device, copied to
+// the host (symmetrised) for the dense coarse eigensolve.
+int galerkin_host(Handle& h, const CsrDev& P, const CsrDev& PT, std::vector<double>& KH, std::vector<double>& MH) {
   int rc = BPJD_OK;
   const int nH = P.n_cols;
   double *dKH = nullptr, *dMH = nullptr;
-  std::vector<double> KH((size_t)nH * nH), MH((size_t)nH * nH);
+  KH.assign((size_t)nH * nH, 0.0);
+  MH.assign((size_t)nH * nH, 0.0);
   CK(cudaMalloc(&dKH, sizeof(double) * nH * nH));
   CK(cudaMalloc(&dMH, sizeof(double) * nH * nH));
   CKI(launch_galerkin(h.A, h.same_pattern ? CsrDev{h.A.n_rows, h.A.n_cols, h.A.nnz, h.A.row_ptr, h.A.col, h.M.val}
@@ -182,12 +215,16 @@ int coarse_pencil(Handle& h, const CsrDev& P, const CsrDev& PT, std::vector<doub
       double b = 0.5 * (MH[(size_t)i * nH + j] + MH[(size_t)j * nH + i]);
       MH[(size_t)i * nH + j] = MH[(size_t)j * nH + i] = b;
     }
-  rc = gen_eig_host(nH, KH, MH, lam, Phi);
 fail:
   cudaFree(dKH);
   cudaFree(dMH);
   return rc;
 }
+
+struct EigResult {
+  int rc = BPJD_OK;
+  std::vector<double> lam, Phi;
+};
 
 }  // namespace
 
@@ -269,7 +306,7 @@ extern "C" int bpjd_setup(const bpjd_csr* A, const bpjd_csr* M, const bpjd_csr* 
   h->stream = (cudaStream_t)opts->stream;
 
   {
-    HostCsr hA, hM, hP, hP0, hPT, hP0T;
+    HostCsr hP, hP0, hPT, hP0T;
     std::vector<int64_t> sub_ptr_buf;
     std::vector<int32_t> sub_dofs_buf;
     const int64_t* sptr;
@@ -278,20 +315,25 @@ extern "C" int bpjd_setup(const bpjd_csr* A, const bpjd_csr* M, const bpjd_csr* 
     std::vector<double> lamH, Phi, lam0H, Phi0;
     int64_t sum_nl;
     int bw = 0;
-    std::vector<int32_t> loc;
-    std::vector<int64_t> posK, posM;
     int64_t* dposK = nullptr;
     int64_t* dposM = nullptr;
     std::vector<int32_t> rtp, rtpos;
     CsrDev dP0, dP0T;
     double* dPhi0 = nullptr;
+    PhaseTimer pt;
+    Handle tmp0;  // device copies of P0 and its transpose (released at the end of setup)
+    std::future<EigResult> eigP, eigP0;
 
-    if ((rc = host_view(A, on_dev, false, hA)) != BPJD_OK) goto fail;
-    if ((rc = host_view(M, on_dev, false, hM)) != BPJD_OK) goto fail;
+    if (!on_dev) {
+      // host inputs are validated before any device work (device inputs on the device below)
+      HostCsr vA, vM;
+      host_view(A, false, false, vA);
+      host_view(M, false, false, vM);
+      if ((rc = validate_csr(vA)) != BPJD_OK) goto fail;
+      if ((rc = validate_csr(vM)) != BPJD_OK) goto fail;
+    }
     if ((rc = host_view(P, on_dev, true, hP)) != BPJD_OK) goto fail;
     if (P0 && (rc = host_view(P0, on_dev, true, hP0)) != BPJD_OK) goto fail;
-    if ((rc = validate_csr(hA)) != BPJD_OK) goto fail;
-    if ((rc = validate_csr(hM)) != BPJD_OK) goto fail;
     if ((rc = validate_csr(hP)) != BPJD_OK) goto fail;
     if (P0 && (rc = validate_csr(hP0)) != BPJD_OK) goto fail;
     h->nH = P->n_cols;
@@ -333,46 +375,80 @@ extern "C" int bpjd_setup(const bpjd_csr* A, const bpjd_csr* M, const bpjd_csr* 
     }
     sum_nl = sptr[nsub];
     h->sum_nl = sum_nl;
-    h->same_pattern = (hA.nnz == hM.nnz) && std::equal(hA.rp, hA.rp + n + 1, hM.rp) &&
-                      std::equal(hA.ci, hA.ci + hA.nnz, hM.ci);
 
-    // device copies of the matrices and the partition
+    pt.mark("host_views_validate", h->stream);
+    // device copies of the matrices, validated on the device
     CK(upload_csr(*h, A, on_dev, h->A));
-    if (h->same_pattern) {
-      h->M = h->A;
-      h->M.val = nullptr;
-      CK(dalloc(*h, &h->M.val, (size_t)M->nnz));
-      CK(cudaMemcpyAsync(h->M.val, M->val, sizeof(double) * M->nnz,
-                         on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
-    } else {
-      CK(upload_csr(*h, M, on_dev, h->M));
+    CK(upload_csr(*h, M, on_dev, h->M));
+    CK(dalloc(*h, &h->derr, 4));
+    CK(cudaMemsetAsync(h->derr, 0, 4 * sizeof(int32_t), h->stream));
+    CKI(launch_validate_csr(h->A, h->derr, h->stream));
+    CKI(launch_validate_csr(h->M, h->derr, h->stream));
+    if (A->nnz == M->nnz) CKI(launch_same_pattern(h->A, h->M, h->derr, h->stream));
+    {
+      int32_t flags = 0;
+      CK(cudaMemcpyAsync(&flags, h->derr, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+      if (flags & 1) {
+        rc = BPJD_ERR_CSR_INVALID;
+        goto fail;
+      }
+      h->same_pattern = (A->nnz == M->nnz) && !(flags & 2);
+    }
+    if (h->precision == BPJD_MIXED) {
+      CK(dalloc(*h, &h->Asplit, (size_t)A->nnz));
+      CK(dalloc(*h, &h->Msplit, (size_t)M->nnz));
+      CKI(launch_split_values(h->A.val, A->nnz, h->Asplit, h->stream));
+      CKI(launch_split_values(h->M.val, M->nnz, h->Msplit, h->stream));
     }
     CK(upload_host_csr(*h, hP, h->P));
     transpose_host(hP, hPT);
     CK(upload_host_csr(*h, hPT, h->PT));
+    // coarse pencils: Galerkin products on the device now, dense eigensolves on
+    // host threads while the device-side setup below proceeds
+    {
+      std::vector<double> KH, MH;
+      if ((rc = galerkin_host(*h, h->P, h->PT, KH, MH)) != BPJD_OK) goto fail;
+      const int nH = h->nH;
+      eigP = std::async(std::launch::async, [nH, KH = std::move(KH), MH = std::move(MH)]() {
+        EigResult r;
+        r.rc = gen_eig_host(nH, KH, MH, r.lam, r.Phi);
+        return r;
+      });
+      if (P0) {
+        tmp0.stream = h->stream;
+        CK(upload_host_csr(tmp0, hP0, dP0));
+        transpose_host(hP0, hP0T);
+        CK(upload_host_csr(tmp0, hP0T, dP0T));
+        tmp0.A = h->A;
+        tmp0.M = h->M;
+        tmp0.same_pattern = h->same_pattern;
+        std::vector<double> K0, M0;
+        if ((rc = galerkin_host(tmp0, dP0, dP0T, K0, M0)) != BPJD_OK) goto fail;
+        const int nH0 = h->nH0;
+        eigP0 = std::async(std::launch::async, [nH0, K0 = std::move(K0), M0 = std::move(M0)]() {
+          EigResult r;
+          r.rc = gen_eig_host(nH0, K0, M0, r.lam, r.Phi);
+          return r;
+        });
+      }
+    }
     CK(dalloc(*h, &h->sub_ptr, (size_t)nsub + 1));
     CK(dalloc(*h, &h->sub_dofs, (size_t)sum_nl));
     CK(cudaMemcpyAsync(h->sub_ptr, sptr, sizeof(int64_t) * (nsub + 1), cudaMemcpyHostToDevice, h->stream));
     CK(cudaMemcpyAsync(h->sub_dofs, sdofs, sizeof(int32_t) * sum_nl, cudaMemcpyHostToDevice, h->stream));
 
-    // band structure of every local matrix (principal submatrix on the subdomain dofs)
-    loc.assign(n, -1);
-    for (int l = 0; l < nsub; ++l) {
-      const int32_t* d = sdofs + sptr[l];
-      const int nl = (int)(sptr[l + 1] - sptr[l]);
-      for (int p = 0; p < nl; ++p) loc[d[p]] = p;
-      for (int p = 0; p < nl; ++p) {
-        for (int64_t e = hA.rp[d[p]]; e < hA.rp[d[p] + 1]; ++e) {
-          int q = loc[hA.ci[e]];
-          if (q >= 0 && q <= p) bw = std::max(bw, p - q);
-        }
-        if (!h->same_pattern)
-          for (int64_t e = hM.rp[d[p]]; e < hM.rp[d[p] + 1]; ++e) {
-            int q = loc[hM.ci[e]];
-            if (q >= 0 && q <= p) bw = std::max(bw, p - q);
-          }
-      }
-      for (int p = 0; p < nl; ++p) loc[d[p]] = -1;
+    pt.mark("upload", h->stream);
+    // band structure of every local matrix (principal submatrix on the subdomain
+    // dofs), found on the device by binary search of the CSR columns in the
+    // ascending dof lists
+    {
+      int32_t* dbw = h->derr + 1;
+      CK(cudaMemsetAsync(dbw, 0, sizeof(int32_t), h->stream));
+      CKI(launch_band_width(*h, h->A, dbw));
+      if (!h->same_pattern) CKI(launch_band_width(*h, h->M, dbw));
+      CK(cudaMemcpyAsync(&bw, dbw, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+      CK(cudaStreamSynchronize(h->stream));
     }
     h->B = bw + 1;
     if (h->precision == BPJD_MIXED) {
@@ -385,26 +461,6 @@ extern "C" int bpjd_setup(const bpjd_csr* A, const bpjd_csr* M, const bpjd_csr* 
     }
     {
       const int B = h->B;
-      posK.assign((size_t)sum_nl * B, -1);
-      if (!h->same_pattern) posM.assign((size_t)sum_nl * B, -1);
-      for (int l = 0; l < nsub; ++l) {
-        const int64_t off = sptr[l];
-        const int32_t* d = sdofs + off;
-        const int nl = (int)(sptr[l + 1] - off);
-        for (int p = 0; p < nl; ++p) loc[d[p]] = p;
-        for (int p = 0; p < nl; ++p) {
-          for (int64_t e = hA.rp[d[p]]; e < hA.rp[d[p] + 1]; ++e) {
-            int q = loc[hA.ci[e]];
-            if (q >= 0 && q <= p) posK[(size_t)(off + p) * B + (q - p + bw)] = e;
-          }
-          if (!h->same_pattern)
-            for (int64_t e = hM.rp[d[p]]; e < hM.rp[d[p] + 1]; ++e) {
-              int q = loc[hM.ci[e]];
-              if (q >= 0 && q <= p) posM[(size_t)(off + p) * B + (q - p + bw)] = e;
-            }
-        }
-        for (int p = 0; p < nl; ++p) loc[d[p]] = -1;
-      }
       CK(dalloc(*h, &h->bandK, (size_t)sum_nl * B));
       CK(dalloc(*h, &h->bandM, (size_t)sum_nl * B));
       if (h->precision == BPJD_MIXED) {
@@ -413,16 +469,17 @@ extern "C" int bpjd_setup(const bpjd_csr* A, const bpjd_csr* M, const bpjd_csr* 
         CK(dalloc(*h, &h->bandMf, (size_t)sum_nl * W));
       }
       CK(cudaMalloc(&dposK, sizeof(int64_t) * sum_nl * B));
-      CK(cudaMemcpyAsync(dposK, posK.data(), sizeof(int64_t) * sum_nl * B, cudaMemcpyHostToDevice, h->stream));
+      CKI(launch_band_pos(*h, h->A, dposK));
       CKI(launch_band_gather(*h, dposK, h->A.val, h->bandK, h->bandKf));
       if (h->same_pattern) {
         CKI(launch_band_gather(*h, dposK, h->M.val, h->bandM, h->bandMf));
       } else {
         CK(cudaMalloc(&dposM, sizeof(int64_t) * sum_nl * B));
-        CK(cudaMemcpyAsync(dposM, posM.data(), sizeof(int64_t) * sum_nl * B, cudaMemcpyHostToDevice, h->stream));
+        CKI(launch_band_pos(*h, h->M, dposM));
         CKI(launch_band_gather(*h, dposM, h->M.val, h->bandM, h->bandMf));
       }
     }
+    pt.mark("bands", h->stream);
     // inverse map dof -> packed local positions, ascending subdomain order
     rtp.assign((size_t)n + 1, 0);
     for (int64_t e = 0; e < sum_nl; ++e) rtp[sdofs[e] + 1]++;
@@ -437,9 +494,22 @@ extern "C" int bpjd_setup(const bpjd_csr* A, const bpjd_csr* M, const bpjd_csr* 
     CK(cudaMemcpyAsync(h->rt_ptr, rtp.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, h->stream));
     CK(cudaMemcpyAsync(h->rt_pos, rtpos.data(), sizeof(int32_t) * sum_nl, cudaMemcpyHostToDevice, h->stream));
 
-    // coarse pencil and its eigenbasis
-    if ((rc = coarse_pencil(*h, h->P, h->PT, lamH, Phi)) != BPJD_OK) goto fail;
-    if ((lamH[k] - lamH[k - 1]) <= 1e-8 * std::fabs(lamH[k])) {
+    pt.mark("inverse_map", h->stream);
+    // coarse eigenbases (host threads started above)
+    {
+      EigResult r = eigP.get();
+      if ((rc = r.rc) != BPJD_OK) goto fail;
+      lamH = std::move(r.lam);
+      Phi = std::move(r.Phi);
+      if (P0) {
+        EigResult r0 = eigP0.get();
+        if ((rc = r0.rc) != BPJD_OK) goto fail;
+        lam0H = std::move(r0.lam);
+        Phi0 = std::move(r0.Phi);
+      }
+    }
+    if ((lamH[k] - lamH[k - 1]) <= 1e-8 * std::fabs(lamH[k]) ||
+        (P0 && (lam0H[k] - lam0H[k - 1]) <= 1e-8 * std::fabs(lam0H[k]))) {
       rc = BPJD_ERR_GAP;
       goto fail;
     }
@@ -447,35 +517,18 @@ extern "C" int bpjd_setup(const bpjd_csr* A, const bpjd_csr* M, const bpjd_csr* 
     CK(dalloc(*h, &h->lamH, (size_t)h->nH));
     CK(cudaMemcpyAsync(h->Phi, Phi.data(), sizeof(double) * h->nH * h->nH, cudaMemcpyHostToDevice, h->stream));
     CK(cudaMemcpyAsync(h->lamH, lamH.data(), sizeof(double) * h->nH, cudaMemcpyHostToDevice, h->stream));
+    pt.mark("coarse_eig_join", h->stream);
     // initial guess X0 = P0 Phi0[:, :k] (Step 1)
     CK(dalloc(*h, &h->X0, (size_t)n * k));
     CK(dalloc(*h, &h->lam0, (size_t)k));
     if (P0) {
-      Handle tmp;  // allocations of the temporary coarse space are released below
-      tmp.stream = h->stream;
-      CK(upload_host_csr(tmp, hP0, dP0));
-      transpose_host(hP0, hP0T);
-      CK(upload_host_csr(tmp, hP0T, dP0T));
-      tmp.A = h->A;
-      tmp.M = h->M;
-      tmp.same_pattern = h->same_pattern;
-      rc = coarse_pencil(tmp, dP0, dP0T, lam0H, Phi0);
-      if (rc == BPJD_OK && (lam0H[k] - lam0H[k - 1]) <= 1e-8 * std::fabs(lam0H[k])) rc = BPJD_ERR_GAP;
-      if (rc == BPJD_OK && cudaMalloc(&dPhi0, sizeof(double) * h->nH0 * h->nH0) != cudaSuccess) rc = BPJD_ERR_OOM;
-      if (rc == BPJD_OK &&
-          cudaMemcpyAsync(dPhi0, Phi0.data(), sizeof(double) * h->nH0 * h->nH0, cudaMemcpyHostToDevice,
-                          h->stream) != cudaSuccess)
-        rc = BPJD_ERR_CUDA;
-      if (rc == BPJD_OK && launch_csr_times_dense(dP0, dPhi0, h->nH0, k, h->X0, k, h->stream) != 0)
-        rc = BPJD_ERR_CUDA;
-      cudaStreamSynchronize(h->stream);
-      for (void* p : tmp.allocs) cudaFree(p);
-      cudaFree(dPhi0);
-      if (rc != BPJD_OK) goto fail;
+      CK(dalloc(tmp0, &dPhi0, (size_t)h->nH0 * h->nH0));
+      CK(cudaMemcpyAsync(dPhi0, Phi0.data(), sizeof(double) * h->nH0 * h->nH0, cudaMemcpyHostToDevice, h->stream));
+      CKI(launch_csr_times_dense(dP0, dPhi0, h->nH0, k, h->X0, k, h->stream));
     } else {
       CKI(launch_csr_times_dense(h->P, h->Phi, h->nH, k, h->X0, k, h->stream));
     }
-
+    pt.mark("initial_guess", h->stream);
     // scratch and iteration vectors
     {
       const size_t esz = (h->precision == BPJD_MIXED) ? sizeof(float) : sizeof(double);
@@ -505,18 +558,25 @@ extern "C" int bpjd_setup(const bpjd_csr* A, const bpjd_csr* M, const bpjd_csr* 
     h->hist_rows = h->max_iter + 1;
     CK(dalloc(*h, &h->hist, (size_t)h->hist_rows * k));
     CK(dalloc(*h, &h->dstat, 1));
-    CK(dalloc(*h, &h->derr, 4));
     CK(cudaMallocHost(&h->hstat, sizeof(DevStatus)));
     CK(cudaStreamSynchronize(h->stream));
     if (dposK) cudaFree(dposK);
     if (dposM) cudaFree(dposM);
     dposK = dposM = nullptr;
-    (void)t0;
+    for (void* p : tmp0.allocs) cudaFree(p);
+    tmp0.allocs.clear();
+    pt.mark("alloc", h->stream);
+    pt.emit();
+    h->t_setup = now_s() - t0;
     *out = reinterpret_cast<bpjd_handle*>(h);
     return BPJD_OK;
   fail:
     if (dposK) cudaFree(dposK);
     if (dposM) cudaFree(dposM);
+    if (eigP.valid()) eigP.wait();
+    if (eigP0.valid()) eigP0.wait();
+    cudaStreamSynchronize(h->stream);
+    for (void* p : tmp0.allocs) cudaFree(p);
   }
   bpjd_free(reinterpret_cast<bpjd_handle*>(h));
   return rc;
@@ -602,6 +662,9 @@ extern "C" int bpjd_solve(bpjd_handle* hh, double* eigvals, double* eigvecs, int
       rc = BPJD_ERR_BREAKDOWN;
       break;
     }
+    if (trace_on())
+      std::fprintf(stderr, "{\"bpjd_iter\": %d, \"max_rel_resid\": %.6e, \"sum_abs_dlambda\": %.6e, \"kept\": %d}\n", it,
+                   h.hstat->max_res, h.hstat->sum_dl, h.hstat->kept);
     if (h.hstat->converged) {
       converged = true;
       break;
@@ -615,7 +678,10 @@ extern "C" int bpjd_solve(bpjd_handle* hh, double* eigvals, double* eigvecs, int
     {
       const double* U[1] = {MX};
       const double* V[1] = {h.Z};
-      CKI(launch_inner(h, 1, U, 1, V, C1));
+      if (h.precision == BPJD_MIXED)
+        CKI(launch_gram(h, 1, U, 1, 1, V, nullptr, 0, C1, nullptr));
+      else
+        CKI(launch_inner(h, 1, U, 1, V, C1));
       const double* Win[1] = {X};
       CKI(launch_combine_rows(h, 1, Win, C1, k, k, h.Z, h.T, -1.0));
     }
@@ -642,8 +708,12 @@ extern "C" int bpjd_solve(bpjd_handle* hh, double* eigvals, double* eigvecs, int
       nb = 2;
     }
     const int m = nb * k;
-    CKI(launch_inner(h, nb, W, nb, MW, G));
-    CKI(launch_inner(h, nb, W, nb, AW, Hm));
+    if (h.precision == BPJD_MIXED) {
+      CKI(launch_gram(h, nb, W, nb, 2, MW, AW, 1, G, Hm));
+    } else {
+      CKI(launch_inner(h, nb, W, nb, MW, G));
+      CKI(launch_inner(h, nb, W, nb, AW, Hm));
+    }
     CKI(launch_rr(h, m, G, Hm, lam_cur, Crr, lam_nxt, it + 1));
     CKI(launch_combine_rows(h, nb, W, Crr, k, k, nullptr, Xn, 1.0));
     CKI(launch_spmm(h, Xn, AXn, MXn, k));
@@ -679,7 +749,7 @@ extern "C" int bpjd_solve(bpjd_handle* hh, double* eigvals, double* eigvecs, int
     st->converged = converged ? 1 : 0;
     st->max_rel_resid = h.hstat->max_res;
     st->sum_abs_dlambda = h.hstat->sum_dl;
-    st->t_setup_s = 0;
+    st->t_setup_s = h.t_setup;
     st->t_solve_s = now_s() - t0;
     st->status = rc;
   }

@@ -8,11 +8,7 @@
 
 #include "bpjd.h"
 
-#ifdef __CUDACC__
 #include <cuda_runtime.h>
-#else
-typedef struct CUstream_st* cudaStream_t;
-#endif
 
 namespace bpjd {
 
@@ -51,6 +47,8 @@ struct Handle {
   // ---- matrices
   CsrDev A, M;              // M may share A's pattern arrays (same_pattern)
   bool same_pattern = false;
+  float2* Asplit = nullptr;  // (hi, lo) float pairs of K and M values (double-word SpMM)
+  float2* Msplit = nullptr;
   CsrDev P, PT;             // coarse interpolation and its transpose
   double* Phi = nullptr;    // n_H x n_H row-major, M_H-orthonormal eigenvectors
   double* lamH = nullptr;   // n_H ascending
@@ -103,6 +101,7 @@ struct Handle {
   std::vector<void*> allocs;   // every device allocation (freed in bpjd_free)
   int64_t n_partial_blocks = 0;
   int last_iters = 0;
+  double t_setup = 0;          // seconds spent in bpjd_setup
 };
 
 // Records an event pair around a kernel-class launch when profiling is on.
@@ -130,10 +129,20 @@ int launch_residual(Handle& h, const double* AX, const double* MX, const double*
 int launch_rayleigh(Handle& h, const double* X, const double* AX, const double* MX, double* lam);
 int launch_precond(Handle& h, const double* rho, const double* lam, double* Z);
 int launch_inner(Handle& h, int p, const double* const* U, int q, const double* const* V, double* out);
+// double-word block inner products: out1 = U^T V1 (and out2 = U^T V2 when nv = 2);
+// sym = 1 requires U^T V symmetric (mu == mv) and forms the upper tiles only
+int launch_gram(Handle& h, int nu, const double* const* U, int nvb, int nv, const double* const* V1,
+                const double* const* V2, int sym, double* out1, double* out2);
 int launch_combine_rows(Handle& h, int nin, const double* const* Win, const double* C, int ldc,
                         int csub, const double* Zadd, double* out, double alpha);
 int launch_rr(Handle& h, int m, const double* G, const double* Hm, const double* lam_old, double* C,
               double* lam_new, int hist_row);
+int launch_validate_csr(const CsrDev& c, int32_t* flag, cudaStream_t s);
+int launch_same_pattern(const CsrDev& a, const CsrDev& m, int32_t* flag, cudaStream_t s);
+int launch_validate_part(Handle& h, int32_t* flag);
+int launch_band_width(Handle& h, const CsrDev& c, int32_t* bw);
+int launch_band_pos(Handle& h, const CsrDev& c, int64_t* pos);
+int launch_split_values(const double* v, int64_t nnz, float2* out, cudaStream_t s);
 int launch_band_gather(Handle& h, const int64_t* pos, const double* val, double* out, float* outf);
 int launch_galerkin(const CsrDev& A, const CsrDev& Msp, const CsrDev& P, const CsrDev& PT, double* KH,
                     double* MH, cudaStream_t s);

@@ -78,9 +78,10 @@ void householder_tridiag(int n, std::vector<double>& A, std::vector<double>& d, 
   for (int i = 0; i + 1 < n; ++i) e[i] = A[(size_t)(i + 1) * n + i];
 }
 
-// Implicit symmetric tridiagonal QR with Wilkinson shifts.  Z (n x n row-major)
-// accumulates the rotations from the right.  Returns false if it fails to converge.
-bool tridiag_qr(int n, std::vector<double>& d, std::vector<double>& e, std::vector<double>& Z) {
+// Implicit symmetric tridiagonal QR with Wilkinson shifts.  Zc (n x n, stored
+// column-major: column k contiguous) accumulates the rotations from the right.
+// Returns false if it fails to converge.
+bool tridiag_qr(int n, std::vector<double>& d, std::vector<double>& e, std::vector<double>& Zc) {
   const double eps = 2.220446049250313e-16;
   int iter = 0;
   const int max_iter = 60 * std::max(n, 1);
@@ -125,10 +126,12 @@ bool tridiag_qr(int n, std::vector<double>& d, std::vector<double>& e, std::vect
         bulge = -sn * e[k + 1];
         e[k + 1] = cs * e[k + 1];
       }
+      double* zk = &Zc[(size_t)k * n];
+      double* zk1 = &Zc[(size_t)(k + 1) * n];
       for (int i = 0; i < n; ++i) {
-        double zk = Z[(size_t)i * n + k], zk1 = Z[(size_t)i * n + k + 1];
-        Z[(size_t)i * n + k] = cs * zk - sn * zk1;
-        Z[(size_t)i * n + k + 1] = sn * zk + cs * zk1;
+        const double a = zk[i], b = zk1[i];
+        zk[i] = cs * a - sn * b;
+        zk1[i] = sn * a + cs * b;
       }
     }
   }
@@ -140,7 +143,11 @@ bool tridiag_qr(int n, std::vector<double>& d, std::vector<double>& e, std::vect
 int sym_eig_host(int n, std::vector<double> A, std::vector<double>& lam, std::vector<double>& V) {
   std::vector<double> d, e, Q;
   householder_tridiag(n, A, d, e, Q);
-  if (!tridiag_qr(n, d, e, Q)) return BPJD_ERR_BREAKDOWN;
+  // column-major copy of Q for the rotations
+  std::vector<double> Qc((size_t)n * n);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) Qc[(size_t)j * n + i] = Q[(size_t)i * n + j];
+  if (!tridiag_qr(n, d, e, Qc)) return BPJD_ERR_BREAKDOWN;
   std::vector<int> ord(n);
   std::iota(ord.begin(), ord.end(), 0);
   std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return d[a] < d[b]; });
@@ -148,7 +155,7 @@ int sym_eig_host(int n, std::vector<double> A, std::vector<double>& lam, std::ve
   V.assign((size_t)n * n, 0.0);
   for (int j = 0; j < n; ++j) {
     lam[j] = d[ord[j]];
-    for (int i = 0; i < n; ++i) V[(size_t)i * n + j] = Q[(size_t)i * n + ord[j]];
+    for (int i = 0; i < n; ++i) V[(size_t)i * n + j] = Qc[(size_t)ord[j] * n + i];
   }
   return BPJD_OK;
 }
@@ -169,14 +176,18 @@ int gen_eig_host(int n, const std::vector<double>& K, const std::vector<double>&
       L[(size_t)i * n + j] = t / ljj;
     }
   }
-  // Y = L^{-1} K  (forward substitution on every column)
+  // Y = L^{-1} K  (forward substitution, row by row)
   std::vector<double> Y(K);
-  for (int c = 0; c < n; ++c)
-    for (int i = 0; i < n; ++i) {
-      double t = Y[(size_t)i * n + c];
-      for (int p = 0; p < i; ++p) t -= L[(size_t)i * n + p] * Y[(size_t)p * n + c];
-      Y[(size_t)i * n + c] = t / L[(size_t)i * n + i];
+  for (int i = 0; i < n; ++i) {
+    double* yi = &Y[(size_t)i * n];
+    for (int p = 0; p < i; ++p) {
+      const double lip = L[(size_t)i * n + p];
+      const double* yp = &Y[(size_t)p * n];
+      for (int c = 0; c < n; ++c) yi[c] -= lip * yp[c];
     }
+    const double inv = 1.0 / L[(size_t)i * n + i];
+    for (int c = 0; c < n; ++c) yi[c] *= inv;
+  }
   // C = Y L^{-T} = (L^{-1} Y^T)^T
   std::vector<double> C((size_t)n * n);
   for (int r = 0; r < n; ++r)
@@ -193,14 +204,18 @@ int gen_eig_host(int n, const std::vector<double>& K, const std::vector<double>&
   std::vector<double> Qv;
   int rc = sym_eig_host(n, C, lam, Qv);
   if (rc != BPJD_OK) return rc;
-  // Phi = L^{-T} Q  (backward substitution)
-  Phi.assign((size_t)n * n, 0.0);
-  for (int c = 0; c < n; ++c)
-    for (int i = n - 1; i >= 0; --i) {
-      double t = Qv[(size_t)i * n + c];
-      for (int p = i + 1; p < n; ++p) t -= L[(size_t)p * n + i] * Phi[(size_t)p * n + c];
-      Phi[(size_t)i * n + c] = t / L[(size_t)i * n + i];
+  // Phi = L^{-T} Q  (backward substitution, row by row)
+  Phi = Qv;
+  for (int i = n - 1; i >= 0; --i) {
+    double* fi = &Phi[(size_t)i * n];
+    for (int p = i + 1; p < n; ++p) {
+      const double lpi = L[(size_t)p * n + i];
+      const double* fp = &Phi[(size_t)p * n];
+      for (int c = 0; c < n; ++c) fi[c] -= lpi * fp[c];
     }
+    const double inv = 1.0 / L[(size_t)i * n + i];
+    for (int c = 0; c < n; ++c) fi[c] *= inv;
+  }
   return BPJD_OK;
 }
 

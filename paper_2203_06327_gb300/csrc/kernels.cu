@@ -14,6 +14,7 @@
 #include <type_traits>
 
 #include "bpjd_internal.h"
+#include "dword.cuh"
 
 namespace bpjd {
 
@@ -228,6 +229,255 @@ __global__ void __launch_bounds__(256) k_inner(int n, int k, int p, Ptrs6 U, int
     int o = threadIdx.x + oo * blockDim.x;
     if (o < nout) partial[(int64_t)blockIdx.x * nout + o] = acc[oo];
   }
+}
+
+// ---------------------------------------------------------------------------
+// Block inner products in double-word arithmetic (Dot2 on the FP32 pipe):
+// out_v = U^T V_v for v < NV, with U = [U_0 .. U_{nu-1}] (mu = nu k columns)
+// and V_v = [V_v,0 ..] (mv columns), all n x k FP64 row-major blocks.  With
+// sym = 1 only the 4 x 4 output tiles on or above the diagonal are formed
+// (U^T V symmetric).  Rows are staged in shared memory in chunks, split into
+// (hi, lo) float pairs once; each thread owns one output tile and a slice of
+// the chunk rows; slices are combined in FP64 at the end of the block and the
+// per-block partial sums are reduced over blocks in FP64 by k_gram_reduce.
+// ---------------------------------------------------------------------------
+constexpr int kGramRows = 32;
+
+__device__ __forceinline__ void gram_tile_of(int t, int TU, int TV, int sym, int& ta, int& tb) {
+  if (!sym) {
+    ta = t / TV;
+    tb = t % TV;
+    return;
+  }
+  int a = 0;
+  while (t >= TU - a) {
+    t -= TU - a;
+    ++a;
+  }
+  ta = a;
+  tb = a + t;
+}
+
+template <int NV>
+__global__ void __launch_bounds__(256) k_gram_dw(int n, int k, int nu, Ptrs6 U, int nvb, Ptrs6 V1, Ptrs6 V2, int sym,
+                                                 int rows_per_block, double* partial) {
+  extern __shared__ __align__(16) float gsm[];
+  const int mu = nu * k, mv = nvb * k;
+  const int TU = (mu + 3) / 4, TV = (mv + 3) / 4;
+  const int MU4 = 4 * TU, MV4 = 4 * TV;
+  const int ntiles = sym ? TU * (TU + 1) / 2 : TU * TV;
+  const int S = max(1, (int)blockDim.x / ntiles);
+  float* Uh = gsm;
+  float* Ul = Uh + kGramRows * MU4;
+  float* Vh[NV];
+  float* Vl[NV];
+  {
+    float* p = Ul + kGramRows * MU4;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      Vh[v] = p;
+      Vl[v] = p + kGramRows * MV4;
+      p += 2 * kGramRows * MV4;
+    }
+  }
+  const int tid = threadIdx.x;
+  const int tile = tid % ntiles, slice = tid / ntiles;
+  const bool worker = slice < S;
+  int ta = 0, tb = 0;
+  gram_tile_of(tile, TU, TV, sym, ta, tb);
+  dot2 acc[NV][4][4];
+#pragma unroll
+  for (int v = 0; v < NV; ++v)
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) acc[v][x][y].zero();
+  const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
+  const int64_t r1 = min((int64_t)n, r0 + rows_per_block);
+  for (int64_t rb = r0; rb < r1; rb += kGramRows) {
+    const int nr = (int)min((int64_t)kGramRows, r1 - rb);
+    for (int idx = tid; idx < kGramRows * MU4; idx += blockDim.x) {
+      const int r = idx / MU4, col = idx % MU4;
+      double x = 0.0;
+      if (r < nr && col < mu) x = U.p[col / k][(rb + r) * k + (col % k)];
+      const dw s = split_f64(x);
+      Uh[idx] = s.hi;
+      Ul[idx] = s.lo;
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const Ptrs6& VV = (v == 0) ? V1 : V2;
+      for (int idx = tid; idx < kGramRows * MV4; idx += blockDim.x) {
+        const int r = idx / MV4, col = idx % MV4;
+        double x = 0.0;
+        if (r < nr && col < mv) x = VV.p[col / k][(rb + r) * k + (col % k)];
+        const dw s = split_f64(x);
+        Vh[v][idx] = s.hi;
+        Vl[v][idx] = s.lo;
+      }
+    }
+    __syncthreads();
+    if (worker) {
+      for (int r = slice; r < nr; r += S) {
+        const float4 uh = *reinterpret_cast<const float4*>(Uh + r * MU4 + 4 * ta);
+        const float4 ul = *reinterpret_cast<const float4*>(Ul + r * MU4 + 4 * ta);
+        const float a_h[4] = {uh.x, uh.y, uh.z, uh.w};
+        const float a_l[4] = {ul.x, ul.y, ul.z, ul.w};
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          const float4 vh = *reinterpret_cast<const float4*>(Vh[v] + r * MV4 + 4 * tb);
+          const float4 vl = *reinterpret_cast<const float4*>(Vl[v] + r * MV4 + 4 * tb);
+          const float b_h[4] = {vh.x, vh.y, vh.z, vh.w};
+          const float b_l[4] = {vl.x, vl.y, vl.z, vl.w};
+#pragma unroll
+          for (int x = 0; x < 4; ++x)
+#pragma unroll
+            for (int y = 0; y < 4; ++y) acc[v][x][y].mac(a_h[x], a_l[x], b_h[y], b_l[y]);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // combine the slices of every tile in FP64 (shared memory reused)
+  double* red = reinterpret_cast<double*>(gsm);
+  const int per = NV * 16;
+  double mine[NV * 16];
+#pragma unroll
+  for (int v = 0; v < NV; ++v)
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) mine[v * 16 + x * 4 + y] = acc[v][x][y].value();
+  for (int sl = 1; sl < S; ++sl) {
+    if (worker && slice == sl)
+      for (int e = 0; e < per; ++e) red[tile * per + e] = mine[e];
+    __syncthreads();
+    if (worker && slice == 0)
+      for (int e = 0; e < per; ++e) mine[e] += red[tile * per + e];
+    __syncthreads();
+  }
+  if (worker && slice == 0) {
+    double* out = partial + (int64_t)blockIdx.x * ntiles * per;
+    for (int e = 0; e < per; ++e) out[(e / 16) * ntiles * 16 + tile * 16 + (e % 16)] = mine[e];
+  }
+}
+
+__global__ void k_gram_reduce(int nblk, int nv, int mu, int mv, int sym, const double* __restrict__ partial,
+                              double* out1, double* out2) {
+  const int TU = (mu + 3) / 4, TV = (mv + 3) / 4;
+  const int ntiles = sym ? TU * (TU + 1) / 2 : TU * TV;
+  const int total = nv * ntiles * 16;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  double s = 0;
+  for (int b = 0; b < nblk; ++b) s += partial[(int64_t)b * total + t];
+  const int v = t / (ntiles * 16);
+  const int rem = t % (ntiles * 16);
+  const int tile = rem / 16, e = rem % 16;
+  int ta, tb;
+  gram_tile_of(tile, TU, TV, sym, ta, tb);
+  const int a = 4 * ta + e / 4, c = 4 * tb + e % 4;
+  if (a >= mu || c >= mv) return;
+  double* out = (v == 0) ? out1 : out2;
+  out[a * mv + c] = s;
+  if (sym) out[c * mv + a] = s;
+}
+
+// Row-wise block update in double-word arithmetic:
+// out[r, j] = Zadd[r, j] + sign * sum_b sum_a W_b[r, a] C[(b k + a) ldc + j].
+// A block stages kCombRows rows of W split into (hi, lo) floats and the split
+// coefficient matrix; each thread forms outputs with Dot2 and converts once to
+// FP64.
+constexpr int kCombRows = 64;
+__global__ void __launch_bounds__(256) k_combine_dw(int64_t n, int k, int nin, Ptrs6 W, const double* __restrict__ C,
+                                                    int ldc, int csub, const double* __restrict__ Zadd,
+                                                    double* __restrict__ out, double sign) {
+  extern __shared__ __align__(16) float csm[];
+  const int m = nin * k;
+  float* Ch = csm;                       // m x csub
+  float* Cl = Ch + m * csub;
+  float* Wh = Cl + m * csub;             // kCombRows x m
+  float* Wl = Wh + kCombRows * m;
+  for (int t = threadIdx.x; t < m * csub; t += blockDim.x) {
+    const dw s = split_f64(C[(t / csub) * ldc + (t % csub)]);
+    Ch[t] = s.hi;
+    Cl[t] = s.lo;
+  }
+  const int64_t row0 = (int64_t)blockIdx.x * kCombRows;
+  const int nr = (int)min((int64_t)kCombRows, n - row0);
+  for (int t = threadIdx.x; t < nr * m; t += blockDim.x) {
+    const int r = t / m, a = t % m;
+    const dw s = split_f64(W.p[a / k][(row0 + r) * k + (a % k)]);
+    Wh[t] = s.hi;
+    Wl[t] = s.lo;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < nr * csub; t += blockDim.x) {
+    const int r = t / csub, j = t % csub;
+    dot2 acc;
+    acc.zero();
+    const float* wh = Wh + r * m;
+    const float* wl = Wl + r * m;
+    for (int a = 0; a < m; ++a) acc.mac(wh[a], wl[a], Ch[a * csub + j], Cl[a * csub + j]);
+    double v = sign * acc.value();
+    const int64_t o = (row0 + r) * csub + j;
+    if (Zadd) v += Zadd[o];
+    out[o] = v;
+  }
+}
+
+// CSR SpMM in double-word arithmetic with pre-split matrix values (hi/lo
+// float arrays of K and M): YA = K X, YM = M X.  LANES lanes per row as in
+// k_spmm; each lane owns columns j0 and j0 + LANES.
+template <int LANES>
+__global__ void __launch_bounds__(256) k_spmm_dw(int n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                                 const float2* __restrict__ va, const float2* __restrict__ vm,
+                                                 const double* __restrict__ X, double* __restrict__ YA,
+                                                 double* __restrict__ YM, int ncols) {
+  constexpr int RPW = 32 / LANES;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t row = warp * RPW + lane / LANES;
+  const int j0 = lane % LANES;
+  if (row >= n) return;
+  const int j1 = j0 + LANES;
+  const bool has0 = j0 < ncols, has1 = j1 < ncols;
+  dot2 a0, a1, m0, m1;
+  a0.zero();
+  a1.zero();
+  m0.zero();
+  m1.zero();
+  for (int64_t e = rp[row]; e < rp[row + 1]; ++e) {
+    const int64_t c = ci[e];
+    const float2 av = va[e];
+    const float2 mv = vm ? vm[e] : make_float2(0.f, 0.f);
+    const double* xr = X + c * ncols;
+    if (has0) {
+      const dw x = split_f64(xr[j0]);
+      a0.mac(av.x, av.y, x.hi, x.lo);
+      m0.mac(mv.x, mv.y, x.hi, x.lo);
+    }
+    if (has1) {
+      const dw x = split_f64(xr[j1]);
+      a1.mac(av.x, av.y, x.hi, x.lo);
+      m1.mac(mv.x, mv.y, x.hi, x.lo);
+    }
+  }
+  if (has0) {
+    YA[row * ncols + j0] = a0.value();
+    if (YM) YM[row * ncols + j0] = m0.value();
+  }
+  if (has1) {
+    YA[row * ncols + j1] = a1.value();
+    if (YM) YM[row * ncols + j1] = m1.value();
+  }
+}
+
+__global__ void k_split_values(int64_t nnz, const double* __restrict__ v, float2* __restrict__ out) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nnz) return;
+  const dw s = split_f64(v[t]);
+  out[t] = make_float2(s.hi, s.lo);
 }
 
 __global__ void k_sum_partials(int nblk, int len, const double* partial, double* out) {
@@ -1374,6 +1624,116 @@ __global__ void k_rayleigh_ritz_chol(int m, int k, const double* __restrict__ G,
 }
 
 // ---------------------------------------------------------------------------
+// Device-side setup: input validation, band structure of the local matrices.
+// ---------------------------------------------------------------------------
+// flag |= 1 if the CSR is malformed (row pointers not monotone or not spanning
+// [0, nnz], a column out of range, columns not strictly increasing in a row)
+__global__ void k_validate_csr(int n_rows, int n_cols, int64_t nnz, const int64_t* __restrict__ rp,
+                               const int32_t* __restrict__ ci, int32_t* flag) {
+  const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r == 0 && (rp[0] != 0 || rp[n_rows] != nnz)) atomicOr(flag, 1);
+  if (r >= n_rows) return;
+  const int64_t a = rp[r], b = rp[r + 1];
+  if (b < a || a < 0 || b > nnz) {
+    atomicOr(flag, 1);
+    return;
+  }
+  for (int64_t e = a; e < b; ++e) {
+    const int32_t c = ci[e];
+    if (c < 0 || c >= n_cols || (e > a && c <= ci[e - 1])) {
+      atomicOr(flag, 1);
+      return;
+    }
+  }
+}
+
+// flag |= 2 if two CSR patterns differ (same n and nnz assumed)
+__global__ void k_same_pattern(int n, int64_t nnz, const int64_t* __restrict__ rpA, const int32_t* __restrict__ ciA,
+                               const int64_t* __restrict__ rpM, const int32_t* __restrict__ ciM, int32_t* flag) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t <= n && rpA[t] != rpM[t]) atomicOr(flag, 2);
+  if (t < nnz && ciA[t] != ciM[t]) atomicOr(flag, 2);
+}
+
+__device__ __forceinline__ int sub_of(int nsub, const int64_t* __restrict__ sub_ptr, int64_t idx) {
+  int lo = 0, hi = nsub;  // sub_ptr[lo] <= idx < sub_ptr[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (sub_ptr[mid] <= idx)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+// local index of global dof c in the ascending list d[0..nl), -1 if absent
+__device__ __forceinline__ int local_index(const int32_t* __restrict__ d, int nl, int32_t c) {
+  int lo = 0, hi = nl;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (d[mid] < c)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return (lo < nl && d[lo] == c) ? lo : -1;
+}
+
+// flag |= 4 if a subdomain dof list is out of range or not strictly ascending
+__global__ void k_validate_part(int nsub, int n, int64_t total, const int64_t* __restrict__ sub_ptr,
+                                const int32_t* __restrict__ dofs, int32_t* flag) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  const int l = sub_of(nsub, sub_ptr, t);
+  const int32_t g = dofs[t];
+  if (g < 0 || g >= n || (t > sub_ptr[l] && g <= dofs[t - 1])) atomicOr(flag, 4);
+}
+
+// maximum lower bandwidth max(p - q) over the local matrices (q, p local indices
+// of a stored entry (dofs[p], dofs[q]), q <= p)
+__global__ void k_band_width(int nsub, int64_t total, const int64_t* __restrict__ sub_ptr,
+                             const int32_t* __restrict__ dofs, const int64_t* __restrict__ rp,
+                             const int32_t* __restrict__ ci, int32_t* bw) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  const int l = sub_of(nsub, sub_ptr, t);
+  const int64_t off = sub_ptr[l];
+  const int nl = (int)(sub_ptr[l + 1] - off);
+  const int p = (int)(t - off);
+  const int32_t g = dofs[t];
+  int m = 0;
+  for (int64_t e = rp[g]; e < rp[g + 1]; ++e) {
+    const int32_t c = ci[e];
+    if (c > g) break;
+    const int q = local_index(dofs + off, nl, c);
+    if (q >= 0) m = max(m, p - q);
+  }
+  if (m > 0) atomicMax(bw, m);
+}
+
+// band gather positions: pos[(off + p) B + (q - p + B - 1)] = CSR index of (dofs[p], dofs[q])
+__global__ void k_band_pos(int nsub, int64_t total, const int64_t* __restrict__ sub_ptr,
+                           const int32_t* __restrict__ dofs, const int64_t* __restrict__ rp,
+                           const int32_t* __restrict__ ci, int B, int64_t* __restrict__ pos) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  const int l = sub_of(nsub, sub_ptr, t);
+  const int64_t off = sub_ptr[l];
+  const int nl = (int)(sub_ptr[l + 1] - off);
+  const int p = (int)(t - off);
+  const int32_t g = dofs[t];
+  int64_t* out = pos + t * B;
+  for (int e = 0; e < B; ++e) out[e] = -1;
+  for (int64_t e = rp[g]; e < rp[g + 1]; ++e) {
+    const int32_t c = ci[e];
+    if (c > g) break;
+    const int q = local_index(dofs + off, nl, c);
+    if (q >= 0 && p - q < B) out[q - p + B - 1] = e;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Setup kernels
 // ---------------------------------------------------------------------------
 __global__ void k_band_gather(int64_t total, const int64_t* __restrict__ pos, const double* __restrict__ val,
@@ -1527,6 +1887,33 @@ int launch_spmm(Handle& h, const double* X, double* YA, double* YM, int ncols) {
     k_spmm<LANES><<<(unsigned)blocks, 256, 0, h.stream>>>(n, A.row_ptr, A.col, A.val, vm, X, ya, ym, ncols);
     h.launches += 1;
   };
+  if (h.precision == BPJD_MIXED && h.Asplit) {
+    auto god = [&](auto lanes_tag, const CsrDev& A, const float2* va, const float2* vm, double* ya, double* ym) {
+      constexpr int LANES = decltype(lanes_tag)::value;
+      constexpr int RPW = 32 / LANES;
+      int64_t warps = (n + RPW - 1) / RPW;
+      int64_t blocks = (warps * 32 + 255) / 256;
+      k_spmm_dw<LANES><<<(unsigned)blocks, 256, 0, h.stream>>>(n, A.row_ptr, A.col, va, vm, X, ya, ym, ncols);
+      h.launches += 1;
+    };
+    auto dispatch_dw = [&](const CsrDev& A, const float2* va, const float2* vm, double* ya, double* ym) {
+      if (ncols <= 4)
+        god(std::integral_constant<int, 4>(), A, va, vm, ya, ym);
+      else if (ncols <= 8)
+        god(std::integral_constant<int, 8>(), A, va, vm, ya, ym);
+      else if (ncols <= 16)
+        god(std::integral_constant<int, 16>(), A, va, vm, ya, ym);
+      else
+        god(std::integral_constant<int, 32>(), A, va, vm, ya, ym);
+    };
+    if (h.same_pattern) {
+      dispatch_dw(h.A, h.Asplit, h.Msplit, YA, YM);
+    } else {
+      dispatch_dw(h.A, h.Asplit, nullptr, YA, nullptr);
+      dispatch_dw(h.M, h.Msplit, nullptr, YM, nullptr);
+    }
+    return (int)cudaGetLastError();
+  }
   auto dispatch = [&](const CsrDev& A, const double* vm, double* ya, double* ym) {
     if (ncols <= 4)
       go(std::integral_constant<int, 4>(), A, vm, ya, ym);
@@ -1594,12 +1981,53 @@ int launch_inner(Handle& h, int p, const double* const* U, int q, const double* 
   return (int)cudaGetLastError();
 }
 
+int launch_gram(Handle& h, int nu, const double* const* U, int nvb, int nv, const double* const* V1,
+                const double* const* V2, int sym, double* out1, double* out2) {
+  const int k = h.k;
+  const int mu = nu * k, mv = nvb * k;
+  const int TU = (mu + 3) / 4, TV = (mv + 3) / 4;
+  const int ntiles = sym ? TU * (TU + 1) / 2 : TU * TV;
+  if (ntiles > 256 || nv < 1 || nv > 2) return (int)cudaErrorInvalidValue;
+  ProfScope ps(h, BPJD_PROF_INNER);
+  h.launches += 2;
+  Ptrs6 u{}, v1{}, v2{};
+  for (int b = 0; b < nu; ++b) u.p[b] = U[b];
+  for (int b = 0; b < nvb; ++b) {
+    v1.p[b] = V1[b];
+    if (nv > 1) v2.p[b] = V2[b];
+  }
+  const int nblk = (int)std::min<int64_t>(kPartialBlocks, ((int64_t)h.n + kGramRows - 1) / kGramRows);
+  const int rpb = (int)((((int64_t)h.n + nblk - 1) / nblk + kGramRows - 1) / kGramRows * kGramRows);
+  const int nblk2 = (int)(((int64_t)h.n + rpb - 1) / rpb);
+  const size_t chunk = (size_t)kGramRows * (2 * 4 * TU + nv * 2 * 4 * TV) * sizeof(float);
+  const size_t red = (size_t)ntiles * nv * 16 * sizeof(double);
+  const size_t sm = std::max(chunk, red);
+  if (nv == 2) {
+    cudaFuncSetAttribute(k_gram_dw<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_gram_dw<2><<<nblk2, 256, sm, h.stream>>>(h.n, k, nu, u, nvb, v1, v2, sym, rpb, h.partial);
+  } else {
+    cudaFuncSetAttribute(k_gram_dw<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_gram_dw<1><<<nblk2, 256, sm, h.stream>>>(h.n, k, nu, u, nvb, v1, v2, sym, rpb, h.partial);
+  }
+  const int total = nv * ntiles * 16;
+  k_gram_reduce<<<(total + 255) / 256, 256, 0, h.stream>>>(nblk2, nv, mu, mv, sym, h.partial, out1, out2);
+  return (int)cudaGetLastError();
+}
+
 int launch_combine_rows(Handle& h, int nin, const double* const* Win, const double* C, int ldc, int csub,
                         const double* Zadd, double* out, double sign) {
   ProfScope ps(h, BPJD_PROF_COMBINE);
   h.launches += 1;
   Ptrs6 w{};
   for (int b = 0; b < nin; ++b) w.p[b] = Win[b];
+  if (h.precision == BPJD_MIXED) {
+    const int m = nin * h.k;
+    const size_t sm = (size_t)(2 * m * csub + 2 * kCombRows * m) * sizeof(float);
+    if (sm > 48 * 1024) cudaFuncSetAttribute(k_combine_dw, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    const int64_t blocks = ((int64_t)h.n + kCombRows - 1) / kCombRows;
+    k_combine_dw<<<(unsigned)blocks, 256, sm, h.stream>>>(h.n, h.k, nin, w, C, ldc, csub, Zadd, out, sign);
+    return (int)cudaGetLastError();
+  }
   int64_t tot = (int64_t)h.n * csub;
   size_t sm = (size_t)nin * h.k * csub * sizeof(double);
   k_combine_rows<<<(unsigned)((tot + 255) / 256), 256, sm, h.stream>>>(h.n, h.k, nin, w, C, ldc, csub, Zadd, out,
@@ -1694,6 +2122,12 @@ int launch_rr(Handle& h, int m, const double* G, const double* Hm, const double*
   return (int)cudaGetLastError();
 }
 
+int launch_split_values(const double* v, int64_t nnz, float2* out, cudaStream_t s) {
+  if (nnz <= 0) return 0;
+  k_split_values<<<(unsigned)((nnz + 255) / 256), 256, 0, s>>>(nnz, v, out);
+  return (int)cudaGetLastError();
+}
+
 int launch_band_gather(Handle& h, const int64_t* pos, const double* val, double* out, float* outf) {
   int64_t total = h.sum_nl * h.B;
   k_band_gather<<<(unsigned)((total + 255) / 256), 256, 0, h.stream>>>(total, pos, val, out);
@@ -1702,6 +2136,37 @@ int launch_band_gather(Handle& h, const int64_t* pos, const double* val, double*
     const int64_t tw = h.sum_nl * W;
     k_band_pad_f32<<<(unsigned)((tw + 255) / 256), 256, 0, h.stream>>>(h.sum_nl, h.B, W, out, outf);
   }
+  return (int)cudaGetLastError();
+}
+
+int launch_validate_csr(const CsrDev& c, int32_t* flag, cudaStream_t s) {
+  k_validate_csr<<<(c.n_rows + 256) / 256, 256, 0, s>>>(c.n_rows, c.n_cols, c.nnz, c.row_ptr, c.col, flag);
+  return (int)cudaGetLastError();
+}
+
+int launch_same_pattern(const CsrDev& a, const CsrDev& m, int32_t* flag, cudaStream_t s) {
+  const int64_t tot = std::max<int64_t>(a.nnz, (int64_t)a.n_rows + 1);
+  k_same_pattern<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(a.n_rows, a.nnz, a.row_ptr, a.col, m.row_ptr, m.col,
+                                                               flag);
+  return (int)cudaGetLastError();
+}
+
+int launch_validate_part(Handle& h, int32_t* flag) {
+  if (h.sum_nl <= 0) return 0;
+  k_validate_part<<<(unsigned)((h.sum_nl + 255) / 256), 256, 0, h.stream>>>(h.nsub, h.n, h.sum_nl, h.sub_ptr,
+                                                                           h.sub_dofs, flag);
+  return (int)cudaGetLastError();
+}
+
+int launch_band_width(Handle& h, const CsrDev& c, int32_t* bw) {
+  k_band_width<<<(unsigned)((h.sum_nl + 255) / 256), 256, 0, h.stream>>>(h.nsub, h.sum_nl, h.sub_ptr, h.sub_dofs,
+                                                                         c.row_ptr, c.col, bw);
+  return (int)cudaGetLastError();
+}
+
+int launch_band_pos(Handle& h, const CsrDev& c, int64_t* pos) {
+  k_band_pos<<<(unsigned)((h.sum_nl + 127) / 128), 128, 0, h.stream>>>(h.nsub, h.sum_nl, h.sub_ptr, h.sub_dofs,
+                                                                       c.row_ptr, c.col, h.B, pos);
   return (int)cudaGetLastError();
 }
 
