@@ -166,6 +166,17 @@ int bpjd_spmm(bpjd_handle* h, const double* X, double* YA, double* YM, int32_t n
  * handle's precision.  Returns LOCAL_INDEFINITE if a local pivot is <= 0. */
 int bpjd_apply_preconditioner(bpjd_handle* h, const double* rho, const double* lam, double* Z);
 
+/* Block inner products out = U^T V in double-word (FP32-pair, FP64-class)
+ * arithmetic, the product used for the Gram matrices W^T M W, W^T K W of the
+ * Rayleigh-Ritz step (Eq. (3.6)) and the projection coefficients of Eq. (3.5).
+ * U: host array of nu device pointers, each an n x k row-major FP64 block
+ * (k = the handle's k, n = its size); V likewise with nv blocks.  out: device,
+ * (nu k) x (nv k) row-major FP64.  symmetric = 1 asserts U^T V is symmetric
+ * (nu == nv) and forms only the upper half.  (nu k), (nv k) <= 64.  Uses the
+ * handle's scratch; ordered on the handle's stream. */
+int bpjd_block_gram(bpjd_handle* h, int32_t nu, const double* const* U, int32_t nv, const double* const* V,
+                    int32_t symmetric, double* out);
+
 /* Ritz values of every Rayleigh-Ritz step of the last solve (row j = step j,
  * row 0 = initial guess), host array of cap x k doubles; returns rows written. */
 int bpjd_history(const bpjd_handle* h, double* lam_hist, int32_t cap);

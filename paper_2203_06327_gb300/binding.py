@@ -40,7 +40,7 @@ EXPORTED = [
     "bpjd_default_opts", "bpjd_status_string", "bpjd_setup", "bpjd_solve", "bpjd_free", "bpjd_dims",
     "bpjd_spmm", "bpjd_apply_preconditioner", "bpjd_history", "bpjd_device_bytes",
     "bpjd_problem_create", "bpjd_problem_free", "bpjd_profile", "bpjd_profile_read",
-    "bpjd_layout",
+    "bpjd_layout", "bpjd_block_gram",
 ]
 PROF_NAMES = ["local", "coarse", "prolong", "spmm", "inner", "combine", "rr", "resid"]
 
@@ -99,6 +99,7 @@ def _load():
     lib.bpjd_problem_free.argtypes = [C.POINTER(ProblemS)]
     lib.bpjd_problem_free.restype = None
     lib.bpjd_layout.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.bpjd_block_gram.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p]
     lib.bpjd_profile.argtypes = [C.c_void_p, C.c_int32]
     lib.bpjd_profile_read.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
     return lib
@@ -316,6 +317,13 @@ class Solver:
 
     def apply_preconditioner(self, rho, lam, Z):
         _check(lib.bpjd_apply_preconditioner(self._h, _ptr(rho), _ptr(lam), _ptr(Z)), "bpjd_apply_preconditioner")
+
+    def block_gram(self, U, V, out, symmetric: bool = False):
+        """out = [U_0..]^T [V_0..] (double-word arithmetic); U, V lists of n x k CUDA tensors."""
+        pu = (C.c_void_p * len(U))(*[_ptr(u) for u in U])
+        pv = (C.c_void_p * len(V))(*[_ptr(v) for v in V])
+        _check(lib.bpjd_block_gram(self._h, len(U), pu, len(V), pv, 1 if symmetric else 0, _ptr(out)),
+               "bpjd_block_gram")
 
     def history(self) -> np.ndarray:
         buf = np.empty((self.max_iter + 1, self.k), dtype=np.float64)

@@ -553,7 +553,8 @@ extern "C" int bpjd_setup(const bpjd_csr* A, const bpjd_csr* M, const bpjd_csr* 
       for (double** v : vecs) CK(dalloc(*h, v, (size_t)n * k));
     }
     CK(dalloc(*h, &h->lam, (size_t)2 * k));
-    CK(dalloc(*h, &h->partial, (size_t)456 * 96 * 96));
+    h->partial_cap = (size_t)456 * 96 * 96;
+    CK(dalloc(*h, &h->partial, h->partial_cap));
     CK(dalloc(*h, &h->small, (size_t)5 * 96 * 96));
     h->hist_rows = h->max_iter + 1;
     CK(dalloc(*h, &h->hist, (size_t)h->hist_rows * k));
@@ -805,6 +806,19 @@ extern "C" int bpjd_apply_preconditioner(bpjd_handle* hh, const double* rho, con
   return BPJD_OK;
 fail:
   return rc;
+}
+
+extern "C" int bpjd_block_gram(bpjd_handle* hh, int32_t nu, const double* const* U, int32_t nv,
+                               const double* const* V, int32_t symmetric, double* out) {
+  if (!hh || !U || !V || !out || nu < 1 || nv < 1 || nu > 6 || nv > 6) return BPJD_ERR_BAD_ARG;
+  Handle& h = *reinterpret_cast<Handle*>(hh);
+  if (nu * h.k > 64 || nv * h.k > 64 || (symmetric && nu != nv)) return BPJD_ERR_BAD_ARG;
+  for (int b = 0; b < nu; ++b)
+    if (!U[b]) return BPJD_ERR_BAD_ARG;
+  for (int b = 0; b < nv; ++b)
+    if (!V[b]) return BPJD_ERR_BAD_ARG;
+  if (launch_gram(h, nu, U, nv, 1, V, nullptr, symmetric ? 1 : 0, out, nullptr) != 0) return BPJD_ERR_CUDA;
+  return BPJD_OK;
 }
 
 extern "C" int bpjd_history(const bpjd_handle* hh, double* lam_hist, int32_t cap) {

@@ -81,6 +81,7 @@ struct Handle {
   double *rho = nullptr, *Z = nullptr;
   double* lam = nullptr;       // k
   double* partial = nullptr;   // block partial sums
+  size_t partial_cap = 0;      // capacity of partial in doubles
   double* small = nullptr;     // small dense matrices (Gram, C, ...)
   double* hist = nullptr;      // (max_iter + 1) x k Ritz values
   int32_t hist_rows = 0;
@@ -133,6 +134,13 @@ int launch_inner(Handle& h, int p, const double* const* U, int q, const double* 
 // sym = 1 requires U^T V symmetric (mu == mv) and forms the upper tiles only
 int launch_gram(Handle& h, int nu, const double* const* U, int nvb, int nv, const double* const* V1,
                 const double* const* V2, int sym, double* out1, double* out2);
+// doubles of partial sums launch_gram_raw needs (one right-hand block set)
+size_t gram_partial_doubles(int64_t n, int k, int nu, int nvb, int sym);
+// the same with an explicit scratch buffer for the per-block partial sums
+// (capacity in doubles) and stream; no handle needed
+int launch_gram_raw(int64_t n, int k, int nu, const double* const* U, int nvb, int nv, const double* const* V1,
+                    const double* const* V2, int sym, double* out1, double* out2, double* partial,
+                    size_t partial_capacity, cudaStream_t stream);
 int launch_combine_rows(Handle& h, int nin, const double* const* Win, const double* C, int ldc,
                         int csub, const double* Zadd, double* out, double alpha);
 int launch_rr(Handle& h, int m, const double* G, const double* Hm, const double* lam_old, double* C,

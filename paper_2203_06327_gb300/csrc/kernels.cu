@@ -1981,37 +1981,53 @@ int launch_inner(Handle& h, int p, const double* const* U, int q, const double* 
   return (int)cudaGetLastError();
 }
 
-int launch_gram(Handle& h, int nu, const double* const* U, int nvb, int nv, const double* const* V1,
-                const double* const* V2, int sym, double* out1, double* out2) {
-  const int k = h.k;
+size_t gram_partial_doubles(int64_t n, int k, int nu, int nvb, int sym) {
   const int mu = nu * k, mv = nvb * k;
   const int TU = (mu + 3) / 4, TV = (mv + 3) / 4;
   const int ntiles = sym ? TU * (TU + 1) / 2 : TU * TV;
-  if (ntiles > 256 || nv < 1 || nv > 2) return (int)cudaErrorInvalidValue;
-  ProfScope ps(h, BPJD_PROF_INNER);
-  h.launches += 2;
+  const int nblk = (int)std::min<int64_t>(kPartialBlocks, (n + kGramRows - 1) / kGramRows);
+  const int rpb = (int)(((n + nblk - 1) / nblk + kGramRows - 1) / kGramRows * kGramRows);
+  const int nblk2 = (int)((n + rpb - 1) / rpb);
+  return (size_t)nblk2 * ntiles * 16;
+}
+
+int launch_gram_raw(int64_t n, int k, int nu, const double* const* U, int nvb, int nv, const double* const* V1,
+                    const double* const* V2, int sym, double* out1, double* out2, double* partial,
+                    size_t partial_capacity, cudaStream_t stream) {
+  const int mu = nu * k, mv = nvb * k;
+  const int TU = (mu + 3) / 4, TV = (mv + 3) / 4;
+  const int ntiles = sym ? TU * (TU + 1) / 2 : TU * TV;
+  if (ntiles > 256 || nv < 1 || nv > 2 || nu > 6 || nvb > 6 || n < 1) return (int)cudaErrorInvalidValue;
   Ptrs6 u{}, v1{}, v2{};
   for (int b = 0; b < nu; ++b) u.p[b] = U[b];
   for (int b = 0; b < nvb; ++b) {
     v1.p[b] = V1[b];
     if (nv > 1) v2.p[b] = V2[b];
   }
-  const int nblk = (int)std::min<int64_t>(kPartialBlocks, ((int64_t)h.n + kGramRows - 1) / kGramRows);
-  const int rpb = (int)((((int64_t)h.n + nblk - 1) / nblk + kGramRows - 1) / kGramRows * kGramRows);
-  const int nblk2 = (int)(((int64_t)h.n + rpb - 1) / rpb);
+  const int nblk = (int)std::min<int64_t>(kPartialBlocks, (n + kGramRows - 1) / kGramRows);
+  const int rpb = (int)(((n + nblk - 1) / nblk + kGramRows - 1) / kGramRows * kGramRows);
+  const int nblk2 = (int)((n + rpb - 1) / rpb);
+  const int total = nv * ntiles * 16;
+  if ((size_t)nblk2 * total > partial_capacity) return (int)cudaErrorInvalidValue;
   const size_t chunk = (size_t)kGramRows * (2 * 4 * TU + nv * 2 * 4 * TV) * sizeof(float);
   const size_t red = (size_t)ntiles * nv * 16 * sizeof(double);
   const size_t sm = std::max(chunk, red);
   if (nv == 2) {
     cudaFuncSetAttribute(k_gram_dw<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_gram_dw<2><<<nblk2, 256, sm, h.stream>>>(h.n, k, nu, u, nvb, v1, v2, sym, rpb, h.partial);
+    k_gram_dw<2><<<nblk2, 256, sm, stream>>>((int)n, k, nu, u, nvb, v1, v2, sym, rpb, partial);
   } else {
     cudaFuncSetAttribute(k_gram_dw<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_gram_dw<1><<<nblk2, 256, sm, h.stream>>>(h.n, k, nu, u, nvb, v1, v2, sym, rpb, h.partial);
+    k_gram_dw<1><<<nblk2, 256, sm, stream>>>((int)n, k, nu, u, nvb, v1, v2, sym, rpb, partial);
   }
-  const int total = nv * ntiles * 16;
-  k_gram_reduce<<<(total + 255) / 256, 256, 0, h.stream>>>(nblk2, nv, mu, mv, sym, h.partial, out1, out2);
+  k_gram_reduce<<<(total + 255) / 256, 256, 0, stream>>>(nblk2, nv, mu, mv, sym, partial, out1, out2);
   return (int)cudaGetLastError();
+}
+
+int launch_gram(Handle& h, int nu, const double* const* U, int nvb, int nv, const double* const* V1,
+                const double* const* V2, int sym, double* out1, double* out2) {
+  ProfScope ps(h, BPJD_PROF_INNER);
+  h.launches += 2;
+  return launch_gram_raw(h.n, h.k, nu, U, nvb, nv, V1, V2, sym, out1, out2, h.partial, h.partial_cap, h.stream);
 }
 
 int launch_combine_rows(Handle& h, int nin, const double* const* Win, const double* C, int ldc, int csub,

@@ -161,3 +161,24 @@ def test_paper_stop_rule():
     assert st["converged"] == 1 and st["sum_abs_dlambda"] < 1e-10
     assert st["iters"] == ref.iterations
     np.testing.assert_allclose(lam, ref.lam, rtol=1e-10)
+
+
+def test_block_gram_matches_oracle_products():
+    """bpjd_block_gram (double-word Dot2 products) against FP64 NumPy products."""
+    spec = config_small_2d()
+    pb, sv = _solver(spec, precision=B.MIXED)
+    rng = np.random.default_rng(11)
+    k = spec.k
+    blocks = [rng.standard_normal((sv.n, k)) * 10.0 ** rng.integers(-3, 3) for _ in range(3)]
+    U = [torch.tensor(b, device=DEV) for b in blocks]
+    out = torch.empty((3 * k, 3 * k), dtype=torch.float64, device=DEV)
+    sv.block_gram(U, U, out, symmetric=True)
+    Wn = np.hstack(blocks)
+    ref = Wn.T @ Wn
+    scale = np.abs(Wn).T @ np.abs(Wn)
+    assert np.all(np.abs(out.cpu().numpy() - ref) <= 1e-14 * scale)
+    out2 = torch.empty((k, 2 * k), dtype=torch.float64, device=DEV)
+    sv.block_gram(U[:1], U[1:], out2, symmetric=False)
+    ref2 = blocks[0].T @ np.hstack(blocks[1:])
+    scale2 = np.abs(blocks[0]).T @ np.abs(np.hstack(blocks[1:]))
+    assert np.all(np.abs(out2.cpu().numpy() - ref2) <= 1e-14 * scale2)
