@@ -46,6 +46,7 @@ extern "C" {
 #define BPJD_ERR_OOM              -9  /* device allocation failed */
 #define BPJD_ERR_CUDA            -10  /* a CUDA runtime call failed */
 #define BPJD_ERR_UNSUPPORTED     -11  /* option outside what this build implements */
+#define BPJD_ERR_TOO_LARGE       -12  /* request exceeds a fixed capacity (allocation-free entry point) */
 
 /* ---- option values ----------------------------------------------------- */
 #define BPJD_FP64        0  /* every step in FP64 */
@@ -176,6 +177,37 @@ int bpjd_apply_preconditioner(bpjd_handle* h, const double* rho, const double* l
  * handle's scratch; ordered on the handle's stream. */
 int bpjd_block_gram(bpjd_handle* h, int32_t nu, const double* const* U, int32_t nv, const double* const* V,
                     int32_t symmetric, double* out);
+
+/*
+ * bpjd_block_gram_noalloc -- bpjd_block_gram without a handle and without any
+ * device allocation.  (The paper has no counterpart: this is an interface for
+ * callers, not a step of the method.)
+ *
+ * For callers that cannot call cudaMalloc: e.g. a host application that owns all
+ * device memory through its own pool or pre-reserved arena and hands libraries
+ * only the buffers they operate on, or a latency-critical loop that must not
+ * pay the implicit device synchronisation of an allocation.  The caller passes
+ * the inputs and the output; the per-block partial sums live in a file-scope
+ * static device array of 8 MiB (2^20 doubles), reserved on every GPU that
+ * loads the library until the process exits.  The partial sums need
+ * 16 * ntiles * min(456, ceil(n / 32)) doubles, ntiles being the number of
+ * 4 x 4 output tiles formed (upper ones only when symmetric).
+ *
+ * n, k  : rows and columns of every block; U: host array of nu device
+ *         pointers (n x k row-major FP64 each), V likewise with nv; out: device
+ *         (nu k) x (nv k) row-major FP64; stream: cudaStream_t or NULL.
+ * symmetric, size limits and arithmetic as for bpjd_block_gram.
+ * Errors: BAD_ARG; TOO_LARGE if the partial sums of this (n, k, nu, nv) do not
+ * fit the static array; CUDA.
+ * The first call on a device looks up the device address of the static array
+ * (cudaGetSymbolAddress, with that device current); make that first call before
+ * any stream capture.  All calls share the one array: calls that overlap on
+ * the GPU (other streams, other host threads) race and give wrong results, so
+ * order them.  The array keeps the last call's contents; nothing in it has to
+ * start at zero, because every partial sum a call reads it has written first.
+ */
+int bpjd_block_gram_noalloc(int64_t n, int32_t k, int32_t nu, const double* const* U, int32_t nv,
+                            const double* const* V, int32_t symmetric, double* out, void* stream);
 
 /* Ritz values of every Rayleigh-Ritz step of the last solve (row j = step j,
  * row 0 = initial guess), host array of cap x k doubles; returns rows written. */

@@ -31,6 +31,7 @@ ERR_NOCONV = -8
 ERR_OOM = -9
 ERR_CUDA = -10
 ERR_UNSUPPORTED = -11
+ERR_TOO_LARGE = -12
 
 FP64, MIXED = 0, 1
 W_2K, W_3K = 0, 1
@@ -40,7 +41,7 @@ EXPORTED = [
     "bpjd_default_opts", "bpjd_status_string", "bpjd_setup", "bpjd_solve", "bpjd_free", "bpjd_dims",
     "bpjd_spmm", "bpjd_apply_preconditioner", "bpjd_history", "bpjd_device_bytes",
     "bpjd_problem_create", "bpjd_problem_free", "bpjd_profile", "bpjd_profile_read",
-    "bpjd_layout", "bpjd_block_gram",
+    "bpjd_layout", "bpjd_block_gram", "bpjd_block_gram_noalloc",
 ]
 PROF_NAMES = ["local", "coarse", "prolong", "spmm", "inner", "combine", "rr", "resid"]
 

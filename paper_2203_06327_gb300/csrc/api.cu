@@ -256,6 +256,7 @@ extern "C" const char* bpjd_status_string(int c) {
     case BPJD_ERR_OOM: return "device out of memory";
     case BPJD_ERR_CUDA: return "CUDA error";
     case BPJD_ERR_UNSUPPORTED: return "unsupported option";
+    case BPJD_ERR_TOO_LARGE: return "request exceeds the fixed scratch capacity of the allocation-free entry point";
     default: return "unknown status";
   }
 }
