@@ -21,6 +21,8 @@ struct DevStatus {
   int32_t err_local;    // a local pivot was <= 0
   int32_t err_breakdown;// Rayleigh-Ritz kept fewer than k directions
   int32_t kept;         // directions kept by the last Rayleigh-Ritz step
+  int32_t sweeps;       // Jacobi sweeps of the last Rayleigh-Ritz step
+  long long rr_cycles[8];  // SM cycles spent in the phases of the last Rayleigh-Ritz step
   double res[64];       // per-column relative residuals
 };
 

@@ -13,12 +13,14 @@
 // about u^2 * sum |a_i b_i| (plus the conditioning term of Dot2), i.e. the
 // accuracy of an FP64 evaluation.
 //
-// FP64 <-> double-word conversions use integer operations only (no FP64
-// pipe): split_f64 truncates the significand to 24 bits for hi and converts
-// the remaining 29 bits for lo; dw_to_f64 rebuilds both floats as doubles from
-// their bit fields and adds them with one FP64 addition.  Inputs with
-// |x| < 2^-74 lose their lo part (relative error then 2^-23); inputs beyond
-// the float range fall back to a native conversion.
+// FP64 <-> double-word conversions use integer operations only (no FP64 or
+// conversion pipe): split_f64 truncates the significand to 24 bits for hi and
+// builds lo from the remaining 29 bits; dw_to_f64 rebuilds both floats as
+// doubles from their bit fields and adds them with one FP64 addition.  (Native
+// float<->double conversions execute on the FP64 pipe of this GPU, which is
+// why none is used.)  Inputs with |x| < 2^-74 lose their lo part (relative
+// error then 2^-23); |x| < 2^-126 becomes a signed zero and |x| >= 2^128 a
+// signed infinity.
 #ifndef BPJD_DWORD_CUH_
 #define BPJD_DWORD_CUH_
 
@@ -51,24 +53,31 @@ __device__ __forceinline__ dw split_f64(double x) {
   const unsigned int sign = (unsigned int)(b >> 63) << 31;
   const int e = (int)((b >> 52) & 0x7ff);
   dw r;
-  if (e < 897) {  // |x| < 2^-126 (including zero): below the normal float range
-    r.hi = 0.f;
+  if (e < 897) {  // |x| < 2^-126 (including zero): flushed to a signed zero
+    r.hi = __uint_as_float(sign);
     r.lo = 0.f;
-    if (e > 0) r.hi = (float)x;
     return r;
   }
-  if (e > 1150) {  // beyond the float range
-    r.hi = (float)x;
+  if (e > 1150) {  // beyond the float range: signed infinity
+    r.hi = __uint_as_float(sign | 0x7f800000u);
     r.lo = 0.f;
     return r;
   }
   const unsigned long long mant = b & 0xfffffffffffffULL;
   r.hi = __uint_as_float(sign | ((unsigned int)(e - 896) << 23) | (unsigned int)(mant >> 29));
+  // lo = rem * 2^(e - 1075), rem < 2^29, built from its bit pattern (normalised
+  // by a leading-zero count, significand truncated to 24 bits): no conversion
+  // instruction, which would run on the FP64 pipe
   const unsigned int rem = (unsigned int)(mant & 0x1fffffffULL);
-  // lo = rem * 2^(e - 1075)
-  float lo = __uint2float_rn(rem);
-  const int se = e - 948;  // biased float exponent of 2^(e - 1075)
-  lo = (se >= 1) ? lo * __uint_as_float((unsigned int)se << 23) : 0.f;
+  float lo = 0.f;
+  if (rem) {
+    const int lz = __clz(rem);
+    const int fe = (31 - lz) + e - 948;  // biased float exponent of lo
+    if (fe >= 1) {
+      const unsigned int m23 = (unsigned int)((((unsigned long long)rem) << (lz + 1)) >> 9) & 0x7fffffu;
+      lo = __uint_as_float(((unsigned int)fe << 23) | m23);
+    }
+  }
   r.lo = sign ? -lo : lo;
   return r;
 }
@@ -76,10 +85,11 @@ __device__ __forceinline__ dw split_f64(double x) {
 __device__ __forceinline__ double f32_to_f64_bits(float f) {
   const unsigned int u = __float_as_uint(f);
   const unsigned int e = (u >> 23) & 0xff;
-  if (e == 0 || e == 0xff) return (double)f;  // zero, subnormal, inf/nan: native path
   const unsigned long long s = (unsigned long long)(u >> 31) << 63;
-  const unsigned long long ex = (unsigned long long)(e + 896) << 52;
   const unsigned long long m = (unsigned long long)(u & 0x7fffff) << 29;
+  unsigned long long ex = (unsigned long long)(e + 896) << 52;
+  if (e == 0) return __longlong_as_double((long long)s);  // zero and subnormals: signed zero
+  if (e == 0xff) ex = 0x7ffULL << 52;                       // inf / nan
   return __longlong_as_double((long long)(s | ex | m));
 }
 

@@ -241,7 +241,8 @@ __global__ void __launch_bounds__(256) k_inner(int n, int k, int p, Ptrs6 U, int
 // the chunk rows; slices are combined in FP64 at the end of the block and the
 // per-block partial sums are reduced over blocks in FP64 by k_gram_reduce.
 // ---------------------------------------------------------------------------
-constexpr int kGramRows = 32;
+constexpr int kGramRows = 64;
+constexpr int kGramBlocks = 304;  // two resident blocks on each of the 152 SMs: one wave
 
 __device__ __forceinline__ void gram_tile_of(int t, int TU, int TV, int sym, int& ta, int& tb) {
   if (!sym) {
@@ -259,7 +260,7 @@ __device__ __forceinline__ void gram_tile_of(int t, int TU, int TV, int sym, int
 }
 
 template <int NV>
-__global__ void __launch_bounds__(256) k_gram_dw(int n, int k, int nu, Ptrs6 U, int nvb, Ptrs6 V1, Ptrs6 V2, int sym,
+__global__ void __launch_bounds__(256, 2) k_gram_dw(int n, int k, int nu, Ptrs6 U, int nvb, Ptrs6 V1, Ptrs6 V2, int sym,
                                                  int rows_per_block, double* partial) {
   extern __shared__ __align__(16) float gsm[];
   const int mu = nu * k, mv = nvb * k;
@@ -1404,8 +1405,8 @@ __device__ void rayleigh_ritz_eig(int m, int k, const double* __restrict__ G, co
 // entry, lower triangle mirrored) into a second buffer, and V' = V J.
 // A, A2, V, V2 have leading dimension kRRMax; returns (via the buffers that end
 // up holding the result) pointers in *Aout / *Vout.
-__device__ void jacobi_eig_sym(double* A, double* A2, double* V, double* V2, int m, double** Aout, double** Vout,
-                               double* fr, double* gr, int* partner) {
+__device__ int jacobi_eig_sym(double* A, double* A2, double* V, double* V2, int m, double** Aout, double** Vout,
+                              double* fr, double* gr, int* partner) {
   const int mp = m + (m & 1);
   const int ld = kRRMax;
   const int tid = threadIdx.x;
@@ -1428,7 +1429,8 @@ __device__ void jacobi_eig_sym(double* A, double* A2, double* V, double* V2, int
         ++t;
       }
   }
-  for (int sweep = 0; sweep < 60; ++sweep) {
+  int sweep = 0;
+  for (; sweep < 60; ++sweep) {
     if (tid == 0) done = 1;
     __syncthreads();
     for (int round = 0; round < mp - 1; ++round) {
@@ -1444,7 +1446,7 @@ __device__ void jacobi_eig_sym(double* A, double* A2, double* V, double* V2, int
         const int p = min(e0, e1), q = max(e0, e1);
         const double apq = A[p * ld + q], app = A[p * ld + p], aqq = A[q * ld + q];
         double c = 1.0, s = 0.0;
-        if (fabs(apq) > 1e-300 && fabs(apq) > 1e-17 * sqrt(fabs(app * aqq))) {
+        if (fabs(apq) > 1e-300 && fabs(apq) > 1e-15 * sqrt(fabs(app * aqq))) {
           const double tau = (aqq - app) / (2.0 * apq);
           const double tt = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
           c = 1.0 / sqrt(1.0 + tt * tt);
@@ -1485,6 +1487,148 @@ __device__ void jacobi_eig_sym(double* A, double* A2, double* V, double* V2, int
   }
   *Aout = A;
   *Vout = V;
+  return sweep + 1;
+}
+
+// Parallel cyclic Jacobi in double-word arithmetic (planes *h, *l of hi/lo
+// floats, leading dimension kRRMax).  The rotation angle of a pair is chosen
+// in FP32 (t = tan of the angle); c = 1 / sqrt(1 + t^2) and s = t c are then
+// formed in double-word precision (one Newton step on the FP32 estimate), so
+// every rotation is orthogonal to double-word accuracy and only its
+// annihilation of a_pq is approximate (relative 2^-24), which the next sweep
+// removes.  The two-sided update of a round is formed element-wise from the
+// old matrix (Dot2 accumulations) into the second buffer.  Returns sweeps.
+__device__ __forceinline__ dw dw_renorm(float s, float c) {
+  dw r;
+  fast_two_sum(s, c, r.hi, r.lo);
+  return r;
+}
+__device__ __forceinline__ dw dw_lin2(dw f1, float x1h, float x1l, dw f2, float x2h, float x2l) {
+  dot2 a;
+  a.zero();
+  a.mac(f1.hi, f1.lo, x1h, x1l);
+  a.mac(f2.hi, f2.lo, x2h, x2l);
+  return dw_renorm(a.s, a.c);
+}
+
+__device__ int jacobi_eig_dw(float* Ah, float* Al, float* A2h, float* A2l, float* Vh, float* Vl, float* V2h,
+                             float* V2l, int m, float** Aoh, float** Aol, float** Voh, float** Vol, dw* fr, dw* gr,
+                             int* partner) {
+  const int mp = m + (m & 1);
+  const int ld = kRRMax;
+  const int tid = threadIdx.x;
+  __shared__ int done;
+  __shared__ unsigned char tri_r[kRRMax * (kRRMax + 1) / 2], tri_c[kRRMax * (kRRMax + 1) / 2];
+  for (int t = tid; t < mp * ld; t += blockDim.x) {
+    const int r = t / ld, c = t % ld;
+    Vh[t] = (r == c) ? 1.f : 0.f;
+    Vl[t] = 0.f;
+    if ((r >= m || c >= m) && c < mp) {
+      Ah[t] = 0.f;
+      Al[t] = 0.f;
+    }
+  }
+  if (tid == 0) {
+    int t = 0;
+    for (int r = 0; r < mp; ++r)
+      for (int c = 0; c <= r; ++c) {
+        tri_r[t] = (unsigned char)r;
+        tri_c[t] = (unsigned char)c;
+        ++t;
+      }
+  }
+  __syncthreads();
+  const int half = mp / 2;
+  int sweep = 0;
+  for (; sweep < 60; ++sweep) {
+    if (tid == 0) done = 1;
+    __syncthreads();
+    for (int round = 0; round < mp - 1; ++round) {
+      if (tid < half) {
+        int e0 = 0, e1;
+        auto ring = [&](int pos) { return ((pos + round) % (mp - 1)) + 1; };
+        if (tid == 0) {
+          e1 = ring(0);
+        } else {
+          e0 = ring(tid);
+          e1 = ring(mp - 1 - tid);
+        }
+        const int p = min(e0, e1), q = max(e0, e1);
+        const float apq = Ah[p * ld + q] + Al[p * ld + q];
+        const float app = Ah[p * ld + p], aqq = Ah[q * ld + q];
+        dw c = {1.f, 0.f}, s = {0.f, 0.f};
+        if (fabsf(apq) > 1e-37f && fabsf(apq) > 1e-15f * sqrtf(fabsf(app * aqq))) {
+          const float tau = (aqq - app) / (2.f * apq);
+          const float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+          // u = 1 + t^2 exactly in double-word
+          float ph, pe, uh, ue;
+          two_prod(t, t, ph, pe);
+          two_sum(1.f, ph, uh, ue);
+          dw u = dw_renorm(uh, __fadd_rn(ue, pe));
+          // c = u^{-1/2}: c0 = rsqrt(u.hi), r = 1 - u c0^2 (double-word), c = c0 + c0 r / 2
+          const float c0 = rsqrtf(u.hi);
+          float q1, q1e;
+          two_prod(c0, c0, q1, q1e);  // c0^2 = q1 + q1e exactly
+          dot2 acc;
+          acc.zero();
+          acc.add(1.f, 0.f);
+          acc.mac(-u.hi, -u.lo, q1, q1e);
+          const float r = acc.s + acc.c;
+          c = dw_renorm(c0, 0.5f * c0 * r);
+          // s = t c
+          float sh, se;
+          two_prod(t, c.hi, sh, se);
+          s = dw_renorm(sh, __fmaf_rn(t, c.lo, se));
+          done = 0;
+        }
+        fr[p] = c;
+        gr[p] = dw{-s.hi, -s.lo};
+        partner[p] = q;
+        fr[q] = c;
+        gr[q] = s;
+        partner[q] = p;
+      }
+      __syncthreads();
+      for (int t = tid; t < mp * (mp + 1) / 2; t += blockDim.x) {
+        const int r = tri_r[t], c = tri_c[t];
+        const int rb = partner[r], cb = partner[c];
+        const dw i1 = dw_lin2(fr[c], Ah[r * ld + c], Al[r * ld + c], gr[c], Ah[r * ld + cb], Al[r * ld + cb]);
+        const dw i2 = dw_lin2(fr[c], Ah[rb * ld + c], Al[rb * ld + c], gr[c], Ah[rb * ld + cb], Al[rb * ld + cb]);
+        const dw v = dw_lin2(fr[r], i1.hi, i1.lo, gr[r], i2.hi, i2.lo);
+        A2h[r * ld + c] = v.hi;
+        A2l[r * ld + c] = v.lo;
+        A2h[c * ld + r] = v.hi;
+        A2l[c * ld + r] = v.lo;
+      }
+      for (int t = tid; t < mp * mp; t += blockDim.x) {
+        const int x = t / mp, r = t % mp;
+        const int rb = partner[r];
+        const dw v = dw_lin2(fr[r], Vh[x * ld + r], Vl[x * ld + r], gr[r], Vh[x * ld + rb], Vl[x * ld + rb]);
+        V2h[x * ld + r] = v.hi;
+        V2l[x * ld + r] = v.lo;
+      }
+      __syncthreads();
+      float* t0 = Ah;
+      Ah = A2h;
+      A2h = t0;
+      t0 = Al;
+      Al = A2l;
+      A2l = t0;
+      t0 = Vh;
+      Vh = V2h;
+      V2h = t0;
+      t0 = Vl;
+      Vl = V2l;
+      V2l = t0;
+    }
+    if (done) break;
+    __syncthreads();
+  }
+  *Aoh = Ah;
+  *Aol = Al;
+  *Voh = Vh;
+  *Vol = Vl;
+  return sweep + 1;
 }
 
 // Rayleigh-Ritz (Eq. (3.6)) with a Cholesky orthonormalisation of the scaled
@@ -1496,7 +1640,8 @@ __device__ void jacobi_eig_sym(double* A, double* A2, double* V, double* V2, int
 // eigen-based path with dropping runs.
 __global__ void k_rayleigh_ritz_chol(int m, int k, const double* __restrict__ G, const double* __restrict__ H,
                                      double drop_tol, const double* __restrict__ lam_old, double* C,
-                                     double* lam_new, double* hist_row, int stop_rule, double tol, DevStatus* st) {
+                                     double* lam_new, double* hist_row, int stop_rule, double tol, DevStatus* st,
+                                     int dword) {
   extern __shared__ double rr[];
   const int ld = kRRMax;
   const int LL = ld * ld;
@@ -1513,6 +1658,8 @@ __global__ void k_rayleigh_ritz_chol(int m, int k, const double* __restrict__ G,
   __shared__ int ok;
   __shared__ double crit_lhs, crit_rhs;
   const int tid = threadIdx.x;
+  long long tcl[8];
+  tcl[0] = clock64();
   for (int j = tid; j < m; j += blockDim.x) {
     const double g = G[j * m + j];
     sc[j] = (j < k) ? 1.0 : (g > 0 ? 1.0 / sqrt(g) : 0.0);
@@ -1531,6 +1678,7 @@ __global__ void k_rayleigh_ritz_chol(int m, int k, const double* __restrict__ G,
     for (int j = 0; j < m; ++j) tr += B0[j * ld + j];
     crit_rhs = drop_tol * tr;
   }
+  tcl[1] = clock64();
   // right-looking Cholesky in place (lower triangle)
   for (int j = 0; j < m; ++j) {
     if (tid == 0) {
@@ -1549,19 +1697,34 @@ __global__ void k_rayleigh_ritz_chol(int m, int k, const double* __restrict__ G,
     }
     __syncthreads();
   }
-  // B2 = L^{-1} (column c by forward substitution, one thread per column)
-  for (int c = tid; c < m; c += blockDim.x) {
+  tcl[2] = clock64();
+  // B2 = L^{-1}: row i of L^{-1} from rows < i, all columns of a row in parallel;
+  // the dot products run as double-word Dot2 sums (FP64 dependency chains are
+  // long-latency on this GPU)
+  {
+    double* dinv = B3;  // reciprocal diagonal of L
+    for (int i = tid; i < m; i += blockDim.x) dinv[i] = 1.0 / B0[i * ld + i];
+    __syncthreads();
     for (int i = 0; i < m; ++i) {
-      if (i < c) {
-        B2[i * ld + c] = 0.0;
-        continue;
+      for (int c = tid; c < m; c += blockDim.x) {
+        double v = 0.0;
+        if (c == i) {
+          v = dinv[i];
+        } else if (c < i) {
+          dot2 acc;
+          acc.zero();
+          for (int t = c; t < i; ++t) {
+            const dw l = split_f64(B0[i * ld + t]);
+            const dw x = split_f64(B2[t * ld + c]);
+            acc.mac(l.hi, l.lo, x.hi, x.lo);
+          }
+          v = -acc.value() * dinv[i];
+        }
+        B2[i * ld + c] = v;
       }
-      double s = (i == c) ? 1.0 : 0.0;
-      for (int t = c; t < i; ++t) s -= B0[i * ld + t] * B2[t * ld + c];
-      B2[i * ld + c] = s / B0[i * ld + i];
+      __syncthreads();
     }
   }
-  __syncthreads();
   if (tid == 0) {
     double f = 0;
     for (int i = 0; i < m; ++i)
@@ -1575,6 +1738,7 @@ __global__ void k_rayleigh_ritz_chol(int m, int k, const double* __restrict__ G,
     rayleigh_ritz_eig(m, k, G, H, drop_tol, lam_old, C, lam_new, hist_row, stop_rule, tol, st, rr);
     return;
   }
+  tcl[3] = clock64();
   // B3 = H' L^{-T};  B4 = L^{-1} B3  (= H'')
   for (int t = tid; t < m * m; t += blockDim.x) {
     const int a = t / m, b = t % m;
@@ -1596,29 +1760,74 @@ __global__ void k_rayleigh_ritz_chol(int m, int k, const double* __restrict__ G,
     if (a < b) B4[a * ld + b] = B4[b * ld + a];
   }
   __syncthreads();
-  // eigen-decomposition of H'' (A: B4/B0, V: B1/B3; B2 = L^{-1} is kept)
-  double *Ar, *Vr;
-  jacobi_eig_sym(B4, B0, B1, B3, m, &Ar, &Vr, fr, gr, partner);
-  sort_diag(Ar, m, ord);
+  tcl[4] = clock64();
+  int nsweeps = 0;
+  const double* Vd = nullptr;  // FP64 eigenvectors (native path)
+  float *Vrh = nullptr, *Vrl = nullptr;
+  if (!dword) {
+    double* Ar;
+    double* Vr;
+    nsweeps = jacobi_eig_sym(B4, B0, B1, B3, m, &Ar, &Vr, fr, gr, partner);
+    for (int j = tid; j < m; j += blockDim.x) fr[j] = Ar[j * ld + j];
+    Vd = Vr;
+  } else {
+    // double-word Jacobi: A planes in B0, A2 in B1, V in B3, V2 in B4 (after
+    // H'' has been split out of B4); B2 = L^{-1} is kept
+    float* Ah = reinterpret_cast<float*>(B0);
+    float* Al = Ah + LL;
+    for (int t = tid; t < m * m; t += blockDim.x) {
+      const int a = t / m, b = t % m;
+      const dw sp = split_f64(B4[a * ld + b]);
+      Ah[a * ld + b] = sp.hi;
+      Al[a * ld + b] = sp.lo;
+    }
+    __syncthreads();
+    float *Arh, *Arl;
+    nsweeps = jacobi_eig_dw(Ah, Al, reinterpret_cast<float*>(B1), reinterpret_cast<float*>(B1) + LL,
+                            reinterpret_cast<float*>(B3), reinterpret_cast<float*>(B3) + LL,
+                            reinterpret_cast<float*>(B4), reinterpret_cast<float*>(B4) + LL, m, &Arh, &Arl, &Vrh,
+                            &Vrl, reinterpret_cast<dw*>(fr), reinterpret_cast<dw*>(gr), partner);
+    __syncthreads();
+    for (int j = tid; j < m; j += blockDim.x) fr[j] = dw_to_f64(Arh[j * ld + j], Arl[j * ld + j]);
+  }
+  tcl[5] = clock64();
+  __syncthreads();
+  // ascending order of the eigenvalues (ties by index), one rank per thread
+  for (int j = tid; j < m; j += blockDim.x) {
+    const double fj = fr[j];
+    int rank = 0;
+    for (int i2 = 0; i2 < m; ++i2) {
+      const double fi = fr[i2];
+      rank += (fi < fj || (fi == fj && i2 < j)) ? 1 : 0;
+    }
+    ord[rank] = j;
+  }
+  __syncthreads();
+  auto yv = [&](int b, int j) -> double {
+    return Vd ? Vd[b * ld + j] : dw_to_f64(Vrh[b * ld + j], Vrl[b * ld + j]);
+  };
   // C = diag(sc) L^{-T} Y[:, 0..k)
   for (int t = tid; t < m * k; t += blockDim.x) {
     const int a = t / k, c = t % k;
     const int j = ord[c];
     double s = 0;
-    for (int b = a; b < m; ++b) s = fma(B2[b * ld + a], Vr[b * ld + j], s);
+    for (int b = a; b < m; ++b) s = fma(B2[b * ld + a], yv(b, j), s);
     C[a * k + c] = sc[a] * s;
   }
   __syncthreads();
   if (tid == 0) {
     double dl = 0;
     for (int c = 0; c < k; ++c) {
-      const double th = Ar[ord[c] * ld + ord[c]];
+      const double th = fr[ord[c]];
       dl += fabs(th - lam_old[c]);
       lam_new[c] = th;
       if (hist_row) hist_row[c] = th;
     }
     st->sum_dl = dl;
     st->kept = m;
+    st->sweeps = nsweeps;
+    tcl[6] = clock64();
+    for (int q = 0; q < 6; ++q) st->rr_cycles[q] = tcl[q + 1] - tcl[q];
     if (stop_rule == BPJD_STOP_DLAMBDA) st->converged = (dl < tol) ? 1 : 0;
   }
 }
@@ -1985,7 +2194,7 @@ size_t gram_partial_doubles(int64_t n, int k, int nu, int nvb, int sym) {
   const int mu = nu * k, mv = nvb * k;
   const int TU = (mu + 3) / 4, TV = (mv + 3) / 4;
   const int ntiles = sym ? TU * (TU + 1) / 2 : TU * TV;
-  const int nblk = (int)std::min<int64_t>(kPartialBlocks, (n + kGramRows - 1) / kGramRows);
+  const int nblk = (int)std::min<int64_t>(kGramBlocks, (n + kGramRows - 1) / kGramRows);
   const int rpb = (int)(((n + nblk - 1) / nblk + kGramRows - 1) / kGramRows * kGramRows);
   const int nblk2 = (int)((n + rpb - 1) / rpb);
   return (size_t)nblk2 * ntiles * 16;
@@ -2004,7 +2213,7 @@ int launch_gram_raw(int64_t n, int k, int nu, const double* const* U, int nvb, i
     v1.p[b] = V1[b];
     if (nv > 1) v2.p[b] = V2[b];
   }
-  const int nblk = (int)std::min<int64_t>(kPartialBlocks, (n + kGramRows - 1) / kGramRows);
+  const int nblk = (int)std::min<int64_t>(kGramBlocks, (n + kGramRows - 1) / kGramRows);
   const int rpb = (int)(((n + nblk - 1) / nblk + kGramRows - 1) / kGramRows * kGramRows);
   const int nblk2 = (int)((n + rpb - 1) / rpb);
   const int total = nv * ntiles * 16;
@@ -2133,8 +2342,8 @@ int launch_rr(Handle& h, int m, const double* G, const double* Hm, const double*
   ProfScope ps(h, BPJD_PROF_RR);
   h.launches += 1;
   double* hr = (hist_row >= 0 && hist_row < h.hist_rows) ? h.hist + (int64_t)hist_row * h.k : nullptr;
-  k_rayleigh_ritz_chol<<<1, 256, sm, h.stream>>>(m, h.k, G, Hm, h.drop_tol, lam_old, C, lam_new, hr, h.stop_rule,
-                                                 h.tol, h.dstat);
+  k_rayleigh_ritz_chol<<<1, 1024, sm, h.stream>>>(m, h.k, G, Hm, h.drop_tol, lam_old, C, lam_new, hr, h.stop_rule,
+                                                 h.tol, h.dstat, h.precision == BPJD_MIXED ? 1 : 0);
   return (int)cudaGetLastError();
 }
 
