@@ -1537,7 +1537,16 @@ __device__ int jacobi_eig_dw(float* Ah, float* Al, float* A2h, float* A2l, float
         ++t;
       }
   }
+  __shared__ float amax_d;
+  if (tid == 0) {
+    float a = 0.f;
+    for (int j = 0; j < m; ++j) a = fmaxf(a, fabsf(Ah[j * ld + j]));
+    amax_d = a;
+  }
   __syncthreads();
+  // below the double-word noise of the largest diagonal entry an off-diagonal
+  // entry is left (its effect on the eigenpairs is below that noise)
+  const float abs_floor = 1e-14f * amax_d;
   const int half = mp / 2;
   int sweep = 0;
   for (; sweep < 60; ++sweep) {
@@ -1557,9 +1566,10 @@ __device__ int jacobi_eig_dw(float* Ah, float* Al, float* A2h, float* A2l, float
         const float apq = Ah[p * ld + q] + Al[p * ld + q];
         const float app = Ah[p * ld + p], aqq = Ah[q * ld + q];
         dw c = {1.f, 0.f}, s = {0.f, 0.f};
-        if (fabsf(apq) > 1e-37f && fabsf(apq) > 1e-15f * sqrtf(fabsf(app * aqq))) {
-          const float tau = (aqq - app) / (2.f * apq);
-          const float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+        if (fabsf(apq) > abs_floor && fabsf(apq) > 1e-15f * __fsqrt_rn(fabsf(app * aqq))) {
+          // the angle may be approximate; c and s below are orthogonal to double-word accuracy
+          const float tau = __fdividef(aqq - app, 2.f * apq);
+          const float t = __fdividef(tau >= 0.f ? 1.f : -1.f, fabsf(tau) + __fsqrt_rn(1.f + tau * tau));
           // u = 1 + t^2 exactly in double-word
           float ph, pe, uh, ue;
           two_prod(t, t, ph, pe);
@@ -1631,6 +1641,334 @@ __device__ int jacobi_eig_dw(float* Ah, float* Al, float* A2h, float* A2l, float
   return sweep + 1;
 }
 
+// ---------------------------------------------------------------------------
+// Mixed-precision Rayleigh-Ritz solve of the scaled pencil (H', G') (FP64 in
+// Gd, Hd, leading dimension kRRMax):
+//  phase A (FP32): G' = L L^T, B = L^{-T}, Jacobi on B^T H' B, Q = B V
+//                  -- an approximate G'-orthonormal eigenbasis;
+//  phase B (double-word): G2 = Q^T G' Q = I + E, S = I - E/2 + 3E^2/8
+//                  ((I + E)^{-1/2} to O(E^3)), Q' = Q S, H3 = S^T Q^T H' Q S,
+//                  double-word Jacobi on the nearly diagonal H3 (Y), and the
+//                  Ritz basis Q' Y.
+// Returns false (nothing written) when the FP32 Cholesky fails or the Gram
+// matrix is too ill-conditioned for the series; the caller then takes the
+// eigen-based path.  Output: theta (ascending, m values) and the basis Ritz
+// vectors as FP64 in Cout (m x m, column j = j-th Ritz vector).
+// ---------------------------------------------------------------------------
+constexpr int kL = kRRMax * kRRMax;
+
+// C = op(A) * op(B) for m x m double-word matrices (hi/lo planes, ld kRRMax);
+// ta / tb: use the transpose.  B may be an FP32 matrix (Bl == nullptr).
+__device__ void dw_gemm(int m, const float* Ah, const float* Al, bool ta, const float* Bh, const float* Bl, bool tb,
+                        float* Ch, float* Cl) {
+  const int ld = kRRMax;
+  for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+    const int i = t / m, j = t % m;
+    dot2 acc;
+    acc.zero();
+    for (int p = 0; p < m; ++p) {
+      const int ia = ta ? p * ld + i : i * ld + p;
+      const int ib = tb ? j * ld + p : p * ld + j;
+      acc.mac(Ah[ia], Al ? Al[ia] : 0.f, Bh[ib], Bl ? Bl[ib] : 0.f);
+    }
+    dw r;
+    fast_two_sum(acc.s, acc.c, r.hi, r.lo);
+    Ch[i * ld + j] = r.hi;
+    Cl[i * ld + j] = r.lo;
+  }
+  __syncthreads();
+}
+
+// FP32 parallel cyclic Jacobi (same ordering as the double-word version).
+__device__ int jacobi_f32(float* A, float* A2, float* V, float* V2, int m, float** Aout, float** Vout, float* fr,
+                          float* gr, int* partner, float off_tol) {
+  const int mp = m + (m & 1);
+  const int ld = kRRMax;
+  const int tid = threadIdx.x;
+  __shared__ int done;
+  __shared__ unsigned char tri_r[kRRMax * (kRRMax + 1) / 2], tri_c[kRRMax * (kRRMax + 1) / 2];
+  for (int t = tid; t < mp * ld; t += blockDim.x) {
+    const int r = t / ld, c = t % ld;
+    V[t] = (r == c) ? 1.f : 0.f;
+    if ((r >= m || c >= m) && c < mp) A[t] = 0.f;
+  }
+  if (tid == 0) {
+    int t = 0;
+    for (int r = 0; r < mp; ++r)
+      for (int c = 0; c <= r; ++c) {
+        tri_r[t] = (unsigned char)r;
+        tri_c[t] = (unsigned char)c;
+        ++t;
+      }
+  }
+  __syncthreads();
+  const int half = mp / 2;
+  __shared__ float amax_f;
+  if (tid == 0) {
+    float a = 0.f;
+    for (int j = 0; j < m; ++j) a = fmaxf(a, fabsf(A[j * ld + j]));
+    amax_f = a;
+  }
+  __syncthreads();
+  // off-diagonal entries below the FP32 noise of the largest diagonal entry are left
+  const float abs_floor = 1e-6f * amax_f;
+  int sweep = 0;
+  for (; sweep < 30; ++sweep) {
+    if (tid == 0) done = 1;
+    __syncthreads();
+    for (int round = 0; round < mp - 1; ++round) {
+      if (tid < half) {
+        int e0 = 0, e1;
+        auto ring = [&](int pos) { return ((pos + round) % (mp - 1)) + 1; };
+        if (tid == 0) {
+          e1 = ring(0);
+        } else {
+          e0 = ring(tid);
+          e1 = ring(mp - 1 - tid);
+        }
+        const int p = min(e0, e1), q = max(e0, e1);
+        const float apq = A[p * ld + q], app = A[p * ld + p], aqq = A[q * ld + q];
+        float c = 1.f, s = 0.f;
+        if (fabsf(apq) > abs_floor && fabsf(apq) > off_tol * __fsqrt_rn(fabsf(app * aqq))) {
+          // approximate angle (fast intrinsics): phase B restores exact orthogonality
+          const float tau = __fdividef(aqq - app, 2.f * apq);
+          const float t = __fdividef(tau >= 0.f ? 1.f : -1.f, fabsf(tau) + __fsqrt_rn(1.f + tau * tau));
+          c = rsqrtf(1.f + t * t);
+          s = t * c;
+          done = 0;
+        }
+        fr[p] = c;
+        gr[p] = -s;
+        partner[p] = q;
+        fr[q] = c;
+        gr[q] = s;
+        partner[q] = p;
+      }
+      __syncthreads();
+      for (int t = tid; t < mp * (mp + 1) / 2; t += blockDim.x) {
+        const int r = tri_r[t], c = tri_c[t];
+        const int rb = partner[r], cb = partner[c];
+        const float v = fr[r] * (fr[c] * A[r * ld + c] + gr[c] * A[r * ld + cb]) +
+                        gr[r] * (fr[c] * A[rb * ld + c] + gr[c] * A[rb * ld + cb]);
+        A2[r * ld + c] = v;
+        A2[c * ld + r] = v;
+      }
+      for (int t = tid; t < mp * mp; t += blockDim.x) {
+        const int x = t / mp, r = t % mp;
+        V2[x * ld + r] = V[x * ld + r] * fr[r] + V[x * ld + partner[r]] * gr[r];
+      }
+      __syncthreads();
+      float* tA = A;
+      A = A2;
+      A2 = tA;
+      float* tV = V;
+      V = V2;
+      V2 = tV;
+    }
+    if (done) break;
+    __syncthreads();
+  }
+  *Aout = A;
+  *Vout = V;
+  return sweep + 1;
+}
+
+// G, H: the unscaled Gram matrices (FP64, m x m, ld m); sc: column scaling.
+// pool: 12 slots of kL floats.  theta: kRRMax doubles (ascending Ritz values on
+// return); fr/gr/partner/ord: kRRMax entries each (fr, gr 8 bytes per entry).
+// Writes C = diag(sc) Q' Y[:, lowest k] (m x k, ld k).  Returns the number of
+// double-word Jacobi sweeps, or -1 (nothing written).
+__device__ int rr_mixed_solve(int m, int k, const double* __restrict__ G, const double* __restrict__ H,
+                              const double* sc, float* pool, double* theta, double* C, double* fr, double* gr,
+                              int* partner, int* ord, double drop_tol, long long* cyc) {
+  const int ld = kRRMax;
+  const int tid = threadIdx.x;
+  float* s[12];
+  for (int i = 0; i < 12; ++i) s[i] = pool + (size_t)i * kL;
+  __shared__ int ok;
+  float *Gh = s[0], *Gl = s[1], *Hh = s[2], *Hl = s[3];
+  for (int t = tid; t < m * m; t += blockDim.x) {
+    const int a = t / m, b = t % m;
+    const double gs = 0.5 * (G[a * m + b] + G[b * m + a]) * sc[a] * sc[b];
+    const double hs = 0.5 * (H[a * m + b] + H[b * m + a]) * sc[a] * sc[b];
+    const dw g = split_f64(gs), hh = split_f64(hs);
+    Gh[a * ld + b] = g.hi;
+    Gl[a * ld + b] = g.lo;
+    Hh[a * ld + b] = hh.hi;
+    Hl[a * ld + b] = hh.lo;
+  }
+  if (tid == 0) ok = 1;
+  __syncthreads();
+  long long t0 = clock64();
+  // ---- phase A (FP32)
+  float *L = s[4], *Li = s[5], *T32 = s[6];
+  for (int t = tid; t < m * m; t += blockDim.x) L[(t / m) * ld + (t % m)] = Gh[(t / m) * ld + (t % m)];
+  __syncthreads();
+  for (int j = 0; j < m; ++j) {
+    if (tid == 0) {
+      const float d = L[j * ld + j];
+      if (!(d > 0.f)) ok = 0;
+      L[j * ld + j] = (d > 0.f) ? sqrtf(d) : 1.f;
+    }
+    __syncthreads();
+    const float ljj = L[j * ld + j];
+    for (int i = j + 1 + tid; i < m; i += blockDim.x) L[i * ld + j] /= ljj;
+    __syncthreads();
+    const int rem = m - j - 1;
+    for (int t = tid; t < rem * rem; t += blockDim.x) {
+      const int i = j + 1 + t / rem, c = j + 1 + t % rem;
+      if (c <= i) L[i * ld + c] -= L[i * ld + j] * L[c * ld + j];
+    }
+    __syncthreads();
+  }
+  for (int c = tid; c < m; c += blockDim.x)
+    for (int i = 0; i < m; ++i) {
+      float v = 0.f;
+      if (i >= c) {
+        v = (i == c) ? 1.f : 0.f;
+        for (int t = c; t < i; ++t) v -= L[i * ld + t] * Li[t * ld + c];
+        v /= L[i * ld + i];
+      }
+      Li[i * ld + c] = v;
+    }
+  __syncthreads();
+  if (tid == 0) {
+    float f = 0.f, tr = 0.f;
+    for (int i = 0; i < m; ++i) {
+      tr += Gh[i * ld + i];
+      for (int c = 0; c <= i; ++c) f += Li[i * ld + c] * Li[i * ld + c];
+    }
+    // 1 / ||L^{-1}||_F^2 <= lambda_min(G'): keep a margin over the drop threshold
+    // (so the eigen-based basis would drop nothing) and over the conditioning
+    // that the FP32 basis and the series of phase B resolve
+    if (!(1.f / f > (float)(drop_tol * 10.0) * tr) || !(1.f / f > 1e-4f * tr)) ok = 0;
+  }
+  __syncthreads();
+  if (!ok) return -1;
+  long long t1 = clock64();
+  float* A = s[7];
+  for (int t = tid; t < m * m; t += blockDim.x) {
+    const int a = t / m, b = t % m;
+    float v = 0.f;
+    for (int c = 0; c <= b; ++c) v += Hh[a * ld + c] * Li[b * ld + c];
+    T32[a * ld + b] = v;
+  }
+  __syncthreads();
+  for (int t = tid; t < m * m; t += blockDim.x) {
+    const int a = t / m, b = t % m;
+    float v = 0.f;
+    for (int c = 0; c <= a; ++c) v += Li[a * ld + c] * T32[c * ld + b];
+    A[a * ld + b] = v;
+  }
+  __syncthreads();
+  for (int t = tid; t < m * m; t += blockDim.x) {
+    const int a = t / m, b = t % m;
+    if (a < b) {
+      const float v = 0.5f * (A[a * ld + b] + A[b * ld + a]);
+      A[a * ld + b] = v;
+      A[b * ld + a] = v;
+    }
+  }
+  __syncthreads();
+  float *Ar, *Vr;
+  const int sw32 = jacobi_f32(A, s[8], s[9], s[10], m, &Ar, &Vr, reinterpret_cast<float*>(fr),
+                             reinterpret_cast<float*>(gr), partner, 1e-5f);
+  long long t2 = clock64();
+  float* Q = s[11];
+  for (int t = tid; t < m * m; t += blockDim.x) {
+    const int a = t / m, b = t % m;
+    float v = 0.f;
+    for (int c = a; c < m; ++c) v += Li[c * ld + a] * Vr[c * ld + b];
+    Q[a * ld + b] = v;
+  }
+  __syncthreads();
+  // ---- phase B (double-word)
+  float *T1h = s[4], *T1l = s[5], *G2h = s[6], *G2l = s[7], *H2h = s[8], *H2l = s[9];
+  dw_gemm(m, Gh, Gl, false, Q, nullptr, false, T1h, T1l);   // G' Q
+  dw_gemm(m, Q, nullptr, true, T1h, T1l, false, G2h, G2l);  // Q^T G' Q
+  dw_gemm(m, Hh, Hl, false, Q, nullptr, false, T1h, T1l);   // H' Q
+  dw_gemm(m, Q, nullptr, true, T1h, T1l, false, H2h, H2l);  // Q^T H' Q
+  for (int t = tid; t < m; t += blockDim.x) {              // E = G2 - I
+    float hi, lo;
+    two_sum(G2h[t * ld + t], -1.f, hi, lo);
+    const dw e = dw_renorm(hi, __fadd_rn(lo, G2l[t * ld + t]));
+    G2h[t * ld + t] = e.hi;
+    G2l[t * ld + t] = e.lo;
+  }
+  __syncthreads();
+  dw_gemm(m, G2h, G2l, false, G2h, G2l, false, T1h, T1l);  // E^2
+  float *Sh = s[0], *Sl = s[1];
+  for (int t = tid; t < m * m; t += blockDim.x) {         // S = I - E/2 + 3 E^2 / 8
+    const int a = t / m, b = t % m;
+    dot2 acc;
+    acc.zero();
+    if (a == b) acc.add(1.f, 0.f);
+    acc.mac(-0.5f, 0.f, G2h[a * ld + b], G2l[a * ld + b]);
+    acc.mac(0.375f, 0.f, T1h[a * ld + b], T1l[a * ld + b]);
+    const dw r = dw_renorm(acc.s, acc.c);
+    Sh[a * ld + b] = r.hi;
+    Sl[a * ld + b] = r.lo;
+  }
+  __syncthreads();
+  dw_gemm(m, H2h, H2l, false, Sh, Sl, false, T1h, T1l);    // H2 S
+  float *H3h = s[2], *H3l = s[3];
+  dw_gemm(m, Sh, Sl, true, T1h, T1l, false, H3h, H3l);     // S^T H2 S
+  for (int t = tid; t < m * m; t += blockDim.x) {
+    const int a = t / m, b = t % m;
+    if (a < b) {
+      dot2 acc;
+      acc.zero();
+      acc.add(H3h[a * ld + b], H3l[a * ld + b]);
+      acc.add(H3h[b * ld + a], H3l[b * ld + a]);
+      const dw r = dw_renorm(0.5f * acc.s, 0.5f * acc.c);
+      H3h[a * ld + b] = r.hi;
+      H3l[a * ld + b] = r.lo;
+      H3h[b * ld + a] = r.hi;
+      H3l[b * ld + a] = r.lo;
+    }
+  }
+  __syncthreads();
+  float *Qph = s[6], *Qpl = s[7];
+  dw_gemm(m, Q, nullptr, false, Sh, Sl, false, Qph, Qpl);  // Q' = Q S
+  long long t3 = clock64();
+  float *Arh, *Arl, *Vrh, *Vrl;
+  const int sw = jacobi_eig_dw(H3h, H3l, s[8], s[9], s[4], s[5], s[0], s[1], m, &Arh, &Arl, &Vrh, &Vrl,
+                               reinterpret_cast<dw*>(fr), reinterpret_cast<dw*>(gr), partner);
+  __syncthreads();
+  long long t4 = clock64();
+  for (int j = tid; j < m; j += blockDim.x) theta[j] = dw_to_f64(Arh[j * ld + j], Arl[j * ld + j]);
+  __syncthreads();
+  for (int j = tid; j < m; j += blockDim.x) {
+    const double tj = theta[j];
+    int rank = 0;
+    for (int i2 = 0; i2 < m; ++i2) {
+      const double ti = theta[i2];
+      rank += (ti < tj || (ti == tj && i2 < j)) ? 1 : 0;
+    }
+    ord[rank] = j;
+  }
+  __syncthreads();
+  for (int t = tid; t < m * k; t += blockDim.x) {
+    const int a = t / k, c = t % k;
+    const int j = ord[c];
+    dot2 acc;
+    acc.zero();
+    for (int p = 0; p < m; ++p) acc.mac(Qph[a * ld + p], Qpl[a * ld + p], Vrh[p * ld + j], Vrl[p * ld + j]);
+    C[a * k + c] = sc[a] * acc.value();
+  }
+  __syncthreads();
+  if (tid == 0 && cyc) {
+    const long long t5 = clock64();
+    cyc[0] = t1 - t0;
+    cyc[1] = t2 - t1;
+    cyc[2] = t3 - t2;
+    cyc[3] = t4 - t3;
+    cyc[4] = t5 - t4;
+    cyc[5] = sw32 * 1000;
+  }
+  return sw;
+}
+
 // Rayleigh-Ritz (Eq. (3.6)) with a Cholesky orthonormalisation of the scaled
 // Gram matrix G' = L L^T.  When the lower bound 1 / ||L^{-1}||_F^2 of the
 // smallest eigenvalue of G' exceeds drop_tol * trace(G') >= drop_tol * lambda_max,
@@ -1650,7 +1988,7 @@ __global__ void k_rayleigh_ritz_chol(int m, int k, const double* __restrict__ G,
   double* B2 = B1 + LL;
   double* B3 = B2 + LL;
   double* B4 = B3 + LL;
-  double* sc = B4 + LL;
+  double* sc = B4 + 2 * LL;  // B5 (one more slot) belongs to the mixed-precision pool
   double* fr = sc + ld;
   double* gr = fr + ld;
   int* partner = reinterpret_cast<int*>(gr + ld);
@@ -1666,6 +2004,32 @@ __global__ void k_rayleigh_ritz_chol(int m, int k, const double* __restrict__ G,
   }
   if (tid == 0) ok = 1;
   __syncthreads();
+  if (dword) {
+    double* theta = sc + ld;  // fr and gr are workspace of the solve
+    __shared__ double th_s[kRRMax];
+    const int sw = rr_mixed_solve(m, k, G, H, sc, reinterpret_cast<float*>(rr), th_s, C, fr, gr, partner, ord,
+                                  drop_tol, st->rr_cycles);
+    (void)theta;
+    if (sw >= 0) {
+      if (tid == 0) {
+        double dl = 0;
+        for (int c = 0; c < k; ++c) {
+          const double th = th_s[ord[c]];
+          dl += fabs(th - lam_old[c]);
+          lam_new[c] = th;
+          if (hist_row) hist_row[c] = th;
+        }
+        st->sum_dl = dl;
+        st->kept = m;
+        st->sweeps = sw;
+        if (stop_rule == BPJD_STOP_DLAMBDA) st->converged = (dl < tol) ? 1 : 0;
+      }
+      return;
+    }
+    // ill-conditioned: eigen-based orthonormalisation with dropping
+    rayleigh_ritz_eig(m, k, G, H, drop_tol, lam_old, C, lam_new, hist_row, stop_rule, tol, st, rr);
+    return;
+  }
   // B0 = G' (becomes L), B1 = H'
   for (int t = tid; t < m * m; t += blockDim.x) {
     const int a = t / m, b = t % m;
@@ -2337,7 +2701,7 @@ int launch_precond(Handle& h, const double* rho, const double* lam, double* Z) {
 int launch_rr(Handle& h, int m, const double* G, const double* Hm, const double* lam_old, double* C,
               double* lam_new, int hist_row) {
   if (m > kRRMax) return (int)cudaErrorInvalidValue;
-  size_t sm = (size_t)(5 * kRRMax * kRRMax + 3 * kRRMax) * sizeof(double) + 3 * kRRMax * sizeof(int);
+  size_t sm = (size_t)(6 * kRRMax * kRRMax + 3 * kRRMax) * sizeof(double) + 3 * kRRMax * sizeof(int);
   cudaFuncSetAttribute(k_rayleigh_ritz_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   ProfScope ps(h, BPJD_PROF_RR);
   h.launches += 1;
