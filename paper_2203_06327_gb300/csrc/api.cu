@@ -453,7 +453,7 @@ extern "C" int bpjd_setup(const bpjd_csr* A, const bpjd_csr* M, const bpjd_csr* 
     }
     h->B = bw + 1;
     if (h->precision == BPJD_MIXED) {
-      static const int tiers[] = {16, 24, 32, 40, 48, 64};
+      static const int tiers[] = {16, 24, 32, 40, 48, 64, 96, 128};
       for (int t : tiers)
         if (h->B <= t) {
           h->Bpad = t;

@@ -1125,6 +1125,165 @@ __global__ void __launch_bounds__(128, (BMAX <= 32) ? 4 : ((BMAX <= 40) ? 3 : 2)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Local solves for wide bands (window up to 128, e.g. 3-D subdomains): one CTA
+// per (subdomain, shift) with one thread per window column (thread v owns
+// column v, slot u = row mod BMAX, as in k_local_band_reg).  Per elimination
+// step the raw pivot column is published in shared memory and one CTA barrier
+// later every column applies its rank-one update w_v -= c_s * (c_v / pivot),
+// stores its entry of L and receives its entry of the incoming band row
+// (prefetched PD steps ahead); a second barrier lets the owner of the pivot
+// slot gather that row as its new column.  The backward substitution keeps
+// x_{row of slot v} in thread v and needs one barrier per row.
+// ---------------------------------------------------------------------------
+template <int BMAX>
+__global__ void __launch_bounds__(((BMAX + 31) / 32) * 32) k_local_band_team(
+    int npairs, int k, const int64_t* __restrict__ sub_ptr, const int32_t* __restrict__ sub_dofs,
+    const float* __restrict__ bandK, const float* __restrict__ bandM, const double* __restrict__ lam,
+    const double* __restrict__ rho, float* __restrict__ Lbuf, float* __restrict__ wpk, int32_t* err) {
+  constexpr int PD = 4;  // prefetch distance (steps) of the incoming band entries
+  constexpr int PB = 4;  // prefetch distance (rows) of the backward substitution
+  constexpr int NW = (BMAX + 31) / 32;
+  static_assert(BMAX % PD == 0, "the prefetch ring index must be static within a window group");
+  __shared__ __align__(16) float sc[BMAX];  // raw pivot column of the current step
+  __shared__ __align__(16) float sa[BMAX];  // incoming band row
+  __shared__ float srw;
+  __shared__ float sred[2][NW];
+  const int v = threadIdx.x;
+  const bool own = v < BMAX;
+  const int pair = blockIdx.x;
+  if (pair >= npairs) return;
+  const int l = pair / k, i = pair % k;
+  const int64_t off = sub_ptr[l];
+  const int nl = (int)(sub_ptr[l + 1] - off);
+  const int32_t* dofs = sub_dofs + off;
+  const float lm = (float)lam[i];
+  float* Lp = Lbuf + ((size_t)off * k + (size_t)i * nl) * BMAX;
+  const float* gK = bandK + (size_t)off * BMAX;
+  const float* gM = bandM + (size_t)off * BMAX;
+  auto aval = [&](int p, int q) -> float {  // shifted entry (p, q), q <= p
+    if (p >= nl) return (p == q) ? 1.f : 0.f;
+    const int d = p - q;
+    if (d >= BMAX || q < 0) return 0.f;
+    const size_t e = (size_t)p * BMAX + (BMAX - 1 - d);
+    return gK[e] - lm * gM[e];
+  };
+  auto rhs = [&](int p) -> float { return (p < nl) ? (float)rho[(int64_t)dofs[p] * k + i] : 0.f; };
+  // entry of row j + BMAX that column v receives at step j (slot s = j mod BMAX)
+  auto incoming = [&](int j, int s) -> float {
+    int t = v - s;
+    t += (t <= 0) ? BMAX : 0;
+    return own ? aval(j + BMAX, j + t) : 0.f;
+  };
+  float w[BMAX];
+#pragma unroll
+  for (int u = 0; u < BMAX; ++u) w[u] = own ? ((u >= v) ? aval(u, v) : aval(v, u)) : 0.f;
+  float rw = own ? rhs(v) : 0.f;
+  float pre[PD], rpre[PD];
+#pragma unroll
+  for (int d = 0; d < PD; ++d) {
+    pre[d] = incoming(d, d);
+    rpre[d] = rhs(d + BMAX);
+  }
+  bool bad = false;
+  for (int j0 = 0; j0 < nl; j0 += BMAX) {
+    // an opaque zero keeps per-slot comparisons from being hoisted out of the loop
+    int zero;
+    asm volatile("mov.u32 %0, 0;" : "=r"(zero));
+    const int vz = v + zero;
+#pragma unroll
+    for (int s = 0; s < BMAX; ++s) {
+      const int j = j0 + s;
+      if (j >= nl) break;
+      const int pd = s % PD;  // j0 is a multiple of BMAX, hence of PD
+      if (own) sc[vz] = w[s];
+      if (vz == s) srw = rw;
+      __syncthreads();
+      float piv = sc[s];
+      if (!(piv > 0.f)) {  // the same value in every thread
+        bad = true;
+        piv = 1.f;
+      }
+      const float inv = rsqrtf(piv);
+      const float yj = srw * inv;
+      const float lv = w[s] * inv;  // L(row of slot v, j); sqrt(pivot) for v = s
+      const float cv = lv * inv;
+#pragma unroll
+      for (int u4 = 0; u4 < BMAX; u4 += 4) {
+        const float4 q = *reinterpret_cast<const float4*>(sc + u4);
+        w[u4 + 0] = fmaf(-q.x, cv, w[u4 + 0]);
+        w[u4 + 1] = fmaf(-q.y, cv, w[u4 + 1]);
+        w[u4 + 2] = fmaf(-q.z, cv, w[u4 + 2]);
+        w[u4 + 3] = fmaf(-q.w, cv, w[u4 + 3]);
+      }
+      rw = fmaf(-lv, yj, rw);
+      if (own) Lp[(size_t)j * BMAX + vz] = (vz == s) ? inv : lv;
+      if (vz == 0) wpk[(off + j) * k + i] = yj;
+      // row j + BMAX (prefetched PD steps ago) enters slot s
+      const float anew = pre[pd];
+      const float rnew = rpre[pd];
+      w[s] = anew;
+      if (own) sa[vz] = anew;
+      pre[pd] = incoming(j + PD, (s + PD) % BMAX);
+      rpre[pd] = rhs(j + PD + BMAX);
+      __syncthreads();
+      if (vz == s) {
+#pragma unroll
+        for (int u4 = 0; u4 < BMAX; u4 += 4) {
+          const float4 q = *reinterpret_cast<const float4*>(sa + u4);
+          w[u4 + 0] = q.x;
+          w[u4 + 1] = q.y;
+          w[u4 + 2] = q.z;
+          w[u4 + 3] = q.w;
+        }
+        rw = rnew;
+      }
+    }
+  }
+  if (bad) {
+    if (v == 0) atomicOr(err, 1);
+    return;
+  }
+  // backward substitution with L^T: thread v holds x of the row in slot v
+  // (zero for rows not reached yet and for rows beyond nl, whose L entries are zero)
+  float xv = 0.f;
+  float lr[PB], yr[PB], dr[PB];
+  auto load_row = [&](int j, float& lrow, float& y, float& dinv) {
+    lrow = 0.f;
+    y = 0.f;
+    dinv = 0.f;
+    if (j < 0) return;
+    const float* row = Lp + (size_t)j * BMAX;
+    if (own) lrow = row[v];
+    y = wpk[(off + j) * k + i];
+    dinv = row[j % BMAX];
+  };
+#pragma unroll
+  for (int d = 0; d < PB; ++d) load_row(nl - 1 - d, lr[d], yr[d], dr[d]);
+  int par = 0;
+  for (int j1 = nl - 1; j1 >= 0; j1 -= PB) {
+#pragma unroll
+    for (int d = 0; d < PB; ++d) {
+      const int j = j1 - d;
+      if (j < 0) break;
+      const int s = j % BMAX;
+      const float lv = lr[d], y = yr[d], dinv = dr[d];
+      load_row(j - PB, lr[d], yr[d], dr[d]);
+      float part = (own && v != s) ? lv * xv : 0.f;
+      part = warp_sum(part);
+      if ((v & 31) == 0) sred[par][v >> 5] = part;
+      __syncthreads();
+      float tot = 0.f;
+#pragma unroll
+      for (int q = 0; q < NW; ++q) tot += sred[par][q];
+      const float xj = (y - tot) * dinv;
+      if (v == s) xv = xj;
+      if (v == 0) wpk[(off + j) * k + i] = xj;
+      par ^= 1;
+    }
+  }
+}
+
 // c[a, i] = sum_{g} P[g, a] rho[g, i] using P^T (CSR n_H x n); one block per coarse dof.
 __global__ void k_coarse_restrict(int nH, int k, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
                                   const double* __restrict__ pv, const double* __restrict__ rho, double* c) {
@@ -2651,6 +2810,15 @@ int launch_precond(Handle& h, const double* rho, const double* lam, double* Z) {
           k_local_band_reg<64><<<(npairs + 3) / 4, 128, 0, h.stream>>>(npairs, k, h.sub_ptr, h.sub_dofs, 64,
                                                                       h.bandKf, h.bandMf, lam, rho,
                                                                       (float*)h.Lbuf, (float*)h.wpk, h.derr);
+          break;
+        case 96:
+          k_local_band_team<96><<<npairs, 96, 0, h.stream>>>(npairs, k, h.sub_ptr, h.sub_dofs, h.bandKf, h.bandMf,
+                                                             lam, rho, (float*)h.Lbuf, (float*)h.wpk, h.derr);
+          break;
+        case 128:
+          k_local_band_team<128><<<npairs, 128, 0, h.stream>>>(npairs, k, h.sub_ptr, h.sub_dofs, h.bandKf,
+                                                               h.bandMf, lam, rho, (float*)h.Lbuf, (float*)h.wpk,
+                                                               h.derr);
           break;
         default:
           return (int)cudaErrorInvalidValue;
