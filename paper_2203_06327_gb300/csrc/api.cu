@@ -587,37 +587,71 @@ extern "C" int bpjd_setup(const bpjd_csr* A, const bpjd_csr* M, const bpjd_csr* 
 namespace {
 
 // sign normalisation: flip each column so its largest-magnitude entry is
-// positive (lowest row index wins ties)
-__global__ void k_sign_normalise(int n, int k, double* X) {
+// positive (lowest row index wins ties).  Three passes: per-block column
+// maxima over contiguous row ranges, one thread per column over the blocks,
+// then the flip.  The result does not depend on the order of the comparisons.
+constexpr int kSignBlocks = 304;
+
+__device__ __forceinline__ bool sign_better(double a, int ia, double b, int ib) {
+  return a > b || (a == b && ia < ib);
+}
+
+__global__ void __launch_bounds__(256) k_colmax_partial(int n, int k, const double* __restrict__ X,
+                                                        double* __restrict__ partial) {
   __shared__ double bv[256];
   __shared__ int bi[256];
-  const int col = blockIdx.x;
+  const int bs = k * (256 / k);  // threads in use; thread t serves column t % k
+  const int rows = (n + gridDim.x - 1) / gridDim.x;
+  const int r0 = blockIdx.x * rows, r1 = min(n, r0 + rows);
+  const int tid = threadIdx.x;
   double best = -1;
   int bidx = n;
-  for (int r = threadIdx.x; r < n; r += blockDim.x) {
-    double a = fabs(X[(int64_t)r * k + col]);
-    if (a > best) {
+  if (tid < bs) {
+    const int col = tid % k;
+    for (int64_t e = (int64_t)r0 * k + tid; e < (int64_t)r1 * k; e += bs) {
+      const double a = fabs(X[e]);
+      const int r = (int)(e / k);
+      if (sign_better(a, r, best, bidx)) {
+        best = a;
+        bidx = r;
+      }
+    }
+    (void)col;
+  }
+  bv[tid] = best;
+  bi[tid] = bidx;
+  __syncthreads();
+  if (tid < k) {
+    for (int t = tid + k; t < bs; t += k)
+      if (sign_better(bv[t], bi[t], best, bidx)) {
+        best = bv[t];
+        bidx = bi[t];
+      }
+    partial[((int64_t)blockIdx.x * k + tid) * 2] = best;
+    partial[((int64_t)blockIdx.x * k + tid) * 2 + 1] = (double)bidx;
+  }
+}
+
+__global__ void k_colmax_final(int nblk, int n, int k, const double* __restrict__ X, const double* partial,
+                               double* sign) {
+  const int col = threadIdx.x;
+  if (col >= k) return;
+  double best = -1;
+  int bidx = n;
+  for (int b = 0; b < nblk; ++b) {
+    const double a = partial[((int64_t)b * k + col) * 2];
+    const int r = (int)partial[((int64_t)b * k + col) * 2 + 1];
+    if (sign_better(a, r, best, bidx)) {
       best = a;
       bidx = r;
     }
   }
-  bv[threadIdx.x] = best;
-  bi[threadIdx.x] = bidx;
-  __syncthreads();
-  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-    if ((int)threadIdx.x < w) {
-      double o = bv[threadIdx.x + w];
-      int oi = bi[threadIdx.x + w];
-      if (o > bv[threadIdx.x] || (o == bv[threadIdx.x] && oi < bi[threadIdx.x])) {
-        bv[threadIdx.x] = o;
-        bi[threadIdx.x] = oi;
-      }
-    }
-    __syncthreads();
-  }
-  const bool flip = X[(int64_t)bi[0] * k + col] < 0;
-  if (flip)
-    for (int r = threadIdx.x; r < n; r += blockDim.x) X[(int64_t)r * k + col] = -X[(int64_t)r * k + col];
+  sign[col] = (bidx < n && X[(int64_t)bidx * k + col] < 0) ? -1.0 : 1.0;
+}
+
+__global__ void k_col_flip(int64_t nk, int k, const double* __restrict__ sign, double* __restrict__ X) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nk; e += (int64_t)gridDim.x * blockDim.x)
+    if (sign[e % k] < 0) X[e] = -X[e];
 }
 
 }  // namespace
@@ -740,8 +774,15 @@ extern "C" int bpjd_solve(bpjd_handle* hh, double* eigvals, double* eigvecs, int
     ++it;
   }
   if (rc == BPJD_OK || rc == BPJD_ERR_NOCONV) {
-    k_sign_normalise<<<k, 256, 0, h.stream>>>(n, k, X);
-    h.launches += 1;
+    {
+      const int nb = std::min(kSignBlocks, std::max(1, n));
+      double* part = h.partial;
+      double* sgn = h.partial + (size_t)2 * nb * k;
+      k_colmax_partial<<<nb, 256, 0, h.stream>>>(n, k, X, part);
+      k_colmax_final<<<1, 64, 0, h.stream>>>(nb, n, k, X, part, sgn);
+      k_col_flip<<<kSignBlocks, 256, 0, h.stream>>>((int64_t)n * k, k, sgn, X);
+      h.launches += 3;
+    }
     CK(cudaGetLastError());
     if (eigvals) CK(cudaMemcpyAsync(eigvals, lam_cur, sizeof(double) * k, cudaMemcpyDeviceToHost, h.stream));
     if (eigvecs)

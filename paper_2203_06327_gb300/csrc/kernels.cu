@@ -144,17 +144,27 @@ __global__ void k_rq_partial(int64_t nk, int k, const double* __restrict__ X, co
   block_column_partials(s0, s1, k, partial);
 }
 
-__global__ void k_residual_finish(int nblk, int k, const double* partial, const double* lam, int stop_rule,
-                                  double tol, DevStatus* st) {
+// sums[q] = sum_b partial[b * 2k + q] for q < 2k: warp w sums q = w, w + 8, ...,
+// lane l the blocks b = l, l + 32, ... in order, then a fixed butterfly.
+__device__ void column_partial_sums(int nblk, int k, const double* __restrict__ partial, double* sums) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int q = w; q < 2 * k; q += nw) {
+    double a = 0;
+    for (int b = lane; b < nblk; b += 32) a += partial[(int64_t)b * 2 * k + q];
+    a = warp_sum(a);
+    if (lane == 0) sums[q] = a;
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(256) k_residual_finish(int nblk, int k, const double* partial, const double* lam,
+                                                         int stop_rule, double tol, DevStatus* st) {
+  __shared__ double sums[128];
   __shared__ double res[64];
-  int i = threadIdx.x;
+  column_partial_sums(nblk, k, partial, sums);
+  const int i = threadIdx.x;
   if (i < k) {
-    double r2 = 0, m2 = 0;
-    for (int b = 0; b < nblk; ++b) {
-      r2 += partial[(int64_t)b * 2 * k + i];
-      m2 += partial[(int64_t)b * 2 * k + k + i];
-    }
-    double r = sqrt(r2) / (fabs(lam[i]) * sqrt(m2));
+    const double r = sqrt(sums[i]) / (fabs(lam[i]) * sqrt(sums[k + i]));
     res[i] = r;
     st->res[i] = r;
   }
@@ -167,16 +177,11 @@ __global__ void k_residual_finish(int nblk, int k, const double* partial, const 
   }
 }
 
-__global__ void k_rq_finish(int nblk, int k, const double* partial, double* lam) {
-  int i = threadIdx.x;
-  if (i < k) {
-    double a = 0, m = 0;
-    for (int b = 0; b < nblk; ++b) {
-      a += partial[(int64_t)b * 2 * k + i];
-      m += partial[(int64_t)b * 2 * k + k + i];
-    }
-    lam[i] = a / m;
-  }
+__global__ void __launch_bounds__(256) k_rq_finish(int nblk, int k, const double* partial, double* lam) {
+  __shared__ double sums[128];
+  column_partial_sums(nblk, k, partial, sums);
+  const int i = threadIdx.x;
+  if (i < k) lam[i] = sums[i] / sums[k + i];
 }
 
 // ---------------------------------------------------------------------------
@@ -363,15 +368,27 @@ __global__ void __launch_bounds__(256, 2) k_gram_dw(int n, int k, int nu, Ptrs6 
   }
 }
 
-__global__ void k_gram_reduce(int nblk, int nv, int mu, int mv, int sym, const double* __restrict__ partial,
-                              double* out1, double* out2) {
+// Sum of the per-block Gram partials: a block serves 32 consecutive entries;
+// warp w adds blocks b = w, w + 8, ... in order, warp 0 adds the eight results
+// in order (fixed order: bit-reproducible).
+__global__ void __launch_bounds__(256) k_gram_reduce(int nblk, int nv, int mu, int mv, int sym,
+                                                     const double* __restrict__ partial, double* out1,
+                                                     double* out2) {
+  __shared__ double red[8][32];
   const int TU = (mu + 3) / 4, TV = (mv + 3) / 4;
   const int ntiles = sym ? TU * (TU + 1) / 2 : TU * TV;
   const int total = nv * ntiles * 16;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= total) return;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int t = blockIdx.x * 32 + lane;
   double s = 0;
-  for (int b = 0; b < nblk; ++b) s += partial[(int64_t)b * total + t];
+  if (t < total)
+    for (int b = w; b < nblk; b += 8) s += partial[(int64_t)b * total + t];
+  red[w][lane] = s;
+  __syncthreads();
+  if (w != 0 || t >= total) return;
+  s = red[0][lane];
+#pragma unroll
+  for (int q = 1; q < 8; ++q) s += red[q][lane];
   const int v = t / (ntiles * 16);
   const int rem = t % (ntiles * 16);
   const int tile = rem / 16, e = rem % 16;
@@ -2681,7 +2698,7 @@ int launch_residual(Handle& h, const double* AX, const double* MX, const double*
   int nblk = (int)std::min<int64_t>(kPartialBlocks, (nk + bs - 1) / bs);
   h.launches += 2;
   k_residual<<<nblk, bs, 2 * bs * sizeof(double), h.stream>>>(nk, k, AX, MX, lam, rho, h.partial);
-  k_residual_finish<<<1, 64, 0, h.stream>>>(nblk, k, h.partial, lam, h.stop_rule, h.tol, h.dstat);
+  k_residual_finish<<<1, 256, 0, h.stream>>>(nblk, k, h.partial, lam, h.stop_rule, h.tol, h.dstat);
   return (int)cudaGetLastError();
 }
 
@@ -2692,7 +2709,7 @@ int launch_rayleigh(Handle& h, const double* X, const double* AX, const double* 
   int nblk = (int)std::min<int64_t>(kPartialBlocks, (nk + bs - 1) / bs);
   h.launches += 2;
   k_rq_partial<<<nblk, bs, 2 * bs * sizeof(double), h.stream>>>(nk, k, X, AX, MX, h.partial);
-  k_rq_finish<<<1, 64, 0, h.stream>>>(nblk, k, h.partial, lam);
+  k_rq_finish<<<1, 256, 0, h.stream>>>(nblk, k, h.partial, lam);
   return (int)cudaGetLastError();
 }
 
@@ -2751,7 +2768,7 @@ int launch_gram_raw(int64_t n, int k, int nu, const double* const* U, int nvb, i
     cudaFuncSetAttribute(k_gram_dw<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_gram_dw<1><<<nblk2, 256, sm, stream>>>((int)n, k, nu, u, nvb, v1, v2, sym, rpb, partial);
   }
-  k_gram_reduce<<<(total + 255) / 256, 256, 0, stream>>>(nblk2, nv, mu, mv, sym, partial, out1, out2);
+  k_gram_reduce<<<(total + 31) / 32, 256, 0, stream>>>(nblk2, nv, mu, mv, sym, partial, out1, out2);
   return (int)cudaGetLastError();
 }
 
