@@ -1143,6 +1143,343 @@ __global__ void __launch_bounds__(128, (BMAX <= 32) ? 4 : ((BMAX <= 40) ? 3 : 2)
 }
 
 // ---------------------------------------------------------------------------
+// Local solves, forward phase: banded Cholesky factorisation of K_l - lambda_i
+// M_l with the forward substitution L y = rho_l (FP32, window BMAX a multiple
+// of 8, at most 48).  One CTA of four warps per (subdomain l, four shifts), one
+// warp per shift.  The symmetric window (slot u = row mod BMAX) is spread over
+// the warp as a 4 x 8 grid of lanes: lane (rg, cg) holds the TR x TC tile of
+// slot rows rg TR .. and slot columns cg TC .. in registers (TR = 2 TC, so row
+// group rg covers column groups 2 rg and 2 rg + 1).  Per elimination step the
+// four lanes of the pivot column publish the raw column in shared memory
+// (column-group-major, each group padded to TCP floats for 16-byte vector
+// access); after one warp barrier every lane reads the TR + TC entries it
+// needs and applies its rank-one update; the entries of the pivot slot are
+// then replaced by the entering band row.  The band chunk of K_l and M_l
+// enters shared memory through two bulk copies per window group, shared by the
+// four warps; each warp turns it into the shifted rows K - lambda M laid out
+// by slot (padded like the published column), so that the entering entries of
+// a lane are one or two vector loads.  The right-hand side rows are spread
+// over the lanes (slot rg TR + a at lane rg 8 + a mod 8) and eliminated
+// alongside.  Outputs: the columns of L in slot order (1/L_jj at the pivot
+// slot) and y in place of the right-hand side.
+// ---------------------------------------------------------------------------
+template <int BMAX>
+struct TileShape {
+  static constexpr int TR = BMAX / 4, TC = BMAX / 8;
+  static constexpr int TCP = (TC + 3) / 4 * 4;  // padded column group
+  static constexpr int ROW = 8 * TCP;           // padded slot vector
+  static constexpr int BB = BMAX * BMAX;
+  static constexpr size_t smem_floats = (size_t)2 * BB + (size_t)kLocalWarps * (BMAX * ROW + 2 * ROW + BMAX);
+};
+
+template <int BMAX>
+__global__ void __launch_bounds__(128, (BMAX <= 32) ? 4 : 3) k_local_factor_tile(
+    int nsub, int k, const int64_t* __restrict__ sub_ptr, const int32_t* __restrict__ sub_dofs,
+    const float* __restrict__ bandK, const float* __restrict__ bandM, const double* __restrict__ lam,
+    const double* __restrict__ rho, float* __restrict__ Lbuf, float* __restrict__ wpk, int32_t* err) {
+  using S = TileShape<BMAX>;
+  constexpr int TR = S::TR, TC = S::TC, TCP = S::TCP, ROW = S::ROW, BB = S::BB;
+  static_assert(BMAX % 8 == 0 && BMAX <= 48, "window must be a multiple of 8, at most 48");
+  constexpr int NR = (TR + 7) / 8;  // right-hand-side registers per lane
+  constexpr unsigned FULL = 0xffffffffu;
+  extern __shared__ __align__(128) float tsm[];
+  float* sK = tsm;                                // [BB] band chunk of K_l
+  float* sM = sK + BB;                            // [BB] band chunk of M_l
+  float* wbase = sM + BB;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  float* Aw = wbase + (size_t)wib * (BMAX * ROW + 2 * ROW + BMAX);  // [BMAX][ROW] shifted rows by slot
+  float* slw = Aw + BMAX * ROW;                                      // [2][ROW] published columns
+  float* srw = slw + 2 * ROW;                                        // [BMAX] rhs of entering rows
+  __shared__ __align__(8) uint64_t bar;
+  const int rg = lane >> 3, cg = lane & 7;
+  const int groups_per_sub = (k + kLocalWarps - 1) / kLocalWarps;
+  const int l = blockIdx.x / groups_per_sub;
+  const int i = (blockIdx.x % groups_per_sub) * kLocalWarps + wib;
+  const bool active = (i < k);
+  const int ii = active ? i : 0;
+  const int64_t off = sub_ptr[l];
+  const int nl = (int)(sub_ptr[l + 1] - off);
+  const int32_t* dofs = sub_dofs + off;
+  const float lm = (float)lam[ii];
+  float* Lp = Lbuf + ((size_t)off * k + (size_t)ii * nl) * BMAX;
+  const float* gK = bandK + (size_t)off * BMAX;  // band row p at gK + p * BMAX, diagonal at BMAX - 1
+  const float* gM = bandM + (size_t)off * BMAX;
+  const int ngroups = (nl + BMAX - 1) / BMAX;
+  auto pidx = [](int u) { return (u / TC) * TCP + u % TC; };  // padded position of slot u
+  // chunk c = band rows [BMAX (c + 1), BMAX (c + 2)) ∩ [0, nl): the rows entering during group c
+  auto issue_chunk = [&](int c) {
+    const int r0 = BMAX * (c + 1);
+    if (r0 >= nl) return;
+    const int rows = min(BMAX, nl - r0);
+    const uint32_t bytes = (uint32_t)rows * BMAX * sizeof(float);
+    mbar_expect_tx(&bar, 2 * bytes);
+    bulk_load(sK, gK + (size_t)r0 * BMAX, bytes, &bar);
+    bulk_load(sM, gM + (size_t)r0 * BMAX, bytes, &bar);
+  };
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) issue_chunk(0);
+  // initial window rows 0..BMAX-1 straight from global memory
+  auto a0 = [&](int p, int q) -> float {  // q <= p < BMAX
+    if (p >= nl) return (p == q) ? 1.f : 0.f;
+    const int e = BMAX - 1 - (p - q);
+    return gK[(size_t)p * BMAX + e] - lm * gM[(size_t)p * BMAX + e];
+  };
+  auto rhs = [&](int p) -> float { return (p < nl) ? (float)rho[(int64_t)dofs[p] * k + ii] : 0.f; };
+  float w[TR][TC];
+#pragma unroll
+  for (int a = 0; a < TR; ++a)
+#pragma unroll
+    for (int b = 0; b < TC; ++b) {
+      const int u = rg * TR + a, v = cg * TC + b;
+      w[a][b] = (u >= v) ? a0(u, v) : a0(v, u);
+    }
+  // right-hand side rows held by this lane: slot rg TR + cg + 8 q
+  float r[NR];
+  int ridx[NR];
+#pragma unroll
+  for (int q = 0; q < NR; ++q) {
+    const int a = cg + 8 * q;
+    r[q] = (a < TR) ? rhs(rg * TR + a) : 0.f;
+    ridx[q] = (a < TR) ? pidx(rg * TR + a) : 0;
+  }
+  // published-column positions of the slots this lane stores to L
+  const int lidx0 = (lane < BMAX) ? pidx(lane) : 0;
+  const int lidx1 = (lane + 32 < BMAX) ? pidx(lane + 32) : 0;
+  // right-hand sides of the rows entering in group g + 1 (one group ahead)
+  float rn[2];
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    const int v = lane + 32 * c;
+    rn[c] = (v < BMAX) ? rhs(BMAX + v) : 0.f;
+  }
+  bool bad = false, timeout = false;
+  float* yout = wpk + off * k + ii;  // y_j at yout[j k]
+  for (int g = 0; g < ngroups; ++g) {
+    const int j0 = g * BMAX;
+    const bool have_chunk = BMAX * (g + 1) < nl;
+    __syncwarp();  // the previous group's reads of the shifted rows and staged rhs are done
+    if (have_chunk && !timeout && !mbar_wait_bounded(&bar, (uint32_t)(g & 1))) timeout = true;
+    // shifted rows by slot: Aw[s][pidx(v)] = (K - lambda M)(row B(g+1)+s, column of slot v),
+    // the band position of that entry being (v - s - 1) mod BMAX (identity beyond nl)
+    {
+      const int r0 = BMAX * (g + 1);
+      for (int e = lane; e < BMAX * 8; e += 32) {
+        const int s = e >> 3, c = e & 7;  // row s, column group c
+        const bool real = (r0 + s < nl) && !timeout;
+        float o[TCP];
+#pragma unroll
+        for (int b = 0; b < TCP; ++b) {
+          int t = c * TC + b + (BMAX - 1 - s);
+          t -= (t >= BMAX) ? BMAX : 0;
+          float x = 0.f;
+          if (b < TC) {
+            if (real)
+              x = fmaf(-lm, sM[s * BMAX + t], sK[s * BMAX + t]);
+            else
+              x = (t == BMAX - 1) ? 1.f : 0.f;
+          }
+          o[b] = x;
+        }
+#pragma unroll
+        for (int b4 = 0; b4 < TCP; b4 += 4)
+          *reinterpret_cast<float4*>(Aw + s * ROW + c * TCP + b4) = make_float4(o[b4], o[b4 + 1], o[b4 + 2], o[b4 + 3]);
+      }
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const int v = lane + 32 * c;
+        if (v < BMAX) srw[v] = rn[c];
+        rn[c] = (v < BMAX) ? rhs(BMAX * (g + 2) + v) : 0.f;
+      }
+    }
+    __syncthreads();  // every warp has its shifted rows: the K/M buffer may be refilled
+    if (threadIdx.x == 0 && !timeout) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue_chunk(g + 1);
+    }
+    int zero;
+    asm volatile("mov.u32 %0, 0;" : "=r"(zero));
+    const int rgz = rg + zero, cgz = cg + zero;
+    float* Lg = Lp + (size_t)j0 * BMAX;
+    float* yg = yout + (size_t)j0 * k;
+#pragma unroll
+    for (int s = 0; s < BMAX; ++s) {
+      const int j = j0 + s;
+      if (j >= nl) break;
+      const int orr = s / TR, oc = s / TC;  // row and column group of slot s
+      const float piv = __shfl_sync(FULL, w[s % TR][s % TC], orr * 8 + oc);
+      const float rj = __shfl_sync(FULL, r[(s % TR) / 8], orr * 8 + (s % TR) % 8);
+      bad |= !(piv > 0.f);
+      const float inv = rsqrtf(piv);
+      const float inv2 = inv * inv;
+      const float yj = rj * inv;
+      float* slb = slw + (s & 1) * ROW;
+      if (cgz == oc) {  // publish the raw pivot column: this lane's TR slots = column groups 2 rg, 2 rg + 1
+#pragma unroll
+        for (int hf = 0; hf < 2; ++hf)
+#pragma unroll
+          for (int b4 = 0; b4 < TCP; b4 += 4) {
+            float4 o;
+            o.x = (b4 + 0 < TC) ? w[hf * TC + b4 + 0][s % TC] : 0.f;
+            o.y = (b4 + 1 < TC) ? w[hf * TC + b4 + 1][s % TC] : 0.f;
+            o.z = (b4 + 2 < TC) ? w[hf * TC + b4 + 2][s % TC] : 0.f;
+            o.w = (b4 + 3 < TC) ? w[hf * TC + b4 + 3][s % TC] : 0.f;
+            *reinterpret_cast<float4*>(slb + (2 * rgz + hf) * TCP + b4) = o;
+          }
+      }
+      __syncwarp();
+      if (active) {
+        if (lane < BMAX) Lg[s * BMAX + lane] = (lane == s) ? inv : slb[lidx0] * inv;
+        if (lane + 32 < BMAX) Lg[s * BMAX + lane + 32] = (lane + 32 == s) ? inv : slb[lidx1] * inv;
+        if (lane == 0) yg[(size_t)s * k] = yj;
+      }
+      float lr[TR], lc[TCP];
+#pragma unroll
+      for (int hf = 0; hf < 2; ++hf)
+#pragma unroll
+        for (int b4 = 0; b4 < TCP; b4 += 4) {
+          const float4 q = *reinterpret_cast<const float4*>(slb + (2 * rgz + hf) * TCP + b4);
+          if (b4 + 0 < TC) lr[hf * TC + b4 + 0] = q.x;
+          if (b4 + 1 < TC) lr[hf * TC + b4 + 1] = q.y;
+          if (b4 + 2 < TC) lr[hf * TC + b4 + 2] = q.z;
+          if (b4 + 3 < TC) lr[hf * TC + b4 + 3] = q.w;
+        }
+#pragma unroll
+      for (int b4 = 0; b4 < TCP; b4 += 4) {
+        const float4 q = *reinterpret_cast<const float4*>(slb + cgz * TCP + b4);
+        lc[b4 + 0] = q.x * inv2;
+        lc[b4 + 1] = q.y * inv2;
+        lc[b4 + 2] = q.z * inv2;
+        lc[b4 + 3] = q.w * inv2;
+      }
+#pragma unroll
+      for (int a = 0; a < TR; ++a)
+#pragma unroll
+        for (int b = 0; b < TC; ++b) w[a][b] = fmaf(-lr[a], lc[b], w[a][b]);
+      const float yi = yj * inv;  // the raw column times y_j / sqrt(pivot)
+#pragma unroll
+      for (int q = 0; q < NR; ++q)
+        if (cgz + 8 * q < TR) r[q] = fmaf(-slb[ridx[q]], yi, r[q]);
+      // band row j + BMAX enters slot s
+      const float* arow = Aw + s * ROW;
+      if (rgz == orr) {
+#pragma unroll
+        for (int b4 = 0; b4 < TCP; b4 += 4) {
+          const float4 q = *reinterpret_cast<const float4*>(arow + cgz * TCP + b4);
+          if (b4 + 0 < TC) w[s % TR][b4 + 0] = q.x;
+          if (b4 + 1 < TC) w[s % TR][b4 + 1] = q.y;
+          if (b4 + 2 < TC) w[s % TR][b4 + 2] = q.z;
+          if (b4 + 3 < TC) w[s % TR][b4 + 3] = q.w;
+        }
+      }
+      if (cgz == oc) {
+#pragma unroll
+        for (int hf = 0; hf < 2; ++hf)
+#pragma unroll
+          for (int b4 = 0; b4 < TCP; b4 += 4) {
+            const float4 q = *reinterpret_cast<const float4*>(arow + (2 * rgz + hf) * TCP + b4);
+            if (b4 + 0 < TC) w[hf * TC + b4 + 0][s % TC] = q.x;
+            if (b4 + 1 < TC) w[hf * TC + b4 + 1][s % TC] = q.y;
+            if (b4 + 2 < TC) w[hf * TC + b4 + 2][s % TC] = q.z;
+            if (b4 + 3 < TC) w[hf * TC + b4 + 3][s % TC] = q.w;
+          }
+      }
+      if (lane == orr * 8 + (s % TR) % 8) r[(s % TR) / 8] = srw[s];
+    }
+  }
+  if ((bad || timeout) && lane == 0 && active) atomicOr(err, timeout ? 2 : 1);
+}
+
+// ---------------------------------------------------------------------------
+// Local solves, backward phase: L^T x = y for every (subdomain, shift), L in
+// slot order as written by the factorisation.  A warp serves four shifts of
+// one subdomain, eight lanes each; lane e of a group owns the window slots
+// e + 8 c and keeps x of their rows in registers, so a row costs one
+// eight-lane reduction.  Rows are processed in window groups unrolled by BMAX
+// (static slot), the L entries and y of the next PB rows are prefetched.
+// ---------------------------------------------------------------------------
+template <int BMAX>
+__global__ void __launch_bounds__(128) k_local_backward(int nsub, int k, const int64_t* __restrict__ sub_ptr,
+                                                        const float* __restrict__ Lbuf, float* __restrict__ wpk) {
+  constexpr int TC = BMAX / 8;
+  constexpr int PB = 4;
+  const int lane = threadIdx.x & 31, e = lane & 7, grp = lane >> 3;
+  const int wglob = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int wps = (k + 3) / 4;  // warps per subdomain
+  const int l = wglob / wps;
+  if (l >= nsub) return;
+  const int i = (wglob % wps) * 4 + grp;
+  const bool active = i < k;
+  const int ii = active ? i : 0;
+  const int64_t off = sub_ptr[l];
+  const int nl = (int)(sub_ptr[l + 1] - off);
+  const float* Lp = Lbuf + ((size_t)off * k + (size_t)ii * nl) * BMAX;
+  float* yp = wpk + off * k + ii;
+  static_assert(BMAX % PB == 0, "the ring slot must be static");
+  float xw[TC];
+#pragma unroll
+  for (int c = 0; c < TC; ++c) xw[c] = 0.f;
+  // prefetch ring: row j lives in slot j mod PB (PB divides BMAX, so the slot is
+  // static inside the unrolled window group)
+  float lring[PB][TC], yring[PB];
+  auto load = [&](int jr, float* lv, float& y) {
+    if (jr >= 0) {
+#pragma unroll
+      for (int c = 0; c < TC; ++c) lv[c] = Lp[(size_t)jr * BMAX + e + 8 * c];
+      y = yp[(size_t)jr * k];
+    } else {
+#pragma unroll
+      for (int c = 0; c < TC; ++c) lv[c] = 0.f;
+      y = 0.f;
+    }
+  };
+#pragma unroll
+  for (int d = 0; d < PB; ++d) {
+    const int jr = nl - 1 - d;
+    float nv[TC], ny;
+    load(jr, nv, ny);
+    const int slot = (jr % PB + PB) % PB;
+#pragma unroll
+    for (int dd = 0; dd < PB; ++dd)
+      if (dd == slot) {
+#pragma unroll
+        for (int c = 0; c < TC; ++c) lring[dd][c] = nv[c];
+        yring[dd] = ny;
+      }
+  }
+  const int gtop = (nl - 1) / BMAX;
+  for (int g = gtop; g >= 0; --g) {
+#pragma unroll
+    for (int s = BMAX - 1; s >= 0; --s) {
+      const int j = g * BMAX + s;
+      if (j < nl) {
+        const int d = s % PB;
+        const float y = yring[d];
+        float part = 0.f, dg = 0.f;
+#pragma unroll
+        for (int c = 0; c < TC; ++c) {
+          if (e + 8 * c == s)
+            dg = lring[d][c];
+          else
+            part = fmaf(lring[d][c], xw[c], part);
+        }
+        load(j - PB, lring[d], yring[d]);  // row j - PB has slot (j - PB) mod PB = d
+        part += __shfl_xor_sync(0xffffffffu, part, 1);
+        part += __shfl_xor_sync(0xffffffffu, part, 2);
+        part += __shfl_xor_sync(0xffffffffu, part, 4);
+        dg = __shfl_sync(0xffffffffu, dg, (lane & ~7) | (s & 7));
+        const float xj = (y - part) * dg;
+        if (e == (s & 7)) xw[s >> 3] = xj;
+        if (e == 0 && active) yp[(size_t)j * k] = xj;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Local solves for wide bands (window up to 128, e.g. 3-D subdomains): one CTA
 // per (subdomain, shift) with one thread per window column (thread v owns
 // column v, slot u = row mod BMAX, as in k_local_band_reg).  Per elimination
@@ -2807,22 +3144,29 @@ int launch_precond(Handle& h, const double* rho, const double* lam, double* Z) {
   // local band solves
   {
     ProfScope ps(h, BPJD_PROF_LOCAL);
-    h.launches += 1;
     const bool f32 = (h.precision == BPJD_MIXED);
+    h.launches += (f32 && h.Bpad > 0 && h.Bpad <= 48) ? 2 : 1;  // factorisation + backward substitution
     if (f32 && h.Bpad > 0) {
       const int blocks = h.nsub * ((k + kLocalWarps - 1) / kLocalWarps);
-#define BPJD_LOCAL_REG(BM)                                                                                   \
-  case BM:                                                                                                   \
-    k_local_band_tma<BM><<<blocks, 32 * kLocalWarps, 0, h.stream>>>(h.nsub, k, h.sub_ptr, h.sub_dofs,        \
-                                                                    h.bandKf, h.bandMf, lam, rho,            \
-                                                                    (float*)h.Lbuf, (float*)h.wpk, h.derr); \
-    break;
+#define BPJD_LOCAL_TILE(BM)                                                                                    \
+  case BM: {                                                                                                   \
+    const size_t sm = sizeof(float) * TileShape<BM>::smem_floats;                                              \
+    cudaFuncSetAttribute(k_local_factor_tile<BM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);      \
+    k_local_factor_tile<BM><<<blocks, 32 * kLocalWarps, sm, h.stream>>>(h.nsub, k, h.sub_ptr, h.sub_dofs,      \
+                                                                        h.bandKf, h.bandMf, lam, rho,          \
+                                                                        (float*)h.Lbuf, (float*)h.wpk,         \
+                                                                        h.derr);                               \
+    k_local_backward<BM><<<bwd_blocks, 128, 0, h.stream>>>(h.nsub, k, h.sub_ptr, (const float*)h.Lbuf,         \
+                                                           (float*)h.wpk);                                     \
+    break;                                                                                                     \
+  }
+      const int bwd_blocks = (h.nsub * ((k + 3) / 4) + 3) / 4;
       switch (h.Bpad) {
-        BPJD_LOCAL_REG(16)
-        BPJD_LOCAL_REG(24)
-        BPJD_LOCAL_REG(32)
-        BPJD_LOCAL_REG(40)
-        BPJD_LOCAL_REG(48)
+        BPJD_LOCAL_TILE(16)
+        BPJD_LOCAL_TILE(24)
+        BPJD_LOCAL_TILE(32)
+        BPJD_LOCAL_TILE(40)
+        BPJD_LOCAL_TILE(48)
         case 64:
           k_local_band_reg<64><<<(npairs + 3) / 4, 128, 0, h.stream>>>(npairs, k, h.sub_ptr, h.sub_dofs, 64,
                                                                       h.bandKf, h.bandMf, lam, rho,
@@ -2840,7 +3184,7 @@ int launch_precond(Handle& h, const double* rho, const double* lam, double* Z) {
         default:
           return (int)cudaErrorInvalidValue;
       }
-#undef BPJD_LOCAL_REG
+#undef BPJD_LOCAL_TILE
     } else {
       const size_t esz = f32 ? sizeof(float) : sizeof(double);
       const size_t per_warp = (size_t)(B * B + 3 * B) * esz;
