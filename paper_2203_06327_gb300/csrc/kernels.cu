@@ -1395,88 +1395,128 @@ __global__ void __launch_bounds__(128, (BMAX <= 32) ? 4 : 3) k_local_factor_tile
 
 // ---------------------------------------------------------------------------
 // Local solves, backward phase: L^T x = y for every (subdomain, shift), L in
-// slot order as written by the factorisation.  A warp serves four shifts of
-// one subdomain, eight lanes each; lane e of a group owns the window slots
-// e + 8 c and keeps x of their rows in registers, so a row costs one
-// eight-lane reduction.  Rows are processed in window groups unrolled by BMAX
-// (static slot), the L entries and y of the next PB rows are prefetched.
+// slot order as written by the factorisation (row j of the record holds
+// L(row(v), j) at slot v and 1/L_jj at slot j mod BMAX).  A warp serves four
+// shifts of one subdomain, eight lanes each; lane e of a group owns the window
+// slots e + 8 c and keeps x of their rows in registers, so a row costs one
+// eight-lane reduction.  The records enter shared memory half a window group
+// (R = BMAX / 2 rows) at a time through one bulk copy per shift, double
+// buffered (the upper half of a group always in buffer 1, the lower in buffer
+// 0, so slots and buffers are static in the unrolled loop); y of the next
+// chunk is loaded into registers one chunk ahead.
 // ---------------------------------------------------------------------------
 template <int BMAX>
-__global__ void __launch_bounds__(128) k_local_backward(int nsub, int k, const int64_t* __restrict__ sub_ptr,
-                                                        const float* __restrict__ Lbuf, float* __restrict__ wpk) {
-  constexpr int TC = BMAX / 8;
-  constexpr int PB = 4;
-  const int lane = threadIdx.x & 31, e = lane & 7, grp = lane >> 3;
-  const int wglob = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+struct BwdShape {
+  static constexpr int R = BMAX / 2;
+  static constexpr int PS = R * BMAX + 8;  // per-shift buffer stride: shifts land on different banks
+  static constexpr int WPB = 2;            // warps per block
+  static constexpr size_t smem_floats = (size_t)WPB * 2 * 4 * PS;
+};
+
+template <int BMAX>
+__global__ void __launch_bounds__(64) k_local_backward(int nsub, int k, const int64_t* __restrict__ sub_ptr,
+                                                       const float* __restrict__ Lbuf, float* __restrict__ wpk,
+                                                       int32_t* err) {
+  using S = BwdShape<BMAX>;
+  constexpr int TC = BMAX / 8, R = S::R, PS = S::PS, WPB = S::WPB;
+  constexpr int NY = (R + 7) / 8;
+  constexpr unsigned FULL = 0xffffffffu;
+  static_assert(BMAX % 8 == 0, "window must be a multiple of 8");
+  extern __shared__ __align__(128) float bsm[];
+  __shared__ __align__(8) uint64_t bars[WPB][2];
+  const int lane = threadIdx.x & 31, e = lane & 7, p = lane >> 3, wib = threadIdx.x >> 5;
+  const int wglob = blockIdx.x * WPB + wib;
   const int wps = (k + 3) / 4;  // warps per subdomain
   const int l = wglob / wps;
-  if (l >= nsub) return;
-  const int i = (wglob % wps) * 4 + grp;
-  const bool active = i < k;
-  const int ii = active ? i : 0;
+  if (l >= nsub) return;  // whole warps only; no block-wide barrier follows
+  const int i0 = (wglob % wps) * 4;
+  const int nact = min(4, k - i0);  // shifts served by this warp
+  const bool active = p < nact;
+  const int ii = active ? i0 + p : i0;
   const int64_t off = sub_ptr[l];
   const int nl = (int)(sub_ptr[l + 1] - off);
-  const float* Lp = Lbuf + ((size_t)off * k + (size_t)ii * nl) * BMAX;
+  float* buf = bsm + (size_t)wib * 2 * 4 * PS;  // [2][4][PS]
+  uint64_t* bar = bars[wib];
+  const float* Lsub = Lbuf + (size_t)off * k * BMAX;  // record of shift i at Lsub + i nl BMAX
   float* yp = wpk + off * k + ii;
-  static_assert(BMAX % PB == 0, "the ring slot must be static");
+  if (lane == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  const int chtop = (nl - 1) / R;
+  // chunk ch = rows [ch R, min(nl, ch R + R)) of each served shift, into buffer ch & 1
+  auto issue = [&](int ch) {
+    if (ch < 0) return;
+    const int r0 = ch * R;
+    const int rows = min(R, nl - r0);
+    const uint32_t bytes = (uint32_t)rows * BMAX * sizeof(float);
+    uint64_t* b = &bar[ch & 1];
+    mbar_expect_tx(b, bytes * nact);
+    for (int q = 0; q < nact; ++q)
+      bulk_load(buf + ((ch & 1) * 4 + q) * PS, Lsub + ((size_t)(i0 + q) * nl + r0) * BMAX, bytes, b);
+  };
+  auto load_y = [&](int ch, float* y) {
+#pragma unroll
+    for (int q = 0; q < NY; ++q) {
+      const int r = e + 8 * q;
+      const int j = ch * R + r;
+      y[q] = (ch >= 0 && r < R && j < nl) ? yp[(size_t)j * k] : 0.f;
+    }
+  };
+  if (lane == 0) issue(chtop);
+  float ycur[NY], ynext[NY];
+  load_y(chtop, ynext);
   float xw[TC];
 #pragma unroll
   for (int c = 0; c < TC; ++c) xw[c] = 0.f;
-  // prefetch ring: row j lives in slot j mod PB (PB divides BMAX, so the slot is
-  // static inside the unrolled window group)
-  float lring[PB][TC], yring[PB];
-  auto load = [&](int jr, float* lv, float& y) {
-    if (jr >= 0) {
+  uint32_t ph[2] = {0u, 0u};
+  bool timeout = false;
+  for (int g = chtop / 2; g >= 0; --g) {
 #pragma unroll
-      for (int c = 0; c < TC; ++c) lv[c] = Lp[(size_t)jr * BMAX + e + 8 * c];
-      y = yp[(size_t)jr * k];
-    } else {
-#pragma unroll
-      for (int c = 0; c < TC; ++c) lv[c] = 0.f;
-      y = 0.f;
-    }
-  };
-#pragma unroll
-  for (int d = 0; d < PB; ++d) {
-    const int jr = nl - 1 - d;
-    float nv[TC], ny;
-    load(jr, nv, ny);
-    const int slot = (jr % PB + PB) % PB;
-#pragma unroll
-    for (int dd = 0; dd < PB; ++dd)
-      if (dd == slot) {
-#pragma unroll
-        for (int c = 0; c < TC; ++c) lring[dd][c] = nv[c];
-        yring[dd] = ny;
+    for (int half = 1; half >= 0; --half) {
+      const int ch = 2 * g + half;
+      if (ch > chtop) continue;
+      __syncwarp();  // the buffer of chunk ch - 1 (chunk ch + 1's) is no longer read
+      if (lane == 0 && !timeout) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        issue(ch - 1);
       }
-  }
-  const int gtop = (nl - 1) / BMAX;
-  for (int g = gtop; g >= 0; --g) {
 #pragma unroll
-    for (int s = BMAX - 1; s >= 0; --s) {
-      const int j = g * BMAX + s;
-      if (j < nl) {
-        const int d = s % PB;
-        const float y = yring[d];
-        float part = 0.f, dg = 0.f;
+      for (int q = 0; q < NY; ++q) ycur[q] = ynext[q];
+      load_y(ch - 1, ynext);
+      if (!timeout && !mbar_wait_bounded(&bar[half], ph[half])) timeout = true;
+      ph[half] ^= 1u;
+      const float* Lb = buf + (half * 4 + p) * PS;
 #pragma unroll
-        for (int c = 0; c < TC; ++c) {
-          if (e + 8 * c == s)
-            dg = lring[d][c];
-          else
-            part = fmaf(lring[d][c], xw[c], part);
+      for (int r = R - 1; r >= 0; --r) {
+        const int j = ch * R + r;
+        const int s = half * R + r;  // j mod BMAX
+        if (j < nl) {
+          const float* row = Lb + r * BMAX;
+          float part = 0.f, dg = 0.f;
+#pragma unroll
+          for (int c = 0; c < TC; ++c) {
+            const float lv = row[e + 8 * c];
+            if (c == s / 8 && e == s % 8)
+              dg = lv;
+            else
+              part = fmaf(lv, xw[c], part);
+          }
+          part += __shfl_xor_sync(FULL, part, 1);
+          part += __shfl_xor_sync(FULL, part, 2);
+          part += __shfl_xor_sync(FULL, part, 4);
+          dg = __shfl_sync(FULL, dg, (lane & ~7) | (s % 8));
+          const float y = __shfl_sync(FULL, ycur[r / 8], (lane & ~7) | (r % 8));
+          const float xj = (y - part) * dg;
+          if (e == s % 8) xw[s / 8] = xj;
+          if (e == 0 && active && !timeout) yp[(size_t)j * k] = xj;
         }
-        load(j - PB, lring[d], yring[d]);  // row j - PB has slot (j - PB) mod PB = d
-        part += __shfl_xor_sync(0xffffffffu, part, 1);
-        part += __shfl_xor_sync(0xffffffffu, part, 2);
-        part += __shfl_xor_sync(0xffffffffu, part, 4);
-        dg = __shfl_sync(0xffffffffu, dg, (lane & ~7) | (s & 7));
-        const float xj = (y - part) * dg;
-        if (e == (s & 7)) xw[s >> 3] = xj;
-        if (e == 0 && active) yp[(size_t)j * k] = xj;
       }
     }
   }
+  if (timeout && lane == 0) atomicOr(err, 2);
 }
 
 // ---------------------------------------------------------------------------
@@ -3156,11 +3196,15 @@ int launch_precond(Handle& h, const double* rho, const double* lam, double* Z) {
                                                                         h.bandKf, h.bandMf, lam, rho,          \
                                                                         (float*)h.Lbuf, (float*)h.wpk,         \
                                                                         h.derr);                               \
-    k_local_backward<BM><<<bwd_blocks, 128, 0, h.stream>>>(h.nsub, k, h.sub_ptr, (const float*)h.Lbuf,         \
-                                                           (float*)h.wpk);                                     \
+    {                                                                                                          \
+      const size_t bsm = sizeof(float) * BwdShape<BM>::smem_floats;                                            \
+      cudaFuncSetAttribute(k_local_backward<BM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm);       \
+      k_local_backward<BM><<<bwd_blocks, 32 * BwdShape<BM>::WPB, bsm, h.stream>>>(                             \
+          h.nsub, k, h.sub_ptr, (const float*)h.Lbuf, (float*)h.wpk, h.derr);                                  \
+    }                                                                                                          \
     break;                                                                                                     \
   }
-      const int bwd_blocks = (h.nsub * ((k + 3) / 4) + 3) / 4;
+      const int bwd_blocks = (h.nsub * ((k + 3) / 4) + 1) / 2;
       switch (h.Bpad) {
         BPJD_LOCAL_TILE(16)
         BPJD_LOCAL_TILE(24)
