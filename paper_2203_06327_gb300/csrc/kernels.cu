@@ -1394,6 +1394,300 @@ __global__ void __launch_bounds__(128, (BMAX <= 32) ? 4 : 3) k_local_factor_tile
 }
 
 // ---------------------------------------------------------------------------
+// Local solves, forward phase, blocked: banded Cholesky factorisation of
+// K_l - lambda_i M_l eight columns at a time, with the forward substitution
+// L y = rho_l (FP32, window BMAX a multiple of 8, at most 48).  One CTA of four
+// warps per (subdomain l, four shifts), one warp per shift.
+//
+// A block of eight columns j0..j0+7 couples to the rows j0..j0+BMAX+6, so the
+// window holds W = BMAX + 8 rows in W/8 slot blocks used cyclically.  The
+// window (stored negated, both triangles as far as they are read) lives in
+// the accumulators of m16n8k8 tensor-core tiles: lane (g, q) = (lane / 4,
+// lane mod 4) of tile (rt, ct) holds slot rows rt 16 + g (+8) and slot columns
+// ct 8 + 2 q (+1).  Per block step:
+//   1. the pivot column block (tile column sb) goes to shared memory;
+//   2. each lane takes one or two window rows of it and the warp factorises
+//      the 8-column panel column by column (pivot and L entries by shuffle),
+//      eliminating the right-hand side alongside and storing the columns of
+//      L in slot order (1/L_jj at the pivot slot);
+//   3. the panel L (W x 8) returns to shared memory and the trailing update
+//      W <- W - L L^T runs as tensor-core products of every tile, each
+//      operand split into a TF32 head and a TF32 tail (head x head + head x
+//      tail + tail x head: FP32-level accuracy);
+//   4. the eight band rows entering the freed slot block are written into the
+//      row tiles (the lower triangle is all that step 1 ever reads).
+// The band rows of K_l and M_l enter shared memory one window cycle (W rows)
+// ahead through bulk copies shared by the four warps.
+// ---------------------------------------------------------------------------
+template <int BMAX>
+struct MmaShape {
+  static constexpr int W = BMAX + 8;        // window rows
+  static constexpr int NBW = W / 8;         // slot blocks
+  static constexpr int RT = (W + 15) / 16;  // row tiles of 16
+  static constexpr int CT = NBW;            // column tiles of 8
+  static constexpr int NH = (W + 31) / 32;  // window rows per lane in the panel
+  static constexpr int PSTR = 12;           // row stride of the panel buffer (bank-conflict free)
+  static constexpr int PW = RT * 16 * PSTR + W;
+  static constexpr size_t smem_floats = (size_t)4 * W * BMAX + (size_t)kLocalWarps * PW;
+};
+
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void mma_tf32(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+template <int BMAX>
+__global__ void __launch_bounds__(128, (BMAX <= 40) ? 3 : 2) k_local_factor_mma(
+    int nsub, int k, const int64_t* __restrict__ sub_ptr, const int32_t* __restrict__ sub_dofs,
+    const float* __restrict__ bandK, const float* __restrict__ bandM, const double* __restrict__ lam,
+    const double* __restrict__ rho, float* __restrict__ Lbuf, float* __restrict__ wpk, int32_t* err) {
+  using S = MmaShape<BMAX>;
+  constexpr int W = S::W, NBW = S::NBW, RT = S::RT, CT = S::CT, NH = S::NH, PSTR = S::PSTR;
+  constexpr int WB = W * BMAX;
+  constexpr unsigned FULL = 0xffffffffu;
+  static_assert(BMAX % 8 == 0 && BMAX <= 48, "window must be a multiple of 8, at most 48");
+  extern __shared__ __align__(128) float tsm[];
+  __shared__ __align__(8) uint64_t bars[2];
+  const int lane_id = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int lane_g = lane_id >> 2, lane_q = lane_id & 3;
+  const int groups_per_sub = (k + kLocalWarps - 1) / kLocalWarps;
+  const int l = blockIdx.x / groups_per_sub;
+  const int i = (blockIdx.x % groups_per_sub) * kLocalWarps + wib;
+  const bool active = (i < k);
+  const int ii = active ? i : 0;
+  const int64_t off = sub_ptr[l];
+  const int nl = (int)(sub_ptr[l + 1] - off);
+  const int32_t* dofs = sub_dofs + off;
+  const float lm = (float)lam[ii];
+  float* Lrec = Lbuf + ((size_t)off * k + (size_t)ii * nl) * BMAX;  // record of column j at Lrec + j BMAX
+  float* yout = wpk + off * k + ii;                                // y_j at yout[j k]
+  const float* gK = bandK + (size_t)off * BMAX;  // band row p at gK + p * BMAX, diagonal at BMAX - 1
+  const float* gM = bandM + (size_t)off * BMAX;
+  float* pbuf = tsm + 4 * WB + wib * S::PW;  // [RT 16][PSTR] panel / tensor-core operand
+  float* srw = pbuf + RT * 16 * PSTR;        // [W] right-hand sides of the entering rows
+  // chunk c = band rows [W (c + 1), W (c + 2)) ∩ [0, nl), into buffer c & 1
+  auto issue_chunk = [&](int c) {
+    const int r0 = W * (c + 1);
+    if (r0 >= nl) return;
+    const int rows = min(W, nl - r0);
+    const uint32_t bytes = (uint32_t)rows * BMAX * sizeof(float);
+    uint64_t* b = &bars[c & 1];
+    mbar_expect_tx(b, 2 * bytes);
+    bulk_load(tsm + (c & 1) * WB, gK + (size_t)r0 * BMAX, bytes, b);
+    bulk_load(tsm + 2 * WB + (c & 1) * WB, gM + (size_t)r0 * BMAX, bytes, b);
+  };
+  if (threadIdx.x == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  for (int e = lane_id; e < RT * 16 * PSTR; e += 32) pbuf[e] = 0.f;
+  __syncthreads();
+  if (threadIdx.x == 0) issue_chunk(0);
+  // initial window: rows 0..W-1, negated, both triangles
+  auto a0 = [&](int p, int qq) -> float {  // entry (p, qq) of the shifted matrix, qq <= p < W
+    if (p >= nl) return (p == qq) ? 1.f : 0.f;
+    const int d = p - qq;
+    if (d > BMAX - 1) return 0.f;
+    const int e = BMAX - 1 - d;
+    return gK[(size_t)p * BMAX + e] - lm * gM[(size_t)p * BMAX + e];
+  };
+  auto rhs = [&](int p) -> float { return (p < nl) ? (float)rho[(int64_t)dofs[p] * k + ii] : 0.f; };
+  float acc[RT][CT][4];
+#pragma unroll
+  for (int rt = 0; rt < RT; ++rt)
+#pragma unroll
+    for (int ct = 0; ct < CT; ++ct)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int u = rt * 16 + lane_g + 8 * (e >> 1), v = ct * 8 + 2 * lane_q + (e & 1);
+        acc[rt][ct][e] = (u < W) ? -((u >= v) ? a0(u, v) : a0(v, u)) : 0.f;
+      }
+  float r[NH], rn[NH];
+#pragma unroll
+  for (int h = 0; h < NH; ++h) {
+    const int w = lane_id + 32 * h;
+    r[h] = (w < W) ? rhs(w) : 0.f;
+    rn[h] = (w < W) ? rhs(W + w) : 0.f;
+  }
+  bool bad = false, timeout = false;
+  int jm = 0;  // j0 mod BMAX
+  for (int c = 0; c * W < nl; ++c) {
+    __syncthreads();  // every warp is done with chunk c - 1: its buffer may be refilled
+    if (threadIdx.x == 0 && !timeout) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue_chunk(c + 1);
+    }
+#pragma unroll
+    for (int h = 0; h < NH; ++h) {
+      const int w = lane_id + 32 * h;
+      if (w < W) srw[w] = rn[h];
+      rn[h] = (w < W) ? rhs(W * (c + 2) + w) : 0.f;
+    }
+    const bool have_chunk = W * (c + 1) < nl;
+    if (have_chunk && !timeout && !mbar_wait_bounded(&bars[c & 1], (uint32_t)((c >> 1) & 1))) timeout = true;
+    const float* cK = tsm + (c & 1) * WB;
+    const float* cM = tsm + 2 * WB + (c & 1) * WB;
+    const int crow0 = W * (c + 1);  // band row of chunk row 0
+#pragma unroll
+    for (int sb = 0; sb < NBW; ++sb) {
+      const int j0 = c * W + 8 * sb;
+      if (j0 >= nl) break;
+      // an opaque zero keeps the lane-dependent offsets of this block step from
+      // being hoisted out of the cycle loop (NBW copies would occupy registers)
+      int zero;
+      asm volatile("mov.u32 %0, 0;" : "=r"(zero));
+      const int g = lane_g + zero, q = lane_q + zero, lane = lane_id + zero;
+      // 1. pivot column block -> pbuf[slot][0..7] (negated window values)
+      __syncwarp();
+#pragma unroll
+      for (int rt = 0; rt < RT; ++rt) {
+        *reinterpret_cast<float2*>(pbuf + (rt * 16 + g) * PSTR + 2 * q) = make_float2(acc[rt][sb][0], acc[rt][sb][1]);
+        *reinterpret_cast<float2*>(pbuf + (rt * 16 + g + 8) * PSTR + 2 * q) =
+            make_float2(acc[rt][sb][2], acc[rt][sb][3]);
+      }
+      __syncwarp();
+      float p[NH][8];
+      int dr[NH], pos[NH];
+#pragma unroll
+      for (int h = 0; h < NH; ++h) {
+        const int w = lane + 32 * h;
+        const float4 x0 = *reinterpret_cast<const float4*>(pbuf + (w < W ? w : 0) * PSTR);
+        const float4 x1 = *reinterpret_cast<const float4*>(pbuf + (w < W ? w : 0) * PSTR + 4);
+        const bool ok = w < W;
+        p[h][0] = ok ? x0.x : 0.f;
+        p[h][1] = ok ? x0.y : 0.f;
+        p[h][2] = ok ? x0.z : 0.f;
+        p[h][3] = ok ? x0.w : 0.f;
+        p[h][4] = ok ? x1.x : 0.f;
+        p[h][5] = ok ? x1.y : 0.f;
+        p[h][6] = ok ? x1.z : 0.f;
+        p[h][7] = ok ? x1.w : 0.f;
+        int d = w - 8 * sb;
+        d += (d < 0) ? W : 0;
+        dr[h] = ok ? d : W + 8;  // rows past the window never store
+        int ps = jm + d;
+        ps -= (ps >= BMAX) ? BMAX : 0;
+        ps -= (ps >= BMAX) ? BMAX : 0;
+        pos[h] = ps;  // record position of this row: row mod BMAX
+      }
+      __syncwarp();  // pbuf is rewritten with L below
+      // 2. panel factorisation, eight columns
+      float* rec = Lrec + (size_t)j0 * BMAX;
+#pragma unroll
+      for (int cc = 0; cc < 8; ++cc) {
+        const int ws = 8 * sb + cc;  // pivot slot
+        const int own = ws & 31, hs = ws >> 5;
+        const float piv = -__shfl_sync(FULL, p[hs][cc], own);
+        const float rj = __shfl_sync(FULL, r[hs], own);
+        bad |= !(piv > 0.f);
+        const float inv = rsqrtf(piv);
+        const float yj = rj * inv;
+        float lv[NH];
+#pragma unroll
+        for (int h = 0; h < NH; ++h) {
+          lv[h] = -p[h][cc] * inv;
+          r[h] = fmaf(-lv[h], yj, r[h]);
+        }
+#pragma unroll
+        for (int c2 = cc + 1; c2 < 8; ++c2) {
+          const int w2 = 8 * sb + c2;
+          const float l2 = __shfl_sync(FULL, lv[w2 >> 5], w2 & 31);
+#pragma unroll
+          for (int h = 0; h < NH; ++h) p[h][c2] = fmaf(lv[h], l2, p[h][c2]);
+        }
+        if (active && j0 + cc < nl) {
+#pragma unroll
+          for (int h = 0; h < NH; ++h) {
+            const int tt = dr[h] - cc;
+            if (tt >= 0 && tt < BMAX) rec[(size_t)cc * BMAX + pos[h]] = (tt == 0) ? inv : lv[h];
+          }
+          if (lane == 0) yout[(size_t)(j0 + cc) * k] = yj;
+        }
+#pragma unroll
+        for (int h = 0; h < NH; ++h) p[h][cc] = lv[h];
+      }
+      // 3. L (W x 8) -> pbuf, tensor-core update of every tile: acc += L L^T
+#pragma unroll
+      for (int h = 0; h < NH; ++h) {
+        const int w = lane + 32 * h;
+        if (w < W) {
+          *reinterpret_cast<float4*>(pbuf + w * PSTR) = make_float4(p[h][0], p[h][1], p[h][2], p[h][3]);
+          *reinterpret_cast<float4*>(pbuf + w * PSTR + 4) = make_float4(p[h][4], p[h][5], p[h][6], p[h][7]);
+        }
+      }
+      __syncwarp();
+      uint32_t ah[RT][4], al[RT][4];
+#pragma unroll
+      for (int rt = 0; rt < RT; ++rt) {
+        float x[4];
+        x[0] = pbuf[(rt * 16 + g) * PSTR + q];
+        x[1] = pbuf[(rt * 16 + g + 8) * PSTR + q];
+        x[2] = pbuf[(rt * 16 + g) * PSTR + q + 4];
+        x[3] = pbuf[(rt * 16 + g + 8) * PSTR + q + 4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          ah[rt][e] = to_tf32(x[e]);
+          al[rt][e] = to_tf32(x[e] - __uint_as_float(ah[rt][e]));
+        }
+      }
+#pragma unroll
+      for (int rt = 0; rt < RT; ++rt)
+#pragma unroll
+        for (int ct = 0; ct < CT; ++ct) {
+          const int bt = ct >> 1, bo = ct & 1;  // B operand = rows ct 8 .. of L: A fragment of tile bt
+          mma_tf32(acc[rt][ct], al[rt], ah[bt][bo], ah[bt][bo + 2]);
+          mma_tf32(acc[rt][ct], ah[rt], al[bt][bo], al[bt][bo + 2]);
+          mma_tf32(acc[rt][ct], ah[rt], ah[bt][bo], ah[bt][bo + 2]);
+        }
+      // 4. band rows crow0 + 8 sb + du enter slot block sb (row tile sb / 2, half sb % 2),
+      //    negated; this lane's row is du = g, its columns the slots ct 8 + 2 q + e2
+      const int rtn = sb >> 1, hn = sb & 1;
+      const int rowg = 8 * sb + g;
+      const bool realg = crow0 + rowg < nl && !timeout;
+      const float* kg = cK + rowg * BMAX;
+      const float* mg = cM + rowg * BMAX;
+#pragma unroll
+      for (int ct = 0; ct < CT; ++ct)
+#pragma unroll
+        for (int e2 = 0; e2 < 2; ++e2) {
+          float val;
+          if (ct != sb) {
+            // column slot v = ct 8 + 2 q + e2 holds row j0 + dv, dv = ((ct - sb) mod NBW) 8 + 2 q + e2;
+            // entry (crow0 + 8 sb + g, j0 + dv) sits at band position dv - g - 9
+            const int ps = ((ct - sb + NBW) % NBW) * 8 + e2 - 9 + 2 * q - g;
+            val = (realg && ps >= 0) ? fmaf(lm, mg[ps], -kg[ps]) : 0.f;
+          } else {
+            const int du2 = 2 * q + e2;
+            const int lo = (g >= du2) ? rowg : 8 * sb + du2;   // the later row of the pair
+            const int ps = BMAX - 1 - ((g >= du2) ? g - du2 : du2 - g);
+            const bool rl = crow0 + lo < nl && !timeout;
+            val = rl ? fmaf(lm, cM[lo * BMAX + ps], -cK[lo * BMAX + ps]) : ((g == du2) ? -1.f : 0.f);
+          }
+          acc[rtn][ct][2 * hn + e2] = val;
+        }
+#pragma unroll
+      for (int h = 0; h < NH; ++h) {
+        const int w = lane + 32 * h;
+        if (w < W && (w >> 3) == sb) r[h] = srw[w];
+      }
+      jm += 8;
+      jm -= (jm >= BMAX) ? BMAX : 0;
+    }
+  }
+  if ((bad || timeout) && lane_id == 0 && active) atomicOr(err, timeout ? 2 : 1);
+}
+
+// ---------------------------------------------------------------------------
 // Local solves, backward phase: L^T x = y for every (subdomain, shift), L in
 // slot order as written by the factorisation (row j of the record holds
 // L(row(v), j) at slot v and 1/L_jj at slot j mod BMAX).  A warp serves four
@@ -3190,12 +3484,12 @@ int launch_precond(Handle& h, const double* rho, const double* lam, double* Z) {
       const int blocks = h.nsub * ((k + kLocalWarps - 1) / kLocalWarps);
 #define BPJD_LOCAL_TILE(BM)                                                                                    \
   case BM: {                                                                                                   \
-    const size_t sm = sizeof(float) * TileShape<BM>::smem_floats;                                              \
-    cudaFuncSetAttribute(k_local_factor_tile<BM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);      \
-    k_local_factor_tile<BM><<<blocks, 32 * kLocalWarps, sm, h.stream>>>(h.nsub, k, h.sub_ptr, h.sub_dofs,      \
-                                                                        h.bandKf, h.bandMf, lam, rho,          \
-                                                                        (float*)h.Lbuf, (float*)h.wpk,         \
-                                                                        h.derr);                               \
+    const size_t sm = sizeof(float) * MmaShape<BM>::smem_floats;                                               \
+    cudaFuncSetAttribute(k_local_factor_mma<BM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);       \
+    k_local_factor_mma<BM><<<blocks, 32 * kLocalWarps, sm, h.stream>>>(h.nsub, k, h.sub_ptr, h.sub_dofs,       \
+                                                                       h.bandKf, h.bandMf, lam, rho,           \
+                                                                       (float*)h.Lbuf, (float*)h.wpk,          \
+                                                                       h.derr);                                \
     {                                                                                                          \
       const size_t bsm = sizeof(float) * BwdShape<BM>::smem_floats;                                            \
       cudaFuncSetAttribute(k_local_backward<BM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm);       \
