@@ -133,8 +133,8 @@ def schwarz_bytes(lay, k, esz, n, nnzP, nH):
 
 
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one local-solve application
-# (k_local_factor_mma + k_local_backward), keyed by workload, precision, band window
-LOCAL_TRAFFIC = {("c2_kappa_rect_p1_h512", "mixed", 40): 129.197824e6 + 557.361664e6 + 608.806912e6 + 15.802368e6}
+# (k_local_factor_mma<40> + k_local_backward<40>), keyed by workload and precision
+LOCAL_TRAFFIC = {("c2_kappa_rect_p1_h512", "mixed"): 129.197824e6 + 557.361664e6 + 608.806912e6 + 15.802368e6}
 
 
 def _peaks():
@@ -331,7 +331,7 @@ def run_ours(a):
         ach = bytes_per / (dom_ms / dom_cnt / 1e3) / 1e9
         # DRAM bytes (read + write) per application measured by ncu for this kernel
         # version on this workload (profiles/local_solves_c2.md); None elsewhere
-        traffic = LOCAL_TRAFFIC.get((spec.name, a.precision, lay["band_window"])) if dom == "local" else None
+        traffic = LOCAL_TRAFFIC.get((spec.name, a.precision)) if dom == "local" else None
         roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                 "peak_kind": peak_kind, "algorithmic_bytes_per_launch": bytes_per, "traffic": traffic,
                 "avg_launch_ms": dom_ms / dom_cnt}
