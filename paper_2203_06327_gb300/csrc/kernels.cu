@@ -1973,54 +1973,89 @@ __global__ void __launch_bounds__(((BMAX + 31) / 32) * 32) k_local_band_team(
 }
 
 // c[a, i] = sum_{g} P[g, a] rho[g, i] using P^T (CSR n_H x n); one block per coarse dof.
-__global__ void k_coarse_restrict(int nH, int k, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                                  const double* __restrict__ pv, const double* __restrict__ rho, double* c) {
-  __shared__ double red[256];
-  const int a = blockIdx.x;
-  for (int i = 0; i < k; ++i) {
-    double s = 0;
-    for (int64_t e = rp[a] + threadIdx.x; e < rp[a + 1]; e += blockDim.x) s = fma(pv[e], rho[(int64_t)ci[e] * k + i], s);
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-      if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) c[(int64_t)a * k + i] = red[0];
-    __syncthreads();
+// Block reduction of KC per-thread column accumulators in a fixed order:
+// warp butterflies, then the warps' sums added in warp order by thread i.
+// Returns the total of column i in thread i (i < KC), 0 elsewhere.
+template <int KC>
+__device__ __forceinline__ double block_sum_columns(double (&acc)[KC], double* red /* [32][KC] */) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int i = 0; i < KC; ++i) {
+    const double v = warp_sum(acc[i]);
+    if (lane == 0) red[w * KC + i] = v;
   }
+  __syncthreads();
+  double s = 0;
+  if ((int)threadIdx.x < KC)
+    for (int q = 0; q < nw; ++q) s += red[q * KC + threadIdx.x];
+  return s;
+}
+
+// c[a, i] = sum_r P^T[a, r] rho[r, i]: one block per coarse row a, a thread per
+// entry of the row with all KC columns of rho[r, :] in registers.
+template <int KC>
+__global__ void __launch_bounds__(256) k_coarse_restrict(int nH, int k, const int64_t* __restrict__ rp,
+                                                         const int32_t* __restrict__ ci,
+                                                         const double* __restrict__ pv,
+                                                         const double* __restrict__ rho, double* c) {
+  __shared__ double red[8 * KC];
+  const int a = blockIdx.x;
+  double acc[KC];
+#pragma unroll
+  for (int i = 0; i < KC; ++i) acc[i] = 0.0;
+  for (int64_t e = rp[a] + threadIdx.x; e < rp[a + 1]; e += blockDim.x) {
+    const double p = pv[e];
+    const double* row = rho + (int64_t)ci[e] * k;
+#pragma unroll
+    for (int i = 0; i < KC; ++i)
+      if (i < k) acc[i] = fma(p, row[i], acc[i]);
+  }
+  const double s = block_sum_columns<KC>(acc, red);
+  if ((int)threadIdx.x < k) c[(int64_t)a * k + threadIdx.x] = s;
 }
 
 // Coarse term of Eq. (3.3) in the eigenbasis Phi of (K_H, M_H):
 // a[j, i] = (phi_j . c_i) / (lambda_j^H - lambda_i) for j >= k (Q_{s+1}^H), 0 for j < k.
-__global__ void k_coarse_spectral(int nH, int k, const double* __restrict__ Phi, const double* __restrict__ lamH,
-                                  const double* __restrict__ lam, const double* __restrict__ c, double* a) {
-  __shared__ double red[128];
+template <int KC>
+__global__ void __launch_bounds__(256) k_coarse_spectral(int nH, int k, const double* __restrict__ Phi,
+                                                         const double* __restrict__ lamH,
+                                                         const double* __restrict__ lam,
+                                                         const double* __restrict__ c, double* a) {
+  __shared__ double red[8 * KC];
   const int j = blockIdx.x;
-  for (int i = 0; i < k; ++i) {
-    double s = 0;
-    if (j >= k)
-      for (int r = threadIdx.x; r < nH; r += blockDim.x) s = fma(Phi[(int64_t)r * nH + j], c[(int64_t)r * k + i], s);
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-      if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-      __syncthreads();
+  double acc[KC];
+#pragma unroll
+  for (int i = 0; i < KC; ++i) acc[i] = 0.0;
+  if (j >= k)
+    for (int r = threadIdx.x; r < nH; r += blockDim.x) {
+      const double ph = Phi[(int64_t)r * nH + j];
+      const double* row = c + (int64_t)r * k;
+#pragma unroll
+      for (int i = 0; i < KC; ++i)
+        if (i < k) acc[i] = fma(ph, row[i], acc[i]);
     }
-    if (threadIdx.x == 0) a[(int64_t)j * k + i] = (j >= k) ? red[0] / (lamH[j] - lam[i]) : 0.0;
-    __syncthreads();
-  }
+  const double s = block_sum_columns<KC>(acc, red);
+  if ((int)threadIdx.x < k) a[(int64_t)j * k + threadIdx.x] = (j >= k) ? s / (lamH[j] - lam[threadIdx.x]) : 0.0;
 }
 
-// w0 = Phi a (n_H x k)
-__global__ void k_coarse_expand(int nH, int k, const double* __restrict__ Phi, const double* __restrict__ a,
-                                double* w0) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nH * k) return;
-  int r = t / k, i = t % k;
-  double s = 0;
-  for (int j = k; j < nH; ++j) s = fma(Phi[(int64_t)r * nH + j], a[(int64_t)j * k + i], s);
-  w0[t] = s;
+// w0 = Phi a (n_H x k): one block per coarse row r.
+template <int KC>
+__global__ void __launch_bounds__(256) k_coarse_expand(int nH, int k, const double* __restrict__ Phi,
+                                                       const double* __restrict__ a, double* w0) {
+  __shared__ double red[8 * KC];
+  const int r = blockIdx.x;
+  double acc[KC];
+#pragma unroll
+  for (int i = 0; i < KC; ++i) acc[i] = 0.0;
+  for (int j = k + threadIdx.x; j < nH; j += blockDim.x) {
+    const double ph = Phi[(int64_t)r * nH + j];
+    const double* row = a + (int64_t)j * k;
+#pragma unroll
+    for (int i = 0; i < KC; ++i)
+      if (i < k) acc[i] = fma(ph, row[i], acc[i]);
+  }
+  const double s = block_sum_columns<KC>(acc, red);
+  if ((int)threadIdx.x < k) w0[(int64_t)r * k + threadIdx.x] = s;
 }
 
 // z[g, i] = sum_{c} P[g, c] w0[c, i] + sum_{local copies of g} w[pos, i]
@@ -3221,17 +3256,21 @@ __global__ void k_kp_rows(int n, const int64_t* __restrict__ arp, const int32_t*
   cnt[r] = m;
 }
 
-// Pass 2 (one warp per coarse row a): K_H[a, b] = sum_{r in P^T row a, ascending}
-// P[r, a] (K P)[r, b].  Lane j owns the columns b = j mod 32 of a dense row in
-// shared memory, so every entry is summed by one lane in a fixed order.
+// Pass 2 (one block per coarse row a): K_H[a, b] = sum_{r in P^T row a}
+// P[r, a] (K P)[r, b].  Warp w takes a contiguous part of the P^T row and
+// accumulates into its own dense row in shared memory, lane s adding entry s
+// of (K P)[r, :] (distinct columns b, so no two lanes meet); the rows of P^T
+// are visited in ascending order and the warps' rows are added in warp order,
+// so every entry is summed in a fixed order.  The loads of the next
+// kGalerkinUnroll rows are issued before their updates.
+constexpr int kGalerkinUnroll = 8;
 __global__ void k_galerkin_rows(int nH, const int64_t* __restrict__ ptr, const int32_t* __restrict__ ptc,
                                 const double* __restrict__ ptv, const int32_t* __restrict__ kpc,
                                 const double* __restrict__ kpk, const double* __restrict__ kpm,
                                 const int32_t* __restrict__ cnt, double* KH, double* MH) {
   extern __shared__ double rowbuf[];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int a = blockIdx.x * (blockDim.x >> 5) + wib;
-  if (a >= nH) return;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int a = blockIdx.x;
   double* kr = rowbuf + (size_t)wib * 2 * nH;
   double* mr = kr + nH;
   for (int t = lane; t < nH; t += 32) {
@@ -3239,24 +3278,47 @@ __global__ void k_galerkin_rows(int nH, const int64_t* __restrict__ ptr, const i
     mr[t] = 0.0;
   }
   __syncwarp();
-  for (int64_t e = ptr[a]; e < ptr[a + 1]; ++e) {
-    const int64_t r = ptc[e];
-    const double pra = ptv[e];
-    const int m = cnt[r];
-    for (int s = 0; s < m; ++s) {
-      const int b = kpc[r * kKPWidth + s];
-      if ((b & 31) == lane) {
-        kr[b] += pra * kpk[r * kKPWidth + s];
-        mr[b] += pra * kpm[r * kKPWidth + s];
-      }
+  const int64_t e0 = ptr[a], e1 = ptr[a + 1];
+  const int64_t len = (e1 - e0 + nw - 1) / nw;
+  const int64_t eb = e0 + wib * len, ee = min(e1, eb + len);
+  constexpr int GU = kGalerkinUnroll;
+  for (int64_t e = eb; e < ee; e += GU) {
+    int32_t rr[GU], m[GU], b[GU];
+    double p[GU], xk[GU], xm[GU];
+#pragma unroll
+    for (int u = 0; u < GU; ++u) {
+      const bool ok = e + u < ee;
+      rr[u] = ok ? ptc[e + u] : 0;
+      p[u] = ok ? ptv[e + u] : 0.0;
+      m[u] = ok ? cnt[rr[u]] : 0;
     }
+#pragma unroll
+    for (int u = 0; u < GU; ++u) {
+      const bool ok = lane < m[u];
+      const int64_t o = (int64_t)rr[u] * kKPWidth + lane;
+      b[u] = ok ? kpc[o] : 0;
+      xk[u] = ok ? kpk[o] : 0.0;
+      xm[u] = ok ? kpm[o] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < GU; ++u)
+      if (lane < m[u]) {
+        kr[b[u]] += p[u] * xk[u];
+        mr[b[u]] += p[u] * xm[u];
+      }
   }
-  __syncwarp();
-  for (int t = lane; t < nH; t += 32) {
-    KH[(int64_t)a * nH + t] = kr[t];
-    MH[(int64_t)a * nH + t] = mr[t];
+  __syncthreads();
+  for (int t = threadIdx.x; t < nH; t += blockDim.x) {
+    double sk = 0.0, sm = 0.0;
+    for (int q = 0; q < nw; ++q) {
+      sk += rowbuf[(size_t)q * 2 * nH + t];
+      sm += rowbuf[(size_t)q * 2 * nH + nH + t];
+    }
+    KH[(int64_t)a * nH + t] = sk;
+    MH[(int64_t)a * nH + t] = sm;
   }
 }
+
 
 int col_block(int k) { return k * (256 / k); }
 
@@ -3546,9 +3608,18 @@ int launch_precond(Handle& h, const double* rho, const double* lam, double* Z) {
   {
     ProfScope ps(h, BPJD_PROF_COARSE);
     h.launches += 3;
-    k_coarse_restrict<<<h.nH, 256, 0, h.stream>>>(h.nH, k, h.PT.row_ptr, h.PT.col, h.PT.val, rho, h.cH);
-    k_coarse_spectral<<<h.nH, 128, 0, h.stream>>>(h.nH, k, h.Phi, h.lamH, lam, h.cH, h.aH);
-    k_coarse_expand<<<(h.nH * k + 127) / 128, 128, 0, h.stream>>>(h.nH, k, h.Phi, h.aH, h.w0);
+    auto coarse = [&](auto kc) {
+      constexpr int KC = decltype(kc)::value;
+      k_coarse_restrict<KC><<<h.nH, 256, 0, h.stream>>>(h.nH, k, h.PT.row_ptr, h.PT.col, h.PT.val, rho, h.cH);
+      k_coarse_spectral<KC><<<h.nH, 256, 0, h.stream>>>(h.nH, k, h.Phi, h.lamH, lam, h.cH, h.aH);
+      k_coarse_expand<KC><<<h.nH, 256, 0, h.stream>>>(h.nH, k, h.Phi, h.aH, h.w0);
+    };
+    if (k <= 8)
+      coarse(std::integral_constant<int, 8>());
+    else if (k <= 16)
+      coarse(std::integral_constant<int, 16>());
+    else
+      coarse(std::integral_constant<int, 32>());
   }
   // prolongation-add
   {
@@ -3632,7 +3703,7 @@ int launch_galerkin(const CsrDev& A, const CsrDev& Msp, const CsrDev& P, const C
   int32_t *kpc = nullptr, *cnt = nullptr, *ovf = nullptr;
   double *kpk = nullptr, *kpm = nullptr;
   int rc = 0, hov = 0;
-  const int wpb = 4;
+  const int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, (200 * 1024) / (2 * (size_t)nH * sizeof(double))));
   const size_t sm = (size_t)wpb * 2 * nH * sizeof(double);
   cudaError_t e = cudaSuccess;
   if ((e = cudaMalloc(&kpc, sizeof(int32_t) * (size_t)n * kKPWidth)) != cudaSuccess) goto done;
@@ -3644,8 +3715,7 @@ int launch_galerkin(const CsrDev& A, const CsrDev& Msp, const CsrDev& P, const C
   k_kp_rows<<<(n + 127) / 128, 128, 0, s>>>(n, A.row_ptr, A.col, A.val, Msp.row_ptr, Msp.col, Msp.val, P.row_ptr,
                                             P.col, P.val, kpc, kpk, kpm, cnt, ovf);
   if (sm > 48 * 1024) cudaFuncSetAttribute(k_galerkin_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_galerkin_rows<<<(nH + wpb - 1) / wpb, 32 * wpb, sm, s>>>(nH, PT.row_ptr, PT.col, PT.val, kpc, kpk, kpm, cnt,
-                                                              KH, MH);
+  k_galerkin_rows<<<nH, 32 * wpb, sm, s>>>(nH, PT.row_ptr, PT.col, PT.val, kpc, kpk, kpm, cnt, KH, MH);
   if ((e = cudaGetLastError()) != cudaSuccess) goto done;
   if ((e = cudaMemcpyAsync(&hov, ovf, sizeof(int32_t), cudaMemcpyDeviceToHost, s)) != cudaSuccess) goto done;
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) goto done;
