@@ -264,33 +264,70 @@ __device__ __forceinline__ void gram_tile_of(int t, int TU, int TV, int sym, int
   tb = a + t;
 }
 
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Per-block Gram partials in double-word arithmetic (Dot2 per entry).  The
+// row range of a block is processed in chunks of R rows: the FP64 rows of
+// every U / V block are copied asynchronously into a raw staging buffer two
+// chunks ahead (double buffered), split into (hi, lo) planes once per chunk,
+// and every thread accumulates a 4 x 4 tile of the output for every NV over
+// its slice of the chunk's rows.  Plane layout: one segment of R x k values per
+// block (U blocks, then V1, then V2), row-major.
 template <int NV>
 __global__ void __launch_bounds__(256, 2) k_gram_dw(int n, int k, int nu, Ptrs6 U, int nvb, Ptrs6 V1, Ptrs6 V2, int sym,
-                                                 int rows_per_block, double* partial) {
+                                                 int rows_per_block, int R, double* partial) {
   extern __shared__ __align__(16) float gsm[];
   const int mu = nu * k, mv = nvb * k;
   const int TU = (mu + 3) / 4, TV = (mv + 3) / 4;
-  const int MU4 = 4 * TU, MV4 = 4 * TV;
   const int ntiles = sym ? TU * (TU + 1) / 2 : TU * TV;
   const int S = max(1, (int)blockDim.x / ntiles);
-  float* Uh = gsm;
-  float* Ul = Uh + kGramRows * MU4;
-  float* Vh[NV];
-  float* Vl[NV];
-  {
-    float* p = Ul + kGramRows * MU4;
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      Vh[v] = p;
-      Vl[v] = p + kGramRows * MV4;
-      p += 2 * kGramRows * MV4;
-    }
-  }
+  const int nseg = nu + NV * nvb;
+  const int SEG = R * k;    // values per segment
+  const int CH = nseg * SEG;  // values per chunk
+  double* raw = reinterpret_cast<double*>(gsm);    // [2][CH]
+  float* ph = reinterpret_cast<float*>(raw + 2 * CH);  // [CH]
+  float* pl = ph + CH;                                 // [CH]
   const int tid = threadIdx.x;
   const int tile = tid % ntiles, slice = tid / ntiles;
   const bool worker = slice < S;
   int ta = 0, tb = 0;
   gram_tile_of(tile, TU, TV, sym, ta, tb);
+  // plane offsets of this thread's four U columns and four V columns (-1: past the end)
+  int uo[4], vo[4];
+#pragma unroll
+  for (int x = 0; x < 4; ++x) {
+    const int cu = 4 * ta + x, cv = 4 * tb + x;
+    uo[x] = (cu < mu) ? (cu / k) * SEG + cu % k : -1;
+    vo[x] = (cv < mv) ? (nu + cv / k) * SEG + cv % k : -1;
+  }
+  const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
+  const int64_t r1 = min((int64_t)n, r0 + rows_per_block);
+  const int nch = (int)((r1 - r0 + R - 1) / R);
+  auto seg_ptr = [&](int sg) -> const double* {
+    if (sg < nu) return U.p[sg];
+    sg -= nu;
+    if (sg < nvb) return V1.p[sg];
+    return V2.p[sg - nvb];
+  };
+  auto issue = [&](int c) {
+    if (c < nch) {
+      const int64_t rb = r0 + (int64_t)c * R;
+      const int64_t lim = (r1 - rb) * k;  // values of this chunk inside the row range
+      double* dst = raw + (c & 1) * CH;
+      for (int sg = 0; sg < nseg; ++sg) {
+        const double* src = seg_ptr(sg) + rb * k;
+        for (int e = tid; e < SEG; e += blockDim.x)
+          if (e < lim) cp_async8(dst + sg * SEG + e, src + e);
+      }
+    }
+    cp_async_commit();
+  };
   dot2 acc[NV][4][4];
 #pragma unroll
   for (int v = 0; v < NV; ++v)
@@ -298,43 +335,41 @@ __global__ void __launch_bounds__(256, 2) k_gram_dw(int n, int k, int nu, Ptrs6 
     for (int x = 0; x < 4; ++x)
 #pragma unroll
       for (int y = 0; y < 4; ++y) acc[v][x][y].zero();
-  const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
-  const int64_t r1 = min((int64_t)n, r0 + rows_per_block);
-  for (int64_t rb = r0; rb < r1; rb += kGramRows) {
-    const int nr = (int)min((int64_t)kGramRows, r1 - rb);
-    for (int idx = tid; idx < kGramRows * MU4; idx += blockDim.x) {
-      const int r = idx / MU4, col = idx % MU4;
-      double x = 0.0;
-      if (r < nr && col < mu) x = U.p[col / k][(rb + r) * k + (col % k)];
-      const dw s = split_f64(x);
-      Uh[idx] = s.hi;
-      Ul[idx] = s.lo;
-    }
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      const Ptrs6& VV = (v == 0) ? V1 : V2;
-      for (int idx = tid; idx < kGramRows * MV4; idx += blockDim.x) {
-        const int r = idx / MV4, col = idx % MV4;
-        double x = 0.0;
-        if (r < nr && col < mv) x = VV.p[col / k][(rb + r) * k + (col % k)];
-        const dw s = split_f64(x);
-        Vh[v][idx] = s.hi;
-        Vl[v][idx] = s.lo;
+  issue(0);
+  issue(1);
+  for (int c = 0; c < nch; ++c) {
+    cp_async_wait1();
+    __syncthreads();  // chunk c has landed for every thread; the planes are free
+    {
+      const int nr = (int)min((int64_t)R, r1 - (r0 + (int64_t)c * R));
+      const double* src = raw + (c & 1) * CH;
+      for (int e = tid; e < CH; e += blockDim.x) {
+        const int r = (e % SEG) / k;
+        const dw sp = split_f64(r < nr ? src[e] : 0.0);
+        ph[e] = sp.hi;
+        pl[e] = sp.lo;
       }
     }
-    __syncthreads();
+    __syncthreads();  // planes ready; the raw buffer of chunk c is free
+    issue(c + 2);
     if (worker) {
-      for (int r = slice; r < nr; r += S) {
-        const float4 uh = *reinterpret_cast<const float4*>(Uh + r * MU4 + 4 * ta);
-        const float4 ul = *reinterpret_cast<const float4*>(Ul + r * MU4 + 4 * ta);
-        const float a_h[4] = {uh.x, uh.y, uh.z, uh.w};
-        const float a_l[4] = {ul.x, ul.y, ul.z, ul.w};
+      for (int r = slice; r < R; r += S) {
+        const int ro = r * k;
+        float a_h[4], a_l[4];
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+          a_h[x] = (uo[x] >= 0) ? ph[uo[x] + ro] : 0.f;
+          a_l[x] = (uo[x] >= 0) ? pl[uo[x] + ro] : 0.f;
+        }
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-          const float4 vh = *reinterpret_cast<const float4*>(Vh[v] + r * MV4 + 4 * tb);
-          const float4 vl = *reinterpret_cast<const float4*>(Vl[v] + r * MV4 + 4 * tb);
-          const float b_h[4] = {vh.x, vh.y, vh.z, vh.w};
-          const float b_l[4] = {vl.x, vl.y, vl.z, vl.w};
+          float b_h[4], b_l[4];
+#pragma unroll
+          for (int y = 0; y < 4; ++y) {
+            const int o = vo[y] + v * mv * R;  // V2 segments follow the V1 segments
+            b_h[y] = (vo[y] >= 0) ? ph[o + ro] : 0.f;
+            b_l[y] = (vo[y] >= 0) ? pl[o + ro] : 0.f;
+          }
 #pragma unroll
           for (int x = 0; x < 4; ++x)
 #pragma unroll
@@ -342,8 +377,9 @@ __global__ void __launch_bounds__(256, 2) k_gram_dw(int n, int k, int nu, Ptrs6 
         }
       }
     }
-    __syncthreads();
   }
+  cp_async_wait0();
+  __syncthreads();
   // combine the slices of every tile in FP64 (shared memory reused)
   double* red = reinterpret_cast<double*>(gsm);
   const int per = NV * 16;
@@ -3491,15 +3527,20 @@ int launch_gram_raw(int64_t n, int k, int nu, const double* const* U, int nvb, i
   const int nblk2 = (int)((n + rpb - 1) / rpb);
   const int total = nv * ntiles * 16;
   if ((size_t)nblk2 * total > partial_capacity) return (int)cudaErrorInvalidValue;
-  const size_t chunk = (size_t)kGramRows * (2 * 4 * TU + nv * 2 * 4 * TV) * sizeof(float);
+  // chunk rows: a divisor of kGramRows keeping the staging (two raw FP64 buffers
+  // and the hi/lo planes, 24 bytes per value) within 100 KB
+  const int nseg = nu + nv * nvb;
+  int R = 32;
+  while (R > 1 && (size_t)24 * R * k * nseg > 100 * 1024) R /= 2;
+  const size_t stage = (size_t)24 * R * k * nseg;
   const size_t red = (size_t)ntiles * nv * 16 * sizeof(double);
-  const size_t sm = std::max(chunk, red);
+  const size_t sm = std::max(stage, red);
   if (nv == 2) {
     cudaFuncSetAttribute(k_gram_dw<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_gram_dw<2><<<nblk2, 256, sm, stream>>>((int)n, k, nu, u, nvb, v1, v2, sym, rpb, partial);
+    k_gram_dw<2><<<nblk2, 256, sm, stream>>>((int)n, k, nu, u, nvb, v1, v2, sym, rpb, R, partial);
   } else {
     cudaFuncSetAttribute(k_gram_dw<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_gram_dw<1><<<nblk2, 256, sm, stream>>>((int)n, k, nu, u, nvb, v1, v2, sym, rpb, partial);
+    k_gram_dw<1><<<nblk2, 256, sm, stream>>>((int)n, k, nu, u, nvb, v1, v2, sym, rpb, R, partial);
   }
   k_gram_reduce<<<(total + 31) / 32, 256, 0, stream>>>(nblk2, nv, mu, mv, sym, partial, out1, out2);
   return (int)cudaGetLastError();
