@@ -677,6 +677,7 @@ extern "C" int bpjd_solve(bpjd_handle* hh, double* eigvals, double* eigvecs, int
   double *Pc = h.Pd, *APc = h.APd, *MPc = h.MPd;      // current P block (3k)
   double *Pn = h.Pd2, *APn = h.APd2, *MPn = h.MPd2;   // next P block
   bool have_prev = false;
+  const int mixed = (h.precision == BPJD_MIXED) ? 1 : 0;
 
   CK(cudaMemsetAsync(h.dstat, 0, sizeof(DevStatus), h.stream));
   CK(cudaMemsetAsync(h.derr, 0, 4 * sizeof(int32_t), h.stream));
@@ -723,29 +724,31 @@ extern "C" int bpjd_solve(bpjd_handle* hh, double* eigvals, double* eigvecs, int
       else
         CKI(launch_inner(h, 1, U, 1, V, C1));
       const double* Win[1] = {X};
+      // double-word: the preconditioned residual is dominated by its component
+      // along the iterate, so t is a small difference of large terms
       CKI(launch_combine_rows(h, 1, Win, C1, k, k, h.Z, h.T, -1.0));
     }
     CKI(launch_spmm(h, h.T, h.AT, h.MT, k));
     // Step 3: Rayleigh-Ritz in W = U^k + span{t} (+ U^{k-1})
     int nb;
     const double *W[3], *AW[3], *MW[3];
-    W[0] = X;
-    AW[0] = AX;
-    MW[0] = MX;
-    if (h.subspace == BPJD_W_3K && have_prev) {
-      // span{X, P} = U^k + U^{k-1}: P is the part of the previous update outside X
-      W[1] = Pc;
-      AW[1] = APc;
-      MW[1] = MPc;
-      W[2] = h.T;
-      AW[2] = h.AT;
-      MW[2] = h.MT;
-      nb = 3;
+    auto put = [&](int b, const double* w, const double* aw, const double* mw) {
+      W[b] = w;
+      AW[b] = aw;
+      MW[b] = mw;
+    };
+    // span{X, P} = U^k + U^{k-1}: P is the part of the previous update outside X.
+    // Mixed precision: the iterate goes last, so that the upper Gram tiles (the
+    // ones formed) pair the correction and P blocks with the exact products of
+    // the iterate, never the FP32 products of t or P with the iterate.
+    nb = (h.subspace == BPJD_W_3K && have_prev) ? 3 : 2;
+    const int bx = mixed ? nb - 1 : 0;  // block of the iterate
+    put(bx, X, AX, MX);
+    if (nb == 3) {
+      put(1, Pc, APc, MPc);
+      put(mixed ? 0 : 2, h.T, h.AT, h.MT);
     } else {
-      W[1] = h.T;
-      AW[1] = h.AT;
-      MW[1] = h.MT;
-      nb = 2;
+      put(mixed ? 0 : 1, h.T, h.AT, h.MT);
     }
     const int m = nb * k;
     if (h.precision == BPJD_MIXED) {
@@ -758,8 +761,12 @@ extern "C" int bpjd_solve(bpjd_handle* hh, double* eigvals, double* eigvecs, int
     CKI(launch_combine_rows(h, nb, W, Crr, k, k, nullptr, Xn, 1.0));
     CKI(launch_spmm(h, Xn, AXn, MXn, k));
     if (h.subspace == BPJD_W_3K) {
-      // P_new = W[:, k:] C[k:, :], with K P_new and M P_new by SpMM (no cancellation)
-      CKI(launch_combine_rows(h, nb - 1, W + 1, Crr + (size_t)k * k, k, k, nullptr, Pn, 1.0));
+      // P_new = the non-iterate blocks of W times their rows of C, with K P_new and
+      // M P_new by SpMM (no cancellation)
+      if (mixed)
+        CKI(launch_combine_rows(h, nb - 1, W, Crr, k, k, nullptr, Pn, 1.0, 1));
+      else
+        CKI(launch_combine_rows(h, nb - 1, W + 1, Crr + (size_t)k * k, k, k, nullptr, Pn, 1.0));
       CKI(launch_spmm(h, Pn, APn, MPn, k));
       std::swap(Pc, Pn);
       std::swap(APc, APn);

@@ -82,6 +82,17 @@ __device__ __forceinline__ dw split_f64(double x) {
   return r;
 }
 
+// The float nearest below |x| in magnitude (significand truncated to 24 bits):
+// the hi part of split_f64, integer operations only.
+__device__ __forceinline__ float f64_hi(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned int sign = (unsigned int)(b >> 63) << 31;
+  const int e = (int)((b >> 52) & 0x7ff);
+  if (e < 897) return __uint_as_float(sign);
+  if (e > 1150) return __uint_as_float(sign | 0x7f800000u);
+  return __uint_as_float(sign | ((unsigned int)(e - 896) << 23) | (unsigned int)((b & 0xfffffffffffffULL) >> 29));
+}
+
 __device__ __forceinline__ double f32_to_f64_bits(float f) {
   const unsigned int u = __float_as_uint(f);
   const unsigned int e = (u >> 23) & 0xff;

@@ -481,9 +481,10 @@ __global__ void __launch_bounds__(256) k_combine_dw(int64_t n, int k, int nin, P
 }
 
 // CSR SpMM in double-word arithmetic with pre-split matrix values (hi/lo
-// float arrays of K and M): YA = K X, YM = M X.  LANES lanes per row as in
-// k_spmm; each lane owns columns j0 and j0 + LANES.
-template <int LANES>
+// float arrays of K and M): YA = K X, YM = M X.  LANES lanes serve one row;
+// lane j of the group owns columns j + LANES c, c < CPL.  The X entries are
+// split on the fly (integer operations only).
+template <int LANES, int CPL>
 __global__ void __launch_bounds__(256) k_spmm_dw(int n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
                                                  const float2* __restrict__ va, const float2* __restrict__ vm,
                                                  const double* __restrict__ X, double* __restrict__ YA,
@@ -494,36 +495,114 @@ __global__ void __launch_bounds__(256) k_spmm_dw(int n, const int64_t* __restric
   const int64_t row = warp * RPW + lane / LANES;
   const int j0 = lane % LANES;
   if (row >= n) return;
-  const int j1 = j0 + LANES;
-  const bool has0 = j0 < ncols, has1 = j1 < ncols;
-  dot2 a0, a1, m0, m1;
-  a0.zero();
-  a1.zero();
-  m0.zero();
-  m1.zero();
+  dot2 a[CPL], m[CPL];
+#pragma unroll
+  for (int c = 0; c < CPL; ++c) {
+    a[c].zero();
+    m[c].zero();
+  }
   for (int64_t e = rp[row]; e < rp[row + 1]; ++e) {
-    const int64_t c = ci[e];
+    const int64_t col = ci[e];
     const float2 av = va[e];
     const float2 mv = vm ? vm[e] : make_float2(0.f, 0.f);
-    const double* xr = X + c * ncols;
-    if (has0) {
-      const dw x = split_f64(xr[j0]);
-      a0.mac(av.x, av.y, x.hi, x.lo);
-      m0.mac(mv.x, mv.y, x.hi, x.lo);
-    }
-    if (has1) {
-      const dw x = split_f64(xr[j1]);
-      a1.mac(av.x, av.y, x.hi, x.lo);
-      m1.mac(mv.x, mv.y, x.hi, x.lo);
+    const double* xr = X + col * ncols;
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) {
+      const int j = j0 + LANES * c;
+      if (j < ncols) {
+        const dw x = split_f64(xr[j]);
+        a[c].mac(av.x, av.y, x.hi, x.lo);
+        m[c].mac(mv.x, mv.y, x.hi, x.lo);
+      }
     }
   }
-  if (has0) {
-    YA[row * ncols + j0] = a0.value();
-    if (YM) YM[row * ncols + j0] = m0.value();
+#pragma unroll
+  for (int c = 0; c < CPL; ++c) {
+    const int j = j0 + LANES * c;
+    if (j < ncols) {
+      YA[row * ncols + j] = a[c].value();
+      if (YM) YM[row * ncols + j] = m[c].value();
+    }
   }
-  if (has1) {
-    YA[row * ncols + j1] = a1.value();
-    if (YM) YM[row * ncols + j1] = m1.value();
+}
+
+// The same products in FP32 (hi parts of K, M and X, FP32 accumulation) for
+// blocks whose products only have to be consistent with the stored block: the
+// correction t and the previous-update block P of the search space.  Their
+// Gram entries with the current iterate are taken from the exact products of
+// the iterate, so the FP32 error reaches only the entries between correction
+// and previous-update directions, whose Ritz coefficients vanish as the
+// iteration converges.
+template <int LANES, int CPL>
+__global__ void __launch_bounds__(256) k_spmm_f32(int n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                                  const float2* __restrict__ va, const float2* __restrict__ vm,
+                                                  const double* __restrict__ X, double* __restrict__ YA,
+                                                  double* __restrict__ YM, int ncols) {
+  constexpr int RPW = 32 / LANES;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t row = warp * RPW + lane / LANES;
+  const int j0 = lane % LANES;
+  if (row >= n) return;
+  float a[CPL], m[CPL];
+#pragma unroll
+  for (int c = 0; c < CPL; ++c) {
+    a[c] = 0.f;
+    m[c] = 0.f;
+  }
+  for (int64_t e = rp[row]; e < rp[row + 1]; ++e) {
+    const int64_t col = ci[e];
+    const float av = va[e].x;
+    const float mv = vm ? vm[e].x : 0.f;
+    const double* xr = X + col * ncols;
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) {
+      const int j = j0 + LANES * c;
+      if (j < ncols) {
+        const float x = f64_hi(xr[j]);
+        a[c] = fmaf(av, x, a[c]);
+        m[c] = fmaf(mv, x, m[c]);
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < CPL; ++c) {
+    const int j = j0 + LANES * c;
+    if (j < ncols) {
+      YA[row * ncols + j] = f32_to_f64_bits(a[c]);
+      if (YM) YM[row * ncols + j] = f32_to_f64_bits(m[c]);
+    }
+  }
+}
+
+// Row-wise block update in FP32 (hi parts of W and C):
+// out[r, j] = Zadd[r, j] + sign * sum_b sum_a W_b[r, a] C[(b k + a) ldc + j],
+// for the blocks of the search space that need no more than consistency (see
+// k_spmm_f32).  A block stages kCombRows rows of W and the coefficients.
+__global__ void __launch_bounds__(256) k_combine_f32(int64_t n, int k, int nin, Ptrs6 W, const double* __restrict__ C,
+                                                     int ldc, int csub, const double* __restrict__ Zadd,
+                                                     double* __restrict__ out, float sign) {
+  extern __shared__ __align__(16) float csm[];
+  const int m = nin * k;
+  float* Cs = csm;              // m x csub
+  float* Ws = Cs + m * csub;    // kCombRows x m
+  for (int t = threadIdx.x; t < m * csub; t += blockDim.x) Cs[t] = f64_hi(C[(t / csub) * ldc + (t % csub)]);
+  const int64_t row0 = (int64_t)blockIdx.x * kCombRows;
+  const int nr = (int)min((int64_t)kCombRows, n - row0);
+  for (int b = 0; b < nin; ++b) {
+    const double* src = W.p[b] + row0 * k;
+    for (int t = threadIdx.x; t < nr * k; t += blockDim.x) Ws[(t / k) * m + b * k + (t % k)] = f64_hi(src[t]);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < nr * csub; t += blockDim.x) {
+    const int r = t / csub, j = t % csub;
+    float acc = 0.f;
+    const float* w = Ws + r * m;
+    for (int a = 0; a < m; ++a) acc = fmaf(w[a], Cs[a * csub + j], acc);
+    const int64_t o = (row0 + r) * csub + j;
+    float v = sign * acc;
+    if (Zadd) v += f64_hi(Zadd[o]);
+    out[o] = f32_to_f64_bits(v);
   }
 }
 
@@ -2213,12 +2292,14 @@ __device__ void sort_diag(const double* A, int m, int* ord) {
   __syncthreads();
 }
 
-// G, H: m x m (row-major, ld m).  First k columns of W are b-orthonormal Ritz
-// vectors, the rest are scaled to unit M-norm.  Output C (m x k, ld k),
+// G, H: m x m (row-major, ld m).  scale_all = 0: the first k columns of W are
+// M-orthonormal Ritz vectors and stay as they are, the rest are scaled to unit
+// M-norm; scale_all = 1: every column is scaled.  Output C (m x k, ld k),
 // lam_new (k), hist row, status.
 __device__ void rayleigh_ritz_eig(int m, int k, const double* __restrict__ G, const double* __restrict__ H,
                                   double drop_tol, const double* __restrict__ lam_old, double* C, double* lam_new,
-                                  double* hist_row, int stop_rule, double tol, DevStatus* st, double* rr) {
+                                  double* hist_row, int stop_rule, double tol, DevStatus* st, double* rr,
+                                  int scale_all) {
   const int ld = kRRMax;
   double* A = rr;                  // ld x ld
   double* V = A + ld * ld;         // ld x ld
@@ -2234,7 +2315,7 @@ __device__ void rayleigh_ritz_eig(int m, int k, const double* __restrict__ G, co
   const int tid = threadIdx.x;
   for (int j = tid; j < m; j += blockDim.x) {
     double g = G[j * m + j];
-    sc[j] = (j < k) ? 1.0 : (g > 0 ? 1.0 / sqrt(g) : 0.0);
+    sc[j] = (j < k && !scale_all) ? 1.0 : (g > 0 ? 1.0 / sqrt(g) : 0.0);
   }
   __syncthreads();
   for (int t = tid; t < m * m; t += blockDim.x) {
@@ -2918,7 +2999,9 @@ __global__ void k_rayleigh_ritz_chol(int m, int k, const double* __restrict__ G,
   tcl[0] = clock64();
   for (int j = tid; j < m; j += blockDim.x) {
     const double g = G[j * m + j];
-    sc[j] = (j < k) ? 1.0 : (g > 0 ? 1.0 / sqrt(g) : 0.0);
+    // the FP64 path keeps the first k columns (the iterate, M-orthonormal) as they
+    // are; the mixed path scales every column, its iterate block being the last
+    sc[j] = (j < k && !dword) ? 1.0 : (g > 0 ? 1.0 / sqrt(g) : 0.0);
   }
   if (tid == 0) ok = 1;
   __syncthreads();
@@ -2945,7 +3028,7 @@ __global__ void k_rayleigh_ritz_chol(int m, int k, const double* __restrict__ G,
       return;
     }
     // ill-conditioned: eigen-based orthonormalisation with dropping
-    rayleigh_ritz_eig(m, k, G, H, drop_tol, lam_old, C, lam_new, hist_row, stop_rule, tol, st, rr);
+    rayleigh_ritz_eig(m, k, G, H, drop_tol, lam_old, C, lam_new, hist_row, stop_rule, tol, st, rr, dword);
     return;
   }
   // B0 = G' (becomes L), B1 = H'
@@ -3017,7 +3100,7 @@ __global__ void k_rayleigh_ritz_chol(int m, int k, const double* __restrict__ G,
   __syncthreads();
   if (!ok) {
     // ill-conditioned basis: eigen-based orthonormalisation with dropping
-    rayleigh_ritz_eig(m, k, G, H, drop_tol, lam_old, C, lam_new, hist_row, stop_rule, tol, st, rr);
+    rayleigh_ritz_eig(m, k, G, H, drop_tol, lam_old, C, lam_new, hist_row, stop_rule, tol, st, rr, dword);
     return;
   }
   tcl[3] = clock64();
@@ -3394,7 +3477,7 @@ void prof_flush(Handle& h) {
 // ===========================================================================
 // launchers
 // ===========================================================================
-int launch_spmm(Handle& h, const double* X, double* YA, double* YM, int ncols) {
+int launch_spmm(Handle& h, const double* X, double* YA, double* YM, int ncols, int consistency_only) {
   ProfScope ps(h, BPJD_PROF_SPMM);
   const int n = h.n;
   auto go = [&](auto lanes_tag, const CsrDev& A, const double* vm, double* ya, double* ym) {
@@ -3406,23 +3489,40 @@ int launch_spmm(Handle& h, const double* X, double* YA, double* YM, int ncols) {
     h.launches += 1;
   };
   if (h.precision == BPJD_MIXED && h.Asplit) {
-    auto god = [&](auto lanes_tag, const CsrDev& A, const float2* va, const float2* vm, double* ya, double* ym) {
+    // lanes per row and columns per lane: every lane of a row group busy for k = 4, 8, 12, 16, 24, 32
+    auto god = [&](auto lanes_tag, auto cpl_tag, const float2* va, const float2* vm, double* ya, double* ym,
+                   const CsrDev& A) {
       constexpr int LANES = decltype(lanes_tag)::value;
+      constexpr int CPL = decltype(cpl_tag)::value;
       constexpr int RPW = 32 / LANES;
       int64_t warps = (n + RPW - 1) / RPW;
       int64_t blocks = (warps * 32 + 255) / 256;
-      k_spmm_dw<LANES><<<(unsigned)blocks, 256, 0, h.stream>>>(n, A.row_ptr, A.col, va, vm, X, ya, ym, ncols);
+      if (consistency_only)
+        k_spmm_f32<LANES, CPL><<<(unsigned)blocks, 256, 0, h.stream>>>(n, A.row_ptr, A.col, va, vm, X, ya, ym,
+                                                                        ncols);
+      else
+        k_spmm_dw<LANES, CPL><<<(unsigned)blocks, 256, 0, h.stream>>>(n, A.row_ptr, A.col, va, vm, X, ya, ym,
+                                                                       ncols);
       h.launches += 1;
     };
+    using I = std::integral_constant<int, 1>;
+    using I2 = std::integral_constant<int, 2>;
+    using I3 = std::integral_constant<int, 3>;
+    using I4 = std::integral_constant<int, 4>;
+    using I8 = std::integral_constant<int, 8>;
     auto dispatch_dw = [&](const CsrDev& A, const float2* va, const float2* vm, double* ya, double* ym) {
       if (ncols <= 4)
-        god(std::integral_constant<int, 4>(), A, va, vm, ya, ym);
+        god(I4(), I(), va, vm, ya, ym, A);
       else if (ncols <= 8)
-        god(std::integral_constant<int, 8>(), A, va, vm, ya, ym);
+        god(I4(), I2(), va, vm, ya, ym, A);
+      else if (ncols <= 12)
+        god(I4(), I3(), va, vm, ya, ym, A);
       else if (ncols <= 16)
-        god(std::integral_constant<int, 16>(), A, va, vm, ya, ym);
+        god(I4(), I4(), va, vm, ya, ym, A);
+      else if (ncols <= 24)
+        god(I8(), I3(), va, vm, ya, ym, A);
       else
-        god(std::integral_constant<int, 32>(), A, va, vm, ya, ym);
+        god(I8(), I4(), va, vm, ya, ym, A);
     };
     if (h.same_pattern) {
       dispatch_dw(h.A, h.Asplit, h.Msplit, YA, YM);
@@ -3554,11 +3654,19 @@ int launch_gram(Handle& h, int nu, const double* const* U, int nvb, int nv, cons
 }
 
 int launch_combine_rows(Handle& h, int nin, const double* const* Win, const double* C, int ldc, int csub,
-                        const double* Zadd, double* out, double sign) {
+                        const double* Zadd, double* out, double sign, int consistency_only) {
   ProfScope ps(h, BPJD_PROF_COMBINE);
   h.launches += 1;
   Ptrs6 w{};
   for (int b = 0; b < nin; ++b) w.p[b] = Win[b];
+  if (h.precision == BPJD_MIXED && consistency_only) {
+    const int m = nin * h.k;
+    const size_t sm = (size_t)(m * csub + kCombRows * m) * sizeof(float);
+    if (sm > 48 * 1024) cudaFuncSetAttribute(k_combine_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    const int64_t blocks = ((int64_t)h.n + kCombRows - 1) / kCombRows;
+    k_combine_f32<<<(unsigned)blocks, 256, sm, h.stream>>>(h.n, h.k, nin, w, C, ldc, csub, Zadd, out, (float)sign);
+    return (int)cudaGetLastError();
+  }
   if (h.precision == BPJD_MIXED) {
     const int m = nin * h.k;
     const size_t sm = (size_t)(2 * m * csub + 2 * kCombRows * m) * sizeof(float);
