@@ -125,9 +125,7 @@ int gen_eig_host(int n, const std::vector<double>& K, const std::vector<double>&
                  std::vector<double>& Phi);
 
 // kernels.cu launchers (all asynchronous on h.stream; return cudaError_t as int)
-// consistency_only (mixed precision): FP32 products, for the search-space blocks
-// whose products need only match the stored block (see k_spmm_f32)
-int launch_spmm(Handle& h, const double* X, double* YA, double* YM, int ncols, int consistency_only = 0);
+int launch_spmm(Handle& h, const double* X, double* YA, double* YM, int ncols);
 int launch_csr_times_dense(const CsrDev& P, const double* D, int ldd, int ncols, double* Y, int ldy,
                            cudaStream_t s);
 int launch_residual(Handle& h, const double* AX, const double* MX, const double* lam, double* rho);
@@ -145,6 +143,7 @@ size_t gram_partial_doubles(int64_t n, int k, int nu, int nvb, int sym);
 int launch_gram_raw(int64_t n, int k, int nu, const double* const* U, int nvb, int nv, const double* const* V1,
                     const double* const* V2, int sym, double* out1, double* out2, double* partial,
                     size_t partial_capacity, cudaStream_t stream);
+// consistency_only (mixed precision): FP32 update, for the previous-update block P
 int launch_combine_rows(Handle& h, int nin, const double* const* Win, const double* C, int ldc,
                         int csub, const double* Zadd, double* out, double alpha, int consistency_only = 0);
 int launch_rr(Handle& h, int m, const double* G, const double* Hm, const double* lam_old, double* C,

@@ -526,59 +526,12 @@ __global__ void __launch_bounds__(256) k_spmm_dw(int n, const int64_t* __restric
   }
 }
 
-// The same products in FP32 (hi parts of K, M and X, FP32 accumulation) for
-// blocks whose products only have to be consistent with the stored block: the
-// correction t and the previous-update block P of the search space.  Their
-// Gram entries with the current iterate are taken from the exact products of
-// the iterate, so the FP32 error reaches only the entries between correction
-// and previous-update directions, whose Ritz coefficients vanish as the
-// iteration converges.
-template <int LANES, int CPL>
-__global__ void __launch_bounds__(256) k_spmm_f32(int n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                                                  const float2* __restrict__ va, const float2* __restrict__ vm,
-                                                  const double* __restrict__ X, double* __restrict__ YA,
-                                                  double* __restrict__ YM, int ncols) {
-  constexpr int RPW = 32 / LANES;
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t row = warp * RPW + lane / LANES;
-  const int j0 = lane % LANES;
-  if (row >= n) return;
-  float a[CPL], m[CPL];
-#pragma unroll
-  for (int c = 0; c < CPL; ++c) {
-    a[c] = 0.f;
-    m[c] = 0.f;
-  }
-  for (int64_t e = rp[row]; e < rp[row + 1]; ++e) {
-    const int64_t col = ci[e];
-    const float av = va[e].x;
-    const float mv = vm ? vm[e].x : 0.f;
-    const double* xr = X + col * ncols;
-#pragma unroll
-    for (int c = 0; c < CPL; ++c) {
-      const int j = j0 + LANES * c;
-      if (j < ncols) {
-        const float x = f64_hi(xr[j]);
-        a[c] = fmaf(av, x, a[c]);
-        m[c] = fmaf(mv, x, m[c]);
-      }
-    }
-  }
-#pragma unroll
-  for (int c = 0; c < CPL; ++c) {
-    const int j = j0 + LANES * c;
-    if (j < ncols) {
-      YA[row * ncols + j] = f32_to_f64_bits(a[c]);
-      if (YM) YM[row * ncols + j] = f32_to_f64_bits(m[c]);
-    }
-  }
-}
-
 // Row-wise block update in FP32 (hi parts of W and C):
 // out[r, j] = Zadd[r, j] + sign * sum_b sum_a W_b[r, a] C[(b k + a) ldc + j],
-// for the blocks of the search space that need no more than consistency (see
-// k_spmm_f32).  A block stages kCombRows rows of W and the coefficients.
+// for the previous-update block P of the search space, which only has to be
+// consistent with its own products K P and M P (formed afterwards in
+// double-word arithmetic from the stored P).  A block stages kCombRows rows of
+// W and the coefficients.
 __global__ void __launch_bounds__(256) k_combine_f32(int64_t n, int k, int nin, Ptrs6 W, const double* __restrict__ C,
                                                      int ldc, int csub, const double* __restrict__ Zadd,
                                                      double* __restrict__ out, float sign) {
@@ -985,14 +938,7 @@ __global__ void __launch_bounds__(128, (BMAX <= 32) ? 4 : ((BMAX <= 40) ? 3 : 2)
 }
 
 // ---------------------------------------------------------------------------
-// Local solves, register window + TMA-streamed band (FP32).  One CTA of four
-// warps per (subdomain l, four shifts): the warps share the band rows of
-// K_l and M_l, which enter shared memory one window group (BMAX rows) ahead
-// through 1-D bulk tensor copies completing on an mbarrier; each warp runs the
-// banded factorisation of its own shift with the window in registers (lane v
-// owns window columns v and v + 32, slot u = row mod BMAX) and stores the
-// columns of L in slot order.  The FP32 band is stored with width BMAX (zero
-// padded on the left), so that window slot and band position map statically.
+// Bulk-copy and mbarrier helpers (inline PTX).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -1030,483 +976,6 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 }
 
 constexpr int kLocalWarps = 4;
-
-template <int BMAX>
-__global__ void __launch_bounds__(128, (BMAX <= 32) ? 4 : ((BMAX <= 40) ? 3 : 2)) k_local_band_tma(
-    int nsub, int k, const int64_t* __restrict__ sub_ptr, const int32_t* __restrict__ sub_dofs,
-    const float* __restrict__ bandK, const float* __restrict__ bandM, const double* __restrict__ lam,
-    const double* __restrict__ rho, float* __restrict__ Lbuf, float* __restrict__ wpk, int32_t* err) {
-  constexpr int NC = (BMAX + 31) / 32;
-  constexpr unsigned FULL = 0xffffffffu;
-  constexpr uint32_t kChunkBytes = BMAX * BMAX * sizeof(float);
-  __shared__ __align__(128) float sK[2][BMAX * BMAX];
-  __shared__ __align__(128) float sM[2][BMAX * BMAX];
-  __shared__ __align__(16) float sw[kLocalWarps][4][64];
-  __shared__ __align__(8) uint64_t bars[2];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int groups_per_sub = (k + kLocalWarps - 1) / kLocalWarps;
-  const int l = blockIdx.x / groups_per_sub;
-  const int i = (blockIdx.x % groups_per_sub) * kLocalWarps + wib;
-  const bool active = (i < k);
-  const int ii = active ? i : 0;
-  float* sl = sw[wib][0];
-  float* sa = sw[wib][1];
-  float* xs = sw[wib][2];
-  float* sr = sw[wib][3];
-  const int64_t off = sub_ptr[l];
-  const int nl = (int)(sub_ptr[l + 1] - off);
-  const int32_t* dofs = sub_dofs + off;
-  const float lm = (float)lam[ii];
-  float* Lp = Lbuf + ((size_t)off * k + (size_t)ii * nl) * BMAX;
-  const float* gK = bandK + (size_t)off * BMAX;  // band row p at gK + p * BMAX, diagonal at BMAX - 1
-  const float* gM = bandM + (size_t)off * BMAX;
-  const int ngroups = (nl + BMAX - 1) / BMAX;
-  // chunk c = band rows [BMAX (c + 1), BMAX (c + 2)) ∩ [0, nl): the rows entering during group c
-  auto issue_chunk = [&](int c) {
-    const int r0 = BMAX * (c + 1);
-    if (r0 >= nl) return;
-    const int rows = min(BMAX, nl - r0);
-    const uint32_t bytes = (uint32_t)rows * BMAX * sizeof(float);
-    uint64_t* bar = &bars[c & 1];
-    mbar_expect_tx(bar, 2 * bytes);
-    bulk_load(sK[c & 1], gK + (size_t)r0 * BMAX, bytes, bar);
-    bulk_load(sM[c & 1], gM + (size_t)r0 * BMAX, bytes, bar);
-  };
-  if (threadIdx.x == 0) {
-    mbar_init(&bars[0], 1);
-    mbar_init(&bars[1], 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) issue_chunk(0);
-  (void)kChunkBytes;
-  // initial window rows 0..BMAX-1 straight from global memory
-  auto a0 = [&](int p, int q) -> float {  // q <= p < BMAX
-    if (p >= nl) return (p == q) ? 1.f : 0.f;
-    const int e = BMAX - 1 - (p - q);
-    return gK[(size_t)p * BMAX + e] - lm * gM[(size_t)p * BMAX + e];
-  };
-  auto rhs = [&](int p) -> float { return (p < nl) ? (float)rho[(int64_t)dofs[p] * k + ii] : 0.f; };
-  float w[NC][BMAX];
-  float rw[NC];
-#pragma unroll
-  for (int c = 0; c < NC; ++c) {
-    const int v = lane + 32 * c;
-#pragma unroll
-    for (int u = 0; u < BMAX; ++u) {
-      float x = 0.f;
-      if (v < BMAX) x = (u >= v) ? a0(u, v) : a0(v, u);
-      w[c][u] = x;
-    }
-    rw[c] = (v < BMAX) ? rhs(v) : 0.f;
-  }
-  // right-hand sides of the rows entering in group c are staged in sr[] at the
-  // start of group c; rn holds those of the next group (loaded one group ahead)
-  float rn[NC];
-#pragma unroll
-  for (int c = 0; c < NC; ++c) {
-    const int v = lane + 32 * c;
-    rn[c] = (v < BMAX) ? rhs(BMAX + v) : 0.f;
-  }
-  bool bad = false, timeout = false;
-  for (int g = 0; g < ngroups; ++g) {
-    const int j0 = g * BMAX;
-    __syncthreads();  // every warp is done with group g - 1: its buffer may be refilled
-    if (threadIdx.x == 0) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue_chunk(g + 1);
-    }
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      const int v = lane + 32 * c;
-      if (v < BMAX) sr[v] = rn[c];
-      rn[c] = (v < BMAX) ? rhs(BMAX * (g + 2) + v) : 0.f;
-    }
-    const bool have_chunk = BMAX * (g + 1) < nl;
-    if (have_chunk && !mbar_wait_bounded(&bars[g & 1], (uint32_t)((g >> 1) & 1))) timeout = true;
-    __syncwarp();
-    const float* cK = sK[g & 1];
-    const float* cM = sM[g & 1];
-    int zero;
-    asm volatile("mov.u32 %0, 0;" : "=r"(zero));
-    const int vl = lane + zero;
-#pragma unroll
-    for (int s = 0; s < BMAX; ++s) {
-      const int j = j0 + s;
-      if (j >= nl) break;
-      const int sc = s >> 5, so = s & 31;
-      float piv = __shfl_sync(FULL, w[sc][s], so);
-      if (!(piv > 0.f)) {
-        bad = true;
-        piv = 1.f;
-      }
-      const float inv = rsqrtf(piv);
-      const float yj = __shfl_sync(FULL, rw[sc], so) * inv;
-      float lc[NC];
-#pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        const int v = vl + 32 * c;
-        lc[c] = (v != s) ? w[c][s] * inv : 0.f;
-        if (v < BMAX) {
-          if (active) Lp[(size_t)j * BMAX + v] = (v == s) ? inv : lc[c];
-          sl[v] = lc[c];
-        }
-      }
-      if (lane == 0 && active) wpk[(off + j) * k + ii] = yj;
-      __syncwarp();
-#pragma unroll
-      for (int u4 = 0; u4 < BMAX; u4 += 4) {
-        const float4 q = *reinterpret_cast<const float4*>(sl + u4);
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-          w[c][u4 + 0] = fmaf(-q.x, lc[c], w[c][u4 + 0]);
-          w[c][u4 + 1] = fmaf(-q.y, lc[c], w[c][u4 + 1]);
-          w[c][u4 + 2] = fmaf(-q.z, lc[c], w[c][u4 + 2]);
-          w[c][u4 + 3] = fmaf(-q.w, lc[c], w[c][u4 + 3]);
-        }
-      }
-#pragma unroll
-      for (int c = 0; c < NC; ++c) rw[c] = fmaf(-lc[c], yj, rw[c]);
-      // row pn = j + BMAX enters slot s; column v receives entry (pn, j + t),
-      // t = (v - s) mod BMAX in 1..BMAX, band position t - 1
-      const int pn = j + BMAX;
-      const bool real = pn < nl;
-#pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        const int v = vl + 32 * c;
-        if (v < BMAX) {
-          int t = v - s;
-          t += (t <= 0) ? BMAX : 0;
-          float a;
-          if (real)
-            a = cK[s * BMAX + t - 1] - lm * cM[s * BMAX + t - 1];
-          else
-            a = (t == BMAX) ? 1.f : 0.f;
-          w[c][s] = a;
-          sa[v] = a;
-        }
-      }
-      __syncwarp();
-      if (lane == so) {
-#pragma unroll
-        for (int u4 = 0; u4 < BMAX; u4 += 4) {
-          const float4 q = *reinterpret_cast<const float4*>(sa + u4);
-          w[sc][u4 + 0] = q.x;
-          w[sc][u4 + 1] = q.y;
-          w[sc][u4 + 2] = q.z;
-          w[sc][u4 + 3] = q.w;
-        }
-        rw[sc] = sr[s];
-      }
-      __syncwarp();
-    }
-  }
-  if (bad || timeout) {
-    if (lane == 0 && active) atomicOr(err, timeout ? 2 : 1);
-  }
-  if (bad || timeout || !active) return;
-  // backward substitution with L^T: x window by slot in shared memory; row j of L
-  // holds 1/L_jj at slot j mod BMAX and L(row(v), j) at slot v.  A ring of PB
-  // rows is prefetched.
-  constexpr int PB = 4;
-  for (int v = lane; v < BMAX; v += 32) xs[v] = 0.f;
-  __syncwarp();
-  float lr[PB][NC], yv[PB];
-  auto load_row = [&](int j, int d) {
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      const int v = lane + 32 * c;
-      lr[d][c] = (j >= 0 && v < BMAX) ? Lp[(size_t)j * BMAX + v] : 0.f;
-    }
-    yv[d] = (j >= 0) ? wpk[(off + j) * k + ii] : 0.f;
-  };
-#pragma unroll
-  for (int d = 0; d < PB; ++d) load_row(nl - 1 - d, d);
-  int j = nl - 1;
-  while (j >= 0) {
-#pragma unroll
-    for (int d = 0; d < PB; ++d) {
-      if (j >= 0) {
-        const int s = j % BMAX;
-        float part = 0.f;
-        float invj = 0.f;
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-          const int v = lane + 32 * c;
-          if (v < BMAX) {
-            if (v == s)
-              invj = lr[d][c];
-            else
-              part = fmaf(lr[d][c], xs[v], part);
-          }
-        }
-        const float y = yv[d];
-        load_row(j - PB, d);
-        part = warp_sum(part);
-        invj = warp_sum(invj);
-        const float xj = (y - part) * invj;
-        __syncwarp();
-        if (lane == 0) {
-          xs[s] = xj;
-          wpk[(off + j) * k + ii] = xj;
-        }
-        __syncwarp();
-        --j;
-      }
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Local solves, forward phase: banded Cholesky factorisation of K_l - lambda_i
-// M_l with the forward substitution L y = rho_l (FP32, window BMAX a multiple
-// of 8, at most 48).  One CTA of four warps per (subdomain l, four shifts), one
-// warp per shift.  The symmetric window (slot u = row mod BMAX) is spread over
-// the warp as a 4 x 8 grid of lanes: lane (rg, cg) holds the TR x TC tile of
-// slot rows rg TR .. and slot columns cg TC .. in registers (TR = 2 TC, so row
-// group rg covers column groups 2 rg and 2 rg + 1).  Per elimination step the
-// four lanes of the pivot column publish the raw column in shared memory
-// (column-group-major, each group padded to TCP floats for 16-byte vector
-// access); after one warp barrier every lane reads the TR + TC entries it
-// needs and applies its rank-one update; the entries of the pivot slot are
-// then replaced by the entering band row.  The band chunk of K_l and M_l
-// enters shared memory through two bulk copies per window group, shared by the
-// four warps; each warp turns it into the shifted rows K - lambda M laid out
-// by slot (padded like the published column), so that the entering entries of
-// a lane are one or two vector loads.  The right-hand side rows are spread
-// over the lanes (slot rg TR + a at lane rg 8 + a mod 8) and eliminated
-// alongside.  Outputs: the columns of L in slot order (1/L_jj at the pivot
-// slot) and y in place of the right-hand side.
-// ---------------------------------------------------------------------------
-template <int BMAX>
-struct TileShape {
-  static constexpr int TR = BMAX / 4, TC = BMAX / 8;
-  static constexpr int TCP = (TC + 3) / 4 * 4;  // padded column group
-  static constexpr int ROW = 8 * TCP;           // padded slot vector
-  static constexpr int BB = BMAX * BMAX;
-  static constexpr size_t smem_floats = (size_t)2 * BB + (size_t)kLocalWarps * (BMAX * ROW + 2 * ROW + BMAX);
-};
-
-template <int BMAX>
-__global__ void __launch_bounds__(128, (BMAX <= 32) ? 4 : 3) k_local_factor_tile(
-    int nsub, int k, const int64_t* __restrict__ sub_ptr, const int32_t* __restrict__ sub_dofs,
-    const float* __restrict__ bandK, const float* __restrict__ bandM, const double* __restrict__ lam,
-    const double* __restrict__ rho, float* __restrict__ Lbuf, float* __restrict__ wpk, int32_t* err) {
-  using S = TileShape<BMAX>;
-  constexpr int TR = S::TR, TC = S::TC, TCP = S::TCP, ROW = S::ROW, BB = S::BB;
-  static_assert(BMAX % 8 == 0 && BMAX <= 48, "window must be a multiple of 8, at most 48");
-  constexpr int NR = (TR + 7) / 8;  // right-hand-side registers per lane
-  constexpr unsigned FULL = 0xffffffffu;
-  extern __shared__ __align__(128) float tsm[];
-  float* sK = tsm;                                // [BB] band chunk of K_l
-  float* sM = sK + BB;                            // [BB] band chunk of M_l
-  float* wbase = sM + BB;
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  float* Aw = wbase + (size_t)wib * (BMAX * ROW + 2 * ROW + BMAX);  // [BMAX][ROW] shifted rows by slot
-  float* slw = Aw + BMAX * ROW;                                      // [2][ROW] published columns
-  float* srw = slw + 2 * ROW;                                        // [BMAX] rhs of entering rows
-  __shared__ __align__(8) uint64_t bar;
-  const int rg = lane >> 3, cg = lane & 7;
-  const int groups_per_sub = (k + kLocalWarps - 1) / kLocalWarps;
-  const int l = blockIdx.x / groups_per_sub;
-  const int i = (blockIdx.x % groups_per_sub) * kLocalWarps + wib;
-  const bool active = (i < k);
-  const int ii = active ? i : 0;
-  const int64_t off = sub_ptr[l];
-  const int nl = (int)(sub_ptr[l + 1] - off);
-  const int32_t* dofs = sub_dofs + off;
-  const float lm = (float)lam[ii];
-  float* Lp = Lbuf + ((size_t)off * k + (size_t)ii * nl) * BMAX;
-  const float* gK = bandK + (size_t)off * BMAX;  // band row p at gK + p * BMAX, diagonal at BMAX - 1
-  const float* gM = bandM + (size_t)off * BMAX;
-  const int ngroups = (nl + BMAX - 1) / BMAX;
-  auto pidx = [](int u) { return (u / TC) * TCP + u % TC; };  // padded position of slot u
-  // chunk c = band rows [BMAX (c + 1), BMAX (c + 2)) ∩ [0, nl): the rows entering during group c
-  auto issue_chunk = [&](int c) {
-    const int r0 = BMAX * (c + 1);
-    if (r0 >= nl) return;
-    const int rows = min(BMAX, nl - r0);
-    const uint32_t bytes = (uint32_t)rows * BMAX * sizeof(float);
-    mbar_expect_tx(&bar, 2 * bytes);
-    bulk_load(sK, gK + (size_t)r0 * BMAX, bytes, &bar);
-    bulk_load(sM, gM + (size_t)r0 * BMAX, bytes, &bar);
-  };
-  if (threadIdx.x == 0) {
-    mbar_init(&bar, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) issue_chunk(0);
-  // initial window rows 0..BMAX-1 straight from global memory
-  auto a0 = [&](int p, int q) -> float {  // q <= p < BMAX
-    if (p >= nl) return (p == q) ? 1.f : 0.f;
-    const int e = BMAX - 1 - (p - q);
-    return gK[(size_t)p * BMAX + e] - lm * gM[(size_t)p * BMAX + e];
-  };
-  auto rhs = [&](int p) -> float { return (p < nl) ? (float)rho[(int64_t)dofs[p] * k + ii] : 0.f; };
-  float w[TR][TC];
-#pragma unroll
-  for (int a = 0; a < TR; ++a)
-#pragma unroll
-    for (int b = 0; b < TC; ++b) {
-      const int u = rg * TR + a, v = cg * TC + b;
-      w[a][b] = (u >= v) ? a0(u, v) : a0(v, u);
-    }
-  // right-hand side rows held by this lane: slot rg TR + cg + 8 q
-  float r[NR];
-  int ridx[NR];
-#pragma unroll
-  for (int q = 0; q < NR; ++q) {
-    const int a = cg + 8 * q;
-    r[q] = (a < TR) ? rhs(rg * TR + a) : 0.f;
-    ridx[q] = (a < TR) ? pidx(rg * TR + a) : 0;
-  }
-  // published-column positions of the slots this lane stores to L
-  const int lidx0 = (lane < BMAX) ? pidx(lane) : 0;
-  const int lidx1 = (lane + 32 < BMAX) ? pidx(lane + 32) : 0;
-  // right-hand sides of the rows entering in group g + 1 (one group ahead)
-  float rn[2];
-#pragma unroll
-  for (int c = 0; c < 2; ++c) {
-    const int v = lane + 32 * c;
-    rn[c] = (v < BMAX) ? rhs(BMAX + v) : 0.f;
-  }
-  bool bad = false, timeout = false;
-  float* yout = wpk + off * k + ii;  // y_j at yout[j k]
-  for (int g = 0; g < ngroups; ++g) {
-    const int j0 = g * BMAX;
-    const bool have_chunk = BMAX * (g + 1) < nl;
-    __syncwarp();  // the previous group's reads of the shifted rows and staged rhs are done
-    if (have_chunk && !timeout && !mbar_wait_bounded(&bar, (uint32_t)(g & 1))) timeout = true;
-    // shifted rows by slot: Aw[s][pidx(v)] = (K - lambda M)(row B(g+1)+s, column of slot v),
-    // the band position of that entry being (v - s - 1) mod BMAX (identity beyond nl)
-    {
-      const int r0 = BMAX * (g + 1);
-      for (int e = lane; e < BMAX * 8; e += 32) {
-        const int s = e >> 3, c = e & 7;  // row s, column group c
-        const bool real = (r0 + s < nl) && !timeout;
-        float o[TCP];
-#pragma unroll
-        for (int b = 0; b < TCP; ++b) {
-          int t = c * TC + b + (BMAX - 1 - s);
-          t -= (t >= BMAX) ? BMAX : 0;
-          float x = 0.f;
-          if (b < TC) {
-            if (real)
-              x = fmaf(-lm, sM[s * BMAX + t], sK[s * BMAX + t]);
-            else
-              x = (t == BMAX - 1) ? 1.f : 0.f;
-          }
-          o[b] = x;
-        }
-#pragma unroll
-        for (int b4 = 0; b4 < TCP; b4 += 4)
-          *reinterpret_cast<float4*>(Aw + s * ROW + c * TCP + b4) = make_float4(o[b4], o[b4 + 1], o[b4 + 2], o[b4 + 3]);
-      }
-#pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        const int v = lane + 32 * c;
-        if (v < BMAX) srw[v] = rn[c];
-        rn[c] = (v < BMAX) ? rhs(BMAX * (g + 2) + v) : 0.f;
-      }
-    }
-    __syncthreads();  // every warp has its shifted rows: the K/M buffer may be refilled
-    if (threadIdx.x == 0 && !timeout) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue_chunk(g + 1);
-    }
-    int zero;
-    asm volatile("mov.u32 %0, 0;" : "=r"(zero));
-    const int rgz = rg + zero, cgz = cg + zero;
-    float* Lg = Lp + (size_t)j0 * BMAX;
-    float* yg = yout + (size_t)j0 * k;
-#pragma unroll
-    for (int s = 0; s < BMAX; ++s) {
-      const int j = j0 + s;
-      if (j >= nl) break;
-      const int orr = s / TR, oc = s / TC;  // row and column group of slot s
-      const float piv = __shfl_sync(FULL, w[s % TR][s % TC], orr * 8 + oc);
-      const float rj = __shfl_sync(FULL, r[(s % TR) / 8], orr * 8 + (s % TR) % 8);
-      bad |= !(piv > 0.f);
-      const float inv = rsqrtf(piv);
-      const float inv2 = inv * inv;
-      const float yj = rj * inv;
-      float* slb = slw + (s & 1) * ROW;
-      if (cgz == oc) {  // publish the raw pivot column: this lane's TR slots = column groups 2 rg, 2 rg + 1
-#pragma unroll
-        for (int hf = 0; hf < 2; ++hf)
-#pragma unroll
-          for (int b4 = 0; b4 < TCP; b4 += 4) {
-            float4 o;
-            o.x = (b4 + 0 < TC) ? w[hf * TC + b4 + 0][s % TC] : 0.f;
-            o.y = (b4 + 1 < TC) ? w[hf * TC + b4 + 1][s % TC] : 0.f;
-            o.z = (b4 + 2 < TC) ? w[hf * TC + b4 + 2][s % TC] : 0.f;
-            o.w = (b4 + 3 < TC) ? w[hf * TC + b4 + 3][s % TC] : 0.f;
-            *reinterpret_cast<float4*>(slb + (2 * rgz + hf) * TCP + b4) = o;
-          }
-      }
-      __syncwarp();
-      if (active) {
-        if (lane < BMAX) Lg[s * BMAX + lane] = (lane == s) ? inv : slb[lidx0] * inv;
-        if (lane + 32 < BMAX) Lg[s * BMAX + lane + 32] = (lane + 32 == s) ? inv : slb[lidx1] * inv;
-        if (lane == 0) yg[(size_t)s * k] = yj;
-      }
-      float lr[TR], lc[TCP];
-#pragma unroll
-      for (int hf = 0; hf < 2; ++hf)
-#pragma unroll
-        for (int b4 = 0; b4 < TCP; b4 += 4) {
-          const float4 q = *reinterpret_cast<const float4*>(slb + (2 * rgz + hf) * TCP + b4);
-          if (b4 + 0 < TC) lr[hf * TC + b4 + 0] = q.x;
-          if (b4 + 1 < TC) lr[hf * TC + b4 + 1] = q.y;
-          if (b4 + 2 < TC) lr[hf * TC + b4 + 2] = q.z;
-          if (b4 + 3 < TC) lr[hf * TC + b4 + 3] = q.w;
-        }
-#pragma unroll
-      for (int b4 = 0; b4 < TCP; b4 += 4) {
-        const float4 q = *reinterpret_cast<const float4*>(slb + cgz * TCP + b4);
-        lc[b4 + 0] = q.x * inv2;
-        lc[b4 + 1] = q.y * inv2;
-        lc[b4 + 2] = q.z * inv2;
-        lc[b4 + 3] = q.w * inv2;
-      }
-#pragma unroll
-      for (int a = 0; a < TR; ++a)
-#pragma unroll
-        for (int b = 0; b < TC; ++b) w[a][b] = fmaf(-lr[a], lc[b], w[a][b]);
-      const float yi = yj * inv;  // the raw column times y_j / sqrt(pivot)
-#pragma unroll
-      for (int q = 0; q < NR; ++q)
-        if (cgz + 8 * q < TR) r[q] = fmaf(-slb[ridx[q]], yi, r[q]);
-      // band row j + BMAX enters slot s
-      const float* arow = Aw + s * ROW;
-      if (rgz == orr) {
-#pragma unroll
-        for (int b4 = 0; b4 < TCP; b4 += 4) {
-          const float4 q = *reinterpret_cast<const float4*>(arow + cgz * TCP + b4);
-          if (b4 + 0 < TC) w[s % TR][b4 + 0] = q.x;
-          if (b4 + 1 < TC) w[s % TR][b4 + 1] = q.y;
-          if (b4 + 2 < TC) w[s % TR][b4 + 2] = q.z;
-          if (b4 + 3 < TC) w[s % TR][b4 + 3] = q.w;
-        }
-      }
-      if (cgz == oc) {
-#pragma unroll
-        for (int hf = 0; hf < 2; ++hf)
-#pragma unroll
-          for (int b4 = 0; b4 < TCP; b4 += 4) {
-            const float4 q = *reinterpret_cast<const float4*>(arow + (2 * rgz + hf) * TCP + b4);
-            if (b4 + 0 < TC) w[hf * TC + b4 + 0][s % TC] = q.x;
-            if (b4 + 1 < TC) w[hf * TC + b4 + 1][s % TC] = q.y;
-            if (b4 + 2 < TC) w[hf * TC + b4 + 2][s % TC] = q.z;
-            if (b4 + 3 < TC) w[hf * TC + b4 + 3][s % TC] = q.w;
-          }
-      }
-      if (lane == orr * 8 + (s % TR) % 8) r[(s % TR) / 8] = srw[s];
-    }
-  }
-  if ((bad || timeout) && lane == 0 && active) atomicOr(err, timeout ? 2 : 1);
-}
 
 // ---------------------------------------------------------------------------
 // Local solves, forward phase, blocked: banded Cholesky factorisation of
@@ -3477,7 +2946,7 @@ void prof_flush(Handle& h) {
 // ===========================================================================
 // launchers
 // ===========================================================================
-int launch_spmm(Handle& h, const double* X, double* YA, double* YM, int ncols, int consistency_only) {
+int launch_spmm(Handle& h, const double* X, double* YA, double* YM, int ncols) {
   ProfScope ps(h, BPJD_PROF_SPMM);
   const int n = h.n;
   auto go = [&](auto lanes_tag, const CsrDev& A, const double* vm, double* ya, double* ym) {
@@ -3497,12 +2966,7 @@ int launch_spmm(Handle& h, const double* X, double* YA, double* YM, int ncols, i
       constexpr int RPW = 32 / LANES;
       int64_t warps = (n + RPW - 1) / RPW;
       int64_t blocks = (warps * 32 + 255) / 256;
-      if (consistency_only)
-        k_spmm_f32<LANES, CPL><<<(unsigned)blocks, 256, 0, h.stream>>>(n, A.row_ptr, A.col, va, vm, X, ya, ym,
-                                                                        ncols);
-      else
-        k_spmm_dw<LANES, CPL><<<(unsigned)blocks, 256, 0, h.stream>>>(n, A.row_ptr, A.col, va, vm, X, ya, ym,
-                                                                       ncols);
+      k_spmm_dw<LANES, CPL><<<(unsigned)blocks, 256, 0, h.stream>>>(n, A.row_ptr, A.col, va, vm, X, ya, ym, ncols);
       h.launches += 1;
     };
     using I = std::integral_constant<int, 1>;
