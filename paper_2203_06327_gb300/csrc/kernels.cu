@@ -1979,6 +1979,31 @@ __device__ __forceinline__ dw dw_lin2(dw f1, float x1h, float x1l, dw f2, float 
   return dw_renorm(a.s, a.c);
 }
 
+// Round-robin pairings of the parallel cyclic Jacobi (circle method), for
+// mp (even) indices: round r pairs index 0 with ring(0) and ring(i) with
+// ring(mp - 1 - i), ring(x) = (x + r) mod (mp - 1) + 1.  Written once per
+// solve into tp/tq[r half + i], i < half = mp / 2.
+__device__ void jacobi_pair_tables(int mp, unsigned char* tp, unsigned char* tq) {
+  const int half = mp / 2;
+  for (int t = threadIdx.x; t < (mp - 1) * half; t += blockDim.x) {
+    const int round = t / half, i = t % half;
+    auto ring = [&](int pos) { return ((pos + round) % (mp - 1)) + 1; };
+    const int e0 = (i == 0) ? 0 : ring(i);
+    const int e1 = (i == 0) ? ring(0) : ring(mp - 1 - i);
+    tp[t] = (unsigned char)min(e0, e1);
+    tq[t] = (unsigned char)max(e0, e1);
+  }
+}
+
+// Entry (r, c), c <= r, of the lower triangle with linear index t = r (r + 1) / 2 + c.
+__device__ __forceinline__ void tri_entry(int t, int& r, int& c) {
+  int rr = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
+  while (rr * (rr + 1) / 2 > t) --rr;
+  while ((rr + 1) * (rr + 2) / 2 <= t) ++rr;
+  r = rr;
+  c = t - rr * (rr + 1) / 2;
+}
+
 __device__ int jacobi_eig_dw(float* Ah, float* Al, float* A2h, float* A2l, float* Vh, float* Vl, float* V2h,
                              float* V2l, int m, float** Aoh, float** Aol, float** Voh, float** Vol, dw* fr, dw* gr,
                              int* partner) {
@@ -1986,7 +2011,7 @@ __device__ int jacobi_eig_dw(float* Ah, float* Al, float* A2h, float* A2l, float
   const int ld = kRRMax;
   const int tid = threadIdx.x;
   __shared__ int done;
-  __shared__ unsigned char tri_r[kRRMax * (kRRMax + 1) / 2], tri_c[kRRMax * (kRRMax + 1) / 2];
+  __shared__ unsigned char tp[kRRMax * kRRMax / 2], tq[kRRMax * kRRMax / 2];
   for (int t = tid; t < mp * ld; t += blockDim.x) {
     const int r = t / ld, c = t % ld;
     Vh[t] = (r == c) ? 1.f : 0.f;
@@ -1996,14 +2021,23 @@ __device__ int jacobi_eig_dw(float* Ah, float* Al, float* A2h, float* A2l, float
       Al[t] = 0.f;
     }
   }
-  if (tid == 0) {
-    int t = 0;
-    for (int r = 0; r < mp; ++r)
-      for (int c = 0; c <= r; ++c) {
-        tri_r[t] = (unsigned char)r;
-        tri_c[t] = (unsigned char)c;
-        ++t;
-      }
+  jacobi_pair_tables(mp, tp, tq);
+  // this thread's entries (the kernel runs 1024 threads): lower-triangle entries
+  // tid + u blockDim.x of A, entries tid + u blockDim.x of V
+  const int ntri = mp * (mp + 1) / 2;
+  int ar[3], ac[3];  // 3 x 1024 threads cover the 2080 entries of mp = 64
+  for (int u = 0; u < 3; ++u) {
+    const int t = tid + u * (int)blockDim.x;
+    if (t < ntri)
+      tri_entry(t, ar[u], ac[u]);
+    else
+      ar[u] = ac[u] = -1;
+  }
+  int vx[4], vr[4];
+  for (int u = 0; u < 4; ++u) {
+    const int t = tid + u * (int)blockDim.x;
+    vx[u] = (t < mp * mp) ? t / mp : -1;
+    vr[u] = (t < mp * mp) ? t % mp : 0;
   }
   __shared__ float amax_d;
   if (tid == 0) {
@@ -2018,19 +2052,22 @@ __device__ int jacobi_eig_dw(float* Ah, float* Al, float* A2h, float* A2l, float
   const int half = mp / 2;
   int sweep = 0;
   for (; sweep < 60; ++sweep) {
+    // a sweep runs only while some off-diagonal entry passes the rotation test
     if (tid == 0) done = 1;
     __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      if (ar[u] < 0 || ar[u] == ac[u]) continue;
+      const float apq = Ah[ar[u] * ld + ac[u]] + Al[ar[u] * ld + ac[u]];
+      if (fabsf(apq) > abs_floor &&
+          fabsf(apq) > 1e-15f * __fsqrt_rn(fabsf(Ah[ar[u] * ld + ar[u]] * Ah[ac[u] * ld + ac[u]])))
+        done = 0;
+    }
+    __syncthreads();
+    if (done) break;
     for (int round = 0; round < mp - 1; ++round) {
       if (tid < half) {
-        int e0 = 0, e1;
-        auto ring = [&](int pos) { return ((pos + round) % (mp - 1)) + 1; };
-        if (tid == 0) {
-          e1 = ring(0);
-        } else {
-          e0 = ring(tid);
-          e1 = ring(mp - 1 - tid);
-        }
-        const int p = min(e0, e1), q = max(e0, e1);
+        const int p = tp[round * half + tid], q = tq[round * half + tid];
         const float apq = Ah[p * ld + q] + Al[p * ld + q];
         const float app = Ah[p * ld + p], aqq = Ah[q * ld + q];
         dw c = {1.f, 0.f}, s = {0.f, 0.f};
@@ -2057,7 +2094,6 @@ __device__ int jacobi_eig_dw(float* Ah, float* Al, float* A2h, float* A2l, float
           float sh, se;
           two_prod(t, c.hi, sh, se);
           s = dw_renorm(sh, __fmaf_rn(t, c.lo, se));
-          done = 0;
         }
         fr[p] = c;
         gr[p] = dw{-s.hi, -s.lo};
@@ -2067,8 +2103,10 @@ __device__ int jacobi_eig_dw(float* Ah, float* Al, float* A2h, float* A2l, float
         partner[q] = p;
       }
       __syncthreads();
-      for (int t = tid; t < mp * (mp + 1) / 2; t += blockDim.x) {
-        const int r = tri_r[t], c = tri_c[t];
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        if (ar[u] < 0) continue;
+        const int r = ar[u], c = ac[u];
         const int rb = partner[r], cb = partner[c];
         const dw i1 = dw_lin2(fr[c], Ah[r * ld + c], Al[r * ld + c], gr[c], Ah[r * ld + cb], Al[r * ld + cb]);
         const dw i2 = dw_lin2(fr[c], Ah[rb * ld + c], Al[rb * ld + c], gr[c], Ah[rb * ld + cb], Al[rb * ld + cb]);
@@ -2078,8 +2116,10 @@ __device__ int jacobi_eig_dw(float* Ah, float* Al, float* A2h, float* A2l, float
         A2h[c * ld + r] = v.hi;
         A2l[c * ld + r] = v.lo;
       }
-      for (int t = tid; t < mp * mp; t += blockDim.x) {
-        const int x = t / mp, r = t % mp;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (vx[u] < 0) continue;
+        const int x = vx[u], r = vr[u];
         const int rb = partner[r];
         const dw v = dw_lin2(fr[r], Vh[x * ld + r], Vl[x * ld + r], gr[r], Vh[x * ld + rb], Vl[x * ld + rb]);
         V2h[x * ld + r] = v.hi;
@@ -2099,14 +2139,12 @@ __device__ int jacobi_eig_dw(float* Ah, float* Al, float* A2h, float* A2l, float
       Vl = V2l;
       V2l = t0;
     }
-    if (done) break;
-    __syncthreads();
   }
   *Aoh = Ah;
   *Aol = Al;
   *Voh = Vh;
   *Vol = Vl;
-  return sweep + 1;
+  return sweep;
 }
 
 // ---------------------------------------------------------------------------
@@ -2154,20 +2192,27 @@ __device__ int jacobi_f32(float* A, float* A2, float* V, float* V2, int m, float
   const int ld = kRRMax;
   const int tid = threadIdx.x;
   __shared__ int done;
-  __shared__ unsigned char tri_r[kRRMax * (kRRMax + 1) / 2], tri_c[kRRMax * (kRRMax + 1) / 2];
+  __shared__ unsigned char tp[kRRMax * kRRMax / 2], tq[kRRMax * kRRMax / 2];
   for (int t = tid; t < mp * ld; t += blockDim.x) {
     const int r = t / ld, c = t % ld;
     V[t] = (r == c) ? 1.f : 0.f;
     if ((r >= m || c >= m) && c < mp) A[t] = 0.f;
   }
-  if (tid == 0) {
-    int t = 0;
-    for (int r = 0; r < mp; ++r)
-      for (int c = 0; c <= r; ++c) {
-        tri_r[t] = (unsigned char)r;
-        tri_c[t] = (unsigned char)c;
-        ++t;
-      }
+  jacobi_pair_tables(mp, tp, tq);
+  const int ntri = mp * (mp + 1) / 2;
+  int ar[3], ac[3];  // 3 x 1024 threads cover the 2080 entries of mp = 64
+  for (int u = 0; u < 3; ++u) {
+    const int t = tid + u * (int)blockDim.x;
+    if (t < ntri)
+      tri_entry(t, ar[u], ac[u]);
+    else
+      ar[u] = ac[u] = -1;
+  }
+  int vx[4], vr[4];
+  for (int u = 0; u < 4; ++u) {
+    const int t = tid + u * (int)blockDim.x;
+    vx[u] = (t < mp * mp) ? t / mp : -1;
+    vr[u] = (t < mp * mp) ? t % mp : 0;
   }
   __syncthreads();
   const int half = mp / 2;
@@ -2182,19 +2227,22 @@ __device__ int jacobi_f32(float* A, float* A2, float* V, float* V2, int m, float
   const float abs_floor = 1e-6f * amax_f;
   int sweep = 0;
   for (; sweep < 30; ++sweep) {
+    // a sweep runs only while some off-diagonal entry passes the rotation test
     if (tid == 0) done = 1;
     __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      if (ar[u] < 0 || ar[u] == ac[u]) continue;
+      const float apq = A[ar[u] * ld + ac[u]];
+      if (fabsf(apq) > abs_floor &&
+          fabsf(apq) > off_tol * __fsqrt_rn(fabsf(A[ar[u] * ld + ar[u]] * A[ac[u] * ld + ac[u]])))
+        done = 0;
+    }
+    __syncthreads();
+    if (done) break;
     for (int round = 0; round < mp - 1; ++round) {
       if (tid < half) {
-        int e0 = 0, e1;
-        auto ring = [&](int pos) { return ((pos + round) % (mp - 1)) + 1; };
-        if (tid == 0) {
-          e1 = ring(0);
-        } else {
-          e0 = ring(tid);
-          e1 = ring(mp - 1 - tid);
-        }
-        const int p = min(e0, e1), q = max(e0, e1);
+        const int p = tp[round * half + tid], q = tq[round * half + tid];
         const float apq = A[p * ld + q], app = A[p * ld + p], aqq = A[q * ld + q];
         float c = 1.f, s = 0.f;
         if (fabsf(apq) > abs_floor && fabsf(apq) > off_tol * __fsqrt_rn(fabsf(app * aqq))) {
@@ -2203,7 +2251,6 @@ __device__ int jacobi_f32(float* A, float* A2, float* V, float* V2, int m, float
           const float t = __fdividef(tau >= 0.f ? 1.f : -1.f, fabsf(tau) + __fsqrt_rn(1.f + tau * tau));
           c = rsqrtf(1.f + t * t);
           s = t * c;
-          done = 0;
         }
         fr[p] = c;
         gr[p] = -s;
@@ -2213,16 +2260,20 @@ __device__ int jacobi_f32(float* A, float* A2, float* V, float* V2, int m, float
         partner[q] = p;
       }
       __syncthreads();
-      for (int t = tid; t < mp * (mp + 1) / 2; t += blockDim.x) {
-        const int r = tri_r[t], c = tri_c[t];
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        if (ar[u] < 0) continue;
+        const int r = ar[u], c = ac[u];
         const int rb = partner[r], cb = partner[c];
         const float v = fr[r] * (fr[c] * A[r * ld + c] + gr[c] * A[r * ld + cb]) +
                         gr[r] * (fr[c] * A[rb * ld + c] + gr[c] * A[rb * ld + cb]);
         A2[r * ld + c] = v;
         A2[c * ld + r] = v;
       }
-      for (int t = tid; t < mp * mp; t += blockDim.x) {
-        const int x = t / mp, r = t % mp;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (vx[u] < 0) continue;
+        const int x = vx[u], r = vr[u];
         V2[x * ld + r] = V[x * ld + r] * fr[r] + V[x * ld + partner[r]] * gr[r];
       }
       __syncthreads();
@@ -2233,12 +2284,10 @@ __device__ int jacobi_f32(float* A, float* A2, float* V, float* V2, int m, float
       V = V2;
       V2 = tV;
     }
-    if (done) break;
-    __syncthreads();
   }
   *Aout = A;
   *Vout = V;
-  return sweep + 1;
+  return sweep;
 }
 
 // G, H: the unscaled Gram matrices (FP64, m x m, ld m); sc: column scaling.
