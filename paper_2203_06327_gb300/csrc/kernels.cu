@@ -1663,14 +1663,17 @@ __global__ void k_prolong_add(int64_t n, int k, const int64_t* __restrict__ prp,
 // ordering) for the two small symmetric eigenproblems.
 // ---------------------------------------------------------------------------
 constexpr int kRRMax = 64;
+// leading dimension of the reduced matrices in shared memory: one more than the
+// size, so that column accesses fall into distinct banks
+constexpr int kRRLd = kRRMax + 1;
 
-// Symmetric eigen-decomposition of A (m x m, leading dimension ld = kRRMax) in
+// Symmetric eigen-decomposition of A (m x m, leading dimension ld = kRRLd) in
 // shared memory; V receives the eigenvectors (columns), A's diagonal the
 // eigenvalues.  mp = m rounded up to even (the extra index is a zero row/column
 // that never rotates).  Uses all threads of the block.
 __device__ void jacobi_eig(double* A, double* V, int m, double* cs, double* sn, int* pp, int* qq) {
   const int mp = m + (m & 1);
-  const int ld = kRRMax;
+  const int ld = kRRLd;
   const int tid = threadIdx.x;
   for (int t = tid; t < mp * ld; t += blockDim.x) {
     int r = t / ld, c = t % ld;
@@ -1748,7 +1751,7 @@ __device__ void jacobi_eig(double* A, double* V, int m, double* cs, double* sn, 
 
 // Ascending order of diag(A)[0..m): ord[rank] = index (ties by index).
 __device__ void sort_diag(const double* A, int m, int* ord) {
-  const int ld = kRRMax;
+  const int ld = kRRLd;
   for (int j = threadIdx.x; j < m; j += blockDim.x) {
     double dj = A[j * ld + j];
     int rank = 0;
@@ -1769,7 +1772,7 @@ __device__ void rayleigh_ritz_eig(int m, int k, const double* __restrict__ G, co
                                   double drop_tol, const double* __restrict__ lam_old, double* C, double* lam_new,
                                   double* hist_row, int stop_rule, double tol, DevStatus* st, double* rr,
                                   int scale_all) {
-  const int ld = kRRMax;
+  const int ld = kRRLd;
   double* A = rr;                  // ld x ld
   double* V = A + ld * ld;         // ld x ld
   double* Bm = V + ld * ld;        // ld x ld : basis of the kept directions (m x r)
@@ -1871,12 +1874,12 @@ __device__ void rayleigh_ritz_eig(int m, int k, const double* __restrict__ G, co
 // Parallel cyclic Jacobi, one pass per round: with the round's disjoint
 // rotations J, A' = J^T A J is formed element-wise from the old A (4 terms per
 // entry, lower triangle mirrored) into a second buffer, and V' = V J.
-// A, A2, V, V2 have leading dimension kRRMax; returns (via the buffers that end
+// A, A2, V, V2 have leading dimension kRRLd; returns (via the buffers that end
 // up holding the result) pointers in *Aout / *Vout.
 __device__ int jacobi_eig_sym(double* A, double* A2, double* V, double* V2, int m, double** Aout, double** Vout,
                               double* fr, double* gr, int* partner) {
   const int mp = m + (m & 1);
-  const int ld = kRRMax;
+  const int ld = kRRLd;
   const int tid = threadIdx.x;
   __shared__ int done;
   for (int t = tid; t < mp * ld; t += blockDim.x) {
@@ -1959,7 +1962,7 @@ __device__ int jacobi_eig_sym(double* A, double* A2, double* V, double* V2, int 
 }
 
 // Parallel cyclic Jacobi in double-word arithmetic (planes *h, *l of hi/lo
-// floats, leading dimension kRRMax).  The rotation angle of a pair is chosen
+// floats, leading dimension kRRLd).  The rotation angle of a pair is chosen
 // in FP32 (t = tan of the angle); c = 1 / sqrt(1 + t^2) and s = t c are then
 // formed in double-word precision (one Newton step on the FP32 estimate), so
 // every rotation is orthogonal to double-word accuracy and only its
@@ -2008,7 +2011,7 @@ __device__ int jacobi_eig_dw(float* Ah, float* Al, float* A2h, float* A2l, float
                              float* V2l, int m, float** Aoh, float** Aol, float** Voh, float** Vol, dw* fr, dw* gr,
                              int* partner) {
   const int mp = m + (m & 1);
-  const int ld = kRRMax;
+  const int ld = kRRLd;
   const int tid = threadIdx.x;
   __shared__ int done;
   __shared__ unsigned char tp[kRRMax * kRRMax / 2], tq[kRRMax * kRRMax / 2];
@@ -2149,7 +2152,7 @@ __device__ int jacobi_eig_dw(float* Ah, float* Al, float* A2h, float* A2l, float
 
 // ---------------------------------------------------------------------------
 // Mixed-precision Rayleigh-Ritz solve of the scaled pencil (H', G') (FP64 in
-// Gd, Hd, leading dimension kRRMax):
+// Gd, Hd, leading dimension kRRLd):
 //  phase A (FP32): G' = L L^T, B = L^{-T}, Jacobi on B^T H' B, Q = B V
 //                  -- an approximate G'-orthonormal eigenbasis;
 //  phase B (double-word): G2 = Q^T G' Q = I + E, S = I - E/2 + 3E^2/8
@@ -2161,13 +2164,13 @@ __device__ int jacobi_eig_dw(float* Ah, float* Al, float* A2h, float* A2l, float
 // eigen-based path.  Output: theta (ascending, m values) and the basis Ritz
 // vectors as FP64 in Cout (m x m, column j = j-th Ritz vector).
 // ---------------------------------------------------------------------------
-constexpr int kL = kRRMax * kRRMax;
+constexpr int kL = kRRMax * kRRLd;
 
-// C = op(A) * op(B) for m x m double-word matrices (hi/lo planes, ld kRRMax);
+// C = op(A) * op(B) for m x m double-word matrices (hi/lo planes, ld kRRLd);
 // ta / tb: use the transpose.  B may be an FP32 matrix (Bl == nullptr).
 __device__ void dw_gemm(int m, const float* Ah, const float* Al, bool ta, const float* Bh, const float* Bl, bool tb,
                         float* Ch, float* Cl) {
-  const int ld = kRRMax;
+  const int ld = kRRLd;
   for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
     const int i = t / m, j = t % m;
     dot2 acc;
@@ -2189,7 +2192,7 @@ __device__ void dw_gemm(int m, const float* Ah, const float* Al, bool ta, const 
 __device__ int jacobi_f32(float* A, float* A2, float* V, float* V2, int m, float** Aout, float** Vout, float* fr,
                           float* gr, int* partner, float off_tol) {
   const int mp = m + (m & 1);
-  const int ld = kRRMax;
+  const int ld = kRRLd;
   const int tid = threadIdx.x;
   __shared__ int done;
   __shared__ unsigned char tp[kRRMax * kRRMax / 2], tq[kRRMax * kRRMax / 2];
@@ -2298,7 +2301,7 @@ __device__ int jacobi_f32(float* A, float* A2, float* V, float* V2, int m, float
 __device__ int rr_mixed_solve(int m, int k, const double* __restrict__ G, const double* __restrict__ H,
                               const double* sc, float* pool, double* theta, double* C, double* fr, double* gr,
                               int* partner, int* ord, double drop_tol, long long* cyc) {
-  const int ld = kRRMax;
+  const int ld = kRRLd;
   const int tid = threadIdx.x;
   float* s[12];
   for (int i = 0; i < 12; ++i) s[i] = pool + (size_t)i * kL;
@@ -2498,7 +2501,7 @@ __global__ void k_rayleigh_ritz_chol(int m, int k, const double* __restrict__ G,
                                      double* lam_new, double* hist_row, int stop_rule, double tol, DevStatus* st,
                                      int dword) {
   extern __shared__ double rr[];
-  const int ld = kRRMax;
+  const int ld = kRRLd;
   const int LL = ld * ld;
   double* B0 = rr;
   double* B1 = B0 + LL;
@@ -3301,7 +3304,7 @@ int launch_precond(Handle& h, const double* rho, const double* lam, double* Z) {
 int launch_rr(Handle& h, int m, const double* G, const double* Hm, const double* lam_old, double* C,
               double* lam_new, int hist_row) {
   if (m > kRRMax) return (int)cudaErrorInvalidValue;
-  size_t sm = (size_t)(6 * kRRMax * kRRMax + 3 * kRRMax) * sizeof(double) + 3 * kRRMax * sizeof(int);
+  size_t sm = (size_t)(6 * kRRLd * kRRLd + 3 * kRRLd) * sizeof(double) + 3 * kRRLd * sizeof(int);
   cudaFuncSetAttribute(k_rayleigh_ritz_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   ProfScope ps(h, BPJD_PROF_RR);
   h.launches += 1;
