@@ -279,7 +279,9 @@ __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_g
 // and every thread accumulates a 4 x 4 tile of the output for every NV over
 // its slice of the chunk's rows.  Plane layout: one segment of R x k values per
 // block (U blocks, then V1, then V2), row-major.
-template <int NV>
+// VEC: k is a multiple of 4, so the four columns of a tile lie in one block,
+// contiguous and 16-byte aligned in the planes (vector loads, no padding).
+template <int NV, bool VEC>
 __global__ void __launch_bounds__(256, 2) k_gram_dw(int n, int k, int nu, Ptrs6 U, int nvb, Ptrs6 V1, Ptrs6 V2, int sym,
                                                  int rows_per_block, int R, double* partial) {
   extern __shared__ __align__(16) float gsm[];
@@ -343,16 +345,44 @@ __global__ void __launch_bounds__(256, 2) k_gram_dw(int n, int k, int nu, Ptrs6 
     {
       const int nr = (int)min((int64_t)R, r1 - (r0 + (int64_t)c * R));
       const double* src = raw + (c & 1) * CH;
-      for (int e = tid; e < CH; e += blockDim.x) {
-        const int r = (e % SEG) / k;
-        const dw sp = split_f64(r < nr ? src[e] : 0.0);
-        ph[e] = sp.hi;
-        pl[e] = sp.lo;
+      if (nr == R) {
+        for (int e = tid; e < CH; e += blockDim.x) {
+          const dw sp = split_f64(src[e]);
+          ph[e] = sp.hi;
+          pl[e] = sp.lo;
+        }
+      } else {  // last chunk of the range: rows past its end are zero
+        for (int e = tid; e < CH; e += blockDim.x) {
+          const int r = (e % SEG) / k;
+          const dw sp = split_f64(r < nr ? src[e] : 0.0);
+          ph[e] = sp.hi;
+          pl[e] = sp.lo;
+        }
       }
     }
     __syncthreads();  // planes ready; the raw buffer of chunk c is free
     issue(c + 2);
-    if (worker) {
+    if (worker && VEC) {
+      for (int r = slice; r < R; r += S) {
+        const int ro = r * k;
+        const float4 uh = *reinterpret_cast<const float4*>(ph + uo[0] + ro);
+        const float4 ul = *reinterpret_cast<const float4*>(pl + uo[0] + ro);
+        const float a_h[4] = {uh.x, uh.y, uh.z, uh.w};
+        const float a_l[4] = {ul.x, ul.y, ul.z, ul.w};
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          const int o = vo[0] + v * mv * R + ro;
+          const float4 vh = *reinterpret_cast<const float4*>(ph + o);
+          const float4 vl = *reinterpret_cast<const float4*>(pl + o);
+          const float b_h[4] = {vh.x, vh.y, vh.z, vh.w};
+          const float b_l[4] = {vl.x, vl.y, vl.z, vl.w};
+#pragma unroll
+          for (int x = 0; x < 4; ++x)
+#pragma unroll
+            for (int y = 0; y < 4; ++y) acc[v][x][y].mac(a_h[x], a_l[x], b_h[y], b_l[y]);
+        }
+      }
+    } else if (worker) {
       for (int r = slice; r < R; r += S) {
         const int ro = r * k;
         float a_h[4], a_l[4];
@@ -3151,12 +3181,23 @@ int launch_gram_raw(int64_t n, int k, int nu, const double* const* U, int nvb, i
   const size_t stage = (size_t)24 * R * k * nseg;
   const size_t red = (size_t)ntiles * nv * 16 * sizeof(double);
   const size_t sm = std::max(stage, red);
+  auto go = [&](auto nv_tag, auto vec_tag) {
+    constexpr int NV = decltype(nv_tag)::value;
+    constexpr bool VEC = decltype(vec_tag)::value;
+    cudaFuncSetAttribute(k_gram_dw<NV, VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_gram_dw<NV, VEC><<<nblk2, 256, sm, stream>>>((int)n, k, nu, u, nvb, v1, v2, sym, rpb, R, partial);
+  };
+  const bool vec = (k % 4) == 0;
   if (nv == 2) {
-    cudaFuncSetAttribute(k_gram_dw<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_gram_dw<2><<<nblk2, 256, sm, stream>>>((int)n, k, nu, u, nvb, v1, v2, sym, rpb, R, partial);
+    if (vec)
+      go(std::integral_constant<int, 2>(), std::true_type());
+    else
+      go(std::integral_constant<int, 2>(), std::false_type());
   } else {
-    cudaFuncSetAttribute(k_gram_dw<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_gram_dw<1><<<nblk2, 256, sm, stream>>>((int)n, k, nu, u, nvb, v1, v2, sym, rpb, R, partial);
+    if (vec)
+      go(std::integral_constant<int, 1>(), std::true_type());
+    else
+      go(std::integral_constant<int, 1>(), std::false_type());
   }
   k_gram_reduce<<<(total + 31) / 32, 256, 0, stream>>>(nblk2, nv, mu, mv, sym, partial, out1, out2);
   return (int)cudaGetLastError();
