@@ -9,7 +9,7 @@
 //   recorded; the eigenvectors of T are the rotations applied to the identity
 //   (row ranges independently), those of C are Q times them, and those of the
 //   pencil are L^{-T} times those, which are M_H-orthonormal.
-// The O(n^3) stages that act on independent rows or columns run on a few
+// The O(n^3) stages that act on independent rows or columns run on up to 16
 // host threads; every element sees the same operations in the same order
 // whatever the thread count, so the result is bit-reproducible.
 
@@ -25,11 +25,11 @@ namespace bpjd {
 
 namespace {
 
-// body(lo, hi) over [0, n) split into contiguous ranges, one per thread
+// body(lo, hi) over [0, n) split into contiguous ranges, one per thread (at most 16)
 template <typename F>
 void parallel_ranges(int n, F body) {
   const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
-  const int T = std::max(1, std::min<int>({(int)hw, 8, n / 16}));
+  const int T = std::max(1, std::min<int>({(int)hw, 16, n / 16}));
   if (T <= 1) {
     body(0, n);
     return;
@@ -50,9 +50,10 @@ struct Reflectors {
   std::vector<double> beta;
 };
 
-// A: n x n row-major symmetric (overwritten).  On return d, e hold the
-// tridiagonal (e[i] couples i and i+1) and R the reflectors H_k = I - beta v v^T
-// with A_in = Q T Q^T, Q = H_0 H_1 ... H_{n-3}.
+// A: n x n row-major symmetric; only its lower triangle is read and updated
+// (overwritten).  On return d, e hold the tridiagonal (e[i] couples i and i+1)
+// and R the reflectors H_k = I - beta v v^T with A_in = Q T Q^T,
+// Q = H_0 H_1 ... H_{n-3}.
 void householder_tridiag(int n, std::vector<double>& A, std::vector<double>& d, std::vector<double>& e,
                          Reflectors& R) {
   R.v.assign(std::max(0, n - 2), {});
@@ -60,41 +61,52 @@ void householder_tridiag(int n, std::vector<double>& A, std::vector<double>& d, 
   std::vector<double> p(n), w(n);
   for (int k = 0; k + 2 < n; ++k) {
     const int m = n - k - 1;  // length of the reflected part, rows k+1..n-1
+    const int o = k + 1;
     std::vector<double>& v = R.v[k];
     v.resize(m);
     double xnorm2 = 0;
     for (int i = 0; i < m; ++i) {
-      const double x = A[(size_t)(k + 1 + i) * n + k];
+      const double x = A[(size_t)(o + i) * n + k];
       v[i] = x;
       xnorm2 += x * x;
     }
     const double xnorm = std::sqrt(xnorm2);
-    if (xnorm == 0.0) continue;
     const double alpha = (v[0] > 0) ? -xnorm : xnorm;
+    if (xnorm == 0.0) {
+      A[(size_t)o * n + k] = 0.0;
+      continue;
+    }
     v[0] -= alpha;
     double vtv = 0;
     for (int i = 0; i < m; ++i) vtv += v[i] * v[i];
     if (vtv == 0.0) continue;
     const double beta = 2.0 / vtv;
     R.beta[k] = beta;
-    // p = beta * A_sub v
+    // p = beta * A_sub v from the lower triangle: row i contributes A_ij v_j to p_i
+    // and A_ij v_i to p_j for j < i
+    std::fill(p.begin(), p.begin() + m, 0.0);
     for (int i = 0; i < m; ++i) {
-      double s = 0;
-      const double* row = &A[(size_t)(k + 1 + i) * n + (k + 1)];
-      for (int j = 0; j < m; ++j) s += row[j] * v[j];
-      p[i] = beta * s;
+      const double* row = &A[(size_t)(o + i) * n + o];
+      const double vi = v[i];
+      double si = 0;
+      for (int j = 0; j < i; ++j) {
+        si += row[j] * v[j];
+        p[j] += row[j] * vi;
+      }
+      p[i] += si + row[i] * vi;
     }
+    for (int i = 0; i < m; ++i) p[i] *= beta;
     double ptv = 0;
     for (int i = 0; i < m; ++i) ptv += p[i] * v[i];
     const double Kc = 0.5 * beta * ptv;
     for (int i = 0; i < m; ++i) w[i] = p[i] - Kc * v[i];
+    // rank-2 update of the lower triangle
     for (int i = 0; i < m; ++i) {
-      double* row = &A[(size_t)(k + 1 + i) * n + (k + 1)];
+      double* row = &A[(size_t)(o + i) * n + o];
       const double vi = v[i], wi = w[i];
-      for (int j = 0; j < m; ++j) row[j] -= vi * w[j] + wi * v[j];
+      for (int j = 0; j <= i; ++j) row[j] -= vi * w[j] + wi * v[j];
     }
-    A[(size_t)(k + 1) * n + k] = alpha;
-    A[(size_t)k * n + (k + 1)] = alpha;
+    A[(size_t)o * n + k] = alpha;
   }
   d.resize(n);
   e.assign(n > 0 ? n - 1 : 0, 0.0);
@@ -136,7 +148,7 @@ bool tridiag_qr(int n, std::vector<double>& d, std::vector<double>& e, std::vect
         x = e[k - 1];
         z = bulge;
       }
-      const double r = std::hypot(x, z);
+      const double r = std::sqrt(x * x + z * z);
       double cs, sn;
       if (r == 0.0) {
         cs = 1.0;
