@@ -50,6 +50,9 @@ def _args():
     ap.add_argument("--subspace", default="3k", choices=["2k", "3k"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=64)
+    ap.add_argument("--serving-workers", type=int, default=4)
     return ap.parse_args()
 
 
@@ -240,6 +243,50 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
+def run_serving(a, B):
+    """Poisson stream of independent 2-D eigenproblems (mixed sizes and k) through the
+    library's server (one stream per worker), against the same requests solved one at
+    a time.  Mean inter-arrival time = 1.25 x the mean one-at-a-time service time
+    (offered load 0.8).  Latency = submit -> result, per request."""
+    import numpy as np
+    from workloads import serving_stream
+
+    reqs = serving_stream(a.serving_requests, seed=0)
+    pbs = [B.problem_from_spec(r.spec) for r in reqs]          # host assembly, not timed
+    prec = B.MIXED if a.precision == "mixed" else B.FP64
+    # one at a time (host inputs and outputs, the plain per-request path)
+    svc = []
+    for pb, r in zip(pbs, reqs):
+        t0 = time.perf_counter()
+        sv = B.Solver.from_problem(pb, r.spec.k, device=None, precision=prec, subspace=B.W_3K)
+        sv.solve(eigvecs="host")
+        sv.close()
+        svc.append(time.perf_counter() - t0)
+    ktot = sum(r.spec.k for r in reqs)
+    gap = 1.25 * float(np.mean(svc))
+    srv = B.Server(workers=a.serving_workers, precision=prec, subspace=B.W_3K)
+    lat, failed, tickets = [], 0, []
+    t0 = time.perf_counter()
+    for pb, r in zip(pbs, reqs):
+        wait = t0 + r.arrival * gap - time.perf_counter()
+        if wait > 0:
+            time.sleep(wait)
+        tickets.append((srv.submit(pb, r.spec.k), r.spec.k))
+    for t, k in tickets:
+        rc, lam, X, st, times = srv.poll(t)
+        failed += int(rc != B.OK)
+        lat.append(times[2])
+    makespan = time.perf_counter() - t0
+    srv.close()
+    lat = np.array(lat)
+    return {"requests": len(reqs), "workers": a.serving_workers, "offered_load": 0.8,
+            "mean_interarrival_s": gap, "p50_latency_s": float(np.percentile(lat, 50)),
+            "p99_latency_s": float(np.percentile(lat, 99)), "eigenpairs_per_s": ktot / makespan,
+            "one_at_a_time_eigenpairs_per_s": ktot / float(np.sum(svc)),
+            "one_at_a_time_p50_service_s": float(np.percentile(svc, 50)), "failed": failed,
+            "stream": "serving_stream(seed 0): P1 on 64..512 squares, random smooth kappa, k in 4..16, tau 1"}
+
+
 def run_ours(a):
     import numpy as np
     import torch
@@ -364,6 +411,10 @@ def run_ours(a):
                "d2h_bytes_per_step": int(d2h)}
 
     cpu = None
+    serving = None
+    if rank == 0 and not a.no_serving:
+        serving = run_serving(a, B)
+
     if rank == 0 and not a.no_cpu_baseline:
         v, sample, info = oracle_sample(spec, int(round(statistics.mean(iters))), n_local=96)
         cpu = {"value": v, "unit": UNIT, "cores": _blas_threads(), "kind": "oracle", "sample": sample}
@@ -381,7 +432,8 @@ def run_ours(a):
                 "iters": iters, "max_rel_resid": max(res),
                 "schwarz_apply_gbs": schw_gbs,
                 "kernel_ms_per_step": {kk: v[0] / a.steps for kk, v in prof_tot.items()},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": ck, "gpu_launches": launches}
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "serving": serving, "clocks": ck,
+                "gpu_launches": launches}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -46,7 +46,8 @@ extern "C" {
 #define BPJD_ERR_OOM              -9  /* device allocation failed */
 #define BPJD_ERR_CUDA            -10  /* a CUDA runtime call failed */
 #define BPJD_ERR_UNSUPPORTED     -11  /* option outside what this build implements */
-#define BPJD_ERR_TOO_LARGE       -12  /* request exceeds a fixed capacity (allocation-free entry point) */
+#define BPJD_ERR_TOO_LARGE       -12  /* request exceeds a fixed capacity (allocation-free entry point)
+                                         or, alone, the memory budget of a server */
 
 /* ---- option values ----------------------------------------------------- */
 #define BPJD_FP64        0  /* every step in FP64 */
@@ -267,6 +268,61 @@ typedef struct {
 /* Assembles K, M, P, P0 and the box partition on the host.  Errors: BAD_ARG. */
 int bpjd_problem_create(const bpjd_mesh* mesh, bpjd_problem** out);
 void bpjd_problem_free(bpjd_problem* p);
+
+/* ---- serving: many independent eigenproblems on one GPU ----------------
+ *
+ * A server solves a stream of independent requests (each one a full
+ * bpjd_setup + bpjd_solve of its own pencil and partition) on a few worker
+ * threads, each with its own CUDA stream, so that small requests overlap on
+ * the GPU.  Admission is first-in first-out under a device-memory budget: the
+ * request at the head of the queue starts when its estimated device footprint
+ * fits beside the requests in flight.  This is the per-request workflow of
+ * Algorithm 3.1 run many times; the paper itself solves one pencil at a time.
+ */
+#define BPJD_PENDING 1  /* bpjd_server_poll: the request has not finished yet */
+
+typedef struct {
+  size_t  hbm_budget_bytes; /* device bytes the admitted requests may hold together;
+                               0: 80% of the free device memory at creation */
+  int32_t workers;          /* concurrent solves, each on its own stream (default 4, 1..32) */
+  int32_t precision;        /* per-request options, as in bpjd_opts; defaults BPJD_MIXED, */
+  int32_t subspace;         /*   BPJD_W_3K, BPJD_STOP_RESIDUAL, 1e-8, 500                  */
+  int32_t stop_rule;
+  double  tol;
+  int32_t max_iter;
+} bpjd_server_opts;
+
+typedef struct bpjd_server bpjd_server;
+
+void bpjd_server_default_opts(bpjd_server_opts* o);
+
+/* Starts the worker threads on the current device.  Errors: BAD_ARG, CUDA. */
+int bpjd_server_create(const bpjd_server_opts* opts, bpjd_server** out);
+
+/*
+ * Queues one request; every input is host memory and is copied before the call
+ * returns (the caller may free it at once).  P0 may be NULL (tau = 0).
+ * *ticket identifies the request in bpjd_server_poll.  Errors: BAD_ARG,
+ * CSR_INVALID or MAP_INVALID (host checks of the inputs), TOO_LARGE (the
+ * estimated footprint exceeds the whole budget).
+ */
+int bpjd_server_submit(bpjd_server* s, const bpjd_csr* A, const bpjd_csr* M, const bpjd_csr* P,
+                       const bpjd_csr* P0, const bpjd_partition* part, int32_t k, uint64_t* ticket);
+
+/*
+ * Collects a finished request.  wait = 0 returns BPJD_PENDING at once if it is
+ * still queued or running; wait = 1 blocks until it finishes.  On completion the
+ * request's own status is returned (BPJD_OK or its bpjd_setup / bpjd_solve
+ * error) and, where not NULL: eigvals (k), eigvecs (n x k row-major, host),
+ * st, and times[3] = {seconds queued, seconds in service, seconds from submit
+ * to completion}.  A collected ticket is forgotten (BAD_ARG afterwards).
+ */
+int bpjd_server_poll(bpjd_server* s, uint64_t ticket, int32_t wait, double* eigvals, double* eigvecs,
+                     bpjd_stats* st, double* times);
+
+/* Waits for every queued request to finish, then stops the workers and frees
+ * the server (uncollected results are dropped). */
+void bpjd_server_free(bpjd_server* s);
 
 #ifdef __cplusplus
 }

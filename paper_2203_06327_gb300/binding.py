@@ -42,7 +42,10 @@ EXPORTED = [
     "bpjd_spmm", "bpjd_apply_preconditioner", "bpjd_history", "bpjd_device_bytes",
     "bpjd_problem_create", "bpjd_problem_free", "bpjd_profile", "bpjd_profile_read",
     "bpjd_layout", "bpjd_block_gram", "bpjd_block_gram_noalloc",
+    "bpjd_server_default_opts", "bpjd_server_create", "bpjd_server_submit", "bpjd_server_poll",
+    "bpjd_server_free",
 ]
+PENDING = 1
 PROF_NAMES = ["local", "coarse", "prolong", "spmm", "inner", "combine", "rr", "resid"]
 
 
@@ -66,6 +69,11 @@ class Stats(C.Structure):
     _fields_ = [("iters", C.c_int32), ("converged", C.c_int32), ("max_rel_resid", C.c_double),
                 ("sum_abs_dlambda", C.c_double), ("t_setup_s", C.c_double), ("t_solve_s", C.c_double),
                 ("status", C.c_int32)]
+
+
+class ServerOpts(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_size_t), ("workers", C.c_int32), ("precision", C.c_int32),
+                ("subspace", C.c_int32), ("stop_rule", C.c_int32), ("tol", C.c_double), ("max_iter", C.c_int32)]
 
 
 class MeshS(C.Structure):
@@ -101,6 +109,15 @@ def _load():
     lib.bpjd_problem_free.restype = None
     lib.bpjd_layout.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
     lib.bpjd_block_gram.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p]
+    lib.bpjd_server_default_opts.argtypes = [C.POINTER(ServerOpts)]
+    lib.bpjd_server_default_opts.restype = None
+    lib.bpjd_server_create.argtypes = [C.POINTER(ServerOpts), C.POINTER(C.c_void_p)]
+    lib.bpjd_server_submit.argtypes = [C.c_void_p, C.POINTER(Csr), C.POINTER(Csr), C.POINTER(Csr), C.POINTER(Csr),
+                                       C.POINTER(Partition), C.c_int32, C.POINTER(C.c_uint64)]
+    lib.bpjd_server_poll.argtypes = [C.c_void_p, C.c_uint64, C.c_int32, C.c_void_p, C.c_void_p, C.POINTER(Stats),
+                                     C.c_void_p]
+    lib.bpjd_server_free.argtypes = [C.c_void_p]
+    lib.bpjd_server_free.restype = None
     lib.bpjd_profile.argtypes = [C.c_void_p, C.c_int32]
     lib.bpjd_profile_read.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
     return lib
@@ -351,3 +368,61 @@ class Solver:
 
     def device_bytes(self) -> int:
         return int(lib.bpjd_device_bytes(self._h))
+
+
+# ---- serving --------------------------------------------------------------------
+class Server:
+    """Many independent eigenproblems on one GPU (bpjd_server_*): requests are queued
+    first-in first-out, admitted under a device-memory budget and solved by worker
+    threads with one CUDA stream each."""
+
+    def __init__(self, workers: int = 4, hbm_budget_bytes: int = 0, precision: int = MIXED,
+                 subspace: int = W_3K, stop_rule: int = STOP_RESIDUAL, tol: float = 1e-8, max_iter: int = 500):
+        o = ServerOpts()
+        lib.bpjd_server_default_opts(C.byref(o))
+        o.workers, o.hbm_budget_bytes = int(workers), int(hbm_budget_bytes)
+        o.precision, o.subspace, o.stop_rule = precision, subspace, stop_rule
+        o.tol, o.max_iter = float(tol), int(max_iter)
+        h = C.c_void_p()
+        _check(lib.bpjd_server_create(C.byref(o), C.byref(h)), "bpjd_server_create")
+        self._h = h
+        self._meta = {}
+
+    def submit(self, pb: "Problem", k: int) -> int:
+        """Queues one problem (host arrays; copied before returning) and returns its ticket."""
+        K, M, P = pb.K.c(), pb.M.c(), pb.P.c()
+        P0 = pb.P0.c() if pb.tau > 0 else None
+        part = pb.part.c()
+        t = C.c_uint64()
+        _check(lib.bpjd_server_submit(self._h, C.byref(K), C.byref(M), C.byref(P),
+                                      C.byref(P0) if P0 is not None else None, C.byref(part), int(k),
+                                      C.byref(t)), "bpjd_server_submit")
+        self._meta[t.value] = (pb.K.n_rows, int(k))
+        return t.value
+
+    def poll(self, ticket: int, wait: bool = True):
+        """None while pending (wait=False); else (status, eigenvalues, eigenvectors,
+        stats dict, (queued s, service s, latency s))."""
+        n, k = self._meta[ticket]
+        lam = np.empty(k, dtype=np.float64)
+        X = np.empty((n, k), dtype=np.float64)
+        st = Stats()
+        times = np.empty(3, dtype=np.float64)
+        rc = lib.bpjd_server_poll(self._h, C.c_uint64(ticket), 1 if wait else 0, lam.ctypes.data, X.ctypes.data,
+                                  C.byref(st), times.ctypes.data)
+        if rc == PENDING:
+            return None
+        del self._meta[ticket]
+        stats = {f: getattr(st, f) for f, _ in Stats._fields_}
+        return rc, lam, X, stats, tuple(float(x) for x in times)
+
+    def close(self):
+        if self._h:
+            lib.bpjd_server_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -6,11 +6,15 @@
 // run is bit-reproducible for a given launch configuration.
 
 #include <cuda_runtime.h>
+#include <math_constants.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <mutex>
 #include <new>
+#include <set>
+#include <utility>
 #include <type_traits>
 
 #include "bpjd_internal.h"
@@ -21,6 +25,32 @@ namespace bpjd {
 namespace {
 
 constexpr int kPartialBlocks = 456;  // 3 x 152 SMs
+
+// Raises a kernel's dynamic shared memory limit to the device maximum, once per
+// (kernel, device).  A per-launch limit would race between host threads that
+// launch the same kernel with different sizes (concurrent solves): one thread
+// could lower the limit below another's launch.
+std::mutex g_smem_attr_mu;
+std::set<std::pair<const void*, int>> g_smem_attr_done;
+
+int allow_dynamic_smem(const void* kern) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return (int)cudaErrorInvalidDevice;
+  {
+    std::lock_guard<std::mutex> lk(g_smem_attr_mu);
+    if (g_smem_attr_done.count({kern, dev})) return 0;
+  }
+  int optin = 0;
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kern);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+  if (e != cudaSuccess) return (int)e;
+  std::lock_guard<std::mutex> lk(g_smem_attr_mu);
+  g_smem_attr_done.insert({kern, dev});
+  return 0;
+}
 
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -1779,6 +1809,15 @@ __device__ void jacobi_eig(double* A, double* V, int m, double* cs, double* sn, 
   }
 }
 
+// Strict total order for ranking eigenvalues: NaN counts as +infinity and ties
+// go by index, so the ranks always form a permutation (the ranks index shared
+// memory, whatever the data).
+__device__ __forceinline__ bool order_before(double a, int ia, double b, int ib) {
+  a = isnan(a) ? CUDART_INF : a;
+  b = isnan(b) ? CUDART_INF : b;
+  return a < b || (a == b && ia < ib);
+}
+
 // Ascending order of diag(A)[0..m): ord[rank] = index (ties by index).
 __device__ void sort_diag(const double* A, int m, int* ord) {
   const int ld = kRRLd;
@@ -1786,8 +1825,7 @@ __device__ void sort_diag(const double* A, int m, int* ord) {
     double dj = A[j * ld + j];
     int rank = 0;
     for (int i = 0; i < m; ++i) {
-      double di = A[i * ld + i];
-      if (di < dj || (di == dj && i < j)) ++rank;
+      if (order_before(A[i * ld + i], i, dj, j)) ++rank;
     }
     ord[rank] = j;
   }
@@ -2492,8 +2530,7 @@ __device__ int rr_mixed_solve(int m, int k, const double* __restrict__ G, const 
     const double tj = theta[j];
     int rank = 0;
     for (int i2 = 0; i2 < m; ++i2) {
-      const double ti = theta[i2];
-      rank += (ti < tj || (ti == tj && i2 < j)) ? 1 : 0;
+      rank += order_before(theta[i2], i2, tj, j) ? 1 : 0;
     }
     ord[rank] = j;
   }
@@ -2713,8 +2750,7 @@ __global__ void k_rayleigh_ritz_chol(int m, int k, const double* __restrict__ G,
     const double fj = fr[j];
     int rank = 0;
     for (int i2 = 0; i2 < m; ++i2) {
-      const double fi = fr[i2];
-      rank += (fi < fj || (fi == fj && i2 < j)) ? 1 : 0;
+      rank += order_before(fr[i2], i2, fj, j) ? 1 : 0;
     }
     ord[rank] = j;
   }
@@ -3184,7 +3220,7 @@ int launch_gram_raw(int64_t n, int k, int nu, const double* const* U, int nvb, i
   auto go = [&](auto nv_tag, auto vec_tag) {
     constexpr int NV = decltype(nv_tag)::value;
     constexpr bool VEC = decltype(vec_tag)::value;
-    cudaFuncSetAttribute(k_gram_dw<NV, VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    allow_dynamic_smem((const void*)k_gram_dw<NV, VEC>);
     k_gram_dw<NV, VEC><<<nblk2, 256, sm, stream>>>((int)n, k, nu, u, nvb, v1, v2, sym, rpb, R, partial);
   };
   const bool vec = (k % 4) == 0;
@@ -3219,7 +3255,7 @@ int launch_combine_rows(Handle& h, int nin, const double* const* Win, const doub
   if (h.precision == BPJD_MIXED && consistency_only) {
     const int m = nin * h.k;
     const size_t sm = (size_t)(m * csub + kCombRows * m) * sizeof(float);
-    if (sm > 48 * 1024) cudaFuncSetAttribute(k_combine_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    allow_dynamic_smem((const void*)k_combine_f32);
     const int64_t blocks = ((int64_t)h.n + kCombRows - 1) / kCombRows;
     k_combine_f32<<<(unsigned)blocks, 256, sm, h.stream>>>(h.n, h.k, nin, w, C, ldc, csub, Zadd, out, (float)sign);
     return (int)cudaGetLastError();
@@ -3227,7 +3263,7 @@ int launch_combine_rows(Handle& h, int nin, const double* const* Win, const doub
   if (h.precision == BPJD_MIXED) {
     const int m = nin * h.k;
     const size_t sm = (size_t)(2 * m * csub + 2 * kCombRows * m) * sizeof(float);
-    if (sm > 48 * 1024) cudaFuncSetAttribute(k_combine_dw, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    allow_dynamic_smem((const void*)k_combine_dw);
     const int64_t blocks = ((int64_t)h.n + kCombRows - 1) / kCombRows;
     k_combine_dw<<<(unsigned)blocks, 256, sm, h.stream>>>(h.n, h.k, nin, w, C, ldc, csub, Zadd, out, sign);
     return (int)cudaGetLastError();
@@ -3253,14 +3289,14 @@ int launch_precond(Handle& h, const double* rho, const double* lam, double* Z) {
 #define BPJD_LOCAL_TILE(BM)                                                                                    \
   case BM: {                                                                                                   \
     const size_t sm = sizeof(float) * MmaShape<BM>::smem_floats;                                               \
-    cudaFuncSetAttribute(k_local_factor_mma<BM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);       \
+    allow_dynamic_smem((const void*)k_local_factor_mma<BM>);       \
     k_local_factor_mma<BM><<<blocks, 32 * kLocalWarps, sm, h.stream>>>(h.nsub, k, h.sub_ptr, h.sub_dofs,       \
                                                                        h.bandKf, h.bandMf, lam, rho,           \
                                                                        (float*)h.Lbuf, (float*)h.wpk,          \
                                                                        h.derr);                                \
     {                                                                                                          \
       const size_t bsm = sizeof(float) * BwdShape<BM>::smem_floats;                                            \
-      cudaFuncSetAttribute(k_local_backward<BM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm);       \
+      allow_dynamic_smem((const void*)k_local_backward<BM>);       \
       k_local_backward<BM><<<bwd_blocks, 32 * BwdShape<BM>::WPB, bsm, h.stream>>>(                             \
           h.nsub, k, h.sub_ptr, (const float*)h.Lbuf, (float*)h.wpk, h.derr);                                  \
     }                                                                                                          \
@@ -3298,12 +3334,12 @@ int launch_precond(Handle& h, const double* rho, const double* lam, double* Z) {
       size_t sm = per_warp * wpb;
       int blocks = (npairs + wpb - 1) / wpb;
       if (f32) {
-        cudaFuncSetAttribute(k_local_band<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        allow_dynamic_smem((const void*)k_local_band<float>);
         k_local_band<float><<<blocks, 32 * wpb, sm, h.stream>>>(npairs, k, h.sub_ptr, h.sub_dofs, B, h.bandKf,
                                                                 h.bandMf, lam, rho, (float*)h.Lbuf, (float*)h.wpk,
                                                                 h.derr);
       } else {
-        cudaFuncSetAttribute(k_local_band<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        allow_dynamic_smem((const void*)k_local_band<double>);
         k_local_band<double><<<blocks, 32 * wpb, sm, h.stream>>>(npairs, k, h.sub_ptr, h.sub_dofs, B, h.bandK,
                                                                  h.bandM, lam, rho, (double*)h.Lbuf,
                                                                  (double*)h.wpk, h.derr);
@@ -3346,7 +3382,7 @@ int launch_rr(Handle& h, int m, const double* G, const double* Hm, const double*
               double* lam_new, int hist_row) {
   if (m > kRRMax) return (int)cudaErrorInvalidValue;
   size_t sm = (size_t)(6 * kRRLd * kRRLd + 3 * kRRLd) * sizeof(double) + 3 * kRRLd * sizeof(int);
-  cudaFuncSetAttribute(k_rayleigh_ritz_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  allow_dynamic_smem((const void*)k_rayleigh_ritz_chol);
   ProfScope ps(h, BPJD_PROF_RR);
   h.launches += 1;
   double* hr = (hist_row >= 0 && hist_row < h.hist_rows) ? h.hist + (int64_t)hist_row * h.k : nullptr;
@@ -3420,7 +3456,7 @@ int launch_galerkin(const CsrDev& A, const CsrDev& Msp, const CsrDev& P, const C
   if ((e = cudaMemsetAsync(ovf, 0, sizeof(int32_t), s)) != cudaSuccess) goto done;
   k_kp_rows<<<(n + 127) / 128, 128, 0, s>>>(n, A.row_ptr, A.col, A.val, Msp.row_ptr, Msp.col, Msp.val, P.row_ptr,
                                             P.col, P.val, kpc, kpk, kpm, cnt, ovf);
-  if (sm > 48 * 1024) cudaFuncSetAttribute(k_galerkin_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  allow_dynamic_smem((const void*)k_galerkin_rows);
   k_galerkin_rows<<<nH, 32 * wpb, sm, s>>>(nH, PT.row_ptr, PT.col, PT.val, kpc, kpk, kpm, cnt, KH, MH);
   if ((e = cudaGetLastError()) != cudaSuccess) goto done;
   if ((e = cudaMemcpyAsync(&hov, ovf, sizeof(int32_t), cudaMemcpyDeviceToHost, s)) != cudaSuccess) goto done;

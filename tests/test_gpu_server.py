@@ -1,0 +1,81 @@
+"""The serving entry points (bpjd_server_*): independent requests solved concurrently
+on worker streams give exactly the results of the same requests solved one at a
+time, errors stay with their request, and the memory budget is enforced."""
+
+from dataclasses import replace
+
+import numpy as np
+import pytest
+
+from workloads import config_c1, config_small_2d, config_small_3d, serving_stream
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+B = pytest.importorskip("paper_2203_06327_gb300.binding")
+
+
+def _alone(pb, k):
+    sv = B.Solver.from_problem(pb, k, device=None, precision=B.MIXED, subspace=B.W_3K)
+    lam, X, st = sv.solve()
+    sv.close()
+    return lam, X
+
+
+def test_mixed_requests_match_solves_alone():
+    specs = [config_c1(), config_small_2d(), config_small_3d(), config_small_3d(kind="q1_3d"),
+             config_small_2d(nx=64, ny=64, nsx=4, nsy=4, delta=2, k=7),
+             config_small_2d(nx=40, ny=40, nsx=5, nsy=5, delta=1, k=1, kappa="random")]
+    pbs = [B.problem_from_spec(s) for s in specs]
+    srv = B.Server(workers=3)
+    try:
+        tickets = [srv.submit(pb, s.k) for pb, s in zip(pbs, specs)]
+        results = [srv.poll(t) for t in tickets]
+    finally:
+        srv.close()
+    for pb, s, (rc, lam, X, st, times) in zip(pbs, specs, results):
+        assert rc == B.OK, (s.name, rc)
+        assert st["converged"] == 1
+        assert times[0] >= 0 and times[1] > 0 and times[2] >= times[1]
+        lam1, X1 = _alone(pb, s.k)
+        np.testing.assert_array_equal(lam, lam1)
+        np.testing.assert_array_equal(X, X1)
+
+
+def test_serving_stream_requests_solve():
+    """The first requests of the seeded serving stream (mixed sizes and k)."""
+    reqs = serving_stream(6, seed=0)
+    srv = B.Server(workers=4)
+    try:
+        tickets = [(r, srv.submit(B.problem_from_spec(r.spec), r.spec.k)) for r in reqs]
+        for r, t in tickets:
+            rc, lam, X, st, times = srv.poll(t)
+            assert rc == B.OK, r.spec.name
+            assert st["max_rel_resid"] <= 1e-8
+            assert np.all(np.diff(lam) >= 0)
+    finally:
+        srv.close()
+
+
+def test_errors_stay_with_their_request():
+    bad = replace(config_c1(), tau=0)   # first local shifted matrices indefinite
+    good = config_small_2d()
+    srv = B.Server(workers=2)
+    try:
+        t_bad = srv.submit(B.problem_from_spec(bad), bad.k)
+        t_good = srv.submit(B.problem_from_spec(good), good.k)
+        assert srv.poll(t_bad)[0] == B.ERR_LOCAL_INDEFINITE
+        assert srv.poll(t_good)[0] == B.OK
+        with pytest.raises(KeyError):
+            srv.poll(t_bad)
+    finally:
+        srv.close()
+
+
+def test_budget_rejects_oversize_request():
+    srv = B.Server(workers=1, hbm_budget_bytes=1 << 20)
+    try:
+        with pytest.raises(B.BpjdError) as e:
+            srv.submit(B.problem_from_spec(config_c1()), 6)
+        assert e.value.code == B.ERR_TOO_LARGE
+    finally:
+        srv.close()

@@ -207,7 +207,7 @@ def serving_stream(n_requests: int = 64, seed: int = 0) -> List[ServingRequest]:
     random smooth zeta (kappa in [0.5, 2]); k ~ U{4..16}; subdomains per side
     drawn from {4, 8, 16}, then raised (doubling) until the subdomain is at most
     64 elements wide and the coarse space has more than k + 2 functions;
-    overlap 2 layers.  Arrival gaps are exponential with unit mean; the caller
+    overlap 2 layers; initial grid H/2 (tau = 1).  Arrival gaps are exponential with unit mean; the caller
     scales them to seconds.
     """
     rng = np.random.default_rng(seed)
@@ -221,7 +221,9 @@ def serving_stream(n_requests: int = 64, seed: int = 0) -> List[ServingRequest]:
         while n // ns > 64 or (ns - 1) ** 2 <= k + 2:
             ns *= 2
         kap = kappa_field_2d(n, n, 1.0, 1.0, "random", rng=rng)
-        spec = ProblemSpec("p1_2d", (n, n), (1.0, 1.0), (ns, ns), 2, k, kappa=kap,
+        # tau = 1: the Step 1 eigenproblem on the grid H/2 (Section 3), whose
+        # initial Ritz values stay below the local Dirichlet spectra for every k drawn
+        spec = ProblemSpec("p1_2d", (n, n), (1.0, 1.0), (ns, ns), 2, k, kappa=kap, tau=1,
                            name=f"req{rid}_n{n}_k{k}_ns{ns}")
         out.append(ServingRequest(rid, t, spec))
     return out
