@@ -427,9 +427,10 @@ extern "C" int bpjd_setup(const bpjd_csr* A, const bpjd_csr* M, const bpjd_csr* 
         std::vector<double> K0, M0;
         if ((rc = galerkin_host(tmp0, dP0, dP0T, K0, M0)) != BPJD_OK) goto fail;
         const int nH0 = h->nH0;
-        eigP0 = std::async(std::launch::async, [nH0, K0 = std::move(K0), M0 = std::move(M0)]() {
+        eigP0 = std::async(std::launch::async, [nH0, k, K0 = std::move(K0), M0 = std::move(M0)]() {
           EigResult r;
-          r.rc = gen_eig_host(nH0, K0, M0, r.lam, r.Phi);
+          // the initial guess needs the lowest k eigenvectors of the grid H/2^tau only
+          r.rc = gen_eig_host(nH0, K0, M0, r.lam, r.Phi, k);
           return r;
         });
       }

@@ -120,9 +120,11 @@ struct ProfScope {
 void prof_flush(Handle& h);
 
 // dense.cpp
-int sym_eig_host(int n, std::vector<double> A, std::vector<double>& lam, std::vector<double>& V);
+// nvec < n: every eigenvalue, eigenvectors of the lowest nvec only (the other
+// columns of V / Phi are zero)
+int sym_eig_host(int n, std::vector<double> A, std::vector<double>& lam, std::vector<double>& V, int nvec = -1);
 int gen_eig_host(int n, const std::vector<double>& K, const std::vector<double>& M, std::vector<double>& lam,
-                 std::vector<double>& Phi);
+                 std::vector<double>& Phi, int nvec = -1);
 
 // kernels.cu launchers (all asynchronous on h.stream; return cudaError_t as int)
 int launch_spmm(Handle& h, const double* X, double* YA, double* YM, int ncols);

@@ -16,6 +16,7 @@
 #include <algorithm>
 #include <cmath>
 #include <numeric>
+#include <atomic>
 #include <thread>
 #include <vector>
 
@@ -114,15 +115,135 @@ void householder_tridiag(int n, std::vector<double>& A, std::vector<double>& d, 
   for (int i = 0; i + 1 < n; ++i) e[i] = A[(size_t)(i + 1) * n + i];
 }
 
+// The same reduction on T host threads (for n in the hundreds and more): per
+// step, thread 0 forms the reflector, the matrix-vector product runs over
+// fixed chunks of 32 rows with one partial vector per chunk (summed in chunk
+// order, so the result does not depend on T), and the rank-2 update is split
+// by chunks.  Threads meet at a spinning barrier five times per step.
+struct SpinBarrier {
+  std::atomic<int> count{0}, gen{0};
+  int n;
+  explicit SpinBarrier(int n_) : n(n_) {}
+  void wait() {
+    const int g = gen.load(std::memory_order_acquire);
+    if (count.fetch_add(1, std::memory_order_acq_rel) == n - 1) {
+      count.store(0, std::memory_order_relaxed);
+      gen.fetch_add(1, std::memory_order_release);
+    } else {
+      while (gen.load(std::memory_order_acquire) == g) std::this_thread::yield();
+    }
+  }
+};
+
+void householder_tridiag_threads(int n, std::vector<double>& A, std::vector<double>& d, std::vector<double>& e,
+                                 Reflectors& R, int T) {
+  constexpr int CH = 32;
+  R.v.assign(std::max(0, n - 2), {});
+  R.beta.assign(std::max(0, n - 2), 0.0);
+  const int nch_max = (n + CH - 1) / CH;
+  std::vector<double> part((size_t)nch_max * n), p(n), w(n);
+  SpinBarrier bar(T);
+  double alpha_s = 0, beta_s = 0;
+  int skip = 0;
+  auto body = [&](int tid) {
+    for (int k = 0; k + 2 < n; ++k) {
+      const int m = n - k - 1, o = k + 1;
+      std::vector<double>& v = R.v[k];
+      if (tid == 0) {
+        v.resize(m);
+        double xnorm2 = 0;
+        for (int i = 0; i < m; ++i) {
+          const double x = A[(size_t)(o + i) * n + k];
+          v[i] = x;
+          xnorm2 += x * x;
+        }
+        const double xnorm = std::sqrt(xnorm2);
+        alpha_s = (v[0] > 0) ? -xnorm : xnorm;
+        skip = 0;
+        if (xnorm == 0.0) {
+          A[(size_t)o * n + k] = 0.0;
+          skip = 1;
+        } else {
+          v[0] -= alpha_s;
+          double vtv = 0;
+          for (int i = 0; i < m; ++i) vtv += v[i] * v[i];
+          if (vtv == 0.0) {
+            skip = 1;
+          } else {
+            beta_s = 2.0 / vtv;
+            R.beta[k] = beta_s;
+          }
+        }
+      }
+      bar.wait();
+      if (skip) continue;
+      const int nch = (m + CH - 1) / CH;
+      // partial products, one vector per chunk of rows (entries 0 .. last row of the chunk)
+      for (int c = tid; c < nch; c += T) {
+        const int i0 = c * CH, i1 = std::min(m, i0 + CH);
+        double* pc = &part[(size_t)c * n];
+        std::fill(pc, pc + i1, 0.0);
+        for (int i = i0; i < i1; ++i) {
+          const double* row = &A[(size_t)(o + i) * n + o];
+          const double vi = v[i];
+          double si = 0;
+          for (int j = 0; j < i; ++j) {
+            si += row[j] * v[j];
+            pc[j] += row[j] * vi;
+          }
+          pc[i] += si + row[i] * vi;
+        }
+      }
+      bar.wait();
+      // p_j = beta * sum over the chunks that reach row j, in chunk order
+      for (int j0 = tid * CH; j0 < m; j0 += T * CH) {
+        const int j1 = std::min(m, j0 + CH);
+        for (int j = j0; j < j1; ++j) {
+          double sj = 0;
+          for (int c = j / CH; c < nch; ++c) sj += part[(size_t)c * n + j];
+          p[j] = beta_s * sj;
+        }
+      }
+      bar.wait();
+      if (tid == 0) {
+        double ptv = 0;
+        for (int i = 0; i < m; ++i) ptv += p[i] * v[i];
+        const double Kc = 0.5 * beta_s * ptv;
+        for (int i = 0; i < m; ++i) w[i] = p[i] - Kc * v[i];
+      }
+      bar.wait();
+      for (int c = tid; c < nch; c += T) {
+        const int i0 = c * CH, i1 = std::min(m, i0 + CH);
+        for (int i = i0; i < i1; ++i) {
+          double* row = &A[(size_t)(o + i) * n + o];
+          const double vi = v[i], wi = w[i];
+          for (int j = 0; j <= i; ++j) row[j] -= vi * w[j] + wi * v[j];
+        }
+      }
+      bar.wait();
+      if (tid == 0) A[(size_t)o * n + k] = alpha_s;
+    }
+  };
+  std::vector<std::thread> th;
+  for (int t = 1; t < T; ++t) th.emplace_back(body, t);
+  body(0);
+  for (auto& x : th) x.join();
+  d.resize(n);
+  e.assign(n > 0 ? n - 1 : 0, 0.0);
+  for (int i = 0; i < n; ++i) d[i] = A[(size_t)i * n + i];
+  for (int i = 0; i + 1 < n; ++i) e[i] = A[(size_t)(i + 1) * n + i];
+}
+
 struct Rot {
   int k;
   double c, s;
 };
 
 // Implicit symmetric tridiagonal QR with Wilkinson shifts.  The rotation
-// acting on columns (k, k+1) of the eigenvector matrix is recorded in order.
+// acting on columns (k, k+1) of the eigenvector matrix is recorded in order
+// (when rots is not NULL).
 // Returns false if it fails to converge.
-bool tridiag_qr(int n, std::vector<double>& d, std::vector<double>& e, std::vector<Rot>& rots) {
+bool tridiag_qr(int n, std::vector<double>& d, std::vector<double>& e, std::vector<Rot>* rots) {
   const double eps = 2.220446049250313e-16;
   int iter = 0;
   const int max_iter = 60 * std::max(n, 1);
@@ -167,7 +288,7 @@ bool tridiag_qr(int n, std::vector<double>& d, std::vector<double>& e, std::vect
         bulge = -sn * e[k + 1];
         e[k + 1] = cs * e[k + 1];
       }
-      rots.push_back({k, cs, sn});
+      if (rots) rots->push_back({k, cs, sn});
     }
   }
   return true;
@@ -192,15 +313,109 @@ void apply_q(int n, const Reflectors& R, std::vector<double>& Zc, int c0, int c1
   }
 }
 
+// Eigenvectors of the symmetric tridiagonal T (diagonal d, off-diagonal e) for
+// the given ascending eigenvalues mu[0..nv), by inverse iteration (Wilkinson,
+// "The Algebraic Eigenvalue Problem", Ch. 5): (T - mu I) is factorised by
+// Gaussian elimination with partial pivoting, three solves from a fixed start
+// vector, each followed by Gram-Schmidt (twice) against the vectors of
+// eigenvalues closer than 1e-3 ||T|| (a cluster), and normalisation.
+// Z: n x nv, column-major.
+void tridiag_inverse_iteration(int n, const std::vector<double>& d, const std::vector<double>& e,
+                               const std::vector<double>& mu, int nv, std::vector<double>& Z) {
+  double tn = 0;
+  for (int i = 0; i < n; ++i) tn = std::max(tn, std::fabs(d[i]) + (i > 0 ? std::fabs(e[i - 1]) : 0.0) +
+                                                     (i + 1 < n ? std::fabs(e[i]) : 0.0));
+  const double tiny = 1e-15 * std::max(tn, 1e-300);
+  Z.assign((size_t)n * nv, 0.0);
+  std::vector<double> u0(n), u1(n), u2(n), lm(n), x(n);
+  std::vector<char> piv(n);
+  for (int j = 0; j < nv; ++j) {
+    const double m = mu[j];
+    // factorisation of T - m I with row interchanges: U has three diagonals
+    double a0 = d[0] - m, a1 = (n > 1) ? e[0] : 0.0, a2 = 0.0;
+    for (int i = 0; i + 1 < n; ++i) {
+      const double sub = e[i], dn = d[i + 1] - m, up = (i + 2 < n) ? e[i + 1] : 0.0;
+      if (std::fabs(sub) > std::fabs(a0)) {
+        const double f = a0 / sub;
+        u0[i] = sub;
+        u1[i] = dn;
+        u2[i] = up;
+        lm[i] = f;
+        piv[i] = 1;
+        a0 = a1 - f * dn;
+        a1 = a2 - f * up;
+        a2 = 0.0;
+      } else {
+        if (std::fabs(a0) < tiny) a0 = tiny;
+        const double f = sub / a0;
+        u0[i] = a0;
+        u1[i] = a1;
+        u2[i] = a2;
+        lm[i] = f;
+        piv[i] = 0;
+        a0 = dn - f * a1;
+        a1 = up - f * a2;
+        a2 = 0.0;
+      }
+    }
+    if (std::fabs(a0) < tiny) a0 = tiny;
+    u0[n - 1] = a0;
+    u1[n - 1] = u2[n - 1] = 0.0;
+    for (int i = 0; i < n; ++i) x[i] = 1.0 + 0.1 * std::sin(0.7 * i + 0.3 * j);  // fixed start vector
+    for (int it = 0; it < 3; ++it) {
+      for (int i = 0; i + 1 < n; ++i) {
+        if (piv[i]) std::swap(x[i], x[i + 1]);
+        x[i + 1] -= lm[i] * x[i];
+      }
+      x[n - 1] /= u0[n - 1];
+      if (n > 1) x[n - 2] = (x[n - 2] - u1[n - 2] * x[n - 1]) / u0[n - 2];
+      for (int i = n - 3; i >= 0; --i) x[i] = (x[i] - u1[i] * x[i + 1] - u2[i] * x[i + 2]) / u0[i];
+      for (int pass = 0; pass < 2; ++pass)
+        for (int q = j - 1; q >= 0 && mu[j] - mu[q] < 1e-3 * tn; --q) {
+          const double* zq = &Z[(size_t)q * n];
+          double dot = 0;
+          for (int i = 0; i < n; ++i) dot += zq[i] * x[i];
+          for (int i = 0; i < n; ++i) x[i] -= dot * zq[i];
+        }
+      double nrm = 0;
+      for (int i = 0; i < n; ++i) nrm += x[i] * x[i];
+      nrm = std::sqrt(nrm);
+      if (!(nrm > 0)) nrm = 1.0;
+      for (int i = 0; i < n; ++i) x[i] /= nrm;
+    }
+    std::copy(x.begin(), x.end(), Z.begin() + (size_t)j * n);
+  }
+}
+
 }  // namespace
 
-int sym_eig_host(int n, std::vector<double> A, std::vector<double>& lam, std::vector<double>& V) {
+int sym_eig_host(int n, std::vector<double> A, std::vector<double>& lam, std::vector<double>& V, int nvec) {
   std::vector<double> d, e;
   Reflectors R;
-  householder_tridiag(n, A, d, e, R);
+  const int T = std::min<int>(16, (int)std::max(1u, std::thread::hardware_concurrency()));
+  if (n >= 384 && T > 1)
+    householder_tridiag_threads(n, A, d, e, R, T);
+  else
+    householder_tridiag(n, A, d, e, R);
+  if (nvec < 0 || nvec > n) nvec = n;
+  if (nvec < n) {
+    // eigenvalues by QR without vectors, eigenvectors of the lowest nvec by
+    // inverse iteration, back-transformed by the reflectors
+    std::vector<double> dq(d), eq(e);
+    if (!tridiag_qr(n, dq, eq, nullptr)) return BPJD_ERR_BREAKDOWN;
+    std::sort(dq.begin(), dq.end());
+    std::vector<double> Zc;
+    tridiag_inverse_iteration(n, d, e, dq, nvec, Zc);
+    parallel_ranges(nvec, [&](int c0, int c1) { apply_q(n, R, Zc, c0, c1); });
+    lam = dq;
+    V.assign((size_t)n * n, 0.0);
+    for (int j = 0; j < nvec; ++j)
+      for (int i = 0; i < n; ++i) V[(size_t)i * n + j] = Zc[(size_t)j * n + i];
+    return BPJD_OK;
+  }
   std::vector<Rot> rots;
   rots.reserve((size_t)2 * n * n);
-  if (!tridiag_qr(n, d, e, rots)) return BPJD_ERR_BREAKDOWN;
+  if (!tridiag_qr(n, d, e, &rots)) return BPJD_ERR_BREAKDOWN;
   // eigenvectors of T: the rotations applied to the identity (Zc column-major;
   // each thread updates its own range of rows of every column pair)
   std::vector<double> Zc((size_t)n * n, 0.0);
@@ -231,21 +446,55 @@ int sym_eig_host(int n, std::vector<double> A, std::vector<double>& lam, std::ve
 }
 
 int gen_eig_host(int n, const std::vector<double>& K, const std::vector<double>& M, std::vector<double>& lam,
-                 std::vector<double>& Phi) {
-  // Cholesky M = L L^T (lower, row-major)
+                 std::vector<double>& Phi, int nvec) {
+  if (nvec < 0 || nvec > n) nvec = n;
+  // Cholesky M = L L^T (lower, row-major), column by column; for large n the
+  // rows below the diagonal of a column are shared among threads
   std::vector<double> L((size_t)n * n, 0.0);
-  for (int j = 0; j < n; ++j) {
-    double s = M[(size_t)j * n + j];
-    for (int p = 0; p < j; ++p) s -= L[(size_t)j * n + p] * L[(size_t)j * n + p];
-    if (!(s > 0.0)) return BPJD_ERR_BREAKDOWN;
-    const double ljj = std::sqrt(s);
-    L[(size_t)j * n + j] = ljj;
-    for (int i = j + 1; i < n; ++i) {
+  const int T = std::min<int>(16, (int)std::max(1u, std::thread::hardware_concurrency()));
+  bool spd = true;
+  auto col_rows = [&](int j, int i0, int i1) {
+    const double ljj = L[(size_t)j * n + j];
+    const double* lj = &L[(size_t)j * n];
+    for (int i = i0; i < i1; ++i) {
+      const double* li = &L[(size_t)i * n];
       double t = M[(size_t)i * n + j];
-      for (int p = 0; p < j; ++p) t -= L[(size_t)i * n + p] * L[(size_t)j * n + p];
+      for (int p = 0; p < j; ++p) t -= li[p] * lj[p];
       L[(size_t)i * n + j] = t / ljj;
     }
+  };
+  auto diag = [&](int j) {
+    double s = M[(size_t)j * n + j];
+    for (int p = 0; p < j; ++p) s -= L[(size_t)j * n + p] * L[(size_t)j * n + p];
+    if (!(s > 0.0)) {
+      spd = false;
+      s = 1.0;
+    }
+    L[(size_t)j * n + j] = std::sqrt(s);
+  };
+  if (n >= 384 && T > 1) {
+    SpinBarrier bar(T);
+    auto body = [&](int tid) {
+      for (int j = 0; j < n; ++j) {
+        if (tid == 0) diag(j);
+        bar.wait();
+        const int rows = n - j - 1, per = (rows + T - 1) / T;
+        const int i0 = j + 1 + tid * per, i1 = std::min(n, i0 + per);
+        if (i0 < i1) col_rows(j, i0, i1);
+        bar.wait();
+      }
+    };
+    std::vector<std::thread> th;
+    for (int t = 1; t < T; ++t) th.emplace_back(body, t);
+    body(0);
+    for (auto& x : th) x.join();
+  } else {
+    for (int j = 0; j < n; ++j) {
+      diag(j);
+      col_rows(j, j + 1, n);
+    }
   }
+  if (!spd) return BPJD_ERR_BREAKDOWN;
   // Y = L^{-1} K  (forward substitution, row by row, on a column range)
   std::vector<double> Y(K);
   parallel_ranges(n, [&](int c0, int c1) {
@@ -276,11 +525,11 @@ int gen_eig_host(int n, const std::vector<double>& K, const std::vector<double>&
       C[(size_t)i * n + j] = C[(size_t)j * n + i] = s;
     }
   std::vector<double> Qv;
-  const int rc = sym_eig_host(n, std::move(C), lam, Qv);
+  const int rc = sym_eig_host(n, std::move(C), lam, Qv, nvec);
   if (rc != BPJD_OK) return rc;
   // Phi = L^{-T} Q  (backward substitution, row by row, on a column range)
   Phi = std::move(Qv);
-  parallel_ranges(n, [&](int c0, int c1) {
+  parallel_ranges(nvec, [&](int c0, int c1) {
     for (int i = n - 1; i >= 0; --i) {
       double* fi = &Phi[(size_t)i * n];
       for (int p = i + 1; p < n; ++p) {
