@@ -703,10 +703,11 @@ extern "C" int bpjd_solve(bpjd_handle* hh, double* eigvals, double* eigvecs, int
     if (trace_on())
       std::fprintf(stderr,
                    "{\"bpjd_iter\": %d, \"max_rel_resid\": %.6e, \"sum_abs_dlambda\": %.6e, \"kept\": %d, "
-                   "\"jacobi_sweeps\": %d, \"rr_kcycles\": [%lld, %lld, %lld, %lld, %lld, %lld]}\n",
+                   "\"jacobi_sweeps\": %d, \"rr_kcycles\": [%lld, %lld, %lld, %lld, %lld, %lld, %lld]}\n",
                    it, h.hstat->max_res, h.hstat->sum_dl, h.hstat->kept, h.hstat->sweeps,
                    h.hstat->rr_cycles[0] / 1000, h.hstat->rr_cycles[1] / 1000, h.hstat->rr_cycles[2] / 1000,
-                   h.hstat->rr_cycles[3] / 1000, h.hstat->rr_cycles[4] / 1000, h.hstat->rr_cycles[5] / 1000);
+                   h.hstat->rr_cycles[3] / 1000, h.hstat->rr_cycles[4] / 1000, h.hstat->rr_cycles[5] / 1000,
+                   h.hstat->rr_cycles[6] / 1000);
     if (h.hstat->converged) {
       converged = true;
       break;

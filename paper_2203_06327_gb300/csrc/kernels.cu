@@ -2104,12 +2104,9 @@ __device__ int jacobi_eig_dw(float* Ah, float* Al, float* A2h, float* A2l, float
     else
       ar[u] = ac[u] = -1;
   }
-  int vx[4], vr[4];
-  for (int u = 0; u < 4; ++u) {
-    const int t = tid + u * (int)blockDim.x;
-    vx[u] = (t < mp * mp) ? t / mp : -1;
-    vr[u] = (t < mp * mp) ? t % mp : 0;
-  }
+  // rotation parameters of the current sweep (double-word), kept in the second V buffer
+  float* rcs = V2h;
+  float* rsn = V2l;
   __shared__ float amax_d;
   if (tid == 0) {
     float a = 0.f;
@@ -2172,6 +2169,11 @@ __device__ int jacobi_eig_dw(float* Ah, float* Al, float* A2h, float* A2l, float
         fr[q] = c;
         gr[q] = s;
         partner[q] = p;
+        const int ri = round * half + tid;  // for the update of V after the sweep
+        rcs[2 * ri] = c.hi;
+        rcs[2 * ri + 1] = c.lo;
+        rsn[2 * ri] = s.hi;
+        rsn[2 * ri + 1] = s.lo;
       }
       __syncthreads();
 #pragma unroll
@@ -2187,15 +2189,6 @@ __device__ int jacobi_eig_dw(float* Ah, float* Al, float* A2h, float* A2l, float
         A2h[c * ld + r] = v.hi;
         A2l[c * ld + r] = v.lo;
       }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        if (vx[u] < 0) continue;
-        const int x = vx[u], r = vr[u];
-        const int rb = partner[r];
-        const dw v = dw_lin2(fr[r], Vh[x * ld + r], Vl[x * ld + r], gr[r], Vh[x * ld + rb], Vl[x * ld + rb]);
-        V2h[x * ld + r] = v.hi;
-        V2l[x * ld + r] = v.lo;
-      }
       __syncthreads();
       float* t0 = Ah;
       Ah = A2h;
@@ -2203,13 +2196,29 @@ __device__ int jacobi_eig_dw(float* Ah, float* Al, float* A2h, float* A2l, float
       t0 = Al;
       Al = A2l;
       A2l = t0;
-      t0 = Vh;
-      Vh = V2h;
-      V2h = t0;
-      t0 = Vl;
-      Vl = V2l;
-      V2l = t0;
     }
+    // V <- V J_1 ... J_{mp-1}: a warp per row of V, one lane per rotation of a
+    // round (disjoint columns), rounds in order
+    for (int x = tid >> 5; x < mp; x += (int)blockDim.x >> 5) {
+      const int lane = tid & 31;
+      for (int round = 0; round < mp - 1; ++round) {
+        if (lane < half) {
+          const int ri = round * half + lane;
+          const int p = tp[ri], q = tq[ri];
+          const dw c = {rcs[2 * ri], rcs[2 * ri + 1]}, sn = {rsn[2 * ri], rsn[2 * ri + 1]};
+          const dw msn = {-sn.hi, -sn.lo};
+          const float vph = Vh[x * ld + p], vpl = Vl[x * ld + p], vqh = Vh[x * ld + q], vql = Vl[x * ld + q];
+          const dw np = dw_lin2(c, vph, vpl, msn, vqh, vql);
+          const dw nq = dw_lin2(c, vqh, vql, sn, vph, vpl);
+          Vh[x * ld + p] = np.hi;
+          Vl[x * ld + p] = np.lo;
+          Vh[x * ld + q] = nq.hi;
+          Vl[x * ld + q] = nq.lo;
+        }
+        __syncwarp();
+      }
+    }
+    __syncthreads();
   }
   *Aoh = Ah;
   *Aol = Al;
@@ -2279,12 +2288,9 @@ __device__ int jacobi_f32(float* A, float* A2, float* V, float* V2, int m, float
     else
       ar[u] = ac[u] = -1;
   }
-  int vx[4], vr[4];
-  for (int u = 0; u < 4; ++u) {
-    const int t = tid + u * (int)blockDim.x;
-    vx[u] = (t < mp * mp) ? t / mp : -1;
-    vr[u] = (t < mp * mp) ? t % mp : 0;
-  }
+  // rotation parameters of the current sweep, kept in the second V buffer
+  float* rc = V2;
+  float* rs = V2 + kRRMax * kRRMax / 2;
   __syncthreads();
   const int half = mp / 2;
   __shared__ float amax_f;
@@ -2329,6 +2335,8 @@ __device__ int jacobi_f32(float* A, float* A2, float* V, float* V2, int m, float
         fr[q] = c;
         gr[q] = s;
         partner[q] = p;
+        rc[round * half + tid] = c;  // for the update of V after the sweep
+        rs[round * half + tid] = s;
       }
       __syncthreads();
 #pragma unroll
@@ -2341,20 +2349,27 @@ __device__ int jacobi_f32(float* A, float* A2, float* V, float* V2, int m, float
         A2[r * ld + c] = v;
         A2[c * ld + r] = v;
       }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        if (vx[u] < 0) continue;
-        const int x = vx[u], r = vr[u];
-        V2[x * ld + r] = V[x * ld + r] * fr[r] + V[x * ld + partner[r]] * gr[r];
-      }
       __syncthreads();
       float* tA = A;
       A = A2;
       A2 = tA;
-      float* tV = V;
-      V = V2;
-      V2 = tV;
     }
+    // V <- V J_1 ... J_{mp-1}: a warp per row of V, one lane per rotation of a
+    // round (disjoint columns), rounds in order
+    for (int x = tid >> 5; x < mp; x += (int)blockDim.x >> 5) {
+      const int lane = tid & 31;
+      for (int round = 0; round < mp - 1; ++round) {
+        if (lane < half) {
+          const int p = tp[round * half + lane], q = tq[round * half + lane];
+          const float c = rc[round * half + lane], sn = rs[round * half + lane];
+          const float vp = V[x * ld + p], vq = V[x * ld + q];
+          V[x * ld + p] = c * vp - sn * vq;
+          V[x * ld + q] = sn * vp + c * vq;
+        }
+        __syncwarp();
+      }
+    }
+    __syncthreads();
   }
   *Aout = A;
   *Vout = V;
@@ -2612,6 +2627,7 @@ __global__ void k_rayleigh_ritz_chol(int m, int k, const double* __restrict__ G,
         st->kept = m;
         st->sweeps = sw;
         if (stop_rule == BPJD_STOP_DLAMBDA) st->converged = (dl < tol) ? 1 : 0;
+        st->rr_cycles[6] = clock64() - tcl[0];  // the whole kernel body
       }
       return;
     }
