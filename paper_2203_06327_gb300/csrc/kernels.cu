@@ -1332,20 +1332,304 @@ __global__ void __launch_bounds__(128, (BMAX <= 40) ? 3 : 2) k_local_factor_mma(
 }
 
 // ---------------------------------------------------------------------------
+// Local solves, forward phase, blocked, for wide windows (B_pad = 64 or 96,
+// e.g. 3-D subdomains): one CTA per (subdomain, shift) with one thread per
+// window row (W = B_pad + 8 rows, NW = W / 32 rounded up warps).  The window
+// lives (negated) in m16n8k8 accumulator tiles; warp w owns the column tiles
+// ct = w, w + NW, ... of every row tile.  Per block step of eight columns:
+//   1. the warp owning the pivot column block writes it to shared memory;
+//   2. every thread reads its row of the panel and the 8 x 8 diagonal block,
+//      factorises the diagonal block redundantly in registers and solves for
+//      its own row of L (no barrier per column), eliminating its right-hand
+//      side entry; pivot rows store 1/L_jj, all rows their L entries;
+//   3. the L panel returns to shared memory and each warp applies the
+//      trailing update W <- W - L L^T to its tiles (TF32 head/tail split);
+//   4. each warp writes the entering band rows into its column tiles (values
+//      read from the FP32 band in global memory at the start of the step).
+// Records and y have the layout of k_local_factor_mma, so k_local_backward
+// completes the solve.
+// ---------------------------------------------------------------------------
+template <int BMAX>
+struct WideShape {
+  static constexpr int W = BMAX + 8;
+  static constexpr int NBW = W / 8;
+  static constexpr int RT = (W + 15) / 16;
+  static constexpr int CT = NBW;
+  // warps per CTA: one window row per thread, and at most three column tiles per warp
+  static constexpr int NW = ((W + 31) / 32 > (CT + 2) / 3) ? (W + 31) / 32 : (CT + 2) / 3;
+  static constexpr int CTW = (CT + NW - 1) / NW;  // column tiles per warp (at most)
+  static constexpr int PSTR = 12;
+};
+
+template <int BMAX>
+__global__ void __launch_bounds__(WideShape<BMAX>::NW * 32, 2) k_local_factor_wide(
+    int npairs, int k, const int64_t* __restrict__ sub_ptr, const int32_t* __restrict__ sub_dofs,
+    const float* __restrict__ bandK, const float* __restrict__ bandM, const double* __restrict__ lam,
+    const double* __restrict__ rho, float* __restrict__ Lbuf, float* __restrict__ wpk, int32_t* err) {
+  using S = WideShape<BMAX>;
+  constexpr int W = S::W, NBW = S::NBW, RT = S::RT, CT = S::CT, NW = S::NW, CTW = S::CTW, PSTR = S::PSTR;
+  static_assert(BMAX % 8 == 0 && CTW * 4 * RT <= 128, "window too wide for the register tiles");
+  __shared__ __align__(16) float pbuf[RT * 16 * PSTR];  // panel, then L operand; rows >= W stay zero
+  __shared__ float srhs[8];
+  const int tid = threadIdx.x, lane_id = tid & 31, wid = tid >> 5;
+  const int lane_g = lane_id >> 2, lane_q = lane_id & 3;
+  const int pair = blockIdx.x;
+  if (pair >= npairs) return;
+  const int l = pair / k, i = pair % k;
+  const int64_t off = sub_ptr[l];
+  const int nl = (int)(sub_ptr[l + 1] - off);
+  const int32_t* dofs = sub_dofs + off;
+  const float lm = (float)lam[i];
+  float* Lrec = Lbuf + ((size_t)off * k + (size_t)i * nl) * BMAX;
+  float* yout = wpk + off * k + i;
+  const float* gK = bandK + (size_t)off * BMAX;  // band row p at gK + p * BMAX, diagonal at BMAX - 1
+  const float* gM = bandM + (size_t)off * BMAX;
+  for (int e = tid; e < RT * 16 * PSTR; e += blockDim.x) pbuf[e] = 0.f;
+  // shifted entry (p, q), q <= p (identity rows beyond nl)
+  auto a0 = [&](int p, int q) -> float {
+    if (p >= nl) return (p == q) ? 1.f : 0.f;
+    const int d = p - q;
+    if (d > BMAX - 1 || q < 0) return 0.f;
+    const int e = BMAX - 1 - d;
+    return gK[(size_t)p * BMAX + e] - lm * gM[(size_t)p * BMAX + e];
+  };
+  auto rhs = [&](int p) -> float { return (p < nl) ? (float)rho[(int64_t)dofs[p] * k + i] : 0.f; };
+  // initial window rows 0..W-1 (negated, both triangles) in this warp's column tiles
+  float acc[RT][CTW][4];
+#pragma unroll
+  for (int rt = 0; rt < RT; ++rt)
+#pragma unroll
+    for (int jl = 0; jl < CTW; ++jl)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int ct = wid + NW * jl;
+        const int u = rt * 16 + lane_g + 8 * (e >> 1), v = ct * 8 + 2 * lane_q + (e & 1);
+        acc[rt][jl][e] = (ct < CT && u < W) ? -((u >= v) ? a0(u, v) : a0(v, u)) : 0.f;
+      }
+  float r = (tid < W) ? rhs(tid) : 0.f;  // right-hand side of this thread's window row
+  bool bad = false;
+  int jm = 0;  // j0 mod BMAX
+  __syncthreads();
+  for (int c = 0; c * W < nl; ++c) {
+#pragma unroll
+    for (int sb = 0; sb < NBW; ++sb) {
+      const int j0 = c * W + 8 * sb;
+      if (j0 >= nl) break;
+      int zero;
+      asm volatile("mov.u32 %0, 0;" : "=r"(zero));
+      const int g = lane_g + zero, q = lane_q + zero, t = tid + zero;
+      // entering band rows j0 + W + g (this lane's row of the entering block) for the
+      // row part of this warp's column tiles, read now and written in step 4
+      const int pnew = j0 + W + g;
+      const bool realg = pnew < nl;
+      float ek[CTW][2], em[CTW][2];
+#pragma unroll
+      for (int jl = 0; jl < CTW; ++jl)
+#pragma unroll
+        for (int e2 = 0; e2 < 2; ++e2) {
+          const int ct = wid + NW * jl;
+          float kv = 0.f, mv = 0.f;
+          int pr = pnew, ps = -1;
+          if (ct < CT) {
+            if (ct != sb) {
+              // column slot ct 8 + 2 q + e2 holds row j0 + dv, dv = ((ct - sb) mod NBW) 8 + 2 q + e2
+              ps = ((ct - sb + NBW) % NBW) * 8 + e2 - 9 + 2 * q - g;
+            } else {
+              const int du2 = 2 * q + e2;
+              pr = (g >= du2) ? pnew : j0 + W + du2;  // the later row of the pair
+              ps = BMAX - 1 - ((g >= du2) ? g - du2 : du2 - g);
+            }
+          }
+          if (ps >= 0 && pr < nl) {
+            kv = gK[(size_t)pr * BMAX + ps];
+            mv = gM[(size_t)pr * BMAX + ps];
+          }
+          ek[jl][e2] = kv;
+          em[jl][e2] = mv;
+        }
+      const int d8 = t - 8 * sb;  // position of this row in the pivot block (0..7 there)
+      const float rnew = (d8 >= 0 && d8 < 8) ? rhs(pnew - g + d8) : 0.f;
+      // 1. pivot column block -> pbuf[slot][0..7]; pivot right-hand sides -> srhs
+      if (wid == sb % NW) {
+#pragma unroll
+        for (int rt = 0; rt < RT; ++rt) {
+          *reinterpret_cast<float2*>(pbuf + (rt * 16 + g) * PSTR + 2 * q) =
+              make_float2(acc[rt][sb / NW][0], acc[rt][sb / NW][1]);
+          *reinterpret_cast<float2*>(pbuf + (rt * 16 + g + 8) * PSTR + 2 * q) =
+              make_float2(acc[rt][sb / NW][2], acc[rt][sb / NW][3]);
+        }
+      }
+      if (d8 >= 0 && d8 < 8) srhs[d8] = r;
+      __syncthreads();
+      // 2. own row of the panel and the diagonal block, both negated back
+      int dr = t - 8 * sb;
+      dr += (dr < 0) ? W : 0;
+      const bool row_ok = t < W;
+      float p[8];
+      {
+        const float4 x0 = *reinterpret_cast<const float4*>(pbuf + (row_ok ? t : 0) * PSTR);
+        const float4 x1 = *reinterpret_cast<const float4*>(pbuf + (row_ok ? t : 0) * PSTR + 4);
+        p[0] = -x0.x; p[1] = -x0.y; p[2] = -x0.z; p[3] = -x0.w;
+        p[4] = -x1.x; p[5] = -x1.y; p[6] = -x1.z; p[7] = -x1.w;
+      }
+      float D[8][8];  // lower triangle used
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        const float4 x0 = *reinterpret_cast<const float4*>(pbuf + (8 * sb + a) * PSTR);
+        const float4 x1 = *reinterpret_cast<const float4*>(pbuf + (8 * sb + a) * PSTR + 4);
+        D[a][0] = -x0.x; D[a][1] = -x0.y; D[a][2] = -x0.z; D[a][3] = -x0.w;
+        D[a][4] = -x1.x; D[a][5] = -x1.y; D[a][6] = -x1.z; D[a][7] = -x1.w;
+      }
+      float yv[8];
+#pragma unroll
+      for (int a = 0; a < 8; ++a) yv[a] = srhs[a];
+      __syncthreads();  // pbuf and srhs are rewritten below
+      // Cholesky of the diagonal block (every thread), inverse diagonal in dinv
+      float dinv[8];
+#pragma unroll
+      for (int cc = 0; cc < 8; ++cc) {
+        float s = D[cc][cc];
+#pragma unroll
+        for (int b = 0; b < cc; ++b) s = fmaf(-D[cc][b], D[cc][b], s);
+        bad |= !(s > 0.f);
+        const float inv = rsqrtf(s);
+        dinv[cc] = inv;
+        D[cc][cc] = s * inv;
+#pragma unroll
+        for (int a = cc + 1; a < 8; ++a) {
+          float v = D[a][cc];
+#pragma unroll
+          for (int b = 0; b < cc; ++b) v = fmaf(-D[a][b], D[cc][b], v);
+          D[a][cc] = v * inv;
+        }
+      }
+      // y = L_dd^{-1} rhs of the pivot rows
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        float v = yv[a];
+#pragma unroll
+        for (int b = 0; b < a; ++b) v = fmaf(-D[a][b], yv[b], v);
+        yv[a] = v * dinv[a];
+      }
+      // own row of L: l = p L_dd^{-T}; for a pivot row (dr < 8) this reproduces row dr
+      // of L_dd, whose entries past the diagonal are cleared
+      float lr[8];
+#pragma unroll
+      for (int cc = 0; cc < 8; ++cc) {
+        float v = p[cc];
+#pragma unroll
+        for (int b = 0; b < cc; ++b) v = fmaf(-lr[b], D[cc][b], v);
+        lr[cc] = v * dinv[cc];
+      }
+      if (dr < 8) {
+#pragma unroll
+        for (int cc = 0; cc < 8; ++cc)
+          if (cc > dr) lr[cc] = 0.f;
+      } else {
+#pragma unroll
+        for (int cc = 0; cc < 8; ++cc) r = fmaf(-lr[cc], yv[cc], r);
+      }
+      if (!row_ok) {
+#pragma unroll
+        for (int cc = 0; cc < 8; ++cc) lr[cc] = 0.f;
+      }
+      // records: column j0 + cc holds L(row, j0 + cc) at row mod BMAX, 1/L_jj at the pivot
+      if (row_ok) {
+        int pos = jm + dr;
+        pos -= (pos >= BMAX) ? BMAX : 0;
+        pos -= (pos >= BMAX) ? BMAX : 0;
+        float* rec = Lrec + (size_t)j0 * BMAX + pos;
+#pragma unroll
+        for (int cc = 0; cc < 8; ++cc) {
+          const int tt = dr - cc;
+          if (j0 + cc < nl && tt >= 0 && tt < BMAX) rec[(size_t)cc * BMAX] = (tt == 0) ? dinv[cc] : lr[cc];
+        }
+      }
+      if (t == 0) {
+#pragma unroll
+        for (int cc = 0; cc < 8; ++cc)
+          if (j0 + cc < nl) yout[(size_t)(j0 + cc) * k] = yv[cc];
+      }
+      // 3. L panel -> pbuf, trailing update of this warp's tiles
+      if (row_ok) {
+        *reinterpret_cast<float4*>(pbuf + t * PSTR) = make_float4(lr[0], lr[1], lr[2], lr[3]);
+        *reinterpret_cast<float4*>(pbuf + t * PSTR + 4) = make_float4(lr[4], lr[5], lr[6], lr[7]);
+      }
+      __syncthreads();
+      uint32_t bh[CTW][2], bl[CTW][2];
+#pragma unroll
+      for (int jl = 0; jl < CTW; ++jl) {
+        const int ct = wid + NW * jl;
+        const int row = (ct < CT ? ct : 0) * 8 + g;
+        const float x0 = pbuf[row * PSTR + q], x1 = pbuf[row * PSTR + q + 4];
+        bh[jl][0] = to_tf32(x0);
+        bl[jl][0] = to_tf32(x0 - __uint_as_float(bh[jl][0]));
+        bh[jl][1] = to_tf32(x1);
+        bl[jl][1] = to_tf32(x1 - __uint_as_float(bh[jl][1]));
+      }
+#pragma unroll
+      for (int rt = 0; rt < RT; ++rt) {
+        float x[4];
+        x[0] = pbuf[(rt * 16 + g) * PSTR + q];
+        x[1] = pbuf[(rt * 16 + g + 8) * PSTR + q];
+        x[2] = pbuf[(rt * 16 + g) * PSTR + q + 4];
+        x[3] = pbuf[(rt * 16 + g + 8) * PSTR + q + 4];
+        uint32_t ah[4], al[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          ah[e] = to_tf32(x[e]);
+          al[e] = to_tf32(x[e] - __uint_as_float(ah[e]));
+        }
+#pragma unroll
+        for (int jl = 0; jl < CTW; ++jl) {
+          if (wid + NW * jl >= CT) continue;
+          mma_tf32(acc[rt][jl], al, bh[jl][0], bh[jl][1]);
+          mma_tf32(acc[rt][jl], ah, bl[jl][0], bl[jl][1]);
+          mma_tf32(acc[rt][jl], ah, bh[jl][0], bh[jl][1]);
+        }
+      }
+      // 4. entering rows into slot block sb (row tile sb / 2, half sb % 2), negated
+      {
+        const int rtn = sb >> 1, hn = sb & 1;
+#pragma unroll
+        for (int jl = 0; jl < CTW; ++jl)
+#pragma unroll
+          for (int e2 = 0; e2 < 2; ++e2) {
+            const int ct = wid + NW * jl;
+            float val = fmaf(lm, em[jl][e2], -ek[jl][e2]);
+            if (ct == sb) {
+              const int du2 = 2 * q + e2;
+              const int pr = (g >= du2) ? pnew : j0 + W + du2;
+              if (pr >= nl) val = (g == du2) ? -1.f : 0.f;
+            }
+            acc[rtn][jl][2 * hn + e2] = val;
+          }
+      }
+      if (d8 >= 0 && d8 < 8) r = rnew;
+      __syncthreads();  // pbuf is rewritten by the next extraction
+      jm += 8;
+      jm -= (jm >= BMAX) ? BMAX : 0;
+    }
+  }
+  if (bad && tid == 0) atomicOr(err, 1);
+}
+
+// ---------------------------------------------------------------------------
 // Local solves, backward phase: L^T x = y for every (subdomain, shift), L in
 // slot order as written by the factorisation (row j of the record holds
 // L(row(v), j) at slot v and 1/L_jj at slot j mod BMAX).  A warp serves four
 // shifts of one subdomain, eight lanes each; lane e of a group owns the window
 // slots e + 8 c and keeps x of their rows in registers, so a row costs one
-// eight-lane reduction.  The records enter shared memory half a window group
-// (R = BMAX / 2 rows) at a time through one bulk copy per shift, double
-// buffered (the upper half of a group always in buffer 1, the lower in buffer
-// 0, so slots and buffers are static in the unrolled loop); y of the next
-// chunk is loaded into registers one chunk ahead.
+// eight-lane reduction.  The records enter shared memory R rows at a time (half
+// a window group up to windows of 48, 16 rows beyond) through one bulk copy
+// per shift, double buffered; a window group holds an even number of chunks,
+// so slots and buffers are static in the unrolled loop; y of the next chunk is
+// loaded into registers one chunk ahead.
 // ---------------------------------------------------------------------------
 template <int BMAX>
 struct BwdShape {
-  static constexpr int R = BMAX / 2;
+  static constexpr int R = (BMAX <= 48) ? BMAX / 2 : 16;  // rows per staged chunk
+  static constexpr int NCH = BMAX / R;                    // chunks per window group (even)
   static constexpr int PS = R * BMAX + 8;  // per-shift buffer stride: shifts land on different banks
   static constexpr int WPB = 2;            // warps per block
   static constexpr size_t smem_floats = (size_t)WPB * 2 * 4 * PS;
@@ -1411,10 +1695,13 @@ __global__ void __launch_bounds__(64) k_local_backward(int nsub, int k, const in
   for (int c = 0; c < TC; ++c) xw[c] = 0.f;
   uint32_t ph[2] = {0u, 0u};
   bool timeout = false;
-  for (int g = chtop / 2; g >= 0; --g) {
+  constexpr int NCH = S::NCH;
+  static_assert(NCH % 2 == 0, "chunk parity must be static inside a window group");
+  for (int g = chtop / NCH; g >= 0; --g) {
 #pragma unroll
-    for (int half = 1; half >= 0; --half) {
-      const int ch = 2 * g + half;
+    for (int hc = NCH - 1; hc >= 0; --hc) {
+      const int ch = g * NCH + hc;
+      const int half = hc & 1;  // buffer of chunk ch
       if (ch > chtop) continue;
       __syncwarp();  // the buffer of chunk ch - 1 (chunk ch + 1's) is no longer read
       if (lane == 0 && !timeout) {
@@ -1430,7 +1717,7 @@ __global__ void __launch_bounds__(64) k_local_backward(int nsub, int k, const in
 #pragma unroll
       for (int r = R - 1; r >= 0; --r) {
         const int j = ch * R + r;
-        const int s = half * R + r;  // j mod BMAX
+        const int s = hc * R + r;  // j mod BMAX
         if (j < nl) {
           const float* row = Lb + r * BMAX;
           float part = 0.f, dg = 0.f;
@@ -3299,7 +3586,7 @@ int launch_precond(Handle& h, const double* rho, const double* lam, double* Z) {
   {
     ProfScope ps(h, BPJD_PROF_LOCAL);
     const bool f32 = (h.precision == BPJD_MIXED);
-    h.launches += (f32 && h.Bpad > 0 && h.Bpad <= 48) ? 2 : 1;  // factorisation + backward substitution
+    h.launches += (f32 && h.Bpad > 0 && h.Bpad <= 96) ? 2 : 1;  // factorisation + backward substitution
     if (f32 && h.Bpad > 0) {
       const int blocks = h.nsub * ((k + kLocalWarps - 1) / kLocalWarps);
 #define BPJD_LOCAL_TILE(BM)                                                                                    \
@@ -3325,15 +3612,18 @@ int launch_precond(Handle& h, const double* rho, const double* lam, double* Z) {
         BPJD_LOCAL_TILE(32)
         BPJD_LOCAL_TILE(40)
         BPJD_LOCAL_TILE(48)
-        case 64:
-          k_local_band_reg<64><<<(npairs + 3) / 4, 128, 0, h.stream>>>(npairs, k, h.sub_ptr, h.sub_dofs, 64,
-                                                                      h.bandKf, h.bandMf, lam, rho,
-                                                                      (float*)h.Lbuf, (float*)h.wpk, h.derr);
-          break;
-        case 96:
-          k_local_band_team<96><<<npairs, 96, 0, h.stream>>>(npairs, k, h.sub_ptr, h.sub_dofs, h.bandKf, h.bandMf,
-                                                             lam, rho, (float*)h.Lbuf, (float*)h.wpk, h.derr);
-          break;
+#define BPJD_LOCAL_WIDE(BM)                                                                                    \
+  case BM: {                                                                                                   \
+    k_local_factor_wide<BM><<<npairs, 32 * WideShape<BM>::NW, 0, h.stream>>>(                                 \
+        npairs, k, h.sub_ptr, h.sub_dofs, h.bandKf, h.bandMf, lam, rho, (float*)h.Lbuf, (float*)h.wpk, h.derr); \
+    const size_t bsm = sizeof(float) * BwdShape<BM>::smem_floats;                                              \
+    allow_dynamic_smem((const void*)k_local_backward<BM>);                                                     \
+    k_local_backward<BM><<<bwd_blocks, 32 * BwdShape<BM>::WPB, bsm, h.stream>>>(                               \
+        h.nsub, k, h.sub_ptr, (const float*)h.Lbuf, (float*)h.wpk, h.derr);                                    \
+    break;                                                                                                     \
+  }
+        BPJD_LOCAL_WIDE(64)
+        BPJD_LOCAL_WIDE(96)
         case 128:
           k_local_band_team<128><<<npairs, 128, 0, h.stream>>>(npairs, k, h.sub_ptr, h.sub_dofs, h.bandKf,
                                                                h.bandMf, lam, rho, (float*)h.Lbuf, (float*)h.wpk,
@@ -3343,6 +3633,7 @@ int launch_precond(Handle& h, const double* rho, const double* lam, double* Z) {
           return (int)cudaErrorInvalidValue;
       }
 #undef BPJD_LOCAL_TILE
+#undef BPJD_LOCAL_WIDE
     } else {
       const size_t esz = f32 ? sizeof(float) : sizeof(double);
       const size_t per_warp = (size_t)(B * B + 3 * B) * esz;

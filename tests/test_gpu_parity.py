@@ -54,11 +54,12 @@ def test_spmm_matches_oracle(c1_oracle, ncols):
         assert np.all(np.abs(Y.cpu().numpy() - ref) <= 1e-13 * scale + 1e-300)
 
 
-# band windows 14, 17, 31, 37, 43 (tiled kernel, tiers 16..48), 92 and 111 (one CTA per pair, tiers 96, 128)
+# band windows 14, 17, 31, 37, 43 (blocked tensor-core kernel, tiers 16..48), 58 and 92 (the
+# several-warp blocked kernel, tiers 64 and 96) and 111 (one CTA per pair, tier 128)
 @pytest.mark.parametrize("spec", [config_c1(), config_small_2d(), config_small_2d(nx=112, ny=112, nsx=4, nsy=4, delta=1),
                                   config_small_2d(nx=128, ny=128, nsx=4, nsy=4, delta=2), config_small_3d(),
-                                  config_small_3d(kind="q1_3d"), config_small_3d(n=32, ns=4),
-                                  config_small_3d(n=36, ns=4)],
+                                  config_small_3d(kind="q1_3d"), config_small_3d(n=24, ns=4),
+                                  config_small_3d(n=32, ns=4), config_small_3d(n=36, ns=4)],
                          ids=lambda s: s.name)
 @pytest.mark.parametrize("precision", [B.FP64, B.MIXED], ids=["fp64", "mixed"])
 def test_preconditioner_matches_oracle(spec, precision):
