@@ -773,229 +773,6 @@ __global__ void k_local_band(int npairs, int k, const int64_t* __restrict__ sub_
   }
 }
 
-// ---------------------------------------------------------------------------
-// Local solves, register-window variant (FP32): same banded Cholesky as
-// k_local_band, with the B x B symmetric window held in registers.  Window
-// size BMAX >= B (the band is zero-padded); lane v owns window columns v and
-// v + 32 (slot u of a column = row u mod BMAX).  Steps are unrolled in groups
-// of BMAX so that the pivot slot s = j mod BMAX is a compile-time index.  The
-// column of L at step j is broadcast through shared memory; the new band row
-// j + BMAX enters slot s (each lane loads its own entry, the owner of column
-// s gathers the full row from shared memory).
-// ---------------------------------------------------------------------------
-template <int BMAX>
-__global__ void __launch_bounds__(128, (BMAX <= 32) ? 4 : ((BMAX <= 40) ? 3 : 2)) k_local_band_reg(
-    int npairs, int k, const int64_t* __restrict__ sub_ptr, const int32_t* __restrict__ sub_dofs, int Bt,
-    const float* __restrict__ bandK, const float* __restrict__ bandM, const double* __restrict__ lam,
-    const double* __restrict__ rho, float* __restrict__ Lbuf, float* __restrict__ wpk, int32_t* err) {
-  constexpr int NC = (BMAX + 31) / 32;
-  constexpr int PD = (BMAX >= 40) ? 2 : 4;  // prefetch distance (steps) of the rows entering the window
-  static_assert(BMAX % PD == 0, "the prefetch ring index must be static within a window group");
-  constexpr unsigned FULL = 0xffffffffu;
-  __shared__ __align__(16) float shm[4][3][64];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int pair = blockIdx.x * (blockDim.x >> 5) + wib;
-  if (pair >= npairs) return;
-  float* sl = shm[wib][0];
-  float* sa = shm[wib][1];
-  float* xs = shm[wib][2];
-  const int l = pair / k, i = pair % k;
-  const int64_t off = sub_ptr[l];
-  const int nl = (int)(sub_ptr[l + 1] - off);
-  const int32_t* dofs = sub_dofs + off;
-  const int bt = Bt - 1;
-  const float lm = (float)lam[i];
-  float* Lp = Lbuf + ((size_t)off * k + (size_t)i * nl) * BMAX;
-  auto aval = [&](int p, int q) -> float {  // shifted entry (p, q), q <= p
-    if (p >= nl) return (p == q) ? 1.f : 0.f;
-    const int d = p - q;
-    if (d > bt || q < 0) return 0.f;
-    const size_t e = (size_t)(off + p) * Bt + (bt - d);
-    return bandK[e] - lm * bandM[e];
-  };
-  auto rhs = [&](int p) -> float { return (p < nl) ? (float)rho[(int64_t)dofs[p] * k + i] : 0.f; };
-  // entry of row j + BMAX that column v receives at step j (slot s = j mod BMAX)
-  auto incoming = [&](int j, int s, int v) -> float {
-    int t = v - s;
-    t += (t <= 0) ? BMAX : 0;
-    return aval(j + BMAX, j + t);
-  };
-  float w[NC][BMAX];
-  float rw[NC];
-#pragma unroll
-  for (int c = 0; c < NC; ++c) {
-    const int v = lane + 32 * c;
-#pragma unroll
-    for (int u = 0; u < BMAX; ++u) {
-      float x = 0.f;
-      if (v < BMAX) x = (u >= v) ? aval(u, v) : aval(v, u);
-      w[c][u] = x;
-    }
-    rw[c] = (v < BMAX) ? rhs(v) : 0.f;
-  }
-  // prefetch ring: pre[d] holds the incoming entries of step j when j mod PD == d
-  float pre[PD][NC];
-  float rpre[PD];
-#pragma unroll
-  for (int d = 0; d < PD; ++d) {
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      const int v = lane + 32 * c;
-      pre[d][c] = (v < BMAX) ? incoming(d, d % BMAX, v) : 0.f;
-    }
-    rpre[d] = rhs(d + BMAX);
-  }
-  bool bad = false;
-  for (int j0 = 0; j0 < nl && !bad; j0 += BMAX) {
-    // an opaque zero keeps the per-slot lane offsets from being hoisted out of
-    // this loop (BMAX copies of them would otherwise occupy registers)
-    int zero;
-    asm volatile("mov.u32 %0, 0;" : "=r"(zero));
-    const int vl = lane + zero;
-#pragma unroll
-    for (int s = 0; s < BMAX; ++s) {
-      const int j = j0 + s;
-      if (j >= nl) break;
-      const int sc = s >> 5, so = s & 31;
-      const int pd = s % PD;  // ring slot of step j (j0 is a multiple of BMAX, hence of PD)
-      const float piv = __shfl_sync(FULL, w[sc][s], so);
-      if (!(piv > 0.f)) {
-        bad = true;
-        break;
-      }
-      const float inv = __frsqrt_rn(piv);
-      const float yj = __shfl_sync(FULL, rw[sc], so) * inv;
-      float lc[NC];
-#pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        const int v = vl + 32 * c;
-        lc[c] = (v < BMAX && v != s) ? w[c][s] * inv : 0.f;
-        if (v < BMAX) {
-          int t = v - s;
-          t += (t < 0) ? BMAX : 0;
-          Lp[(size_t)j * BMAX + t] = (t == 0) ? inv : lc[c];
-          sl[v] = lc[c];
-        }
-      }
-      if (lane == 0) wpk[(off + j) * k + i] = yj;
-      __syncwarp();
-#pragma unroll
-      for (int u4 = 0; u4 < BMAX; u4 += 4) {
-        const float4 q = *reinterpret_cast<const float4*>(sl + u4);
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-          w[c][u4 + 0] = fmaf(-q.x, lc[c], w[c][u4 + 0]);
-          w[c][u4 + 1] = fmaf(-q.y, lc[c], w[c][u4 + 1]);
-          w[c][u4 + 2] = fmaf(-q.z, lc[c], w[c][u4 + 2]);
-          w[c][u4 + 3] = fmaf(-q.w, lc[c], w[c][u4 + 3]);
-        }
-      }
-#pragma unroll
-      for (int c = 0; c < NC; ++c) rw[c] = fmaf(-lc[c], yj, rw[c]);
-      // row j + BMAX (prefetched PD steps ago) enters slot s
-      float anew[NC];
-      float rnew = 0.f;
-#pragma unroll
-      for (int d = 0; d < PD; ++d)
-        if (d == pd) {
-#pragma unroll
-          for (int c = 0; c < NC; ++c) anew[c] = pre[d][c];
-          rnew = rpre[d];
-        }
-#pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        const int v = vl + 32 * c;
-        if (v < BMAX) {
-          w[c][s] = anew[c];
-          sa[v] = anew[c];
-        }
-      }
-      // prefetch the entries for step j + PD into the freed ring slot
-      {
-        const int jn = j + PD;
-        const int sn = (s + PD) % BMAX;
-        float nv[NC];
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-          const int v = vl + 32 * c;
-          nv[c] = (v < BMAX) ? incoming(jn, sn, v) : 0.f;
-        }
-        const float nr = rhs(jn + BMAX);
-#pragma unroll
-        for (int d = 0; d < PD; ++d)
-          if (d == pd) {
-#pragma unroll
-            for (int c = 0; c < NC; ++c) pre[d][c] = nv[c];
-            rpre[d] = nr;
-          }
-      }
-      __syncwarp();
-      if (lane == so) {
-#pragma unroll
-        for (int u4 = 0; u4 < BMAX; u4 += 4) {
-          const float4 q = *reinterpret_cast<const float4*>(sa + u4);
-          w[sc][u4 + 0] = q.x;
-          w[sc][u4 + 1] = q.y;
-          w[sc][u4 + 2] = q.z;
-          w[sc][u4 + 3] = q.w;
-        }
-        rw[sc] = rnew;
-      }
-      __syncwarp();
-    }
-  }
-  if (bad) {
-    if (lane == 0) atomicOr(err, 1);
-    return;
-  }
-  // backward substitution with L^T; x window in shared memory (slot = row mod BMAX),
-  // the L columns and right-hand sides of the next two rows are prefetched
-  for (int v = lane; v < BMAX; v += 32) xs[v] = 0.f;
-  __syncwarp();
-  float lrow[2][NC], yv[2], linv[2];
-  auto load_row = [&](int j, float* lr, float& y, float& li) {
-    if (j < 0) return;
-    const int s = j % BMAX;
-    const float* row = Lp + (size_t)j * BMAX;
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      const int v = lane + 32 * c;
-      int t = v - s;
-      t += (t < 0) ? BMAX : 0;
-      lr[c] = (v < BMAX && t > 0 && j + t < nl) ? row[t] : 0.f;
-    }
-    y = wpk[(off + j) * k + i];
-    li = row[0];
-  };
-  load_row(nl - 1, lrow[0], yv[0], linv[0]);
-  load_row(nl - 2, lrow[1], yv[1], linv[1]);
-  for (int j = nl - 1; j >= 0; --j) {
-    const int cur = (nl - 1 - j) & 1;
-    float lr[NC], y, li;
-#pragma unroll
-    for (int c = 0; c < NC; ++c) lr[c] = cur ? lrow[1][c] : lrow[0][c];
-    y = cur ? yv[1] : yv[0];
-    li = cur ? linv[1] : linv[0];
-    if (cur)
-      load_row(j - 2, lrow[1], yv[1], linv[1]);
-    else
-      load_row(j - 2, lrow[0], yv[0], linv[0]);
-    float part = 0.f;
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      const int v = lane + 32 * c;
-      if (v < BMAX) part = fmaf(lr[c], xs[v], part);
-    }
-    part = warp_sum(part);
-    const float xj = (y - part) * li;
-    __syncwarp();
-    if (lane == 0) {
-      xs[j % BMAX] = xj;
-      wpk[(off + j) * k + i] = xj;
-    }
-    __syncwarp();
-  }
-}
 
 // ---------------------------------------------------------------------------
 // Bulk-copy and mbarrier helpers (inline PTX).
@@ -1747,7 +1524,7 @@ __global__ void __launch_bounds__(64) k_local_backward(int nsub, int k, const in
 // ---------------------------------------------------------------------------
 // Local solves for wide bands (window up to 128, e.g. 3-D subdomains): one CTA
 // per (subdomain, shift) with one thread per window column (thread v owns
-// column v, slot u = row mod BMAX, as in k_local_band_reg).  Per elimination
+// column v, slot u = row mod BMAX).  Per elimination
 // step the raw pivot column is published in shared memory and one CTA barrier
 // later every column applies its rank-one update w_v -= c_s * (c_v / pivot),
 // stores its entry of L and receives its entry of the incoming band row
