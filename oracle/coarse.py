@@ -65,7 +65,11 @@ def _weights(kind, r, m):
 
 
 def prolongation(spec) -> sp.csr_matrix:
-    """P (n x n_H) as canonical CSR, float64."""
+    """P (n x n_H) as canonical CSR, float64 (for morley_2d the intergrid transfer of
+    ``oracle.morley.prolongation``)."""
+    if spec.kind == "morley_2d":
+        from . import morley
+        return morley.prolongation(spec.n[0], spec.nsub[0])
     n, S, dim = spec.n, spec.nsub, spec.dim
     ms = [n[d] // S[d] for d in range(dim)]
     if len(set(ms)) != 1:

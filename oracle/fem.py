@@ -135,6 +135,9 @@ def _interior_mask(n):
 def assemble(spec):
     """Stiffness K and mass M on interior dofs for a ``workloads.ProblemSpec``
     (only the mesh fields kind, n, length and kappa are used)."""
+    if spec.kind == "morley_2d":
+        from . import morley
+        return morley.assemble(spec.n[0], spec.length[0])
     kap = spec.kappa_array()
     if spec.kind == "p1_2d":
         Kf, Mf = p1_2d_full(*spec.n, *spec.length, kap)

@@ -16,6 +16,11 @@ Rule used here (box subdomains on the uniform grid, in fine-node index units):
   * they are listed in ascending global dof order;
   * colour = sum_d (s_d mod 2) 2^d, valid (disjoint colour classes) while
     2 delta <= m.
+For Morley elements (morley_2d) the same rule runs on the half-grid that
+carries their dofs (2 n points per axis, subdomains of 2 m half-steps grown by
+2 delta): the dofs strictly inside Omega_l' are the vertices strictly inside
+and the midpoints of the edges not on its boundary, i.e. the Morley functions
+with zero values and normal derivatives on the boundary of Omega_l'.
 """
 
 from __future__ import annotations
@@ -38,8 +43,10 @@ def axis_ranges(n: int, S: int, delta: int):
 
 def box_partition(spec):
     """Returns (sub_ptr int64[N+1], sub_dofs int32[sum n_l], sub_color int32[N], n_colors)."""
-    n, S, dim = spec.n, spec.nsub, spec.dim
-    ranges = [axis_ranges(n[d], S[d], spec.delta) for d in range(dim)]
+    n, S, dim, delta = spec.n, spec.nsub, spec.dim, spec.delta
+    if spec.kind == "morley_2d":
+        n, delta = tuple(2 * m for m in n), 2 * delta
+    ranges = [axis_ranges(n[d], S[d], delta) for d in range(dim)]
     inner = [m - 1 for m in n]                      # interior nodes per axis
     ptr = [0]
     dofs = []

@@ -20,6 +20,10 @@ the experiments of Section 6:
   uniform nx x ny x nz cube grid into six tetrahedra per cube.
 * ``q1_3d``   -- trilinear elements on a uniform cube grid (Section 6,
   Example 6.3).
+* ``morley_2d`` -- the clamped plate Delta^2 u = lambda u (Section 2.1, m = 2)
+  with Morley's nonconforming quadratic triangles on the same square grid as
+  ``p1_2d`` (the paper itself uses BFS elements for this problem); no
+  coefficient, square domain.
 
 Layout of the per-element coefficient array ``kappa`` (float64, C order):
 
@@ -36,8 +40,10 @@ from .specs import (
     config_c1,
     config_c2,
     config_c3,
+    config_c4,
     config_small_2d,
     config_small_3d,
+    config_small_morley,
     config_table1_col1,
     config_table5,
     serving_stream,
@@ -49,8 +55,10 @@ __all__ = [
     "config_c1",
     "config_c2",
     "config_c3",
+    "config_c4",
     "config_small_2d",
     "config_small_3d",
+    "config_small_morley",
     "config_table1_col1",
     "config_table5",
     "serving_stream",

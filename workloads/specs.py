@@ -12,7 +12,7 @@ import numpy as np
 class ProblemSpec:
     """One eigenproblem, described by its mesh and decomposition parameters.
 
-    kind    : "p1_2d" | "p1_3d" | "q1_3d"
+    kind    : "p1_2d" | "p1_3d" | "q1_3d" | "morley_2d"
     n       : elements per direction, (nx, ny) or (nx, ny, nz)
     length  : domain edge lengths; the domain is the box [0, Lx] x [0, Ly] (x [0, Lz])
     kappa   : per-element coefficient (layout in the package docstring), None = 1
@@ -46,17 +46,18 @@ class ProblemSpec:
 
     @property
     def n_dofs(self) -> int:
-        """Interior grid nodes (Dirichlet data removed)."""
+        """Interior grid nodes (Dirichlet data removed); for morley_2d the interior
+        points of the half-grid (2 nx - 1)(2 ny - 1) (clamped data removed)."""
         out = 1
         for m in self.n:
-            out *= m - 1
+            out *= (2 * m - 1) if self.kind == "morley_2d" else (m - 1)
         return out
 
     @property
     def n_coarse(self) -> int:
         out = 1
         for m in self.nsub:
-            out *= m - 1
+            out *= (2 * m - 1) if self.kind == "morley_2d" else (m - 1)
         return out
 
     def kappa_array(self) -> np.ndarray:
@@ -70,14 +71,17 @@ class ProblemSpec:
         return np.ones((nz, ny, nx), dtype=np.float64)
 
     def validate(self) -> None:
-        if self.kind not in ("p1_2d", "p1_3d", "q1_3d"):
+        if self.kind not in ("p1_2d", "p1_3d", "q1_3d", "morley_2d"):
             raise ValueError(f"unknown kind {self.kind}")
-        want_dim = 2 if self.kind == "p1_2d" else 3
+        want_dim = 2 if self.kind in ("p1_2d", "morley_2d") else 3
         if self.dim != want_dim or len(self.length) != want_dim or len(self.nsub) != want_dim:
             raise ValueError("dimension mismatch")
         for m, s in zip(self.n, self.nsub):
             if m % s != 0:
                 raise ValueError("element count must be a multiple of the subdomain count")
+        if self.kind == "morley_2d" and (self.kappa is not None or self.n[0] != self.n[1]
+                                         or self.length[0] != self.length[1]):
+            raise ValueError("morley_2d: square domain and square cells, no coefficient")
         if self.k >= self.n_coarse:
             raise ValueError("k must be smaller than the coarse space dimension")
         ms = {m // s for m, s in zip(self.n, self.nsub)}
@@ -164,6 +168,19 @@ def config_c3() -> ProblemSpec:
     (250047 dofs), k = 10, 8 x 8 x 8 subdomains, overlap 1 layer."""
     return ProblemSpec("p1_3d", (64, 64, 64), (1.0, 1.0, 1.0), (8, 8, 8), 1, 10,
                        name="c3_unit_cube_p1tet_h64")
+
+
+def config_c4() -> ProblemSpec:
+    """Clamped plate Delta^2 u = lambda u on the unit square, Morley elements on
+    256 x 256 squares (261121 dofs), k = 8 (including near-multiple pairs),
+    8 x 8 subdomains, overlap 2 layers."""
+    return ProblemSpec("morley_2d", (256, 256), (1.0, 1.0), (8, 8), 2, 8, name="c4_clamped_plate_morley_h256")
+
+
+def config_small_morley(n: int = 32, ns: int = 4, delta: int = 2, k: int = 6, tau: int = 0) -> ProblemSpec:
+    """A small clamped-plate case (Morley), for parity with the oracle."""
+    return ProblemSpec("morley_2d", (n, n), (1.0, 1.0), (ns, ns), delta, k, tau=tau,
+                       name=f"small_morley_{n}_{ns}_d{delta}_k{k}")
 
 
 def config_small_2d(nx: int = 48, ny: int = 36, nsx: int = 4, nsy: int = 3, delta: int = 2,
