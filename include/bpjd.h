@@ -45,16 +45,24 @@ extern "C" {
 #define BPJD_ERR_NOCONV           -8  /* max_iter reached before the stop rule held */
 #define BPJD_ERR_OOM              -9  /* device allocation failed */
 #define BPJD_ERR_CUDA            -10  /* a CUDA runtime call failed */
-#define BPJD_ERR_UNSUPPORTED     -11  /* option outside what this build implements */
+#define BPJD_ERR_UNSUPPORTED     -11  /* option outside what this build implements, or a local
+                                        band window the shared-memory kernel cannot hold
+                                        (FP64 above 168, mixed above 240 on a 227 KB SM) */
 #define BPJD_ERR_TOO_LARGE       -12  /* request exceeds a fixed capacity (allocation-free entry point)
                                          or, alone, the memory budget of a server */
 
 /* ---- option values ----------------------------------------------------- */
 #define BPJD_FP64        0  /* every step in FP64 */
-#define BPJD_MIXED       1  /* preconditioner (local band factorisations and solves,
-                               coarse solve, prolongation) in FP32; residuals,
-                               projections, Gram matrices, Rayleigh-Ritz and the
-                               Ritz-vector update in FP64 */
+#define BPJD_MIXED       1  /* local band factorisations and solves in FP32 (tensor
+                               cores up to window 152); SpMM, projections, Gram
+                               matrices and the Ritz-vector update in double-word
+                               FP32 pairs (about 2^-46 relative, FP64-class);
+                               residuals and Rayleigh-Ritz in FP64 */
+#define BPJD_MIXED_LOCAL 2  /* local band factorisations and solves in FP32 as in
+                               BPJD_MIXED, every other step in native FP64: for
+                               operators whose residual amplifies product rounding
+                               beyond the double-word floor (fourth-order problems on
+                               fine meshes: |K||x| / |Kx| ~ 1e8) */
 
 #define BPJD_W_2K        0  /* W^{k+1} = U^k + span{t_i}           (Remark 3.1) */
 #define BPJD_W_3K        1  /* W^{k+1} = U^{k-1} + U^k + span{t_i} (Remark 3.1) */
@@ -88,7 +96,7 @@ typedef struct {
 
 typedef struct {
   int32_t k;                /* wanted eigenpairs (the paper's s), 1 <= k <= 32 */
-  int32_t precision;        /* BPJD_FP64 | BPJD_MIXED */
+  int32_t precision;        /* BPJD_FP64 | BPJD_MIXED | BPJD_MIXED_LOCAL */
   int32_t subspace;         /* BPJD_W_2K | BPJD_W_3K */
   int32_t stop_rule;        /* BPJD_STOP_RESIDUAL | BPJD_STOP_DLAMBDA */
   double  tol;              /* threshold of the stop rule (default 1e-8) */
@@ -245,7 +253,16 @@ int bpjd_profile_read(bpjd_handle* h, double* ms, int64_t* count, int64_t* kerne
  *   kind 0 = P1 triangles on a uniform nx x ny grid, squares split SW->NE;
  *   kind 1 = P1 tetrahedra, each cube of a uniform grid split into the six
  *            Kuhn tetrahedra;
- *   kind 2 = trilinear bricks (constant kappa only).
+ *   kind 2 = trilinear bricks (constant kappa only);
+ *   kind 3 = the clamped plate Delta^2 u = lambda u (Section 2.1, m = 2) with
+ *            Morley triangles on the square grid of kind 0 (nx = ny, equal
+ *            sides, kappa NULL).  Dofs are the interior points (X h/2, Y h/2) of
+ *            the half-grid, numbered (Y-1)(2n-1) + (X-1): vertex values at even
+ *            (X, Y), scaled normal derivatives h du/dy, h du/dx and
+ *            h (du/dx - du/dy) at the horizontal, vertical and diagonal edge
+ *            midpoints; the stiffness is the broken Hessian form; P is the
+ *            averaging intergrid transfer from the Morley space of the
+ *            subdomain grid; subdomains follow the box rule on the half-grid.
  * kappa: per-element coefficient, layout [ny][nx][2] (kind 0, entry 0 = the
  * triangle below the diagonal) or [nz][ny][nx] (kinds 1, 2); NULL = 1.
  * Subdomains: nsub boxes per axis grown by delta element layers; the initial

@@ -33,7 +33,7 @@ ERR_CUDA = -10
 ERR_UNSUPPORTED = -11
 ERR_TOO_LARGE = -12
 
-FP64, MIXED = 0, 1
+FP64, MIXED, MIXED_LOCAL = 0, 1, 2
 W_2K, W_3K = 0, 1
 STOP_RESIDUAL, STOP_DLAMBDA = 0, 1
 
@@ -209,7 +209,7 @@ class PartitionArrays:
 
 
 # ---- problem generation -----------------------------------------------------
-_KINDS = {"p1_2d": 0, "p1_3d": 1, "q1_3d": 2}
+_KINDS = {"p1_2d": 0, "p1_3d": 1, "q1_3d": 2, "morley_2d": 3}
 
 
 @dataclass

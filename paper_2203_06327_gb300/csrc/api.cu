@@ -285,7 +285,8 @@ extern "C" int bpjd_setup(const bpjd_csr* A, const bpjd_csr* M, const bpjd_csr* 
       part->n_sub < 1)
     return BPJD_ERR_BAD_ARG;
   if (P0 && (P0->n_rows != n || !P0->row_ptr || !P0->col_idx || !P0->val)) return BPJD_ERR_BAD_ARG;
-  if (opts->precision != BPJD_FP64 && opts->precision != BPJD_MIXED) return BPJD_ERR_UNSUPPORTED;
+  if (opts->precision != BPJD_FP64 && opts->precision != BPJD_MIXED && opts->precision != BPJD_MIXED_LOCAL)
+    return BPJD_ERR_UNSUPPORTED;
   if (opts->subspace != BPJD_W_2K && opts->subspace != BPJD_W_3K) return BPJD_ERR_UNSUPPORTED;
   const int mmax = (opts->subspace == BPJD_W_3K) ? 3 * k : 2 * k;
   if (mmax > 64) return BPJD_ERR_UNSUPPORTED;
@@ -396,7 +397,7 @@ extern "C" int bpjd_setup(const bpjd_csr* A, const bpjd_csr* M, const bpjd_csr* 
       }
       h->same_pattern = (A->nnz == M->nnz) && !(flags & 2);
     }
-    if (h->precision == BPJD_MIXED) {
+    if (h->dword()) {
       CK(dalloc(*h, &h->Asplit, (size_t)A->nnz));
       CK(dalloc(*h, &h->Msplit, (size_t)M->nnz));
       CKI(launch_split_values(h->A.val, A->nnz, h->Asplit, h->stream));
@@ -453,19 +454,30 @@ extern "C" int bpjd_setup(const bpjd_csr* A, const bpjd_csr* M, const bpjd_csr* 
       CK(cudaStreamSynchronize(h->stream));
     }
     h->B = bw + 1;
-    if (h->precision == BPJD_MIXED) {
-      static const int tiers[] = {16, 24, 32, 40, 48, 64, 96, 128};
+    if (h->local_f32()) {
+      static const int tiers[] = {16, 24, 32, 40, 48, 64, 96, 128, 152};
       for (int t : tiers)
         if (h->B <= t) {
           h->Bpad = t;
           break;
         }
     }
+    if (h->Bpad == 0) {
+      // windows above every tier run in the shared-memory kernel, one (B x B) window per warp
+      int dev = 0, optin = 0;
+      CK(cudaGetDevice(&dev));
+      CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+      const size_t esz = h->local_f32() ? sizeof(float) : sizeof(double);
+      if ((size_t)(h->B * h->B + 3 * h->B) * esz > (size_t)optin) {
+        rc = BPJD_ERR_UNSUPPORTED;
+        goto fail;
+      }
+    }
     {
       const int B = h->B;
       CK(dalloc(*h, &h->bandK, (size_t)sum_nl * B));
       CK(dalloc(*h, &h->bandM, (size_t)sum_nl * B));
-      if (h->precision == BPJD_MIXED) {
+      if (h->local_f32()) {
         const size_t W = (size_t)std::max(h->B, h->Bpad);
         CK(dalloc(*h, &h->bandKf, (size_t)sum_nl * W));
         CK(dalloc(*h, &h->bandMf, (size_t)sum_nl * W));
@@ -533,7 +545,7 @@ extern "C" int bpjd_setup(const bpjd_csr* A, const bpjd_csr* M, const bpjd_csr* 
     pt.mark("initial_guess", h->stream);
     // scratch and iteration vectors
     {
-      const size_t esz = (h->precision == BPJD_MIXED) ? sizeof(float) : sizeof(double);
+      const size_t esz = h->local_f32() ? sizeof(float) : sizeof(double);
       const size_t lw = (size_t)std::max(h->B, h->Bpad);
       void* p;
       CK(cudaMalloc(&p, esz * (size_t)sum_nl * k * lw));
@@ -678,7 +690,7 @@ extern "C" int bpjd_solve(bpjd_handle* hh, double* eigvals, double* eigvecs, int
   double *Pc = h.Pd, *APc = h.APd, *MPc = h.MPd;      // current P block (3k)
   double *Pn = h.Pd2, *APn = h.APd2, *MPn = h.MPd2;   // next P block
   bool have_prev = false;
-  const int mixed = (h.precision == BPJD_MIXED) ? 1 : 0;
+  const int mixed = h.dword() ? 1 : 0;
 
   CK(cudaMemsetAsync(h.dstat, 0, sizeof(DevStatus), h.stream));
   CK(cudaMemsetAsync(h.derr, 0, 4 * sizeof(int32_t), h.stream));
@@ -721,7 +733,7 @@ extern "C" int bpjd_solve(bpjd_handle* hh, double* eigvals, double* eigvecs, int
     {
       const double* U[1] = {MX};
       const double* V[1] = {h.Z};
-      if (h.precision == BPJD_MIXED)
+      if (h.dword())
         CKI(launch_gram(h, 1, U, 1, 1, V, nullptr, 0, C1, nullptr));
       else
         CKI(launch_inner(h, 1, U, 1, V, C1));
@@ -753,7 +765,7 @@ extern "C" int bpjd_solve(bpjd_handle* hh, double* eigvals, double* eigvecs, int
       put(mixed ? 0 : 1, h.T, h.AT, h.MT);
     }
     const int m = nb * k;
-    if (h.precision == BPJD_MIXED) {
+    if (h.dword()) {
       CKI(launch_gram(h, nb, W, nb, 2, MW, AW, 1, G, Hm));
     } else {
       CKI(launch_inner(h, nb, W, nb, MW, G));

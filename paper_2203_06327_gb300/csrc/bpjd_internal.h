@@ -42,6 +42,10 @@ struct Handle {
   int64_t sum_nl = 0;       // sum of local sizes
   int32_t max_nl = 0;
   int32_t precision = BPJD_FP64, subspace = BPJD_W_2K, stop_rule = BPJD_STOP_RESIDUAL;
+  // local band factorisations and solves in FP32 (BPJD_MIXED, BPJD_MIXED_LOCAL)
+  bool local_f32() const { return precision == BPJD_MIXED || precision == BPJD_MIXED_LOCAL; }
+  // SpMM, Gram matrices and row combinations in double-word arithmetic (BPJD_MIXED)
+  bool dword() const { return precision == BPJD_MIXED; }
   int32_t max_iter = 500;
   double tol = 1e-8, drop_tol = 1e-10;
   cudaStream_t stream = nullptr;

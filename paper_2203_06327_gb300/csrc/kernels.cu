@@ -1133,13 +1133,16 @@ struct WideShape {
   static constexpr int RT = (W + 15) / 16;
   static constexpr int CT = NBW;
   // warps per CTA: one window row per thread, and at most three column tiles per warp
-  static constexpr int NW = ((W + 31) / 32 > (CT + 2) / 3) ? (W + 31) / 32 : (CT + 2) / 3;
+  // (two above 128 rows, where the CTA has a whole SM: 80 accumulator registers)
+  static constexpr int CTMAX = (W > 128) ? 2 : 3;
+  static constexpr int NW = ((W + 31) / 32 > (CT + CTMAX - 1) / CTMAX) ? (W + 31) / 32 : (CT + CTMAX - 1) / CTMAX;
   static constexpr int CTW = (CT + NW - 1) / NW;  // column tiles per warp (at most)
   static constexpr int PSTR = 12;
+  static constexpr int MINB = (W > 128) ? 1 : 2;  // resident CTAs per SM the registers are sized for
 };
 
 template <int BMAX>
-__global__ void __launch_bounds__(WideShape<BMAX>::NW * 32, 2) k_local_factor_wide(
+__global__ void __launch_bounds__(WideShape<BMAX>::NW * 32, WideShape<BMAX>::MINB) k_local_factor_wide(
     int npairs, int k, const int64_t* __restrict__ sub_ptr, const int32_t* __restrict__ sub_dofs,
     const float* __restrict__ bandK, const float* __restrict__ bandM, const double* __restrict__ lam,
     const double* __restrict__ rho, float* __restrict__ Lbuf, float* __restrict__ wpk, int32_t* err) {
@@ -1405,8 +1408,9 @@ __global__ void __launch_bounds__(WideShape<BMAX>::NW * 32, 2) k_local_factor_wi
 // ---------------------------------------------------------------------------
 template <int BMAX>
 struct BwdShape {
-  static constexpr int R = (BMAX <= 48) ? BMAX / 2 : 16;  // rows per staged chunk
-  static constexpr int NCH = BMAX / R;                    // chunks per window group (even)
+  // rows per staged chunk: R divides BMAX into an even number of chunks
+  static constexpr int R = (BMAX <= 48) ? BMAX / 2 : ((BMAX % 32 == 0) ? 16 : BMAX / 8);
+  static constexpr int NCH = BMAX / R;  // chunks per window group (even)
   static constexpr int PS = R * BMAX + 8;  // per-shift buffer stride: shifts land on different banks
   static constexpr int WPB = 2;            // warps per block
   static constexpr size_t smem_floats = (size_t)WPB * 2 * 4 * PS;
@@ -3155,7 +3159,7 @@ int launch_spmm(Handle& h, const double* X, double* YA, double* YM, int ncols) {
     k_spmm<LANES><<<(unsigned)blocks, 256, 0, h.stream>>>(n, A.row_ptr, A.col, A.val, vm, X, ya, ym, ncols);
     h.launches += 1;
   };
-  if (h.precision == BPJD_MIXED && h.Asplit) {
+  if (h.dword() && h.Asplit) {
     // lanes per row and columns per lane: every lane of a row group busy for k = 4, 8, 12, 16, 24, 32
     auto god = [&](auto lanes_tag, auto cpl_tag, const float2* va, const float2* vm, double* ya, double* ym,
                    const CsrDev& A) {
@@ -3332,7 +3336,7 @@ int launch_combine_rows(Handle& h, int nin, const double* const* Win, const doub
   h.launches += 1;
   Ptrs6 w{};
   for (int b = 0; b < nin; ++b) w.p[b] = Win[b];
-  if (h.precision == BPJD_MIXED && consistency_only) {
+  if (h.dword() && consistency_only) {
     const int m = nin * h.k;
     const size_t sm = (size_t)(m * csub + kCombRows * m) * sizeof(float);
     allow_dynamic_smem((const void*)k_combine_f32);
@@ -3340,7 +3344,7 @@ int launch_combine_rows(Handle& h, int nin, const double* const* Win, const doub
     k_combine_f32<<<(unsigned)blocks, 256, sm, h.stream>>>(h.n, h.k, nin, w, C, ldc, csub, Zadd, out, (float)sign);
     return (int)cudaGetLastError();
   }
-  if (h.precision == BPJD_MIXED) {
+  if (h.dword()) {
     const int m = nin * h.k;
     const size_t sm = (size_t)(2 * m * csub + 2 * kCombRows * m) * sizeof(float);
     allow_dynamic_smem((const void*)k_combine_dw);
@@ -3362,8 +3366,8 @@ int launch_precond(Handle& h, const double* rho, const double* lam, double* Z) {
   // local band solves
   {
     ProfScope ps(h, BPJD_PROF_LOCAL);
-    const bool f32 = (h.precision == BPJD_MIXED);
-    h.launches += (f32 && h.Bpad > 0 && h.Bpad <= 96) ? 2 : 1;  // factorisation + backward substitution
+    const bool f32 = h.local_f32();
+    h.launches += (f32 && h.Bpad > 0 && h.Bpad != 128) ? 2 : 1;  // factorisation + backward substitution
     if (f32 && h.Bpad > 0) {
       const int blocks = h.nsub * ((k + kLocalWarps - 1) / kLocalWarps);
 #define BPJD_LOCAL_TILE(BM)                                                                                    \
@@ -3401,6 +3405,7 @@ int launch_precond(Handle& h, const double* rho, const double* lam, double* Z) {
   }
         BPJD_LOCAL_WIDE(64)
         BPJD_LOCAL_WIDE(96)
+        BPJD_LOCAL_WIDE(152)
         case 128:
           k_local_band_team<128><<<npairs, 128, 0, h.stream>>>(npairs, k, h.sub_ptr, h.sub_dofs, h.bandKf,
                                                                h.bandMf, lam, rho, (float*)h.Lbuf, (float*)h.wpk,
@@ -3452,7 +3457,7 @@ int launch_precond(Handle& h, const double* rho, const double* lam, double* Z) {
     ProfScope ps(h, BPJD_PROF_PROLONG);
     h.launches += 1;
     int64_t tot = (int64_t)h.n * k;
-    if (h.precision == BPJD_MIXED)
+    if (h.local_f32())
       k_prolong_add<float><<<(unsigned)((tot + 255) / 256), 256, 0, h.stream>>>(
           h.n, k, h.P.row_ptr, h.P.col, h.P.val, h.w0, h.rt_ptr, h.rt_pos, (const float*)h.wpk, Z);
     else
@@ -3471,7 +3476,7 @@ int launch_rr(Handle& h, int m, const double* G, const double* Hm, const double*
   h.launches += 1;
   double* hr = (hist_row >= 0 && hist_row < h.hist_rows) ? h.hist + (int64_t)hist_row * h.k : nullptr;
   k_rayleigh_ritz_chol<<<1, 1024, sm, h.stream>>>(m, h.k, G, Hm, h.drop_tol, lam_old, C, lam_new, hr, h.stop_rule,
-                                                 h.tol, h.dstat, h.precision == BPJD_MIXED ? 1 : 0);
+                                                 h.tol, h.dstat, h.dword() ? 1 : 0);
   return (int)cudaGetLastError();
 }
 

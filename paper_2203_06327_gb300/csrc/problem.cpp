@@ -1,6 +1,7 @@
 // Host-side problem generation: finite-element assembly of the model problems
 // (Section 2.1, Section 2.2, Section 6), overlapping box subdomains with their
-// colouring (Section 2.3, Assumption 2) and the nodal interpolation V^H -> V^h.
+// colouring (Section 2.3, Assumption 2) and the nodal interpolation V^H -> V^h
+// (for Morley elements, the averaging intergrid transfer).
 //
 // Degrees of freedom are interior grid nodes, lexicographic with x fastest;
 // Dirichlet data are imposed by omitting boundary nodes.  The sparsity pattern
@@ -398,18 +399,292 @@ int coarse_interp(const bpjd_mesh& m, int dim, const int32_t* S, CsrBuf& P) {
   return BPJD_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Morley elements for the clamped plate (Section 2.1 with m = 2; the paper's own
+// element for this problem is BFS).  Broken Hessian form sum_T int_T D^2u : D^2v
+// and b(u, v) = int u v on the square grid of kind 0 (squares split SW->NE).
+// The dofs live on the half-grid (X h/2, Y h/2), X, Y = 0..2n: vertex values at
+// (even, even); scaled normal derivatives h du/dy at (odd, even), h du/dx at
+// (even, odd) and h (du/dx - du/dy) at (odd, odd) (diagonal edge midpoints).
+// Clamped data remove exactly the boundary half-grid points, so the dofs are the
+// interior points numbered (Y-1)(2n-1) + (X-1): a subdomain's ascending dofs then
+// follow the half-grid rows and its band spans about two cell rows.
+// Element quantities are rationals (exact arithmetic below), scaled by h^-2
+// (stiffness) or h^2 (mass); the transfer matrix entries are rationals rounded
+// once to double.
+// ---------------------------------------------------------------------------
+
+int64_t gcd64(int64_t a, int64_t b) {
+  if (a < 0) a = -a;
+  if (b < 0) b = -b;
+  while (b) {
+    int64_t t = a % b;
+    a = b;
+    b = t;
+  }
+  return a;
+}
+
+struct Rat {
+  int64_t p = 0, q = 1;  // q > 0, gcd(p, q) = 1
+  Rat() = default;
+  Rat(int64_t a, int64_t b = 1) : p(a), q(b) {
+    if (q < 0) {
+      p = -p;
+      q = -q;
+    }
+    int64_t g = gcd64(p, q);
+    if (g > 1) {
+      p /= g;
+      q /= g;
+    }
+  }
+  Rat operator+(const Rat& o) const {
+    int64_t g = gcd64(q, o.q);
+    return Rat(p * (o.q / g) + o.p * (q / g), (q / g) * o.q);
+  }
+  Rat operator-(const Rat& o) const { return *this + Rat(-o.p, o.q); }
+  Rat operator*(const Rat& o) const {
+    int64_t g1 = gcd64(p, o.q), g2 = gcd64(o.p, q);
+    if (g1 == 0) g1 = 1;
+    if (g2 == 0) g2 = 1;
+    return Rat((p / g1) * (o.p / g2), (q / g2) * (o.q / g1));
+  }
+  Rat operator/(const Rat& o) const { return *this * Rat(o.q, o.p); }
+  bool zero() const { return p == 0; }
+  double to_double() const { return (double)p / (double)q; }
+};
+
+enum MorleyFn { MV = 0, MDY = 1, MDX = 2, MDD = 3 };  // value, d/deta, d/dxi, d/dxi - d/deta
+const int kMono[6][2] = {{0, 0}, {1, 0}, {0, 1}, {2, 0}, {1, 1}, {0, 2}};
+
+Rat rpow(const Rat& x, int e) {
+  Rat r(1);
+  for (int i = 0; i < e; ++i) r = r * x;
+  return r;
+}
+
+// functional f applied to xi^p eta^q at (x, y)
+Rat morley_functional(int f, int p, int q, const Rat& x, const Rat& y) {
+  auto dxi = [&]() { return p > 0 ? Rat(p) * rpow(x, p - 1) * rpow(y, q) : Rat(0); };
+  auto deta = [&]() { return q > 0 ? Rat(q) * rpow(x, p) * rpow(y, q - 1) : Rat(0); };
+  switch (f) {
+    case MV:
+      return rpow(x, p) * rpow(y, q);
+    case MDY:
+      return deta();
+    case MDX:
+      return dxi();
+    default:
+      return dxi() - deta();
+  }
+}
+
+int morley_kind(int X, int Y) { return (X & 1) ? ((Y & 1) ? MDD : MDY) : ((Y & 1) ? MDX : MV); }
+
+struct MorleyRef {
+  // local dofs: half-grid offsets within the square and functional
+  int off[6][2];
+  int fn[6];
+  Rat C[6][6];  // C[m][a]: coefficient of monomial m in basis function a
+  Rat S[6][6], R[6][6];
+};
+
+// shape 0: (SW, SE, NE) below the diagonal, edges bottom / right / diagonal;
+// shape 1: (SW, NE, NW) above it, edges diagonal / top / left
+MorleyRef morley_reference(int shape) {
+  MorleyRef E;
+  static const int offs[2][6][2] = {{{0, 0}, {2, 0}, {2, 2}, {1, 0}, {2, 1}, {1, 1}},
+                                    {{0, 0}, {2, 2}, {0, 2}, {1, 1}, {1, 2}, {0, 1}}};
+  for (int a = 0; a < 6; ++a) {
+    E.off[a][0] = offs[shape][a][0];
+    E.off[a][1] = offs[shape][a][1];
+    E.fn[a] = morley_kind(E.off[a][0], E.off[a][1]);
+  }
+  // Vandermonde V[r][m] = N_r(monomial m), inverted by Gauss-Jordan
+  Rat A[6][12];
+  for (int r = 0; r < 6; ++r) {
+    Rat x(E.off[r][0], 2), y(E.off[r][1], 2);
+    for (int m = 0; m < 6; ++m) A[r][m] = morley_functional(E.fn[r], kMono[m][0], kMono[m][1], x, y);
+    for (int m = 0; m < 6; ++m) A[r][6 + m] = Rat(r == m ? 1 : 0);
+  }
+  for (int c = 0; c < 6; ++c) {
+    int piv = c;
+    while (A[piv][c].zero()) ++piv;
+    for (int j = 0; j < 12; ++j) std::swap(A[c][j], A[piv][j]);
+    Rat inv = Rat(1) / A[c][c];
+    for (int j = 0; j < 12; ++j) A[c][j] = A[c][j] * inv;
+    for (int r = 0; r < 6; ++r) {
+      if (r == c || A[r][c].zero()) continue;
+      Rat f = A[r][c];
+      for (int j = 0; j < 12; ++j) A[r][j] = A[r][j] - f * A[c][j];
+    }
+  }
+  for (int m = 0; m < 6; ++m)
+    for (int a = 0; a < 6; ++a) E.C[m][a] = A[m][6 + a];
+  // reference-triangle monomial integrals: lower {0 <= eta <= xi <= 1}: 1/((q+1)(p+q+2));
+  // upper {0 <= xi <= eta <= 1}: 1/((p+1)(p+q+2))
+  auto tri = [&](int p, int q) { return shape == 0 ? Rat(1, (q + 1) * (p + q + 2)) : Rat(1, (p + 1) * (p + q + 2)); };
+  for (int a = 0; a < 6; ++a)
+    for (int b = 0; b < 6; ++b) {
+      // area 1/2 times the Frobenius product of the Hessians [[2 c_xx, c_xy], [c_xy, 2 c_yy]]
+      Rat hh = Rat(4) * E.C[3][a] * E.C[3][b] + Rat(2) * E.C[4][a] * E.C[4][b] + Rat(4) * E.C[5][a] * E.C[5][b];
+      E.S[a][b] = Rat(1, 2) * hh;
+      Rat acc(0);
+      for (int m1 = 0; m1 < 6; ++m1)
+        for (int m2 = 0; m2 < 6; ++m2)
+          acc = acc + E.C[m1][a] * E.C[m2][b] * tri(kMono[m1][0] + kMono[m2][0], kMono[m1][1] + kMono[m2][1]);
+      E.R[a][b] = acc;
+    }
+  return E;
+}
+
+int assemble_morley(const bpjd_mesh& m, CsrBuf& K, CsrBuf& M) {
+  const int n = m.n[0];
+  const double h = m.length[0] / n;
+  const int inner = 2 * n - 1;
+  const int64_t N = (int64_t)inner * inner;
+  auto dof = [&](int X, int Y) -> int64_t {
+    if (X <= 0 || X >= 2 * n || Y <= 0 || Y >= 2 * n) return -1;
+    return (int64_t)(Y - 1) * inner + (X - 1);
+  };
+  std::vector<Entry> ent;
+  ent.reserve((size_t)n * n * 2 * 36);
+  for (int shape = 0; shape < 2; ++shape) {
+    const MorleyRef E = morley_reference(shape);
+    double Ke[6][6], Me[6][6];
+    for (int a = 0; a < 6; ++a)
+      for (int b = 0; b < 6; ++b) {
+        Ke[a][b] = E.S[a][b].to_double() / (h * h);
+        Me[a][b] = E.R[a][b].to_double() * (h * h);
+      }
+    for (int j = 0; j < n; ++j)
+      for (int i = 0; i < n; ++i) {
+        int64_t d[6];
+        for (int a = 0; a < 6; ++a) d[a] = dof(2 * i + E.off[a][0], 2 * j + E.off[a][1]);
+        for (int a = 0; a < 6; ++a) {
+          if (d[a] < 0) continue;
+          for (int b = 0; b < 6; ++b) {
+            if (d[b] < 0) continue;
+            Entry e;
+            e.key = d[a] * N + d[b];
+            e.k = Ke[a][b];
+            e.m = Me[a][b];
+            ent.push_back(e);
+          }
+        }
+      }
+  }
+  entries_to_csr(ent, N, K, M);
+  return BPJD_OK;
+}
+
+// Intergrid transfer V^H -> V^h for Morley (S coarse cells per side, mm = n / S
+// fine cells per coarse cell): a fine dof takes its functional of the coarse
+// function on every coarse triangle whose closure holds the dof's point (the
+// fine edge, for an edge dof), averaged over those triangles.  Boundary coarse
+// dofs (clamped) and exact zeros are dropped.
+int morley_transfer(const bpjd_mesh& m, int S, CsrBuf& P) {
+  const int n = m.n[0];
+  if (S < 1 || n % S != 0) return BPJD_ERR_BAD_ARG;
+  const int mm = n / S, w = 2 * mm;
+  const int inner = 2 * n - 1, cinner = 2 * S - 1;
+  const int64_t N = (int64_t)inner * inner;
+  if (cinner < 1) return BPJD_ERR_BAD_ARG;
+  const MorleyRef E[2] = {morley_reference(0), morley_reference(1)};
+  // per local position (xl, yl) in a coarse cell: the basis functionals of both triangles
+  // (valid where the triangle holds the point), already scaled to the fine functional
+  std::vector<std::array<Rat, 12>> table((size_t)(w + 1) * (w + 1));
+  for (int yl = 0; yl <= w; ++yl)
+    for (int xl = 0; xl <= w; ++xl) {
+      const int f = morley_kind(xl, yl);  // same parity as the fine point (w is even)
+      Rat xi(xl, w), eta(yl, w);
+      for (int s = 0; s < 2; ++s)
+        for (int a = 0; a < 6; ++a) {
+          Rat v(0);
+          for (int q = 0; q < 6; ++q) v = v + E[s].C[q][a] * morley_functional(f, kMono[q][0], kMono[q][1], xi, eta);
+          if (f != MV) v = v / Rat(mm);  // fine h d/dx = (h / H) coarse scaled derivative
+          table[(size_t)yl * (w + 1) + xl][s * 6 + a] = v;
+        }
+    }
+  P.n_rows = (int32_t)N;
+  P.n_cols = (int32_t)((int64_t)cinner * cinner);
+  P.row_ptr.assign(N + 1, 0);
+  auto cells = [&](int X, int* c) {
+    if (X % w == 0) {
+      int k = 0;
+      for (int q : {X / w - 1, X / w})
+        if (q >= 0 && q < S) c[k++] = q;
+      return k;
+    }
+    c[0] = X / w;
+    return 1;
+  };
+  std::vector<std::pair<int64_t, Rat>> row;
+  for (int Y = 1; Y < 2 * n; ++Y)
+    for (int X = 1; X < 2 * n; ++X) {
+      int ci[2], cj[2];
+      const int ni = cells(X, ci), nj = cells(Y, cj);
+      int n_el = 0;
+      for (int a = 0; a < ni; ++a)
+        for (int b = 0; b < nj; ++b) {
+          const int xl = X - w * ci[a], yl = Y - w * cj[b];
+          n_el += (xl >= yl) + (xl <= yl);
+        }
+      row.clear();
+      for (int a = 0; a < ni; ++a)
+        for (int b = 0; b < nj; ++b) {
+          const int I = ci[a], J = cj[b];
+          const int xl = X - w * I, yl = Y - w * J;
+          for (int s = 0; s < 2; ++s) {
+            if ((s == 0 && xl < yl) || (s == 1 && xl > yl)) continue;
+            for (int e = 0; e < 6; ++e) {
+              const int Xc = 2 * I + E[s].off[e][0], Yc = 2 * J + E[s].off[e][1];
+              if (Xc <= 0 || Xc >= 2 * S || Yc <= 0 || Yc >= 2 * S) continue;
+              const int64_t c = (int64_t)(Yc - 1) * cinner + (Xc - 1);
+              const Rat v = table[(size_t)yl * (w + 1) + xl][s * 6 + e] / Rat(n_el);
+              bool found = false;
+              for (auto& r : row)
+                if (r.first == c) {
+                  r.second = r.second + v;
+                  found = true;
+                  break;
+                }
+              if (!found) row.push_back({c, v});
+            }
+          }
+        }
+      std::sort(row.begin(), row.end(), [](const std::pair<int64_t, Rat>& u, const std::pair<int64_t, Rat>& v) {
+        return u.first < v.first;
+      });
+      const int64_t g = (int64_t)(Y - 1) * inner + (X - 1);
+      for (auto& r : row) {
+        if (r.second.zero()) continue;
+        P.col.push_back((int32_t)r.first);
+        P.val.push_back(r.second.to_double());
+      }
+      P.row_ptr[g + 1] = (int64_t)P.col.size();
+    }
+  return BPJD_OK;
+}
+
 }  // namespace
 
 extern "C" int bpjd_problem_create(const bpjd_mesh* mesh, bpjd_problem** out) {
   if (!mesh || !out) return BPJD_ERR_BAD_ARG;
   *out = nullptr;
   const bpjd_mesh& m = *mesh;
-  int dim = (m.kind == 0) ? 2 : 3;
-  if (m.kind < 0 || m.kind > 2) return BPJD_ERR_BAD_ARG;
+  int dim = (m.kind == 0 || m.kind == 3) ? 2 : 3;
+  if (m.kind < 0 || m.kind > 3) return BPJD_ERR_BAD_ARG;
   for (int d = 0; d < dim; ++d) {
     if (m.n[d] < 2 || m.nsub[d] < 1 || m.n[d] % m.nsub[d] != 0 || !(m.length[d] > 0)) return BPJD_ERR_BAD_ARG;
   }
   if (m.delta < 0 || m.tau < 0 || m.tau > 6) return BPJD_ERR_BAD_ARG;
+  if (m.kind == 3) {
+    if (m.n[0] != m.n[1] || m.nsub[0] != m.nsub[1] || m.length[0] != m.length[1]) return BPJD_ERR_BAD_ARG;
+    if (m.kappa) return BPJD_ERR_UNSUPPORTED;
+    if ((m.n[0] / m.nsub[0]) % (1 << m.tau) != 0) return BPJD_ERR_BAD_ARG;
+  }
   if (m.kind == 2 && m.kappa) {
     size_t ne = (size_t)m.n[0] * m.n[1] * m.n[2];
     for (size_t e = 1; e < ne; ++e)
@@ -419,23 +694,42 @@ extern "C" int bpjd_problem_create(const bpjd_mesh* mesh, bpjd_problem** out) {
   if (!P) return BPJD_ERR_OOM;
   int rc;
   try {
-    if (m.kind == 0)
-      rc = assemble_p1_2d(m, P->K, P->M);
-    else if (m.kind == 1)
-      rc = assemble_p1_3d(m, P->K, P->M);
-    else
-      rc = assemble_q1_3d(m, P->K, P->M);
-    if (rc == BPJD_OK) rc = coarse_interp(m, dim, m.nsub, P->P);
-    if (rc == BPJD_OK) {
-      if (m.tau == 0) {
-        P->P0 = P->P;
-      } else {
-        int32_t S0[3];
-        for (int d = 0; d < 3; ++d) S0[d] = m.nsub[d] << m.tau;
-        rc = coarse_interp(m, dim, S0, P->P0);
+    if (m.kind == 3) {
+      rc = assemble_morley(m, P->K, P->M);
+      if (rc == BPJD_OK) rc = morley_transfer(m, m.nsub[0], P->P);
+      if (rc == BPJD_OK) {
+        if (m.tau == 0)
+          P->P0 = P->P;
+        else
+          rc = morley_transfer(m, m.nsub[0] << m.tau, P->P0);
       }
+      if (rc == BPJD_OK) {
+        // the box rule on the half-grid carrying the Morley dofs
+        bpjd_mesh half = m;
+        half.n[0] = 2 * m.n[0];
+        half.n[1] = 2 * m.n[1];
+        half.delta = 2 * m.delta;
+        box_partition(half, dim, *P);
+      }
+    } else {
+      if (m.kind == 0)
+        rc = assemble_p1_2d(m, P->K, P->M);
+      else if (m.kind == 1)
+        rc = assemble_p1_3d(m, P->K, P->M);
+      else
+        rc = assemble_q1_3d(m, P->K, P->M);
+      if (rc == BPJD_OK) rc = coarse_interp(m, dim, m.nsub, P->P);
+      if (rc == BPJD_OK) {
+        if (m.tau == 0) {
+          P->P0 = P->P;
+        } else {
+          int32_t S0[3];
+          for (int d = 0; d < 3; ++d) S0[d] = m.nsub[d] << m.tau;
+          rc = coarse_interp(m, dim, S0, P->P0);
+        }
+      }
+      if (rc == BPJD_OK) box_partition(m, dim, *P);
     }
-    if (rc == BPJD_OK) box_partition(m, dim, *P);
   } catch (...) {
     rc = BPJD_ERR_OOM;
   }

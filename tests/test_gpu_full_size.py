@@ -3,13 +3,15 @@
 * the eigenvalues printed in the paper (Section 6, Table 1 first column and Table 5
   first two columns, all to 8 decimals), solved by the library on its own assembly of
   the same discretisation;
-* the bench workload at full size (C2, 261,121 dofs) against the k lowest generalised
-  eigenpairs from a shift-invert Lanczos solve (scipy ``eigsh``) of the same matrices.
+* the bench workload at full size (C2, 261,121 dofs) and the clamped plate (C4, Morley,
+  261,121 dofs) against the k lowest generalised eigenpairs from a shift-invert
+  Lanczos solve (scipy ``eigsh``) of the same matrices.
 
 Tolerances: printed values carry 8 decimals (|error| <= 5e-9 plus the solve's
 eigenvalue error, quadratic in the 1e-8 residual), hence 6e-9 absolute as in the
-oracle's pins; full-size eigenvalues 1e-9 relative, residuals <= 1e-8, cluster
-subspace gaps <= 1e-6 (the acceptance bar of the solve).
+oracle's pins; full-size eigenvalues 1e-9 relative, residuals <= 1e-8 (1e-7 for the
+clamped plate, whose FP64 residual floor is near 1.7e-8), cluster subspace gaps <= 1e-6
+(the acceptance bar of the solve).
 """
 
 import numpy as np
@@ -19,7 +21,7 @@ import scipy.sparse.linalg as sla
 
 from conftest import golden
 from oracle import metrics
-from workloads import config_c2, config_table1_col1, config_table5
+from workloads import config_c2, config_c4, config_table1_col1, config_table5
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -62,16 +64,23 @@ def test_table5_columns_on_gpu(col, n):
     assert metrics.rel_residuals(_csr(pb.K), _csr(pb.M), lam, X).max() <= 1e-8
 
 
-def test_bench_workload_full_size():
-    """C2 (the bench workload) at full size, mixed precision, against eigsh."""
-    spec = config_c2()
-    pb, lam, X, st = _solve(spec, B.MIXED)
+@pytest.mark.parametrize("which", ["c2", "c4"])
+def test_full_size_against_eigsh(which):
+    """C2 (the bench workload, mixed precision) and C4 (clamped plate, Morley; FP32 local
+    solves with every other step in FP64) at full size against eigsh.  C4's residual
+    tolerance is 1e-7: for its first eigenvector |K||x| / |Kx| = 1.1e8, so FP64 rounding
+    alone leaves a relative residual near 1.2e-8 (the solve levels off at 1.7e-8)."""
+    if which == "c2":
+        spec, precision, tol = config_c2(), B.MIXED, 1e-8
+    else:
+        spec, precision, tol = config_c4(), B.MIXED_LOCAL, 1e-7
+    pb, lam, X, st = _solve(spec, precision, tol=tol, max_iter=2000)
     K, M = _csr(pb.K), _csr(pb.M)
     w, V = sla.eigsh(K.tocsc(), spec.k + 4, M.tocsc(), sigma=0.0, which="LM", tol=1e-13)
     order = np.argsort(w)
     w, V = w[order], V[:, order]
     np.testing.assert_allclose(lam, w[: spec.k], rtol=1e-9)
-    assert metrics.rel_residuals(K, M, lam, X).max() <= 1e-8
+    assert metrics.rel_residuals(K, M, lam, X).max() <= tol
     # clusters judged on the wider reference spectrum; a cluster that the k-th
     # eigenvalue shares with the (k+1)-th is pinned by its eigenvalues only
     for a, b in metrics.clusters(w[: spec.k + 1]):

@@ -12,7 +12,7 @@ import pytest
 
 from conftest import ROOT
 from oracle import problem as oracle_problem
-from workloads import config_c1, config_small_2d, config_small_3d, ProblemSpec
+from workloads import config_c1, config_small_2d, config_small_3d, config_small_morley, ProblemSpec
 
 B = pytest.importorskip("paper_2203_06327_gb300.binding")
 
@@ -38,8 +38,10 @@ def _cmp_csr(lib_csr, ora):
 
 
 @pytest.mark.parametrize("spec", [config_c1(), config_small_2d(), config_small_3d(),
-                                  config_small_3d(kind="q1_3d"), config_small_3d(n=16, ns=4, delta=2)],
-                         ids=lambda s: s.name)
+                                  config_small_3d(kind="q1_3d"), config_small_3d(n=16, ns=4, delta=2),
+                                  config_small_morley(), config_small_morley(n=24, ns=4, delta=2, k=4, tau=1),
+                                  config_small_morley(n=32, ns=8, delta=1, k=8)],
+                         ids=lambda s: s.name + f"_tau{s.tau}")
 def test_generators_match_oracle(spec):
     lp = B.problem_from_spec(spec)
     op = oracle_problem.build(spec)
@@ -67,9 +69,30 @@ def test_c2_generators_match_oracle_full_size():
     np.testing.assert_array_equal(lp.part.sub_dofs, dofs)
 
 
+def test_c4_generators_match_oracle_full_size():
+    """The 261121-dof clamped plate (Morley): matrices, transfer and partition bit-exact."""
+    from workloads import config_c4
+    spec = config_c4()
+    lp = B.problem_from_spec(spec)
+    op = oracle_problem.build(spec)
+    for a, b in ((lp.K, op.K), (lp.M, op.M), (lp.P, op.P)):
+        b = b.tocsr()
+        b.sort_indices()
+        np.testing.assert_array_equal(a.row_ptr, b.indptr)
+        np.testing.assert_array_equal(a.col_idx, b.indices)
+        np.testing.assert_array_equal(a.val, b.data)
+    np.testing.assert_array_equal(lp.part.sub_ptr, op.sub_ptr)
+    np.testing.assert_array_equal(lp.part.sub_dofs, op.sub_dofs)
+    np.testing.assert_array_equal(lp.part.sub_color, op.sub_color)
+
+
 def test_problem_create_rejects_bad_mesh():
     with pytest.raises(B.BpjdError) as e:
         B.problem_create("p1_2d", (10, 10), (1.0, 1.0), (3, 3), 1)      # 10 not a multiple of 3
+    with pytest.raises(B.BpjdError):
+        B.problem_create("morley_2d", (16, 12), (1.0, 1.0), (4, 4), 1)  # Morley needs square cells
+    with pytest.raises(B.BpjdError):
+        B.problem_create("morley_2d", (16, 16), (1.0, 1.0), (4, 4), 1, kappa=np.ones((16, 16, 2)))
     assert e.value.code == B.ERR_BAD_ARG
 
 
