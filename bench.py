@@ -254,8 +254,10 @@ def run_reference(a):
 def run_serving(a, B):
     """Poisson stream of independent 2-D eigenproblems (mixed sizes and k) through the
     library's server (one stream per worker), against the same requests solved one at
-    a time.  Mean inter-arrival time = 1.25 x the mean one-at-a-time service time
-    (offered load 0.8).  Latency = submit -> result, per request."""
+    a time (same precision, and plain FP64).  Mean inter-arrival time = 1.25 x the mean
+    one-at-a-time service time (offered load 0.8).  Latency = submit -> result, per
+    request; throughput of the served form = all requests submitted at once, total
+    eigenpairs / makespan."""
     import numpy as np
     from workloads import serving_stream
 
@@ -270,6 +272,14 @@ def run_serving(a, B):
         sv.solve(eigvecs="host")
         sv.close()
         svc.append(time.perf_counter() - t0)
+    # the plain FP64 solver, one request at a time (the baseline the served form is compared with)
+    svc64 = []
+    for pb, r in zip(pbs, reqs):
+        t0 = time.perf_counter()
+        sv = B.Solver.from_problem(pb, r.spec.k, device=None, precision=B.FP64, subspace=B.W_3K)
+        sv.solve(eigvecs="host")
+        sv.close()
+        svc64.append(time.perf_counter() - t0)
     ktot = sum(r.spec.k for r in reqs)
     gap = 1.25 * float(np.mean(svc))
     srv = B.Server(workers=a.serving_workers, precision=prec, subspace=B.W_3K)
@@ -286,11 +296,21 @@ def run_serving(a, B):
         lat.append(times[2])
     makespan = time.perf_counter() - t0
     srv.close()
+    # saturated: every request submitted at once (throughput of the served form)
+    srv = B.Server(workers=a.serving_workers, precision=prec, subspace=B.W_3K)
+    t0 = time.perf_counter()
+    tickets2 = [srv.submit(pb, r.spec.k) for pb, r in zip(pbs, reqs)]
+    for t in tickets2:
+        failed += int(srv.poll(t)[0] != B.OK)
+    sat = time.perf_counter() - t0
+    srv.close()
     lat = np.array(lat)
     return {"requests": len(reqs), "workers": a.serving_workers, "offered_load": 0.8,
             "mean_interarrival_s": gap, "p50_latency_s": float(np.percentile(lat, 50)),
             "p99_latency_s": float(np.percentile(lat, 99)), "eigenpairs_per_s": ktot / makespan,
+            "saturated_eigenpairs_per_s": ktot / sat,
             "one_at_a_time_eigenpairs_per_s": ktot / float(np.sum(svc)),
+            "fp64_one_at_a_time_eigenpairs_per_s": ktot / float(np.sum(svc64)),
             "one_at_a_time_p50_service_s": float(np.percentile(svc, 50)), "failed": failed,
             "stream": "serving_stream(seed 0): P1 on 64..512 squares, random smooth kappa, k in 4..16, tau 1"}
 
