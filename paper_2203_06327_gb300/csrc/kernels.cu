@@ -852,6 +852,27 @@ struct MmaShape {
   static constexpr size_t smem_floats = (size_t)4 * W * BMAX + (size_t)kLocalWarps * PW;
 };
 
+// Position of slot block b in the elimination order that follows pivot block sb
+// (0 = the next to be eliminated); -1 for sb itself and for blocks past the window.
+template <int NBW>
+__device__ __forceinline__ int elim_pos(int b, int sb) {
+  if (b == sb || b >= NBW) return -1;
+  const int p = b - sb - 1;
+  return (p < 0) ? p + NBW : p;
+}
+
+// A window tile (row tile rt = slot blocks 2 rt, 2 rt + 1; column tile ct = slot block
+// ct) is read again only where its rows come at or after its columns in the
+// elimination order (pivot columns, diagonal blocks); the relative order of two
+// blocks in the window never changes, so the trailing update skips the other tiles
+// and the pivot's own column tile (whose slot block is refilled by entering rows).
+template <int NBW>
+__device__ __forceinline__ bool tile_live(int sb, int rt, int ct) {
+  if (ct == sb) return false;
+  const int pr = max(elim_pos<NBW>(2 * rt, sb), elim_pos<NBW>(2 * rt + 1, sb));
+  return pr >= elim_pos<NBW>(ct, sb);
+}
+
 __device__ __forceinline__ uint32_t to_tf32(float x) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
@@ -1065,6 +1086,7 @@ __global__ void __launch_bounds__(128, (BMAX <= 40) ? 3 : 2) k_local_factor_mma(
       for (int rt = 0; rt < RT; ++rt)
 #pragma unroll
         for (int ct = 0; ct < CT; ++ct) {
+          if (!tile_live<NBW>(sb, rt, ct)) continue;  // compile-time: sb, rt, ct are unrolled
           const int bt = ct >> 1, bo = ct & 1;  // B operand = rows ct 8 .. of L: A fragment of tile bt
           mma_tf32(acc[rt][ct], al[rt], ah[bt][bo], ah[bt][bo + 2]);
           mma_tf32(acc[rt][ct], ah[rt], al[bt][bo], al[bt][bo + 2]);
@@ -1362,7 +1384,8 @@ __global__ void __launch_bounds__(WideShape<BMAX>::NW * 32, WideShape<BMAX>::MIN
         }
 #pragma unroll
         for (int jl = 0; jl < CTW; ++jl) {
-          if (wid + NW * jl >= CT) continue;
+          const int ct = wid + NW * jl;
+          if (ct >= CT || !tile_live<NBW>(sb, rt, ct)) continue;  // warp-uniform
           mma_tf32(acc[rt][jl], al, bh[jl][0], bh[jl][1]);
           mma_tf32(acc[rt][jl], ah, bl[jl][0], bl[jl][1]);
           mma_tf32(acc[rt][jl], ah, bh[jl][0], bh[jl][1]);
