@@ -139,7 +139,7 @@ def schwarz_bytes(lay, k, esz, n, nnzP, nH):
 
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one local-solve application
 # (k_local_factor_mma<40> + k_local_backward<40>), keyed by workload and precision
-LOCAL_TRAFFIC = {("c2_kappa_rect_p1_h512", "mixed"): 129.197824e6 + 557.361664e6 + 608.806912e6 + 15.802368e6}
+LOCAL_TRAFFIC = {("c2_kappa_rect_p1_h512", "mixed"): 127.334144e6 + 555.139840e6 + 608.864256e6 + 15.797248e6}
 
 
 def _peaks():
