@@ -81,7 +81,7 @@ def test_full_size_against_eigsh(which):
     w, V = w[order], V[:, order]
     np.testing.assert_allclose(lam, w[: spec.k], rtol=1e-9)
     assert metrics.rel_residuals(K, M, lam, X).max() <= tol
-    # clusters judged on the wider reference spectrum; a cluster that the k-th
+    # clusters taken from the wider reference spectrum; a cluster that the k-th
     # eigenvalue shares with the (k+1)-th is pinned by its eigenvalues only
     for a, b in metrics.clusters(w[: spec.k + 1]):
         if b <= spec.k:

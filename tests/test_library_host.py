@@ -128,3 +128,14 @@ def test_setup_rejects_invalid_map_and_k():
     with pytest.raises(B.BpjdError) as e:
         B.Solver(pb.K, pb.M, pb.P, None, pb.part, 0)
     assert e.value.code == B.ERR_BAD_ARG
+
+
+def test_setup_rejects_unknown_precision_and_subspace():
+    """Precision must be FP64, MIXED or MIXED_LOCAL, the search space 2k or 3k; both are
+    checked before any device work."""
+    pb = _c1_arrays()
+    for kw in ({"precision": 3}, {"precision": -1}, {"subspace": 2}):
+        with pytest.raises(B.BpjdError) as e:
+            B.Solver(pb.K, pb.M, pb.P, pb.P0, pb.part, 6, **kw)
+        assert e.value.code == B.ERR_UNSUPPORTED
+    assert (B.FP64, B.MIXED, B.MIXED_LOCAL) == (0, 1, 2)
