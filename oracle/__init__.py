@@ -11,6 +11,8 @@ Modules
   fem        finite-element stiffness/mass assembly (Section 2.2, Section 6)
   morley     Morley elements for the clamped plate (Section 2.1, m = 2): assembly,
              intergrid transfer V^H -> V^h, half-grid dof numbering
+  bfs        Bogner-Fox-Schmit elements for the clamped plate (Section 2.2, m = 2):
+             tensor-product assembly and the nested coarse interpolation
   partition  overlapping box subdomains and colouring (Section 2.3, Assumption 2)
   coarse     nodal interpolation from the coarse space V^H (Section 2.3)
   bpjd       the two-level BPJD method (Section 3, Algorithm 3.1, Eq. (3.3))

@@ -70,6 +70,9 @@ def prolongation(spec) -> sp.csr_matrix:
     if spec.kind == "morley_2d":
         from . import morley
         return morley.prolongation(spec.n[0], spec.nsub[0])
+    if spec.kind == "bfs_2d":
+        from . import bfs
+        return bfs.prolongation(spec.n[0], spec.nsub[0])
     n, S, dim = spec.n, spec.nsub, spec.dim
     ms = [n[d] // S[d] for d in range(dim)]
     if len(set(ms)) != 1:

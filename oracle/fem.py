@@ -138,6 +138,9 @@ def assemble(spec):
     if spec.kind == "morley_2d":
         from . import morley
         return morley.assemble(spec.n[0], spec.length[0])
+    if spec.kind == "bfs_2d":
+        from . import bfs
+        return bfs.assemble(spec.n[0], spec.length[0])
     kap = spec.kappa_array()
     if spec.kind == "p1_2d":
         Kf, Mf = p1_2d_full(*spec.n, *spec.length, kap)

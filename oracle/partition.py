@@ -21,6 +21,8 @@ carries their dofs (2 n points per axis, subdomains of 2 m half-steps grown by
 2 delta): the dofs strictly inside Omega_l' are the vertices strictly inside
 and the midpoints of the edges not on its boundary, i.e. the Morley functions
 with zero values and normal derivatives on the boundary of Omega_l'.
+For BFS elements (bfs_2d) the rule picks nodes as for p1_2d, each with its four
+dofs (node-major), i.e. the BFS functions in H^2_0(Omega_l').
 """
 
 from __future__ import annotations
@@ -64,6 +66,8 @@ def box_partition(spec):
             g = g + (axes[d] - 1).reshape(shape) * stride
             stride *= inner[d]
         local = np.sort(g.ravel())
+        if spec.kind == "bfs_2d":
+            local = (4 * local[:, None] + np.arange(4)[None, :]).ravel()
         dofs.append(local)
         ptr.append(ptr[-1] + len(local))
         colors.append(sum((s[d] % 2) << d for d in range(dim)))

@@ -24,6 +24,9 @@ the experiments of Section 6:
   with Morley's nonconforming quadratic triangles on the same square grid as
   ``p1_2d`` (the paper itself uses BFS elements for this problem); no
   coefficient, square domain.
+* ``bfs_2d`` -- the clamped plate with the paper's conforming Bogner-Fox-Schmit
+  element (bicubic Hermite: value, two first and the mixed derivative per node);
+  no coefficient, square domain.
 
 Layout of the per-element coefficient array ``kappa`` (float64, C order):
 
@@ -41,8 +44,10 @@ from .specs import (
     config_c2,
     config_c3,
     config_c4,
+    config_c4_bfs,
     config_small_2d,
     config_small_3d,
+    config_small_bfs,
     config_small_morley,
     config_table1_col1,
     config_table5,
@@ -56,8 +61,10 @@ __all__ = [
     "config_c2",
     "config_c3",
     "config_c4",
+    "config_c4_bfs",
     "config_small_2d",
     "config_small_3d",
+    "config_small_bfs",
     "config_small_morley",
     "config_table1_col1",
     "config_table5",

@@ -12,7 +12,7 @@ import numpy as np
 class ProblemSpec:
     """One eigenproblem, described by its mesh and decomposition parameters.
 
-    kind    : "p1_2d" | "p1_3d" | "q1_3d" | "morley_2d"
+    kind    : "p1_2d" | "p1_3d" | "q1_3d" | "morley_2d" | "bfs_2d"
     n       : elements per direction, (nx, ny) or (nx, ny, nz)
     length  : domain edge lengths; the domain is the box [0, Lx] x [0, Ly] (x [0, Lz])
     kappa   : per-element coefficient (layout in the package docstring), None = 1
@@ -47,15 +47,16 @@ class ProblemSpec:
     @property
     def n_dofs(self) -> int:
         """Interior grid nodes (Dirichlet data removed); for morley_2d the interior
-        points of the half-grid (2 nx - 1)(2 ny - 1) (clamped data removed)."""
-        out = 1
+        points of the half-grid (2 nx - 1)(2 ny - 1), for bfs_2d four dofs per interior
+        node (clamped data removed)."""
+        out = 4 if self.kind == "bfs_2d" else 1
         for m in self.n:
             out *= (2 * m - 1) if self.kind == "morley_2d" else (m - 1)
         return out
 
     @property
     def n_coarse(self) -> int:
-        out = 1
+        out = 4 if self.kind == "bfs_2d" else 1
         for m in self.nsub:
             out *= (2 * m - 1) if self.kind == "morley_2d" else (m - 1)
         return out
@@ -71,17 +72,17 @@ class ProblemSpec:
         return np.ones((nz, ny, nx), dtype=np.float64)
 
     def validate(self) -> None:
-        if self.kind not in ("p1_2d", "p1_3d", "q1_3d", "morley_2d"):
+        if self.kind not in ("p1_2d", "p1_3d", "q1_3d", "morley_2d", "bfs_2d"):
             raise ValueError(f"unknown kind {self.kind}")
-        want_dim = 2 if self.kind in ("p1_2d", "morley_2d") else 3
+        want_dim = 2 if self.kind in ("p1_2d", "morley_2d", "bfs_2d") else 3
         if self.dim != want_dim or len(self.length) != want_dim or len(self.nsub) != want_dim:
             raise ValueError("dimension mismatch")
         for m, s in zip(self.n, self.nsub):
             if m % s != 0:
                 raise ValueError("element count must be a multiple of the subdomain count")
-        if self.kind == "morley_2d" and (self.kappa is not None or self.n[0] != self.n[1]
-                                         or self.length[0] != self.length[1]):
-            raise ValueError("morley_2d: square domain and square cells, no coefficient")
+        if self.kind in ("morley_2d", "bfs_2d") and (self.kappa is not None or self.n[0] != self.n[1]
+                                                     or self.length[0] != self.length[1]):
+            raise ValueError(f"{self.kind}: square domain and square cells, no coefficient")
         if self.k >= self.n_coarse:
             raise ValueError("k must be smaller than the coarse space dimension")
         ms = {m // s for m, s in zip(self.n, self.nsub)}
@@ -181,6 +182,18 @@ def config_small_morley(n: int = 32, ns: int = 4, delta: int = 2, k: int = 6, ta
     """A small clamped-plate case (Morley), for parity with the oracle."""
     return ProblemSpec("morley_2d", (n, n), (1.0, 1.0), (ns, ns), delta, k, tau=tau,
                        name=f"small_morley_{n}_{ns}_d{delta}_k{k}")
+
+
+def config_c4_bfs() -> ProblemSpec:
+    """The clamped plate of C4 with the paper's conforming element (BFS) instead of Morley:
+    256 x 256 squares (260100 dofs), k = 8, 8 x 8 subdomains, overlap 2 layers."""
+    return ProblemSpec("bfs_2d", (256, 256), (1.0, 1.0), (8, 8), 2, 8, name="c4_clamped_plate_bfs_h256")
+
+
+def config_small_bfs(n: int = 32, ns: int = 4, delta: int = 2, k: int = 4, tau: int = 0) -> ProblemSpec:
+    """A small clamped-plate case with BFS elements, for parity with the oracle."""
+    return ProblemSpec("bfs_2d", (n, n), (1.0, 1.0), (ns, ns), delta, k, tau=tau,
+                       name=f"small_bfs_{n}_{ns}_d{delta}_k{k}")
 
 
 def config_small_2d(nx: int = 48, ny: int = 36, nsx: int = 4, nsy: int = 3, delta: int = 2,
