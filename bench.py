@@ -45,7 +45,7 @@ def _args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c4bfs"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "mixed_local", "fp64"])
     ap.add_argument("--tol", type=float, default=1e-8, help="relative residual of the stop test")
     ap.add_argument("--max-iter", type=int, default=2000)
@@ -59,8 +59,8 @@ def _args():
 
 
 def _spec(name):
-    from workloads import config_c1, config_c2, config_c3, config_c4
-    return {"c1": config_c1, "c2": config_c2, "c3": config_c3, "c4": config_c4}[name]()
+    from workloads import config_c1, config_c2, config_c3, config_c4, config_c4_bfs
+    return {"c1": config_c1, "c2": config_c2, "c3": config_c3, "c4": config_c4, "c4bfs": config_c4_bfs}[name]()
 
 
 # ---------------------------------------------------------------------------
@@ -214,7 +214,7 @@ def oracle_sample(spec, iters_needed: int, n_local: int = 4, op=None):
 def _oracle_locals(spec, n):
     """Subdomains in the oracle's local-solve sample: clamped-plate subdomains hold ~5000
     dofs (dense Cholesky ~0.5 s each per shift), so only a few are timed there."""
-    return 4 if spec.kind == "morley_2d" else n
+    return 4 if spec.kind in ("morley_2d", "bfs_2d") else n
 
 
 def _blas_threads():
@@ -232,7 +232,7 @@ def run_reference(a):
     if rank != 0:
         return
     spec = _spec(a.workload)
-    iters = {"c1": 21, "c2": 38, "c3": 45, "c4": 665}[a.workload]  # iterations the GPU solve takes (c4: to 1e-7)
+    iters = {"c1": 21, "c2": 38, "c3": 45, "c4": 665, "c4bfs": 100}[a.workload]  # iterations the GPU solve takes (c4: to 1e-7)
     vals = []
     sample = ""
     op = oracle_problem(spec)

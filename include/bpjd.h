@@ -262,7 +262,13 @@ int bpjd_profile_read(bpjd_handle* h, double* ms, int64_t* count, int64_t* kerne
  *            h (du/dx - du/dy) at the horizontal, vertical and diagonal edge
  *            midpoints; the stiffness is the broken Hessian form; P is the
  *            averaging intergrid transfer from the Morley space of the
- *            subdomain grid; subdomains follow the box rule on the half-grid.
+ *            subdomain grid; subdomains follow the box rule on the half-grid;
+ *   kind 4 = the clamped plate with Bogner-Fox-Schmit bicubics (Section 2.2,
+ *            the paper's element for m = 2) on an n x n square grid (equal
+ *            sides, kappa NULL): four dofs per interior node, node-major
+ *            4 node + c for (u, h du/dx, h du/dy, h^2 d^2u/dxdy); P is the
+ *            nested interpolation from BFS on the subdomain grid; subdomains
+ *            take the box rule on nodes with all four dofs.
  * kappa: per-element coefficient, layout [ny][nx][2] (kind 0, entry 0 = the
  * triangle below the diagonal) or [nz][ny][nx] (kinds 1, 2); NULL = 1.
  * Subdomains: nsub boxes per axis grown by delta element layers; the initial

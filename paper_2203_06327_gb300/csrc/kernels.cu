@@ -3024,9 +3024,9 @@ __global__ void k_band_pad_f32(int64_t rows, int B, int W, const double* __restr
 
 // Galerkin products K_H = P^T K P and M_H = P^T M P in two deterministic passes.
 // Pass 1 (thread per fine row r): the sparse rows (K P)[r, :] and (M P)[r, :],
-// at most kKPWidth coarse columns each, accumulated in a fixed order.
-constexpr int kKPWidth = 32;
-__global__ void k_kp_rows(int n, const int64_t* __restrict__ arp, const int32_t* __restrict__ aci,
+// at most `width` coarse columns each (32 first; wider on overflow, e.g. for the
+// 16-entry rows of the BFS interpolation), accumulated in a fixed order.
+__global__ void k_kp_rows(int n, int width, const int64_t* __restrict__ arp, const int32_t* __restrict__ aci,
                           const double* __restrict__ av, const int64_t* __restrict__ mrp,
                           const int32_t* __restrict__ mci, const double* __restrict__ mv,
                           const int64_t* __restrict__ prp, const int32_t* __restrict__ pci,
@@ -3034,16 +3034,16 @@ __global__ void k_kp_rows(int n, const int64_t* __restrict__ arp, const int32_t*
                           int32_t* overflow) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
-  int32_t* cols = kpc + (int64_t)r * kKPWidth;
-  double* vk = kpk + (int64_t)r * kKPWidth;
-  double* vm = kpm + (int64_t)r * kKPWidth;
+  int32_t* cols = kpc + (int64_t)r * width;
+  double* vk = kpk + (int64_t)r * width;
+  double* vm = kpm + (int64_t)r * width;
   int m = 0;
   bool full = false;
   auto add = [&](int32_t b, double x, bool isk) {
     int s = 0;
     while (s < m && cols[s] != b) ++s;
     if (s == m) {
-      if (m == kKPWidth) {
+      if (m == width) {
         full = true;
         return;
       }
@@ -3077,7 +3077,7 @@ __global__ void k_kp_rows(int n, const int64_t* __restrict__ arp, const int32_t*
 // so every entry is summed in a fixed order.  The loads of the next
 // kGalerkinUnroll rows are issued before their updates.
 constexpr int kGalerkinUnroll = 8;
-__global__ void k_galerkin_rows(int nH, const int64_t* __restrict__ ptr, const int32_t* __restrict__ ptc,
+__global__ void k_galerkin_rows(int nH, int width, const int64_t* __restrict__ ptr, const int32_t* __restrict__ ptc,
                                 const double* __restrict__ ptv, const int32_t* __restrict__ kpc,
                                 const double* __restrict__ kpk, const double* __restrict__ kpm,
                                 const int32_t* __restrict__ cnt, double* KH, double* MH) {
@@ -3105,20 +3105,23 @@ __global__ void k_galerkin_rows(int nH, const int64_t* __restrict__ ptr, const i
       p[u] = ok ? ptv[e + u] : 0.0;
       m[u] = ok ? cnt[rr[u]] : 0;
     }
+    // entries hb + lane of each (K P) row, 32 at a time (one pass for rows of <= 32)
+    for (int hb = 0; hb < width; hb += 32) {
 #pragma unroll
-    for (int u = 0; u < GU; ++u) {
-      const bool ok = lane < m[u];
-      const int64_t o = (int64_t)rr[u] * kKPWidth + lane;
-      b[u] = ok ? kpc[o] : 0;
-      xk[u] = ok ? kpk[o] : 0.0;
-      xm[u] = ok ? kpm[o] : 0.0;
-    }
-#pragma unroll
-    for (int u = 0; u < GU; ++u)
-      if (lane < m[u]) {
-        kr[b[u]] += p[u] * xk[u];
-        mr[b[u]] += p[u] * xm[u];
+      for (int u = 0; u < GU; ++u) {
+        const bool ok = hb + lane < m[u];
+        const int64_t o = (int64_t)rr[u] * width + hb + lane;
+        b[u] = ok ? kpc[o] : 0;
+        xk[u] = ok ? kpk[o] : 0.0;
+        xm[u] = ok ? kpm[o] : 0.0;
       }
+#pragma unroll
+      for (int u = 0; u < GU; ++u)
+        if (hb + lane < m[u]) {
+          kr[b[u]] += p[u] * xk[u];
+          mr[b[u]] += p[u] * xm[u];
+        }
+    }
   }
   __syncthreads();
   for (int t = threadIdx.x; t < nH; t += blockDim.x) {
@@ -3554,33 +3557,42 @@ int launch_band_pos(Handle& h, const CsrDev& c, int64_t* pos) {
 int launch_galerkin(const CsrDev& A, const CsrDev& Msp, const CsrDev& P, const CsrDev& PT, double* KH,
                     double* MH, cudaStream_t s) {
   const int n = A.n_rows, nH = P.n_cols;
-  int32_t *kpc = nullptr, *cnt = nullptr, *ovf = nullptr;
-  double *kpk = nullptr, *kpm = nullptr;
-  int rc = 0, hov = 0;
   const int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, (200 * 1024) / (2 * (size_t)nH * sizeof(double))));
   const size_t sm = (size_t)wpb * 2 * nH * sizeof(double);
-  cudaError_t e = cudaSuccess;
-  if ((e = cudaMalloc(&kpc, sizeof(int32_t) * (size_t)n * kKPWidth)) != cudaSuccess) goto done;
-  if ((e = cudaMalloc(&kpk, sizeof(double) * (size_t)n * kKPWidth)) != cudaSuccess) goto done;
-  if ((e = cudaMalloc(&kpm, sizeof(double) * (size_t)n * kKPWidth)) != cudaSuccess) goto done;
-  if ((e = cudaMalloc(&cnt, sizeof(int32_t) * (size_t)n)) != cudaSuccess) goto done;
-  if ((e = cudaMalloc(&ovf, sizeof(int32_t))) != cudaSuccess) goto done;
-  if ((e = cudaMemsetAsync(ovf, 0, sizeof(int32_t), s)) != cudaSuccess) goto done;
-  k_kp_rows<<<(n + 127) / 128, 128, 0, s>>>(n, A.row_ptr, A.col, A.val, Msp.row_ptr, Msp.col, Msp.val, P.row_ptr,
-                                            P.col, P.val, kpc, kpk, kpm, cnt, ovf);
-  allow_dynamic_smem((const void*)k_galerkin_rows);
-  k_galerkin_rows<<<nH, 32 * wpb, sm, s>>>(nH, PT.row_ptr, PT.col, PT.val, kpc, kpk, kpm, cnt, KH, MH);
-  if ((e = cudaGetLastError()) != cudaSuccess) goto done;
-  if ((e = cudaMemcpyAsync(&hov, ovf, sizeof(int32_t), cudaMemcpyDeviceToHost, s)) != cudaSuccess) goto done;
-  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) goto done;
-  if (hov) rc = (int)cudaErrorInvalidValue;
-done:
-  cudaFree(kpc);
-  cudaFree(kpk);
-  cudaFree(kpm);
-  cudaFree(cnt);
-  cudaFree(ovf);
-  return e != cudaSuccess ? (int)e : rc;
+  int rc = (int)cudaErrorInvalidValue;
+  for (int width = 32; width <= 128 && rc == (int)cudaErrorInvalidValue; width *= 2) {
+    int32_t *kpc = nullptr, *cnt = nullptr, *ovf = nullptr;
+    double *kpk = nullptr, *kpm = nullptr;
+    int hov = 0;
+    cudaError_t e = cudaSuccess;
+    rc = 0;
+    if ((e = cudaMalloc(&kpc, sizeof(int32_t) * (size_t)n * width)) != cudaSuccess) goto done;
+    if ((e = cudaMalloc(&kpk, sizeof(double) * (size_t)n * width)) != cudaSuccess) goto done;
+    if ((e = cudaMalloc(&kpm, sizeof(double) * (size_t)n * width)) != cudaSuccess) goto done;
+    if ((e = cudaMalloc(&cnt, sizeof(int32_t) * (size_t)n)) != cudaSuccess) goto done;
+    if ((e = cudaMalloc(&ovf, sizeof(int32_t))) != cudaSuccess) goto done;
+    if ((e = cudaMemsetAsync(ovf, 0, sizeof(int32_t), s)) != cudaSuccess) goto done;
+    k_kp_rows<<<(n + 127) / 128, 128, 0, s>>>(n, width, A.row_ptr, A.col, A.val, Msp.row_ptr, Msp.col, Msp.val,
+                                              P.row_ptr, P.col, P.val, kpc, kpk, kpm, cnt, ovf);
+    if ((e = cudaMemcpyAsync(&hov, ovf, sizeof(int32_t), cudaMemcpyDeviceToHost, s)) != cudaSuccess) goto done;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) goto done;
+    if (hov) {
+      rc = (int)cudaErrorInvalidValue;  // a row of K P holds more coarse columns: retry wider
+      goto done;
+    }
+    allow_dynamic_smem((const void*)k_galerkin_rows);
+    k_galerkin_rows<<<nH, 32 * wpb, sm, s>>>(nH, width, PT.row_ptr, PT.col, PT.val, kpc, kpk, kpm, cnt, KH, MH);
+    if ((e = cudaGetLastError()) != cudaSuccess) goto done;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) goto done;
+  done:
+    cudaFree(kpc);
+    cudaFree(kpk);
+    cudaFree(kpm);
+    cudaFree(cnt);
+    cudaFree(ovf);
+    if (e != cudaSuccess) return (int)e;
+  }
+  return rc;
 }
 
 }  // namespace bpjd

@@ -256,7 +256,7 @@ int assemble_q1_3d(const bpjd_mesh& m, CsrBuf& K, CsrBuf& M) {
 // Box partition: along axis d, subdomain s spans the open node-index interval
 // (lo, hi), lo = s m - delta (0 for s = 0), hi = (s+1) m + delta (n for the last);
 // its dofs are the nodes strictly inside, ascending; colour = sum_d (s_d mod 2) 2^d.
-void box_partition(const bpjd_mesh& m, int dim, ProblemImpl& P) {
+void box_partition(const bpjd_mesh& m, int dim, ProblemImpl& P, int dofs_per_node = 1) {
   int S[3] = {1, 1, 1}, n[3] = {2, 2, 2};
   for (int d = 0; d < dim; ++d) {
     S[d] = m.nsub[d];
@@ -285,7 +285,7 @@ void box_partition(const bpjd_mesh& m, int dim, ProblemImpl& P) {
           for (int j = a[1]; j <= b[1]; ++j)
             for (int i = a[0]; i <= b[0]; ++i) {
               int64_t g = (i - 1) + inner[0] * ((j - 1) + (dim == 3 ? inner[1] * (l - 1) : 0));
-              P.sub_dofs.push_back((int32_t)g);
+              for (int c = 0; c < dofs_per_node; ++c) P.sub_dofs.push_back((int32_t)(dofs_per_node * g + c));
             }
         P.sub_ptr.push_back((int64_t)P.sub_dofs.size());
         int col = 0;
@@ -668,19 +668,189 @@ int morley_transfer(const bpjd_mesh& m, int S, CsrBuf& P) {
   return BPJD_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Bogner-Fox-Schmit elements for the clamped plate (Section 2.1, Section 2.2,
+// m = 2): C^1 bicubics, tensor products of 1-D cubic Hermite functions.  Each
+// node carries u, h du/dx, h du/dy, h^2 d^2u/dxdy (node-major dofs
+// 4 node + a + 2 b, a / b = x / y derivative order); clamped data remove the
+// boundary nodes.  With the 1-D matrices M0 = int phi psi, K1 = int phi' psi',
+// K2 = int phi'' psi'' (scaled by h, 1/h, 1/h^3) the stiffness is
+// M0 (x) K2 + 2 K1 (x) K1 + K2 (x) M0 (y factor first) and the mass M0 (x) M0;
+// on H^2_0 int D^2u : D^2v equals int Delta u Delta v.
+// ---------------------------------------------------------------------------
+
+// cubic Hermite basis on [0, 1]: C[p][a] = coefficient of s^p in basis a
+// (a = value / derivative at 0, value / derivative at 1)
+void hermite_basis(Rat C[4][4]) {
+  Rat A[4][8];
+  const int V[4][4] = {{1, 0, 0, 0}, {0, 1, 0, 0}, {1, 1, 1, 1}, {0, 1, 2, 3}};
+  for (int r = 0; r < 4; ++r)
+    for (int j = 0; j < 8; ++j) A[r][j] = Rat(j < 4 ? V[r][j] : (j - 4 == r ? 1 : 0));
+  for (int c = 0; c < 4; ++c) {
+    int piv = c;
+    while (A[piv][c].zero()) ++piv;
+    for (int j = 0; j < 8; ++j) std::swap(A[c][j], A[piv][j]);
+    Rat inv = Rat(1) / A[c][c];
+    for (int j = 0; j < 8; ++j) A[c][j] = A[c][j] * inv;
+    for (int r = 0; r < 4; ++r) {
+      if (r == c || A[r][c].zero()) continue;
+      Rat f = A[r][c];
+      for (int j = 0; j < 8; ++j) A[r][j] = A[r][j] - f * A[c][j];
+    }
+  }
+  for (int p = 0; p < 4; ++p)
+    for (int a = 0; a < 4; ++a) C[p][a] = A[p][4 + a];
+}
+
+// 1-D element matrices on the unit cell: E[0] = M0, E[1] = K1, E[2] = K2
+void hermite_element(Rat E[3][4][4]) {
+  Rat C[4][4];
+  hermite_basis(C);
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b)
+      for (int d = 0; d < 3; ++d) {
+        // int_0^1 (d-th derivative of basis a)(d-th derivative of basis b)
+        Rat acc(0);
+        for (int p = d; p < 4; ++p)
+          for (int q = d; q < 4; ++q) {
+            int64_t fp = 1, fq = 1;
+            for (int t = 0; t < d; ++t) {
+              fp *= (p - t);
+              fq *= (q - t);
+            }
+            acc = acc + C[p][a] * C[q][b] * Rat(fp * fq, (p - d) + (q - d) + 1);
+          }
+        E[d][a][b] = acc;
+      }
+}
+
+int assemble_bfs(const bpjd_mesh& m, CsrBuf& K, CsrBuf& M) {
+  const int n = m.n[0];
+  const double h = m.length[0] / n;
+  const int mi = n - 1;  // interior nodes per axis
+  Rat E[3][4][4];
+  hermite_element(E);
+  const double scale[3] = {h, 1.0 / h, 1.0 / std::pow(h, 3)};
+  // assembled 1-D matrices over the interior node dofs (value, h derivative), in the
+  // order the cells are visited; entry (r, dr) holds row r, column r + dr - 3
+  std::vector<double> G[3];
+  const int nd = 2 * mi;
+  for (int d = 0; d < 3; ++d) G[d].assign((size_t)nd * 7, 0.0);
+  for (int e = 0; e < n; ++e) {
+    for (int a = 0; a < 4; ++a) {
+      const int ra = 2 * (e - 1) + a;  // interior dof index (node e - 1 + (a >> 1))
+      if (ra < 0 || ra >= nd) continue;
+      for (int b = 0; b < 4; ++b) {
+        const int rb = 2 * (e - 1) + b;
+        if (rb < 0 || rb >= nd) continue;
+        for (int d = 0; d < 3; ++d) G[d][(size_t)ra * 7 + (rb - ra + 3)] += E[d][a][b].to_double() * scale[d];
+      }
+    }
+  }
+  auto g1 = [&](int d, int r, int c) { return G[d][(size_t)r * 7 + (c - r + 3)]; };
+  const int64_t N = 4 * (int64_t)mi * mi;
+  K.n_rows = K.n_cols = M.n_rows = M.n_cols = (int32_t)N;
+  K.row_ptr.assign(N + 1, 0);
+  for (int j = 0; j < mi; ++j)
+    for (int i = 0; i < mi; ++i)
+      for (int c = 0; c < 4; ++c) {
+        const int a = c & 1, b = c >> 1;
+        const int rx = 2 * i + a, ry = 2 * j + b;
+        const int64_t row = 4 * ((int64_t)j * mi + i) + c;
+        for (int j2 = std::max(0, j - 1); j2 <= std::min(mi - 1, j + 1); ++j2)
+          for (int i2 = std::max(0, i - 1); i2 <= std::min(mi - 1, i + 1); ++i2)
+            for (int c2 = 0; c2 < 4; ++c2) {
+              const int cx = 2 * i2 + (c2 & 1), cy = 2 * j2 + (c2 >> 1);
+              const double My0 = g1(0, ry, cy), Ky1 = g1(1, ry, cy), Ky2 = g1(2, ry, cy);
+              const double Mx0 = g1(0, rx, cx), Kx1 = g1(1, rx, cx), Kx2 = g1(2, rx, cx);
+              K.col.push_back((int32_t)(4 * ((int64_t)j2 * mi + i2) + c2));
+              K.val.push_back((My0 * Kx2 + 2.0 * (Ky1 * Kx1)) + Ky2 * Mx0);
+              M.col.push_back(K.col.back());
+              M.val.push_back(My0 * Mx0);
+            }
+        K.row_ptr[row + 1] = (int64_t)K.col.size();
+      }
+  M.row_ptr = K.row_ptr;
+  return BPJD_OK;
+}
+
+// Nested coarse interpolation for BFS: fine node dofs of the coarse bicubic Hermite
+// functions, a tensor product of the 1-D transfers (exact rationals rounded once).
+int bfs_transfer(const bpjd_mesh& m, int S, CsrBuf& P) {
+  const int n = m.n[0];
+  if (S < 2 || n % S != 0) return BPJD_ERR_BAD_ARG;
+  const int mm = n / S;
+  Rat C[4][4];
+  hermite_basis(C);
+  // 1-D: for fine dof fd (node f, order a) the coarse dofs and values
+  std::vector<std::vector<std::pair<int, Rat>>> T1((size_t)2 * (n + 1));
+  for (int f = 0; f <= n; ++f) {
+    const int cell = std::min(f / mm, S - 1);
+    const Rat s(f - cell * mm, mm);
+    for (int a = 0; a < 4; ++a) {
+      const int cdof = 2 * (cell + (a >> 1)) + (a & 1);
+      Rat val(0), der(0);
+      for (int p = 0; p < 4; ++p) {
+        val = val + C[p][a] * rpow(s, p);
+        if (p) der = der + Rat(p) * C[p][a] * rpow(s, p - 1);
+      }
+      der = der / Rat(mm);
+      if (!val.zero()) T1[2 * f].push_back({cdof, val});
+      if (!der.zero()) T1[2 * f + 1].push_back({cdof, der});
+    }
+  }
+  const int mi = n - 1, mc = S - 1;
+  const int64_t N = 4 * (int64_t)mi * mi;
+  P.n_rows = (int32_t)N;
+  P.n_cols = (int32_t)(4 * (int64_t)mc * mc);
+  P.row_ptr.assign(N + 1, 0);
+  std::vector<std::pair<int64_t, Rat>> row;
+  for (int j = 1; j < n; ++j)
+    for (int i = 1; i < n; ++i)
+      for (int c = 0; c < 4; ++c) {
+        const int a = c & 1, b = c >> 1;
+        row.clear();
+        for (auto& ty : T1[2 * j + b])
+          for (auto& tx : T1[2 * i + a]) {
+            const int jc = ty.first >> 1, bc = ty.first & 1, ic = tx.first >> 1, ac = tx.first & 1;
+            if (ic <= 0 || ic >= S || jc <= 0 || jc >= S) continue;  // clamped coarse nodes
+            const int64_t col = 4 * ((int64_t)(jc - 1) * mc + (ic - 1)) + ac + 2 * bc;
+            const Rat v = tx.second * ty.second;
+            bool found = false;
+            for (auto& r : row)
+              if (r.first == col) {
+                r.second = r.second + v;
+                found = true;
+                break;
+              }
+            if (!found) row.push_back({col, v});
+          }
+        std::sort(row.begin(), row.end(),
+                  [](const std::pair<int64_t, Rat>& u, const std::pair<int64_t, Rat>& v) { return u.first < v.first; });
+        const int64_t g = 4 * ((int64_t)(j - 1) * mi + (i - 1)) + c;
+        for (auto& r : row) {
+          if (r.second.zero()) continue;
+          P.col.push_back((int32_t)r.first);
+          P.val.push_back(r.second.to_double());
+        }
+        P.row_ptr[g + 1] = (int64_t)P.col.size();
+      }
+  return BPJD_OK;
+}
+
 }  // namespace
 
 extern "C" int bpjd_problem_create(const bpjd_mesh* mesh, bpjd_problem** out) {
   if (!mesh || !out) return BPJD_ERR_BAD_ARG;
   *out = nullptr;
   const bpjd_mesh& m = *mesh;
-  int dim = (m.kind == 0 || m.kind == 3) ? 2 : 3;
-  if (m.kind < 0 || m.kind > 3) return BPJD_ERR_BAD_ARG;
+  int dim = (m.kind == 0 || m.kind == 3 || m.kind == 4) ? 2 : 3;
+  if (m.kind < 0 || m.kind > 4) return BPJD_ERR_BAD_ARG;
   for (int d = 0; d < dim; ++d) {
     if (m.n[d] < 2 || m.nsub[d] < 1 || m.n[d] % m.nsub[d] != 0 || !(m.length[d] > 0)) return BPJD_ERR_BAD_ARG;
   }
   if (m.delta < 0 || m.tau < 0 || m.tau > 6) return BPJD_ERR_BAD_ARG;
-  if (m.kind == 3) {
+  if (m.kind == 3 || m.kind == 4) {
     if (m.n[0] != m.n[1] || m.nsub[0] != m.nsub[1] || m.length[0] != m.length[1]) return BPJD_ERR_BAD_ARG;
     if (m.kappa) return BPJD_ERR_UNSUPPORTED;
     if ((m.n[0] / m.nsub[0]) % (1 << m.tau) != 0) return BPJD_ERR_BAD_ARG;
@@ -694,7 +864,17 @@ extern "C" int bpjd_problem_create(const bpjd_mesh* mesh, bpjd_problem** out) {
   if (!P) return BPJD_ERR_OOM;
   int rc;
   try {
-    if (m.kind == 3) {
+    if (m.kind == 4) {
+      rc = assemble_bfs(m, P->K, P->M);
+      if (rc == BPJD_OK) rc = bfs_transfer(m, m.nsub[0], P->P);
+      if (rc == BPJD_OK) {
+        if (m.tau == 0)
+          P->P0 = P->P;
+        else
+          rc = bfs_transfer(m, m.nsub[0] << m.tau, P->P0);
+      }
+      if (rc == BPJD_OK) box_partition(m, dim, *P, 4);
+    } else if (m.kind == 3) {
       rc = assemble_morley(m, P->K, P->M);
       if (rc == BPJD_OK) rc = morley_transfer(m, m.nsub[0], P->P);
       if (rc == BPJD_OK) {

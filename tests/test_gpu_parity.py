@@ -17,7 +17,7 @@ import scipy.linalg as la
 
 from oracle import bpjd as obpjd
 from oracle import metrics, problem as oproblem
-from workloads import config_c1, config_small_2d, config_small_3d, config_small_morley, ProblemSpec
+from workloads import config_c1, config_small_2d, config_small_3d, config_small_bfs, config_small_morley, ProblemSpec
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -63,7 +63,8 @@ def test_spmm_matches_oracle(c1_oracle, ncols):
                                   config_small_3d(n=32, ns=4), config_small_3d(n=36, ns=4),
                                   config_small_morley(n=32, ns=8, delta=1, k=8),
                                   config_small_morley(n=32, ns=4, delta=2, k=6, tau=1),
-                                  config_small_morley(n=128, ns=4, delta=2, k=2)],
+                                  config_small_morley(n=128, ns=4, delta=2, k=2),
+                                  config_small_bfs(), config_small_bfs(n=32, ns=8, delta=1, k=8)],
                          ids=lambda s: s.name)
 @pytest.mark.parametrize("precision", [B.FP64, B.MIXED], ids=["fp64", "mixed"])
 def test_preconditioner_matches_oracle(spec, precision):
@@ -81,10 +82,10 @@ def test_preconditioner_matches_oracle(spec, precision):
     # FP32 local factorisations: forward error ~ sqrt(B) kappa eps_32 with kappa the (diagonally
     # scaled) condition number of K_l - lambda M_l: a few hundred for the second-order windows
     # here; about 4.3e4 for clamped-plate windows of 36 cells (fourth order: kappa ~ (H/h)^4),
-    # i.e. sqrt(145) 4.3e4 6e-8 = 3e-2 at window 145
+    # i.e. sqrt(145) 4.3e4 6e-8 = 3e-2 at window 145 (Morley and BFS alike)
     if precision == B.FP64:
         tol = 1e-10
-    elif spec.kind == "morley_2d":
+    elif spec.kind in ("morley_2d", "bfs_2d"):
         tol = 5e-2
     else:
         tol = 2e-3
@@ -147,7 +148,8 @@ def test_c1_solve_matches_oracle(c1_oracle, subspace, precision):
 @pytest.mark.parametrize("spec", [config_small_2d(), config_small_3d(), config_small_3d(kind="q1_3d"),
                                   config_small_2d(nx=40, ny=40, nsx=5, nsy=5, delta=1, k=1, kappa="random"),
                                   config_small_morley(n=32, ns=8, delta=1, k=8),
-                                  config_small_morley(n=32, ns=4, delta=2, k=6, tau=1)],
+                                  config_small_morley(n=32, ns=4, delta=2, k=6, tau=1),
+                                  config_small_bfs(), config_small_bfs(n=32, ns=8, delta=1, k=8)],
                          ids=lambda s: s.name)
 def test_other_problems_solve(spec):
     op = oproblem.build(spec)

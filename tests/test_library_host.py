@@ -12,7 +12,7 @@ import pytest
 
 from conftest import ROOT
 from oracle import problem as oracle_problem
-from workloads import config_c1, config_small_2d, config_small_3d, config_small_morley, ProblemSpec
+from workloads import config_c1, config_small_2d, config_small_3d, config_small_bfs, config_small_morley, ProblemSpec
 
 B = pytest.importorskip("paper_2203_06327_gb300.binding")
 
@@ -40,7 +40,8 @@ def _cmp_csr(lib_csr, ora):
 @pytest.mark.parametrize("spec", [config_c1(), config_small_2d(), config_small_3d(),
                                   config_small_3d(kind="q1_3d"), config_small_3d(n=16, ns=4, delta=2),
                                   config_small_morley(), config_small_morley(n=24, ns=4, delta=2, k=4, tau=1),
-                                  config_small_morley(n=32, ns=8, delta=1, k=8)],
+                                  config_small_morley(n=32, ns=8, delta=1, k=8),
+                                  config_small_bfs(), config_small_bfs(n=24, ns=4, delta=2, k=4, tau=1)],
                          ids=lambda s: s.name + f"_tau{s.tau}")
 def test_generators_match_oracle(spec):
     lp = B.problem_from_spec(spec)
@@ -93,6 +94,8 @@ def test_problem_create_rejects_bad_mesh():
         B.problem_create("morley_2d", (16, 12), (1.0, 1.0), (4, 4), 1)  # Morley needs square cells
     with pytest.raises(B.BpjdError):
         B.problem_create("morley_2d", (16, 16), (1.0, 1.0), (4, 4), 1, kappa=np.ones((16, 16, 2)))
+    with pytest.raises(B.BpjdError):
+        B.problem_create("bfs_2d", (16, 16), (1.0, 2.0), (4, 4), 1)       # BFS needs square cells
     assert e.value.code == B.ERR_BAD_ARG
 
 
