@@ -217,6 +217,24 @@ def _oracle_locals(spec, n):
     return 4 if spec.kind in ("morley_2d", "bfs_2d") else n
 
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The slowest rank's time (replicas run independently; the job ends with the last);
+    a barrier follows so that no rank leaves while another still reduces."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def replica_throughput(world: int, k: int, steps: int, total_ms: float) -> float:
+    """Whole-job eigenpairs/s: every rank solves `steps` problems of k eigenpairs."""
+    return world * k * steps / (total_ms / 1e3)
+
+
 def _blas_threads():
     try:
         from threadpoolctl import threadpool_info
@@ -384,13 +402,8 @@ def run_ours(a):
             sv.close()
     torch.cuda.synchronize()
     ck = clocks.stop()
-    total_ms = sum(times)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        dist.barrier()
-    value = world * k * a.steps / (total_ms / 1e3)
+    total_ms = max_over_ranks(sum(times), world, dev)
+    value = replica_throughput(world, k, a.steps, total_ms)
 
     # roofline of the dominant kernel class (local band solves expected)
     dom = max(prof_tot, key=lambda kk: prof_tot[kk][0])
