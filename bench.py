@@ -250,7 +250,7 @@ def run_reference(a):
     if rank != 0:
         return
     spec = _spec(a.workload)
-    iters = {"c1": 21, "c2": 38, "c3": 45, "c4": 665, "c4bfs": 100}[a.workload]  # iterations the GPU solve takes (c4: to 1e-7)
+    iters = {"c1": 21, "c2": 38, "c3": 45, "c4": 77, "c4bfs": 82}[a.workload]  # iterations the GPU solve takes (c4*: to 1e-7)
     vals = []
     sample = ""
     op = oracle_problem(spec)

@@ -260,9 +260,9 @@ int bpjd_profile_read(bpjd_handle* h, double* ms, int64_t* count, int64_t* kerne
  *            the half-grid, numbered (Y-1)(2n-1) + (X-1): vertex values at even
  *            (X, Y), scaled normal derivatives h du/dy, h du/dx and
  *            h (du/dx - du/dy) at the horizontal, vertical and diagonal edge
- *            midpoints; the stiffness is the broken Hessian form; P is the
- *            averaging intergrid transfer from the Morley space of the
- *            subdomain grid; subdomains follow the box rule on the half-grid;
+ *            midpoints; the stiffness is the broken Hessian form; the coarse
+ *            space is BFS (kind 4) on the subdomain grid and P its Morley
+ *            interpolant; subdomains follow the box rule on the half-grid;
  *   kind 4 = the clamped plate with Bogner-Fox-Schmit bicubics (Section 2.2,
  *            the paper's element for m = 2) on an n x n square grid (equal
  *            sides, kappa NULL): four dofs per interior node, node-major

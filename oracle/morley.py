@@ -24,6 +24,12 @@ half-grid points on the boundary: the dofs are the interior half-grid points,
 numbered (Y - 1)(2n - 1) + (X - 1) (x fastest).  Simply supported conditions
 (u = 0 on the boundary only) keep the boundary edge midpoints.
 
+The coarse space is conforming: BFS bicubics on the subdomain grid, brought into
+V^h by the Morley interpolant (their values at fine vertices and scaled normal
+derivatives at fine edge midpoints); its Galerkin eigenvalues lie within a few
+tenths of a percent of the fine ones, where an averaging transfer from a coarse
+Morley space gives a coarse pencil 1.7 to 30 times too stiff.
+
 All rational work uses ``fractions.Fraction``; floats appear only when the
 element matrices are scaled by h and when the transfer matrix is returned.
 """
@@ -194,72 +200,68 @@ def assemble(n: int, L: float = 1.0, bc: str = "clamped"):
     return K, M
 
 
-def _candidate_cells(X: int, w: int, S: int):
-    """Coarse cells (of width w half-grid units) whose closure contains coordinate X."""
-    if X % w == 0:
-        return [c for c in (X // w - 1, X // w) if 0 <= c < S]
-    return [X // w]
-
-
-@lru_cache(maxsize=None)
-def _row_pattern(m: int, xl: int, yl: int, kind: str):
-    """Contributions of one coarse element (local coordinates (xl, yl) of the fine point
-    in half-grid units, 0..2m) to a fine dof of the given kind: list of
-    (shape, coarse local dof a, value) over the coarse triangles of the cell whose
-    closure contains the point."""
-    w = 2 * m
-    out = []
-    for shape in ("lower", "upper"):
-        if (shape == "lower" and xl < yl) or (shape == "upper" and xl > yl):
-            continue
-        C = reference_basis(shape)
-        xi, eta = F(xl, w), F(yl, w)
-        for a in range(6):
-            v = sum(C[mi][a] * functional(kind, p, q, xi, eta) for mi, (p, q) in enumerate(MONO))
-            if kind != "v":
-                v = v / m           # fine h d/dx = (h / H) times the coarse scaled derivative
-            out.append((shape, a, v))
-    return tuple(out)
-
-
 def transfer_full(n: int, S: int):
-    """The intergrid transfer V^H -> V^h over all half-grid points, as a dict
-    {(fine point, coarse point): Fraction}.  A fine dof takes its functional of the
-    coarse function on every coarse triangle whose closure contains the dof's point
-    (the fine edge, for an edge dof), averaged over those triangles; coarse and fine
-    points are ids Y (2n + 1) + X and Y_c (2S + 1) + X_c."""
+    """The transfer V^H -> V^h over all half-grid points, as a dict
+    {(fine point, coarse dof): Fraction}.  V^H is the conforming BFS space (C^1
+    bicubic Hermite functions, ``oracle.bfs``) on the S x S subdomain grid, coarse
+    dofs 4 (J (S + 1) + I) + a + 2 b for node (I, J) with x / y derivative orders a, b
+    (derivatives scaled by H); a fine dof takes its Morley functional (value or scaled
+    normal derivative at its point) of the coarse function, which is C^1, so every
+    coarse cell holding the point gives the same value; the lowest-indexed one is used."""
     if n % S != 0:
         raise ValueError("n must be a multiple of S")
     m = n // S
-    w = 2 * m
-    side, cside = 2 * n + 1, 2 * S + 1
+    side, cside = 2 * n + 1, S + 1
     out = {}
-    offs = {shape: _local_offsets(shape) for shape in ("lower", "upper")}
     for Y in range(side):
         for X in range(side):
-            kind = half_grid_kind(X, Y)
-            contrib = []
-            for I in _candidate_cells(X, w, S):
-                for J in _candidate_cells(Y, w, S):
-                    for shape, a, v in _row_pattern(m, X - w * I, Y - w * J, kind):
-                        ox, oy = offs[shape][a]
-                        contrib.append(((I, J, shape), (2 * J + oy) * cside + (2 * I + ox), v))
-            n_el = len({c[0] for c in contrib})
-            for _, c, v in contrib:
+            I, J = min(X // (2 * m), S - 1), min(Y // (2 * m), S - 1)
+            for a, b, val in _cell_values(m, X - 2 * m * I, Y - 2 * m * J, half_grid_kind(X, Y)):
+                c = 4 * ((J + (b >> 1)) * cside + I + (a >> 1)) + (a & 1) + 2 * (b & 1)
                 key = (Y * side + X, c)
-                out[key] = out.get(key, F(0)) + v / n_el
+                out[key] = out.get(key, F(0)) + val
     return out
+
+
+@lru_cache(maxsize=None)
+def _cell_values(m: int, tx: int, ty: int, kind: str):
+    """The fine functional `kind` of the 16 coarse bicubic Hermite basis functions of a
+    coarse cell at local position (tx, ty) / (2 m): tuples (a, b, value), nonzero only;
+    a / b = local x / y dof (node offset a >> 1, derivative order a & 1)."""
+    from .bfs import hermite_basis
+    C = hermite_basis()
+
+    def herm(s):
+        v = [sum(C[p][a] * s ** p for p in range(4)) for a in range(4)]
+        d = [sum(p * C[p][a] * s ** (p - 1) for p in range(1, 4)) for a in range(4)]
+        return v, d
+
+    vx, dx = herm(F(tx, 2 * m))
+    vy, dy = herm(F(ty, 2 * m))
+    res = []
+    for b in range(4):
+        for a in range(4):
+            u = vx[a] * vy[b]
+            ux = dx[a] * vy[b] / m              # fine h d/dx = (h / H) d/ds
+            uy = vx[a] * dy[b] / m
+            val = {"v": u, "dy": uy, "dx": ux, "dd": ux - uy}[kind]
+            if val != 0:
+                res.append((a, b, val))
+    return tuple(res)
 
 
 def prolongation(n: int, S: int) -> sp.csr_matrix:
     """P (n_dofs x n_H) between the clamped spaces: rows = fine interior half-grid points,
-    columns = coarse interior half-grid points, exact zeros dropped, each entry the
-    correctly rounded value of its rational."""
-    side, cside = 2 * n + 1, 2 * S + 1
+    columns = the four dofs of the interior coarse nodes (node-major), exact zeros
+    dropped, each entry the correctly rounded value of its rational."""
+    side, cside = 2 * n + 1, S + 1
     fine = -np.ones(side * side, dtype=np.int64)
     fine[dof_points(n)] = np.arange((2 * n - 1) ** 2)
-    coarse = -np.ones(cside * cside, dtype=np.int64)
-    coarse[dof_points(S)] = np.arange((2 * S - 1) ** 2)
+    coarse = -np.ones(4 * cside * cside, dtype=np.int64)
+    for J in range(1, S):
+        for I in range(1, S):
+            for c in range(4):
+                coarse[4 * (J * cside + I) + c] = 4 * ((J - 1) * (S - 1) + (I - 1)) + c
     rows, cols, vals = [], [], []
     for (f, c), v in transfer_full(n, S).items():
         if v == 0 or fine[f] < 0 or coarse[c] < 0:
@@ -267,7 +269,7 @@ def prolongation(n: int, S: int) -> sp.csr_matrix:
         rows.append(fine[f])
         cols.append(coarse[c])
         vals.append(float(v))
-    P = sp.csr_matrix((vals, (rows, cols)), shape=((2 * n - 1) ** 2, (2 * S - 1) ** 2))
+    P = sp.csr_matrix((vals, (rows, cols)), shape=((2 * n - 1) ** 2, 4 * (S - 1) ** 2))
     P.sum_duplicates()
     P.sort_indices()
     return P

@@ -410,8 +410,8 @@ int coarse_interp(const bpjd_mesh& m, int dim, const int32_t* S, CsrBuf& P) {
 // interior points numbered (Y-1)(2n-1) + (X-1): a subdomain's ascending dofs then
 // follow the half-grid rows and its band spans about two cell rows.
 // Element quantities are rationals (exact arithmetic below), scaled by h^-2
-// (stiffness) or h^2 (mass); the transfer matrix entries are rationals rounded
-// once to double.
+// (stiffness) or h^2 (mass); the coarse space is BFS on the subdomain grid and the
+// transfer matrix entries are rationals rounded once to double.
 // ---------------------------------------------------------------------------
 
 int64_t gcd64(int64_t a, int64_t b) {
@@ -579,89 +579,63 @@ int assemble_morley(const bpjd_mesh& m, CsrBuf& K, CsrBuf& M) {
   return BPJD_OK;
 }
 
-// Intergrid transfer V^H -> V^h for Morley (S coarse cells per side, mm = n / S
-// fine cells per coarse cell): a fine dof takes its functional of the coarse
-// function on every coarse triangle whose closure holds the dof's point (the
-// fine edge, for an edge dof), averaged over those triangles.  Boundary coarse
-// dofs (clamped) and exact zeros are dropped.
+void hermite_basis(Rat C[4][4]);  // cubic Hermite basis on [0, 1] (BFS section below)
+
+// Coarse space for Morley: the conforming BFS space (C^1 bicubic Hermite functions)
+// on the S x S subdomain grid, brought into V^h by the Morley interpolant: a fine
+// dof takes its value or scaled normal derivative of the coarse function, which is
+// C^1, so any coarse cell holding the point gives the same number (the lowest-
+// indexed one is used).  Coarse dofs are node-major 4 node + a + 2 b (derivatives
+// scaled by H); boundary coarse nodes (clamped) and exact zeros are dropped.
 int morley_transfer(const bpjd_mesh& m, int S, CsrBuf& P) {
   const int n = m.n[0];
-  if (S < 1 || n % S != 0) return BPJD_ERR_BAD_ARG;
+  if (S < 2 || n % S != 0) return BPJD_ERR_BAD_ARG;
   const int mm = n / S, w = 2 * mm;
-  const int inner = 2 * n - 1, cinner = 2 * S - 1;
+  const int inner = 2 * n - 1, mc = S - 1;
   const int64_t N = (int64_t)inner * inner;
-  if (cinner < 1) return BPJD_ERR_BAD_ARG;
-  const MorleyRef E[2] = {morley_reference(0), morley_reference(1)};
-  // per local position (xl, yl) in a coarse cell: the basis functionals of both triangles
-  // (valid where the triangle holds the point), already scaled to the fine functional
-  std::vector<std::array<Rat, 12>> table((size_t)(w + 1) * (w + 1));
-  for (int yl = 0; yl <= w; ++yl)
-    for (int xl = 0; xl <= w; ++xl) {
-      const int f = morley_kind(xl, yl);  // same parity as the fine point (w is even)
-      Rat xi(xl, w), eta(yl, w);
-      for (int s = 0; s < 2; ++s)
-        for (int a = 0; a < 6; ++a) {
-          Rat v(0);
-          for (int q = 0; q < 6; ++q) v = v + E[s].C[q][a] * morley_functional(f, kMono[q][0], kMono[q][1], xi, eta);
-          if (f != MV) v = v / Rat(mm);  // fine h d/dx = (h / H) coarse scaled derivative
-          table[(size_t)yl * (w + 1) + xl][s * 6 + a] = v;
-        }
+  Rat C[4][4];
+  hermite_basis(C);
+  // 1-D Hermite values (0..3) and derivatives (4..7) at local positions t / w, t = 0..w
+  std::vector<std::array<Rat, 8>> H1((size_t)w + 1);
+  for (int t = 0; t <= w; ++t) {
+    const Rat x(t, w);
+    for (int a = 0; a < 4; ++a) {
+      Rat v(0), d(0);
+      for (int p = 0; p < 4; ++p) {
+        v = v + C[p][a] * rpow(x, p);
+        if (p) d = d + Rat(p) * C[p][a] * rpow(x, p - 1);
+      }
+      H1[t][a] = v;
+      H1[t][4 + a] = d;
     }
+  }
   P.n_rows = (int32_t)N;
-  P.n_cols = (int32_t)((int64_t)cinner * cinner);
+  P.n_cols = 4 * mc * mc;
   P.row_ptr.assign(N + 1, 0);
-  auto cells = [&](int X, int* c) {
-    if (X % w == 0) {
-      int k = 0;
-      for (int q : {X / w - 1, X / w})
-        if (q >= 0 && q < S) c[k++] = q;
-      return k;
-    }
-    c[0] = X / w;
-    return 1;
-  };
-  std::vector<std::pair<int64_t, Rat>> row;
+  std::vector<std::pair<int64_t, double>> row;
   for (int Y = 1; Y < 2 * n; ++Y)
     for (int X = 1; X < 2 * n; ++X) {
-      int ci[2], cj[2];
-      const int ni = cells(X, ci), nj = cells(Y, cj);
-      int n_el = 0;
-      for (int a = 0; a < ni; ++a)
-        for (int b = 0; b < nj; ++b) {
-          const int xl = X - w * ci[a], yl = Y - w * cj[b];
-          n_el += (xl >= yl) + (xl <= yl);
-        }
+      const int f = morley_kind(X, Y);
+      const int I = std::min(X / w, S - 1), J = std::min(Y / w, S - 1);
+      const auto& hx = H1[X - w * I];
+      const auto& hy = H1[Y - w * J];
       row.clear();
-      for (int a = 0; a < ni; ++a)
-        for (int b = 0; b < nj; ++b) {
-          const int I = ci[a], J = cj[b];
-          const int xl = X - w * I, yl = Y - w * J;
-          for (int s = 0; s < 2; ++s) {
-            if ((s == 0 && xl < yl) || (s == 1 && xl > yl)) continue;
-            for (int e = 0; e < 6; ++e) {
-              const int Xc = 2 * I + E[s].off[e][0], Yc = 2 * J + E[s].off[e][1];
-              if (Xc <= 0 || Xc >= 2 * S || Yc <= 0 || Yc >= 2 * S) continue;
-              const int64_t c = (int64_t)(Yc - 1) * cinner + (Xc - 1);
-              const Rat v = table[(size_t)yl * (w + 1) + xl][s * 6 + e] / Rat(n_el);
-              bool found = false;
-              for (auto& r : row)
-                if (r.first == c) {
-                  r.second = r.second + v;
-                  found = true;
-                  break;
-                }
-              if (!found) row.push_back({c, v});
-            }
-          }
+      for (int b = 0; b < 4; ++b)
+        for (int a = 0; a < 4; ++a) {
+          const int In = I + (a >> 1), Jn = J + (b >> 1);
+          if (In <= 0 || In >= S || Jn <= 0 || Jn >= S) continue;
+          const Rat u = hx[a] * hy[b];
+          const Rat ux = hx[4 + a] * hy[b] / Rat(mm);  // fine h d/dx = (h / H) d/ds
+          const Rat uy = hx[a] * hy[4 + b] / Rat(mm);
+          const Rat v = (f == MV) ? u : (f == MDY) ? uy : (f == MDX) ? ux : ux - uy;
+          if (v.zero()) continue;
+          row.push_back({4 * ((int64_t)(Jn - 1) * mc + (In - 1)) + (a & 1) + 2 * (b & 1), v.to_double()});
         }
-      std::sort(row.begin(), row.end(), [](const std::pair<int64_t, Rat>& u, const std::pair<int64_t, Rat>& v) {
-        return u.first < v.first;
-      });
+      std::sort(row.begin(), row.end());
       const int64_t g = (int64_t)(Y - 1) * inner + (X - 1);
       for (auto& r : row) {
-        if (r.second.zero()) continue;
         P.col.push_back((int32_t)r.first);
-        P.val.push_back(r.second.to_double());
+        P.val.push_back(r.second);
       }
       P.row_ptr[g + 1] = (int64_t)P.col.size();
     }

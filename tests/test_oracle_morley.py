@@ -6,9 +6,10 @@ transfer and partition are pinned against what the mathematics fixes:
 * element matrices against an independent symbolic construction (sympy: basis
   solved in physical coordinates, exact integration over the triangle);
 * exactness on quadratics: the Morley space contains P2, so the assembled forms
-  of a global quadratic equal its exact integrals, and the transfer maps the
-  coarse interpolant of a quadratic to its fine interpolant exactly;
-* the averaging rule of the transfer against a symbolic brute force;
+  of a global quadratic equal its exact integrals;
+* the coarse space (BFS bicubics, Morley-interpolated): the transfer maps the BFS
+  dofs of any bicubic to its fine Morley functionals exactly, each row touches one
+  coarse cell, and the Galerkin eigenvalues bound the fine ones from above;
 * eigenvalue limits: the simply supported plate has the closed form
   pi^4 (i^2 + j^2)^2, and the first clamped eigenvalue of the unit square is
   1294.9339795917 (Bjorstad and Tjostheim, BIT 39 (1999), high-accuracy
@@ -124,76 +125,84 @@ def test_assembled_forms_exact_on_quadratics():
     assert q1 @ (Mf @ q2) == pytest.approx(b_exact, rel=1e-12)
 
 
-def test_transfer_reproduces_quadratics_exactly():
+def _bfs_coarse_dofs(coef, S, L):
+    """BFS node dofs (u, H u_x, H u_y, H^2 u_xy) of the bicubic q = sum coef[r][p] x^p y^r at
+    the (S+1)^2 coarse nodes, node-major."""
+    H = F(L) / S
+    out = []
+    for J in range(S + 1):
+        for I in range(S + 1):
+            x, y = I * H, J * H
+            u = ux = uy = uxy = F(0)
+            for r in range(4):
+                for p in range(4):
+                    c = coef[r][p]
+                    u += c * x ** p * y ** r
+                    if p:
+                        ux += c * p * x ** (p - 1) * y ** r
+                    if r:
+                        uy += c * r * x ** p * y ** (r - 1)
+                    if p and r:
+                        uxy += c * p * r * x ** (p - 1) * y ** (r - 1)
+            out += [u, H * ux, H * uy, H * H * uxy]
+    return out
+
+
+def _morley_functionals(coef, n, L):
+    """Fine Morley dofs (all half-grid points) of the bicubic q: values at vertices and the
+    scaled normal derivatives of the module docstring at edge midpoints."""
+    h = F(L) / n
+    out = []
+    for Y in range(2 * n + 1):
+        for X in range(2 * n + 1):
+            x, y = X * h / 2, Y * h / 2
+            u = ux = uy = F(0)
+            for r in range(4):
+                for p in range(4):
+                    c = coef[r][p]
+                    u += c * x ** p * y ** r
+                    if p:
+                        ux += c * p * x ** (p - 1) * y ** r
+                    if r:
+                        uy += c * r * x ** p * y ** (r - 1)
+            out.append({"v": u, "dy": h * uy, "dx": h * ux, "dd": h * (ux - uy)}[morley.half_grid_kind(X, Y)])
+    return out
+
+
+def test_transfer_reproduces_coarse_bicubics_exactly():
+    """P maps the BFS dofs of any bicubic (one piece of the coarse space) to its Morley
+    functionals on the fine grid; each row only touches the 16 dofs of one coarse cell that
+    holds the row's point (the coarse function is C^1, so any holding cell gives the same)."""
     rng = np.random.default_rng(5)
-    n, S, L = 12, 3, 1
+    n, S = 12, 3
+    m = n // S
     T = morley.transfer_full(n, S)
-    coef = [F(int(v), 3) for v in rng.integers(-9, 10, 6)]
-    fine = _quadratic_dofs(coef, n, L)
-    coarse = _quadratic_dofs(coef, S, L)
-    got = [F(0)] * len(fine)
+    for trial in range(2):
+        coef = [[F(int(v), 5) for v in rng.integers(-5, 6, 4)] for _ in range(4)]
+        fine = _morley_functionals(coef, n, 1)
+        coarse = _bfs_coarse_dofs(coef, S, 1)
+        got = [F(0)] * len(fine)
+        for (f, c), v in T.items():
+            got[f] += v * coarse[c]
+        assert got == fine
+    side = 2 * n + 1
     for (f, c), v in T.items():
-        got[f] += v * coarse[c]
-    assert got == fine
+        Y, X = divmod(f, side)
+        J, I = divmod(c // 4, S + 1)
+        # the coarse node (I, J) is a corner of a coarse cell whose closure holds the point
+        assert 2 * m * (I - 1) <= X <= 2 * m * (I + 1) and 2 * m * (J - 1) <= Y <= 2 * m * (J + 1)
 
 
-def test_transfer_against_symbolic_brute_force():
-    """n = 4 fine cells, S = 2 coarse cells: every coarse Morley basis function is built
-    symbolically on each coarse triangle; each fine dof averages its functional over the
-    coarse triangles whose closure holds the dof's point (barycentric test)."""
-    sympy = pytest.importorskip("sympy")
-    x, y = sympy.symbols("x y")
-    n, S = 4, 2
-    H, h = sympy.Rational(1, S), sympy.Rational(1, n)
-    T = morley.transfer_full(n, S)
-    # coarse triangles with their dofs as (half-grid point, functional)
-    tris = []
-    for J in range(S):
-        for I in range(S):
-            x0, y0 = I * H, J * H
-            for shape in ("lower", "upper"):
-                if shape == "lower":
-                    verts = [(x0, y0), (x0 + H, y0), (x0 + H, y0 + H)]
-                    pts = [(2 * I, 2 * J), (2 * I + 2, 2 * J), (2 * I + 2, 2 * J + 2),
-                           (2 * I + 1, 2 * J), (2 * I + 2, 2 * J + 1), (2 * I + 1, 2 * J + 1)]
-                else:
-                    verts = [(x0, y0), (x0 + H, y0 + H), (x0, y0 + H)]
-                    pts = [(2 * I, 2 * J), (2 * I + 2, 2 * J + 2), (2 * I, 2 * J + 2),
-                           (2 * I + 1, 2 * J + 1), (2 * I + 1, 2 * J + 2), (2 * I, 2 * J + 1)]
-
-                def functional(P, Xc, Yc, step):
-                    px, py = Xc * step / 2, Yc * step / 2
-                    kind = morley.half_grid_kind(Xc, Yc)
-                    if kind == "v":
-                        return P.subs({x: px, y: py})
-                    gx, gy = sympy.diff(P, x).subs({x: px, y: py}), sympy.diff(P, y).subs({x: px, y: py})
-                    return step * {"dy": gy, "dx": gx, "dd": gx - gy}[kind]
-
-                dofs = [(lambda P, X_=X_, Y_=Y_: functional(P, X_, Y_, H)) for (X_, Y_) in pts]
-                basis = _sym_basis(verts, dofs, x, y)
-                tris.append((verts, pts, basis, functional))
-    cside, side = 2 * S + 1, 2 * n + 1
-    for Y in range(side):
-        for X in range(side):
-            px, py = X * h / 2, Y * h / 2
-            holders = []
-            for verts, pts, basis, functional in tris:
-                (ax, ay), (bx, by), (cx, cy) = verts
-                det = (bx - ax) * (cy - ay) - (cx - ax) * (by - ay)
-                l1 = ((px - ax) * (cy - ay) - (cx - ax) * (py - ay)) / det
-                l2 = ((bx - ax) * (py - ay) - (px - ax) * (by - ay)) / det
-                if l1 >= 0 and l2 >= 0 and 1 - l1 - l2 >= 0:
-                    holders.append((pts, basis, functional))
-            want = {}
-            for pts, basis, functional in holders:
-                for (Xc, Yc), phi in zip(pts, basis):
-                    v = functional(phi, X, Y, h) / len(holders)
-                    key = Yc * cside + Xc
-                    want[key] = want.get(key, 0) + v
-            got = {c: v for (f, c), v in T.items() if f == Y * side + X}
-            for key in set(want) | set(got):
-                assert sympy.Rational(got.get(key, F(0)).numerator, got.get(key, F(0)).denominator) \
-                    == sympy.nsimplify(want.get(key, 0)), (X, Y, key)
+def test_coarse_pencil_bounds_fine_spectrum_from_above():
+    """range(P) is a subspace of the Morley space, so the Galerkin eigenvalues are upper bounds
+    of the fine ones (Courant-Fischer); the conforming coarse space keeps them close."""
+    n, S, k = 32, 4, 6
+    K, M = morley.assemble(n)
+    P = morley.prolongation(n, S)
+    lh = la.eigh((P.T @ K @ P).toarray(), (P.T @ M @ P).toarray(), eigvals_only=True)[:k]
+    w = la.eigh(K.toarray(), M.toarray(), eigvals_only=True)[:k]
+    assert np.all(lh >= w * (1 - 1e-12))
+    assert np.all(lh <= 1.1 * w)
 
 
 def _lowest(K, M, k):

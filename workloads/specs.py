@@ -56,9 +56,11 @@ class ProblemSpec:
 
     @property
     def n_coarse(self) -> int:
-        out = 4 if self.kind == "bfs_2d" else 1
+        """Coarse dimension: interior subdomain-grid nodes, four dofs each for the plate
+        elements (their coarse space is BFS on the subdomain grid)."""
+        out = 4 if self.kind in ("bfs_2d", "morley_2d") else 1
         for m in self.nsub:
-            out *= (2 * m - 1) if self.kind == "morley_2d" else (m - 1)
+            out *= m - 1
         return out
 
     def kappa_array(self) -> np.ndarray:
