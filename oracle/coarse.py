@@ -73,6 +73,17 @@ def prolongation(spec) -> sp.csr_matrix:
     if spec.kind == "bfs_2d":
         from . import bfs
         return bfs.prolongation(spec.n[0], spec.nsub[0])
+    if spec.kind == "p1_lshape":
+        # the square's nodal interpolation, rows and columns restricted to the interior
+        # nodes of the fine and coarse L-shapes (coarse functions vanish on its boundary)
+        from dataclasses import replace
+        from .fem import lshape_map
+        Psq = prolongation(replace(spec, kind="p1_2d"))
+        rows = np.flatnonzero(lshape_map(spec.n[0]) >= 0)
+        cols = np.flatnonzero(lshape_map(spec.nsub[0]) >= 0)
+        P = Psq[rows][:, cols].tocsr()
+        P.sort_indices()
+        return P
     n, S, dim = spec.n, spec.nsub, spec.dim
     ms = [n[d] // S[d] for d in range(dim)]
     if len(set(ms)) != 1:

@@ -132,6 +132,19 @@ def _interior_mask(n):
     return np.flatnonzero(mask.ravel())
 
 
+def lshape_map(n: int) -> np.ndarray:
+    """For the L-shaped domain of Section 6, Example 6.2 (the square grid of n x n cells
+    minus the quadrant x >= 0, y <= 0 of the centred square): position of every interior
+    node of the square (index (j-1)(n-1) + (i-1)) in the L-shape's dof list, -1 for the
+    nodes of the closed removed quadrant (i >= n/2, j <= n/2), which carry Dirichlet data.
+    The dofs keep the square's lexicographic order."""
+    i, j = np.meshgrid(np.arange(1, n), np.arange(1, n), indexing="xy")
+    keep = ~((i >= n // 2) & (j <= n // 2)).ravel()
+    out = -np.ones(keep.size, dtype=np.int64)
+    out[keep] = np.arange(int(keep.sum()))
+    return out
+
+
 def assemble(spec):
     """Stiffness K and mass M on interior dofs for a ``workloads.ProblemSpec``
     (only the mesh fields kind, n, length and kappa are used)."""
@@ -141,6 +154,15 @@ def assemble(spec):
     if spec.kind == "bfs_2d":
         from . import bfs
         return bfs.assemble(spec.n[0], spec.length[0])
+    if spec.kind == "p1_lshape":
+        # every triangle of the removed quadrant has its three vertices in the closed
+        # quadrant, i.e. on the Dirichlet boundary: the square's matrices restricted to
+        # the L-shape's interior nodes are the L-shape's own
+        n = spec.n[0]
+        Kf, Mf = p1_2d_full(n, n, *spec.length, np.ones((n, n, 2)))
+        Ks, Ms = _restrict_interior(Kf, Mf, _interior_mask(spec.n))
+        keep = np.flatnonzero(lshape_map(n) >= 0)
+        return _restrict_interior(Ks, Ms, keep)
     kap = spec.kappa_array()
     if spec.kind == "p1_2d":
         Kf, Mf = p1_2d_full(*spec.n, *spec.length, kap)

@@ -44,7 +44,30 @@ def axis_ranges(n: int, S: int, delta: int):
 
 
 def box_partition(spec):
-    """Returns (sub_ptr int64[N+1], sub_dofs int32[sum n_l], sub_color int32[N], n_colors)."""
+    """Returns (sub_ptr int64[N+1], sub_dofs int32[sum n_l], sub_color int32[N], n_colors).
+
+    For the L-shaped domain (p1_lshape) the partition J_H of the domain is the boxes of
+    the square whose cells lie in the domain (s_x < S/2 or s_y >= S/2); their dofs are
+    mapped to the L-shape's numbering (nodes of the removed quadrant dropped); ids follow
+    the remaining boxes in order, colours are kept."""
+    if spec.kind == "p1_lshape":
+        from dataclasses import replace
+        from .fem import lshape_map
+        ptr, dofs, col, nc = box_partition(replace(spec, kind="p1_2d"))
+        lm = lshape_map(spec.n[0])
+        S = spec.nsub[0]
+        nptr, ndofs, ncol = [0], [], []
+        for l in range(len(ptr) - 1):
+            sx, sy = l % S, l // S
+            if sx >= S // 2 and sy < S // 2:
+                continue
+            d = lm[dofs[ptr[l]:ptr[l + 1]]]
+            d = d[d >= 0]
+            ndofs.append(d)
+            nptr.append(nptr[-1] + len(d))
+            ncol.append(col[l])
+        return (np.asarray(nptr, dtype=np.int64), np.concatenate(ndofs).astype(np.int32),
+                np.asarray(ncol, dtype=np.int32), nc)
     n, S, dim, delta = spec.n, spec.nsub, spec.dim, spec.delta
     if spec.kind == "morley_2d":
         n, delta = tuple(2 * m for m in n), 2 * delta

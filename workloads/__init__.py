@@ -24,6 +24,9 @@ the experiments of Section 6:
   with Morley's nonconforming quadratic triangles on the same square grid as
   ``p1_2d`` (the paper itself uses BFS elements for this problem); no
   coefficient, square domain.
+* ``p1_lshape`` -- P1 (as ``p1_2d``) on the L-shaped domain of Section 6,
+  Example 6.2: the square [-L/2, L/2]^2 minus the quadrant [0, L/2) x (-L/2, 0],
+  i.e. the square's grid with the cells of that quadrant removed; no coefficient.
 * ``bfs_2d`` -- the clamped plate with the paper's conforming Bogner-Fox-Schmit
   element (bicubic Hermite: value, two first and the mixed derivative per node);
   no coefficient, square domain.
@@ -48,8 +51,10 @@ from .specs import (
     config_small_2d,
     config_small_3d,
     config_small_bfs,
+    config_small_lshape,
     config_small_morley,
     config_table1_col1,
+    config_table3_col1,
     config_table5,
     serving_stream,
 )
@@ -65,8 +70,10 @@ __all__ = [
     "config_small_2d",
     "config_small_3d",
     "config_small_bfs",
+    "config_small_lshape",
     "config_small_morley",
     "config_table1_col1",
+    "config_table3_col1",
     "config_table5",
     "serving_stream",
 ]

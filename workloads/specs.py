@@ -12,7 +12,7 @@ import numpy as np
 class ProblemSpec:
     """One eigenproblem, described by its mesh and decomposition parameters.
 
-    kind    : "p1_2d" | "p1_3d" | "q1_3d" | "morley_2d" | "bfs_2d"
+    kind    : "p1_2d" | "p1_3d" | "q1_3d" | "morley_2d" | "bfs_2d" | "p1_lshape"
     n       : elements per direction, (nx, ny) or (nx, ny, nz)
     length  : domain edge lengths; the domain is the box [0, Lx] x [0, Ly] (x [0, Lz])
     kappa   : per-element coefficient (layout in the package docstring), None = 1
@@ -49,6 +49,9 @@ class ProblemSpec:
         """Interior grid nodes (Dirichlet data removed); for morley_2d the interior
         points of the half-grid (2 nx - 1)(2 ny - 1), for bfs_2d four dofs per interior
         node (clamped data removed)."""
+        if self.kind == "p1_lshape":
+            n = self.n[0]
+            return (n - 1) ** 2 - (n // 2) ** 2
         out = 4 if self.kind == "bfs_2d" else 1
         for m in self.n:
             out *= (2 * m - 1) if self.kind == "morley_2d" else (m - 1)
@@ -58,6 +61,9 @@ class ProblemSpec:
     def n_coarse(self) -> int:
         """Coarse dimension: interior subdomain-grid nodes, four dofs each for the plate
         elements (their coarse space is BFS on the subdomain grid)."""
+        if self.kind == "p1_lshape":
+            S = self.nsub[0]
+            return (S - 1) ** 2 - (S // 2) ** 2
         out = 4 if self.kind in ("bfs_2d", "morley_2d") else 1
         for m in self.nsub:
             out *= m - 1
@@ -74,17 +80,19 @@ class ProblemSpec:
         return np.ones((nz, ny, nx), dtype=np.float64)
 
     def validate(self) -> None:
-        if self.kind not in ("p1_2d", "p1_3d", "q1_3d", "morley_2d", "bfs_2d"):
+        if self.kind not in ("p1_2d", "p1_3d", "q1_3d", "morley_2d", "bfs_2d", "p1_lshape"):
             raise ValueError(f"unknown kind {self.kind}")
-        want_dim = 2 if self.kind in ("p1_2d", "morley_2d", "bfs_2d") else 3
+        want_dim = 2 if self.kind in ("p1_2d", "morley_2d", "bfs_2d", "p1_lshape") else 3
         if self.dim != want_dim or len(self.length) != want_dim or len(self.nsub) != want_dim:
             raise ValueError("dimension mismatch")
         for m, s in zip(self.n, self.nsub):
             if m % s != 0:
                 raise ValueError("element count must be a multiple of the subdomain count")
-        if self.kind in ("morley_2d", "bfs_2d") and (self.kappa is not None or self.n[0] != self.n[1]
-                                                     or self.length[0] != self.length[1]):
+        if self.kind in ("morley_2d", "bfs_2d", "p1_lshape") and (
+                self.kappa is not None or self.n[0] != self.n[1] or self.length[0] != self.length[1]):
             raise ValueError(f"{self.kind}: square domain and square cells, no coefficient")
+        if self.kind == "p1_lshape" and (self.n[0] % 2 or self.nsub[0] % 2):
+            raise ValueError("p1_lshape: even cell and subdomain counts (the removed quadrant is a union of both)")
         if self.k >= self.n_coarse:
             raise ValueError("k must be smaller than the coarse space dimension")
         ms = {m // s for m, s in zip(self.n, self.nsub)}
@@ -223,6 +231,22 @@ def config_table5(n: int) -> ProblemSpec:
     s = 20, 8 x 8 x 8 subdomains (H = pi/8), overlap H/2."""
     return ProblemSpec("q1_3d", (n, n, n), (np.pi, np.pi, np.pi), (8, 8, 8), max(1, n // 16), 20,
                        name=f"table5_n{n}")
+
+
+def config_table3_col1() -> ProblemSpec:
+    """Section 6, Example 6.2 / Table 3 first column: -Laplace u = lambda u on the L-shaped
+    domain (-pi, pi)^2 minus [0, pi) x (-pi, 0], P1 on the 128 x 128 grid of the square
+    (squares split SW->NE) restricted to the domain (12033 dofs), s = 20.  The subdomain
+    grid is the paper's H = pi/8 (16 x 16 boxes over the square, those in the removed
+    quadrant dropped) with delta / H = 1/4 (2 layers); the printed eigenvalues do not
+    depend on the decomposition."""
+    return ProblemSpec("p1_lshape", (128, 128), (2 * np.pi, 2 * np.pi), (16, 16), 2, 20, name="table3_col1")
+
+
+def config_small_lshape(n: int = 32, ns: int = 8, delta: int = 1, k: int = 4) -> ProblemSpec:
+    """A small L-shaped case (P1), for parity with the oracle."""
+    return ProblemSpec("p1_lshape", (n, n), (2 * np.pi, 2 * np.pi), (ns, ns), delta, k,
+                       name=f"small_lshape_{n}_{ns}_d{delta}_k{k}")
 
 
 @dataclass
