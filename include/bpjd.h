@@ -268,7 +268,12 @@ int bpjd_profile_read(bpjd_handle* h, double* ms, int64_t* count, int64_t* kerne
  *            sides, kappa NULL): four dofs per interior node, node-major
  *            4 node + c for (u, h du/dx, h du/dy, h^2 d^2u/dxdy); P is the
  *            nested interpolation from BFS on the subdomain grid; subdomains
- *            take the box rule on nodes with all four dofs.
+ *            take the box rule on nodes with all four dofs;
+ *   kind 5 = P1 as kind 0 on the L-shaped domain of Example 6.2: the square
+ *            [0, L]^2 of an n x n grid (n and nsub even, equal sides, kappa
+ *            NULL) minus the quadrant of its centre (x >= L/2, y <= L/2); dofs
+ *            are the square's interior nodes outside the closed quadrant, in
+ *            the square's order; subdomains are the boxes of the domain.
  * kappa: per-element coefficient, layout [ny][nx][2] (kind 0, entry 0 = the
  * triangle below the diagonal) or [nz][ny][nx] (kinds 1, 2); NULL = 1.
  * Subdomains: nsub boxes per axis grown by delta element layers; the initial

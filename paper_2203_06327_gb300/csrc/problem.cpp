@@ -812,19 +812,98 @@ int bfs_transfer(const bpjd_mesh& m, int S, CsrBuf& P) {
   return BPJD_OK;
 }
 
+// ---------------------------------------------------------------------------
+// L-shaped domain of Section 6, Example 6.2: the square grid of kind 0 (n x n
+// cells, kappa = 1) minus the quadrant x >= 0, y <= 0 of the centred square.
+// Every triangle of that quadrant has its three vertices in the closed quadrant,
+// which carries Dirichlet data, so the L-shape's matrices, coarse interpolation
+// and subdomain dofs are the square's restricted to the L-shape's interior nodes
+// (the square's lexicographic order is kept); the boxes of the domain partition
+// are those of the square whose cells lie in the domain.
+// ---------------------------------------------------------------------------
+
+// position of every interior node of the square grid (index (j-1)(n-1) + (i-1)) in
+// the L-shape's dof list, -1 for the nodes of the closed removed quadrant
+std::vector<int64_t> lshape_map(int n) {
+  std::vector<int64_t> out((size_t)(n - 1) * (n - 1), -1);
+  int64_t next = 0;
+  for (int j = 1; j < n; ++j)
+    for (int i = 1; i < n; ++i)
+      if (!(i >= n / 2 && j <= n / 2)) out[(size_t)(j - 1) * (n - 1) + (i - 1)] = next++;
+  return out;
+}
+
+void restrict_csr(const CsrBuf& A, const std::vector<int64_t>& rmap, const std::vector<int64_t>& cmap,
+                  CsrBuf& out) {
+  int64_t nr = 0, nc = 0;
+  for (int64_t v : rmap) nr += (v >= 0);
+  for (int64_t v : cmap) nc += (v >= 0);
+  out.n_rows = (int32_t)nr;
+  out.n_cols = (int32_t)nc;
+  out.row_ptr.assign(nr + 1, 0);
+  out.col.clear();
+  out.val.clear();
+  for (int64_t r = 0; r < A.n_rows; ++r) {
+    if (rmap[r] < 0) continue;
+    for (int64_t e = A.row_ptr[r]; e < A.row_ptr[r + 1]; ++e) {
+      const int64_t c = cmap[A.col[e]];
+      if (c < 0) continue;
+      out.col.push_back((int32_t)c);
+      out.val.push_back(A.val[e]);
+    }
+    out.row_ptr[rmap[r] + 1] = (int64_t)out.col.size();
+  }
+}
+
+int build_lshape(const bpjd_mesh& m, ProblemImpl& P) {
+  const int n = m.n[0], S = m.nsub[0];
+  bpjd_mesh sq = m;
+  sq.kind = 0;
+  sq.kappa = nullptr;
+  CsrBuf K, M, Pc, P0;
+  int rc = assemble_p1_2d(sq, K, M);
+  if (rc == BPJD_OK) rc = coarse_interp(sq, 2, m.nsub, Pc);
+  int32_t S0[3] = {S << m.tau, S << m.tau, 1};
+  if (rc == BPJD_OK && m.tau > 0) rc = coarse_interp(sq, 2, S0, P0);
+  if (rc != BPJD_OK) return rc;
+  const std::vector<int64_t> fm = lshape_map(n), cm = lshape_map(S);
+  restrict_csr(K, fm, fm, P.K);
+  restrict_csr(M, fm, fm, P.M);
+  restrict_csr(Pc, fm, cm, P.P);
+  if (m.tau > 0)
+    restrict_csr(P0, fm, lshape_map(S0[0]), P.P0);
+  else
+    P.P0 = P.P;
+  ProblemImpl box;
+  box_partition(sq, 2, box);
+  P.sub_ptr.assign(1, 0);
+  for (int l = 0; l + 1 < (int)box.sub_ptr.size(); ++l) {
+    const int sx = l % S, sy = l / S;
+    if (sx >= S / 2 && sy < S / 2) continue;  // box of the removed quadrant
+    for (int64_t e = box.sub_ptr[l]; e < box.sub_ptr[l + 1]; ++e) {
+      const int64_t d = fm[box.sub_dofs[e]];
+      if (d >= 0) P.sub_dofs.push_back((int32_t)d);
+    }
+    P.sub_ptr.push_back((int64_t)P.sub_dofs.size());
+    P.sub_color.push_back(box.sub_color[l]);
+  }
+  return BPJD_OK;
+}
+
 }  // namespace
 
 extern "C" int bpjd_problem_create(const bpjd_mesh* mesh, bpjd_problem** out) {
   if (!mesh || !out) return BPJD_ERR_BAD_ARG;
   *out = nullptr;
   const bpjd_mesh& m = *mesh;
-  int dim = (m.kind == 0 || m.kind == 3 || m.kind == 4) ? 2 : 3;
-  if (m.kind < 0 || m.kind > 4) return BPJD_ERR_BAD_ARG;
+  int dim = (m.kind == 0 || m.kind == 3 || m.kind == 4 || m.kind == 5) ? 2 : 3;
+  if (m.kind < 0 || m.kind > 5) return BPJD_ERR_BAD_ARG;
   for (int d = 0; d < dim; ++d) {
     if (m.n[d] < 2 || m.nsub[d] < 1 || m.n[d] % m.nsub[d] != 0 || !(m.length[d] > 0)) return BPJD_ERR_BAD_ARG;
   }
   if (m.delta < 0 || m.tau < 0 || m.tau > 6) return BPJD_ERR_BAD_ARG;
-  if (m.kind == 3 || m.kind == 4) {
+  if (m.kind == 5 && (m.n[0] % 2 || m.nsub[0] % 2)) return BPJD_ERR_BAD_ARG;
+  if (m.kind == 3 || m.kind == 4 || m.kind == 5) {
     if (m.n[0] != m.n[1] || m.nsub[0] != m.nsub[1] || m.length[0] != m.length[1]) return BPJD_ERR_BAD_ARG;
     if (m.kappa) return BPJD_ERR_UNSUPPORTED;
     if ((m.n[0] / m.nsub[0]) % (1 << m.tau) != 0) return BPJD_ERR_BAD_ARG;
@@ -838,7 +917,9 @@ extern "C" int bpjd_problem_create(const bpjd_mesh* mesh, bpjd_problem** out) {
   if (!P) return BPJD_ERR_OOM;
   int rc;
   try {
-    if (m.kind == 4) {
+    if (m.kind == 5) {
+      rc = build_lshape(m, *P);
+    } else if (m.kind == 4) {
       rc = assemble_bfs(m, P->K, P->M);
       if (rc == BPJD_OK) rc = bfs_transfer(m, m.nsub[0], P->P);
       if (rc == BPJD_OK) {

@@ -17,7 +17,8 @@ import scipy.linalg as la
 
 from oracle import bpjd as obpjd
 from oracle import metrics, problem as oproblem
-from workloads import config_c1, config_small_2d, config_small_3d, config_small_bfs, config_small_morley, ProblemSpec
+from workloads import (config_c1, config_small_2d, config_small_3d, config_small_bfs, config_small_lshape,
+                       config_small_morley, ProblemSpec)
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -149,7 +150,8 @@ def test_c1_solve_matches_oracle(c1_oracle, subspace, precision):
                                   config_small_2d(nx=40, ny=40, nsx=5, nsy=5, delta=1, k=1, kappa="random"),
                                   config_small_morley(n=32, ns=8, delta=1, k=8),
                                   config_small_morley(n=32, ns=4, delta=2, k=6, tau=1),
-                                  config_small_bfs(), config_small_bfs(n=32, ns=8, delta=1, k=8)],
+                                  config_small_bfs(), config_small_bfs(n=32, ns=8, delta=1, k=8),
+                                  config_small_lshape()],
                          ids=lambda s: s.name)
 def test_other_problems_solve(spec):
     op = oproblem.build(spec)
