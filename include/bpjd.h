@@ -273,7 +273,10 @@ int bpjd_profile_read(bpjd_handle* h, double* ms, int64_t* count, int64_t* kerne
  *            [0, L]^2 of an n x n grid (n and nsub even, equal sides, kappa
  *            NULL) minus the quadrant of its centre (x >= L/2, y <= L/2); dofs
  *            are the square's interior nodes outside the closed quadrant, in
- *            the square's order; subdomains are the boxes of the domain.
+ *            the square's order; subdomains are the boxes of the domain;
+ *   kind 6 = trilinear bricks as kind 2 on the L-shaped prism of Example 6.4:
+ *            the box minus the prism x >= Lx/2, y >= Ly/2 (x / y cell and
+ *            subdomain counts even, kappa NULL), restricted in the same way.
  * kappa: per-element coefficient, layout [ny][nx][2] (kind 0, entry 0 = the
  * triangle below the diagonal) or [nz][ny][nx] (kinds 1, 2); NULL = 1.
  * Subdomains: nsub boxes per axis grown by delta element layers; the initial

@@ -73,6 +73,15 @@ def prolongation(spec) -> sp.csr_matrix:
     if spec.kind == "bfs_2d":
         from . import bfs
         return bfs.prolongation(spec.n[0], spec.nsub[0])
+    if spec.kind == "q1_lshape":
+        from dataclasses import replace
+        from .fem import lshape3_map
+        Pbox = prolongation(replace(spec, kind="q1_3d"))
+        rows = np.flatnonzero(lshape3_map(*spec.n) >= 0)
+        cols = np.flatnonzero(lshape3_map(*spec.nsub) >= 0)
+        P = Pbox[rows][:, cols].tocsr()
+        P.sort_indices()
+        return P
     if spec.kind == "p1_lshape":
         # the square's nodal interpolation, rows and columns restricted to the interior
         # nodes of the fine and coarse L-shapes (coarse functions vanish on its boundary)

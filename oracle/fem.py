@@ -145,6 +145,18 @@ def lshape_map(n: int) -> np.ndarray:
     return out
 
 
+def lshape3_map(nx: int, ny: int, nz: int) -> np.ndarray:
+    """For the L-shaped prism of Section 6, Example 6.4 (the box grid of nx x ny x nz cells
+    minus the prism x >= Lx/2, y >= Ly/2): position of every interior node of the box
+    (index ((l-1)(ny-1) + (j-1))(nx-1) + (i-1)) in the domain's dof list, -1 for the nodes
+    of the closed removed prism (i >= nx/2, j >= ny/2), which carry Dirichlet data."""
+    l, j, i = np.meshgrid(np.arange(1, nz), np.arange(1, ny), np.arange(1, nx), indexing="ij")
+    keep = ~((i >= nx // 2) & (j >= ny // 2)).ravel()
+    out = -np.ones(keep.size, dtype=np.int64)
+    out[keep] = np.arange(int(keep.sum()))
+    return out
+
+
 def assemble(spec):
     """Stiffness K and mass M on interior dofs for a ``workloads.ProblemSpec``
     (only the mesh fields kind, n, length and kappa are used)."""
@@ -154,6 +166,11 @@ def assemble(spec):
     if spec.kind == "bfs_2d":
         from . import bfs
         return bfs.assemble(spec.n[0], spec.length[0])
+    if spec.kind == "q1_lshape":
+        # as for the 2-D L-shape: the cells of the removed prism touch only Dirichlet nodes
+        K, M = q1_3d_interior(*spec.n, *spec.length)
+        keep = np.flatnonzero(lshape3_map(*spec.n) >= 0)
+        return _restrict_interior(K, M, keep)
     if spec.kind == "p1_lshape":
         # every triangle of the removed quadrant has its three vertices in the closed
         # quadrant, i.e. on the Dirichlet boundary: the square's matrices restricted to

@@ -50,6 +50,24 @@ def box_partition(spec):
     the square whose cells lie in the domain (s_x < S/2 or s_y >= S/2); their dofs are
     mapped to the L-shape's numbering (nodes of the removed quadrant dropped); ids follow
     the remaining boxes in order, colours are kept."""
+    if spec.kind == "q1_lshape":
+        from dataclasses import replace
+        from .fem import lshape3_map
+        ptr, dofs, col, nc = box_partition(replace(spec, kind="q1_3d"))
+        lm = lshape3_map(*spec.n)
+        Sx, Sy, _ = spec.nsub
+        nptr, ndofs, ncol = [0], [], []
+        for l in range(len(ptr) - 1):
+            sx, sy = l % Sx, (l // Sx) % Sy
+            if sx >= Sx // 2 and sy >= Sy // 2:
+                continue                               # box of the removed prism
+            d = lm[dofs[ptr[l]:ptr[l + 1]]]
+            d = d[d >= 0]
+            ndofs.append(d)
+            nptr.append(nptr[-1] + len(d))
+            ncol.append(col[l])
+        return (np.asarray(nptr, dtype=np.int64), np.concatenate(ndofs).astype(np.int32),
+                np.asarray(ncol, dtype=np.int32), nc)
     if spec.kind == "p1_lshape":
         from dataclasses import replace
         from .fem import lshape_map

@@ -209,7 +209,7 @@ class PartitionArrays:
 
 
 # ---- problem generation -----------------------------------------------------
-_KINDS = {"p1_2d": 0, "p1_3d": 1, "q1_3d": 2, "morley_2d": 3, "bfs_2d": 4, "p1_lshape": 5}
+_KINDS = {"p1_2d": 0, "p1_3d": 1, "q1_3d": 2, "morley_2d": 3, "bfs_2d": 4, "p1_lshape": 5, "q1_lshape": 6}
 
 
 @dataclass

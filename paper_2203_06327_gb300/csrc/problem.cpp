@@ -890,6 +890,55 @@ int build_lshape(const bpjd_mesh& m, ProblemImpl& P) {
   return BPJD_OK;
 }
 
+// L-shaped prism of Section 6, Example 6.4: the box grid of kind 2 (trilinear
+// bricks) minus the prism x >= Lx/2, y >= Ly/2; restricted like the 2-D L-shape.
+std::vector<int64_t> lshape3_map(int nx, int ny, int nz) {
+  std::vector<int64_t> out((size_t)(nx - 1) * (ny - 1) * (nz - 1), -1);
+  int64_t next = 0;
+  for (int l = 1; l < nz; ++l)
+    for (int j = 1; j < ny; ++j)
+      for (int i = 1; i < nx; ++i)
+        if (!(i >= nx / 2 && j >= ny / 2)) out[((size_t)(l - 1) * (ny - 1) + (j - 1)) * (nx - 1) + (i - 1)] = next++;
+  return out;
+}
+
+int build_q1_lshape(const bpjd_mesh& m, ProblemImpl& P) {
+  bpjd_mesh bx = m;
+  bx.kind = 2;
+  bx.kappa = nullptr;
+  CsrBuf K, M, Pc, P0;
+  int rc = assemble_q1_3d(bx, K, M);
+  if (rc == BPJD_OK) rc = coarse_interp(bx, 3, m.nsub, Pc);
+  int32_t S0[3];
+  for (int d = 0; d < 3; ++d) S0[d] = m.nsub[d] << m.tau;
+  if (rc == BPJD_OK && m.tau > 0) rc = coarse_interp(bx, 3, S0, P0);
+  if (rc != BPJD_OK) return rc;
+  const std::vector<int64_t> fm = lshape3_map(m.n[0], m.n[1], m.n[2]);
+  const std::vector<int64_t> cm = lshape3_map(m.nsub[0], m.nsub[1], m.nsub[2]);
+  restrict_csr(K, fm, fm, P.K);
+  restrict_csr(M, fm, fm, P.M);
+  restrict_csr(Pc, fm, cm, P.P);
+  if (m.tau > 0)
+    restrict_csr(P0, fm, lshape3_map(S0[0], S0[1], S0[2]), P.P0);
+  else
+    P.P0 = P.P;
+  ProblemImpl box;
+  box_partition(bx, 3, box);
+  const int Sx = m.nsub[0], Sy = m.nsub[1];
+  P.sub_ptr.assign(1, 0);
+  for (int l = 0; l + 1 < (int)box.sub_ptr.size(); ++l) {
+    const int sx = l % Sx, sy = (l / Sx) % Sy;
+    if (sx >= Sx / 2 && sy >= Sy / 2) continue;  // box of the removed prism
+    for (int64_t e = box.sub_ptr[l]; e < box.sub_ptr[l + 1]; ++e) {
+      const int64_t d = fm[box.sub_dofs[e]];
+      if (d >= 0) P.sub_dofs.push_back((int32_t)d);
+    }
+    P.sub_ptr.push_back((int64_t)P.sub_dofs.size());
+    P.sub_color.push_back(box.sub_color[l]);
+  }
+  return BPJD_OK;
+}
+
 }  // namespace
 
 extern "C" int bpjd_problem_create(const bpjd_mesh* mesh, bpjd_problem** out) {
@@ -897,12 +946,16 @@ extern "C" int bpjd_problem_create(const bpjd_mesh* mesh, bpjd_problem** out) {
   *out = nullptr;
   const bpjd_mesh& m = *mesh;
   int dim = (m.kind == 0 || m.kind == 3 || m.kind == 4 || m.kind == 5) ? 2 : 3;
-  if (m.kind < 0 || m.kind > 5) return BPJD_ERR_BAD_ARG;
+  if (m.kind < 0 || m.kind > 6) return BPJD_ERR_BAD_ARG;
   for (int d = 0; d < dim; ++d) {
     if (m.n[d] < 2 || m.nsub[d] < 1 || m.n[d] % m.nsub[d] != 0 || !(m.length[d] > 0)) return BPJD_ERR_BAD_ARG;
   }
   if (m.delta < 0 || m.tau < 0 || m.tau > 6) return BPJD_ERR_BAD_ARG;
   if (m.kind == 5 && (m.n[0] % 2 || m.nsub[0] % 2)) return BPJD_ERR_BAD_ARG;
+  if (m.kind == 6) {
+    if (m.n[0] % 2 || m.n[1] % 2 || m.nsub[0] % 2 || m.nsub[1] % 2) return BPJD_ERR_BAD_ARG;
+    if (m.kappa) return BPJD_ERR_UNSUPPORTED;
+  }
   if (m.kind == 3 || m.kind == 4 || m.kind == 5) {
     if (m.n[0] != m.n[1] || m.nsub[0] != m.nsub[1] || m.length[0] != m.length[1]) return BPJD_ERR_BAD_ARG;
     if (m.kappa) return BPJD_ERR_UNSUPPORTED;
@@ -917,7 +970,9 @@ extern "C" int bpjd_problem_create(const bpjd_mesh* mesh, bpjd_problem** out) {
   if (!P) return BPJD_ERR_OOM;
   int rc;
   try {
-    if (m.kind == 5) {
+    if (m.kind == 6) {
+      rc = build_q1_lshape(m, *P);
+    } else if (m.kind == 5) {
       rc = build_lshape(m, *P);
     } else if (m.kind == 4) {
       rc = assemble_bfs(m, P->K, P->M);

@@ -13,7 +13,7 @@ import pytest
 from conftest import ROOT
 from oracle import problem as oracle_problem
 from workloads import (config_c1, config_small_2d, config_small_3d, config_small_bfs, config_small_lshape,
-                       config_small_morley, config_table3_col1, ProblemSpec)
+                       config_small_morley, config_table3_col1, config_table7_col1, ProblemSpec)
 
 B = pytest.importorskip("paper_2203_06327_gb300.binding")
 
@@ -43,7 +43,7 @@ def _cmp_csr(lib_csr, ora):
                                   config_small_morley(), config_small_morley(n=24, ns=4, delta=2, k=4, tau=1),
                                   config_small_morley(n=32, ns=8, delta=1, k=8),
                                   config_small_bfs(), config_small_bfs(n=24, ns=4, delta=2, k=4, tau=1),
-                                  config_small_lshape(), config_table3_col1()],
+                                  config_small_lshape(), config_table3_col1(), config_table7_col1()],
                          ids=lambda s: s.name + f"_tau{s.tau}")
 def test_generators_match_oracle(spec):
     lp = B.problem_from_spec(spec)

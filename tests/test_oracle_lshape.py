@@ -1,7 +1,7 @@
-"""Pins of the oracle's L-shaped domain (Section 6, Example 6.2).
+"""Pins of the oracle's L-shaped domains (Section 6, Examples 6.2 and 6.4).
 
-* Table 3, first column: the 20 printed eigenvalues (8 decimals) of the oracle's
-  assembly, by a shift-invert Lanczos solve (scipy eigsh);
+* Table 3 and Table 7, first columns: the 20 printed eigenvalues (8 decimals) of the
+  oracle's assembly, by a shift-invert Lanczos solve (scipy eigsh);
 * the restriction of the square's matrices equals an assembly over the L-shape's own
   triangles (every triangle of the removed quadrant has all its vertices on the
   Dirichlet boundary);
@@ -19,7 +19,9 @@ import scipy.sparse.linalg as sla
 
 from conftest import golden
 from oracle import bpjd, fem, metrics, partition, problem
-from workloads import config_small_lshape, config_table3_col1
+from dataclasses import replace
+
+from workloads import config_small_lshape, config_table3_col1, config_table7_col1
 
 
 def test_table3_first_column():
@@ -102,3 +104,26 @@ def test_bpjd_on_lshape_matches_dense_eigensolve():
     for a, b in metrics.clusters(w[:k + 1]):
         if b <= k:
             assert metrics.gap_b(res.X[:, a:b], V[:, a:b], pb.M) <= 1e-6
+
+
+def test_table7_first_column():
+    spec = config_table7_col1()
+    K, M = fem.assemble(spec)
+    assert K.shape[0] == 10575
+    w = np.sort(sla.eigsh(K.tocsc(), 20, M.tocsc(), sigma=0.0, which="LM", tol=1e-14)[0])
+    want = np.array([r[0] for r in golden("table7_col1.txt")])
+    np.testing.assert_allclose(w, want, rtol=0, atol=6e-9)
+
+
+def test_prism_coarse_space_is_nested_and_partition_has_the_papers_n():
+    spec = config_table7_col1()
+    small = replace(spec, n=(16, 16, 8), nsub=(8, 8, 4))
+    pb = problem.build(small)
+    Kc, Mc = fem.assemble(replace(small, n=(8, 8, 4)))
+    np.testing.assert_allclose((pb.P.T @ pb.K @ pb.P).toarray(), Kc.toarray(), rtol=0, atol=1e-12)
+    np.testing.assert_allclose((pb.P.T @ pb.M @ pb.P).toarray(), Mc.toarray(), rtol=0, atol=1e-13)
+    ptr, dofs, col, nc = partition.box_partition(spec)
+    assert len(ptr) - 1 == 1536                      # the paper's N
+    covered = np.zeros(spec.n_dofs, dtype=bool)
+    covered[dofs] = True
+    assert covered.all()

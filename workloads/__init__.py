@@ -27,6 +27,9 @@ the experiments of Section 6:
 * ``p1_lshape`` -- P1 (as ``p1_2d``) on the L-shaped domain of Section 6,
   Example 6.2: the square [-L/2, L/2]^2 minus the quadrant [0, L/2) x (-L/2, 0],
   i.e. the square's grid with the cells of that quadrant removed; no coefficient.
+* ``q1_lshape`` -- trilinear elements (as ``q1_3d``) on the L-shaped prism of
+  Section 6, Example 6.4: the box [0, Lx] x [0, Ly] x [0, Lz] minus
+  [Lx/2, Lx) x [Ly/2, Ly) x (0, Lz); no coefficient.
 * ``bfs_2d`` -- the clamped plate with the paper's conforming Bogner-Fox-Schmit
   element (bicubic Hermite: value, two first and the mixed derivative per node);
   no coefficient, square domain.
@@ -56,6 +59,7 @@ from .specs import (
     config_table1_col1,
     config_table3_col1,
     config_table5,
+    config_table7_col1,
     serving_stream,
 )
 
@@ -75,5 +79,6 @@ __all__ = [
     "config_table1_col1",
     "config_table3_col1",
     "config_table5",
+    "config_table7_col1",
     "serving_stream",
 ]

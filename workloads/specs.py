@@ -12,7 +12,7 @@ import numpy as np
 class ProblemSpec:
     """One eigenproblem, described by its mesh and decomposition parameters.
 
-    kind    : "p1_2d" | "p1_3d" | "q1_3d" | "morley_2d" | "bfs_2d" | "p1_lshape"
+    kind    : "p1_2d" | "p1_3d" | "q1_3d" | "morley_2d" | "bfs_2d" | "p1_lshape" | "q1_lshape"
     n       : elements per direction, (nx, ny) or (nx, ny, nz)
     length  : domain edge lengths; the domain is the box [0, Lx] x [0, Ly] (x [0, Lz])
     kappa   : per-element coefficient (layout in the package docstring), None = 1
@@ -52,6 +52,9 @@ class ProblemSpec:
         if self.kind == "p1_lshape":
             n = self.n[0]
             return (n - 1) ** 2 - (n // 2) ** 2
+        if self.kind == "q1_lshape":
+            nx, ny, nz = self.n
+            return (nx - 1) * (ny - 1) * (nz - 1) - (nx // 2) * (ny // 2) * (nz - 1)
         out = 4 if self.kind == "bfs_2d" else 1
         for m in self.n:
             out *= (2 * m - 1) if self.kind == "morley_2d" else (m - 1)
@@ -64,6 +67,9 @@ class ProblemSpec:
         if self.kind == "p1_lshape":
             S = self.nsub[0]
             return (S - 1) ** 2 - (S // 2) ** 2
+        if self.kind == "q1_lshape":
+            sx, sy, sz = self.nsub
+            return (sx - 1) * (sy - 1) * (sz - 1) - (sx // 2) * (sy // 2) * (sz - 1)
         out = 4 if self.kind in ("bfs_2d", "morley_2d") else 1
         for m in self.nsub:
             out *= m - 1
@@ -80,7 +86,7 @@ class ProblemSpec:
         return np.ones((nz, ny, nx), dtype=np.float64)
 
     def validate(self) -> None:
-        if self.kind not in ("p1_2d", "p1_3d", "q1_3d", "morley_2d", "bfs_2d", "p1_lshape"):
+        if self.kind not in ("p1_2d", "p1_3d", "q1_3d", "morley_2d", "bfs_2d", "p1_lshape", "q1_lshape"):
             raise ValueError(f"unknown kind {self.kind}")
         want_dim = 2 if self.kind in ("p1_2d", "morley_2d", "bfs_2d", "p1_lshape") else 3
         if self.dim != want_dim or len(self.length) != want_dim or len(self.nsub) != want_dim:
@@ -93,6 +99,9 @@ class ProblemSpec:
             raise ValueError(f"{self.kind}: square domain and square cells, no coefficient")
         if self.kind == "p1_lshape" and (self.n[0] % 2 or self.nsub[0] % 2):
             raise ValueError("p1_lshape: even cell and subdomain counts (the removed quadrant is a union of both)")
+        if self.kind == "q1_lshape" and (self.n[0] % 2 or self.n[1] % 2 or self.nsub[0] % 2 or self.nsub[1] % 2
+                                         or self.kappa is not None):
+            raise ValueError("q1_lshape: even x / y cell and subdomain counts, no coefficient")
         if self.k >= self.n_coarse:
             raise ValueError("k must be smaller than the coarse space dimension")
         ms = {m // s for m, s in zip(self.n, self.nsub)}
@@ -241,6 +250,15 @@ def config_table3_col1() -> ProblemSpec:
     quadrant dropped) with delta / H = 1/4 (2 layers); the printed eigenvalues do not
     depend on the decomposition."""
     return ProblemSpec("p1_lshape", (128, 128), (2 * np.pi, 2 * np.pi), (16, 16), 2, 20, name="table3_col1")
+
+
+def config_table7_col1() -> ProblemSpec:
+    """Section 6, Example 6.4 / Table 7 first column: -Laplace u = lambda u on the prism
+    (0, 2 pi) x (0, 2 pi) x (0, pi) minus [pi, 2 pi) x [pi, 2 pi) x (0, pi), trilinear
+    elements on 32 x 32 x 16 cubes of side pi/16 (10575 dofs), s = 20; subdomains are the
+    paper's N = 1536 cubes of side H = pi/8 with delta / H = 1/2 (one layer)."""
+    return ProblemSpec("q1_lshape", (32, 32, 16), (2 * np.pi, 2 * np.pi, np.pi), (16, 16, 8), 1, 20,
+                       name="table7_col1")
 
 
 def config_small_lshape(n: int = 32, ns: int = 8, delta: int = 1, k: int = 4) -> ProblemSpec:
