@@ -93,38 +93,37 @@ def _global_1d(n: int, L: float, interior: bool):
     return mats
 
 
-def _node_major(m: int):
-    """Permutation from Kronecker order ((2 j + b) 2m + 2 i + a) to node-major order
-    4 (j m + i) + a + 2 b, for m nodes per axis."""
-    perm = np.empty(4 * m * m, dtype=np.int64)
-    for j in range(m):
-        for i in range(m):
-            for b in range(2):
-                for a in range(2):
-                    perm[4 * (j * m + i) + a + 2 * b] = (2 * j + b) * 2 * m + 2 * i + a
-    return perm
-
-
 def assemble(n: int, L: float = 1.0, interior: bool = True):
     """K, M of the clamped plate (interior=True) or over all nodes (interior=False),
-    node-major CSR with the pattern of dof pairs sharing a cell."""
+    node-major CSR with the pattern of dof pairs sharing a cell.  Entry
+    ((i, j, a, b), (i', j', a', b')) = M0y K2x + 2 (K1y K1x) + K2y M0x (the Kronecker
+    products of the 1-D matrices, y factor first), evaluated on that pattern only."""
     M0, K1, K2 = _global_1d(n, L, interior)
     m = (n - 1) if interior else (n + 1)
-    Kk = np.kron(M0, K2) + 2.0 * np.kron(K1, K1) + np.kron(K2, M0)
-    Mk = np.kron(M0, M0)
-    perm = _node_major(m)
-    K = Kk[np.ix_(perm, perm)]
-    Mm = Mk[np.ix_(perm, perm)]
-    # pattern: dof pairs whose nodes share a cell (node offsets at most 1 on each axis)
-    node = np.arange(4 * m * m) // 4
-    nx, ny = node % m, node // m
-    share = (np.abs(nx[:, None] - nx[None, :]) <= 1) & (np.abs(ny[:, None] - ny[None, :]) <= 1)
-    rows, cols = np.nonzero(share)
-    Kc = sp.csr_matrix((K[rows, cols], (rows, cols)), shape=K.shape)
-    Mc = sp.csr_matrix((Mm[rows, cols], (rows, cols)), shape=K.shape)
-    for A in (Kc, Mc):
+    dof = np.arange(4 * m * m)
+    node, c = dof // 4, dof % 4
+    ni, nj = node % m, node // m
+    rows, cols = [], []
+    for dj in (-1, 0, 1):
+        for di in (-1, 0, 1):
+            ok = (ni + di >= 0) & (ni + di < m) & (nj + dj >= 0) & (nj + dj < m)
+            r = dof[ok]
+            q = (nj[ok] + dj) * m + (ni[ok] + di)
+            for c2 in range(4):
+                rows.append(r)
+                cols.append(4 * q + c2)
+    rows = np.concatenate(rows)
+    cols = np.concatenate(cols)
+    rx, ry = 2 * ni[rows] + (c[rows] & 1), 2 * nj[rows] + (c[rows] >> 1)
+    cn, cc = cols // 4, cols % 4
+    cx, cy = 2 * (cn % m) + (cc & 1), 2 * (cn // m) + (cc >> 1)
+    kv = (M0[ry, cy] * K2[rx, cx] + 2.0 * (K1[ry, cy] * K1[rx, cx])) + K2[ry, cy] * M0[rx, cx]
+    mv = M0[ry, cy] * M0[rx, cx]
+    K = sp.csr_matrix((kv, (rows, cols)), shape=(4 * m * m, 4 * m * m))
+    M = sp.csr_matrix((mv, (rows, cols)), shape=(4 * m * m, 4 * m * m))
+    for A in (K, M):
         A.sort_indices()
-    return Kc, Mc
+    return K, M
 
 
 def _transfer_1d(n: int, S: int):
