@@ -1,7 +1,7 @@
 // Host-side problem generation: finite-element assembly of the model problems
 // (Section 2.1, Section 2.2, Section 6), overlapping box subdomains with their
 // colouring (Section 2.3, Assumption 2) and the nodal interpolation V^H -> V^h
-// (for Morley elements, the averaging intergrid transfer).
+// (for Morley elements, the Morley interpolant of the BFS coarse space).
 //
 // Degrees of freedom are interior grid nodes, lexicographic with x fastest;
 // Dirichlet data are imposed by omitting boundary nodes.  The sparsity pattern
