@@ -44,23 +44,30 @@ def _solve(spec, precision, **kw):
     return pb, lam, X, st
 
 
-@pytest.mark.parametrize("precision", [B.FP64, B.MIXED], ids=["fp64", "mixed"])
-def test_table1_first_column_on_gpu(precision):
-    """Example 6.1: P1 on (0, pi)^2, 128 x 128 squares, the 19 printed eigenvalues."""
-    spec = config_table1_col1()
+@pytest.mark.parametrize("precision,col", [(B.FP64, 0), (B.MIXED, 0), (B.MIXED, 1)],
+                         ids=["fp64-128", "mixed-128", "mixed-256"])
+def test_table1_columns_on_gpu(precision, col):
+    """Example 6.1: P1 on (0, pi)^2, 128 x 128 and 256 x 256 squares (subdomain grid 8 x 8 and
+    16 x 16, delta / H = 1/4 as in the paper), the 19 printed eigenvalues."""
+    from dataclasses import replace
+    n = 128 << col
+    spec = replace(config_table1_col1(), n=(n, n), nsub=(8 << col, 8 << col))
     pb, lam, X, st = _solve(spec, precision)
-    want = np.array([r[0] for r in golden("table1_col1.txt")])
+    want = np.array([r[col] for r in golden("table1.txt")])
     np.testing.assert_allclose(lam, want, rtol=0, atol=6e-9)
     assert metrics.rel_residuals(_csr(pb.K), _csr(pb.M), lam, X).max() <= 1e-8
 
 
-@pytest.mark.parametrize("precision", [B.FP64, B.MIXED], ids=["fp64", "mixed"])
-def test_table3_first_column_on_gpu(precision):
-    """Example 6.2: P1 on the L-shaped domain (-pi, pi)^2 minus [0, pi) x (-pi, 0], the 20
-    printed eigenvalues (re-entrant corner: singular eigenfunctions)."""
-    spec = config_table3_col1()
+@pytest.mark.parametrize("precision,col", [(B.FP64, 0), (B.MIXED, 0), (B.MIXED, 1)],
+                         ids=["fp64-128", "mixed-128", "mixed-256"])
+def test_table3_columns_on_gpu(precision, col):
+    """Example 6.2: P1 on the L-shaped domain (-pi, pi)^2 minus [0, pi) x (-pi, 0], 128 x 128
+    and 256 x 256 grids of the square (delta / H = 1/4 as in the paper), the 20 printed
+    eigenvalues (re-entrant corner: singular eigenfunctions)."""
+    from dataclasses import replace
+    spec = replace(config_table3_col1(), n=(128 << col, 128 << col), delta=2 << col)
     pb, lam, X, st = _solve(spec, precision)
-    want = np.array([r[0] for r in golden("table3_col1.txt")])
+    want = np.array([r[col] for r in golden("table3.txt")])
     np.testing.assert_allclose(lam, want, rtol=0, atol=6e-9)
     assert metrics.rel_residuals(_csr(pb.K), _csr(pb.M), lam, X).max() <= 1e-8
 
@@ -71,7 +78,7 @@ def test_table7_first_column_on_gpu(precision):
     subdomains, the 20 printed eigenvalues (a triple at 6.05809793)."""
     spec = config_table7_col1()
     pb, lam, X, st = _solve(spec, precision)
-    want = np.array([r[0] for r in golden("table7_col1.txt")])
+    want = np.array([r[0] for r in golden("table7.txt")])
     np.testing.assert_allclose(lam, want, rtol=0, atol=6e-9)
     assert metrics.rel_residuals(_csr(pb.K), _csr(pb.M), lam, X).max() <= 1e-8
 

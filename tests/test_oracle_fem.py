@@ -19,12 +19,14 @@ def _lowest(K, M, k):
     return np.sort(w)
 
 
-def test_table1_first_column():
-    """Table 1 (Example 6.1), 16129 dofs: all 19 printed eigenvalues to 8 decimals."""
-    spec = config_table1_col1()
+@pytest.mark.parametrize("col,n", [(0, 128), (1, 256)])
+def test_table1_columns(col, n):
+    """Table 1 (Example 6.1), 16129 and 65025 dofs: all 19 printed eigenvalues to 8 decimals."""
+    from dataclasses import replace
+    spec = replace(config_table1_col1(), n=(n, n))
     K, M = fem.assemble(spec)
-    assert K.shape == (16129, 16129)
-    want = np.array([r[0] for r in golden("table1_col1.txt")])
+    assert K.shape == ((n - 1) ** 2, (n - 1) ** 2)
+    want = np.array([r[col] for r in golden("table1.txt")])
     got = _lowest(K, M, 19)
     np.testing.assert_allclose(got, want, rtol=0, atol=6e-9)
 
