@@ -106,7 +106,7 @@ def test_full_size_against_eigsh(which):
         spec, precision, tol = config_c4(), B.MIXED_LOCAL, 1e-7
     pb, lam, X, st = _solve(spec, precision, tol=tol, max_iter=2000)
     K, M = _csr(pb.K), _csr(pb.M)
-    w, V = sla.eigsh(K.tocsc(), spec.k + 4, M.tocsc(), sigma=0.0, which="LM", tol=1e-13)
+    w, V = sla.eigsh(K.tocsc(), spec.k + 4, M.tocsc(), v0=np.random.default_rng(0).standard_normal(K.shape[0]), sigma=0.0, which="LM", tol=1e-13)
     order = np.argsort(w)
     w, V = w[order], V[:, order]
     np.testing.assert_allclose(lam, w[: spec.k], rtol=1e-9)
