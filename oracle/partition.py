@@ -114,3 +114,61 @@ def box_partition(spec):
         colors.append(sum((s[d] % 2) << d for d in range(dim)))
     return (np.asarray(ptr, dtype=np.int64), np.concatenate(dofs).astype(np.int32),
             np.asarray(colors, dtype=np.int32), 1 << dim)
+
+
+def triangle_partition(n: int, S: int, layers: int):
+    """The paper's partition J_H of Section 6, Example 6.1: each of the S x S coarse squares of
+    the uniform n x n grid (n a multiple of S) split along its SW->NE diagonal into two
+    coarse triangles (N = 2 S^2), each enlarged by `layers` rings of fine triangles (Section
+    2.3: whole fine elements added layer by layer; a ring = every fine triangle sharing a
+    vertex with the region); the dofs of a subdomain are the interior nodes all of whose fine
+    triangles lie in the enlarged region (zero trace on its boundary), ascending.
+
+    Subdomain id = 2 (s_x + S s_y) + t (t = 0 below the diagonal); colour = 2 ((s_x mod 2)
+    + 2 (s_y mod 2)) + t.  Returns (sub_ptr, sub_dofs, sub_color, n_colors = 8)."""
+    m = n // S
+    # fine triangle (i, j, t) of square (i, j): t = 0 (SW, SE, NE), t = 1 (SW, NE, NW)
+    vert = {0: ((0, 0), (1, 0), (1, 1)), 1: ((0, 0), (1, 1), (0, 1))}
+    ii, jj = np.meshgrid(np.arange(n), np.arange(n), indexing="xy")      # [j, i]
+    ptr, dofs, colors = [0], [], []
+    for sy in range(S):
+        for sx in range(S):
+            for T in (0, 1):
+                li, lj = ii - sx * m, jj - sy * m
+                inside = (li >= 0) & (li < m) & (lj >= 0) & (lj < m)
+                reg = np.zeros((2, n, n), dtype=bool)                     # [t, j, i]
+                if T == 0:
+                    reg[0] = inside & (li >= lj)
+                    reg[1] = inside & (li > lj)
+                else:
+                    reg[0] = inside & (li < lj)
+                    reg[1] = inside & (li <= lj)
+                for _ in range(layers):
+                    node = np.zeros((n + 1, n + 1), dtype=bool)           # [j, i]
+                    for t in (0, 1):
+                        for (di, dj) in vert[t]:
+                            node[dj:dj + n, di:di + n] |= reg[t]
+                    for t in (0, 1):
+                        touch = np.zeros((n, n), dtype=bool)
+                        for (di, dj) in vert[t]:
+                            touch |= node[dj:dj + n, di:di + n]
+                        reg[t] |= touch
+                # a node is a dof when every fine triangle around it is in the region
+                ok = np.ones((n + 1, n + 1), dtype=bool)
+                cover = np.zeros((n + 1, n + 1), dtype=np.int32)
+                for t in (0, 1):
+                    for (di, dj) in vert[t]:
+                        pad = np.zeros((n + 1, n + 1), dtype=bool)
+                        pad[dj:dj + n, di:di + n] = reg[t]
+                        cnt = np.zeros((n + 1, n + 1), dtype=np.int32)
+                        cnt[dj:dj + n, di:di + n] = 1
+                        cover += pad.astype(np.int32)
+                        ok &= ~((cnt == 1) & ~pad)
+                jn, in_ = np.nonzero(ok & (cover > 0))
+                keep = (in_ > 0) & (in_ < n) & (jn > 0) & (jn < n)
+                local = np.sort((jn[keep] - 1) * (n - 1) + (in_[keep] - 1))
+                dofs.append(local)
+                ptr.append(ptr[-1] + len(local))
+                colors.append(2 * ((sx % 2) + 2 * (sy % 2)) + T)
+    return (np.asarray(ptr, dtype=np.int64), np.concatenate(dofs).astype(np.int32),
+            np.asarray(colors, dtype=np.int32), 8)

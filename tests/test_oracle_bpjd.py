@@ -18,7 +18,7 @@ import scipy.sparse as sp
 import scipy.sparse.linalg as sla
 
 from oracle import bpjd, metrics, problem
-from workloads import ProblemSpec, config_c1, config_small_2d, config_small_3d
+from workloads import ProblemSpec, config_c1, config_small_2d, config_small_3d, config_table1_col1
 
 
 @pytest.fixture(scope="module")
@@ -160,3 +160,39 @@ def test_local_indefinite_detected():
     S = pb.setup()
     with pytest.raises(bpjd.LocalIndefinite):
         bpjd.solve(S, tol=1e-8, max_iter=2)
+
+
+def test_paper_triangle_partition_is_a_coloured_cover():
+    """Example 6.1's partition J_H: 512 coarse triangles of the 16 x 16 grid of (0, pi)^2, each
+    enlarged by rings of fine triangles; every dof is covered and same-coloured subdomains are
+    disjoint (Assumption 2)."""
+    from oracle import partition
+    for layers in (2, 3):
+        ptr, dofs, col, nc = partition.triangle_partition(128, 16, layers)
+        assert len(ptr) - 1 == 512 and nc == 8
+        covered = np.zeros(127 * 127, dtype=bool)
+        covered[dofs] = True
+        assert covered.all()
+        for c in range(nc):
+            members = np.concatenate([dofs[ptr[l]:ptr[l + 1]] for l in range(512) if col[l] == c])
+            assert len(np.unique(members)) == len(members)
+
+
+def test_paper_iteration_count_with_its_partition():
+    """Section 6, Table 1, first column: 21 iterations to sum |lambda^{k+1} - lambda^k| < 1e-10
+    with N = 512 triangles and delta / H = 1/4.  delta = H/4 = sqrt(2) pi / 64 is 2.83 fine steps
+    (h = pi / 128); with the enlargement by 3 and by 2 rings of fine triangles, the W^{k+1} =
+    U^{k-1} + U^k + span{t} space (Remark 3.1) and the paper's stop rule, the oracle's counts
+    bracket the printed 21."""
+    from oracle import partition
+    spec = replace(config_table1_col1(), nsub=(16, 16), delta=2)      # coarse P1 on the 16 x 16 grid
+    pb = problem.build(spec)
+    its = {}
+    for layers in (2, 3):
+        ptr, dofs, col, nc = partition.triangle_partition(128, 16, layers)
+        S = bpjd.setup(pb.K, pb.M, pb.P, ptr, dofs, 19)
+        res = bpjd.solve(S, tol=1e-10, stop="dlambda", subspace="3s", max_iter=60)
+        assert res.converged
+        its[layers] = res.iterations
+    assert its[3] <= 21 <= its[2], its
+    assert its[2] - its[3] <= 3, its
