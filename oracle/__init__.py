@@ -19,6 +19,12 @@ Modules
   metrics    gap between subspaces (Definition 2.1), residuals, clusters
 
 Every function cites the passage it follows.  Functions without an external
-pin are marked "parity unpinned" in their docstrings; at present every
-function is pinned by a test in ``tests/test_oracle_*.py``.
+pin are marked "parity unpinned" in their docstrings.  Pins by module:
+fem, coarse, partition -> tests/test_oracle_fem.py,
+tests/test_oracle_partition_coarse.py, tests/test_oracle_lshape.py (paper
+tables, closed forms, brute force); morley -> tests/test_oracle_morley.py;
+bfs -> tests/test_oracle_bfs.py; bpjd -> tests/test_oracle_bpjd.py (dense
+eigensolves, textbook reductions, paper iteration counts); metrics ->
+tests/test_oracle_metrics.py (hand-computed angles and residuals, principal
+angles of scipy on the Cholesky-transformed spans, hand-made clusters).
 """

@@ -9,6 +9,13 @@ Oracle (test infrastructure only).
 * ``clusters``: groups of adjacent eigenvalues whose relative spacing is below
   a threshold; eigenvectors are compared cluster by cluster because a basis of
   a (nearly) multiple eigenspace is not unique.
+
+Pinned by tests/test_oracle_metrics.py: lines at a known angle (Euclidean and in
+a diagonal b-product), planes with known principal angles, a general SPD
+b-product reduced to Euclidean principal angles (scipy) of the Cholesky-
+transformed spans, unequal dimensions (the max of Definition 2.1), residuals of
+exact and perturbed eigenpairs worked out by hand, and a hand-made spectrum
+with a pair and a triple.
 """
 
 from __future__ import annotations
