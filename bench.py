@@ -264,7 +264,8 @@ def run_reference(a):
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * spec.k / value, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": spec.name, "n_dofs": spec.n_dofs, "k": spec.k},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle, extrapolated",
+                             "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -419,7 +420,7 @@ def run_ours(a):
     if bytes_per is not None and dom_cnt:
         ach = bytes_per / (dom_ms / dom_cnt / 1e3) / 1e9
         # DRAM bytes (read + write) per application measured by ncu for this kernel
-        # version on this workload (profiles/local_solves_c2.md); None elsewhere
+        # version on this workload; None elsewhere
         traffic = LOCAL_TRAFFIC.get((spec.name, a.precision)) if dom == "local" else None
         roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                 "peak_kind": peak_kind, "algorithmic_bytes_per_launch": bytes_per, "traffic": traffic,
@@ -460,7 +461,7 @@ def run_ours(a):
 
     if rank == 0 and not a.no_cpu_baseline:
         v, sample, info = oracle_sample(spec, int(round(statistics.mean(iters))), n_local=_oracle_locals(spec, 96))
-        cpu = {"value": v, "unit": UNIT, "cores": _blas_threads(), "kind": "oracle", "sample": sample}
+        cpu = {"value": v, "unit": UNIT, "cores": _blas_threads(), "kind": "oracle, extrapolated", "sample": sample}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,

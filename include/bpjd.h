@@ -206,8 +206,9 @@ int bpjd_block_gram(bpjd_handle* h, int32_t nu, const double* const* U, int32_t 
  *         pointers (n x k row-major FP64 each), V likewise with nv; out: device
  *         (nu k) x (nv k) row-major FP64; stream: cudaStream_t or NULL.
  * symmetric, size limits and arithmetic as for bpjd_block_gram.
- * Errors: BAD_ARG; TOO_LARGE if the partial sums of this (n, k, nu, nv) do not
- * fit the static array; CUDA.
+ * Errors: BAD_ARG; TOO_LARGE if n > 2^31 - 1 (rows are indexed with 32-bit
+ * integers) or if the partial sums of this (n, k, nu, nv) do not fit the static
+ * array (both checked on the host before any launch); CUDA.
  * The first call on a device looks up the device address of the static array
  * (cudaGetSymbolAddress, with that device current); make that first call before
  * any stream capture.  All calls share the one array: calls that overlap on

@@ -125,7 +125,15 @@ def triangle_partition(n: int, S: int, layers: int):
     triangles lie in the enlarged region (zero trace on its boundary), ascending.
 
     Subdomain id = 2 (s_x + S s_y) + t (t = 0 below the diagonal); colour = 2 ((s_x mod 2)
-    + 2 (s_y mod 2)) + t.  Returns (sub_ptr, sub_dofs, sub_color, n_colors = 8)."""
+    + 2 (s_y mod 2)) + t.  Two triangles of one colour lie at least one coarse square (n / S fine
+    cells) apart, and each grows by `layers` cells towards the other, so same-coloured
+    subdomains stay disjoint (Assumption 2) only while 2 layers < n / S; wider enlargements
+    are rejected.  Returns (sub_ptr, sub_dofs, sub_color, n_colors = 8)."""
+    if S < 1 or n % S != 0:
+        raise ValueError(f"the fine grid ({n}) must refine the coarse grid ({S}) evenly")
+    if not 0 <= 2 * layers < n // S:
+        raise ValueError(f"{layers} rings on coarse squares of {n // S} cells would overlap same-coloured "
+                         "subdomains (Assumption 2 needs 2 layers < n / S)")
     m = n // S
     # fine triangle (i, j, t) of square (i, j): t = 0 (SW, SE, NE), t = 1 (SW, NE, NW)
     vert = {0: ((0, 0), (1, 0), (1, 1)), 1: ((0, 0), (1, 1), (0, 1))}

@@ -8,6 +8,7 @@
 
 #include <cuda_runtime.h>
 
+#include <cstdint>
 #include <mutex>
 
 #include "bpjd_internal.h"
@@ -42,6 +43,8 @@ int scratch_on_current_device(double** out) {
 extern "C" int bpjd_block_gram_noalloc(int64_t n, int32_t k, int32_t nu, const double* const* U, int32_t nv,
                                        const double* const* V, int32_t symmetric, double* out, void* stream) {
   if (n < 1 || k < 1 || !U || !V || !out || nu < 1 || nv < 1 || nu > 6 || nv > 6) return BPJD_ERR_BAD_ARG;
+  // the kernels index rows with 32-bit integers: larger blocks are refused before any launch
+  if (n > (int64_t)INT32_MAX) return BPJD_ERR_TOO_LARGE;
   if (nu * k > 64 || nv * k > 64 || (symmetric && nu != nv)) return BPJD_ERR_BAD_ARG;
   for (int b = 0; b < nu; ++b)
     if (!U[b]) return BPJD_ERR_BAD_ARG;

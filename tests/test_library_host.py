@@ -144,3 +144,21 @@ def test_setup_rejects_unknown_precision_and_subspace():
             B.Solver(pb.K, pb.M, pb.P, pb.P0, pb.part, 6, **kw)
         assert e.value.code == B.ERR_UNSUPPORTED
     assert (B.FP64, B.MIXED, B.MIXED_LOCAL) == (0, 1, 2)
+
+
+def test_noalloc_gram_refuses_oversize_rows_before_any_launch():
+    """The allocation-free block inner product indexes rows with 32-bit integers, so
+    n > 2^31 - 1 is refused on the host (no device work: the fake pointers below are
+    never dereferenced), as are the other size limits."""
+    fn = B.lib.bpjd_block_gram_noalloc
+    fn.argtypes = [C.c_int64, C.c_int32, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p,
+                   C.c_void_p]
+    fn.restype = C.c_int
+    fake = (C.c_void_p * 2)(0x1000, 0x2000)
+    out = C.c_void_p(0x3000)
+    assert fn(1 << 31, 4, 2, fake, 2, fake, 1, out, None) == B.ERR_TOO_LARGE
+    assert fn((1 << 40) + 5, 1, 1, fake, 1, fake, 0, out, None) == B.ERR_TOO_LARGE
+    # bad arguments come back as BAD_ARG, also before any launch
+    assert fn(0, 4, 2, fake, 2, fake, 1, out, None) == B.ERR_BAD_ARG
+    assert fn(100, 40, 2, fake, 2, fake, 1, out, None) == B.ERR_BAD_ARG      # 80 columns > 64
+    assert fn(100, 4, 2, fake, 1, fake, 1, out, None) == B.ERR_BAD_ARG       # symmetric needs nu == nv

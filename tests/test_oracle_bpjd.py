@@ -176,6 +176,11 @@ def test_paper_triangle_partition_is_a_coloured_cover():
         for c in range(nc):
             members = np.concatenate([dofs[ptr[l]:ptr[l + 1]] for l in range(512) if col[l] == c])
             assert len(np.unique(members)) == len(members)
+    # enlargements that would make same-coloured subdomains overlap are rejected
+    with pytest.raises(ValueError):
+        partition.triangle_partition(128, 16, 4)
+    with pytest.raises(ValueError):
+        partition.triangle_partition(100, 16, 1)
 
 
 def test_paper_iteration_count_with_its_partition():
@@ -194,5 +199,8 @@ def test_paper_iteration_count_with_its_partition():
         res = bpjd.solve(S, tol=1e-10, stop="dlambda", subspace="3s", max_iter=60)
         assert res.converged
         its[layers] = res.iterations
+    # against the paper: the two enlargements bracket the printed count
     assert its[3] <= 21 <= its[2], its
     assert its[2] - its[3] <= 3, its
+    # against drift of the configuration or the arithmetic: the oracle's own counts
+    assert its == {2: 22, 3: 20}, its

@@ -54,8 +54,13 @@ def test_noalloc_gram_matches_block_gram_twice():
 
 
 def test_noalloc_gram_rejects_oversize():
+    """Four n x k blocks with n = 2^20, k = 16 (64 columns, the full tile set) need more
+    partial sums than the static array holds.  The blocks are real (one 128 MiB tensor
+    behind all four pointers) and so is the output, so that a broken size guard makes
+    the assertion fail instead of reading past an allocation."""
     n, k = 1 << 20, 16
-    dummy = torch.zeros(1, dtype=torch.float64, device="cuda")
-    out = torch.zeros(1, dtype=torch.float64, device="cuda")
-    U = [dummy] * 4          # 64 columns, full tile set: more partial sums than the static array holds
+    block = torch.zeros((n, k), dtype=torch.float64, device="cuda")
+    out = torch.zeros((4 * k, 4 * k), dtype=torch.float64, device="cuda")
+    U = [block] * 4
     assert _noalloc(n, k, U, U, out, False) == B.ERR_TOO_LARGE
+    del block
