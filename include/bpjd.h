@@ -50,6 +50,10 @@ extern "C" {
                                         (FP64 above 168, mixed above 240 on a 227 KB SM) */
 #define BPJD_ERR_TOO_LARGE       -12  /* request exceeds a fixed capacity (allocation-free entry point)
                                          or, alone, the memory budget of a server */
+#define BPJD_ERR_TIMEOUT         -13  /* a bounded device-side wait ran out: a local-solve kernel
+                                         waited bpjd_set_wait_limit() attempts for a bulk copy
+                                         into shared memory, gave up and returned (its results
+                                         are invalid; the handle and the context stay usable) */
 
 /* ---- option values ----------------------------------------------------- */
 #define BPJD_FP64        0  /* every step in FP64 */
@@ -150,7 +154,8 @@ int bpjd_setup(const bpjd_csr* A, const bpjd_csr* M, const bpjd_csr* P, const bp
  *           host memory if eigvecs_on_device == 0, device memory otherwise.
  * st      : statistics, or NULL.
  * May be called repeatedly; every call restarts from the initial guess.
- * Errors: LOCAL_INDEFINITE, BREAKDOWN, NOCONV (results still written), CUDA.
+ * Errors: LOCAL_INDEFINITE, BREAKDOWN, NOCONV (results still written), TIMEOUT,
+ * CUDA.
  */
 int bpjd_solve(bpjd_handle* h, double* eigvals, double* eigvecs, int32_t eigvecs_on_device,
                bpjd_stats* st);
@@ -173,7 +178,8 @@ int bpjd_spmm(bpjd_handle* h, const double* X, double* YA, double* YM, int32_t n
 
 /* z_i = (B_i)^{-1} rho_i (Eq. (3.3)) for the k columns of the device n x k
  * array rho, with shifts lam (device, k doubles).  Z: device n x k.  Uses the
- * handle's precision.  Returns LOCAL_INDEFINITE if a local pivot is <= 0. */
+ * handle's precision.  Returns LOCAL_INDEFINITE if a local pivot is <= 0,
+ * TIMEOUT if a bounded wait of the local solves ran out. */
 int bpjd_apply_preconditioner(bpjd_handle* h, const double* rho, const double* lam, double* Z);
 
 /* Block inner products out = U^T V in double-word (FP32-pair, FP64-class)
@@ -218,6 +224,15 @@ int bpjd_block_gram(bpjd_handle* h, int32_t nu, const double* const* U, int32_t 
  */
 int bpjd_block_gram_noalloc(int64_t n, int32_t k, int32_t nu, const double* const* U, int32_t nv,
                             const double* const* V, int32_t symmetric, double* out, void* stream);
+
+/* Attempts of every bounded device-side wait of the handle's kernels (the local
+ * solves spin on an mbarrier until a bulk copy into shared memory completes;
+ * each attempt is one mbarrier.try_wait, which may suspend briefly) before the
+ * kernel gives up, flags BPJD_ERR_TIMEOUT for the call and returns after its
+ * copies in flight have landed.  Default 1 << 22 (far beyond any normal copy);
+ * 0 gives up at once, which exercises the timeout path without a hang.
+ * Errors: BAD_ARG (NULL handle or attempts < 0). */
+int bpjd_set_wait_limit(bpjd_handle* h, int32_t attempts);
 
 /* Ritz values of every Rayleigh-Ritz step of the last solve (row j = step j,
  * row 0 = initial guess), host array of cap x k doubles; returns rows written. */

@@ -32,6 +32,7 @@ ERR_OOM = -9
 ERR_CUDA = -10
 ERR_UNSUPPORTED = -11
 ERR_TOO_LARGE = -12
+ERR_TIMEOUT = -13
 
 FP64, MIXED, MIXED_LOCAL = 0, 1, 2
 W_2K, W_3K = 0, 1
@@ -43,7 +44,7 @@ EXPORTED = [
     "bpjd_problem_create", "bpjd_problem_free", "bpjd_profile", "bpjd_profile_read",
     "bpjd_layout", "bpjd_block_gram", "bpjd_block_gram_noalloc",
     "bpjd_server_default_opts", "bpjd_server_create", "bpjd_server_submit", "bpjd_server_poll",
-    "bpjd_server_free",
+    "bpjd_server_free", "bpjd_set_wait_limit",
 ]
 PENDING = 1
 PROF_NAMES = ["local", "coarse", "prolong", "spmm", "inner", "combine", "rr", "resid"]
@@ -118,6 +119,7 @@ def _load():
                                      C.c_void_p]
     lib.bpjd_server_free.argtypes = [C.c_void_p]
     lib.bpjd_server_free.restype = None
+    lib.bpjd_set_wait_limit.argtypes = [C.c_void_p, C.c_int32]
     lib.bpjd_profile.argtypes = [C.c_void_p, C.c_int32]
     lib.bpjd_profile_read.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
     return lib
@@ -349,6 +351,10 @@ class Solver:
         if rows < 0:
             raise BpjdError(rows, "bpjd_history")
         return buf[:rows].copy()
+
+    def set_wait_limit(self, attempts: int):
+        """Attempts of every bounded device-side wait before a kernel gives up (TIMEOUT)."""
+        _check(lib.bpjd_set_wait_limit(self._h, int(attempts)), "bpjd_set_wait_limit")
 
     def profile(self, enable: bool = True):
         _check(lib.bpjd_profile(self._h, 1 if enable else 0), "bpjd_profile")

@@ -257,6 +257,7 @@ extern "C" const char* bpjd_status_string(int c) {
     case BPJD_ERR_CUDA: return "CUDA error";
     case BPJD_ERR_UNSUPPORTED: return "unsupported option";
     case BPJD_ERR_TOO_LARGE: return "request exceeds the fixed scratch capacity of the allocation-free entry point";
+    case BPJD_ERR_TIMEOUT: return "a bounded device-side wait ran out (bulk copy not completed in time)";
     default: return "unknown status";
   }
 }
@@ -705,7 +706,7 @@ extern "C" int bpjd_solve(bpjd_handle* hh, double* eigvals, double* eigvecs, int
     CK(cudaMemcpyAsync(herr, h.derr, sizeof(herr), cudaMemcpyDeviceToHost, h.stream));
     CK(cudaStreamSynchronize(h.stream));
     if (herr[0]) {
-      rc = BPJD_ERR_LOCAL_INDEFINITE;
+      rc = local_status(herr[0]);
       break;
     }
     if (h.hstat->err_breakdown) {
@@ -869,10 +870,15 @@ extern "C" int bpjd_apply_preconditioner(bpjd_handle* hh, const double* rho, con
   CKI(launch_precond(h, rho, lam, Z));
   CK(cudaMemcpyAsync(herr, h.derr, sizeof(herr), cudaMemcpyDeviceToHost, h.stream));
   CK(cudaStreamSynchronize(h.stream));
-  if (herr[0]) return BPJD_ERR_LOCAL_INDEFINITE;
-  return BPJD_OK;
+  return local_status(herr[0]);
 fail:
   return rc;
+}
+
+extern "C" int bpjd_set_wait_limit(bpjd_handle* hh, int32_t attempts) {
+  if (!hh || attempts < 0) return BPJD_ERR_BAD_ARG;
+  reinterpret_cast<Handle*>(hh)->wait_limit = attempts;
+  return BPJD_OK;
 }
 
 extern "C" int bpjd_block_gram(bpjd_handle* hh, int32_t nu, const double* const* U, int32_t nv,

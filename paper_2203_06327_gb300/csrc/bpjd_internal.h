@@ -48,6 +48,7 @@ struct Handle {
   bool dword() const { return precision == BPJD_MIXED; }
   int32_t max_iter = 500;
   double tol = 1e-8, drop_tol = 1e-10;
+  int32_t wait_limit = 1 << 22;  // attempts of every bounded device-side wait (bpjd_set_wait_limit)
   cudaStream_t stream = nullptr;
 
   // ---- matrices
@@ -110,6 +111,14 @@ struct Handle {
   int last_iters = 0;
   double t_setup = 0;          // seconds spent in bpjd_setup
 };
+
+// Status of the local-solve error bits (h.derr[0]): a wait that ran out (or copies
+// that never completed) outranks a non-positive pivot, which it may have caused.
+inline int local_status(int32_t bits) {
+  if (bits & 6) return BPJD_ERR_TIMEOUT;
+  if (bits & 1) return BPJD_ERR_LOCAL_INDEFINITE;
+  return BPJD_OK;
+}
 
 // Records an event pair around a kernel-class launch when profiling is on.
 struct ProfScope {

@@ -805,12 +805,24 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
-// Bounded wait on an mbarrier phase; false after the iteration limit.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+// Bounded wait on an mbarrier phase; false after `limit` attempts (the limit is
+// a launch parameter: bpjd_set_wait_limit).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int limit) {
+  for (int it = 0; it < limit; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+// Before a kernel that gave up waiting returns, the thread that issued the bulk
+// copies waits for the ones still in flight (they write this CTA's shared
+// memory), with a fixed bound of its own; false if even that runs out.
+__device__ __forceinline__ bool mbar_drain(uint64_t* bar, uint32_t parity) {
   for (int it = 0; it < (1 << 22); ++it)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
+// Error bits of the local-solve kernels (h.derr[0]): a non-positive pivot, a
+// bounded wait that ran out, and copies still in flight when the drain gave up.
+constexpr int32_t kErrPivot = 1, kErrTimeout = 2, kErrDrain = 4;
 
 constexpr int kLocalWarps = 4;
 
@@ -891,7 +903,8 @@ template <int BMAX>
 __global__ void __launch_bounds__(128, (BMAX <= 40) ? 3 : 2) k_local_factor_mma(
     int nsub, int k, const int64_t* __restrict__ sub_ptr, const int32_t* __restrict__ sub_dofs,
     const float* __restrict__ bandK, const float* __restrict__ bandM, const double* __restrict__ lam,
-    const double* __restrict__ rho, float* __restrict__ Lbuf, float* __restrict__ wpk, int32_t* err) {
+    const double* __restrict__ rho, float* __restrict__ Lbuf, float* __restrict__ wpk, int32_t* err,
+    int wait_limit) {
   using S = MmaShape<BMAX>;
   constexpr int W = S::W, NBW = S::NBW, RT = S::RT, CT = S::CT, NH = S::NH, PSTR = S::PSTR;
   constexpr int WB = W * BMAX;
@@ -917,9 +930,11 @@ __global__ void __launch_bounds__(128, (BMAX <= 40) ? 3 : 2) k_local_factor_mma(
   float* pbuf = tsm + 4 * WB + wib * S::PW;  // [RT 16][PSTR] panel / tensor-core operand
   float* srw = pbuf + RT * 16 * PSTR;        // [W] right-hand sides of the entering rows
   // chunk c = band rows [W (c + 1), W (c + 2)) ∩ [0, nl), into buffer c & 1
+  int last_issued = -1, last_done = -1;  // thread 0: chunks issued / waited for successfully
   auto issue_chunk = [&](int c) {
     const int r0 = W * (c + 1);
     if (r0 >= nl) return;
+    last_issued = c;
     const int rows = min(W, nl - r0);
     const uint32_t bytes = (uint32_t)rows * BMAX * sizeof(float);
     uint64_t* b = &bars[c & 1];
@@ -976,7 +991,12 @@ __global__ void __launch_bounds__(128, (BMAX <= 40) ? 3 : 2) k_local_factor_mma(
       rn[h] = (w < W) ? rhs(W * (c + 2) + w) : 0.f;
     }
     const bool have_chunk = W * (c + 1) < nl;
-    if (have_chunk && !timeout && !mbar_wait_bounded(&bars[c & 1], (uint32_t)((c >> 1) & 1))) timeout = true;
+    if (have_chunk && !timeout) {
+      if (mbar_wait_bounded(&bars[c & 1], (uint32_t)((c >> 1) & 1), wait_limit))
+        last_done = c;
+      else
+        timeout = true;
+    }
     const float* cK = tsm + (c & 1) * WB;
     const float* cM = tsm + 2 * WB + (c & 1) * WB;
     const int crow0 = W * (c + 1);  // band row of chunk row 0
@@ -1127,7 +1147,12 @@ __global__ void __launch_bounds__(128, (BMAX <= 40) ? 3 : 2) k_local_factor_mma(
       jm -= (jm >= BMAX) ? BMAX : 0;
     }
   }
-  if ((bad || timeout) && lane_id == 0 && active) atomicOr(err, timeout ? 2 : 1);
+  if ((bad || timeout) && lane_id == 0 && active) atomicOr(err, timeout ? kErrTimeout : kErrPivot);
+  // thread 0 issued every copy: the ones it did not see complete (at most one per
+  // barrier, since no copy is issued after a wait runs out) finish before the CTA exits
+  if (threadIdx.x == 0)
+    for (int c = last_done + 1; c <= last_issued; ++c)
+      if (!mbar_drain(&bars[c & 1], (uint32_t)((c >> 1) & 1))) atomicOr(err, kErrDrain);
 }
 
 // ---------------------------------------------------------------------------
@@ -1442,7 +1467,7 @@ struct BwdShape {
 template <int BMAX>
 __global__ void __launch_bounds__(64) k_local_backward(int nsub, int k, const int64_t* __restrict__ sub_ptr,
                                                        const float* __restrict__ Lbuf, float* __restrict__ wpk,
-                                                       int32_t* err) {
+                                                       int32_t* err, int wait_limit) {
   using S = BwdShape<BMAX>;
   constexpr int TC = BMAX / 8, R = S::R, PS = S::PS, WPB = S::WPB;
   constexpr int NY = (R + 7) / 8;
@@ -1472,9 +1497,13 @@ __global__ void __launch_bounds__(64) k_local_backward(int nsub, int k, const in
   }
   __syncwarp();
   const int chtop = (nl - 1) / R;
+  // lane 0: lowest chunk issued and lowest chunk waited for successfully (chunks go
+  // from chtop down to 0)
+  int low_issued = chtop + 1, low_done = chtop + 1;
   // chunk ch = rows [ch R, min(nl, ch R + R)) of each served shift, into buffer ch & 1
   auto issue = [&](int ch) {
     if (ch < 0) return;
+    low_issued = ch;
     const int r0 = ch * R;
     const int rows = min(R, nl - r0);
     const uint32_t bytes = (uint32_t)rows * BMAX * sizeof(float);
@@ -1515,7 +1544,12 @@ __global__ void __launch_bounds__(64) k_local_backward(int nsub, int k, const in
 #pragma unroll
       for (int q = 0; q < NY; ++q) ycur[q] = ynext[q];
       load_y(ch - 1, ynext);
-      if (!timeout && !mbar_wait_bounded(&bar[half], ph[half])) timeout = true;
+      if (!timeout) {
+        if (mbar_wait_bounded(&bar[half], ph[half], wait_limit))
+          low_done = ch;
+        else
+          timeout = true;
+      }
       ph[half] ^= 1u;
       const float* Lb = buf + (half * 4 + p) * PS;
 #pragma unroll
@@ -1545,7 +1579,12 @@ __global__ void __launch_bounds__(64) k_local_backward(int nsub, int k, const in
       }
     }
   }
-  if (timeout && lane == 0) atomicOr(err, 2);
+  if (timeout && lane == 0) atomicOr(err, kErrTimeout);
+  // lane 0 issued every copy of this warp: drain the ones it did not see complete
+  // (chunk ch is the floor((chtop - ch) / 2)-th use of its barrier)
+  if (lane == 0)
+    for (int ch = low_done - 1; ch >= low_issued; --ch)
+      if (!mbar_drain(&bar[ch & 1], (uint32_t)(((chtop - ch) >> 1) & 1))) atomicOr(err, kErrDrain);
 }
 
 // ---------------------------------------------------------------------------
@@ -3403,12 +3442,12 @@ int launch_precond(Handle& h, const double* rho, const double* lam, double* Z) {
     k_local_factor_mma<BM><<<blocks, 32 * kLocalWarps, sm, h.stream>>>(h.nsub, k, h.sub_ptr, h.sub_dofs,       \
                                                                        h.bandKf, h.bandMf, lam, rho,           \
                                                                        (float*)h.Lbuf, (float*)h.wpk,          \
-                                                                       h.derr);                                \
+                                                                       h.derr, h.wait_limit);                  \
     {                                                                                                          \
       const size_t bsm = sizeof(float) * BwdShape<BM>::smem_floats;                                            \
       allow_dynamic_smem((const void*)k_local_backward<BM>);       \
       k_local_backward<BM><<<bwd_blocks, 32 * BwdShape<BM>::WPB, bsm, h.stream>>>(                             \
-          h.nsub, k, h.sub_ptr, (const float*)h.Lbuf, (float*)h.wpk, h.derr);                                  \
+          h.nsub, k, h.sub_ptr, (const float*)h.Lbuf, (float*)h.wpk, h.derr, h.wait_limit);                    \
     }                                                                                                          \
     break;                                                                                                     \
   }
@@ -3426,7 +3465,7 @@ int launch_precond(Handle& h, const double* rho, const double* lam, double* Z) {
     const size_t bsm = sizeof(float) * BwdShape<BM>::smem_floats;                                              \
     allow_dynamic_smem((const void*)k_local_backward<BM>);                                                     \
     k_local_backward<BM><<<bwd_blocks, 32 * BwdShape<BM>::WPB, bsm, h.stream>>>(                               \
-        h.nsub, k, h.sub_ptr, (const float*)h.Lbuf, (float*)h.wpk, h.derr);                                    \
+        h.nsub, k, h.sub_ptr, (const float*)h.Lbuf, (float*)h.wpk, h.derr, h.wait_limit);                      \
     break;                                                                                                     \
   }
         BPJD_LOCAL_WIDE(64)

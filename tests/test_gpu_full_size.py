@@ -22,7 +22,8 @@ import scipy.sparse.linalg as sla
 
 from conftest import golden
 from oracle import metrics
-from workloads import config_c2, config_c4, config_table1_col1, config_table3_col1, config_table5, config_table7_col1
+from workloads import (config_c2, config_c3, config_c4, config_table1_col1, config_table3_col1, config_table5,
+                       config_table7_col1)
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -94,14 +95,18 @@ def test_table5_columns_on_gpu(col, n):
     assert metrics.rel_residuals(_csr(pb.K), _csr(pb.M), lam, X).max() <= 1e-8
 
 
-@pytest.mark.parametrize("which", ["c2", "c4"])
+@pytest.mark.parametrize("which", ["c2", "c2-fp64", "c4"])
 def test_full_size_against_eigsh(which):
-    """C2 (the bench workload, mixed precision) and C4 (clamped plate, Morley; FP32 local
-    solves with every other step in FP64) at full size against eigsh.  C4's residual
-    tolerance is 1e-7: for its first eigenvector |K||x| / |Kx| = 1.1e8, so FP64 rounding
-    alone leaves a relative residual near 1.2e-8 (the solve levels off at 1.7e-8)."""
+    """C2 (the bench workload, mixed precision and the plain FP64 path) and C4 (clamped
+    plate, Morley; FP32 local solves with every other step in FP64) at full size against
+    eigsh.  C4's residual tolerance is 1e-7: for its first eigenvector |K||x| / |Kx| =
+    1.1e8, so FP64 rounding alone leaves a relative residual near 1.2e-8 (the solve
+    levels off at 1.7e-8)."""
+    rtol = 1e-9
     if which == "c2":
         spec, precision, tol = config_c2(), B.MIXED, 1e-8
+    elif which == "c2-fp64":
+        spec, precision, tol, rtol = config_c2(), B.FP64, 1e-8, 1e-10
     else:
         spec, precision, tol = config_c4(), B.MIXED_LOCAL, 1e-7
     pb, lam, X, st = _solve(spec, precision, tol=tol, max_iter=2000)
@@ -109,7 +114,7 @@ def test_full_size_against_eigsh(which):
     w, V = sla.eigsh(K.tocsc(), spec.k + 4, M.tocsc(), v0=np.random.default_rng(0).standard_normal(K.shape[0]), sigma=0.0, which="LM", tol=1e-13)
     order = np.argsort(w)
     w, V = w[order], V[:, order]
-    np.testing.assert_allclose(lam, w[: spec.k], rtol=1e-9)
+    np.testing.assert_allclose(lam, w[: spec.k], rtol=rtol)
     assert metrics.rel_residuals(K, M, lam, X).max() <= tol
     # clusters taken from the wider reference spectrum; a cluster that the k-th
     # eigenvalue shares with the (k+1)-th is pinned by its eigenvalues only
@@ -118,3 +123,47 @@ def test_full_size_against_eigsh(which):
             assert metrics.gap_b(X[:, a:b], V[:, a:b], M) <= 1e-6
     G = X.T @ (M @ X)
     np.testing.assert_allclose(G, np.eye(spec.k), atol=1e-10)
+
+
+def _kuhn_stiffness_inverse(K, n, h):
+    """On the Kuhn split of a uniform cube grid the P1 stiffness matrix is h times the
+    7-point Laplacian T (+) T (+) T, T = tridiag(-1, 2, -1) of order n - 1 (checked here
+    entry by entry); its inverse is applied exactly by the type-I sine transform, whose
+    basis diagonalises T with eigenvalues 2 - 2 cos(j pi / n)."""
+    import scipy.fft as fft
+    m = n - 1
+    T = sp.diags([-np.ones(m - 1), 2 * np.ones(m), -np.ones(m - 1)], [-1, 0, 1])
+    I = sp.eye(m)
+    L = (sp.kron(sp.kron(I, I), T) + sp.kron(sp.kron(I, T), I) + sp.kron(sp.kron(T, I), I)) * h
+    assert abs(K - L).max() <= 1e-15 * abs(L).max()
+    ev = 2 - 2 * np.cos(np.arange(1, m + 1) * np.pi / n)
+    D = h * (ev[:, None, None] + ev[None, :, None] + ev[None, None, :])
+
+    def apply(b):
+        c = fft.dstn(b.reshape(m, m, m), type=1)
+        return fft.idstn(c / D, type=1).ravel()
+    b = np.random.default_rng(1).standard_normal(m ** 3)
+    assert np.abs(K @ apply(b) - b).max() <= 1e-12 * np.abs(b).max()
+    return sla.LinearOperator(K.shape, matvec=apply, dtype=float)
+
+
+def test_c3_full_size_against_reference():
+    """C3 (P1 Kuhn tetrahedra on 64^3 cubes, 250,047 dofs, 8^3 subdomains, delta = 1, k = 10,
+    mixed precision) against shift-invert Lanczos (eigsh at sigma = 0) of the library's own
+    matrices, with K^{-1} applied by the fast sine transform (a sparse LU of this 3-D
+    matrix takes far too long on the host): eigenvalues 1e-9 relative, cluster gaps
+    <= 1e-6 (pairs and a near-triple at 6 pi^2 and 11 pi^2), residuals <= 1e-8."""
+    spec = config_c3()
+    pb, lam, X, st = _solve(spec, B.MIXED)
+    K, M = _csr(pb.K), _csr(pb.M)
+    opinv = _kuhn_stiffness_inverse(K, spec.n[0], spec.length[0] / spec.n[0])
+    w, V = sla.eigsh(K, spec.k + 4, M, sigma=0.0, which="LM", tol=1e-13, OPinv=opinv,
+                     v0=np.random.default_rng(0).standard_normal(K.shape[0]))
+    order = np.argsort(w)
+    w, V = w[order], V[:, order]
+    np.testing.assert_allclose(lam, w[: spec.k], rtol=1e-9)
+    assert metrics.rel_residuals(K, M, lam, X).max() <= 1e-8
+    for a, b in metrics.clusters(w[: spec.k + 1]):
+        if b <= spec.k:
+            assert metrics.gap_b(X[:, a:b], V[:, a:b], M) <= 1e-6
+    np.testing.assert_allclose(X.T @ (M @ X), np.eye(spec.k), atol=1e-10)

@@ -56,6 +56,42 @@ def test_serving_stream_requests_solve():
         srv.close()
 
 
+def test_serving_stream_requests_match_reference_eigenpairs():
+    """The first 8 requests of the seeded serving stream (P1 on 64..512 squares, random
+    smooth kappa, k in 4..16) solved by the server, each checked against the k lowest
+    generalised eigenpairs of the oracle's own assembly of the same request (dense eigh
+    below 4000 dofs, shift-invert eigsh above): eigenvalues to 1e-9 relative, cluster
+    subspace gaps <= 1e-6, relative residuals <= 1e-8, X^T M X = I."""
+    import scipy.linalg as la
+    import scipy.sparse.linalg as sla
+    from oracle import metrics, problem as oproblem
+    reqs = serving_stream(8, seed=0)
+    srv = B.Server(workers=4)
+    try:
+        tickets = [(r, srv.submit(B.problem_from_spec(r.spec), r.spec.k)) for r in reqs]
+        results = [(r, srv.poll(t)) for r, t in tickets]
+    finally:
+        srv.close()
+    for r, (rc, lam, X, st, times) in results:
+        assert rc == B.OK, r.spec.name
+        k = r.spec.k
+        op = oproblem.build(r.spec)
+        K, M = op.K.tocsr(), op.M.tocsr()
+        if K.shape[0] < 4000:
+            w, V = la.eigh(K.toarray(), M.toarray(), subset_by_index=[0, k])
+        else:
+            w, V = sla.eigsh(K.tocsc(), k + 4, M.tocsc(), sigma=0.0, which="LM", tol=1e-13,
+                             v0=np.random.default_rng(0).standard_normal(K.shape[0]))
+            order = np.argsort(w)
+            w, V = w[order], V[:, order]
+        np.testing.assert_allclose(lam, w[:k], rtol=1e-9, err_msg=r.spec.name)
+        assert metrics.rel_residuals(K, M, lam, X).max() <= 1e-8, r.spec.name
+        for a, b in metrics.clusters(w[: k + 1]):
+            if b <= k:
+                assert metrics.gap_b(X[:, a:b], V[:, a:b], M) <= 1e-6, (r.spec.name, a, b)
+        np.testing.assert_allclose(X.T @ (M @ X), np.eye(k), atol=1e-10)
+
+
 def test_errors_stay_with_their_request():
     bad = replace(config_c1(), tau=0)   # first local shifted matrices indefinite
     good = config_small_2d()

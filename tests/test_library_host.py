@@ -29,13 +29,13 @@ def test_exports_every_declared_symbol():
     assert set(B.EXPORTED) <= declared
 
 
-def _cmp_csr(lib_csr, ora):
+def _cmp_csr(lib_csr, ora, rel=2e-15):
     ora = ora.tocsr()
     ora.sort_indices()
     np.testing.assert_array_equal(lib_csr.row_ptr, ora.indptr)
     np.testing.assert_array_equal(lib_csr.col_idx, ora.indices)
     scale = np.abs(ora.data).max()
-    np.testing.assert_allclose(lib_csr.val, ora.data, rtol=0, atol=2e-15 * scale)
+    np.testing.assert_allclose(lib_csr.val, ora.data, rtol=0, atol=rel * scale)
 
 
 @pytest.mark.parametrize("spec", [config_c1(), config_small_2d(), config_small_3d(),
@@ -70,6 +70,27 @@ def test_c2_generators_match_oracle_full_size():
     ptr, dofs, col, nc = partition.box_partition(spec)
     np.testing.assert_array_equal(lp.part.sub_ptr, ptr)
     np.testing.assert_array_equal(lp.part.sub_dofs, dofs)
+
+
+def test_c3_generators_match_oracle_full_size():
+    """The 250047-dof C3 workload (P1 Kuhn tetrahedra on 64^3 cubes, 8^3 boxes, delta = 1):
+    patterns, coarse interpolation and partition bit-exact, values to 4e-15."""
+    from workloads import config_c3
+    spec = config_c3()
+    lp = B.problem_from_spec(spec)
+    op = oracle_problem.build(spec)
+    # a diagonal entry sums the contributions of 24 tetrahedra, added in different
+    # orders by the two assemblies: up to 24 half-ulps (2.7e-15) relative
+    _cmp_csr(lp.K, op.K, rel=4e-15)
+    _cmp_csr(lp.M, op.M, rel=4e-15)
+    P = op.P.tocsr()
+    P.sort_indices()
+    np.testing.assert_array_equal(lp.P.row_ptr, P.indptr)
+    np.testing.assert_array_equal(lp.P.col_idx, P.indices)
+    np.testing.assert_array_equal(lp.P.val, P.data)
+    np.testing.assert_array_equal(lp.part.sub_ptr, op.sub_ptr)
+    np.testing.assert_array_equal(lp.part.sub_dofs, op.sub_dofs)
+    np.testing.assert_array_equal(lp.part.sub_color, op.sub_color)
 
 
 def test_c4_generators_match_oracle_full_size():
