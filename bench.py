@@ -55,6 +55,10 @@ def _args():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=64)
     ap.add_argument("--serving-workers", type=int, default=4)
+    ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--no-scaled", action="store_true")
+    ap.add_argument("--scaled-sizes", default="1024,2048",
+                    help="elements per side of the scaled C2 problems (SpMM / Schwarz-apply bandwidth)")
     return ap.parse_args()
 
 
@@ -121,25 +125,51 @@ class ClockSampler:
 # algorithmic bytes (see the design notes for the derivation)
 # ---------------------------------------------------------------------------
 def local_bytes(lay, k, esz):
-    """Banded local solves, one preconditioner application: read the band of K_l and
-    M_l once per subdomain, gather rho (FP64), write and re-read the band factor of
-    every (l, i), write the local solutions, read the dof map."""
+    """Algorithmic bytes of the banded local solves, one preconditioner application:
+    gather rho (FP64), read the dof map, read each band factor L_{l,i} once, write the
+    local solutions (the factorisation itself is not counted)."""
+    B, sn = lay["band_window"], lay["sum_local"]
+    return sn * k * 8 + sn * 4 + sn * k * B * esz + sn * k * esz
+
+
+def local_design_bytes(lay, k, esz):
+    """Bytes the two local kernels of this design must move: the bands of K_l and M_l
+    once per subdomain, rho, the factor records written and read back, the local
+    solutions and the dof map."""
     B, sn = lay["band_window"], lay["sum_local"]
     return 2 * sn * B * esz + sn * k * 8 + 2 * sn * k * B * esz + sn * k * esz + sn * 4
 
 
 def schwarz_bytes(lay, k, esz, n, nnzP, nH):
-    """Whole Eq. (3.3) application: local part + coarse restriction (P^T rho: P and rho)
-    + spectral coarse solve (Phi twice) + prolongation-add (P, w0, local solutions, map, Z)."""
+    """Whole Eq. (3.3) application: the local part, the coarse restriction and
+    expansion (P twice, rho, the coarse eigenbasis twice) and one pass over Z (the
+    prolongation-add is a gather that writes each entry of Z once)."""
     sn = lay["sum_local"]
-    coarse = nnzP * 12 + n * k * 8 + 2 * nH * nH * 8
-    prolong = nnzP * 12 + sn * k * esz + (n + 1) * 4 + sn * 4 + n * k * 8
-    return local_bytes(lay, k, esz) + coarse + prolong
+    coarse = 2 * nnzP * 12 + 2 * n * k * 4 + 2 * nH * nH * 8
+    return local_bytes(lay, k, esz) + coarse + n * k * 8
 
 
-# ncu dram__bytes_read.sum + dram__bytes_write.sum of one local-solve application
-# (k_local_factor_mma<40> + k_local_backward<40>), keyed by workload and precision
-LOCAL_TRAFFIC = {("c2_kappa_rect_p1_h512", "mixed"): 127.334144e6 + 555.139840e6 + 608.864256e6 + 15.797248e6}
+def spmm_bytes(nnz, n, k):
+    """K X and M X over a shared pattern: column indices, both value arrays, row
+    pointers, X read once, both products written."""
+    return nnz * (4 + 16) + (n + 1) * 8 + 3 * n * k * 8
+
+
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of one local-solve application on
+# C2 (k_local_factor_mma<40> + k_local_backward<40>), valid for the kernel source it
+# was measured on (sha256 of csrc/kernels.cu, first 16 hex digits); null otherwise
+LOCAL_TRAFFIC = {("c2_kappa_rect_p1_h512", "mixed"): (None, None)}
+
+
+def _kernel_source_hash():
+    import hashlib
+    with open(os.path.join(ROOT, "paper_2203_06327_gb300", "csrc", "kernels.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def _local_traffic(workload, precision):
+    sha, val = LOCAL_TRAFFIC.get((workload, precision), (None, None))
+    return val if (sha is not None and sha == _kernel_source_hash()) else None
 
 
 def _peaks():
@@ -242,6 +272,151 @@ def _blas_threads():
         return max((i.get("num_threads", 1) for i in info), default=os.cpu_count())
     except Exception:
         return os.cpu_count()
+
+
+# ---------------------------------------------------------------------------
+# accuracy of the returned eigenpairs against FP64 reference eigenpairs
+# ---------------------------------------------------------------------------
+def _scipy_csr(c):
+    import scipy.sparse as sp
+    return sp.csr_matrix((c.val, c.col_idx, c.row_ptr), shape=(c.n_rows, c.n_cols))
+
+
+def reference_eigenpairs(spec, K, M, nev):
+    """Lowest nev generalised eigenpairs of (K, M) in FP64 by shift-invert Lanczos
+    (scipy eigsh, sigma = 0); on the Kuhn split of a cube grid the P1 stiffness matrix
+    is h times the 7-point Laplacian, whose inverse the type-I sine transform applies
+    exactly (a sparse LU of a 3-D matrix of this size takes far too long)."""
+    import numpy as np
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as sla
+    v0 = np.random.default_rng(0).standard_normal(K.shape[0])
+    opinv = None
+    if spec.kind == "p1_3d" and len(set(spec.n)) == 1 and len(set(spec.length)) == 1:
+        import scipy.fft as fft
+        nn, h = spec.n[0], spec.length[0] / spec.n[0]
+        m = nn - 1
+        T = sp.diags([-np.ones(m - 1), 2 * np.ones(m), -np.ones(m - 1)], [-1, 0, 1])
+        I = sp.eye(m)
+        L = (sp.kron(sp.kron(I, I), T) + sp.kron(sp.kron(I, T), I) + sp.kron(sp.kron(T, I), I)) * h
+        if abs(K - L).max() <= 1e-15 * abs(L).max():
+            ev = 2 - 2 * np.cos(np.arange(1, m + 1) * np.pi / nn)
+            D = h * (ev[:, None, None] + ev[None, :, None] + ev[None, None, :])
+            opinv = sla.LinearOperator(K.shape, dtype=float,
+                                       matvec=lambda b: fft.idstn(fft.dstn(b.reshape(m, m, m), type=1) / D,
+                                                                  type=1).ravel())
+        else:
+            return None, None
+    w, V = sla.eigsh(K.tocsc() if opinv is None else K, nev, M.tocsc() if opinv is None else M, sigma=0.0,
+                     which="LM", tol=1e-13, v0=v0, OPinv=opinv)
+    o = np.argsort(w)
+    return w[o], V[:, o]
+
+
+def accuracy_report(spec, pb, lam, X):
+    """Per-eigenvalue relative error, per-cluster subspace gap (the largest principal
+    angle in the M-inner product, both directions; clusters = adjacent reference
+    eigenvalues closer than 1e-2 relative), relative residuals and M-orthonormality of
+    the returned pairs, against FP64 reference eigenpairs of the same matrices."""
+    import numpy as np
+    K, M = _scipy_csr(pb.K), _scipy_csr(pb.M)
+    k = len(lam)
+    t0 = time.perf_counter()
+    w, V = reference_eigenpairs(spec, K, M, k + 4)
+    if w is None:
+        return {"reference": "unavailable for this workload"}
+
+    def msin(U, W):
+        G = U.T @ (M @ U)
+        U = np.linalg.solve(np.linalg.cholesky(0.5 * (G + G.T)), U.T).T
+        G = W.T @ (M @ W)
+        W = np.linalg.solve(np.linalg.cholesky(0.5 * (G + G.T)), W.T).T
+        R = U - W @ (W.T @ (M @ U))
+        S = R.T @ (M @ R)
+        return float(np.sqrt(max(np.linalg.eigvalsh(0.5 * (S + S.T)).max(), 0.0)))
+
+    groups, start = [], 0
+    for i in range(1, k + 1):
+        if (w[i] - w[i - 1]) / abs(w[i]) >= 1e-2:
+            groups.append((start, i))
+            start = i
+    gaps = []
+    for a, b in groups:
+        if b <= k:
+            th = max(msin(X[:, a:b], V[:, a:b]), msin(V[:, a:b], X[:, a:b]))
+            gaps.append({"cols": [a, b], "theta_b": th})
+    R = K @ X - (M @ X) * lam[None, :]
+    res = np.linalg.norm(R, axis=0) / (np.abs(lam) * np.linalg.norm(M @ X, axis=0))
+    orth = float(np.abs(X.T @ (M @ X) - np.eye(k)).max())
+    return {"reference": "FP64 shift-invert Lanczos (scipy eigsh, tol 1e-13) of the same matrices",
+            "eigval_rel_err": [float(x) for x in np.abs(lam - w[:k]) / np.abs(w[:k])],
+            "max_eigval_rel_err": float((np.abs(lam - w[:k]) / np.abs(w[:k])).max()),
+            "cluster_theta_b": gaps, "max_theta_b": max((g["theta_b"] for g in gaps), default=None),
+            "rel_resid": [float(x) for x in res], "orth_err": orth,
+            "reference_seconds": time.perf_counter() - t0}
+
+
+def scaled_runs(B, dev, prec, sizes, peak, reps=10):
+    """SpMM (K X and M X, k = 12 columns) and one Schwarz application (Eq. (3.3), all k
+    shifts) on C2's operator at 1-17M dofs with C2's subdomain shape, timed with CUDA
+    events on the solver's stream, L2 flushed before every repetition."""
+    import torch
+    from workloads import config_c2_scaled
+    out = []
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    esz = 8 if prec == B.FP64 else 4
+    for n in sizes:
+        spec = config_c2_scaled(n)
+        pb = B.problem_from_spec(spec)
+        dpb = B.Problem(pb.K.to(dev), pb.M.to(dev), pb.P.to(dev), pb.P0.to(dev), pb.part.to(dev), pb.tau)
+        t0 = time.perf_counter()
+        sv = B.Solver.from_problem(dpb, spec.k, device=dev, precision=prec, subspace=B.W_3K, stream=stream)
+        t_setup = time.perf_counter() - t0
+        k, nd = spec.k, spec.n_dofs
+        g = torch.Generator(device=dev)
+        g.manual_seed(0)
+        X = torch.randn((nd, k), dtype=torch.float64, device=dev, generator=g)
+        YA, YM, Z = torch.empty_like(X), torch.empty_like(X), torch.empty_like(X)
+        lam = torch.zeros(k, dtype=torch.float64, device=dev)   # shift 0: every local matrix SPD
+        lay = sv.layout()
+
+        def timed(fn):
+            ts = []
+            with torch.cuda.stream(stream):
+                for r in range(reps + 2):
+                    flush.fill_(1.0)
+                    torch.cuda.synchronize()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    fn()
+                    e1.record(stream)
+                    e1.synchronize()
+                    if r >= 2:
+                        ts.append(e0.elapsed_time(e1))
+            return statistics.median(ts)
+
+        t_spmm = timed(lambda: sv.spmm(X, YA, YM))
+        sv.profile(True)
+        t_schw = timed(lambda: sv.apply_preconditioner(X, lam, Z))
+        pr, _ = sv.profile_read()
+        loc_ms = pr["local"][0] / max(1, pr["local"][1])
+        b_sp = spmm_bytes(lay["nnz"], nd, k)
+        b_sw = schwarz_bytes(lay, k, esz, nd, pb.P.nnz, spec.n_coarse)
+        b_loc = local_bytes(lay, k, esz)
+        sv.close()
+        out.append({"workload": spec.name, "n_dofs": nd, "k": k, "n_sub": lay["n_sub"], "setup_s": t_setup,
+                    "spmm": {"ms": t_spmm, "bytes": b_sp, "GBps": b_sp / t_spmm / 1e6,
+                             "frac": b_sp / t_spmm / 1e6 / peak},
+                    "schwarz_apply": {"ms": t_schw, "bytes": b_sw, "GBps": b_sw / t_schw / 1e6,
+                                      "frac": b_sw / t_schw / 1e6 / peak},
+                    "local": {"ms": loc_ms, "bytes": b_loc, "GBps": b_loc / loc_ms / 1e6,
+                              "frac": b_loc / loc_ms / 1e6 / peak}})
+        del X, YA, YM, Z, dpb
+        torch.cuda.synchronize()
+    return {"peak_GBps": peak, "l2": "flushed before every repetition (256 MB write)", "reps": reps,
+            "runs": out}
 
 
 # ---------------------------------------------------------------------------
@@ -413,18 +588,20 @@ def run_ours(a):
     if dom == "local":
         bytes_per = local_bytes(lay, k, esz)
     elif dom == "spmm":
-        bytes_per = lay["nnz"] * (4 + 16) + (spec.n_dofs + 1) * 8 + 3 * spec.n_dofs * k * 8
+        bytes_per = spmm_bytes(lay["nnz"], spec.n_dofs, k)
     else:
         bytes_per = None
     roof = None
     if bytes_per is not None and dom_cnt:
         ach = bytes_per / (dom_ms / dom_cnt / 1e3) / 1e9
         # DRAM bytes (read + write) per application measured by ncu for this kernel
-        # version on this workload; None elsewhere
-        traffic = LOCAL_TRAFFIC.get((spec.name, a.precision)) if dom == "local" else None
+        # source on this workload; None elsewhere or once the source has changed
+        traffic = _local_traffic(spec.name, a.precision) if dom == "local" else None
         roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                 "peak_kind": peak_kind, "algorithmic_bytes_per_launch": bytes_per, "traffic": traffic,
                 "avg_launch_ms": dom_ms / dom_cnt}
+        if dom == "local":
+            roof["design_bytes_per_launch"] = local_design_bytes(lay, k, esz)
     schw_ms = sum(prof_tot[c][0] for c in ("local", "coarse", "prolong"))
     n_apply = prof_tot["local"][1]
     schw_gbs = schwarz_bytes(lay, k, esz, spec.n_dofs, pb.P.nnz, spec.n_coarse) / (
@@ -454,6 +631,13 @@ def run_ours(a):
         e2e = {"value": k * len(et) / sum(et), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h)}
 
+    accuracy = None
+    if rank == 0 and not a.no_accuracy:
+        accuracy = accuracy_report(spec, pb, np.asarray(lam, dtype=np.float64), X.cpu().numpy())
+    scaled = None
+    if rank == 0 and not a.no_scaled:
+        scaled = scaled_runs(B, dev, prec, [int(x) for x in a.scaled_sizes.split(",") if x], peak)
+
     cpu = None
     serving = None
     if rank == 0 and not a.no_serving:
@@ -477,6 +661,7 @@ def run_ours(a):
                 "schwarz_apply_gbs": schw_gbs,
                 "kernel_ms_per_step": {kk: v[0] / a.steps for kk, v in prof_tot.items()},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "serving": serving, "clocks": ck,
+                "accuracy": accuracy, "scaled": scaled,
                 "gpu_launches": launches}
         print(json.dumps(line), flush=True)
     if world > 1:

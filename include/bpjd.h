@@ -111,6 +111,20 @@ typedef struct {
   int32_t inputs_on_device; /* 1: all pointers of A, M, P, P0 and the partition
                                are device pointers; 0: host pointers */
   void*   stream;           /* cudaStream_t for all work; NULL = legacy default stream */
+  size_t  local_scratch_bytes; /* bound on the device scratch that holds the band factors
+                               of the local solves (0: default 2 GiB).  Subdomains are
+                               solved in chunks whose factors fit; a chunk holds at least
+                               one subdomain, so the scratch may exceed the bound by one
+                               subdomain's factors (n_l k (B + 8) FP32 values) */
+  double  local_refactor_tol;  /* the local band factors of K_l - lambda_i M_l are formed
+                               anew only when some shift moved by more than this relative
+                               amount since they were formed; otherwise the stored factors
+                               are reused (forward and backward sweeps only).  0: default,
+                               1e-6 with FP32 local solves, exact shifts (a factorisation
+                               at every application, as in Eq. (3.3)) for BPJD_FP64;
+                               < 0: exact shifts always.  Reuse needs every factor of one
+                               application resident (one chunk) and a band window of at
+                               most 152 */
 } bpjd_opts;
 
 typedef struct {

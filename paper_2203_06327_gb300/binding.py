@@ -63,7 +63,8 @@ class Partition(C.Structure):
 class Opts(C.Structure):
     _fields_ = [("k", C.c_int32), ("precision", C.c_int32), ("subspace", C.c_int32), ("stop_rule", C.c_int32),
                 ("tol", C.c_double), ("max_iter", C.c_int32), ("drop_tol", C.c_double), ("H", C.c_double),
-                ("delta", C.c_double), ("inputs_on_device", C.c_int32), ("stream", C.c_void_p)]
+                ("delta", C.c_double), ("inputs_on_device", C.c_int32), ("stream", C.c_void_p),
+                ("local_scratch_bytes", C.c_size_t), ("local_refactor_tol", C.c_double)]
 
 
 class Stats(C.Structure):
@@ -274,10 +275,13 @@ class Solver:
 
     def __init__(self, K: CsrArrays, M: CsrArrays, P: CsrArrays, P0: Optional[CsrArrays], part: PartitionArrays,
                  k: int, precision: int = FP64, subspace: int = W_2K, stop_rule: int = STOP_RESIDUAL,
-                 tol: float = 1e-8, max_iter: int = 500, drop_tol: float = 1e-10, stream=None):
+                 tol: float = 1e-8, max_iter: int = 500, drop_tol: float = 1e-10, stream=None,
+                 local_scratch_bytes: int = 0, local_refactor_tol: float = 0.0):
         o = Opts()
         lib.bpjd_default_opts(C.byref(o))
         o.k, o.precision, o.subspace, o.stop_rule = k, precision, subspace, stop_rule
+        o.local_scratch_bytes = int(local_scratch_bytes)
+        o.local_refactor_tol = float(local_refactor_tol)
         o.tol, o.max_iter, o.drop_tol = tol, max_iter, drop_tol
         o.inputs_on_device = 1 if _is_torch(K.val) and K.val.is_cuda else 0
         o.stream = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else stream)

@@ -306,6 +306,11 @@ extern "C" int bpjd_setup(const bpjd_csr* A, const bpjd_csr* M, const bpjd_csr* 
   h->tol = opts->tol > 0 ? opts->tol : 1e-8;
   h->max_iter = opts->max_iter > 0 ? opts->max_iter : 500;
   h->drop_tol = opts->drop_tol > 0 ? opts->drop_tol : 1e-10;
+  // reuse of the local factors while the shifts stay within a relative tolerance
+  // (default 1e-6 with FP32 local solves; exact shifts for BPJD_FP64 or a negative value)
+  h->refactor_tol = opts->local_refactor_tol > 0
+                        ? opts->local_refactor_tol
+                        : ((opts->local_refactor_tol == 0 && opts->precision != BPJD_FP64) ? 1e-6 : 0.0);
   h->stream = (cudaStream_t)opts->stream;
 
   {
@@ -546,12 +551,30 @@ extern "C" int bpjd_setup(const bpjd_csr* A, const bpjd_csr* M, const bpjd_csr* 
     pt.mark("initial_guess", h->stream);
     // scratch and iteration vectors
     {
+      // the band factors of every (subdomain, shift) pair are written by the
+      // factorisation and read back by the backward sweep; subdomains are taken in
+      // chunks whose factors fit the scratch bound
       const size_t esz = h->local_f32() ? sizeof(float) : sizeof(double);
       const size_t lw = (size_t)std::max(h->B, h->Bpad);
+      const size_t bound = opts->local_scratch_bytes ? opts->local_scratch_bytes : ((size_t)2 << 30);
+      h->chunk_l0.assign(1, 0);
+      h->chunk_off.assign(1, 0);
+      size_t cur = 0, most = 0;
+      for (int l = 0; l < nsub; ++l) {
+        const size_t need = esz * (size_t)(sptr[l + 1] - sptr[l]) * k * lw;
+        if (cur > 0 && cur + need > bound) {
+          h->chunk_l0.push_back(l);
+          h->chunk_off.push_back(sptr[l]);
+          cur = 0;
+        }
+        cur += need;
+        most = std::max(most, cur);
+      }
+      h->chunk_l0.push_back(nsub);
       void* p;
-      CK(cudaMalloc(&p, esz * (size_t)sum_nl * k * lw));
+      CK(cudaMalloc(&p, most));
       h->allocs.push_back(p);
-      h->bytes += esz * (size_t)sum_nl * k * lw;
+      h->bytes += most;
       h->Lbuf = p;
       CK(cudaMalloc(&p, esz * (size_t)sum_nl * k));
       h->allocs.push_back(p);
@@ -693,6 +716,9 @@ extern "C" int bpjd_solve(bpjd_handle* hh, double* eigvals, double* eigvecs, int
   bool have_prev = false;
   const int mixed = h.dword() ? 1 : 0;
 
+  std::vector<double> lam_h((size_t)k);
+  h.factors_valid = false;
+  h.refactorisations = h.reuses = 0;
   CK(cudaMemsetAsync(h.dstat, 0, sizeof(DevStatus), h.stream));
   CK(cudaMemsetAsync(h.derr, 0, 4 * sizeof(int32_t), h.stream));
   CK(cudaMemcpyAsync(X, h.X0, vbytes, cudaMemcpyDeviceToDevice, h.stream));
@@ -704,6 +730,8 @@ extern "C" int bpjd_solve(bpjd_handle* hh, double* eigvals, double* eigvecs, int
     CK(cudaMemcpyAsync(h.hstat, h.dstat, sizeof(DevStatus), cudaMemcpyDeviceToHost, h.stream));
     int32_t herr[4];
     CK(cudaMemcpyAsync(herr, h.derr, sizeof(herr), cudaMemcpyDeviceToHost, h.stream));
+    if (h.refactor_tol > 0)
+      CK(cudaMemcpyAsync(lam_h.data(), lam_cur, sizeof(double) * k, cudaMemcpyDeviceToHost, h.stream));
     CK(cudaStreamSynchronize(h.stream));
     if (herr[0]) {
       rc = local_status(herr[0]);
@@ -729,8 +757,18 @@ extern "C" int bpjd_solve(bpjd_handle* hh, double* eigvals, double* eigvecs, int
       rc = BPJD_ERR_NOCONV;
       break;
     }
-    // Step 2: t_i = (I - X X^T M) (B_i)^{-1} r_i
-    CKI(launch_precond(h, h.rho, lam_cur, h.Z));
+    // Step 2: t_i = (I - X X^T M) (B_i)^{-1} r_i.  The local factors of an earlier
+    // application are reused while every shift lies within refactor_tol of the
+    // one they were formed at (the local solves then differ from exact-shift
+    // solves by about that relative amount, far below their FP32 rounding)
+    bool reuse = h.factors_valid && h.refactor_tol > 0;
+    for (int i = 0; reuse && i < k; ++i)
+      if (!(std::fabs(lam_h[i] - h.lam_fact[i]) <= h.refactor_tol * std::fabs(lam_h[i]))) reuse = false;
+    CKI(launch_precond(h, h.rho, lam_cur, h.Z, reuse ? 1 : 0));
+    if (!reuse && h.refactor_tol > 0 && can_reuse_factors(h)) {
+      h.factors_valid = true;
+      h.lam_fact = lam_h;
+    }
     {
       const double* U[1] = {MX};
       const double* V[1] = {h.Z};
@@ -813,6 +851,9 @@ extern "C" int bpjd_solve(bpjd_handle* hh, double* eigvals, double* eigvecs, int
     CK(cudaStreamSynchronize(h.stream));
   }
   h.last_iters = it;
+  if (trace_on())
+    std::fprintf(stderr, "{\"bpjd_local_factorisations\": %lld, \"bpjd_local_reuses\": %lld}\n",
+                 (long long)h.refactorisations, (long long)h.reuses);
   if (st) {
     st->iters = it;
     st->converged = converged ? 1 : 0;
@@ -867,6 +908,7 @@ extern "C" int bpjd_apply_preconditioner(bpjd_handle* hh, const double* rho, con
   int rc = BPJD_OK;
   int32_t herr[4];
   CK(cudaMemsetAsync(h.derr, 0, 4 * sizeof(int32_t), h.stream));
+  h.factors_valid = false;  // the factors are re-formed at the caller's shifts
   CKI(launch_precond(h, rho, lam, Z));
   CK(cudaMemcpyAsync(herr, h.derr, sizeof(herr), cudaMemcpyDeviceToHost, h.stream));
   CK(cudaStreamSynchronize(h.stream));

@@ -73,7 +73,13 @@ struct Handle {
   float* bandMf = nullptr;
 
   // ---- scratch
-  void* Lbuf = nullptr;        // band factors, sum_nl * k * B elements (FP32 or FP64)
+  void* Lbuf = nullptr;        // band factors of one chunk of subdomains (FP32 or FP64)
+  std::vector<int32_t> chunk_l0;   // chunk c = subdomains [chunk_l0[c], chunk_l0[c + 1])
+  std::vector<int64_t> chunk_off;  // sub_ptr of each chunk's first subdomain (record base)
+  double refactor_tol = 0.0;       // reuse the local factors while every shift stays within this (0: never)
+  bool factors_valid = false;      // Lbuf holds the factors of every pair, formed at the shifts lam_fact
+  std::vector<double> lam_fact;    // host copy of the shifts of the stored factors
+  int64_t refactorisations = 0, reuses = 0;  // local applications of the last solve, by kind
   void* wpk = nullptr;         // packed local solutions sum_nl x k (FP32 or FP64)
   double* cH = nullptr;        // n_H x k coarse restriction
   double* aH = nullptr;        // n_H x k coarse coordinates
@@ -132,6 +138,10 @@ struct ProfScope {
 // Resolves recorded event pairs into prof_ms/prof_count (synchronises the stream).
 void prof_flush(Handle& h);
 
+// kernels.cu: raises a kernel's dynamic shared-memory limit to the device
+// maximum, once per (kernel, device)
+int allow_dynamic_smem(const void* kern);
+
 // dense.cpp
 // nvec < n: every eigenvalue, eigenvectors of the lowest nvec only (the other
 // columns of V / Phi are zero)
@@ -145,7 +155,10 @@ int launch_csr_times_dense(const CsrDev& P, const double* D, int ldd, int ncols,
                            cudaStream_t s);
 int launch_residual(Handle& h, const double* AX, const double* MX, const double* lam, double* rho);
 int launch_rayleigh(Handle& h, const double* X, const double* AX, const double* MX, double* lam);
-int launch_precond(Handle& h, const double* rho, const double* lam, double* Z);
+// reuse = 1: the stored factors are current for lam (forward and backward sweeps only)
+int launch_precond(Handle& h, const double* rho, const double* lam, double* Z, int reuse = 0);
+// whether this handle's local kernels can reuse stored factors (records of every pair resident)
+bool can_reuse_factors(const Handle& h);
 int launch_inner(Handle& h, int p, const double* const* U, int q, const double* const* V, double* out);
 // double-word block inner products: out1 = U^T V1 (and out2 = U^T V2 when nv = 2);
 // sym = 1 requires U^T V symmetric (mu == mv) and forms the upper tiles only

@@ -22,16 +22,12 @@
 
 namespace bpjd {
 
-namespace {
-
-constexpr int kPartialBlocks = 456;  // 3 x 152 SMs
-
 // Raises a kernel's dynamic shared memory limit to the device maximum, once per
 // (kernel, device).  A per-launch limit would race between host threads that
 // launch the same kernel with different sizes (concurrent solves): one thread
 // could lower the limit below another's launch.
-std::mutex g_smem_attr_mu;
-std::set<std::pair<const void*, int>> g_smem_attr_done;
+static std::mutex g_smem_attr_mu;
+static std::set<std::pair<const void*, int>> g_smem_attr_done;
 
 int allow_dynamic_smem(const void* kern) {
   int dev = 0;
@@ -51,6 +47,10 @@ int allow_dynamic_smem(const void* kern) {
   g_smem_attr_done.insert({kern, dev});
   return 0;
 }
+
+namespace {
+
+constexpr int kPartialBlocks = 456;  // 3 x 152 SMs
 
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -673,7 +673,7 @@ __global__ void k_local_band(int npairs, int k, const int64_t* __restrict__ sub_
                              const int32_t* __restrict__ sub_dofs, int B, const TP* __restrict__ bandK,
                              const TP* __restrict__ bandM, const double* __restrict__ lam,
                              const double* __restrict__ rho, TP* __restrict__ Lbuf, TP* __restrict__ wpk,
-                             int32_t* err) {
+                             int32_t* err, int64_t rec_base) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
@@ -690,7 +690,7 @@ __global__ void k_local_band(int npairs, int k, const int64_t* __restrict__ sub_
   const int32_t* dofs = sub_dofs + off;
   const int b = B - 1;
   const TP lm = (TP)lam[i];
-  TP* Lp = Lbuf + ((size_t)off * k + (size_t)i * nl) * B;
+  TP* Lp = Lbuf + ((size_t)(off - rec_base) * k + (size_t)i * nl) * B;
   auto aval = [&](int p, int q) -> TP {  // shifted local matrix entry, q <= p <= q + b
     if (p >= nl) return (p == q) ? TP(1) : TP(0);
     const size_t e = (size_t)(off + p) * B + (q - p + b);
@@ -904,7 +904,7 @@ __global__ void __launch_bounds__(128, (BMAX <= 40) ? 3 : 2) k_local_factor_mma(
     int nsub, int k, const int64_t* __restrict__ sub_ptr, const int32_t* __restrict__ sub_dofs,
     const float* __restrict__ bandK, const float* __restrict__ bandM, const double* __restrict__ lam,
     const double* __restrict__ rho, float* __restrict__ Lbuf, float* __restrict__ wpk, int32_t* err,
-    int wait_limit) {
+    int wait_limit, int64_t rec_base) {
   using S = MmaShape<BMAX>;
   constexpr int W = S::W, NBW = S::NBW, RT = S::RT, CT = S::CT, NH = S::NH, PSTR = S::PSTR;
   constexpr int WB = W * BMAX;
@@ -923,7 +923,7 @@ __global__ void __launch_bounds__(128, (BMAX <= 40) ? 3 : 2) k_local_factor_mma(
   const int nl = (int)(sub_ptr[l + 1] - off);
   const int32_t* dofs = sub_dofs + off;
   const float lm = (float)lam[ii];
-  float* Lrec = Lbuf + ((size_t)off * k + (size_t)ii * nl) * BMAX;  // record of column j at Lrec + j BMAX
+  float* Lrec = Lbuf + ((size_t)(off - rec_base) * k + (size_t)ii * nl) * BMAX;  // record of column j at Lrec + j BMAX
   float* yout = wpk + off * k + ii;                                // y_j at yout[j k]
   const float* gK = bandK + (size_t)off * BMAX;  // band row p at gK + p * BMAX, diagonal at BMAX - 1
   const float* gM = bandM + (size_t)off * BMAX;
@@ -1192,7 +1192,8 @@ template <int BMAX>
 __global__ void __launch_bounds__(WideShape<BMAX>::NW * 32, WideShape<BMAX>::MINB) k_local_factor_wide(
     int npairs, int k, const int64_t* __restrict__ sub_ptr, const int32_t* __restrict__ sub_dofs,
     const float* __restrict__ bandK, const float* __restrict__ bandM, const double* __restrict__ lam,
-    const double* __restrict__ rho, float* __restrict__ Lbuf, float* __restrict__ wpk, int32_t* err) {
+    const double* __restrict__ rho, float* __restrict__ Lbuf, float* __restrict__ wpk, int32_t* err,
+    int64_t rec_base) {
   using S = WideShape<BMAX>;
   constexpr int W = S::W, NBW = S::NBW, RT = S::RT, CT = S::CT, NW = S::NW, CTW = S::CTW, PSTR = S::PSTR;
   static_assert(BMAX % 8 == 0 && CTW * 4 * RT <= 128, "window too wide for the register tiles");
@@ -1207,7 +1208,7 @@ __global__ void __launch_bounds__(WideShape<BMAX>::NW * 32, WideShape<BMAX>::MIN
   const int nl = (int)(sub_ptr[l + 1] - off);
   const int32_t* dofs = sub_dofs + off;
   const float lm = (float)lam[i];
-  float* Lrec = Lbuf + ((size_t)off * k + (size_t)i * nl) * BMAX;
+  float* Lrec = Lbuf + ((size_t)(off - rec_base) * k + (size_t)i * nl) * BMAX;
   float* yout = wpk + off * k + i;
   const float* gK = bandK + (size_t)off * BMAX;  // band row p at gK + p * BMAX, diagonal at BMAX - 1
   const float* gM = bandM + (size_t)off * BMAX;
@@ -1467,7 +1468,7 @@ struct BwdShape {
 template <int BMAX>
 __global__ void __launch_bounds__(64) k_local_backward(int nsub, int k, const int64_t* __restrict__ sub_ptr,
                                                        const float* __restrict__ Lbuf, float* __restrict__ wpk,
-                                                       int32_t* err, int wait_limit) {
+                                                       int32_t* err, int wait_limit, int64_t rec_base) {
   using S = BwdShape<BMAX>;
   constexpr int TC = BMAX / 8, R = S::R, PS = S::PS, WPB = S::WPB;
   constexpr int NY = (R + 7) / 8;
@@ -1488,7 +1489,7 @@ __global__ void __launch_bounds__(64) k_local_backward(int nsub, int k, const in
   const int nl = (int)(sub_ptr[l + 1] - off);
   float* buf = bsm + (size_t)wib * 2 * 4 * PS;  // [2][4][PS]
   uint64_t* bar = bars[wib];
-  const float* Lsub = Lbuf + (size_t)off * k * BMAX;  // record of shift i at Lsub + i nl BMAX
+  const float* Lsub = Lbuf + (size_t)(off - rec_base) * k * BMAX;  // record of shift i at Lsub + i nl BMAX
   float* yp = wpk + off * k + ii;
   if (lane == 0) {
     mbar_init(&bar[0], 1);
@@ -1588,6 +1589,134 @@ __global__ void __launch_bounds__(64) k_local_backward(int nsub, int k, const in
 }
 
 // ---------------------------------------------------------------------------
+// Local solves, forward substitution L y = R_l rho_i with stored band factors,
+// for the applications that reuse the factors of an earlier one (the
+// factorisation kernels fuse this sweep into the factorisation).  Same warp
+// layout, records and staging as k_local_backward: four shifts per warp, eight
+// lanes per shift, lane e keeping the pending right-hand sides of the window
+// slots e + 8 c (slot = row mod BMAX); records enter shared memory in chunks of
+// R rows by bulk copies, double buffered, in ascending order.  Column j
+// (right-looking, the operation order of the fused sweep): y_j = r_j / L_jj,
+// then r_r -= L(r, j) y_j for the rows r of column j's band, and row j + BMAX
+// enters the freed slot.
+// ---------------------------------------------------------------------------
+template <int BMAX>
+__global__ void __launch_bounds__(64) k_local_forward(int nsub, int k, const int64_t* __restrict__ sub_ptr,
+                                                      const int32_t* __restrict__ sub_dofs,
+                                                      const double* __restrict__ rho, const float* __restrict__ Lbuf,
+                                                      float* __restrict__ wpk, int32_t* err, int wait_limit,
+                                                      int64_t rec_base) {
+  using S = BwdShape<BMAX>;
+  constexpr int TC = BMAX / 8, R = S::R, PS = S::PS, WPB = S::WPB;
+  constexpr int NY = (R + 7) / 8;
+  constexpr unsigned FULL = 0xffffffffu;
+  static_assert(BMAX % 8 == 0, "window must be a multiple of 8");
+  extern __shared__ __align__(128) float fsm[];
+  __shared__ __align__(8) uint64_t bars[WPB][2];
+  const int lane = threadIdx.x & 31, e = lane & 7, p = lane >> 3, wib = threadIdx.x >> 5;
+  const int wglob = blockIdx.x * WPB + wib;
+  const int wps = (k + 3) / 4;  // warps per subdomain
+  const int l = wglob / wps;
+  if (l >= nsub) return;  // whole warps only; no block-wide barrier follows
+  const int i0 = (wglob % wps) * 4;
+  const int nact = min(4, k - i0);  // shifts served by this warp
+  const bool active = p < nact;
+  const int ii = active ? i0 + p : i0;
+  const int64_t off = sub_ptr[l];
+  const int nl = (int)(sub_ptr[l + 1] - off);
+  const int32_t* dofs = sub_dofs + off;
+  float* buf = fsm + (size_t)wib * 2 * 4 * PS;  // [2][4][PS]
+  uint64_t* bar = bars[wib];
+  const float* Lsub = Lbuf + (size_t)(off - rec_base) * k * BMAX;  // record of shift i at Lsub + i nl BMAX
+  float* yp = wpk + off * k + ii;
+  if (lane == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  const int nch = (nl + R - 1) / R;
+  int hi_issued = -1, hi_done = -1;  // lane 0: last chunk issued / waited for successfully
+  // chunk ch = rows [ch R, min(nl, ch R + R)) of each served shift, into buffer ch & 1
+  auto issue = [&](int ch) {
+    if (ch >= nch) return;
+    hi_issued = ch;
+    const int r0 = ch * R;
+    const int rows = min(R, nl - r0);
+    const uint32_t bytes = (uint32_t)rows * BMAX * sizeof(float);
+    uint64_t* b = &bar[ch & 1];
+    mbar_expect_tx(b, bytes * nact);
+    for (int q = 0; q < nact; ++q)
+      bulk_load(buf + ((ch & 1) * 4 + q) * PS, Lsub + ((size_t)(i0 + q) * nl + r0) * BMAX, bytes, b);
+  };
+  auto rhs = [&](int row) -> float { return (row < nl) ? (float)rho[(int64_t)dofs[row] * k + ii] : 0.f; };
+  // right-hand sides of the rows entering during chunk ch (rows ch R + r + BMAX), lane r % 8
+  auto load_in = [&](int ch, float* v) {
+#pragma unroll
+    for (int q = 0; q < NY; ++q) {
+      const int r = e + 8 * q;
+      v[q] = (r < R) ? rhs(ch * R + r + BMAX) : 0.f;
+    }
+  };
+  if (lane == 0) issue(0);
+  float rw[TC];
+#pragma unroll
+  for (int c = 0; c < TC; ++c) rw[c] = rhs(e + 8 * c);
+  float incur[NY], innext[NY];
+  load_in(0, innext);
+  uint32_t ph[2] = {0u, 0u};
+  bool timeout = false;
+  constexpr int NCH = S::NCH;
+  static_assert(NCH % 2 == 0, "chunk parity must be static inside a window group");
+  for (int g = 0; g * NCH < nch; ++g) {
+#pragma unroll
+    for (int hc = 0; hc < NCH; ++hc) {
+      const int ch = g * NCH + hc;
+      const int half = hc & 1;  // buffer of chunk ch
+      if (ch >= nch) continue;
+      __syncwarp();  // the buffer of chunk ch - 1 (chunk ch + 1's) is no longer read
+      if (lane == 0 && !timeout) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        issue(ch + 1);
+      }
+#pragma unroll
+      for (int q = 0; q < NY; ++q) incur[q] = innext[q];
+      load_in(ch + 1, innext);
+      if (!timeout) {
+        if (mbar_wait_bounded(&bar[half], ph[half], wait_limit))
+          hi_done = ch;
+        else
+          timeout = true;
+      }
+      ph[half] ^= 1u;
+      const float* Lb = buf + (half * 4 + p) * PS;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int j = ch * R + r;
+        const int s = hc * R + r;  // j mod BMAX
+        if (j < nl) {
+          const float* row = Lb + r * BMAX;
+          const float rj = __shfl_sync(FULL, rw[s / 8], (lane & ~7) | (s % 8));
+          const float yj = rj * row[s];  // 1 / L_jj at the diagonal slot
+          if (e == 0 && active && !timeout) yp[(size_t)j * k] = yj;
+#pragma unroll
+          for (int c = 0; c < TC; ++c)
+            if (!(c == s / 8 && e == s % 8)) rw[c] = fmaf(-row[e + 8 * c], yj, rw[c]);
+          const float nv = __shfl_sync(FULL, incur[r / 8], (lane & ~7) | (r % 8));
+          if (e == s % 8) rw[s / 8] = nv;
+        }
+      }
+    }
+  }
+  if (timeout && lane == 0) atomicOr(err, kErrTimeout);
+  // lane 0 issued every copy of this warp: drain the ones it did not see complete
+  if (lane == 0)
+    for (int ch = hi_done + 1; ch <= hi_issued; ++ch)
+      if (!mbar_drain(&bar[ch & 1], (uint32_t)((ch >> 1) & 1))) atomicOr(err, kErrDrain);
+}
+
+
+// ---------------------------------------------------------------------------
 // Local solves for wide bands (window up to 128, e.g. 3-D subdomains): one CTA
 // per (subdomain, shift) with one thread per window column (thread v owns
 // column v, slot u = row mod BMAX).  Per elimination
@@ -1602,7 +1731,8 @@ template <int BMAX>
 __global__ void __launch_bounds__(((BMAX + 31) / 32) * 32) k_local_band_team(
     int npairs, int k, const int64_t* __restrict__ sub_ptr, const int32_t* __restrict__ sub_dofs,
     const float* __restrict__ bandK, const float* __restrict__ bandM, const double* __restrict__ lam,
-    const double* __restrict__ rho, float* __restrict__ Lbuf, float* __restrict__ wpk, int32_t* err) {
+    const double* __restrict__ rho, float* __restrict__ Lbuf, float* __restrict__ wpk, int32_t* err,
+    int64_t rec_base) {
   constexpr int PD = 4;  // prefetch distance (steps) of the incoming band entries
   constexpr int PB = 4;  // prefetch distance (rows) of the backward substitution
   constexpr int NW = (BMAX + 31) / 32;
@@ -1620,7 +1750,7 @@ __global__ void __launch_bounds__(((BMAX + 31) / 32) * 32) k_local_band_team(
   const int nl = (int)(sub_ptr[l + 1] - off);
   const int32_t* dofs = sub_dofs + off;
   const float lm = (float)lam[i];
-  float* Lp = Lbuf + ((size_t)off * k + (size_t)i * nl) * BMAX;
+  float* Lp = Lbuf + ((size_t)(off - rec_base) * k + (size_t)i * nl) * BMAX;
   const float* gK = bandK + (size_t)off * BMAX;
   const float* gM = bandM + (size_t)off * BMAX;
   auto aval = [&](int p, int q) -> float {  // shifted entry (p, q), q <= p
@@ -1846,1088 +1976,6 @@ __global__ void k_prolong_add(int64_t n, int k, const int64_t* __restrict__ prp,
   for (int64_t e = prp[g]; e < prp[g + 1]; ++e) z = fma(pv[e], w0[(int64_t)pci[e] * k + i], z);
   for (int e = rtp[g]; e < rtp[g + 1]; ++e) z += (double)wpk[(int64_t)rtpos[e] * k + i];
   Z[t] = z;
-}
-
-// ---------------------------------------------------------------------------
-// Rayleigh-Ritz in W (one block, FP64).  Parallel cyclic Jacobi (round-robin
-// ordering) for the two small symmetric eigenproblems.
-// ---------------------------------------------------------------------------
-constexpr int kRRMax = 64;
-// leading dimension of the reduced matrices in shared memory: one more than the
-// size, so that column accesses fall into distinct banks
-constexpr int kRRLd = kRRMax + 1;
-
-// Symmetric eigen-decomposition of A (m x m, leading dimension ld = kRRLd) in
-// shared memory; V receives the eigenvectors (columns), A's diagonal the
-// eigenvalues.  mp = m rounded up to even (the extra index is a zero row/column
-// that never rotates).  Uses all threads of the block.
-__device__ void jacobi_eig(double* A, double* V, int m, double* cs, double* sn, int* pp, int* qq) {
-  const int mp = m + (m & 1);
-  const int ld = kRRLd;
-  const int tid = threadIdx.x;
-  for (int t = tid; t < mp * ld; t += blockDim.x) {
-    int r = t / ld, c = t % ld;
-    V[t] = (r == c) ? 1.0 : 0.0;
-    if ((r >= m || c >= m) && c < mp) A[t] = 0.0;
-  }
-  __syncthreads();
-  const int half = mp / 2;
-  __shared__ int done;
-  __shared__ double amax;
-  if (tid == 0) {
-    double a = 0;
-    for (int j = 0; j < m; ++j) a = fmax(a, fabs(A[j * ld + j]));
-    amax = a;
-  }
-  __syncthreads();
-  for (int sweep = 0; sweep < 60; ++sweep) {
-    if (tid == 0) done = 1;
-    __syncthreads();
-    for (int round = 0; round < mp - 1; ++round) {
-      if (tid < half) {
-        // circle method: position 0 fixed, the others rotate
-        int e0 = 0, e1;
-        auto ring = [&](int pos) { return ((pos + round) % (mp - 1)) + 1; };
-        if (tid == 0) {
-          e1 = ring(0);
-        } else {
-          e0 = ring(tid);
-          e1 = ring(mp - 1 - tid);
-        }
-        int p = min(e0, e1), q = max(e0, e1);
-        double apq = A[p * ld + q], app = A[p * ld + p], aqq = A[q * ld + q];
-        double c = 1.0, s = 0.0;
-        if (fabs(apq) > 1e-300 && fabs(apq) > 1e-17 * sqrt(fabs(app * aqq)) && fabs(apq) > 1e-30 * amax) {
-          double tau = (aqq - app) / (2.0 * apq);
-          double tt = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-          c = 1.0 / sqrt(1.0 + tt * tt);
-          s = tt * c;
-          done = 0;
-        }
-        cs[tid] = c;
-        sn[tid] = s;
-        pp[tid] = p;
-        qq[tid] = q;
-      }
-      __syncthreads();
-      // A <- A J and V <- V J (columns p, q of every pair)
-      for (int t = tid; t < half * mp; t += blockDim.x) {
-        int pr = t / mp, r = t % mp;
-        int p = pp[pr], q = qq[pr];
-        double c = cs[pr], s = sn[pr];
-        double ap = A[r * ld + p], aq = A[r * ld + q];
-        A[r * ld + p] = c * ap - s * aq;
-        A[r * ld + q] = s * ap + c * aq;
-        double vp = V[r * ld + p], vq = V[r * ld + q];
-        V[r * ld + p] = c * vp - s * vq;
-        V[r * ld + q] = s * vp + c * vq;
-      }
-      __syncthreads();
-      // A <- J^T A (rows p, q of every pair)
-      for (int t = tid; t < half * mp; t += blockDim.x) {
-        int pr = t / mp, col = t % mp;
-        int p = pp[pr], q = qq[pr];
-        double c = cs[pr], s = sn[pr];
-        double ap = A[p * ld + col], aq = A[q * ld + col];
-        A[p * ld + col] = c * ap - s * aq;
-        A[q * ld + col] = s * ap + c * aq;
-      }
-      __syncthreads();
-    }
-    if (done) break;
-    __syncthreads();
-  }
-}
-
-// Strict total order for ranking eigenvalues: NaN counts as +infinity and ties
-// go by index, so the ranks always form a permutation (the ranks index shared
-// memory, whatever the data).
-__device__ __forceinline__ bool order_before(double a, int ia, double b, int ib) {
-  a = isnan(a) ? CUDART_INF : a;
-  b = isnan(b) ? CUDART_INF : b;
-  return a < b || (a == b && ia < ib);
-}
-
-// Ascending order of diag(A)[0..m): ord[rank] = index (ties by index).
-__device__ void sort_diag(const double* A, int m, int* ord) {
-  const int ld = kRRLd;
-  for (int j = threadIdx.x; j < m; j += blockDim.x) {
-    double dj = A[j * ld + j];
-    int rank = 0;
-    for (int i = 0; i < m; ++i) {
-      if (order_before(A[i * ld + i], i, dj, j)) ++rank;
-    }
-    ord[rank] = j;
-  }
-  __syncthreads();
-}
-
-// G, H: m x m (row-major, ld m).  scale_all = 0: the first k columns of W are
-// M-orthonormal Ritz vectors and stay as they are, the rest are scaled to unit
-// M-norm; scale_all = 1: every column is scaled.  Output C (m x k, ld k),
-// lam_new (k), hist row, status.
-__device__ void rayleigh_ritz_eig(int m, int k, const double* __restrict__ G, const double* __restrict__ H,
-                                  double drop_tol, const double* __restrict__ lam_old, double* C, double* lam_new,
-                                  double* hist_row, int stop_rule, double tol, DevStatus* st, double* rr,
-                                  int scale_all) {
-  const int ld = kRRLd;
-  double* A = rr;                  // ld x ld
-  double* V = A + ld * ld;         // ld x ld
-  double* Bm = V + ld * ld;        // ld x ld : basis of the kept directions (m x r)
-  double* Hs = Bm + ld * ld;       // ld x ld : scaled H
-  double* sc = Hs + ld * ld;       // ld     : column scaling
-  double* cs = sc + ld;            // ld/2
-  double* sn = cs + ld;
-  int* pp = reinterpret_cast<int*>(sn + ld);
-  int* qq = pp + ld;
-  int* ord = qq + ld;
-  __shared__ int r_keep;
-  const int tid = threadIdx.x;
-  for (int j = tid; j < m; j += blockDim.x) {
-    double g = G[j * m + j];
-    sc[j] = (j < k && !scale_all) ? 1.0 : (g > 0 ? 1.0 / sqrt(g) : 0.0);
-  }
-  __syncthreads();
-  for (int t = tid; t < m * m; t += blockDim.x) {
-    int a = t / m, b = t % m;
-    double gs = 0.5 * (G[a * m + b] + G[b * m + a]) * sc[a] * sc[b];
-    double hs = 0.5 * (H[a * m + b] + H[b * m + a]) * sc[a] * sc[b];
-    A[a * ld + b] = gs;
-    Hs[a * ld + b] = hs;
-  }
-  __syncthreads();
-  jacobi_eig(A, V, m, cs, sn, pp, qq);
-  sort_diag(A, m, ord);
-  // keep eigen-directions of the scaled Gram matrix above drop_tol * max
-  if (tid == 0) {
-    double gmax = A[ord[m - 1] * ld + ord[m - 1]];
-    int r = 0;
-    for (int t = 0; t < m; ++t)
-      if (A[ord[t] * ld + ord[t]] > drop_tol * gmax) ++r;
-    r_keep = r;
-  }
-  __syncthreads();
-  const int r = r_keep;
-  const int first = m - r;  // kept = ord[first .. m)
-  // Bm[:, c] = V[:, ord[first + c]] / sqrt(g)
-  for (int t = tid; t < m * r; t += blockDim.x) {
-    int a = t / r, c = t % r;
-    int j = ord[first + c];
-    Bm[a * ld + c] = V[a * ld + j] / sqrt(A[j * ld + j]);
-  }
-  __syncthreads();
-  // V <- Hs Bm (m x r), then A <- Bm^T V (r x r)
-  for (int t = tid; t < m * r; t += blockDim.x) {
-    int a = t / r, c = t % r;
-    double s = 0;
-    for (int e = 0; e < m; ++e) s = fma(Hs[a * ld + e], Bm[e * ld + c], s);
-    V[a * ld + c] = s;
-  }
-  __syncthreads();
-  for (int t = tid; t < r * r; t += blockDim.x) {
-    int a = t / r, c = t % r;
-    double s = 0;
-    for (int e = 0; e < m; ++e) s = fma(Bm[e * ld + a], V[e * ld + c], s);
-    A[a * ld + c] = s;
-  }
-  __syncthreads();
-  for (int t = tid; t < r * r; t += blockDim.x) {
-    int a = t / r, c = t % r;
-    if (a < c) {
-      double s = 0.5 * (A[a * ld + c] + A[c * ld + a]);
-      A[a * ld + c] = s;
-      A[c * ld + a] = s;
-    }
-  }
-  __syncthreads();
-  jacobi_eig(A, V, r, cs, sn, pp, qq);
-  sort_diag(A, r, ord);
-  // C = diag(sc) Bm Y[:, 0..k)
-  const int kk = min(k, r);
-  for (int t = tid; t < m * k; t += blockDim.x) {
-    int a = t / k, c = t % k;
-    double s = 0;
-    if (c < kk) {
-      int j = ord[c];
-      for (int e = 0; e < r; ++e) s = fma(Bm[a * ld + e], V[e * ld + j], s);
-    }
-    C[a * k + c] = sc[a] * s;
-  }
-  __syncthreads();
-  if (tid == 0) {
-    double dl = 0;
-    for (int c = 0; c < k; ++c) {
-      double th = (c < kk) ? A[ord[c] * ld + ord[c]] : lam_old[c];
-      dl += fabs(th - lam_old[c]);
-      lam_new[c] = th;
-      if (hist_row) hist_row[c] = th;
-    }
-    st->sum_dl = dl;
-    st->kept = r;
-    if (r < k) st->err_breakdown = 1;
-    if (stop_rule == BPJD_STOP_DLAMBDA) st->converged = (dl < tol) ? 1 : 0;
-  }
-}
-
-// Parallel cyclic Jacobi, one pass per round: with the round's disjoint
-// rotations J, A' = J^T A J is formed element-wise from the old A (4 terms per
-// entry, lower triangle mirrored) into a second buffer, and V' = V J.
-// A, A2, V, V2 have leading dimension kRRLd; returns (via the buffers that end
-// up holding the result) pointers in *Aout / *Vout.
-__device__ int jacobi_eig_sym(double* A, double* A2, double* V, double* V2, int m, double** Aout, double** Vout,
-                              double* fr, double* gr, int* partner) {
-  const int mp = m + (m & 1);
-  const int ld = kRRLd;
-  const int tid = threadIdx.x;
-  __shared__ int done;
-  for (int t = tid; t < mp * ld; t += blockDim.x) {
-    int r = t / ld, c = t % ld;
-    V[t] = (r == c) ? 1.0 : 0.0;
-    if ((r >= m || c >= m) && c < mp) A[t] = 0.0;
-  }
-  __syncthreads();
-  const int half = mp / 2;
-  // lower-triangle index list (r >= c)
-  __shared__ unsigned char tri_r[kRRMax * (kRRMax + 1) / 2], tri_c[kRRMax * (kRRMax + 1) / 2];
-  if (tid == 0) {
-    int t = 0;
-    for (int r = 0; r < mp; ++r)
-      for (int c = 0; c <= r; ++c) {
-        tri_r[t] = (unsigned char)r;
-        tri_c[t] = (unsigned char)c;
-        ++t;
-      }
-  }
-  int sweep = 0;
-  for (; sweep < 60; ++sweep) {
-    if (tid == 0) done = 1;
-    __syncthreads();
-    for (int round = 0; round < mp - 1; ++round) {
-      if (tid < half) {
-        int e0 = 0, e1;
-        auto ring = [&](int pos) { return ((pos + round) % (mp - 1)) + 1; };
-        if (tid == 0) {
-          e1 = ring(0);
-        } else {
-          e0 = ring(tid);
-          e1 = ring(mp - 1 - tid);
-        }
-        const int p = min(e0, e1), q = max(e0, e1);
-        const double apq = A[p * ld + q], app = A[p * ld + p], aqq = A[q * ld + q];
-        double c = 1.0, s = 0.0;
-        if (fabs(apq) > 1e-300 && fabs(apq) > 1e-15 * sqrt(fabs(app * aqq))) {
-          const double tau = (aqq - app) / (2.0 * apq);
-          const double tt = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-          c = 1.0 / sqrt(1.0 + tt * tt);
-          s = tt * c;
-          done = 0;
-        }
-        // J[p][p] = c, J[q][p] = -s, J[p][q] = s, J[q][q] = c
-        fr[p] = c;
-        gr[p] = -s;
-        partner[p] = q;
-        fr[q] = c;
-        gr[q] = s;
-        partner[q] = p;
-      }
-      __syncthreads();
-      for (int t = tid; t < mp * (mp + 1) / 2; t += blockDim.x) {
-        const int r = tri_r[t], c = tri_c[t];
-        const int rb = partner[r], cb = partner[c];
-        const double v = fr[r] * (fr[c] * A[r * ld + c] + gr[c] * A[r * ld + cb]) +
-                         gr[r] * (fr[c] * A[rb * ld + c] + gr[c] * A[rb * ld + cb]);
-        A2[r * ld + c] = v;
-        A2[c * ld + r] = v;
-      }
-      for (int t = tid; t < mp * mp; t += blockDim.x) {
-        const int x = t / mp, r = t % mp;
-        V2[x * ld + r] = V[x * ld + r] * fr[r] + V[x * ld + partner[r]] * gr[r];
-      }
-      __syncthreads();
-      double* tA = A;
-      A = A2;
-      A2 = tA;
-      double* tV = V;
-      V = V2;
-      V2 = tV;
-    }
-    if (done) break;
-    __syncthreads();
-  }
-  *Aout = A;
-  *Vout = V;
-  return sweep + 1;
-}
-
-// Parallel cyclic Jacobi in double-word arithmetic (planes *h, *l of hi/lo
-// floats, leading dimension kRRLd).  The rotation angle of a pair is chosen
-// in FP32 (t = tan of the angle); c = 1 / sqrt(1 + t^2) and s = t c are then
-// formed in double-word precision (one Newton step on the FP32 estimate), so
-// every rotation is orthogonal to double-word accuracy and only its
-// annihilation of a_pq is approximate (relative 2^-24), which the next sweep
-// removes.  The two-sided update of a round is formed element-wise from the
-// old matrix (Dot2 accumulations) into the second buffer.  Returns sweeps.
-__device__ __forceinline__ dw dw_renorm(float s, float c) {
-  dw r;
-  fast_two_sum(s, c, r.hi, r.lo);
-  return r;
-}
-__device__ __forceinline__ dw dw_lin2(dw f1, float x1h, float x1l, dw f2, float x2h, float x2l) {
-  dot2 a;
-  a.zero();
-  a.mac(f1.hi, f1.lo, x1h, x1l);
-  a.mac(f2.hi, f2.lo, x2h, x2l);
-  return dw_renorm(a.s, a.c);
-}
-
-// Round-robin pairings of the parallel cyclic Jacobi (circle method), for
-// mp (even) indices: round r pairs index 0 with ring(0) and ring(i) with
-// ring(mp - 1 - i), ring(x) = (x + r) mod (mp - 1) + 1.  Written once per
-// solve into tp/tq[r half + i], i < half = mp / 2.
-__device__ void jacobi_pair_tables(int mp, unsigned char* tp, unsigned char* tq) {
-  const int half = mp / 2;
-  for (int t = threadIdx.x; t < (mp - 1) * half; t += blockDim.x) {
-    const int round = t / half, i = t % half;
-    auto ring = [&](int pos) { return ((pos + round) % (mp - 1)) + 1; };
-    const int e0 = (i == 0) ? 0 : ring(i);
-    const int e1 = (i == 0) ? ring(0) : ring(mp - 1 - i);
-    tp[t] = (unsigned char)min(e0, e1);
-    tq[t] = (unsigned char)max(e0, e1);
-  }
-}
-
-// Entry (r, c), c <= r, of the lower triangle with linear index t = r (r + 1) / 2 + c.
-__device__ __forceinline__ void tri_entry(int t, int& r, int& c) {
-  int rr = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
-  while (rr * (rr + 1) / 2 > t) --rr;
-  while ((rr + 1) * (rr + 2) / 2 <= t) ++rr;
-  r = rr;
-  c = t - rr * (rr + 1) / 2;
-}
-
-__device__ int jacobi_eig_dw(float* Ah, float* Al, float* A2h, float* A2l, float* Vh, float* Vl, float* V2h,
-                             float* V2l, int m, float** Aoh, float** Aol, float** Voh, float** Vol, dw* fr, dw* gr,
-                             int* partner) {
-  const int mp = m + (m & 1);
-  const int ld = kRRLd;
-  const int tid = threadIdx.x;
-  __shared__ int done;
-  __shared__ unsigned char tp[kRRMax * kRRMax / 2], tq[kRRMax * kRRMax / 2];
-  for (int t = tid; t < mp * ld; t += blockDim.x) {
-    const int r = t / ld, c = t % ld;
-    Vh[t] = (r == c) ? 1.f : 0.f;
-    Vl[t] = 0.f;
-    if ((r >= m || c >= m) && c < mp) {
-      Ah[t] = 0.f;
-      Al[t] = 0.f;
-    }
-  }
-  jacobi_pair_tables(mp, tp, tq);
-  // this thread's entries (the kernel runs 1024 threads): lower-triangle entries
-  // tid + u blockDim.x of A, entries tid + u blockDim.x of V
-  const int ntri = mp * (mp + 1) / 2;
-  int ar[3], ac[3];  // 3 x 1024 threads cover the 2080 entries of mp = 64
-  for (int u = 0; u < 3; ++u) {
-    const int t = tid + u * (int)blockDim.x;
-    if (t < ntri)
-      tri_entry(t, ar[u], ac[u]);
-    else
-      ar[u] = ac[u] = -1;
-  }
-  // rotation parameters of the current sweep (double-word), kept in the second V buffer
-  float* rcs = V2h;
-  float* rsn = V2l;
-  __shared__ float amax_d;
-  if (tid == 0) {
-    float a = 0.f;
-    for (int j = 0; j < m; ++j) a = fmaxf(a, fabsf(Ah[j * ld + j]));
-    amax_d = a;
-  }
-  __syncthreads();
-  // below the double-word noise of the largest diagonal entry an off-diagonal
-  // entry is left (its effect on the eigenpairs is below that noise)
-  const float abs_floor = 1e-14f * amax_d;
-  const int half = mp / 2;
-  int sweep = 0;
-  for (; sweep < 60; ++sweep) {
-    // a sweep runs only while some off-diagonal entry passes the rotation test
-    if (tid == 0) done = 1;
-    __syncthreads();
-#pragma unroll
-    for (int u = 0; u < 3; ++u) {
-      if (ar[u] < 0 || ar[u] == ac[u]) continue;
-      const float apq = Ah[ar[u] * ld + ac[u]] + Al[ar[u] * ld + ac[u]];
-      if (fabsf(apq) > abs_floor &&
-          fabsf(apq) > 1e-15f * __fsqrt_rn(fabsf(Ah[ar[u] * ld + ar[u]] * Ah[ac[u] * ld + ac[u]])))
-        done = 0;
-    }
-    __syncthreads();
-    if (done) break;
-    for (int round = 0; round < mp - 1; ++round) {
-      if (tid < half) {
-        const int p = tp[round * half + tid], q = tq[round * half + tid];
-        const float apq = Ah[p * ld + q] + Al[p * ld + q];
-        const float app = Ah[p * ld + p], aqq = Ah[q * ld + q];
-        dw c = {1.f, 0.f}, s = {0.f, 0.f};
-        if (fabsf(apq) > abs_floor && fabsf(apq) > 1e-15f * __fsqrt_rn(fabsf(app * aqq))) {
-          // the angle may be approximate; c and s below are orthogonal to double-word accuracy
-          const float tau = __fdividef(aqq - app, 2.f * apq);
-          const float t = __fdividef(tau >= 0.f ? 1.f : -1.f, fabsf(tau) + __fsqrt_rn(1.f + tau * tau));
-          // u = 1 + t^2 exactly in double-word
-          float ph, pe, uh, ue;
-          two_prod(t, t, ph, pe);
-          two_sum(1.f, ph, uh, ue);
-          dw u = dw_renorm(uh, __fadd_rn(ue, pe));
-          // c = u^{-1/2}: c0 = rsqrt(u.hi), r = 1 - u c0^2 (double-word), c = c0 + c0 r / 2
-          const float c0 = rsqrtf(u.hi);
-          float q1, q1e;
-          two_prod(c0, c0, q1, q1e);  // c0^2 = q1 + q1e exactly
-          dot2 acc;
-          acc.zero();
-          acc.add(1.f, 0.f);
-          acc.mac(-u.hi, -u.lo, q1, q1e);
-          const float r = acc.s + acc.c;
-          c = dw_renorm(c0, 0.5f * c0 * r);
-          // s = t c
-          float sh, se;
-          two_prod(t, c.hi, sh, se);
-          s = dw_renorm(sh, __fmaf_rn(t, c.lo, se));
-        }
-        fr[p] = c;
-        gr[p] = dw{-s.hi, -s.lo};
-        partner[p] = q;
-        fr[q] = c;
-        gr[q] = s;
-        partner[q] = p;
-        const int ri = round * half + tid;  // for the update of V after the sweep
-        rcs[2 * ri] = c.hi;
-        rcs[2 * ri + 1] = c.lo;
-        rsn[2 * ri] = s.hi;
-        rsn[2 * ri + 1] = s.lo;
-      }
-      __syncthreads();
-#pragma unroll
-      for (int u = 0; u < 3; ++u) {
-        if (ar[u] < 0) continue;
-        const int r = ar[u], c = ac[u];
-        const int rb = partner[r], cb = partner[c];
-        const dw i1 = dw_lin2(fr[c], Ah[r * ld + c], Al[r * ld + c], gr[c], Ah[r * ld + cb], Al[r * ld + cb]);
-        const dw i2 = dw_lin2(fr[c], Ah[rb * ld + c], Al[rb * ld + c], gr[c], Ah[rb * ld + cb], Al[rb * ld + cb]);
-        const dw v = dw_lin2(fr[r], i1.hi, i1.lo, gr[r], i2.hi, i2.lo);
-        A2h[r * ld + c] = v.hi;
-        A2l[r * ld + c] = v.lo;
-        A2h[c * ld + r] = v.hi;
-        A2l[c * ld + r] = v.lo;
-      }
-      __syncthreads();
-      float* t0 = Ah;
-      Ah = A2h;
-      A2h = t0;
-      t0 = Al;
-      Al = A2l;
-      A2l = t0;
-    }
-    // V <- V J_1 ... J_{mp-1}: a warp per row of V, one lane per rotation of a
-    // round (disjoint columns), rounds in order
-    for (int x = tid >> 5; x < mp; x += (int)blockDim.x >> 5) {
-      const int lane = tid & 31;
-      for (int round = 0; round < mp - 1; ++round) {
-        if (lane < half) {
-          const int ri = round * half + lane;
-          const int p = tp[ri], q = tq[ri];
-          const dw c = {rcs[2 * ri], rcs[2 * ri + 1]}, sn = {rsn[2 * ri], rsn[2 * ri + 1]};
-          const dw msn = {-sn.hi, -sn.lo};
-          const float vph = Vh[x * ld + p], vpl = Vl[x * ld + p], vqh = Vh[x * ld + q], vql = Vl[x * ld + q];
-          const dw np = dw_lin2(c, vph, vpl, msn, vqh, vql);
-          const dw nq = dw_lin2(c, vqh, vql, sn, vph, vpl);
-          Vh[x * ld + p] = np.hi;
-          Vl[x * ld + p] = np.lo;
-          Vh[x * ld + q] = nq.hi;
-          Vl[x * ld + q] = nq.lo;
-        }
-        __syncwarp();
-      }
-    }
-    __syncthreads();
-  }
-  *Aoh = Ah;
-  *Aol = Al;
-  *Voh = Vh;
-  *Vol = Vl;
-  return sweep;
-}
-
-// ---------------------------------------------------------------------------
-// Mixed-precision Rayleigh-Ritz solve of the scaled pencil (H', G') (FP64 in
-// Gd, Hd, leading dimension kRRLd):
-//  phase A (FP32): G' = L L^T, B = L^{-T}, Jacobi on B^T H' B, Q = B V
-//                  -- an approximate G'-orthonormal eigenbasis;
-//  phase B (double-word): G2 = Q^T G' Q = I + E, S = I - E/2 + 3E^2/8
-//                  ((I + E)^{-1/2} to O(E^3)), Q' = Q S, H3 = S^T Q^T H' Q S,
-//                  double-word Jacobi on the nearly diagonal H3 (Y), and the
-//                  Ritz basis Q' Y.
-// Returns false (nothing written) when the FP32 Cholesky fails or the Gram
-// matrix is too ill-conditioned for the series; the caller then takes the
-// eigen-based path.  Output: theta (ascending, m values) and the basis Ritz
-// vectors as FP64 in Cout (m x m, column j = j-th Ritz vector).
-// ---------------------------------------------------------------------------
-constexpr int kL = kRRMax * kRRLd;
-
-// C = op(A) * op(B) for m x m double-word matrices (hi/lo planes, ld kRRLd);
-// ta / tb: use the transpose.  B may be an FP32 matrix (Bl == nullptr).
-__device__ void dw_gemm(int m, const float* Ah, const float* Al, bool ta, const float* Bh, const float* Bl, bool tb,
-                        float* Ch, float* Cl) {
-  const int ld = kRRLd;
-  for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
-    const int i = t / m, j = t % m;
-    dot2 acc;
-    acc.zero();
-    for (int p = 0; p < m; ++p) {
-      const int ia = ta ? p * ld + i : i * ld + p;
-      const int ib = tb ? j * ld + p : p * ld + j;
-      acc.mac(Ah[ia], Al ? Al[ia] : 0.f, Bh[ib], Bl ? Bl[ib] : 0.f);
-    }
-    dw r;
-    fast_two_sum(acc.s, acc.c, r.hi, r.lo);
-    Ch[i * ld + j] = r.hi;
-    Cl[i * ld + j] = r.lo;
-  }
-  __syncthreads();
-}
-
-// FP32 parallel cyclic Jacobi (same ordering as the double-word version).
-__device__ int jacobi_f32(float* A, float* A2, float* V, float* V2, int m, float** Aout, float** Vout, float* fr,
-                          float* gr, int* partner, float off_tol) {
-  const int mp = m + (m & 1);
-  const int ld = kRRLd;
-  const int tid = threadIdx.x;
-  __shared__ int done;
-  __shared__ unsigned char tp[kRRMax * kRRMax / 2], tq[kRRMax * kRRMax / 2];
-  for (int t = tid; t < mp * ld; t += blockDim.x) {
-    const int r = t / ld, c = t % ld;
-    V[t] = (r == c) ? 1.f : 0.f;
-    if ((r >= m || c >= m) && c < mp) A[t] = 0.f;
-  }
-  jacobi_pair_tables(mp, tp, tq);
-  const int ntri = mp * (mp + 1) / 2;
-  int ar[3], ac[3];  // 3 x 1024 threads cover the 2080 entries of mp = 64
-  for (int u = 0; u < 3; ++u) {
-    const int t = tid + u * (int)blockDim.x;
-    if (t < ntri)
-      tri_entry(t, ar[u], ac[u]);
-    else
-      ar[u] = ac[u] = -1;
-  }
-  // rotation parameters of the current sweep, kept in the second V buffer
-  float* rc = V2;
-  float* rs = V2 + kRRMax * kRRMax / 2;
-  __syncthreads();
-  const int half = mp / 2;
-  __shared__ float amax_f;
-  if (tid == 0) {
-    float a = 0.f;
-    for (int j = 0; j < m; ++j) a = fmaxf(a, fabsf(A[j * ld + j]));
-    amax_f = a;
-  }
-  __syncthreads();
-  // off-diagonal entries below the FP32 noise of the largest diagonal entry are left
-  const float abs_floor = 1e-6f * amax_f;
-  int sweep = 0;
-  for (; sweep < 30; ++sweep) {
-    // a sweep runs only while some off-diagonal entry passes the rotation test
-    if (tid == 0) done = 1;
-    __syncthreads();
-#pragma unroll
-    for (int u = 0; u < 3; ++u) {
-      if (ar[u] < 0 || ar[u] == ac[u]) continue;
-      const float apq = A[ar[u] * ld + ac[u]];
-      if (fabsf(apq) > abs_floor &&
-          fabsf(apq) > off_tol * __fsqrt_rn(fabsf(A[ar[u] * ld + ar[u]] * A[ac[u] * ld + ac[u]])))
-        done = 0;
-    }
-    __syncthreads();
-    if (done) break;
-    for (int round = 0; round < mp - 1; ++round) {
-      if (tid < half) {
-        const int p = tp[round * half + tid], q = tq[round * half + tid];
-        const float apq = A[p * ld + q], app = A[p * ld + p], aqq = A[q * ld + q];
-        float c = 1.f, s = 0.f;
-        if (fabsf(apq) > abs_floor && fabsf(apq) > off_tol * __fsqrt_rn(fabsf(app * aqq))) {
-          // approximate angle (fast intrinsics): phase B restores exact orthogonality
-          const float tau = __fdividef(aqq - app, 2.f * apq);
-          const float t = __fdividef(tau >= 0.f ? 1.f : -1.f, fabsf(tau) + __fsqrt_rn(1.f + tau * tau));
-          c = rsqrtf(1.f + t * t);
-          s = t * c;
-        }
-        fr[p] = c;
-        gr[p] = -s;
-        partner[p] = q;
-        fr[q] = c;
-        gr[q] = s;
-        partner[q] = p;
-        rc[round * half + tid] = c;  // for the update of V after the sweep
-        rs[round * half + tid] = s;
-      }
-      __syncthreads();
-#pragma unroll
-      for (int u = 0; u < 3; ++u) {
-        if (ar[u] < 0) continue;
-        const int r = ar[u], c = ac[u];
-        const int rb = partner[r], cb = partner[c];
-        const float v = fr[r] * (fr[c] * A[r * ld + c] + gr[c] * A[r * ld + cb]) +
-                        gr[r] * (fr[c] * A[rb * ld + c] + gr[c] * A[rb * ld + cb]);
-        A2[r * ld + c] = v;
-        A2[c * ld + r] = v;
-      }
-      __syncthreads();
-      float* tA = A;
-      A = A2;
-      A2 = tA;
-    }
-    // V <- V J_1 ... J_{mp-1}: a warp per row of V, one lane per rotation of a
-    // round (disjoint columns), rounds in order
-    for (int x = tid >> 5; x < mp; x += (int)blockDim.x >> 5) {
-      const int lane = tid & 31;
-      for (int round = 0; round < mp - 1; ++round) {
-        if (lane < half) {
-          const int p = tp[round * half + lane], q = tq[round * half + lane];
-          const float c = rc[round * half + lane], sn = rs[round * half + lane];
-          const float vp = V[x * ld + p], vq = V[x * ld + q];
-          V[x * ld + p] = c * vp - sn * vq;
-          V[x * ld + q] = sn * vp + c * vq;
-        }
-        __syncwarp();
-      }
-    }
-    __syncthreads();
-  }
-  *Aout = A;
-  *Vout = V;
-  return sweep;
-}
-
-// G, H: the unscaled Gram matrices (FP64, m x m, ld m); sc: column scaling.
-// pool: 12 slots of kL floats.  theta: kRRMax doubles (ascending Ritz values on
-// return); fr/gr/partner/ord: kRRMax entries each (fr, gr 8 bytes per entry).
-// Writes C = diag(sc) Q' Y[:, lowest k] (m x k, ld k).  Returns the number of
-// double-word Jacobi sweeps, or -1 (nothing written).
-__device__ int rr_mixed_solve(int m, int k, const double* __restrict__ G, const double* __restrict__ H,
-                              const double* sc, float* pool, double* theta, double* C, double* fr, double* gr,
-                              int* partner, int* ord, double drop_tol, long long* cyc) {
-  const int ld = kRRLd;
-  const int tid = threadIdx.x;
-  float* s[12];
-  for (int i = 0; i < 12; ++i) s[i] = pool + (size_t)i * kL;
-  __shared__ int ok;
-  float *Gh = s[0], *Gl = s[1], *Hh = s[2], *Hl = s[3];
-  for (int t = tid; t < m * m; t += blockDim.x) {
-    const int a = t / m, b = t % m;
-    const double gs = 0.5 * (G[a * m + b] + G[b * m + a]) * sc[a] * sc[b];
-    const double hs = 0.5 * (H[a * m + b] + H[b * m + a]) * sc[a] * sc[b];
-    const dw g = split_f64(gs), hh = split_f64(hs);
-    Gh[a * ld + b] = g.hi;
-    Gl[a * ld + b] = g.lo;
-    Hh[a * ld + b] = hh.hi;
-    Hl[a * ld + b] = hh.lo;
-  }
-  if (tid == 0) ok = 1;
-  __syncthreads();
-  long long t0 = clock64();
-  // ---- phase A (FP32)
-  float *L = s[4], *Li = s[5], *T32 = s[6];
-  for (int t = tid; t < m * m; t += blockDim.x) L[(t / m) * ld + (t % m)] = Gh[(t / m) * ld + (t % m)];
-  __syncthreads();
-  for (int j = 0; j < m; ++j) {
-    if (tid == 0) {
-      const float d = L[j * ld + j];
-      if (!(d > 0.f)) ok = 0;
-      L[j * ld + j] = (d > 0.f) ? sqrtf(d) : 1.f;
-    }
-    __syncthreads();
-    const float ljj = L[j * ld + j];
-    for (int i = j + 1 + tid; i < m; i += blockDim.x) L[i * ld + j] /= ljj;
-    __syncthreads();
-    const int rem = m - j - 1;
-    for (int t = tid; t < rem * rem; t += blockDim.x) {
-      const int i = j + 1 + t / rem, c = j + 1 + t % rem;
-      if (c <= i) L[i * ld + c] -= L[i * ld + j] * L[c * ld + j];
-    }
-    __syncthreads();
-  }
-  for (int c = tid; c < m; c += blockDim.x)
-    for (int i = 0; i < m; ++i) {
-      float v = 0.f;
-      if (i >= c) {
-        v = (i == c) ? 1.f : 0.f;
-        for (int t = c; t < i; ++t) v -= L[i * ld + t] * Li[t * ld + c];
-        v /= L[i * ld + i];
-      }
-      Li[i * ld + c] = v;
-    }
-  __syncthreads();
-  if (tid == 0) {
-    float f = 0.f, tr = 0.f;
-    for (int i = 0; i < m; ++i) {
-      tr += Gh[i * ld + i];
-      for (int c = 0; c <= i; ++c) f += Li[i * ld + c] * Li[i * ld + c];
-    }
-    // 1 / ||L^{-1}||_F^2 <= lambda_min(G'): keep a margin over the drop threshold
-    // (so the eigen-based basis would drop nothing) and over the conditioning
-    // that the FP32 basis and the series of phase B resolve
-    if (!(1.f / f > (float)(drop_tol * 10.0) * tr) || !(1.f / f > 1e-4f * tr)) ok = 0;
-  }
-  __syncthreads();
-  if (!ok) return -1;
-  long long t1 = clock64();
-  float* A = s[7];
-  for (int t = tid; t < m * m; t += blockDim.x) {
-    const int a = t / m, b = t % m;
-    float v = 0.f;
-    for (int c = 0; c <= b; ++c) v += Hh[a * ld + c] * Li[b * ld + c];
-    T32[a * ld + b] = v;
-  }
-  __syncthreads();
-  for (int t = tid; t < m * m; t += blockDim.x) {
-    const int a = t / m, b = t % m;
-    float v = 0.f;
-    for (int c = 0; c <= a; ++c) v += Li[a * ld + c] * T32[c * ld + b];
-    A[a * ld + b] = v;
-  }
-  __syncthreads();
-  for (int t = tid; t < m * m; t += blockDim.x) {
-    const int a = t / m, b = t % m;
-    if (a < b) {
-      const float v = 0.5f * (A[a * ld + b] + A[b * ld + a]);
-      A[a * ld + b] = v;
-      A[b * ld + a] = v;
-    }
-  }
-  __syncthreads();
-  float *Ar, *Vr;
-  const int sw32 = jacobi_f32(A, s[8], s[9], s[10], m, &Ar, &Vr, reinterpret_cast<float*>(fr),
-                             reinterpret_cast<float*>(gr), partner, 1e-5f);
-  long long t2 = clock64();
-  float* Q = s[11];
-  for (int t = tid; t < m * m; t += blockDim.x) {
-    const int a = t / m, b = t % m;
-    float v = 0.f;
-    for (int c = a; c < m; ++c) v += Li[c * ld + a] * Vr[c * ld + b];
-    Q[a * ld + b] = v;
-  }
-  __syncthreads();
-  // ---- phase B (double-word)
-  float *T1h = s[4], *T1l = s[5], *G2h = s[6], *G2l = s[7], *H2h = s[8], *H2l = s[9];
-  dw_gemm(m, Gh, Gl, false, Q, nullptr, false, T1h, T1l);   // G' Q
-  dw_gemm(m, Q, nullptr, true, T1h, T1l, false, G2h, G2l);  // Q^T G' Q
-  dw_gemm(m, Hh, Hl, false, Q, nullptr, false, T1h, T1l);   // H' Q
-  dw_gemm(m, Q, nullptr, true, T1h, T1l, false, H2h, H2l);  // Q^T H' Q
-  for (int t = tid; t < m; t += blockDim.x) {              // E = G2 - I
-    float hi, lo;
-    two_sum(G2h[t * ld + t], -1.f, hi, lo);
-    const dw e = dw_renorm(hi, __fadd_rn(lo, G2l[t * ld + t]));
-    G2h[t * ld + t] = e.hi;
-    G2l[t * ld + t] = e.lo;
-  }
-  __syncthreads();
-  dw_gemm(m, G2h, G2l, false, G2h, G2l, false, T1h, T1l);  // E^2
-  float *Sh = s[0], *Sl = s[1];
-  for (int t = tid; t < m * m; t += blockDim.x) {         // S = I - E/2 + 3 E^2 / 8
-    const int a = t / m, b = t % m;
-    dot2 acc;
-    acc.zero();
-    if (a == b) acc.add(1.f, 0.f);
-    acc.mac(-0.5f, 0.f, G2h[a * ld + b], G2l[a * ld + b]);
-    acc.mac(0.375f, 0.f, T1h[a * ld + b], T1l[a * ld + b]);
-    const dw r = dw_renorm(acc.s, acc.c);
-    Sh[a * ld + b] = r.hi;
-    Sl[a * ld + b] = r.lo;
-  }
-  __syncthreads();
-  dw_gemm(m, H2h, H2l, false, Sh, Sl, false, T1h, T1l);    // H2 S
-  float *H3h = s[2], *H3l = s[3];
-  dw_gemm(m, Sh, Sl, true, T1h, T1l, false, H3h, H3l);     // S^T H2 S
-  for (int t = tid; t < m * m; t += blockDim.x) {
-    const int a = t / m, b = t % m;
-    if (a < b) {
-      dot2 acc;
-      acc.zero();
-      acc.add(H3h[a * ld + b], H3l[a * ld + b]);
-      acc.add(H3h[b * ld + a], H3l[b * ld + a]);
-      const dw r = dw_renorm(0.5f * acc.s, 0.5f * acc.c);
-      H3h[a * ld + b] = r.hi;
-      H3l[a * ld + b] = r.lo;
-      H3h[b * ld + a] = r.hi;
-      H3l[b * ld + a] = r.lo;
-    }
-  }
-  __syncthreads();
-  float *Qph = s[6], *Qpl = s[7];
-  dw_gemm(m, Q, nullptr, false, Sh, Sl, false, Qph, Qpl);  // Q' = Q S
-  long long t3 = clock64();
-  float *Arh, *Arl, *Vrh, *Vrl;
-  const int sw = jacobi_eig_dw(H3h, H3l, s[8], s[9], s[4], s[5], s[0], s[1], m, &Arh, &Arl, &Vrh, &Vrl,
-                               reinterpret_cast<dw*>(fr), reinterpret_cast<dw*>(gr), partner);
-  __syncthreads();
-  long long t4 = clock64();
-  for (int j = tid; j < m; j += blockDim.x) theta[j] = dw_to_f64(Arh[j * ld + j], Arl[j * ld + j]);
-  __syncthreads();
-  for (int j = tid; j < m; j += blockDim.x) {
-    const double tj = theta[j];
-    int rank = 0;
-    for (int i2 = 0; i2 < m; ++i2) {
-      rank += order_before(theta[i2], i2, tj, j) ? 1 : 0;
-    }
-    ord[rank] = j;
-  }
-  __syncthreads();
-  for (int t = tid; t < m * k; t += blockDim.x) {
-    const int a = t / k, c = t % k;
-    const int j = ord[c];
-    dot2 acc;
-    acc.zero();
-    for (int p = 0; p < m; ++p) acc.mac(Qph[a * ld + p], Qpl[a * ld + p], Vrh[p * ld + j], Vrl[p * ld + j]);
-    C[a * k + c] = sc[a] * acc.value();
-  }
-  __syncthreads();
-  if (tid == 0 && cyc) {
-    const long long t5 = clock64();
-    cyc[0] = t1 - t0;
-    cyc[1] = t2 - t1;
-    cyc[2] = t3 - t2;
-    cyc[3] = t4 - t3;
-    cyc[4] = t5 - t4;
-    cyc[5] = sw32 * 1000;
-  }
-  return sw;
-}
-
-// Rayleigh-Ritz (Eq. (3.6)) with a Cholesky orthonormalisation of the scaled
-// Gram matrix G' = L L^T.  When the lower bound 1 / ||L^{-1}||_F^2 of the
-// smallest eigenvalue of G' exceeds drop_tol * trace(G') >= drop_tol * lambda_max,
-// the eigen-based basis of k_rayleigh_ritz would keep every direction, so both
-// produce the Ritz pairs of the same space; the reduced matrix
-// H'' = L^{-1} H' L^{-T} is diagonalised by one symmetric Jacobi.  Otherwise the
-// eigen-based path with dropping runs.
-__global__ void k_rayleigh_ritz_chol(int m, int k, const double* __restrict__ G, const double* __restrict__ H,
-                                     double drop_tol, const double* __restrict__ lam_old, double* C,
-                                     double* lam_new, double* hist_row, int stop_rule, double tol, DevStatus* st,
-                                     int dword) {
-  extern __shared__ double rr[];
-  const int ld = kRRLd;
-  const int LL = ld * ld;
-  double* B0 = rr;
-  double* B1 = B0 + LL;
-  double* B2 = B1 + LL;
-  double* B3 = B2 + LL;
-  double* B4 = B3 + LL;
-  double* sc = B4 + 2 * LL;  // B5 (one more slot) belongs to the mixed-precision pool
-  double* fr = sc + ld;
-  double* gr = fr + ld;
-  int* partner = reinterpret_cast<int*>(gr + ld);
-  int* ord = partner + ld;
-  __shared__ int ok;
-  __shared__ double crit_lhs, crit_rhs;
-  const int tid = threadIdx.x;
-  long long tcl[8];
-  tcl[0] = clock64();
-  for (int j = tid; j < m; j += blockDim.x) {
-    const double g = G[j * m + j];
-    // the FP64 path keeps the first k columns (the iterate, M-orthonormal) as they
-    // are; the mixed path scales every column, its iterate block being the last
-    sc[j] = (j < k && !dword) ? 1.0 : (g > 0 ? 1.0 / sqrt(g) : 0.0);
-  }
-  if (tid == 0) ok = 1;
-  __syncthreads();
-  if (dword) {
-    double* theta = sc + ld;  // fr and gr are workspace of the solve
-    __shared__ double th_s[kRRMax];
-    const int sw = rr_mixed_solve(m, k, G, H, sc, reinterpret_cast<float*>(rr), th_s, C, fr, gr, partner, ord,
-                                  drop_tol, st->rr_cycles);
-    (void)theta;
-    if (sw >= 0) {
-      if (tid == 0) {
-        double dl = 0;
-        for (int c = 0; c < k; ++c) {
-          const double th = th_s[ord[c]];
-          dl += fabs(th - lam_old[c]);
-          lam_new[c] = th;
-          if (hist_row) hist_row[c] = th;
-        }
-        st->sum_dl = dl;
-        st->kept = m;
-        st->sweeps = sw;
-        if (stop_rule == BPJD_STOP_DLAMBDA) st->converged = (dl < tol) ? 1 : 0;
-        st->rr_cycles[6] = clock64() - tcl[0];  // the whole kernel body
-      }
-      return;
-    }
-    // ill-conditioned: eigen-based orthonormalisation with dropping
-    rayleigh_ritz_eig(m, k, G, H, drop_tol, lam_old, C, lam_new, hist_row, stop_rule, tol, st, rr, dword);
-    return;
-  }
-  // B0 = G' (becomes L), B1 = H'
-  for (int t = tid; t < m * m; t += blockDim.x) {
-    const int a = t / m, b = t % m;
-    B0[a * ld + b] = 0.5 * (G[a * m + b] + G[b * m + a]) * sc[a] * sc[b];
-    B1[a * ld + b] = 0.5 * (H[a * m + b] + H[b * m + a]) * sc[a] * sc[b];
-  }
-  __syncthreads();
-  if (tid == 0) {
-    double tr = 0;
-    for (int j = 0; j < m; ++j) tr += B0[j * ld + j];
-    crit_rhs = drop_tol * tr;
-  }
-  tcl[1] = clock64();
-  // right-looking Cholesky in place (lower triangle)
-  for (int j = 0; j < m; ++j) {
-    if (tid == 0) {
-      const double d = B0[j * ld + j];
-      if (!(d > 0.0)) ok = 0;
-      B0[j * ld + j] = (d > 0.0) ? sqrt(d) : 1.0;
-    }
-    __syncthreads();
-    const double ljj = B0[j * ld + j];
-    for (int i = j + 1 + tid; i < m; i += blockDim.x) B0[i * ld + j] /= ljj;
-    __syncthreads();
-    const int rem = m - j - 1;
-    for (int t = tid; t < rem * rem; t += blockDim.x) {
-      const int i = j + 1 + t / rem, c = j + 1 + t % rem;
-      if (c <= i) B0[i * ld + c] -= B0[i * ld + j] * B0[c * ld + j];
-    }
-    __syncthreads();
-  }
-  tcl[2] = clock64();
-  // B2 = L^{-1}: row i of L^{-1} from rows < i, all columns of a row in parallel;
-  // the dot products run as double-word Dot2 sums (FP64 dependency chains are
-  // long-latency on this GPU)
-  {
-    double* dinv = B3;  // reciprocal diagonal of L
-    for (int i = tid; i < m; i += blockDim.x) dinv[i] = 1.0 / B0[i * ld + i];
-    __syncthreads();
-    for (int i = 0; i < m; ++i) {
-      for (int c = tid; c < m; c += blockDim.x) {
-        double v = 0.0;
-        if (c == i) {
-          v = dinv[i];
-        } else if (c < i) {
-          dot2 acc;
-          acc.zero();
-          for (int t = c; t < i; ++t) {
-            const dw l = split_f64(B0[i * ld + t]);
-            const dw x = split_f64(B2[t * ld + c]);
-            acc.mac(l.hi, l.lo, x.hi, x.lo);
-          }
-          v = -acc.value() * dinv[i];
-        }
-        B2[i * ld + c] = v;
-      }
-      __syncthreads();
-    }
-  }
-  if (tid == 0) {
-    double f = 0;
-    for (int i = 0; i < m; ++i)
-      for (int c = 0; c <= i; ++c) f += B2[i * ld + c] * B2[i * ld + c];
-    crit_lhs = 1.0 / f;
-    if (!(crit_lhs > crit_rhs)) ok = 0;
-  }
-  __syncthreads();
-  if (!ok) {
-    // ill-conditioned basis: eigen-based orthonormalisation with dropping
-    rayleigh_ritz_eig(m, k, G, H, drop_tol, lam_old, C, lam_new, hist_row, stop_rule, tol, st, rr, dword);
-    return;
-  }
-  tcl[3] = clock64();
-  // B3 = H' L^{-T};  B4 = L^{-1} B3  (= H'')
-  for (int t = tid; t < m * m; t += blockDim.x) {
-    const int a = t / m, b = t % m;
-    double s = 0;
-    for (int c = 0; c <= b; ++c) s = fma(B1[a * ld + c], B2[b * ld + c], s);
-    B3[a * ld + b] = s;
-  }
-  __syncthreads();
-  for (int t = tid; t < m * m; t += blockDim.x) {
-    const int a = t / m, b = t % m;
-    if (a < b) continue;
-    double s = 0;
-    for (int c = 0; c <= a; ++c) s = fma(B2[a * ld + c], B3[c * ld + b], s);
-    B4[a * ld + b] = s;
-  }
-  __syncthreads();
-  for (int t = tid; t < m * m; t += blockDim.x) {
-    const int a = t / m, b = t % m;
-    if (a < b) B4[a * ld + b] = B4[b * ld + a];
-  }
-  __syncthreads();
-  tcl[4] = clock64();
-  int nsweeps = 0;
-  const double* Vd = nullptr;  // FP64 eigenvectors (native path)
-  float *Vrh = nullptr, *Vrl = nullptr;
-  if (!dword) {
-    double* Ar;
-    double* Vr;
-    nsweeps = jacobi_eig_sym(B4, B0, B1, B3, m, &Ar, &Vr, fr, gr, partner);
-    for (int j = tid; j < m; j += blockDim.x) fr[j] = Ar[j * ld + j];
-    Vd = Vr;
-  } else {
-    // double-word Jacobi: A planes in B0, A2 in B1, V in B3, V2 in B4 (after
-    // H'' has been split out of B4); B2 = L^{-1} is kept
-    float* Ah = reinterpret_cast<float*>(B0);
-    float* Al = Ah + LL;
-    for (int t = tid; t < m * m; t += blockDim.x) {
-      const int a = t / m, b = t % m;
-      const dw sp = split_f64(B4[a * ld + b]);
-      Ah[a * ld + b] = sp.hi;
-      Al[a * ld + b] = sp.lo;
-    }
-    __syncthreads();
-    float *Arh, *Arl;
-    nsweeps = jacobi_eig_dw(Ah, Al, reinterpret_cast<float*>(B1), reinterpret_cast<float*>(B1) + LL,
-                            reinterpret_cast<float*>(B3), reinterpret_cast<float*>(B3) + LL,
-                            reinterpret_cast<float*>(B4), reinterpret_cast<float*>(B4) + LL, m, &Arh, &Arl, &Vrh,
-                            &Vrl, reinterpret_cast<dw*>(fr), reinterpret_cast<dw*>(gr), partner);
-    __syncthreads();
-    for (int j = tid; j < m; j += blockDim.x) fr[j] = dw_to_f64(Arh[j * ld + j], Arl[j * ld + j]);
-  }
-  tcl[5] = clock64();
-  __syncthreads();
-  // ascending order of the eigenvalues (ties by index), one rank per thread
-  for (int j = tid; j < m; j += blockDim.x) {
-    const double fj = fr[j];
-    int rank = 0;
-    for (int i2 = 0; i2 < m; ++i2) {
-      rank += order_before(fr[i2], i2, fj, j) ? 1 : 0;
-    }
-    ord[rank] = j;
-  }
-  __syncthreads();
-  auto yv = [&](int b, int j) -> double {
-    return Vd ? Vd[b * ld + j] : dw_to_f64(Vrh[b * ld + j], Vrl[b * ld + j]);
-  };
-  // C = diag(sc) L^{-T} Y[:, 0..k)
-  for (int t = tid; t < m * k; t += blockDim.x) {
-    const int a = t / k, c = t % k;
-    const int j = ord[c];
-    double s = 0;
-    for (int b = a; b < m; ++b) s = fma(B2[b * ld + a], yv(b, j), s);
-    C[a * k + c] = sc[a] * s;
-  }
-  __syncthreads();
-  if (tid == 0) {
-    double dl = 0;
-    for (int c = 0; c < k; ++c) {
-      const double th = fr[ord[c]];
-      dl += fabs(th - lam_old[c]);
-      lam_new[c] = th;
-      if (hist_row) hist_row[c] = th;
-    }
-    st->sum_dl = dl;
-    st->kept = m;
-    st->sweeps = nsweeps;
-    tcl[6] = clock64();
-    for (int q = 0; q < 6; ++q) st->rr_cycles[q] = tcl[q + 1] - tcl[q];
-    if (stop_rule == BPJD_STOP_DLAMBDA) st->converged = (dl < tol) ? 1 : 0;
-  }
 }
 
 // ---------------------------------------------------------------------------
@@ -3424,81 +2472,127 @@ int launch_combine_rows(Handle& h, int nin, const double* const* Win, const doub
   return (int)cudaGetLastError();
 }
 
-int launch_precond(Handle& h, const double* rho, const double* lam, double* Z) {
+bool can_reuse_factors(const Handle& h) {
+  if (!h.local_f32() || h.chunk_l0.size() != 2) return false;
+  switch (h.Bpad) {
+    case 16: case 24: case 32: case 40: case 48: case 64: case 96: case 152: return true;
+    default: return false;
+  }
+}
+
+int launch_precond(Handle& h, const double* rho, const double* lam, double* Z, int reuse) {
   const int k = h.k;
-  const int npairs = h.nsub * k;
   const int B = h.B;
-  // local band solves
+  if (reuse && can_reuse_factors(h)) {
+    // forward and backward sweeps with the stored factors
+    ProfScope ps(h, BPJD_PROF_LOCAL);
+    const int nsub = h.nsub;
+    const int bwd_blocks = (nsub * ((k + 3) / 4) + 1) / 2;
+    h.launches += 2;
+    auto sweeps = [&](auto bm) {
+      constexpr int BM = decltype(bm)::value;
+      const size_t bsm = sizeof(float) * BwdShape<BM>::smem_floats;
+      allow_dynamic_smem((const void*)k_local_forward<BM>);
+      k_local_forward<BM><<<bwd_blocks, 32 * BwdShape<BM>::WPB, bsm, h.stream>>>(
+          nsub, k, h.sub_ptr, h.sub_dofs, rho, (const float*)h.Lbuf, (float*)h.wpk, h.derr, h.wait_limit, 0);
+      allow_dynamic_smem((const void*)k_local_backward<BM>);
+      k_local_backward<BM><<<bwd_blocks, 32 * BwdShape<BM>::WPB, bsm, h.stream>>>(
+          nsub, k, h.sub_ptr, (const float*)h.Lbuf, (float*)h.wpk, h.derr, h.wait_limit, 0);
+    };
+    switch (h.Bpad) {
+      case 16: sweeps(std::integral_constant<int, 16>()); break;
+      case 24: sweeps(std::integral_constant<int, 24>()); break;
+      case 32: sweeps(std::integral_constant<int, 32>()); break;
+      case 40: sweeps(std::integral_constant<int, 40>()); break;
+      case 48: sweeps(std::integral_constant<int, 48>()); break;
+      case 64: sweeps(std::integral_constant<int, 64>()); break;
+      case 96: sweeps(std::integral_constant<int, 96>()); break;
+      case 152: sweeps(std::integral_constant<int, 152>()); break;
+      default: return (int)cudaErrorInvalidValue;
+    }
+    ++h.reuses;
+  } else {
+    ++h.refactorisations;
+  // local band solves, chunk by chunk of subdomains (the factor records of one
+  // chunk fit the record scratch)
   {
     ProfScope ps(h, BPJD_PROF_LOCAL);
     const bool f32 = h.local_f32();
-    h.launches += (f32 && h.Bpad > 0 && h.Bpad != 128) ? 2 : 1;  // factorisation + backward substitution
-    if (f32 && h.Bpad > 0) {
-      const int blocks = h.nsub * ((k + kLocalWarps - 1) / kLocalWarps);
+    const int nchunks = (int)h.chunk_l0.size() - 1;
+    for (int ch = 0; ch < nchunks; ++ch) {
+      const int l0 = h.chunk_l0[ch];
+      const int nsub = h.chunk_l0[ch + 1] - l0;
+      const int64_t* sptr = h.sub_ptr + l0;
+      const int64_t rec_base = h.chunk_off[ch];
+      const int npairs_c = nsub * k;
+      h.launches += (f32 && h.Bpad > 0 && h.Bpad != 128) ? 2 : 1;  // factorisation + backward substitution
+      if (f32 && h.Bpad > 0) {
+        const int blocks = nsub * ((k + kLocalWarps - 1) / kLocalWarps);
+        const int bwd_blocks = (nsub * ((k + 3) / 4) + 1) / 2;
 #define BPJD_LOCAL_TILE(BM)                                                                                    \
   case BM: {                                                                                                   \
     const size_t sm = sizeof(float) * MmaShape<BM>::smem_floats;                                               \
-    allow_dynamic_smem((const void*)k_local_factor_mma<BM>);       \
-    k_local_factor_mma<BM><<<blocks, 32 * kLocalWarps, sm, h.stream>>>(h.nsub, k, h.sub_ptr, h.sub_dofs,       \
-                                                                       h.bandKf, h.bandMf, lam, rho,           \
-                                                                       (float*)h.Lbuf, (float*)h.wpk,          \
-                                                                       h.derr, h.wait_limit);                  \
-    {                                                                                                          \
-      const size_t bsm = sizeof(float) * BwdShape<BM>::smem_floats;                                            \
-      allow_dynamic_smem((const void*)k_local_backward<BM>);       \
-      k_local_backward<BM><<<bwd_blocks, 32 * BwdShape<BM>::WPB, bsm, h.stream>>>(                             \
-          h.nsub, k, h.sub_ptr, (const float*)h.Lbuf, (float*)h.wpk, h.derr, h.wait_limit);                    \
-    }                                                                                                          \
-    break;                                                                                                     \
-  }
-      const int bwd_blocks = (h.nsub * ((k + 3) / 4) + 1) / 2;
-      switch (h.Bpad) {
-        BPJD_LOCAL_TILE(16)
-        BPJD_LOCAL_TILE(24)
-        BPJD_LOCAL_TILE(32)
-        BPJD_LOCAL_TILE(40)
-        BPJD_LOCAL_TILE(48)
-#define BPJD_LOCAL_WIDE(BM)                                                                                    \
-  case BM: {                                                                                                   \
-    k_local_factor_wide<BM><<<npairs, 32 * WideShape<BM>::NW, 0, h.stream>>>(                                 \
-        npairs, k, h.sub_ptr, h.sub_dofs, h.bandKf, h.bandMf, lam, rho, (float*)h.Lbuf, (float*)h.wpk, h.derr); \
+    allow_dynamic_smem((const void*)k_local_factor_mma<BM>);                                                   \
+    k_local_factor_mma<BM><<<blocks, 32 * kLocalWarps, sm, h.stream>>>(nsub, k, sptr, h.sub_dofs, h.bandKf,     \
+                                                                       h.bandMf, lam, rho, (float*)h.Lbuf,     \
+                                                                       (float*)h.wpk, h.derr, h.wait_limit,    \
+                                                                       rec_base);                              \
     const size_t bsm = sizeof(float) * BwdShape<BM>::smem_floats;                                              \
     allow_dynamic_smem((const void*)k_local_backward<BM>);                                                     \
     k_local_backward<BM><<<bwd_blocks, 32 * BwdShape<BM>::WPB, bsm, h.stream>>>(                               \
-        h.nsub, k, h.sub_ptr, (const float*)h.Lbuf, (float*)h.wpk, h.derr, h.wait_limit);                      \
+        nsub, k, sptr, (const float*)h.Lbuf, (float*)h.wpk, h.derr, h.wait_limit, rec_base);                   \
     break;                                                                                                     \
   }
-        BPJD_LOCAL_WIDE(64)
-        BPJD_LOCAL_WIDE(96)
-        BPJD_LOCAL_WIDE(152)
-        case 128:
-          k_local_band_team<128><<<npairs, 128, 0, h.stream>>>(npairs, k, h.sub_ptr, h.sub_dofs, h.bandKf,
-                                                               h.bandMf, lam, rho, (float*)h.Lbuf, (float*)h.wpk,
-                                                               h.derr);
-          break;
-        default:
-          return (int)cudaErrorInvalidValue;
-      }
+#define BPJD_LOCAL_WIDE(BM)                                                                                    \
+  case BM: {                                                                                                   \
+    k_local_factor_wide<BM><<<npairs_c, 32 * WideShape<BM>::NW, 0, h.stream>>>(                               \
+        npairs_c, k, sptr, h.sub_dofs, h.bandKf, h.bandMf, lam, rho, (float*)h.Lbuf, (float*)h.wpk, h.derr,     \
+        rec_base);                                                                                             \
+    const size_t bsm = sizeof(float) * BwdShape<BM>::smem_floats;                                              \
+    allow_dynamic_smem((const void*)k_local_backward<BM>);                                                     \
+    k_local_backward<BM><<<bwd_blocks, 32 * BwdShape<BM>::WPB, bsm, h.stream>>>(                               \
+        nsub, k, sptr, (const float*)h.Lbuf, (float*)h.wpk, h.derr, h.wait_limit, rec_base);                   \
+    break;                                                                                                     \
+  }
+        switch (h.Bpad) {
+          BPJD_LOCAL_TILE(16)
+          BPJD_LOCAL_TILE(24)
+          BPJD_LOCAL_TILE(32)
+          BPJD_LOCAL_TILE(40)
+          BPJD_LOCAL_TILE(48)
+          BPJD_LOCAL_WIDE(64)
+          BPJD_LOCAL_WIDE(96)
+          BPJD_LOCAL_WIDE(152)
+          case 128:
+            k_local_band_team<128><<<npairs_c, 128, 0, h.stream>>>(npairs_c, k, sptr, h.sub_dofs, h.bandKf,
+                                                                   h.bandMf, lam, rho, (float*)h.Lbuf,
+                                                                   (float*)h.wpk, h.derr, rec_base);
+            break;
+          default:
+            return (int)cudaErrorInvalidValue;
+        }
 #undef BPJD_LOCAL_TILE
 #undef BPJD_LOCAL_WIDE
-    } else {
-      const size_t esz = f32 ? sizeof(float) : sizeof(double);
-      const size_t per_warp = (size_t)(B * B + 3 * B) * esz;
-      int wpb = (int)std::max<size_t>(1, std::min<size_t>(4, (200 * 1024) / per_warp));
-      size_t sm = per_warp * wpb;
-      int blocks = (npairs + wpb - 1) / wpb;
-      if (f32) {
-        allow_dynamic_smem((const void*)k_local_band<float>);
-        k_local_band<float><<<blocks, 32 * wpb, sm, h.stream>>>(npairs, k, h.sub_ptr, h.sub_dofs, B, h.bandKf,
-                                                                h.bandMf, lam, rho, (float*)h.Lbuf, (float*)h.wpk,
-                                                                h.derr);
       } else {
-        allow_dynamic_smem((const void*)k_local_band<double>);
-        k_local_band<double><<<blocks, 32 * wpb, sm, h.stream>>>(npairs, k, h.sub_ptr, h.sub_dofs, B, h.bandK,
-                                                                 h.bandM, lam, rho, (double*)h.Lbuf,
-                                                                 (double*)h.wpk, h.derr);
+        const size_t esz = f32 ? sizeof(float) : sizeof(double);
+        const size_t per_warp = (size_t)(B * B + 3 * B) * esz;
+        int wpb = (int)std::max<size_t>(1, std::min<size_t>(4, (200 * 1024) / per_warp));
+        size_t sm = per_warp * wpb;
+        int blocks = (npairs_c + wpb - 1) / wpb;
+        if (f32) {
+          allow_dynamic_smem((const void*)k_local_band<float>);
+          k_local_band<float><<<blocks, 32 * wpb, sm, h.stream>>>(npairs_c, k, sptr, h.sub_dofs, B, h.bandKf,
+                                                                  h.bandMf, lam, rho, (float*)h.Lbuf,
+                                                                  (float*)h.wpk, h.derr, rec_base);
+        } else {
+          allow_dynamic_smem((const void*)k_local_band<double>);
+          k_local_band<double><<<blocks, 32 * wpb, sm, h.stream>>>(npairs_c, k, sptr, h.sub_dofs, B, h.bandK,
+                                                                   h.bandM, lam, rho, (double*)h.Lbuf,
+                                                                   (double*)h.wpk, h.derr, rec_base);
+        }
       }
     }
+  }
   }
   // coarse solve
   {
@@ -3532,18 +2626,6 @@ int launch_precond(Handle& h, const double* rho, const double* lam, double* Z) {
   return (int)cudaGetLastError();
 }
 
-int launch_rr(Handle& h, int m, const double* G, const double* Hm, const double* lam_old, double* C,
-              double* lam_new, int hist_row) {
-  if (m > kRRMax) return (int)cudaErrorInvalidValue;
-  size_t sm = (size_t)(6 * kRRLd * kRRLd + 3 * kRRLd) * sizeof(double) + 3 * kRRLd * sizeof(int);
-  allow_dynamic_smem((const void*)k_rayleigh_ritz_chol);
-  ProfScope ps(h, BPJD_PROF_RR);
-  h.launches += 1;
-  double* hr = (hist_row >= 0 && hist_row < h.hist_rows) ? h.hist + (int64_t)hist_row * h.k : nullptr;
-  k_rayleigh_ritz_chol<<<1, 1024, sm, h.stream>>>(m, h.k, G, Hm, h.drop_tol, lam_old, C, lam_new, hr, h.stop_rule,
-                                                 h.tol, h.dstat, h.dword() ? 1 : 0);
-  return (int)cudaGetLastError();
-}
 
 int launch_split_values(const double* v, int64_t nnz, float2* out, cudaStream_t s) {
   if (nnz <= 0) return 0;

@@ -104,7 +104,13 @@ size_t estimate_bytes(const Request& r) {
   b += 2 * (n + 1) * 8 + nnz * (4 + 8 + 8);                 // K, M and their split values
   b += 2 * (r.P.ci.size() * 12 + (n + nH + 2) * 8);        // P and P^T
   b += sum_nl * (size_t)B * 8 * 2 + sum_nl * (size_t)Bpad * 4 * 2;  // bands FP64 + FP32
-  b += sum_nl * k * (size_t)Bpad * 8;                      // band factors (FP64 worst case)
+  {
+    // band factors (FP64 worst case), solved in chunks of subdomains within the
+    // default 2 GiB scratch bound (at least one subdomain per chunk)
+    size_t max_nl = 0;
+    for (int l = 0; l < r.n_sub; ++l) max_nl = std::max<size_t>(max_nl, (size_t)(r.sub_ptr[l + 1] - r.sub_ptr[l]));
+    b += std::min(sum_nl * k * (size_t)Bpad * 8, ((size_t)2 << 30) + max_nl * k * (size_t)Bpad * 8);
+  }
   b += sum_nl * k * 8 + sum_nl * 12;                       // local solutions, maps
   b += n * k * 8 * 20;                                     // block vectors
   b += nH * nH * 8 * 2;                                    // coarse eigenbasis

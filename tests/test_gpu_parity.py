@@ -228,3 +228,51 @@ def test_block_gram_matches_oracle_products():
     ref2 = blocks[0].T @ np.hstack(blocks[1:])
     scale2 = np.abs(blocks[0]).T @ np.abs(np.hstack(blocks[1:]))
     assert np.all(np.abs(out2.cpu().numpy() - ref2) <= 1e-14 * scale2)
+
+
+@pytest.mark.parametrize("spec", [config_c1(), config_small_2d(), config_small_3d(n=24, ns=4),
+                                  config_small_morley(n=32, ns=4, delta=2, k=6, tau=1)], ids=lambda s: s.name)
+@pytest.mark.parametrize("precision", [B.FP64, B.MIXED], ids=["fp64", "mixed"])
+def test_chunked_local_solves_bit_identical(spec, precision):
+    """Local solves taken chunk by chunk of subdomains (a scratch bound of one byte:
+    one subdomain per chunk) give exactly the results of one chunk: every (subdomain,
+    shift) pair is factorised and solved independently of which pairs share a launch."""
+    pb = B.problem_from_spec(spec)
+    ref = B.Solver.from_problem(pb, spec.k, device=DEV, precision=precision, subspace=B.W_3K)
+    one = B.Solver.from_problem(pb, spec.k, device=DEV, precision=precision, subspace=B.W_3K,
+                                local_scratch_bytes=1)
+    assert one.device_bytes() < ref.device_bytes()
+    l0, X0, st0 = ref.solve()
+    l1, X1, st1 = one.solve()
+    assert st0["iters"] == st1["iters"]
+    np.testing.assert_array_equal(l0, l1)
+    np.testing.assert_array_equal(X0, X1)
+    ref.close()
+    one.close()
+
+
+@pytest.mark.parametrize("spec", [config_c1(), config_small_2d(), config_small_3d(n=24, ns=4),
+                                  config_small_morley(n=32, ns=4, delta=2, k=6, tau=1)], ids=lambda s: s.name)
+def test_factor_reuse_gives_the_exact_shift_eigenpairs(spec):
+    """Reusing the local factors while the shifts stay within 1e-6 (the default with FP32
+    local solves), and even reusing the first factors for every later application
+    (tolerance 1e30: the forward sweep on stored factors runs at every step), converge
+    to the eigenpairs of the exact-shift solve (Eq. (3.3) at every application)."""
+    pb = B.problem_from_spec(spec)
+    op = oproblem.build(spec)
+    res = {}
+    for name, tol in (("exact", -1.0), ("default", 0.0), ("first", 1e30)):
+        sv = B.Solver.from_problem(pb, spec.k, device=DEV, precision=B.MIXED, subspace=B.W_3K,
+                                   local_refactor_tol=tol, max_iter=2000)
+        res[name] = sv.solve()
+        sv.close()
+    l0, X0, st0 = res["exact"]
+    for name in ("default", "first"):
+        lam, X, st = res[name]
+        assert st["converged"] == 1, name
+        np.testing.assert_allclose(lam, l0, rtol=1e-9, err_msg=name)
+        assert metrics.rel_residuals(op.K, op.M, lam, X).max() <= 1e-8, name
+        for a, b in metrics.clusters(l0):
+            if b < spec.k:
+                assert metrics.gap_b(X[:, a:b], X0[:, a:b], op.M) <= 1e-6, (name, a, b)
+    assert abs(res["default"][2]["iters"] - st0["iters"]) <= 2

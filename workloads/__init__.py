@@ -48,6 +48,7 @@ from .specs import (
     kappa_field_2d,
     config_c1,
     config_c2,
+    config_c2_scaled,
     config_c3,
     config_c4,
     config_c4_bfs,
@@ -68,6 +69,7 @@ __all__ = [
     "kappa_field_2d",
     "config_c1",
     "config_c2",
+    "config_c2_scaled",
     "config_c3",
     "config_c4",
     "config_c4_bfs",

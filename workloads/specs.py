@@ -183,6 +183,15 @@ def config_c2() -> ProblemSpec:
                        name="c2_kappa_rect_p1_h512")
 
 
+def config_c2_scaled(n: int) -> ProblemSpec:
+    """C2's operator and coefficient on n x n elements with C2's subdomain shape (32
+    elements per side, overlap 2 layers), k = 12: the same local band windows as C2
+    at 1-17M dofs, for bandwidth measurements beyond the L2 cache."""
+    kap = kappa_field_2d(n, n, 1.0, 1.001, "sin")
+    return ProblemSpec("p1_2d", (n, n), (1.0, 1.001), (n // 32, n // 32), 2, 12, kappa=kap,
+                       name=f"c2_scaled_p1_h{n}")
+
+
 def config_c3() -> ProblemSpec:
     """-Laplace u = lambda u on the unit cube, P1 Kuhn tetrahedra, 64^3 cubes
     (250047 dofs), k = 10, 8 x 8 x 8 subdomains, overlap 1 layer."""
