@@ -335,11 +335,17 @@ void bpjd_problem_free(bpjd_problem* p);
  * A server solves a stream of independent requests (each one a full
  * bpjd_setup + bpjd_solve of its own pencil and partition) on a few worker
  * threads, each with its own CUDA stream, so that small requests overlap on
- * the GPU.  Admission is first-in first-out under a device-memory budget: the
- * request at the head of the queue starts when its estimated device footprint
- * fits beside the requests in flight.  This is the per-request workflow of
+ * the GPU.  Admission is under a device-memory budget: a queued request starts
+ * when its estimated device footprint fits beside the requests in flight.
+ * Among the requests that fit, the default order takes the smallest estimated
+ * work first (dofs x k), except that a request waiting longer than
+ * starvation_s seconds goes ahead of every younger one (oldest first), so that
+ * small requests are not held up behind large ones and large ones still start;
+ * BPJD_ADMIT_FIFO keeps arrival order.  This is the per-request workflow of
  * Algorithm 3.1 run many times; the paper itself solves one pencil at a time.
  */
+#define BPJD_ADMIT_SMALLEST 0  /* smallest estimated work first, with aging (default) */
+#define BPJD_ADMIT_FIFO     1  /* arrival order */
 #define BPJD_PENDING 1  /* bpjd_server_poll: the request has not finished yet */
 
 typedef struct {
@@ -351,6 +357,8 @@ typedef struct {
   int32_t stop_rule;
   double  tol;
   int32_t max_iter;
+  int32_t admission;        /* BPJD_ADMIT_SMALLEST (default) | BPJD_ADMIT_FIFO */
+  double  starvation_s;     /* aging limit of BPJD_ADMIT_SMALLEST (default 1 s) */
 } bpjd_server_opts;
 
 typedef struct bpjd_server bpjd_server;

@@ -35,6 +35,7 @@ ERR_TOO_LARGE = -12
 ERR_TIMEOUT = -13
 
 FP64, MIXED, MIXED_LOCAL = 0, 1, 2
+ADMIT_SMALLEST, ADMIT_FIFO = 0, 1
 W_2K, W_3K = 0, 1
 STOP_RESIDUAL, STOP_DLAMBDA = 0, 1
 
@@ -75,7 +76,8 @@ class Stats(C.Structure):
 
 class ServerOpts(C.Structure):
     _fields_ = [("hbm_budget_bytes", C.c_size_t), ("workers", C.c_int32), ("precision", C.c_int32),
-                ("subspace", C.c_int32), ("stop_rule", C.c_int32), ("tol", C.c_double), ("max_iter", C.c_int32)]
+                ("subspace", C.c_int32), ("stop_rule", C.c_int32), ("tol", C.c_double), ("max_iter", C.c_int32),
+                ("admission", C.c_int32), ("starvation_s", C.c_double)]
 
 
 class MeshS(C.Structure):
@@ -382,17 +384,19 @@ class Solver:
 
 # ---- serving --------------------------------------------------------------------
 class Server:
-    """Many independent eigenproblems on one GPU (bpjd_server_*): requests are queued
-    first-in first-out, admitted under a device-memory budget and solved by worker
-    threads with one CUDA stream each."""
+    """Many independent eigenproblems on one GPU (bpjd_server_*): requests are queued,
+    admitted under a device-memory budget (smallest estimated work first with aging, or
+    first-in first-out) and solved by worker threads with one CUDA stream each."""
 
     def __init__(self, workers: int = 4, hbm_budget_bytes: int = 0, precision: int = MIXED,
-                 subspace: int = W_3K, stop_rule: int = STOP_RESIDUAL, tol: float = 1e-8, max_iter: int = 500):
+                 subspace: int = W_3K, stop_rule: int = STOP_RESIDUAL, tol: float = 1e-8, max_iter: int = 500,
+                 admission: int = 0, starvation_s: float = 1.0):
         o = ServerOpts()
         lib.bpjd_server_default_opts(C.byref(o))
         o.workers, o.hbm_budget_bytes = int(workers), int(hbm_budget_bytes)
         o.precision, o.subspace, o.stop_rule = precision, subspace, stop_rule
         o.tol, o.max_iter = float(tol), int(max_iter)
+        o.admission, o.starvation_s = int(admission), float(starvation_s)
         h = C.c_void_p()
         _check(lib.bpjd_server_create(C.byref(o), C.byref(h)), "bpjd_server_create")
         self._h = h

@@ -266,6 +266,9 @@ extern "C" void bpjd_free(bpjd_handle* hh) {
   if (!hh) return;
   Handle* h = reinterpret_cast<Handle*>(hh);
   if (h->stream) cudaStreamSynchronize(h->stream);
+  if (h->gexec) cudaGraphExecDestroy((cudaGraphExec_t)h->gexec);
+  for (void* st : h->gside)
+    if (st) cudaStreamDestroy((cudaStream_t)st);
   for (void* p : h->allocs) cudaFree(p);
   for (void* e : h->ev_pool) cudaEventDestroy((cudaEvent_t)e);
   if (h->hstat) cudaFreeHost(h->hstat);
@@ -598,6 +601,12 @@ extern "C" int bpjd_setup(const bpjd_csr* A, const bpjd_csr* M, const bpjd_csr* 
     CK(dalloc(*h, &h->hist, (size_t)h->hist_rows * k));
     CK(dalloc(*h, &h->dstat, 1));
     CK(cudaMallocHost(&h->hstat, sizeof(DevStatus)));
+    CK(dalloc(*h, &h->dctl, 4));
+    CK(dalloc(*h, &h->dlam_fact, (size_t)k));
+    {
+      double* cb[12] = {h->X, h->AX, h->MX, h->Xn, h->AXn, h->MXn, h->Pd, h->APd, h->MPd, h->Pd2, h->APd2, h->MPd2};
+      for (int q = 0; q < 12; ++q) h->canon[q] = cb[q];
+    }
     CK(cudaStreamSynchronize(h->stream));
     if (dposK) cudaFree(dposK);
     if (dposM) cudaFree(dposM);
@@ -693,6 +702,292 @@ __global__ void k_col_flip(int64_t nk, int k, const double* __restrict__ sign, d
 
 }  // namespace
 
+namespace {
+
+// ---------------------------------------------------------------------------
+// The iteration loop captured as one CUDA graph.  A WHILE node repeats a body of
+// two BPJD steps (the buffers of the iterate and of the previous update swap
+// roles from one step to the next, so the body holds one step of each parity;
+// the second sits in an IF node).  Kernels set the conditions on the device:
+// after every step k_step_done evaluates the stop test of the new iterate (and
+// any local error flag) exactly as the host loop does, and ahead of every
+// preconditioner application k_factor_decide chooses between forming the local
+// factors anew and reusing them (an IF/ELSE node: factorisation or forward sweep,
+// then the shared backward sweep), with the host loop's rule.  No host round
+// trip happens until the loop ends.
+// ---------------------------------------------------------------------------
+
+// ctl[0]: stored factors valid, ctl[1]: factorisations, ctl[2]: reuses
+__global__ void k_factor_decide(int k, const double* __restrict__ lam, double* lam_fact, int32_t* ctl, double tol,
+                                cudaGraphConditionalHandle hfac) {
+  if (threadIdx.x != 0) return;
+  bool reuse = ctl[0] != 0;
+  for (int i = 0; reuse && i < k; ++i)
+    if (!(fabs(lam[i] - lam_fact[i]) <= tol * fabs(lam[i]))) reuse = false;
+  if (!reuse) {
+    for (int i = 0; i < k; ++i) lam_fact[i] = lam[i];
+    ctl[0] = 1;
+    ++ctl[1];
+  } else {
+    ++ctl[2];
+  }
+  cudaGraphSetConditional(hfac, reuse ? 0u : 1u);
+}
+
+// ctl[3]: steps taken; continue while no stop rule, error or step limit holds
+__global__ void k_step_done(const DevStatus* st, const int32_t* derr, int32_t* ctl, int max_iter,
+                            cudaGraphConditionalHandle h1, cudaGraphConditionalHandle h2, int set2) {
+  if (threadIdx.x != 0) return;
+  const int it = ++ctl[3];
+  const unsigned go = (!st->converged && derr[0] == 0 && !st->err_breakdown && it < max_iter) ? 1u : 0u;
+  cudaGraphSetConditional(h1, go);
+  if (set2) cudaGraphSetConditional(h2, go);
+}
+
+struct StepBufs {
+  double *X, *AX, *MX, *Xn, *AXn, *MXn, *Pc, *APc, *MPc, *Pn, *APn, *MPn, *lam_cur, *lam_nxt;
+  void advance(bool p_block) {
+    if (p_block) {
+      std::swap(Pc, Pn);
+      std::swap(APc, APn);
+      std::swap(MPc, MPn);
+    }
+    std::swap(X, Xn);
+    std::swap(AX, AXn);
+    std::swap(MX, MXn);
+    std::swap(lam_cur, lam_nxt);
+  }
+};
+
+struct CaptureCtx {
+  cudaGraphConditionalHandle hfac;  // IF/ELSE of the local factorisation
+  cudaStream_t side;                // stream that captures the two branches
+  bool decide;                      // the handle can reuse factors: device decision
+};
+
+// One BPJD step after the stop test: Algorithm 3.1 Step 2 (preconditioner and
+// projection) and Step 3 (Rayleigh-Ritz), the new iterate and, for the 3k space,
+// the previous-update block; the buffers advance.  Eager: the host decides factor
+// reuse (reuse) and numbers the history row (it); captured (cap): the device does.
+int run_step(Handle& h, StepBufs& b, int nb, int it, bool reuse, const CaptureCtx* cap) {
+  int rc = BPJD_OK;
+  const int k = h.k;
+  const int mixed = h.dword() ? 1 : 0;
+  double* C1 = h.small;                 // k x k
+  double* G = h.small + 2 * 96 * 96;    // m x m
+  double* Hm = h.small + 3 * 96 * 96;   // m x m
+  double* Crr = h.small + 4 * 96 * 96;  // m x k
+  // Step 2: t_i = (I - X X^T M) (B_i)^{-1} r_i.  The local factors of an earlier
+  // application are reused while every shift lies within refactor_tol of the
+  // one they were formed at (the local solves then differ from exact-shift
+  // solves by about that relative amount, far below their FP32 rounding)
+  if (cap && cap->decide) {
+    k_factor_decide<<<1, 32, 0, h.stream>>>(k, b.lam_cur, h.dlam_fact, h.dctl, h.refactor_tol, cap->hfac);
+    h.launches += 1;
+    CK(cudaGetLastError());
+    {
+      cudaStreamCaptureStatus cs;
+      cudaGraph_t cg;
+      const cudaGraphNode_t* deps = nullptr;
+      size_t nd = 0;
+      CK(cudaStreamGetCaptureInfo(h.stream, &cs, nullptr, &cg, &deps, nullptr, &nd));
+      cudaGraphNodeParams np{};
+      np.type = cudaGraphNodeTypeConditional;
+      np.conditional.handle = cap->hfac;
+      np.conditional.type = cudaGraphCondTypeIf;
+      np.conditional.size = 2;
+      cudaGraphNode_t node;
+      CK(cudaGraphAddNode(&node, cg, deps, nullptr, nd, &np));
+      cudaGraph_t branch[2] = {np.conditional.phGraph_out[0], np.conditional.phGraph_out[1]};
+      cudaStream_t main = h.stream;
+      h.stream = cap->side;
+      for (int q = 0; q < 2 && rc == BPJD_OK; ++q) {
+        CK(cudaStreamBeginCaptureToGraph(cap->side, branch[q], nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+        const int e = launch_local(h, h.rho, b.lam_cur, q == 0 ? kLocalFactorOnly : kLocalForwardOnly);
+        cudaGraph_t done;
+        const cudaError_t ee = cudaStreamEndCapture(cap->side, &done);
+        if (e != 0 || ee != cudaSuccess) rc = BPJD_ERR_CUDA;
+      }
+      h.stream = main;
+      if (rc != BPJD_OK) goto fail;
+      CK(cudaStreamUpdateCaptureDependencies(h.stream, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    }
+    CKI(launch_local(h, h.rho, b.lam_cur, kLocalBackwardOnly));
+    CKI(launch_coarse_prolong(h, h.rho, b.lam_cur, h.Z));
+  } else {
+    CKI(launch_precond(h, h.rho, b.lam_cur, h.Z, reuse ? 1 : 0));
+  }
+  {
+    const double* U[1] = {b.MX};
+    const double* V[1] = {h.Z};
+    if (h.dword())
+      CKI(launch_gram(h, 1, U, 1, 1, V, nullptr, 0, C1, nullptr));
+    else
+      CKI(launch_inner(h, 1, U, 1, V, C1));
+    const double* Win[1] = {b.X};
+    // double-word: the preconditioned residual is dominated by its component
+    // along the iterate, so t is a small difference of large terms
+    CKI(launch_combine_rows(h, 1, Win, C1, k, k, h.Z, h.T, -1.0));
+  }
+  CKI(launch_spmm(h, h.T, h.AT, h.MT, k));
+  {
+    // Step 3: Rayleigh-Ritz in W = U^k + span{t} (+ U^{k-1})
+    const double *W[3], *AW[3], *MW[3];
+    auto put = [&](int q, const double* w, const double* aw, const double* mw) {
+      W[q] = w;
+      AW[q] = aw;
+      MW[q] = mw;
+    };
+    // span{X, P} = U^k + U^{k-1}: P is the part of the previous update outside X.
+    // Mixed precision: the iterate goes last, so that the upper Gram tiles (the
+    // ones formed) pair the correction and P blocks with the exact products of
+    // the iterate, never the FP32 products of t or P with the iterate.
+    const int bx = mixed ? nb - 1 : 0;  // block of the iterate
+    put(bx, b.X, b.AX, b.MX);
+    if (nb == 3) {
+      put(1, b.Pc, b.APc, b.MPc);
+      put(mixed ? 0 : 2, h.T, h.AT, h.MT);
+    } else {
+      put(mixed ? 0 : 1, h.T, h.AT, h.MT);
+    }
+    const int m = nb * k;
+    if (h.dword()) {
+      CKI(launch_gram(h, nb, W, nb, 2, MW, AW, 1, G, Hm));
+    } else {
+      CKI(launch_inner(h, nb, W, nb, MW, G));
+      CKI(launch_inner(h, nb, W, nb, AW, Hm));
+    }
+    CKI(launch_rr(h, m, G, Hm, b.lam_cur, Crr, b.lam_nxt, it + 1, cap ? h.dctl + 3 : nullptr));
+    CKI(launch_combine_rows(h, nb, W, Crr, k, k, nullptr, b.Xn, 1.0));
+    CKI(launch_spmm(h, b.Xn, b.AXn, b.MXn, k));
+    if (h.subspace == BPJD_W_3K) {
+      // P_new = the non-iterate blocks of W times their rows of C, with K P_new and
+      // M P_new by SpMM (no cancellation)
+      if (mixed)
+        CKI(launch_combine_rows(h, nb - 1, W, Crr, k, k, nullptr, b.Pn, 1.0, 1));
+      else
+        CKI(launch_combine_rows(h, nb - 1, W + 1, Crr + (size_t)k * k, k, k, nullptr, b.Pn, 1.0));
+      CKI(launch_spmm(h, b.Pn, b.APn, b.MPn, k));
+    }
+  }
+  b.advance(h.subspace == BPJD_W_3K);
+  return BPJD_OK;
+fail:
+  return rc;
+}
+
+// Captures the loop (from the buffer state b, steps of nb blocks) into h.gexec.
+int build_loop_graph(Handle& h, const StepBufs& b0, int nb) {
+  int rc = BPJD_OK;
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  cudaStream_t main = h.stream;
+  bool capturing = false;
+  cudaStream_t cap_stream = nullptr;
+  const int64_t launches0 = h.launches;
+  const bool decide = h.refactor_tol > 0 && can_reuse_factors(h);
+  StepBufs b = b0;
+  cudaGraphConditionalHandle hw, hodd, hfa, hfb;
+  CKI(prime_kernel_attributes(h));
+  for (int q = 0; q < 3; ++q)
+    if (!h.gside[q]) {
+      cudaStream_t st;
+      CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+      h.gside[q] = st;
+    }
+  CK(cudaGraphCreate(&g, 0));
+  CK(cudaGraphConditionalHandleCreate(&hw, g, 1, cudaGraphCondAssignDefault));
+  CK(cudaGraphConditionalHandleCreate(&hodd, g, 0, cudaGraphCondAssignDefault));
+  CK(cudaGraphConditionalHandleCreate(&hfa, g, 1, cudaGraphCondAssignDefault));
+  CK(cudaGraphConditionalHandleCreate(&hfb, g, 1, cudaGraphCondAssignDefault));
+  {
+    cudaGraphNodeParams wp{};
+    wp.type = cudaGraphNodeTypeConditional;
+    wp.conditional.handle = hw;
+    wp.conditional.type = cudaGraphCondTypeWhile;
+    wp.conditional.size = 1;
+    cudaGraphNode_t wn;
+    CK(cudaGraphAddNode(&wn, g, nullptr, nullptr, 0, &wp));
+    cudaGraph_t body = wp.conditional.phGraph_out[0];
+    cudaStream_t s1 = (cudaStream_t)h.gside[0], s2 = (cudaStream_t)h.gside[1], s3 = (cudaStream_t)h.gside[2];
+    h.stream = s1;
+    CK(cudaStreamBeginCaptureToGraph(s1, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    capturing = true;
+    cap_stream = s1;
+    {
+      const CaptureCtx ca{hfa, s2, decide};
+      if ((rc = run_step(h, b, nb, 0, false, &ca)) != BPJD_OK) goto fail;
+      CKI(launch_residual(h, b.AX, b.MX, b.lam_cur, h.rho));
+      k_step_done<<<1, 32, 0, s1>>>(h.dstat, h.derr, h.dctl, h.max_iter, hw, hodd, 1);
+      CK(cudaGetLastError());
+      // the second step of the body, in an IF node on the first one's verdict
+      cudaStreamCaptureStatus cs;
+      cudaGraph_t cg;
+      const cudaGraphNode_t* deps = nullptr;
+      size_t nd = 0;
+      CK(cudaStreamGetCaptureInfo(s1, &cs, nullptr, &cg, &deps, nullptr, &nd));
+      cudaGraphNodeParams ip{};
+      ip.type = cudaGraphNodeTypeConditional;
+      ip.conditional.handle = hodd;
+      ip.conditional.type = cudaGraphCondTypeIf;
+      ip.conditional.size = 1;
+      cudaGraphNode_t in;
+      CK(cudaGraphAddNode(&in, cg, deps, nullptr, nd, &ip));
+      cudaGraph_t second = ip.conditional.phGraph_out[0];
+      h.stream = s2;
+      CK(cudaStreamBeginCaptureToGraph(s2, second, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+      cap_stream = s2;
+      const CaptureCtx cb{hfb, s3, decide};
+      if ((rc = run_step(h, b, nb, 0, false, &cb)) != BPJD_OK) goto fail;
+      CKI(launch_residual(h, b.AX, b.MX, b.lam_cur, h.rho));
+      k_step_done<<<1, 32, 0, s2>>>(h.dstat, h.derr, h.dctl, h.max_iter, hw, hw, 0);
+      CK(cudaGetLastError());
+      {
+        cudaGraph_t done;
+        CK(cudaStreamEndCapture(s2, &done));
+      }
+      cap_stream = s1;
+      h.stream = s1;
+      CK(cudaStreamUpdateCaptureDependencies(s1, &in, nullptr, 1, cudaStreamSetCaptureDependencies));
+    }
+    {
+      cudaGraph_t done;
+      CK(cudaStreamEndCapture(s1, &done));
+    }
+    capturing = false;
+  }
+  h.stream = main;
+  CK(cudaGraphInstantiate(&ge, g, 0));
+  cudaGraphDestroy(g);
+  g = nullptr;
+  h.gexec = ge;
+  // kernels per step: the launches of the two captured steps (with both branches
+  // of each factorisation decision, of which one runs), plus the two stop tests
+  h.graph_step_launches = (h.launches - launches0 + 2) / 2 - (decide ? 1 : 0);
+  h.launches = launches0;
+  return BPJD_OK;
+fail:
+  if (capturing && cap_stream) {
+    cudaGraph_t junk = nullptr;
+    if (cap_stream != (cudaStream_t)h.gside[0] && cudaStreamEndCapture(cap_stream, &junk) == cudaSuccess && junk)
+      cudaGraphDestroy(junk);
+    junk = nullptr;
+    if (cudaStreamEndCapture((cudaStream_t)h.gside[0], &junk) == cudaSuccess && junk) cudaGraphDestroy(junk);
+  }
+  cudaGetLastError();
+  h.stream = main;
+  h.launches = launches0;
+  if (g) cudaGraphDestroy(g);
+  return rc == BPJD_OK ? BPJD_ERR_CUDA : rc;
+}
+
+bool graphs_enabled() {
+  const char* e = std::getenv("BPJD_GRAPH");
+  return !(e && e[0] == '0');
+}
+
+}  // namespace
+
 extern "C" int bpjd_solve(bpjd_handle* hh, double* eigvals, double* eigvecs, int32_t eigvecs_on_device,
                           bpjd_stats* st) {
   if (!hh) return BPJD_ERR_BAD_ARG;
@@ -703,18 +998,15 @@ extern "C" int bpjd_solve(bpjd_handle* hh, double* eigvals, double* eigvecs, int
   const double t0 = now_s();
   int it = 0;
   bool converged = false;
-  double* lam_cur = h.lam;
-  double* lam_nxt = h.lam + k;
-  double* C1 = h.small;                 // k x k
-  double* G = h.small + 2 * 96 * 96;    // m x m
-  double* Hm = h.small + 3 * 96 * 96;   // m x m
-  double* Crr = h.small + 4 * 96 * 96;  // m x k
-  double *X = h.X, *AX = h.AX, *MX = h.MX;
-  double *Xn = h.Xn, *AXn = h.AXn, *MXn = h.MXn;
-  double *Pc = h.Pd, *APc = h.APd, *MPc = h.MPd;      // current P block (3k)
-  double *Pn = h.Pd2, *APn = h.APd2, *MPn = h.MPd2;   // next P block
+  // every solve starts from the same buffer assignment (a captured loop refers to it)
+  StepBufs b{h.canon[0], h.canon[1], h.canon[2], h.canon[3], h.canon[4], h.canon[5], h.canon[6],
+             h.canon[7], h.canon[8], h.canon[9], h.canon[10], h.canon[11], h.lam, h.lam + k};
+  double *&X = b.X, *&AX = b.AX, *&MX = b.MX;
+  double*& lam_cur = b.lam_cur;
   bool have_prev = false;
-  const int mixed = h.dword() ? 1 : 0;
+  // the loop runs as one CUDA graph once every step has the same shape (eager
+  // when profiling or tracing, which need the host between kernels)
+  bool graph = graphs_enabled() && !h.profile && !trace_on();
 
   std::vector<double> lam_h((size_t)k);
   h.factors_valid = false;
@@ -757,79 +1049,50 @@ extern "C" int bpjd_solve(bpjd_handle* hh, double* eigvals, double* eigvecs, int
       rc = BPJD_ERR_NOCONV;
       break;
     }
-    // Step 2: t_i = (I - X X^T M) (B_i)^{-1} r_i.  The local factors of an earlier
-    // application are reused while every shift lies within refactor_tol of the
-    // one they were formed at (the local solves then differ from exact-shift
-    // solves by about that relative amount, far below their FP32 rounding)
+    const int nb = (h.subspace == BPJD_W_3K && have_prev) ? 3 : 2;
+    if (graph && (have_prev || h.subspace == BPJD_W_2K)) {
+      // from here every step has nb blocks: the rest of the loop as one graph
+      if (!h.gexec && build_loop_graph(h, b, nb) != BPJD_OK) {
+        graph = false;  // capture failed: the loop stays on the host
+        goto eager;
+      }
+      {
+        int32_t ctl[4] = {h.factors_valid ? 1 : 0, 0, 0, it};
+        if (h.factors_valid)
+          CK(cudaMemcpyAsync(h.dlam_fact, h.lam_fact.data(), sizeof(double) * k, cudaMemcpyHostToDevice, h.stream));
+        CK(cudaMemcpyAsync(h.dctl, ctl, sizeof(ctl), cudaMemcpyHostToDevice, h.stream));
+        CK(cudaGraphLaunch((cudaGraphExec_t)h.gexec, h.stream));
+        CK(cudaMemcpyAsync(ctl, h.dctl, sizeof(ctl), cudaMemcpyDeviceToHost, h.stream));
+        CK(cudaMemcpyAsync(h.hstat, h.dstat, sizeof(DevStatus), cudaMemcpyDeviceToHost, h.stream));
+        CK(cudaMemcpyAsync(herr, h.derr, sizeof(herr), cudaMemcpyDeviceToHost, h.stream));
+        CK(cudaStreamSynchronize(h.stream));
+        const int steps = ctl[3] - it;
+        if (steps & 1) b.advance(h.subspace == BPJD_W_3K);  // the graph ends on its second step's buffers otherwise
+        it = ctl[3];
+        h.refactorisations += ctl[1];
+        h.reuses += ctl[2];
+        h.launches += h.graph_step_launches * steps;
+        if (herr[0])
+          rc = local_status(herr[0]);
+        else if (h.hstat->err_breakdown)
+          rc = BPJD_ERR_BREAKDOWN;
+        else if (h.hstat->converged)
+          converged = true;
+        else
+          rc = BPJD_ERR_NOCONV;
+      }
+      break;
+    }
+  eager: {
     bool reuse = h.factors_valid && h.refactor_tol > 0;
     for (int i = 0; reuse && i < k; ++i)
       if (!(std::fabs(lam_h[i] - h.lam_fact[i]) <= h.refactor_tol * std::fabs(lam_h[i]))) reuse = false;
-    CKI(launch_precond(h, h.rho, lam_cur, h.Z, reuse ? 1 : 0));
+    if ((rc = run_step(h, b, nb, it, reuse, nullptr)) != BPJD_OK) goto fail;
     if (!reuse && h.refactor_tol > 0 && can_reuse_factors(h)) {
       h.factors_valid = true;
       h.lam_fact = lam_h;
     }
-    {
-      const double* U[1] = {MX};
-      const double* V[1] = {h.Z};
-      if (h.dword())
-        CKI(launch_gram(h, 1, U, 1, 1, V, nullptr, 0, C1, nullptr));
-      else
-        CKI(launch_inner(h, 1, U, 1, V, C1));
-      const double* Win[1] = {X};
-      // double-word: the preconditioned residual is dominated by its component
-      // along the iterate, so t is a small difference of large terms
-      CKI(launch_combine_rows(h, 1, Win, C1, k, k, h.Z, h.T, -1.0));
-    }
-    CKI(launch_spmm(h, h.T, h.AT, h.MT, k));
-    // Step 3: Rayleigh-Ritz in W = U^k + span{t} (+ U^{k-1})
-    int nb;
-    const double *W[3], *AW[3], *MW[3];
-    auto put = [&](int b, const double* w, const double* aw, const double* mw) {
-      W[b] = w;
-      AW[b] = aw;
-      MW[b] = mw;
-    };
-    // span{X, P} = U^k + U^{k-1}: P is the part of the previous update outside X.
-    // Mixed precision: the iterate goes last, so that the upper Gram tiles (the
-    // ones formed) pair the correction and P blocks with the exact products of
-    // the iterate, never the FP32 products of t or P with the iterate.
-    nb = (h.subspace == BPJD_W_3K && have_prev) ? 3 : 2;
-    const int bx = mixed ? nb - 1 : 0;  // block of the iterate
-    put(bx, X, AX, MX);
-    if (nb == 3) {
-      put(1, Pc, APc, MPc);
-      put(mixed ? 0 : 2, h.T, h.AT, h.MT);
-    } else {
-      put(mixed ? 0 : 1, h.T, h.AT, h.MT);
-    }
-    const int m = nb * k;
-    if (h.dword()) {
-      CKI(launch_gram(h, nb, W, nb, 2, MW, AW, 1, G, Hm));
-    } else {
-      CKI(launch_inner(h, nb, W, nb, MW, G));
-      CKI(launch_inner(h, nb, W, nb, AW, Hm));
-    }
-    CKI(launch_rr(h, m, G, Hm, lam_cur, Crr, lam_nxt, it + 1));
-    CKI(launch_combine_rows(h, nb, W, Crr, k, k, nullptr, Xn, 1.0));
-    CKI(launch_spmm(h, Xn, AXn, MXn, k));
-    if (h.subspace == BPJD_W_3K) {
-      // P_new = the non-iterate blocks of W times their rows of C, with K P_new and
-      // M P_new by SpMM (no cancellation)
-      if (mixed)
-        CKI(launch_combine_rows(h, nb - 1, W, Crr, k, k, nullptr, Pn, 1.0, 1));
-      else
-        CKI(launch_combine_rows(h, nb - 1, W + 1, Crr + (size_t)k * k, k, k, nullptr, Pn, 1.0));
-      CKI(launch_spmm(h, Pn, APn, MPn, k));
-      std::swap(Pc, Pn);
-      std::swap(APc, APn);
-      std::swap(MPc, MPn);
-    }
-    // the new iterate becomes the current one
-    std::swap(X, Xn);
-    std::swap(AX, AXn);
-    std::swap(MX, MXn);
-    std::swap(lam_cur, lam_nxt);
+  }
     have_prev = true;
     ++it;
   }
@@ -863,13 +1126,6 @@ extern "C" int bpjd_solve(bpjd_handle* hh, double* eigvals, double* eigvecs, int
     st->t_solve_s = now_s() - t0;
     st->status = rc;
   }
-  // keep the handle's notion of the current buffers consistent for the next call
-  h.X = X;
-  h.AX = AX;
-  h.MX = MX;
-  h.Xn = Xn;
-  h.AXn = AXn;
-  h.MXn = MXn;
   return rc;
 fail:
   if (st) st->status = rc;

@@ -80,6 +80,14 @@ struct Handle {
   bool factors_valid = false;      // Lbuf holds the factors of every pair, formed at the shifts lam_fact
   std::vector<double> lam_fact;    // host copy of the shifts of the stored factors
   int64_t refactorisations = 0, reuses = 0;  // local applications of the last solve, by kind
+
+  // ---- the iteration loop as one CUDA graph (conditional nodes decide on the device)
+  int32_t* dctl = nullptr;      // device: [0] stored factors valid, [1] factorisations, [2] reuses, [3] steps
+  double* dlam_fact = nullptr;  // device copy of the shifts of the stored factors (k)
+  void* gexec = nullptr;        // cudaGraphExec_t of the loop, built on first use
+  void* gside[3] = {nullptr, nullptr, nullptr};  // streams that capture the conditional bodies
+  int64_t graph_step_launches = 0;  // kernels launched per captured step
+  double* canon[12] = {};       // buffer assignment at the start of every solve (X, AX, MX, Xn, ..., MPd2)
   void* wpk = nullptr;         // packed local solutions sum_nl x k (FP32 or FP64)
   double* cH = nullptr;        // n_H x k coarse restriction
   double* aH = nullptr;        // n_H x k coarse coordinates
@@ -157,8 +165,15 @@ int launch_residual(Handle& h, const double* AX, const double* MX, const double*
 int launch_rayleigh(Handle& h, const double* X, const double* AX, const double* MX, double* lam);
 // reuse = 1: the stored factors are current for lam (forward and backward sweeps only)
 int launch_precond(Handle& h, const double* rho, const double* lam, double* Z, int reuse = 0);
+// the two parts of launch_precond; modes of launch_local:
+enum { kLocalFull = 0, kLocalReuse = 1, kLocalFactorOnly = 2, kLocalForwardOnly = 3, kLocalBackwardOnly = 4 };
+int launch_local(Handle& h, const double* rho, const double* lam, int mode);
+int launch_coarse_prolong(Handle& h, const double* rho, const double* lam, double* Z);
 // whether this handle's local kernels can reuse stored factors (records of every pair resident)
 bool can_reuse_factors(const Handle& h);
+// sets the dynamic shared-memory limits of every kernel the handle's iterations launch
+// (done before a stream capture, where the attribute calls are best avoided)
+int prime_kernel_attributes(Handle& h);
 int launch_inner(Handle& h, int p, const double* const* U, int q, const double* const* V, double* out);
 // double-word block inner products: out1 = U^T V1 (and out2 = U^T V2 when nv = 2);
 // sym = 1 requires U^T V symmetric (mu == mv) and forms the upper tiles only
@@ -174,8 +189,10 @@ int launch_gram_raw(int64_t n, int k, int nu, const double* const* U, int nvb, i
 // consistency_only (mixed precision): FP32 update, for the previous-update block P
 int launch_combine_rows(Handle& h, int nin, const double* const* Win, const double* C, int ldc,
                         int csub, const double* Zadd, double* out, double alpha, int consistency_only = 0);
+// hist_row: history row of the Ritz values (host count), or d_row != NULL: the
+// device step counter + 1 (captured iterations)
 int launch_rr(Handle& h, int m, const double* G, const double* Hm, const double* lam_old, double* C,
-              double* lam_new, int hist_row);
+              double* lam_new, int hist_row, const int32_t* d_row = nullptr);
 int launch_validate_csr(const CsrDev& c, int32_t* flag, cudaStream_t s);
 int launch_same_pattern(const CsrDev& a, const CsrDev& m, int32_t* flag, cudaStream_t s);
 int launch_validate_part(Handle& h, int32_t* flag);

@@ -1650,20 +1650,32 @@ __global__ void __launch_bounds__(64) k_local_forward(int nsub, int k, const int
       bulk_load(buf + ((ch & 1) * 4 + q) * PS, Lsub + ((size_t)(i0 + q) * nl + r0) * BMAX, bytes, b);
   };
   auto rhs = [&](int row) -> float { return (row < nl) ? (float)rho[(int64_t)dofs[row] * k + ii] : 0.f; };
-  // right-hand sides of the rows entering during chunk ch (rows ch R + r + BMAX), lane r % 8
-  auto load_in = [&](int ch, float* v) {
+  // right-hand sides of the rows entering during chunk ch (rows ch R + r + BMAX), lane r % 8,
+  // fetched in two stages so that no load waits on another: the dof indices two chunks
+  // ahead, the values (from indices already in registers) one chunk ahead
+  auto load_dofs = [&](int ch, int* dv) {
 #pragma unroll
     for (int q = 0; q < NY; ++q) {
-      const int r = e + 8 * q;
-      v[q] = (r < R) ? rhs(ch * R + r + BMAX) : 0.f;
+      const int r = e + 8 * q, row = ch * R + r + BMAX;
+      dv[q] = (r < R && row < nl) ? dofs[row] : -1;
     }
+  };
+  auto load_vals = [&](const int* dv, float* v) {
+#pragma unroll
+    for (int q = 0; q < NY; ++q) v[q] = (dv[q] >= 0) ? (float)rho[(int64_t)dv[q] * k + ii] : 0.f;
   };
   if (lane == 0) issue(0);
   float rw[TC];
 #pragma unroll
   for (int c = 0; c < TC; ++c) rw[c] = rhs(e + 8 * c);
   float incur[NY], innext[NY];
-  load_in(0, innext);
+  int dnext[NY];
+  {
+    int d0[NY];
+    load_dofs(0, d0);
+    load_vals(d0, innext);
+    load_dofs(1, dnext);
+  }
   uint32_t ph[2] = {0u, 0u};
   bool timeout = false;
   constexpr int NCH = S::NCH;
@@ -1681,7 +1693,8 @@ __global__ void __launch_bounds__(64) k_local_forward(int nsub, int k, const int
       }
 #pragma unroll
       for (int q = 0; q < NY; ++q) incur[q] = innext[q];
-      load_in(ch + 1, innext);
+      load_vals(dnext, innext);  // chunk ch + 1
+      load_dofs(ch + 2, dnext);
       if (!timeout) {
         if (mbar_wait_bounded(&bar[half], ph[half], wait_limit))
           hi_done = ch;
@@ -2480,24 +2493,35 @@ bool can_reuse_factors(const Handle& h) {
   }
 }
 
-int launch_precond(Handle& h, const double* rho, const double* lam, double* Z, int reuse) {
+// The local part of Eq. (3.3): mode kLocalFull factorises every (subdomain, shift)
+// pair and solves (chunk by chunk); kLocalReuse runs the forward and backward
+// sweeps on stored factors; the three single-kernel modes serve the captured
+// iteration, where the factorisation and the forward sweep sit in the two
+// branches of a device-decided conditional node ahead of the shared backward sweep.
+int launch_local(Handle& h, const double* rho, const double* lam, int mode) {
   const int k = h.k;
   const int B = h.B;
-  if (reuse && can_reuse_factors(h)) {
-    // forward and backward sweeps with the stored factors
+  if (mode != kLocalFull && mode != kLocalFactorOnly) {
+    if (!can_reuse_factors(h)) return (int)cudaErrorInvalidValue;
+    // sweeps with the stored factors (all resident: one chunk)
     ProfScope ps(h, BPJD_PROF_LOCAL);
     const int nsub = h.nsub;
     const int bwd_blocks = (nsub * ((k + 3) / 4) + 1) / 2;
-    h.launches += 2;
+    const bool fwd = mode != kLocalBackwardOnly, bwd = mode != kLocalForwardOnly;
+    h.launches += (fwd ? 1 : 0) + (bwd ? 1 : 0);
     auto sweeps = [&](auto bm) {
       constexpr int BM = decltype(bm)::value;
       const size_t bsm = sizeof(float) * BwdShape<BM>::smem_floats;
-      allow_dynamic_smem((const void*)k_local_forward<BM>);
-      k_local_forward<BM><<<bwd_blocks, 32 * BwdShape<BM>::WPB, bsm, h.stream>>>(
-          nsub, k, h.sub_ptr, h.sub_dofs, rho, (const float*)h.Lbuf, (float*)h.wpk, h.derr, h.wait_limit, 0);
-      allow_dynamic_smem((const void*)k_local_backward<BM>);
-      k_local_backward<BM><<<bwd_blocks, 32 * BwdShape<BM>::WPB, bsm, h.stream>>>(
-          nsub, k, h.sub_ptr, (const float*)h.Lbuf, (float*)h.wpk, h.derr, h.wait_limit, 0);
+      if (fwd) {
+        allow_dynamic_smem((const void*)k_local_forward<BM>);
+        k_local_forward<BM><<<bwd_blocks, 32 * BwdShape<BM>::WPB, bsm, h.stream>>>(
+            nsub, k, h.sub_ptr, h.sub_dofs, rho, (const float*)h.Lbuf, (float*)h.wpk, h.derr, h.wait_limit, 0);
+      }
+      if (bwd) {
+        allow_dynamic_smem((const void*)k_local_backward<BM>);
+        k_local_backward<BM><<<bwd_blocks, 32 * BwdShape<BM>::WPB, bsm, h.stream>>>(
+            nsub, k, h.sub_ptr, (const float*)h.Lbuf, (float*)h.wpk, h.derr, h.wait_limit, 0);
+      }
     };
     switch (h.Bpad) {
       case 16: sweeps(std::integral_constant<int, 16>()); break;
@@ -2510,9 +2534,11 @@ int launch_precond(Handle& h, const double* rho, const double* lam, double* Z, i
       case 152: sweeps(std::integral_constant<int, 152>()); break;
       default: return (int)cudaErrorInvalidValue;
     }
-    ++h.reuses;
-  } else {
-    ++h.refactorisations;
+    if (mode == kLocalReuse) ++h.reuses;
+    return (int)cudaGetLastError();
+  }
+  if (mode == kLocalFactorOnly && !can_reuse_factors(h)) return (int)cudaErrorInvalidValue;
+  if (mode == kLocalFull) ++h.refactorisations;
   // local band solves, chunk by chunk of subdomains (the factor records of one
   // chunk fit the record scratch)
   {
@@ -2525,7 +2551,8 @@ int launch_precond(Handle& h, const double* rho, const double* lam, double* Z, i
       const int64_t* sptr = h.sub_ptr + l0;
       const int64_t rec_base = h.chunk_off[ch];
       const int npairs_c = nsub * k;
-      h.launches += (f32 && h.Bpad > 0 && h.Bpad != 128) ? 2 : 1;  // factorisation + backward substitution
+      // factorisation (+ backward substitution)
+      h.launches += (f32 && h.Bpad > 0 && h.Bpad != 128 && mode == kLocalFull) ? 2 : 1;
       if (f32 && h.Bpad > 0) {
         const int blocks = nsub * ((k + kLocalWarps - 1) / kLocalWarps);
         const int bwd_blocks = (nsub * ((k + 3) / 4) + 1) / 2;
@@ -2537,10 +2564,12 @@ int launch_precond(Handle& h, const double* rho, const double* lam, double* Z, i
                                                                        h.bandMf, lam, rho, (float*)h.Lbuf,     \
                                                                        (float*)h.wpk, h.derr, h.wait_limit,    \
                                                                        rec_base);                              \
-    const size_t bsm = sizeof(float) * BwdShape<BM>::smem_floats;                                              \
-    allow_dynamic_smem((const void*)k_local_backward<BM>);                                                     \
-    k_local_backward<BM><<<bwd_blocks, 32 * BwdShape<BM>::WPB, bsm, h.stream>>>(                               \
-        nsub, k, sptr, (const float*)h.Lbuf, (float*)h.wpk, h.derr, h.wait_limit, rec_base);                   \
+    if (mode == kLocalFull) {                                                                                  \
+      const size_t bsm = sizeof(float) * BwdShape<BM>::smem_floats;                                            \
+      allow_dynamic_smem((const void*)k_local_backward<BM>);                                                   \
+      k_local_backward<BM><<<bwd_blocks, 32 * BwdShape<BM>::WPB, bsm, h.stream>>>(                             \
+          nsub, k, sptr, (const float*)h.Lbuf, (float*)h.wpk, h.derr, h.wait_limit, rec_base);                 \
+    }                                                                                                          \
     break;                                                                                                     \
   }
 #define BPJD_LOCAL_WIDE(BM)                                                                                    \
@@ -2548,10 +2577,12 @@ int launch_precond(Handle& h, const double* rho, const double* lam, double* Z, i
     k_local_factor_wide<BM><<<npairs_c, 32 * WideShape<BM>::NW, 0, h.stream>>>(                               \
         npairs_c, k, sptr, h.sub_dofs, h.bandKf, h.bandMf, lam, rho, (float*)h.Lbuf, (float*)h.wpk, h.derr,     \
         rec_base);                                                                                             \
-    const size_t bsm = sizeof(float) * BwdShape<BM>::smem_floats;                                              \
-    allow_dynamic_smem((const void*)k_local_backward<BM>);                                                     \
-    k_local_backward<BM><<<bwd_blocks, 32 * BwdShape<BM>::WPB, bsm, h.stream>>>(                               \
-        nsub, k, sptr, (const float*)h.Lbuf, (float*)h.wpk, h.derr, h.wait_limit, rec_base);                   \
+    if (mode == kLocalFull) {                                                                                  \
+      const size_t bsm = sizeof(float) * BwdShape<BM>::smem_floats;                                            \
+      allow_dynamic_smem((const void*)k_local_backward<BM>);                                                   \
+      k_local_backward<BM><<<bwd_blocks, 32 * BwdShape<BM>::WPB, bsm, h.stream>>>(                             \
+          nsub, k, sptr, (const float*)h.Lbuf, (float*)h.wpk, h.derr, h.wait_limit, rec_base);                 \
+    }                                                                                                          \
     break;                                                                                                     \
   }
         switch (h.Bpad) {
@@ -2593,7 +2624,39 @@ int launch_precond(Handle& h, const double* rho, const double* lam, double* Z, i
       }
     }
   }
+  return (int)cudaGetLastError();
+}
+
+int prime_kernel_attributes(Handle& h) {
+  auto tier = [&](auto bm) {
+    constexpr int BM = decltype(bm)::value;
+    allow_dynamic_smem((const void*)k_local_forward<BM>);
+    allow_dynamic_smem((const void*)k_local_backward<BM>);
+  };
+  switch (h.local_f32() ? h.Bpad : 0) {
+    case 16: tier(std::integral_constant<int, 16>()); allow_dynamic_smem((const void*)k_local_factor_mma<16>); break;
+    case 24: tier(std::integral_constant<int, 24>()); allow_dynamic_smem((const void*)k_local_factor_mma<24>); break;
+    case 32: tier(std::integral_constant<int, 32>()); allow_dynamic_smem((const void*)k_local_factor_mma<32>); break;
+    case 40: tier(std::integral_constant<int, 40>()); allow_dynamic_smem((const void*)k_local_factor_mma<40>); break;
+    case 48: tier(std::integral_constant<int, 48>()); allow_dynamic_smem((const void*)k_local_factor_mma<48>); break;
+    case 64: tier(std::integral_constant<int, 64>()); break;
+    case 96: tier(std::integral_constant<int, 96>()); break;
+    case 152: tier(std::integral_constant<int, 152>()); break;
+    default: break;
   }
+  allow_dynamic_smem((const void*)k_local_band<float>);
+  allow_dynamic_smem((const void*)k_local_band<double>);
+  return (int)cudaGetLastError();
+}
+
+int launch_precond(Handle& h, const double* rho, const double* lam, double* Z, int reuse) {
+  int e = launch_local(h, rho, lam, (reuse && can_reuse_factors(h)) ? kLocalReuse : kLocalFull);
+  if (e) return e;
+  return launch_coarse_prolong(h, rho, lam, Z);
+}
+
+int launch_coarse_prolong(Handle& h, const double* rho, const double* lam, double* Z) {
+  const int k = h.k;
   // coarse solve
   {
     ProfScope ps(h, BPJD_PROF_COARSE);

@@ -877,8 +877,10 @@ __device__ int rr_mixed_solve(int m, int k, const double* __restrict__ G, const 
 // eigen-based path with dropping runs.
 __global__ void k_rayleigh_ritz_chol(int m, int k, const double* __restrict__ G, const double* __restrict__ H,
                                      double drop_tol, const double* __restrict__ lam_old, double* C,
-                                     double* lam_new, double* hist_row, int stop_rule, double tol, DevStatus* st,
-                                     int dword) {
+                                     double* lam_new, double* hist, int hist_rows, int row_host,
+                                     const int32_t* d_row, int stop_rule, double tol, DevStatus* st, int dword) {
+  const int row = d_row ? *d_row + 1 : row_host;
+  double* hist_row = (hist && row >= 0 && row < hist_rows) ? hist + (size_t)row * k : nullptr;
   extern __shared__ double rr[];
   const int ld = kRRLd;
   const int LL = ld * ld;
@@ -1722,8 +1724,11 @@ __device__ bool rr_refined_solve(int m, int k, const double* __restrict__ G, con
 // eigen-based path with dropping when phase A fails.
 __global__ void __launch_bounds__(kRFThreads) k_rayleigh_ritz_refined(
     int m, int k, const double* __restrict__ G, const double* __restrict__ H, double drop_tol,
-    const double* __restrict__ lam_old, double* C, double* lam_new, double* hist_row, int stop_rule, double tol,
-    DevStatus* st) {
+    const double* __restrict__ lam_old, double* C, double* lam_new, double* hist, int hist_rows, int row_host,
+    const int32_t* d_row, int stop_rule, double tol, DevStatus* st) {
+  // history row: the host's step count, or (captured iterations) the device counter + 1
+  const int row = d_row ? *d_row + 1 : row_host;
+  double* hist_row = (hist && row >= 0 && row < hist_rows) ? hist + (size_t)row * k : nullptr;
   extern __shared__ __align__(16) double rfsm[];
   __shared__ double sc[kRFMax], theta[kRFMax];
   __shared__ int ord[kRFMax];
@@ -1761,11 +1766,10 @@ __global__ void __launch_bounds__(kRFThreads) k_rayleigh_ritz_refined(
 }  // namespace
 
 int launch_rr(Handle& h, int m, const double* G, const double* Hm, const double* lam_old, double* C,
-              double* lam_new, int hist_row) {
+              double* lam_new, int hist_row, const int32_t* d_row) {
   if (m > kRRMax) return (int)cudaErrorInvalidValue;
   ProfScope ps(h, BPJD_PROF_RR);
   h.launches += 1;
-  double* hr = (hist_row >= 0 && hist_row < h.hist_rows) ? h.hist + (int64_t)hist_row * h.k : nullptr;
   if (h.dword() && m <= kRFMax) {
     // refined form; its shared memory also holds the eigen-based fallback
     const int mp = m + (m & 1);
@@ -1774,13 +1778,15 @@ int launch_rr(Handle& h, int m, const double* G, const double* Hm, const double*
     const size_t eig = (size_t)(4 * kRRLd * kRRLd + 3 * kRRLd) * sizeof(double) + 3 * kRRLd * sizeof(int);
     allow_dynamic_smem((const void*)k_rayleigh_ritz_refined);
     k_rayleigh_ritz_refined<<<1, kRFThreads, std::max(fast, eig), h.stream>>>(
-        m, h.k, G, Hm, h.drop_tol, lam_old, C, lam_new, hr, h.stop_rule, h.tol, h.dstat);
+        m, h.k, G, Hm, h.drop_tol, lam_old, C, lam_new, h.hist, h.hist_rows, hist_row, d_row, h.stop_rule, h.tol,
+        h.dstat);
     return (int)cudaGetLastError();
   }
   size_t sm = (size_t)(6 * kRRLd * kRRLd + 3 * kRRLd) * sizeof(double) + 3 * kRRLd * sizeof(int);
   allow_dynamic_smem((const void*)k_rayleigh_ritz_chol);
-  k_rayleigh_ritz_chol<<<1, 1024, sm, h.stream>>>(m, h.k, G, Hm, h.drop_tol, lam_old, C, lam_new, hr, h.stop_rule,
-                                                 h.tol, h.dstat, h.dword() ? 1 : 0);
+  k_rayleigh_ritz_chol<<<1, 1024, sm, h.stream>>>(m, h.k, G, Hm, h.drop_tol, lam_old, C, lam_new, h.hist,
+                                                 h.hist_rows, hist_row, d_row, h.stop_rule, h.tol, h.dstat,
+                                                 h.dword() ? 1 : 0);
   return (int)cudaGetLastError();
 }
 

@@ -58,6 +58,7 @@ struct Request {
   std::vector<int32_t> sub_dofs, sub_color;
   int32_t n_sub = 0, n_colors = 0;
   size_t est_bytes = 0;
+  double est_work = 0;      // dofs x k: the admission order of BPJD_ADMIT_SMALLEST
   double t_submit = 0, t_start = 0, t_end = 0;
   bool done = false;
   int status = BPJD_OK;
@@ -164,6 +165,25 @@ void run_request(bpjd_server* s, Request& r, cudaStream_t stream) {
   r.status = rc;
 }
 
+// Index of the queued request to start next, or -1 when none fits the budget
+// (a request always fits when nothing runs).  FIFO: the head only.  Smallest
+// first: any request older than the aging limit goes first (oldest of those),
+// otherwise the smallest estimated work among those that fit, ties by arrival.
+int pick_request(const bpjd_server* s, double now) {
+  auto fits = [&](const Request& r) { return s->in_use + r.est_bytes <= s->budget || s->running == 0; };
+  if (s->queue.empty()) return -1;
+  if (s->o.admission == BPJD_ADMIT_FIFO) return fits(*s->queue.front()) ? 0 : -1;
+  const double limit = s->o.starvation_s > 0 ? s->o.starvation_s : 1.0;
+  if (now - s->queue.front()->t_submit > limit) return fits(*s->queue.front()) ? 0 : -1;
+  int best = -1;
+  for (int i = 0; i < (int)s->queue.size(); ++i) {
+    const Request& r = *s->queue[i];
+    if (!fits(r)) continue;
+    if (best < 0 || r.est_work < s->queue[best]->est_work) best = i;
+  }
+  return best;
+}
+
 void worker(bpjd_server* s) {
   cudaSetDevice(s->device);
   cudaStream_t stream = nullptr;
@@ -172,13 +192,15 @@ void worker(bpjd_server* s) {
     std::shared_ptr<Request> r;
     {
       std::unique_lock<std::mutex> lk(s->mu);
+      int pick = -1;
       s->cv_work.wait(lk, [&] {
         if (s->queue.empty()) return s->stop;
-        return s->in_use + s->queue.front()->est_bytes <= s->budget || s->running == 0;
+        pick = pick_request(s, now_s());
+        return pick >= 0;
       });
       if (s->queue.empty()) break;
-      r = s->queue.front();
-      s->queue.pop_front();
+      r = s->queue[pick];
+      s->queue.erase(s->queue.begin() + pick);
       s->in_use += r->est_bytes;
       ++s->running;
       r->t_start = now_s();
@@ -212,12 +234,15 @@ extern "C" void bpjd_server_default_opts(bpjd_server_opts* o) {
   o->stop_rule = BPJD_STOP_RESIDUAL;
   o->tol = 1e-8;
   o->max_iter = 500;
+  o->admission = BPJD_ADMIT_SMALLEST;
+  o->starvation_s = 1.0;
 }
 
 extern "C" int bpjd_server_create(const bpjd_server_opts* opts, bpjd_server** out) {
   if (!opts || !out) return BPJD_ERR_BAD_ARG;
   *out = nullptr;
   if (opts->workers < 1 || opts->workers > 32) return BPJD_ERR_BAD_ARG;
+  if (opts->admission != BPJD_ADMIT_SMALLEST && opts->admission != BPJD_ADMIT_FIFO) return BPJD_ERR_BAD_ARG;
   auto* s = new bpjd_server;
   s->o = *opts;
   if (cudaGetDevice(&s->device) != cudaSuccess) {
@@ -266,6 +291,7 @@ extern "C" int bpjd_server_submit(bpjd_server* s, const bpjd_csr* A, const bpjd_
     }
   if (part->sub_color) r->sub_color.assign(part->sub_color, part->sub_color + r->n_sub);
   r->est_bytes = estimate_bytes(*r);
+  r->est_work = (double)n * (double)k;
   if (r->est_bytes > s->budget) return BPJD_ERR_TOO_LARGE;
   {
     std::lock_guard<std::mutex> lk(s->mu);

@@ -278,3 +278,40 @@ def test_factor_reuse_gives_the_exact_shift_eigenpairs(spec):
             if b < spec.k:
                 assert metrics.gap_b(X[:, a:b], X0[:, a:b], op.M) <= 1e-6, (name, a, b)
     assert abs(res["default"][2]["iters"] - st0["iters"]) <= 2
+
+
+@pytest.mark.parametrize("spec,precision,subspace,extra", [
+    (config_c1(), B.MIXED, B.W_3K, {}),                                   # window tier 16: factor-reuse IF/ELSE
+    (config_c1(), B.FP64, B.W_3K, {}),                                    # exact shifts, native FP64
+    (config_c1(), B.MIXED, B.W_2K, {}),                                   # 2k space: the graph runs from step 0
+    (config_small_3d(n=24, ns=4), B.MIXED, B.W_3K, {}),                   # wide tier 64
+    (config_small_morley(n=32, ns=4, delta=2, k=6, tau=1), B.MIXED, B.W_3K, {}),   # shared-memory kernel
+    (config_small_2d(), B.MIXED, B.W_3K, {"local_scratch_bytes": 1}),     # chunked local solves
+    (config_c1(), B.MIXED, B.W_3K, {"stop_rule": B.STOP_DLAMBDA, "tol": 1e-10}),
+    (config_c1(), B.MIXED, B.W_3K, {"max_iter": 5}),                      # step limit
+], ids=["c1-mixed", "c1-fp64", "c1-2k", "cube24", "morley", "chunked", "dlambda", "maxiter"])
+def test_graph_loop_equals_host_loop(spec, precision, subspace, extra, monkeypatch):
+    """The iteration loop captured as one CUDA graph (stop test, step limit and factor-reuse
+    decision taken on the device by kernels that set conditional nodes) runs the same
+    kernels in the same order as the host-driven loop: bit-identical eigenpairs, Ritz-value
+    history and iteration count; a second solve on the same handle reuses the graph."""
+    pb = B.problem_from_spec(spec)
+    out = {}
+    for mode in ("1", "0"):
+        monkeypatch.setenv("BPJD_GRAPH", mode)
+        sv = B.Solver.from_problem(pb, spec.k, device=DEV, precision=precision, subspace=subspace, **extra)
+        lam, X, st = sv.solve(raise_on_noconv=False)
+        hist = sv.history()
+        lam2, X2, st2 = sv.solve(raise_on_noconv=False)
+        np.testing.assert_array_equal(lam2, lam)
+        np.testing.assert_array_equal(X2, X)
+        assert st2["iters"] == st["iters"] and st2["status"] == st["status"]
+        out[mode] = (lam, X, st, hist)
+        sv.close()
+    (lg, Xg, sg, hg), (le, Xe, se, he) = out["1"], out["0"]
+    assert sg["iters"] == se["iters"] and sg["status"] == se["status"] and sg["converged"] == se["converged"]
+    np.testing.assert_array_equal(lg, le)
+    np.testing.assert_array_equal(Xg, Xe)
+    np.testing.assert_array_equal(hg, he)
+    if "max_iter" in extra:
+        assert sg["status"] == B.ERR_NOCONV and sg["iters"] == extra["max_iter"]
