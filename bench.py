@@ -55,6 +55,8 @@ def _args():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=64)
     ap.add_argument("--serving-workers", type=int, default=4)
+    ap.add_argument("--refactor-tol", type=float, default=0.0,
+                    help="relative shift change that re-forms the local factors (0: the library default)")
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-scaled", action="store_true")
     ap.add_argument("--scaled-sizes", default="1024,2048",
@@ -535,7 +537,7 @@ def run_ours(a):
 
     def one_step(profile=False):
         sv = B.Solver.from_problem(dpb, k, device=dev, precision=prec, subspace=sub, stream=stream,
-                                   tol=a.tol, max_iter=a.max_iter)
+                                   tol=a.tol, max_iter=a.max_iter, local_refactor_tol=a.refactor_tol)
         if profile:
             sv.profile(True)
         lam, X, st = sv.solve(eigvecs="device")

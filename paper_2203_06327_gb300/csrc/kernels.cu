@@ -1730,6 +1730,225 @@ __global__ void __launch_bounds__(64) k_local_forward(int nsub, int k, const int
 
 
 // ---------------------------------------------------------------------------
+// Blocked sweeps with the stored band factors (window tiers up to 48): the
+// rows are taken eight at a time, one block per staged chunk, so that a
+// block's eight columns are handled together instead of one dependent row at a
+// time.  Layout as in k_local_backward (four shifts per warp, eight lanes per
+// shift, lane e keeping window slots e + 8 t, slot = row mod BMAX); the chunks
+// of a window group have a buffer each (BMAX / 8 of them), so the bulk copies
+// run up to BMAX / 8 - 1 blocks ahead.
+//   backward: for the block's columns q (rows j0 + q), the partial sums over the
+//   solved window rows run in parallel (lane partials, three xor shuffles
+//   each), then the 8 x 8 triangle is solved redundantly in every lane;
+//   forward: the 8 x 8 triangle first (the fused sweep's operation order), then
+//   every other window row takes the block's eight updates in column order, and
+//   the eight entering rows take theirs, so that y equals the fused sweep's bit
+//   for bit.
+// ---------------------------------------------------------------------------
+template <int BMAX>
+struct BlkShape {
+  static constexpr int NCH = BMAX / 8;      // blocks (chunks) per window group, one buffer each
+  static constexpr int PS = 8 * BMAX + 4;   // per-shift buffer stride
+  static constexpr int WPB = 2;             // warps per block
+  static constexpr size_t smem_floats = (size_t)WPB * NCH * 4 * PS;
+};
+
+template <int BMAX, bool FWD>
+__global__ void __launch_bounds__(64) k_local_sweep_blk(int nsub, int k, const int64_t* __restrict__ sub_ptr,
+                                                        const int32_t* __restrict__ sub_dofs,
+                                                        const double* __restrict__ rho,
+                                                        const float* __restrict__ Lbuf, float* __restrict__ wpk,
+                                                        int32_t* err, int wait_limit, int64_t rec_base) {
+  using S = BlkShape<BMAX>;
+  constexpr int TC = BMAX / 8, NCH = S::NCH, PS = S::PS, WPB = S::WPB;
+  constexpr unsigned FULL = 0xffffffffu;
+  static_assert(BMAX % 8 == 0 && BMAX <= 48, "window tier of the blocked sweeps");
+  extern __shared__ __align__(128) float ssm[];
+  __shared__ __align__(8) uint64_t bars[WPB][NCH];
+  const int lane = threadIdx.x & 31, e = lane & 7, p = lane >> 3, wib = threadIdx.x >> 5;
+  const int wglob = blockIdx.x * WPB + wib;
+  const int wps = (k + 3) / 4;  // warps per subdomain
+  const int l = wglob / wps;
+  if (l >= nsub) return;  // whole warps only; no block-wide barrier follows
+  const int i0 = (wglob % wps) * 4;
+  const int nact = min(4, k - i0);  // shifts served by this warp
+  const bool active = p < nact;
+  const int ii = active ? i0 + p : i0;
+  const int64_t off = sub_ptr[l];
+  const int nl = (int)(sub_ptr[l + 1] - off);
+  const int32_t* dofs = sub_dofs + off;
+  float* buf = ssm + (size_t)wib * NCH * 4 * PS;  // [NCH][4][PS]
+  uint64_t* bar = bars[wib];
+  const float* Lsub = Lbuf + (size_t)(off - rec_base) * k * BMAX;  // record of shift i at Lsub + i nl BMAX
+  float* yp = wpk + off * k + ii;
+  if (lane == 0) {
+    for (int b = 0; b < NCH; ++b) mbar_init(&bar[b], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  const int nblk = (nl + 7) / 8;
+  // lane 0: copies issued and waited for, per buffer (for the drain on a timeout)
+  int uses[NCH], dones[NCH];
+#pragma unroll
+  for (int b = 0; b < NCH; ++b) uses[b] = dones[b] = 0;
+  // block ch = rows [8 ch, min(nl, 8 ch + 8)) of each served shift, into buffer ch % NCH
+  auto issue = [&](int ch, int b) {
+    if (ch < 0 || ch >= nblk) return;
+    const int r0 = 8 * ch;
+    const int rows = min(8, nl - r0);
+    const uint32_t bytes = (uint32_t)rows * BMAX * sizeof(float);
+    mbar_expect_tx(&bar[b], bytes * nact);
+    for (int q = 0; q < nact; ++q)
+      bulk_load(buf + (b * 4 + q) * PS, Lsub + ((size_t)(i0 + q) * nl + r0) * BMAX, bytes, &bar[b]);
+    ++uses[b];
+  };
+  auto rhs = [&](int row) -> float { return (row < nl) ? (float)rho[(int64_t)dofs[row] * k + ii] : 0.f; };
+  float w[TC];  // backward: x of the window rows; forward: their pending right-hand sides
+#pragma unroll
+  for (int t = 0; t < TC; ++t) w[t] = FWD ? rhs(e + 8 * t) : 0.f;
+  // per block, lane e's row j0 + e: y (backward) or the entering row's right-hand
+  // side (forward), fetched one block ahead (the dof index two blocks ahead)
+  float vcur = 0.f, vnext = 0.f;
+  int dnext = -1;
+  auto row_of = [&](int ch) { return 8 * ch + e + (FWD ? BMAX : 0); };
+  auto fetch = [&](int ch) -> float {
+    const int r = row_of(ch);
+    if (ch < 0 || ch >= nblk || r >= nl) return 0.f;
+    return FWD ? 0.f : yp[(size_t)r * k];
+  };
+  uint32_t phase = 0;  // bit b: parity of buffer b's next wait
+  bool timeout = false;
+  if (FWD) {
+    if (lane == 0)
+      for (int b = 0; b < NCH - 1; ++b) issue(b, b);
+    {
+      const int r0 = row_of(0), r1 = row_of(1);
+      vnext = (r0 < nl) ? (float)rho[(int64_t)dofs[r0] * k + ii] : 0.f;
+      dnext = (nblk > 1 && r1 < nl) ? dofs[r1] : -1;
+    }
+  } else {
+    if (lane == 0)
+      for (int d = 0; d < NCH - 1; ++d) issue(nblk - 1 - d, (nblk - 1 - d) % NCH);
+    vnext = fetch(nblk - 1);
+  }
+  const int g0 = FWD ? 0 : (nblk - 1) / NCH, g1 = FWD ? (nblk - 1) / NCH : 0;
+  for (int g = g0; FWD ? (g <= g1) : (g >= g1); g += FWD ? 1 : -1) {
+#pragma unroll
+    for (int hq = 0; hq < NCH; ++hq) {
+      const int hc = FWD ? hq : NCH - 1 - hq;  // buffer and slot block of this block
+      const int ch = g * NCH + hc;
+      if (ch >= nblk) continue;
+      __syncwarp();  // the buffer of the previous block is no longer read
+      if (lane == 0 && !timeout) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        // the previous block's buffer takes the block NCH - 1 ahead
+        const int nb = FWD ? ch + NCH - 1 : ch - (NCH - 1);
+        issue(nb, FWD ? (hc + NCH - 1) % NCH : (hc + 1) % NCH);
+      }
+      vcur = vnext;
+      if (FWD) {
+        vnext = (dnext >= 0) ? (float)rho[(int64_t)dnext * k + ii] : 0.f;
+        const int r2 = row_of(ch + 2);
+        dnext = (ch + 2 < nblk && r2 < nl) ? dofs[r2] : -1;
+      } else {
+        vnext = fetch(ch - 1);
+      }
+      if (!timeout) {
+        if (mbar_wait_bounded(&bar[hc], (phase >> hc) & 1u, wait_limit))
+          ++dones[hc];
+        else
+          timeout = true;
+      }
+      phase ^= 1u << hc;
+      const float* Lb = buf + (hc * 4 + p) * PS;  // records of rows 8 ch .. 8 ch + 7 (shift p)
+      const int j0 = 8 * ch;
+      const int nr = min(8, nl - j0);
+      const int s0 = 8 * hc;  // slot of row j0
+      float xb[8];
+      if (FWD) {
+        // the block's pending right-hand sides, then its 8 x 8 triangle
+#pragma unroll
+        for (int q = 0; q < 8; ++q) xb[q] = __shfl_sync(FULL, w[hc], (lane & ~7) | q);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          float r = xb[q];
+#pragma unroll
+          for (int d = 0; d < q; ++d) r = fmaf(-Lb[d * BMAX + s0 + q], xb[d], r);
+          xb[q] = (q < nr) ? r * Lb[q * BMAX + s0 + q] : 0.f;
+        }
+        // other window rows: the block's updates in column order
+#pragma unroll
+        for (int t = 0; t < TC; ++t) {
+          if (t == hc) continue;
+#pragma unroll
+          for (int d = 0; d < 8; ++d)
+            if (d < nr) w[t] = fmaf(-Lb[d * BMAX + e + 8 * t], xb[d], w[t]);
+        }
+        // the entering row j0 + BMAX + e takes slot s0 + e and the updates of the
+        // block's later columns
+        {
+          const float nv = __shfl_sync(FULL, vcur, (lane & ~7) | e);
+          float r = nv;
+#pragma unroll
+          for (int d = 1; d < 8; ++d)
+            if (d > e && d < nr) r = fmaf(-Lb[d * BMAX + s0 + e], xb[d], r);
+          w[hc] = r;
+        }
+      } else {
+        // partial sums over the solved window rows for the block's columns: lane e's
+        // slot s0 + e holds row j0 + e + BMAX, in column q's band iff e < q
+        float part[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          float a = 0.f;
+#pragma unroll
+          for (int t = 0; t < TC; ++t) {
+            const float lv = Lb[q * BMAX + e + 8 * t];
+            a = (t != hc || e < q) ? fmaf(lv, w[t], a) : a;
+          }
+          part[q] = a;
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          part[q] += __shfl_xor_sync(FULL, part[q], 1);
+          part[q] += __shfl_xor_sync(FULL, part[q], 2);
+          part[q] += __shfl_xor_sync(FULL, part[q], 4);
+        }
+        // the 8 x 8 triangle, descending
+#pragma unroll
+        for (int qq = 0; qq < 8; ++qq) {
+          const int q = 7 - qq;
+          const float yq = __shfl_sync(FULL, vcur, (lane & ~7) | q);
+          float r = yq - part[q];
+#pragma unroll
+          for (int d = q + 1; d < 8; ++d) r = fmaf(-Lb[q * BMAX + s0 + d], xb[d], r);
+          xb[q] = (q < nr) ? r * Lb[q * BMAX + s0 + q] : 0.f;
+        }
+        // lane e's slot takes row j0 + e
+        float v = 0.f;
+#pragma unroll
+        for (int d = 0; d < 8; ++d) v = (e == d) ? xb[d] : v;
+        w[hc] = v;
+      }
+      {
+        float v = 0.f;
+#pragma unroll
+        for (int d = 0; d < 8; ++d) v = (e == d) ? xb[d] : v;
+        if (active && !timeout && e < nr) yp[(size_t)(j0 + e) * k] = v;
+      }
+    }
+  }
+  if (timeout && lane == 0) atomicOr(err, kErrTimeout);
+  // lane 0 issued every copy of this warp: drain the ones it did not see complete
+  // (buffer b's phases complete in order; its last uses[b] - dones[b] are pending)
+  if (lane == 0)
+#pragma unroll
+    for (int b = 0; b < NCH; ++b)
+      for (int u = dones[b]; u < uses[b]; ++u)
+        if (!mbar_drain(&bar[b], (uint32_t)(u & 1))) atomicOr(err, kErrDrain);
+}
+
+// ---------------------------------------------------------------------------
 // Local solves for wide bands (window up to 128, e.g. 3-D subdomains): one CTA
 // per (subdomain, shift) with one thread per window column (thread v owns
 // column v, slot u = row mod BMAX).  Per elimination
@@ -2420,9 +2639,10 @@ int launch_gram_raw(int64_t n, int k, int nu, const double* const* U, int nvb, i
   const int total = nv * ntiles * 16;
   if ((size_t)nblk2 * total > partial_capacity) return (int)cudaErrorInvalidValue;
   // chunk rows: a divisor of kGramRows keeping the staging (two raw FP64 buffers
-  // and the hi/lo planes, 24 bytes per value) within 100 KB
+  // and the hi/lo planes, 24 bytes per value) within 100 KB (few blocks: long
+  // chunks, fewer barriers per row)
   const int nseg = nu + nv * nvb;
-  int R = 32;
+  int R = kGramRows;
   while (R > 1 && (size_t)24 * R * k * nseg > 100 * 1024) R /= 2;
   const size_t stage = (size_t)24 * R * k * nseg;
   const size_t red = (size_t)ntiles * nv * 16 * sizeof(double);
@@ -2511,6 +2731,21 @@ int launch_local(Handle& h, const double* rho, const double* lam, int mode) {
     h.launches += (fwd ? 1 : 0) + (bwd ? 1 : 0);
     auto sweeps = [&](auto bm) {
       constexpr int BM = decltype(bm)::value;
+      if constexpr (BM <= 48) {
+        // blocked sweeps, eight rows per step
+        const size_t ssm = sizeof(float) * BlkShape<BM>::smem_floats;
+        if (fwd) {
+          allow_dynamic_smem((const void*)k_local_sweep_blk<BM, true>);
+          k_local_sweep_blk<BM, true><<<bwd_blocks, 32 * BlkShape<BM>::WPB, ssm, h.stream>>>(
+              nsub, k, h.sub_ptr, h.sub_dofs, rho, (const float*)h.Lbuf, (float*)h.wpk, h.derr, h.wait_limit, 0);
+        }
+        if (bwd) {
+          allow_dynamic_smem((const void*)k_local_sweep_blk<BM, false>);
+          k_local_sweep_blk<BM, false><<<bwd_blocks, 32 * BlkShape<BM>::WPB, ssm, h.stream>>>(
+              nsub, k, h.sub_ptr, h.sub_dofs, rho, (const float*)h.Lbuf, (float*)h.wpk, h.derr, h.wait_limit, 0);
+        }
+        return;
+      }
       const size_t bsm = sizeof(float) * BwdShape<BM>::smem_floats;
       if (fwd) {
         allow_dynamic_smem((const void*)k_local_forward<BM>);
@@ -2565,10 +2800,10 @@ int launch_local(Handle& h, const double* rho, const double* lam, int mode) {
                                                                        (float*)h.wpk, h.derr, h.wait_limit,    \
                                                                        rec_base);                              \
     if (mode == kLocalFull) {                                                                                  \
-      const size_t bsm = sizeof(float) * BwdShape<BM>::smem_floats;                                            \
-      allow_dynamic_smem((const void*)k_local_backward<BM>);                                                   \
-      k_local_backward<BM><<<bwd_blocks, 32 * BwdShape<BM>::WPB, bsm, h.stream>>>(                             \
-          nsub, k, sptr, (const float*)h.Lbuf, (float*)h.wpk, h.derr, h.wait_limit, rec_base);                 \
+      const size_t ssm = sizeof(float) * BlkShape<BM>::smem_floats;                                            \
+      allow_dynamic_smem((const void*)k_local_sweep_blk<BM, false>);                                           \
+      k_local_sweep_blk<BM, false><<<bwd_blocks, 32 * BlkShape<BM>::WPB, ssm, h.stream>>>(                     \
+          nsub, k, sptr, h.sub_dofs, rho, (const float*)h.Lbuf, (float*)h.wpk, h.derr, h.wait_limit, rec_base); \
     }                                                                                                          \
     break;                                                                                                     \
   }
@@ -2630,8 +2865,13 @@ int launch_local(Handle& h, const double* rho, const double* lam, int mode) {
 int prime_kernel_attributes(Handle& h) {
   auto tier = [&](auto bm) {
     constexpr int BM = decltype(bm)::value;
-    allow_dynamic_smem((const void*)k_local_forward<BM>);
-    allow_dynamic_smem((const void*)k_local_backward<BM>);
+    if constexpr (BM <= 48) {
+      allow_dynamic_smem((const void*)k_local_sweep_blk<BM, true>);
+      allow_dynamic_smem((const void*)k_local_sweep_blk<BM, false>);
+    } else {
+      allow_dynamic_smem((const void*)k_local_forward<BM>);
+      allow_dynamic_smem((const void*)k_local_backward<BM>);
+    }
   };
   switch (h.local_f32() ? h.Bpad : 0) {
     case 16: tier(std::integral_constant<int, 16>()); allow_dynamic_smem((const void*)k_local_factor_mma<16>); break;
