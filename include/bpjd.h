@@ -120,7 +120,7 @@ typedef struct {
                                anew only when some shift moved by more than this relative
                                amount since they were formed; otherwise the stored factors
                                are reused (forward and backward sweeps only).  0: default,
-                               1e-6 with FP32 local solves, exact shifts (a factorisation
+                               1e-4 with FP32 local solves, exact shifts (a factorisation
                                at every application, as in Eq. (3.3)) for BPJD_FP64;
                                < 0: exact shifts always.  Reuse needs every factor of one
                                application resident (one chunk) and a band window of at
@@ -309,8 +309,19 @@ int bpjd_profile_read(bpjd_handle* h, double* ms, int64_t* count, int64_t* kerne
  *            subdomain counts even, kappa NULL), restricted in the same way.
  * kappa: per-element coefficient, layout [ny][nx][2] (kind 0, entry 0 = the
  * triangle below the diagonal) or [nz][ny][nx] (kinds 1, 2); NULL = 1.
- * Subdomains: nsub boxes per axis grown by delta element layers; the initial
- * grid of Step 1 is the subdomain grid refined tau times. */
+ * Subdomains (partition): BPJD_PART_BOXES (0): nsub boxes per axis grown by
+ * delta element layers (colours 2^dim); BPJD_PART_TRIANGLES (1, kind 0 only,
+ * nx = ny, equal nsub, 2 delta < nx / nsub): the partition of Example 6.1,
+ * every coarse square cut along its SW->NE diagonal into two coarse triangles
+ * (N = 2 nsub^2), each grown by delta rings of fine triangles (a ring adds
+ * every fine triangle sharing a vertex with the region); local dofs are the
+ * interior nodes whose six fine triangles all lie in the grown region; id
+ * 2 (sx + nsub sy) + T (T = 0 below the diagonal), 8 colours
+ * 2 ((sx mod 2) + 2 (sy mod 2)) + T.  The coarse space is P1 on the coarse
+ * triangles either way (the coarse squares split SW->NE).  The initial grid of
+ * Step 1 is the subdomain grid refined tau times. */
+#define BPJD_PART_BOXES     0
+#define BPJD_PART_TRIANGLES 1
 typedef struct {
   int32_t kind;
   int32_t n[3];
@@ -319,6 +330,7 @@ typedef struct {
   int32_t delta;
   int32_t tau;
   const double* kappa;
+  int32_t partition;  /* BPJD_PART_BOXES (0) | BPJD_PART_TRIANGLES */
 } bpjd_mesh;
 
 typedef struct {
@@ -326,7 +338,8 @@ typedef struct {
   bpjd_partition part;
 } bpjd_problem;
 
-/* Assembles K, M, P, P0 and the box partition on the host.  Errors: BAD_ARG. */
+/* Assembles K, M, P, P0 and the partition on the host.  Errors: BAD_ARG (also for
+ * a triangle partition on another kind, unequal axes, or 2 delta >= nx / nsub). */
 int bpjd_problem_create(const bpjd_mesh* mesh, bpjd_problem** out);
 void bpjd_problem_free(bpjd_problem* p);
 

@@ -310,10 +310,10 @@ extern "C" int bpjd_setup(const bpjd_csr* A, const bpjd_csr* M, const bpjd_csr* 
   h->max_iter = opts->max_iter > 0 ? opts->max_iter : 500;
   h->drop_tol = opts->drop_tol > 0 ? opts->drop_tol : 1e-10;
   // reuse of the local factors while the shifts stay within a relative tolerance
-  // (default 1e-6 with FP32 local solves; exact shifts for BPJD_FP64 or a negative value)
+  // (default 1e-4 with FP32 local solves; exact shifts for BPJD_FP64 or a negative value)
   h->refactor_tol = opts->local_refactor_tol > 0
                         ? opts->local_refactor_tol
-                        : ((opts->local_refactor_tol == 0 && opts->precision != BPJD_FP64) ? 1e-6 : 0.0);
+                        : ((opts->local_refactor_tol == 0 && opts->precision != BPJD_FP64) ? 1e-4 : 0.0);
   h->stream = (cudaStream_t)opts->stream;
 
   {
@@ -518,41 +518,8 @@ extern "C" int bpjd_setup(const bpjd_csr* A, const bpjd_csr* M, const bpjd_csr* 
     CK(cudaMemcpyAsync(h->rt_pos, rtpos.data(), sizeof(int32_t) * sum_nl, cudaMemcpyHostToDevice, h->stream));
 
     pt.mark("inverse_map", h->stream);
-    // coarse eigenbases (host threads started above)
-    {
-      EigResult r = eigP.get();
-      if ((rc = r.rc) != BPJD_OK) goto fail;
-      lamH = std::move(r.lam);
-      Phi = std::move(r.Phi);
-      if (P0) {
-        EigResult r0 = eigP0.get();
-        if ((rc = r0.rc) != BPJD_OK) goto fail;
-        lam0H = std::move(r0.lam);
-        Phi0 = std::move(r0.Phi);
-      }
-    }
-    if ((lamH[k] - lamH[k - 1]) <= 1e-8 * std::fabs(lamH[k]) ||
-        (P0 && (lam0H[k] - lam0H[k - 1]) <= 1e-8 * std::fabs(lam0H[k]))) {
-      rc = BPJD_ERR_GAP;
-      goto fail;
-    }
-    CK(dalloc(*h, &h->Phi, (size_t)h->nH * h->nH));
-    CK(dalloc(*h, &h->lamH, (size_t)h->nH));
-    CK(cudaMemcpyAsync(h->Phi, Phi.data(), sizeof(double) * h->nH * h->nH, cudaMemcpyHostToDevice, h->stream));
-    CK(cudaMemcpyAsync(h->lamH, lamH.data(), sizeof(double) * h->nH, cudaMemcpyHostToDevice, h->stream));
-    pt.mark("coarse_eig_join", h->stream);
-    // initial guess X0 = P0 Phi0[:, :k] (Step 1)
-    CK(dalloc(*h, &h->X0, (size_t)n * k));
-    CK(dalloc(*h, &h->lam0, (size_t)k));
-    if (P0) {
-      CK(dalloc(tmp0, &dPhi0, (size_t)h->nH0 * h->nH0));
-      CK(cudaMemcpyAsync(dPhi0, Phi0.data(), sizeof(double) * h->nH0 * h->nH0, cudaMemcpyHostToDevice, h->stream));
-      CKI(launch_csr_times_dense(dP0, dPhi0, h->nH0, k, h->X0, k, h->stream));
-    } else {
-      CKI(launch_csr_times_dense(h->P, h->Phi, h->nH, k, h->X0, k, h->stream));
-    }
-    pt.mark("initial_guess", h->stream);
-    // scratch and iteration vectors
+    // scratch and iteration vectors (allocated while the host threads finish the
+    // coarse eigensolves)
     {
       // the band factors of every (subdomain, shift) pair are written by the
       // factorisation and read back by the backward sweep; subdomains are taken in
@@ -607,13 +574,48 @@ extern "C" int bpjd_setup(const bpjd_csr* A, const bpjd_csr* M, const bpjd_csr* 
       double* cb[12] = {h->X, h->AX, h->MX, h->Xn, h->AXn, h->MXn, h->Pd, h->APd, h->MPd, h->Pd2, h->APd2, h->MPd2};
       for (int q = 0; q < 12; ++q) h->canon[q] = cb[q];
     }
+    pt.mark("alloc", h->stream);
+    // coarse eigenbases (host threads started above)
+    {
+      EigResult r = eigP.get();
+      if ((rc = r.rc) != BPJD_OK) goto fail;
+      lamH = std::move(r.lam);
+      Phi = std::move(r.Phi);
+      if (P0) {
+        EigResult r0 = eigP0.get();
+        if ((rc = r0.rc) != BPJD_OK) goto fail;
+        lam0H = std::move(r0.lam);
+        Phi0 = std::move(r0.Phi);
+      }
+    }
+    if ((lamH[k] - lamH[k - 1]) <= 1e-8 * std::fabs(lamH[k]) ||
+        (P0 && (lam0H[k] - lam0H[k - 1]) <= 1e-8 * std::fabs(lam0H[k]))) {
+      rc = BPJD_ERR_GAP;
+      goto fail;
+    }
+    CK(dalloc(*h, &h->Phi, (size_t)h->nH * h->nH));
+    CK(dalloc(*h, &h->lamH, (size_t)h->nH));
+    CK(cudaMemcpyAsync(h->Phi, Phi.data(), sizeof(double) * h->nH * h->nH, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->lamH, lamH.data(), sizeof(double) * h->nH, cudaMemcpyHostToDevice, h->stream));
+    pt.mark("coarse_eig_join", h->stream);
+    // initial guess X0 = P0 Phi0[:, :k] (Step 1)
+    CK(dalloc(*h, &h->X0, (size_t)n * k));
+    CK(dalloc(*h, &h->lam0, (size_t)k));
+    if (P0) {
+      CK(dalloc(tmp0, &dPhi0, (size_t)h->nH0 * h->nH0));
+      CK(cudaMemcpyAsync(dPhi0, Phi0.data(), sizeof(double) * h->nH0 * h->nH0, cudaMemcpyHostToDevice, h->stream));
+      CKI(launch_csr_times_dense(dP0, dPhi0, h->nH0, k, h->X0, k, h->stream));
+    } else {
+      CKI(launch_csr_times_dense(h->P, h->Phi, h->nH, k, h->X0, k, h->stream));
+    }
+    pt.mark("initial_guess", h->stream);
     CK(cudaStreamSynchronize(h->stream));
     if (dposK) cudaFree(dposK);
     if (dposM) cudaFree(dposM);
     dposK = dposM = nullptr;
     for (void* p : tmp0.allocs) cudaFree(p);
     tmp0.allocs.clear();
-    pt.mark("alloc", h->stream);
+    pt.mark("release", h->stream);
     pt.emit();
     h->t_setup = now_s() - t0;
     *out = reinterpret_cast<bpjd_handle*>(h);

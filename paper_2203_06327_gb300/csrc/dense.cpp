@@ -15,6 +15,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <numeric>
 #include <atomic>
 #include <thread>
@@ -294,6 +295,29 @@ bool tridiag_qr(int n, std::vector<double>& d, std::vector<double>& e, std::vect
   return true;
 }
 
+// The rotation sequence applied to nr rows (row stride ldz) starting at z0: each
+// row's pair of entries (k, k+1) is loaded for all rows first, then stored, so
+// that the rows proceed independently.  NR > 0 fixes the row count.
+template <int NR>
+void rotate_rows(const std::vector<Rot>& rots, double* z0, int ldz, int nr) {
+  constexpr int kMax = 8;
+  const int cnt = NR > 0 ? NR : nr;
+  for (const Rot& g : rots) {
+    double* z = z0 + g.k;
+    double a[kMax], b[kMax];
+#pragma GCC unroll 8
+    for (int i = 0; i < cnt; ++i) {
+      a[i] = z[(size_t)i * ldz];
+      b[i] = z[(size_t)i * ldz + 1];
+    }
+#pragma GCC unroll 8
+    for (int i = 0; i < cnt; ++i) {
+      z[(size_t)i * ldz] = g.c * a[i] - g.s * b[i];
+      z[(size_t)i * ldz + 1] = g.s * a[i] + g.c * b[i];
+    }
+  }
+}
+
 // Zc (n x n, column-major: column j contiguous) <- Q Zc with Q = H_0 ... H_{n-3},
 // for the columns [c0, c1): reflectors applied in reverse order.
 void apply_q(int n, const Reflectors& R, std::vector<double>& Zc, int c0, int c1) {
@@ -416,21 +440,29 @@ int sym_eig_host(int n, std::vector<double> A, std::vector<double>& lam, std::ve
   std::vector<Rot> rots;
   rots.reserve((size_t)2 * n * n);
   if (!tridiag_qr(n, d, e, &rots)) return BPJD_ERR_BREAKDOWN;
-  // eigenvectors of T: the rotations applied to the identity (Zc column-major;
-  // each thread updates its own range of rows of every column pair)
-  std::vector<double> Zc((size_t)n * n, 0.0);
-  for (int i = 0; i < n; ++i) Zc[(size_t)i * n + i] = 1.0;
+  // eigenvectors of T: the rotations applied to the identity.  Rows are
+  // independent (a rotation mixes two columns within each row), so each thread
+  // takes a range of rows of a row-major copy (rows padded to whole cache lines,
+  // so no two threads write the same line) and applies the whole rotation
+  // sequence to eight rows at a time; then the result is transposed into the
+  // column-major Zc of the reflector back-transformation.
+  const int ldz = (n + 7) & ~7;
+  std::vector<double> zbuf((size_t)n * ldz + 8, 0.0);
+  double* Zr = zbuf.data() + ((8 - ((reinterpret_cast<uintptr_t>(zbuf.data()) / sizeof(double)) & 7)) & 7);
+  for (int i = 0; i < n; ++i) Zr[(size_t)i * ldz + i] = 1.0;
   parallel_ranges(n, [&](int r0, int r1) {
-    for (const Rot& g : rots) {
-      double* zk = &Zc[(size_t)g.k * n];
-      double* zk1 = &Zc[(size_t)(g.k + 1) * n];
-      for (int i = r0; i < r1; ++i) {
-        const double a = zk[i], b = zk1[i];
-        zk[i] = g.c * a - g.s * b;
-        zk1[i] = g.s * a + g.c * b;
-      }
+    for (int i0 = r0; i0 < r1; i0 += 8) {
+      const int nr = std::min(8, r1 - i0);
+      double* z0 = Zr + (size_t)i0 * ldz;
+      if (nr == 8)
+        rotate_rows<8>(rots, z0, ldz, 8);
+      else
+        rotate_rows<0>(rots, z0, ldz, nr);
     }
   });
+  std::vector<double> Zc((size_t)n * n);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) Zc[(size_t)j * n + i] = Zr[(size_t)i * ldz + j];
   parallel_ranges(n, [&](int c0, int c1) { apply_q(n, R, Zc, c0, c1); });
   std::vector<int> ord(n);
   std::iota(ord.begin(), ord.end(), 0);
