@@ -36,5 +36,8 @@ def build(spec) -> OracleProblem:
     K, M = fem.assemble(spec)
     P = coarse.prolongation(spec)
     P0 = P if spec.tau == 0 else coarse.prolongation(spec.initial_grid())
-    ptr, dofs, col, nc = partition.box_partition(spec)
+    if getattr(spec, "partition", "boxes") == "triangles":
+        ptr, dofs, col, nc = partition.triangle_partition(spec.n[0], spec.nsub[0], spec.delta)
+    else:
+        ptr, dofs, col, nc = partition.box_partition(spec)
     return OracleProblem(spec, K, M, P, P0, ptr, dofs, col, nc)

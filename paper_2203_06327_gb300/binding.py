@@ -82,7 +82,7 @@ class ServerOpts(C.Structure):
 
 class MeshS(C.Structure):
     _fields_ = [("kind", C.c_int32), ("n", C.c_int32 * 3), ("length", C.c_double * 3), ("nsub", C.c_int32 * 3),
-                ("delta", C.c_int32), ("tau", C.c_int32), ("kappa", C.c_void_p)]
+                ("delta", C.c_int32), ("tau", C.c_int32), ("kappa", C.c_void_p), ("partition", C.c_int32)]
 
 
 class ProblemS(C.Structure):
@@ -237,7 +237,11 @@ def _copy_csr(c: Csr) -> CsrArrays:
     return CsrArrays(c.n_rows, c.n_cols, rp, ci, v)
 
 
-def problem_create(kind: str, n, length, nsub, delta: int, tau: int = 0, kappa: Optional[np.ndarray] = None) -> Problem:
+_PARTITIONS = {"boxes": 0, "triangles": 1}
+
+
+def problem_create(kind: str, n, length, nsub, delta: int, tau: int = 0, kappa: Optional[np.ndarray] = None,
+                   partition: str = "boxes") -> Problem:
     m = MeshS()
     m.kind = _KINDS[kind]
     for d in range(3):
@@ -246,6 +250,7 @@ def problem_create(kind: str, n, length, nsub, delta: int, tau: int = 0, kappa: 
         m.nsub[d] = int(nsub[d]) if d < len(nsub) else 1
     m.delta = int(delta)
     m.tau = int(tau)
+    m.partition = _PARTITIONS[partition]
     kap = None
     if kappa is not None:
         kap = np.ascontiguousarray(kappa, dtype=np.float64)
@@ -268,7 +273,8 @@ def problem_create(kind: str, n, length, nsub, delta: int, tau: int = 0, kappa: 
 
 def problem_from_spec(spec) -> Problem:
     """Builds the library's own problem arrays for a ``workloads.ProblemSpec``."""
-    return problem_create(spec.kind, spec.n, spec.length, spec.nsub, spec.delta, spec.tau, spec.kappa)
+    return problem_create(spec.kind, spec.n, spec.length, spec.nsub, spec.delta, spec.tau, spec.kappa,
+                          getattr(spec, "partition", "boxes"))
 
 
 # ---- solver -------------------------------------------------------------------

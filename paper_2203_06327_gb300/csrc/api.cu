@@ -326,8 +326,6 @@ extern "C" int bpjd_setup(const bpjd_csr* A, const bpjd_csr* M, const bpjd_csr* 
     std::vector<double> lamH, Phi, lam0H, Phi0;
     int64_t sum_nl;
     int bw = 0;
-    int64_t* dposK = nullptr;
-    int64_t* dposM = nullptr;
     std::vector<int32_t> rtp, rtpos;
     CsrDev dP0, dP0T;
     double* dPhi0 = nullptr;
@@ -482,24 +480,26 @@ extern "C" int bpjd_setup(const bpjd_csr* A, const bpjd_csr* M, const bpjd_csr* 
         goto fail;
       }
     }
-    {
-      const int B = h->B;
-      CK(dalloc(*h, &h->bandK, (size_t)sum_nl * B));
-      CK(dalloc(*h, &h->bandM, (size_t)sum_nl * B));
-      if (h->local_f32()) {
-        const size_t W = (size_t)std::max(h->B, h->Bpad);
-        CK(dalloc(*h, &h->bandKf, (size_t)sum_nl * W));
-        CK(dalloc(*h, &h->bandMf, (size_t)sum_nl * W));
-      }
-      CK(cudaMalloc(&dposK, sizeof(int64_t) * sum_nl * B));
-      CKI(launch_band_pos(*h, h->A, dposK));
-      CKI(launch_band_gather(*h, dposK, h->A.val, h->bandK, h->bandKf));
+    // band rows of the local matrices: FP32 (padded to the kernel tier) for FP32
+    // local solves, FP64 otherwise
+    if (h->local_f32()) {
+      const size_t W = (size_t)std::max(h->B, h->Bpad);
+      CK(dalloc(*h, &h->bandKf, (size_t)sum_nl * W));
+      CK(dalloc(*h, &h->bandMf, (size_t)sum_nl * W));
       if (h->same_pattern) {
-        CKI(launch_band_gather(*h, dposK, h->M.val, h->bandM, h->bandMf));
+        CKI(launch_band_fill(*h, h->A, h->M.val, nullptr, nullptr, h->bandKf, h->bandMf));
       } else {
-        CK(cudaMalloc(&dposM, sizeof(int64_t) * sum_nl * B));
-        CKI(launch_band_pos(*h, h->M, dposM));
-        CKI(launch_band_gather(*h, dposM, h->M.val, h->bandM, h->bandMf));
+        CKI(launch_band_fill(*h, h->A, nullptr, nullptr, nullptr, h->bandKf, nullptr));
+        CKI(launch_band_fill(*h, h->M, nullptr, nullptr, nullptr, h->bandMf, nullptr));
+      }
+    } else {
+      CK(dalloc(*h, &h->bandK, (size_t)sum_nl * h->B));
+      CK(dalloc(*h, &h->bandM, (size_t)sum_nl * h->B));
+      if (h->same_pattern) {
+        CKI(launch_band_fill(*h, h->A, h->M.val, h->bandK, h->bandM, nullptr, nullptr));
+      } else {
+        CKI(launch_band_fill(*h, h->A, nullptr, h->bandK, nullptr, nullptr, nullptr));
+        CKI(launch_band_fill(*h, h->M, nullptr, h->bandM, nullptr, nullptr, nullptr));
       }
     }
     pt.mark("bands", h->stream);
@@ -610,9 +610,6 @@ extern "C" int bpjd_setup(const bpjd_csr* A, const bpjd_csr* M, const bpjd_csr* 
     }
     pt.mark("initial_guess", h->stream);
     CK(cudaStreamSynchronize(h->stream));
-    if (dposK) cudaFree(dposK);
-    if (dposM) cudaFree(dposM);
-    dposK = dposM = nullptr;
     for (void* p : tmp0.allocs) cudaFree(p);
     tmp0.allocs.clear();
     pt.mark("release", h->stream);
@@ -621,8 +618,6 @@ extern "C" int bpjd_setup(const bpjd_csr* A, const bpjd_csr* M, const bpjd_csr* 
     *out = reinterpret_cast<bpjd_handle*>(h);
     return BPJD_OK;
   fail:
-    if (dposK) cudaFree(dposK);
-    if (dposM) cudaFree(dposM);
     if (eigP.valid()) eigP.wait();
     if (eigP0.valid()) eigP0.wait();
     cudaStreamSynchronize(h->stream);

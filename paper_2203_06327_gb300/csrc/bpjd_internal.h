@@ -67,10 +67,10 @@ struct Handle {
   int32_t* sub_dofs = nullptr;
   int32_t* rt_ptr = nullptr;   // n + 1: inverse map dof -> packed local positions
   int32_t* rt_pos = nullptr;   // sum_nl, packed position sub_ptr[l] + p
-  double* bandK = nullptr;     // sum_nl x B, row p holds K_l(p, p-B+1 .. p)
+  double* bandK = nullptr;     // FP64 local solves: sum_nl x B, row p holds K_l(p, p-B+1 .. p)
   double* bandM = nullptr;
-  float* bandKf = nullptr;     // FP32 copies for the mixed path
-  float* bandMf = nullptr;
+  float* bandKf = nullptr;     // FP32 local solves: sum_nl x max(B, Bpad), the same rows
+  float* bandMf = nullptr;     //   left-padded with zeros
 
   // ---- scratch
   void* Lbuf = nullptr;        // band factors of one chunk of subdomains (FP32 or FP64)
@@ -197,9 +197,12 @@ int launch_validate_csr(const CsrDev& c, int32_t* flag, cudaStream_t s);
 int launch_same_pattern(const CsrDev& a, const CsrDev& m, int32_t* flag, cudaStream_t s);
 int launch_validate_part(Handle& h, int32_t* flag);
 int launch_band_width(Handle& h, const CsrDev& c, int32_t* bw);
-int launch_band_pos(Handle& h, const CsrDev& c, int64_t* pos);
 int launch_split_values(const double* v, int64_t nnz, float2* out, cudaStream_t s);
-int launch_band_gather(Handle& h, const int64_t* pos, const double* val, double* out, float* outf);
+// band rows of the local matrices of c (and of a second matrix with c's pattern,
+// values val2): FP32 rows of width max(B, Bpad) into outf / outf2 when outf is
+// set, else FP64 rows of width B into out / out2
+int launch_band_fill(Handle& h, const CsrDev& c, const double* val2, double* out, double* out2, float* outf,
+                     float* outf2);
 int launch_galerkin(const CsrDev& A, const CsrDev& Msp, const CsrDev& P, const CsrDev& PT, double* KH,
                     double* MH, cudaStream_t s);
 

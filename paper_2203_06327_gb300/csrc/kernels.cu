@@ -2299,10 +2299,21 @@ __global__ void k_band_width(int nsub, int64_t total, const int64_t* __restrict_
   if (m > 0) atomicMax(bw, m);
 }
 
-// band gather positions: pos[(off + p) B + (q - p + B - 1)] = CSR index of (dofs[p], dofs[q])
-__global__ void k_band_pos(int nsub, int64_t total, const int64_t* __restrict__ sub_ptr,
-                           const int32_t* __restrict__ dofs, const int64_t* __restrict__ rp,
-                           const int32_t* __restrict__ ci, int B, int64_t* __restrict__ pos) {
+// ---------------------------------------------------------------------------
+// Setup kernels
+// ---------------------------------------------------------------------------
+// Band rows of the local matrices (principal submatrices of a CSR matrix on the
+// ascending subdomain dof lists), one thread per local row p of a subdomain:
+// the row of width W holds A_l(p, p - B + 1 .. p) in its last B positions
+// (the diagonal last), zero where A_l has no entry and in the W - B leading
+// pad positions; values rounded to T.  val2 / out2 (optional): a second
+// matrix with the same pattern, filled alongside.
+template <typename T>
+__global__ void k_band_fill(int nsub, int64_t total, const int64_t* __restrict__ sub_ptr,
+                            const int32_t* __restrict__ dofs, const int64_t* __restrict__ rp,
+                            const int32_t* __restrict__ ci, const double* __restrict__ val,
+                            const double* __restrict__ val2, int B, int W, T* __restrict__ out,
+                            T* __restrict__ out2) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= total) return;
   const int l = sub_of(nsub, sub_ptr, t);
@@ -2310,35 +2321,21 @@ __global__ void k_band_pos(int nsub, int64_t total, const int64_t* __restrict__ 
   const int nl = (int)(sub_ptr[l + 1] - off);
   const int p = (int)(t - off);
   const int32_t g = dofs[t];
-  int64_t* out = pos + t * B;
-  for (int e = 0; e < B; ++e) out[e] = -1;
+  T* o = out + t * W;
+  T* o2 = out2 ? out2 + t * W : nullptr;
+  for (int e = 0; e < W; ++e) o[e] = T(0);
+  if (o2)
+    for (int e = 0; e < W; ++e) o2[e] = T(0);
   for (int64_t e = rp[g]; e < rp[g + 1]; ++e) {
     const int32_t c = ci[e];
     if (c > g) break;
     const int q = local_index(dofs + off, nl, c);
-    if (q >= 0 && p - q < B) out[q - p + B - 1] = e;
+    if (q >= 0 && p - q < B) {
+      const int slot = (W - B) + (q - p + B - 1);
+      o[slot] = (T)val[e];
+      if (o2) o2[slot] = (T)val2[e];
+    }
   }
-}
-
-// ---------------------------------------------------------------------------
-// Setup kernels
-// ---------------------------------------------------------------------------
-__global__ void k_band_gather(int64_t total, const int64_t* __restrict__ pos, const double* __restrict__ val,
-                              double* out) {
-  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= total) return;
-  int64_t p = pos[t];
-  out[t] = (p >= 0) ? val[p] : 0.0;
-}
-
-// FP32 copy of a band of width B into width W >= B, zero-padded on the left
-// (the diagonal stays in the last position of each row).
-__global__ void k_band_pad_f32(int64_t rows, int B, int W, const double* __restrict__ in, float* __restrict__ out) {
-  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= rows * W) return;
-  const int64_t r = t / W;
-  const int e = (int)(t % W) - (W - B);
-  out[t] = (e >= 0) ? (float)in[r * B + e] : 0.f;
 }
 
 // Galerkin products K_H = P^T K P and M_H = P^T M P in two deterministic passes.
@@ -2936,13 +2933,16 @@ int launch_split_values(const double* v, int64_t nnz, float2* out, cudaStream_t 
   return (int)cudaGetLastError();
 }
 
-int launch_band_gather(Handle& h, const int64_t* pos, const double* val, double* out, float* outf) {
-  int64_t total = h.sum_nl * h.B;
-  k_band_gather<<<(unsigned)((total + 255) / 256), 256, 0, h.stream>>>(total, pos, val, out);
+int launch_band_fill(Handle& h, const CsrDev& c, const double* val2, double* out, double* out2, float* outf,
+                     float* outf2) {
+  const unsigned blocks = (unsigned)((h.sum_nl + 127) / 128);
   if (outf) {
     const int W = std::max(h.B, h.Bpad);
-    const int64_t tw = h.sum_nl * W;
-    k_band_pad_f32<<<(unsigned)((tw + 255) / 256), 256, 0, h.stream>>>(h.sum_nl, h.B, W, out, outf);
+    k_band_fill<float><<<blocks, 128, 0, h.stream>>>(h.nsub, h.sum_nl, h.sub_ptr, h.sub_dofs, c.row_ptr, c.col, c.val,
+                                                     val2, h.B, W, outf, outf2);
+  } else {
+    k_band_fill<double><<<blocks, 128, 0, h.stream>>>(h.nsub, h.sum_nl, h.sub_ptr, h.sub_dofs, c.row_ptr, c.col,
+                                                      c.val, val2, h.B, h.B, out, out2);
   }
   return (int)cudaGetLastError();
 }
@@ -2972,11 +2972,6 @@ int launch_band_width(Handle& h, const CsrDev& c, int32_t* bw) {
   return (int)cudaGetLastError();
 }
 
-int launch_band_pos(Handle& h, const CsrDev& c, int64_t* pos) {
-  k_band_pos<<<(unsigned)((h.sum_nl + 127) / 128), 128, 0, h.stream>>>(h.nsub, h.sum_nl, h.sub_ptr, h.sub_dofs,
-                                                                       c.row_ptr, c.col, h.B, pos);
-  return (int)cudaGetLastError();
-}
 
 int launch_galerkin(const CsrDev& A, const CsrDev& Msp, const CsrDev& P, const CsrDev& PT, double* KH,
                     double* MH, cudaStream_t s) {

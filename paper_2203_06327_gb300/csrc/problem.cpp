@@ -41,6 +41,7 @@ struct ProblemImpl {
   CsrBuf K, M, P, P0;
   std::vector<int64_t> sub_ptr;
   std::vector<int32_t> sub_dofs, sub_color;
+  int32_t n_colors = 0;  // 0: 2^dim (box partitions)
 };
 
 struct Entry {
@@ -292,6 +293,75 @@ void box_partition(const bpjd_mesh& m, int dim, ProblemImpl& P, int dofs_per_nod
         for (int d = 0; d < dim; ++d) col |= (s[d] & 1) << d;
         P.sub_color.push_back(col);
       }
+}
+
+// The partition J_H of Example 6.1 (Section 6) on the P1 grid of kind 0 (n x n
+// squares split SW->NE, S x S coarse squares of c = n / S cells): every coarse
+// square is cut along its own SW->NE diagonal into two coarse triangles, T = 0
+// below it (towards SE) and T = 1 above it, which the fine triangles resolve
+// exactly; each is enlarged by `rings` rings of fine triangles (Section 2.3:
+// whole elements added layer by layer; one ring adds every fine triangle that
+// shares a vertex with the region).  The local dofs are the interior nodes
+// whose six surrounding fine triangles all lie in the enlarged region (the
+// local functions vanish on its boundary), ascending.  Subdomain id
+// 2 (sx + S sy) + T, colour 2 ((sx mod 2) + 2 (sy mod 2)) + T: two coarse
+// triangles of one colour are at least c cells apart and each grows by `rings`
+// cells, so the colour classes stay disjoint (Assumption 2) while 2 rings < c
+// (checked by the caller).
+// Fine triangle (i, j, t) of cell (i, j): t = 0 has the vertices (i, j),
+// (i+1, j), (i+1, j+1); t = 1 has (i, j), (i+1, j+1), (i, j+1).
+void triangle_partition(int n, int S, int rings, ProblemImpl& P) {
+  const int c = n / S;
+  // cell offsets (di, dj) of the vertices of the two fine triangles of a cell
+  static const int vx[2][3] = {{0, 1, 1}, {0, 1, 0}}, vy[2][3] = {{0, 0, 1}, {0, 1, 1}};
+  P.sub_ptr.assign(1, 0);
+  P.sub_dofs.clear();
+  P.sub_color.clear();
+  std::vector<uint8_t> tri, node;
+  for (int sy = 0; sy < S; ++sy)
+    for (int sx = 0; sx < S; ++sx)
+      for (int T = 0; T < 2; ++T) {
+        // the enlarged region stays within `rings` cells of the coarse square
+        const int x0 = std::max(0, sx * c - rings), x1 = std::min(n, (sx + 1) * c + rings);
+        const int y0 = std::max(0, sy * c - rings), y1 = std::min(n, (sy + 1) * c + rings);
+        const int W = x1 - x0, H = y1 - y0;
+        auto at = [&](int t, int i, int j) -> uint8_t& { return tri[((size_t)t * H + (j - y0)) * W + (i - x0)]; };
+        auto nd = [&](int i, int j) -> uint8_t& { return node[(size_t)(j - y0) * (W + 1) + (i - x0)]; };
+        tri.assign((size_t)2 * W * H, 0);
+        for (int j = sy * c; j < (sy + 1) * c; ++j)
+          for (int i = sx * c; i < (sx + 1) * c; ++i) {
+            const int a = i - sx * c, b = j - sy * c;  // a > b: cell below the diagonal
+            at(0, i, j) = (T == 0) ? (a >= b) : (a < b);
+            at(1, i, j) = (T == 0) ? (a > b) : (a <= b);
+          }
+        for (int r = 0; r < rings; ++r) {
+          node.assign((size_t)(W + 1) * (H + 1), 0);
+          for (int t = 0; t < 2; ++t)
+            for (int j = y0; j < y1; ++j)
+              for (int i = x0; i < x1; ++i)
+                if (at(t, i, j))
+                  for (int v = 0; v < 3; ++v) nd(i + vx[t][v], j + vy[t][v]) = 1;
+          for (int t = 0; t < 2; ++t)
+            for (int j = y0; j < y1; ++j)
+              for (int i = x0; i < x1; ++i)
+                for (int v = 0; v < 3; ++v)
+                  if (nd(i + vx[t][v], j + vy[t][v])) at(t, i, j) = 1;
+        }
+        // interior node (i, j) is a vertex of t = 0 in the cells (i, j), (i-1, j),
+        // (i-1, j-1) and of t = 1 in (i, j), (i-1, j-1), (i, j-1)
+        auto in_region = [&](int t, int i, int j) {
+          return i >= x0 && i < x1 && j >= y0 && j < y1 && at(t, i, j) != 0;
+        };
+        for (int j = std::max(1, y0); j <= std::min(n - 1, y1); ++j)
+          for (int i = std::max(1, x0); i <= std::min(n - 1, x1); ++i) {
+            const bool all = in_region(0, i, j) && in_region(0, i - 1, j) && in_region(0, i - 1, j - 1) &&
+                             in_region(1, i, j) && in_region(1, i - 1, j - 1) && in_region(1, i, j - 1);
+            if (all) P.sub_dofs.push_back((int32_t)((int64_t)(j - 1) * (n - 1) + (i - 1)));
+          }
+        P.sub_ptr.push_back((int64_t)P.sub_dofs.size());
+        P.sub_color.push_back(2 * ((sx & 1) + 2 * (sy & 1)) + T);
+      }
+  P.n_colors = 8;
 }
 
 // Nodal interpolation of the coarse basis (same element kind on the grid of
@@ -951,6 +1021,10 @@ extern "C" int bpjd_problem_create(const bpjd_mesh* mesh, bpjd_problem** out) {
     if (m.n[d] < 2 || m.nsub[d] < 1 || m.n[d] % m.nsub[d] != 0 || !(m.length[d] > 0)) return BPJD_ERR_BAD_ARG;
   }
   if (m.delta < 0 || m.tau < 0 || m.tau > 6) return BPJD_ERR_BAD_ARG;
+  if (m.partition != BPJD_PART_BOXES && m.partition != BPJD_PART_TRIANGLES) return BPJD_ERR_BAD_ARG;
+  if (m.partition == BPJD_PART_TRIANGLES &&
+      (m.kind != 0 || m.n[0] != m.n[1] || m.nsub[0] != m.nsub[1] || !(2 * m.delta < m.n[0] / m.nsub[0])))
+    return BPJD_ERR_BAD_ARG;
   if (m.kind == 5 && (m.n[0] % 2 || m.nsub[0] % 2)) return BPJD_ERR_BAD_ARG;
   if (m.kind == 6) {
     if (m.n[0] % 2 || m.n[1] % 2 || m.nsub[0] % 2 || m.nsub[1] % 2) return BPJD_ERR_BAD_ARG;
@@ -1018,7 +1092,12 @@ extern "C" int bpjd_problem_create(const bpjd_mesh* mesh, bpjd_problem** out) {
           rc = coarse_interp(m, dim, S0, P->P0);
         }
       }
-      if (rc == BPJD_OK) box_partition(m, dim, *P);
+      if (rc == BPJD_OK) {
+        if (m.partition == BPJD_PART_TRIANGLES)
+          triangle_partition(m.n[0], m.nsub[0], m.delta, *P);
+        else
+          box_partition(m, dim, *P);
+      }
     }
   } catch (...) {
     rc = BPJD_ERR_OOM;
@@ -1035,7 +1114,7 @@ extern "C" int bpjd_problem_create(const bpjd_mesh* mesh, bpjd_problem** out) {
   P->pub.part.sub_ptr = P->sub_ptr.data();
   P->pub.part.sub_dofs = P->sub_dofs.data();
   P->pub.part.sub_color = P->sub_color.data();
-  P->pub.part.n_colors = 1 << dim;
+  P->pub.part.n_colors = P->n_colors ? P->n_colors : (1 << dim);
   *out = &P->pub;
   return BPJD_OK;
 }

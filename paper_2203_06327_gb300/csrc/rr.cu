@@ -1154,6 +1154,16 @@ __device__ __forceinline__ float rf_rotated(const float* A, int ld, const RFRot*
   return __fmaf_rn(rr.c, x, __fmul_rn(rr.g, y));
 }
 
+// The same entry from the four entries of A at rows {r, partner(r)} x columns
+// {c, partner(c)} held in registers (v_rc = a_{r,c}, v_rp = a_{r,pc}, v_pc = a_{pr,c},
+// v_pp = a_{pr,pc}) and the rotations (cr, gr) of r and (cc, gc) of c.
+__device__ __forceinline__ float rf_rot4(float cr, float gr, float cc, float gc, float v_rc, float v_rp, float v_pc,
+                                         float v_pp) {
+  const float x = __fmaf_rn(cc, v_rc, __fmul_rn(gc, v_rp));
+  const float y = __fmaf_rn(cc, v_pc, __fmul_rn(gc, v_pp));
+  return __fmaf_rn(cr, x, __fmul_rn(gr, y));
+}
+
 // Rotation annihilating a_pq (FP32; the angle need not be exact, phase B
 // refines the basis).  Returns false for an identity rotation.
 __device__ __forceinline__ bool rf_rotation(float app, float aqq, float apq, float floor_abs, float off_tol,
@@ -1331,33 +1341,37 @@ __device__ bool rr_refined_solve(int m, int k, const double* __restrict__ G, con
   const float floor_abs = 1e-7f * amax, off_tol = 1e-6f;
   const int wid = tid >> 5, lane = tid & 31;
   const int ut = tid - 32, nut = (int)blockDim.x - 32;  // update threads (warps 1..)
-  // this thread's lower-triangle entries of A and entries of V, (r << 8 | c), -1 past the end
-  constexpr int kNU = (kRFMax * (kRFMax + 1) / 2 + (kRFThreads - 32) - 1) / (kRFThreads - 32);
-  constexpr int kNV = (kRFMax * kRFMax + (kRFThreads - 32) - 1) / (kRFThreads - 32);
-  int ent[kNU], vent[kNV];
+  // Update items of warps 1.. for a round whose rotations pair (p_a, q_a), a < half:
+  //  * the 2 x 2 block of A at rows {p_a, q_a} x columns {p_b, q_b}, a >= b (code a << 8 | b):
+  //    its four entries are the only inputs of its four rotated entries, so each entry of A
+  //    is read once per round;
+  //  * rows x0 .. x0 + 3 of V at columns {p_b, q_b} (code 1 << 16 | x0 << 8 | b).
+  const int nblk = half * (half + 1) / 2, nvg = ((mp + 3) / 4) * half;
+  constexpr int kNI = ((kRFMax / 2) * (kRFMax / 2 + 1) / 2 + (kRFMax / 4) * (kRFMax / 2) + (kRFThreads - 32) - 1) /
+                      (kRFThreads - 32);
+  int item[kNI];
 #pragma unroll
-  for (int u = 0; u < kNU; ++u) {
+  for (int u = 0; u < kNI; ++u) {
     const int t = ut + u * nut;
-    int r = 0, c = 0;
-    const bool ok = ut >= 0 && t < ntri;
-    if (ok) tri_entry(t, r, c);
-    ent[u] = ok ? ((r << 8) | c) : -1;
-  }
-#pragma unroll
-  for (int u = 0; u < kNV; ++u) {
-    const int t = ut + u * nut;
-    const bool ok = ut >= 0 && t < mp * mp;
-    vent[u] = ok ? (((t / mp) << 8) | (t % mp)) : -1;
+    int code = -1;
+    if (ut >= 0 && t < nblk) {
+      int a = 0, b = 0;
+      tri_entry(t, a, b);
+      code = (a << 8) | b;
+    } else if (ut >= 0 && t < nblk + nvg) {
+      const int w = t - nblk;
+      code = (1 << 16) | ((4 * (w / half)) << 8) | (w % half);
+    }
+    item[u] = code;
   }
   __shared__ int rany[2];
   int sweeps = 0;
   for (; sweeps < 30; ++sweeps) {
     // any off-diagonal entry above the thresholds?  (warp 0: rotations of round 0)
     int need = 0;
-#pragma unroll
-    for (int u = 0; u < kNU; ++u) {
-      if (ent[u] < 0) continue;
-      const int r = ent[u] >> 8, c = ent[u] & 255;
+    for (int t = tid; t < ntri; t += blockDim.x) {
+      int r = 0, c = 0;
+      tri_entry(t, r, c);
       if (r != c) {
         float cc, ss;
         need |= rf_rotation(A[r * ld + r], A[c * ld + c], A[r * ld + c], floor_abs, off_tol, cc, ss) ? 1 : 0;
@@ -1395,20 +1409,47 @@ __device__ bool rr_refined_solve(int m, int k, const double* __restrict__ G, con
           if (lane == 0) rany[(round + 1) & 1] = any ? 1 : 0;
         }
       } else if (act) {
+        const int ri = round * half;
 #pragma unroll
-        for (int u = 0; u < kNU; ++u) {
-          if (ent[u] < 0) continue;
-          const int r = ent[u] >> 8, c = ent[u] & 255;
-          const float v = rf_rotated(A, ld, rc, r, c);
-          A2[r * ld + c] = v;
-          A2[c * ld + r] = v;
-        }
+        for (int u = 0; u < kNI; ++u) {
+          const int it = item[u];
+          if (it < 0) continue;
+          if (it >> 16) {
+            // V <- V J on four rows, columns p, q of pair b (rot[q].g = -rot[p].g)
+            const int x0 = (it >> 8) & 255;
+            const RFRot rp = rc[tp[ri + (it & 255)]];
+            const int pcol = tp[ri + (it & 255)], qcol = rp.partner;
+            const float gq = -rp.g;
+            const int x1 = min(x0 + 4, mp);
+            for (int x = x0; x < x1; ++x) {
+              const float vp = V[x * ld + pcol], vq = V[x * ld + qcol];
+              V2[x * ld + pcol] = __fmaf_rn(vp, rp.c, __fmul_rn(vq, rp.g));
+              V2[x * ld + qcol] = __fmaf_rn(vq, rp.c, __fmul_rn(vp, gq));
+            }
+          } else {
+            const int a = it >> 8, b = it & 255;
+            const int P1[2] = {tp[ri + a], tq[ri + a]}, P2[2] = {tp[ri + b], tq[ri + b]};
+            const RFRot r1 = rc[P1[0]], r2 = rc[P2[0]];
+            const float g1[2] = {r1.g, -r1.g}, g2[2] = {r2.g, -r2.g};
+            float w[2][2];
 #pragma unroll
-        for (int u = 0; u < kNV; ++u) {
-          if (vent[u] < 0) continue;
-          const int x = vent[u] >> 8, col = vent[u] & 255;
-          const RFRot rv = rc[col];
-          V2[x * ld + col] = __fmaf_rn(V[x * ld + col], rv.c, __fmul_rn(V[x * ld + rv.partner], rv.g));
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+              for (int j = 0; j < 2; ++j) w[i][j] = A[P1[i] * ld + P2[j]];
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+              for (int j = 0; j < 2; ++j) {
+                if (a == b && i < j) continue;  // the diagonal block's upper entry is its lower one
+                const int R = P1[i], Cc = P2[j];
+                // the entry is formed in the orientation row >= column, as rf_rotated does
+                const float v = (R >= Cc)
+                                    ? rf_rot4(r1.c, g1[i], r2.c, g2[j], w[i][j], w[i][1 - j], w[1 - i][j], w[1 - i][1 - j])
+                                    : rf_rot4(r2.c, g2[j], r1.c, g1[i], w[i][j], w[1 - i][j], w[i][1 - j], w[1 - i][1 - j]);
+                A2[R * ld + Cc] = v;
+                A2[Cc * ld + R] = v;
+              }
+          }
         }
       }
       __syncthreads();
@@ -1722,7 +1763,7 @@ __device__ bool rr_refined_solve(int m, int k, const double* __restrict__ G, con
 
 // Mixed-precision Rayleigh-Ritz launch of the refined form (m <= kRFMax); the
 // eigen-based path with dropping when phase A fails.
-__global__ void __launch_bounds__(kRFThreads) k_rayleigh_ritz_refined(
+__global__ void __launch_bounds__(kRFThreads, 1) k_rayleigh_ritz_refined(
     int m, int k, const double* __restrict__ G, const double* __restrict__ H, double drop_tol,
     const double* __restrict__ lam_old, double* C, double* lam_new, double* hist, int hist_rows, int row_host,
     const int32_t* d_row, int stop_rule, double tol, DevStatus* st) {

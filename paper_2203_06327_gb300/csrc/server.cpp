@@ -104,7 +104,7 @@ size_t estimate_bytes(const Request& r) {
   size_t b = 0;
   b += 2 * (n + 1) * 8 + nnz * (4 + 8 + 8);                 // K, M and their split values
   b += 2 * (r.P.ci.size() * 12 + (n + nH + 2) * 8);        // P and P^T
-  b += sum_nl * (size_t)B * 8 * 2 + sum_nl * (size_t)Bpad * 4 * 2;  // bands FP64 + FP32
+  b += sum_nl * std::max((size_t)B * 8, (size_t)Bpad * 4) * 2;  // bands of K_l and M_l (FP64, or FP32 padded)
   {
     // band factors (FP64 worst case), solved in chunks of subdomains within the
     // default 2 GiB scratch bound (at least one subdomain per chunk)

@@ -13,7 +13,8 @@ import pytest
 from conftest import ROOT
 from oracle import problem as oracle_problem
 from workloads import (config_c1, config_small_2d, config_small_3d, config_small_bfs, config_small_lshape,
-                       config_small_morley, config_table3_col1, config_table7_col1, ProblemSpec)
+                       config_small_morley, config_table1_col1, config_table3_col1, config_table7_col1,
+                       ProblemSpec)
 
 B = pytest.importorskip("paper_2203_06327_gb300.binding")
 
@@ -108,6 +109,40 @@ def test_c4_generators_match_oracle_full_size():
     np.testing.assert_array_equal(lp.part.sub_ptr, op.sub_ptr)
     np.testing.assert_array_equal(lp.part.sub_dofs, op.sub_dofs)
     np.testing.assert_array_equal(lp.part.sub_color, op.sub_color)
+
+
+@pytest.mark.parametrize("n,S,rings", [(128, 16, 2), (128, 16, 3), (64, 8, 1), (96, 4, 5), (256, 16, 6),
+                                        (48, 3, 0), (32, 2, 7)])
+def test_triangle_partition_matches_oracle(n, S, rings):
+    """Example 6.1's partition J_H (coarse squares cut along the SW->NE diagonal, each
+    coarse triangle grown by rings of fine triangles): the library's generator and the
+    oracle's, written independently from the same definition, agree bit for bit; the
+    matrices and the coarse interpolation are those of the box partition."""
+    from dataclasses import replace
+    spec = replace(config_table1_col1(), n=(n, n), nsub=(S, S), delta=rings, k=min(4, (S - 1) ** 2 - 1),
+                   partition="triangles")
+    lp = B.problem_from_spec(spec)
+    op = oracle_problem.build(spec)
+    np.testing.assert_array_equal(lp.part.sub_ptr, op.sub_ptr)
+    np.testing.assert_array_equal(lp.part.sub_dofs, op.sub_dofs)
+    np.testing.assert_array_equal(lp.part.sub_color, op.sub_color)
+    assert lp.part.n_colors == op.n_colors == 8
+    assert len(lp.part.sub_ptr) - 1 == 2 * S * S
+    box = B.problem_from_spec(replace(spec, partition="boxes"))
+    for a, b in ((lp.K, box.K), (lp.M, box.M), (lp.P, box.P)):
+        np.testing.assert_array_equal(a.col_idx, b.col_idx)
+        np.testing.assert_array_equal(a.val, b.val)
+
+
+def test_triangle_partition_rejects_bad_meshes():
+    for args in [dict(kind="p1_2d", n=(64, 64), nsub=(8, 8), delta=4),      # 2 delta = n / nsub
+                 dict(kind="p1_2d", n=(64, 32), nsub=(8, 4), delta=1),      # unequal axes
+                 dict(kind="p1_3d", n=(8, 8, 8), nsub=(2, 2, 2), delta=1),  # not the P1 square grid
+                 dict(kind="morley_2d", n=(16, 16), nsub=(4, 4), delta=1)]:
+        L = (1.0,) * len(args["n"])
+        with pytest.raises(B.BpjdError) as e:
+            B.problem_create(args["kind"], args["n"], L, args["nsub"], args["delta"], partition="triangles")
+        assert e.value.code == B.ERR_BAD_ARG
 
 
 def test_problem_create_rejects_bad_mesh():

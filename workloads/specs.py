@@ -22,6 +22,10 @@ class ProblemSpec:
     tol     : relative residual tolerance of the stop test
     tau     : the initial eigenproblem of Algorithm 3.1 Step 1 is solved on the
               coarse grid refined tau times (H~ = H / 2^tau); tau = 0 uses J_H
+    partition : "boxes" (nsub boxes per axis grown by delta element layers) or
+              "triangles" (p1_2d on a square grid: the partition of Example 6.1, every
+              coarse square cut along its SW->NE diagonal into two coarse triangles,
+              each grown by delta rings of fine triangles; 2 delta < n / nsub)
     """
 
     kind: str
@@ -35,6 +39,7 @@ class ProblemSpec:
     tau: int = 0
     name: str = ""
     extra: dict = field(default_factory=dict)
+    partition: str = "boxes"
 
     @property
     def dim(self) -> int:
@@ -102,6 +107,12 @@ class ProblemSpec:
         if self.kind == "q1_lshape" and (self.n[0] % 2 or self.n[1] % 2 or self.nsub[0] % 2 or self.nsub[1] % 2
                                          or self.kappa is not None):
             raise ValueError("q1_lshape: even x / y cell and subdomain counts, no coefficient")
+        if self.partition not in ("boxes", "triangles"):
+            raise ValueError(f"unknown partition {self.partition}")
+        if self.partition == "triangles" and (self.kind != "p1_2d" or self.n[0] != self.n[1]
+                                              or self.nsub[0] != self.nsub[1]
+                                              or not 2 * self.delta < self.n[0] // self.nsub[0]):
+            raise ValueError("triangles: p1_2d on a square grid with 2 delta < n / nsub")
         if self.k >= self.n_coarse:
             raise ValueError("k must be smaller than the coarse space dimension")
         ms = {m // s for m, s in zip(self.n, self.nsub)}
