@@ -55,6 +55,8 @@ def _args():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=64)
     ap.add_argument("--serving-workers", type=int, default=4)
+    ap.add_argument("--no-serving-fp64", action="store_true",
+                    help="skip the plain FP64 one-at-a-time baseline of the serving block")
     ap.add_argument("--refactor-tol", type=float, default=0.0,
                     help="relative shift change that re-forms the local factors (0: the library default)")
     ap.add_argument("--no-accuracy", action="store_true")
@@ -157,10 +159,11 @@ def spmm_bytes(nnz, n, k):
     return nnz * (4 + 16) + (n + 1) * 8 + 3 * n * k * 8
 
 
-# ncu dram__bytes_read.sum + dram__bytes_write.sum of one local-solve application on
-# C2 (k_local_factor_mma<40> + k_local_backward<40>), valid for the kernel source it
-# was measured on (sha256 of csrc/kernels.cu, first 16 hex digits); null otherwise
-LOCAL_TRAFFIC = {("c2_kappa_rect_p1_h512", "mixed"): (None, None)}
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of the local-solve kernels of one
+# C2 solve (k_local_factor_mma<40>, k_local_sweep_blk<40, 0/1>: 7 factorisations, 39
+# backward and 32 forward sweeps), divided by its 39 applications; valid for the kernel
+# source it was measured on (sha256 of csrc/kernels.cu, first 16 hex digits), null otherwise
+LOCAL_TRAFFIC = {("c2_kappa_rect_p1_h512", "mixed"): ("c794f34af717b20d", 1.264e9)}
 
 
 def _kernel_source_hash():
@@ -470,7 +473,7 @@ def run_serving(a, B):
         svc.append(time.perf_counter() - t0)
     # the plain FP64 solver, one request at a time (the baseline the served form is compared with)
     svc64 = []
-    for pb, r in zip(pbs, reqs):
+    for pb, r in zip(pbs, reqs) if not a.no_serving_fp64 else []:
         t0 = time.perf_counter()
         sv = B.Solver.from_problem(pb, r.spec.k, device=None, precision=B.FP64, subspace=B.W_3K)
         sv.solve(eigvecs="host")
@@ -506,7 +509,7 @@ def run_serving(a, B):
             "p99_latency_s": float(np.percentile(lat, 99)), "eigenpairs_per_s": ktot / makespan,
             "saturated_eigenpairs_per_s": ktot / sat,
             "one_at_a_time_eigenpairs_per_s": ktot / float(np.sum(svc)),
-            "fp64_one_at_a_time_eigenpairs_per_s": ktot / float(np.sum(svc64)),
+            "fp64_one_at_a_time_eigenpairs_per_s": ktot / float(np.sum(svc64)) if svc64 else None,
             "one_at_a_time_p50_service_s": float(np.percentile(svc, 50)), "failed": failed,
             "stream": "serving_stream(seed 0): P1 on 64..512 squares, random smooth kappa, k in 4..16, tau 1"}
 
