@@ -54,7 +54,9 @@ def _args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=64)
-    ap.add_argument("--serving-workers", type=int, default=4)
+    ap.add_argument("--serving-workers", type=int, default=8)
+    ap.add_argument("--serving-graph", action="store_true",
+                    help="run each served request's loop as a CUDA graph (default: host-driven loop)")
     ap.add_argument("--no-serving-fp64", action="store_true",
                     help="skip the plain FP64 one-at-a-time baseline of the serving block")
     ap.add_argument("--refactor-tol", type=float, default=0.0,
@@ -481,7 +483,7 @@ def run_serving(a, B):
         svc64.append(time.perf_counter() - t0)
     ktot = sum(r.spec.k for r in reqs)
     gap = 1.25 * float(np.mean(svc))
-    srv = B.Server(workers=a.serving_workers, precision=prec, subspace=B.W_3K)
+    srv = B.Server(workers=a.serving_workers, precision=prec, subspace=B.W_3K, host_loop=not a.serving_graph)
     lat, failed, tickets = [], 0, []
     t0 = time.perf_counter()
     for pb, r in zip(pbs, reqs):
@@ -496,7 +498,7 @@ def run_serving(a, B):
     makespan = time.perf_counter() - t0
     srv.close()
     # saturated: every request submitted at once (throughput of the served form)
-    srv = B.Server(workers=a.serving_workers, precision=prec, subspace=B.W_3K)
+    srv = B.Server(workers=a.serving_workers, precision=prec, subspace=B.W_3K, host_loop=not a.serving_graph)
     t0 = time.perf_counter()
     tickets2 = [srv.submit(pb, r.spec.k) for pb, r in zip(pbs, reqs)]
     for t in tickets2:

@@ -125,6 +125,10 @@ typedef struct {
                                < 0: exact shifts always.  Reuse needs every factor of one
                                application resident (one chunk) and a band window of at
                                most 152 */
+  int32_t host_loop;           /* 0 (default): after its first steps the iteration loop runs
+                               as one CUDA graph per handle, the stop test evaluated on the
+                               device; 1: the host drives every step (one synchronisation
+                               per step).  Results are bit-identical either way */
 } bpjd_opts;
 
 typedef struct {
@@ -364,7 +368,7 @@ void bpjd_problem_free(bpjd_problem* p);
 typedef struct {
   size_t  hbm_budget_bytes; /* device bytes the admitted requests may hold together;
                                0: 80% of the free device memory at creation */
-  int32_t workers;          /* concurrent solves, each on its own stream (default 4, 1..32) */
+  int32_t workers;          /* concurrent solves, each on its own stream (default 8, 1..32) */
   int32_t precision;        /* per-request options, as in bpjd_opts; defaults BPJD_MIXED, */
   int32_t subspace;         /*   BPJD_W_3K, BPJD_STOP_RESIDUAL, 1e-8, 500                  */
   int32_t stop_rule;
@@ -372,6 +376,8 @@ typedef struct {
   int32_t max_iter;
   int32_t admission;        /* BPJD_ADMIT_SMALLEST (default) | BPJD_ADMIT_FIFO */
   double  starvation_s;     /* aging limit of BPJD_ADMIT_SMALLEST (default 1 s) */
+  int32_t host_loop;        /* per-request loop mode, as in bpjd_opts; default 1, each
+                               request's loop driven by its worker thread */
 } bpjd_server_opts;
 
 typedef struct bpjd_server bpjd_server;

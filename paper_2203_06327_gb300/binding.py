@@ -65,7 +65,8 @@ class Opts(C.Structure):
     _fields_ = [("k", C.c_int32), ("precision", C.c_int32), ("subspace", C.c_int32), ("stop_rule", C.c_int32),
                 ("tol", C.c_double), ("max_iter", C.c_int32), ("drop_tol", C.c_double), ("H", C.c_double),
                 ("delta", C.c_double), ("inputs_on_device", C.c_int32), ("stream", C.c_void_p),
-                ("local_scratch_bytes", C.c_size_t), ("local_refactor_tol", C.c_double)]
+                ("local_scratch_bytes", C.c_size_t), ("local_refactor_tol", C.c_double),
+                ("host_loop", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -77,7 +78,7 @@ class Stats(C.Structure):
 class ServerOpts(C.Structure):
     _fields_ = [("hbm_budget_bytes", C.c_size_t), ("workers", C.c_int32), ("precision", C.c_int32),
                 ("subspace", C.c_int32), ("stop_rule", C.c_int32), ("tol", C.c_double), ("max_iter", C.c_int32),
-                ("admission", C.c_int32), ("starvation_s", C.c_double)]
+                ("admission", C.c_int32), ("starvation_s", C.c_double), ("host_loop", C.c_int32)]
 
 
 class MeshS(C.Structure):
@@ -284,12 +285,13 @@ class Solver:
     def __init__(self, K: CsrArrays, M: CsrArrays, P: CsrArrays, P0: Optional[CsrArrays], part: PartitionArrays,
                  k: int, precision: int = FP64, subspace: int = W_2K, stop_rule: int = STOP_RESIDUAL,
                  tol: float = 1e-8, max_iter: int = 500, drop_tol: float = 1e-10, stream=None,
-                 local_scratch_bytes: int = 0, local_refactor_tol: float = 0.0):
+                 local_scratch_bytes: int = 0, local_refactor_tol: float = 0.0, host_loop: bool = False):
         o = Opts()
         lib.bpjd_default_opts(C.byref(o))
         o.k, o.precision, o.subspace, o.stop_rule = k, precision, subspace, stop_rule
         o.local_scratch_bytes = int(local_scratch_bytes)
         o.local_refactor_tol = float(local_refactor_tol)
+        o.host_loop = 1 if host_loop else 0
         o.tol, o.max_iter, o.drop_tol = tol, max_iter, drop_tol
         o.inputs_on_device = 1 if _is_torch(K.val) and K.val.is_cuda else 0
         o.stream = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else stream)
@@ -394,15 +396,16 @@ class Server:
     admitted under a device-memory budget (smallest estimated work first with aging, or
     first-in first-out) and solved by worker threads with one CUDA stream each."""
 
-    def __init__(self, workers: int = 4, hbm_budget_bytes: int = 0, precision: int = MIXED,
+    def __init__(self, workers: int = 8, hbm_budget_bytes: int = 0, precision: int = MIXED,
                  subspace: int = W_3K, stop_rule: int = STOP_RESIDUAL, tol: float = 1e-8, max_iter: int = 500,
-                 admission: int = 0, starvation_s: float = 1.0):
+                 admission: int = 0, starvation_s: float = 1.0, host_loop: bool = True):
         o = ServerOpts()
         lib.bpjd_server_default_opts(C.byref(o))
         o.workers, o.hbm_budget_bytes = int(workers), int(hbm_budget_bytes)
         o.precision, o.subspace, o.stop_rule = precision, subspace, stop_rule
         o.tol, o.max_iter = float(tol), int(max_iter)
         o.admission, o.starvation_s = int(admission), float(starvation_s)
+        o.host_loop = 1 if host_loop else 0
         h = C.c_void_p()
         _check(lib.bpjd_server_create(C.byref(o), C.byref(h)), "bpjd_server_create")
         self._h = h

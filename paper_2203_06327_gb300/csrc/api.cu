@@ -159,37 +159,16 @@ cudaError_t upload_csr(Handle& h, const bpjd_csr* c, bool on_dev, CsrDev& d, boo
   return cudaSuccess;
 }
 
-cudaError_t upload_host_csr(Handle& h, const HostCsr& c, CsrDev& d) {
-  bpjd_csr v;
-  v.n_rows = c.n_rows;
-  v.n_cols = c.n_cols;
-  v.nnz = c.nnz;
-  v.row_ptr = c.rp;
-  v.col_idx = c.ci;
-  v.val = c.v;
-  return upload_csr(h, &v, false, d, true);
-}
-
-// Transpose of a host CSR (rows of the result sorted by column = original row).
-void transpose_host(const HostCsr& a, HostCsr& t) {
-  t.n_rows = a.n_cols;
-  t.n_cols = a.n_rows;
-  t.nnz = a.nnz;
-  t.rp_buf.assign((size_t)a.n_cols + 1, 0);
-  t.ci_buf.resize((size_t)std::max<int64_t>(a.nnz, 1));
-  t.v_buf.resize((size_t)std::max<int64_t>(a.nnz, 1));
-  for (int64_t e = 0; e < a.nnz; ++e) t.rp_buf[a.ci[e] + 1]++;
-  for (int32_t c = 0; c < a.n_cols; ++c) t.rp_buf[c + 1] += t.rp_buf[c];
-  std::vector<int64_t> fill(t.rp_buf.begin(), t.rp_buf.end() - 1);
-  for (int64_t r = 0; r < a.n_rows; ++r)
-    for (int64_t e = a.rp[r]; e < a.rp[r + 1]; ++e) {
-      int64_t dst = fill[a.ci[e]]++;
-      t.ci_buf[dst] = (int32_t)r;
-      t.v_buf[dst] = a.v[e];
-    }
-  t.rp = t.rp_buf.data();
-  t.ci = t.ci_buf.data();
-  t.v = t.v_buf.data();
+// Subdomain lists: sub_ptr starts at 0 and grows strictly, every list ascending
+// within [0, n).
+int validate_partition(int nsub, int n, const int64_t* sptr, const int32_t* sdofs) {
+  if (sptr[0] != 0) return BPJD_ERR_MAP_INVALID;
+  for (int l = 0; l < nsub; ++l) {
+    if (sptr[l + 1] <= sptr[l]) return BPJD_ERR_MAP_INVALID;
+    for (int64_t e = sptr[l]; e < sptr[l + 1]; ++e)
+      if (sdofs[e] < 0 || sdofs[e] >= n || (e > sptr[l] && sdofs[e] <= sdofs[e - 1])) return BPJD_ERR_MAP_INVALID;
+  }
+  return BPJD_OK;
 }
 
 // Galerkin products K_H = P^T K P and M_H = P^T M P on the device, copied to
@@ -315,13 +294,13 @@ extern "C" int bpjd_setup(const bpjd_csr* A, const bpjd_csr* M, const bpjd_csr* 
                         ? opts->local_refactor_tol
                         : ((opts->local_refactor_tol == 0 && opts->precision != BPJD_FP64) ? 1e-4 : 0.0);
   h->stream = (cudaStream_t)opts->stream;
+  h->host_loop = opts->host_loop != 0;
 
   {
-    HostCsr hP, hP0, hPT, hP0T;
     std::vector<int64_t> sub_ptr_buf;
     std::vector<int32_t> sub_dofs_buf;
-    const int64_t* sptr;
-    const int32_t* sdofs;
+    const int64_t* sptr = nullptr;
+    const int32_t* sdofs = nullptr;
     const int nsub = part->n_sub;
     std::vector<double> lamH, Phi, lam0H, Phi0;
     int64_t sum_nl;
@@ -335,64 +314,43 @@ extern "C" int bpjd_setup(const bpjd_csr* A, const bpjd_csr* M, const bpjd_csr* 
 
     if (!on_dev) {
       // host inputs are validated before any device work (device inputs on the device below)
-      HostCsr vA, vM;
+      HostCsr vA, vM, vP, vP0;
       host_view(A, false, false, vA);
       host_view(M, false, false, vM);
+      host_view(P, false, false, vP);
       if ((rc = validate_csr(vA)) != BPJD_OK) goto fail;
       if ((rc = validate_csr(vM)) != BPJD_OK) goto fail;
+      if ((rc = validate_csr(vP)) != BPJD_OK) goto fail;
+      if (P0) {
+        host_view(P0, false, false, vP0);
+        if ((rc = validate_csr(vP0)) != BPJD_OK) goto fail;
+      }
+      if ((rc = validate_partition(nsub, n, part->sub_ptr, part->sub_dofs)) != BPJD_OK) goto fail;
     }
-    if ((rc = host_view(P, on_dev, true, hP)) != BPJD_OK) goto fail;
-    if (P0 && (rc = host_view(P0, on_dev, true, hP0)) != BPJD_OK) goto fail;
-    if ((rc = validate_csr(hP)) != BPJD_OK) goto fail;
-    if (P0 && (rc = validate_csr(hP0)) != BPJD_OK) goto fail;
     h->nH = P->n_cols;
     h->nH0 = P0 ? P0->n_cols : P->n_cols;
     if (!(k < h->nH) || !(k < h->nH0)) {
       rc = BPJD_ERR_K_TOO_LARGE;
       goto fail;
     }
-    // partition
-    if (on_dev) {
-      sub_ptr_buf.resize(nsub + 1);
-      CK(cudaMemcpy(sub_ptr_buf.data(), part->sub_ptr, sizeof(int64_t) * (nsub + 1), cudaMemcpyDeviceToHost));
-      sub_dofs_buf.resize((size_t)std::max<int64_t>(sub_ptr_buf[nsub], 1));
-      if (sub_ptr_buf[nsub] > 0)
-        CK(cudaMemcpy(sub_dofs_buf.data(), part->sub_dofs, sizeof(int32_t) * sub_ptr_buf[nsub],
-                      cudaMemcpyDeviceToHost));
-      sptr = sub_ptr_buf.data();
-      sdofs = sub_dofs_buf.data();
-    } else {
-      sptr = part->sub_ptr;
-      sdofs = part->sub_dofs;
-    }
-    if (sptr[0] != 0) {
-      rc = BPJD_ERR_MAP_INVALID;
+    if (h->nH > kTransposeMaxCols || h->nH0 > kTransposeMaxCols) {
+      rc = BPJD_ERR_TOO_LARGE;
       goto fail;
     }
-    for (int l = 0; l < nsub; ++l) {
-      if (sptr[l + 1] <= sptr[l]) {
-        rc = BPJD_ERR_MAP_INVALID;
-        goto fail;
-      }
-      for (int64_t e = sptr[l]; e < sptr[l + 1]; ++e) {
-        if (sdofs[e] < 0 || sdofs[e] >= n || (e > sptr[l] && sdofs[e] <= sdofs[e - 1])) {
-          rc = BPJD_ERR_MAP_INVALID;
-          goto fail;
-        }
-      }
-      h->max_nl = std::max<int32_t>(h->max_nl, (int32_t)(sptr[l + 1] - sptr[l]));
-    }
-    sum_nl = sptr[nsub];
-    h->sum_nl = sum_nl;
-
-    pt.mark("host_views_validate", h->stream);
-    // device copies of the matrices, validated on the device
+    pt.mark("host_validate", h->stream);
+    // device copies of the matrices and interpolations, validated on the device
+    // before any kernel indexes with them
     CK(upload_csr(*h, A, on_dev, h->A));
     CK(upload_csr(*h, M, on_dev, h->M));
+    CK(upload_csr(*h, P, on_dev, h->P));
+    tmp0.stream = h->stream;
+    if (P0) CK(upload_csr(tmp0, P0, on_dev, dP0));
     CK(dalloc(*h, &h->derr, 4));
     CK(cudaMemsetAsync(h->derr, 0, 4 * sizeof(int32_t), h->stream));
     CKI(launch_validate_csr(h->A, h->derr, h->stream));
     CKI(launch_validate_csr(h->M, h->derr, h->stream));
+    CKI(launch_validate_csr(h->P, h->derr, h->stream));
+    if (P0) CKI(launch_validate_csr(dP0, h->derr, h->stream));
     if (A->nnz == M->nnz) CKI(launch_same_pattern(h->A, h->M, h->derr, h->stream));
     {
       int32_t flags = 0;
@@ -410,9 +368,14 @@ extern "C" int bpjd_setup(const bpjd_csr* A, const bpjd_csr* M, const bpjd_csr* 
       CKI(launch_split_values(h->A.val, A->nnz, h->Asplit, h->stream));
       CKI(launch_split_values(h->M.val, M->nnz, h->Msplit, h->stream));
     }
-    CK(upload_host_csr(*h, hP, h->P));
-    transpose_host(hP, hPT);
-    CK(upload_host_csr(*h, hPT, h->PT));
+    // P^T on the device (rows in ascending fine index)
+    h->PT.n_rows = h->nH;
+    h->PT.n_cols = n;
+    h->PT.nnz = P->nnz;
+    CK(dalloc(*h, &h->PT.row_ptr, (size_t)h->nH + 1));
+    CK(dalloc(*h, &h->PT.col, (size_t)P->nnz));
+    CK(dalloc(*h, &h->PT.val, (size_t)P->nnz));
+    CKI(launch_csr_transpose(h->P, h->PT.row_ptr, h->PT.col, h->PT.val, h->stream));
     // coarse pencils: Galerkin products on the device now, dense eigensolves on
     // host threads while the device-side setup below proceeds
     {
@@ -425,10 +388,13 @@ extern "C" int bpjd_setup(const bpjd_csr* A, const bpjd_csr* M, const bpjd_csr* 
         return r;
       });
       if (P0) {
-        tmp0.stream = h->stream;
-        CK(upload_host_csr(tmp0, hP0, dP0));
-        transpose_host(hP0, hP0T);
-        CK(upload_host_csr(tmp0, hP0T, dP0T));
+        dP0T.n_rows = h->nH0;
+        dP0T.n_cols = n;
+        dP0T.nnz = P0->nnz;
+        CK(dalloc(tmp0, &dP0T.row_ptr, (size_t)h->nH0 + 1));
+        CK(dalloc(tmp0, &dP0T.col, (size_t)P0->nnz));
+        CK(dalloc(tmp0, &dP0T.val, (size_t)P0->nnz));
+        CKI(launch_csr_transpose(dP0, dP0T.row_ptr, dP0T.col, dP0T.val, h->stream));
         tmp0.A = h->A;
         tmp0.M = h->M;
         tmp0.same_pattern = h->same_pattern;
@@ -443,12 +409,31 @@ extern "C" int bpjd_setup(const bpjd_csr* A, const bpjd_csr* M, const bpjd_csr* 
         });
       }
     }
+    pt.mark("validate_upload_galerkin", h->stream);
+    // partition (validated on the host while the coarse eigensolves run)
+    if (on_dev) {
+      sub_ptr_buf.resize(nsub + 1);
+      CK(cudaMemcpy(sub_ptr_buf.data(), part->sub_ptr, sizeof(int64_t) * (nsub + 1), cudaMemcpyDeviceToHost));
+      sub_dofs_buf.resize((size_t)std::max<int64_t>(sub_ptr_buf[nsub], 1));
+      if (sub_ptr_buf[nsub] > 0)
+        CK(cudaMemcpy(sub_dofs_buf.data(), part->sub_dofs, sizeof(int32_t) * sub_ptr_buf[nsub],
+                      cudaMemcpyDeviceToHost));
+      sptr = sub_ptr_buf.data();
+      sdofs = sub_dofs_buf.data();
+    } else {
+      sptr = part->sub_ptr;
+      sdofs = part->sub_dofs;
+    }
+    if (on_dev && (rc = validate_partition(nsub, n, sptr, sdofs)) != BPJD_OK) goto fail;
+    for (int l = 0; l < nsub; ++l) h->max_nl = std::max<int32_t>(h->max_nl, (int32_t)(sptr[l + 1] - sptr[l]));
+    sum_nl = sptr[nsub];
+    h->sum_nl = sum_nl;
     CK(dalloc(*h, &h->sub_ptr, (size_t)nsub + 1));
     CK(dalloc(*h, &h->sub_dofs, (size_t)sum_nl));
     CK(cudaMemcpyAsync(h->sub_ptr, sptr, sizeof(int64_t) * (nsub + 1), cudaMemcpyHostToDevice, h->stream));
     CK(cudaMemcpyAsync(h->sub_dofs, sdofs, sizeof(int32_t) * sum_nl, cudaMemcpyHostToDevice, h->stream));
 
-    pt.mark("upload", h->stream);
+    pt.mark("partition", h->stream);
     // band structure of every local matrix (principal submatrix on the subdomain
     // dofs), found on the device by binary search of the CSR columns in the
     // ascending dof lists
@@ -1003,7 +988,7 @@ extern "C" int bpjd_solve(bpjd_handle* hh, double* eigvals, double* eigvecs, int
   bool have_prev = false;
   // the loop runs as one CUDA graph once every step has the same shape (eager
   // when profiling or tracing, which need the host between kernels)
-  bool graph = graphs_enabled() && !h.profile && !trace_on();
+  bool graph = !h.host_loop && graphs_enabled() && !h.profile && !trace_on();
 
   std::vector<double> lam_h((size_t)k);
   h.factors_valid = false;
@@ -1033,11 +1018,11 @@ extern "C" int bpjd_solve(bpjd_handle* hh, double* eigvals, double* eigvecs, int
     if (trace_on())
       std::fprintf(stderr,
                    "{\"bpjd_iter\": %d, \"max_rel_resid\": %.6e, \"sum_abs_dlambda\": %.6e, \"kept\": %d, "
-                   "\"jacobi_sweeps\": %d, \"rr_kcycles\": [%lld, %lld, %lld, %lld, %lld, %lld, %lld]}\n",
+                   "\"jacobi_sweeps\": %d, \"rr_kcycles\": [%lld, %lld, %lld, %lld, %lld, %lld, %lld, %lld]}\n",
                    it, h.hstat->max_res, h.hstat->sum_dl, h.hstat->kept, h.hstat->sweeps,
                    h.hstat->rr_cycles[0] / 1000, h.hstat->rr_cycles[1] / 1000, h.hstat->rr_cycles[2] / 1000,
                    h.hstat->rr_cycles[3] / 1000, h.hstat->rr_cycles[4] / 1000, h.hstat->rr_cycles[5] / 1000,
-                   h.hstat->rr_cycles[6] / 1000);
+                   h.hstat->rr_cycles[6] / 1000, h.hstat->rr_cycles[7] / 1000);
     if (h.hstat->converged) {
       converged = true;
       break;

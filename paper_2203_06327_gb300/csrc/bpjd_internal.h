@@ -77,6 +77,7 @@ struct Handle {
   std::vector<int32_t> chunk_l0;   // chunk c = subdomains [chunk_l0[c], chunk_l0[c + 1])
   std::vector<int64_t> chunk_off;  // sub_ptr of each chunk's first subdomain (record base)
   double refactor_tol = 0.0;       // reuse the local factors while every shift stays within this (0: never)
+  bool host_loop = false;          // the host drives every step (no loop graph)
   bool factors_valid = false;      // Lbuf holds the factors of every pair, formed at the shifts lam_fact
   std::vector<double> lam_fact;    // host copy of the shifts of the stored factors
   int64_t refactorisations = 0, reuses = 0;  // local applications of the last solve, by kind
@@ -196,6 +197,10 @@ int launch_rr(Handle& h, int m, const double* G, const double* Hm, const double*
 int launch_validate_csr(const CsrDev& c, int32_t* flag, cudaStream_t s);
 int launch_same_pattern(const CsrDev& a, const CsrDev& m, int32_t* flag, cudaStream_t s);
 int launch_validate_part(Handle& h, int32_t* flag);
+// transpose of a validated CSR (rows of the result in ascending original row) into
+// caller-allocated arrays (n_cols + 1, nnz, nnz); at most kTransposeMaxCols columns
+constexpr int kTransposeMaxCols = 24576;
+int launch_csr_transpose(const CsrDev& a, int64_t* rpT, int32_t* ciT, double* valT, cudaStream_t s);
 int launch_band_width(Handle& h, const CsrDev& c, int32_t* bw);
 int launch_split_values(const double* v, int64_t nnz, float2* out, cudaStream_t s);
 // band rows of the local matrices of c (and of a second matrix with c's pattern,

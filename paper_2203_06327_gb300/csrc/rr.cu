@@ -1266,6 +1266,7 @@ __device__ bool rr_refined_solve(int m, int k, const double* __restrict__ G, con
     __syncthreads();
   }
   if (__syncthreads_or(fail ? 1 : 0)) return false;
+  const long long tchol = clock64();
   // Li = L^{-1} (slot 7), one column per thread; condition check as in the
   // eigen-based path: 1 / ||L^{-1}||_F^2 <= lambda_min(G')
   float* Li = slot[7];
@@ -1492,45 +1493,89 @@ __device__ bool rr_refined_solve(int m, int k, const double* __restrict__ G, con
   int step = 0;
   bool last = false;
   for (; !last; ++step) {
-    // GQ = G' Q, HQ = H' Q
-    for (int t = tid; t < m * m; t += blockDim.x) {
-      const int a = t / m, b = t % m;
-      dot2 g, h;
-      g.zero();
-      h.zero();
+    // GQ = G' Q, HQ = H' Q, a 2 x 2 tile of outputs per thread (each output sums
+    // over c in ascending order, as one output at a time would); with m odd the
+    // tiles reach the pad row / column, whose outputs are not stored
+    const int hm = (m + 1) / 2;
+    for (int t = tid; t < hm * hm; t += blockDim.x) {
+      const int a0 = 2 * (t / hm), b0 = 2 * (t % hm);
+      dot2 g[2][2], h[2][2];
+#pragma unroll
+      for (int x = 0; x < 2; ++x)
+#pragma unroll
+        for (int y = 0; y < 2; ++y) {
+          g[x][y].zero();
+          h[x][y].zero();
+        }
       for (int c = 0; c < m; ++c) {
-        const float qh = Qh[c * ld + b], ql = Ql[c * ld + b];
-        g.mac(Gh[a * ld + c], Gl[a * ld + c], qh, ql);
-        h.mac(Hh[a * ld + c], Hl[a * ld + c], qh, ql);
+        const float qh[2] = {Qh[c * ld + b0], Qh[c * ld + b0 + 1]}, ql[2] = {Ql[c * ld + b0], Ql[c * ld + b0 + 1]};
+#pragma unroll
+        for (int x = 0; x < 2; ++x) {
+          const float gh = Gh[(a0 + x) * ld + c], gl = Gl[(a0 + x) * ld + c];
+          const float hh = Hh[(a0 + x) * ld + c], hl = Hl[(a0 + x) * ld + c];
+#pragma unroll
+          for (int y = 0; y < 2; ++y) {
+            g[x][y].mac(gh, gl, qh[y], ql[y]);
+            h[x][y].mac(hh, hl, qh[y], ql[y]);
+          }
+        }
       }
-      const dw gv = dw_from_sum(g), hv = dw_from_sum(h);
-      GQh[a * ld + b] = gv.hi;
-      GQl[a * ld + b] = gv.lo;
-      HQh[a * ld + b] = hv.hi;
-      HQl[a * ld + b] = hv.lo;
+#pragma unroll
+      for (int x = 0; x < 2; ++x)
+#pragma unroll
+        for (int y = 0; y < 2; ++y) {
+          const int a = a0 + x, b = b0 + y;
+          if (a >= m || b >= m) continue;
+          const dw gv = dw_from_sum(g[x][y]), hv = dw_from_sum(h[x][y]);
+          GQh[a * ld + b] = gv.hi;
+          GQl[a * ld + b] = gv.lo;
+          HQh[a * ld + b] = hv.hi;
+          HQl[a * ld + b] = hv.lo;
+        }
     }
     __syncthreads();
-    // R = Q^T GQ, S = Q^T HQ (both triangles written)
-    for (int t = tid; t < m * m; t += blockDim.x) {
-      const int a = t / m, b = t % m;
-      if (a > b) continue;
-      dot2 r, s;
-      r.zero();
-      s.zero();
+    // R = Q^T GQ, S = Q^T HQ on the tiles on or above the diagonal (entries a <= b
+    // formed, both triangles written)
+    for (int t = tid; t < hm * hm; t += blockDim.x) {
+      const int ta = t / hm, tb = t % hm;
+      if (ta > tb) continue;
+      const int a0 = 2 * ta, b0 = 2 * tb;
+      dot2 r[2][2], sacc[2][2];
+#pragma unroll
+      for (int x = 0; x < 2; ++x)
+#pragma unroll
+        for (int y = 0; y < 2; ++y) {
+          r[x][y].zero();
+          sacc[x][y].zero();
+        }
       for (int c = 0; c < m; ++c) {
-        const float qh = Qh[c * ld + a], ql = Ql[c * ld + a];
-        r.mac(qh, ql, GQh[c * ld + b], GQl[c * ld + b]);
-        s.mac(qh, ql, HQh[c * ld + b], HQl[c * ld + b]);
+        const float qh[2] = {Qh[c * ld + a0], Qh[c * ld + a0 + 1]}, ql[2] = {Ql[c * ld + a0], Ql[c * ld + a0 + 1]};
+        const float gh[2] = {GQh[c * ld + b0], GQh[c * ld + b0 + 1]}, gl[2] = {GQl[c * ld + b0], GQl[c * ld + b0 + 1]};
+        const float hh[2] = {HQh[c * ld + b0], HQh[c * ld + b0 + 1]}, hl[2] = {HQl[c * ld + b0], HQl[c * ld + b0 + 1]};
+#pragma unroll
+        for (int x = 0; x < 2; ++x)
+#pragma unroll
+          for (int y = 0; y < 2; ++y) {
+            r[x][y].mac(qh[x], ql[x], gh[y], gl[y]);
+            sacc[x][y].mac(qh[x], ql[x], hh[y], hl[y]);
+          }
       }
-      const dw rv = dw_from_sum(r), sv = dw_from_sum(s);
-      Rh[a * ld + b] = rv.hi;
-      Rl[a * ld + b] = rv.lo;
-      Sh[a * ld + b] = sv.hi;
-      Sl[a * ld + b] = sv.lo;
-      Rh[b * ld + a] = rv.hi;
-      Rl[b * ld + a] = rv.lo;
-      Sh[b * ld + a] = sv.hi;
-      Sl[b * ld + a] = sv.lo;
+#pragma unroll
+      for (int x = 0; x < 2; ++x)
+#pragma unroll
+        for (int y = 0; y < 2; ++y) {
+          const int a = a0 + x, b = b0 + y;
+          if (a > b || b >= m) continue;
+          const dw rv = dw_from_sum(r[x][y]), sv = dw_from_sum(sacc[x][y]);
+          Rh[a * ld + b] = rv.hi;
+          Rl[a * ld + b] = rv.lo;
+          Sh[a * ld + b] = sv.hi;
+          Sl[a * ld + b] = sv.lo;
+          Rh[b * ld + a] = rv.hi;
+          Rl[b * ld + a] = rv.lo;
+          Sh[b * ld + a] = sv.hi;
+          Sl[b * ld + a] = sv.lo;
+        }
     }
     if (tid == 0) {
       emax_s = 0.f;
@@ -1757,6 +1802,7 @@ __device__ bool rr_refined_solve(int m, int k, const double* __restrict__ G, con
     cyc[3] = t4 - t3;
     cyc[4] = t5 - t4;
     cyc[5] = (long long)step * 1000;
+    cyc[7] = tchol - t0;  // of cyc[0]: the pencil's load and the Cholesky
   }
   return true;
 }

@@ -149,6 +149,7 @@ void run_request(bpjd_server* s, Request& r, cudaStream_t stream) {
   o.max_iter = s->o.max_iter;
   o.inputs_on_device = 0;
   o.stream = stream;
+  o.host_loop = s->o.host_loop;
   const bpjd_csr A = r.A.view(), M = r.M.view(), P = r.P.view();
   bpjd_csr P0;
   if (r.has_p0) P0 = r.P0.view();
@@ -228,7 +229,7 @@ extern "C" void bpjd_server_default_opts(bpjd_server_opts* o) {
   if (!o) return;
   std::memset(o, 0, sizeof(*o));
   o->hbm_budget_bytes = 0;
-  o->workers = 4;
+  o->workers = 8;
   o->precision = BPJD_MIXED;
   o->subspace = BPJD_W_3K;
   o->stop_rule = BPJD_STOP_RESIDUAL;
@@ -236,6 +237,7 @@ extern "C" void bpjd_server_default_opts(bpjd_server_opts* o) {
   o->max_iter = 500;
   o->admission = BPJD_ADMIT_SMALLEST;
   o->starvation_s = 1.0;
+  o->host_loop = 1;
 }
 
 extern "C" int bpjd_server_create(const bpjd_server_opts* opts, bpjd_server** out) {
