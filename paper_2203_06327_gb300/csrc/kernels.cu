@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <map>
 #include <mutex>
 #include <new>
 #include <set>
@@ -545,7 +546,7 @@ __global__ void __launch_bounds__(256) k_combine_dw(int64_t n, int k, int nin, P
 // lane j of the group owns columns j + LANES c, c < CPL.  The X entries are
 // split on the fly (integer operations only).
 template <int LANES, int CPL>
-__global__ void __launch_bounds__(256) k_spmm_dw(int n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+__global__ void __launch_bounds__(256, 4) k_spmm_dw(int n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
                                                  const float2* __restrict__ va, const float2* __restrict__ vm,
                                                  const double* __restrict__ X, double* __restrict__ YA,
                                                  double* __restrict__ YM, int ncols) {
@@ -1466,7 +1467,7 @@ struct BwdShape {
 };
 
 template <int BMAX>
-__global__ void __launch_bounds__(64) k_local_backward(int nsub, int k, const int64_t* __restrict__ sub_ptr,
+__global__ void __launch_bounds__(64, 1) k_local_backward(int nsub, int k, const int64_t* __restrict__ sub_ptr,
                                                        const float* __restrict__ Lbuf, float* __restrict__ wpk,
                                                        int32_t* err, int wait_limit, int64_t rec_base) {
   using S = BwdShape<BMAX>;
@@ -1601,7 +1602,7 @@ __global__ void __launch_bounds__(64) k_local_backward(int nsub, int k, const in
 // enters the freed slot.
 // ---------------------------------------------------------------------------
 template <int BMAX>
-__global__ void __launch_bounds__(64) k_local_forward(int nsub, int k, const int64_t* __restrict__ sub_ptr,
+__global__ void __launch_bounds__(64, 1) k_local_forward(int nsub, int k, const int64_t* __restrict__ sub_ptr,
                                                       const int32_t* __restrict__ sub_dofs,
                                                       const double* __restrict__ rho, const float* __restrict__ Lbuf,
                                                       float* __restrict__ wpk, int32_t* err, int wait_limit,
@@ -1734,9 +1735,11 @@ __global__ void __launch_bounds__(64) k_local_forward(int nsub, int k, const int
 // rows are taken eight at a time, one block per staged chunk, so that a
 // block's eight columns are handled together instead of one dependent row at a
 // time.  Layout as in k_local_backward (four shifts per warp, eight lanes per
-// shift, lane e keeping window slots e + 8 t, slot = row mod BMAX); the chunks
-// of a window group have a buffer each (BMAX / 8 of them), so the bulk copies
-// run up to BMAX / 8 - 1 blocks ahead.
+// shift, lane e keeping window slots e + 8 t, slot = row mod BMAX).  The blocks
+// of records enter shared memory by bulk copies into a ring of nbuf buffers per
+// warp, so the copies run nbuf - 1 blocks ahead; nbuf is a launch parameter,
+// the largest ring whose shared memory still lets every warp of the launch be
+// resident at once (sweep_ring_buffers).
 //   backward: for the block's columns q (rows j0 + q), the partial sums over the
 //   solved window rows run in parallel (lane partials, three xor shuffles
 //   each), then the 8 x 8 triangle is solved redundantly in every lane;
@@ -1744,27 +1747,35 @@ __global__ void __launch_bounds__(64) k_local_forward(int nsub, int k, const int
 //   every other window row takes the block's eight updates in column order, and
 //   the eight entering rows take theirs, so that y equals the fused sweep's bit
 //   for bit.
+// The per-row values that come from global memory (y for the backward sweep,
+// the gathered right-hand side rho for the forward sweep) are loaded NCH blocks
+// ahead into a register ring indexed by the block's window slot block (the dof
+// index of the gather 2 NCH blocks ahead), so that a block step does not wait
+// for a global load issued one step earlier.
 // ---------------------------------------------------------------------------
 template <int BMAX>
 struct BlkShape {
-  static constexpr int NCH = BMAX / 8;      // blocks (chunks) per window group, one buffer each
+  static constexpr int NCH = BMAX / 8;      // blocks (chunks) per window group
   static constexpr int PS = 8 * BMAX + 4;   // per-shift buffer stride
   static constexpr int WPB = 2;             // warps per block
-  static constexpr size_t smem_floats = (size_t)WPB * NCH * 4 * PS;
+  static constexpr int NBUF_MAX = 16;       // ring buffers per warp, at most
+  // dynamic shared memory of a block with nbuf buffers per warp
+  static size_t smem_floats(int nbuf) { return (size_t)WPB * nbuf * 4 * PS; }
 };
 
 template <int BMAX, bool FWD>
-__global__ void __launch_bounds__(64) k_local_sweep_blk(int nsub, int k, const int64_t* __restrict__ sub_ptr,
+__global__ void __launch_bounds__(64, 1) k_local_sweep_blk(int nsub, int k, const int64_t* __restrict__ sub_ptr,
                                                         const int32_t* __restrict__ sub_dofs,
                                                         const double* __restrict__ rho,
                                                         const float* __restrict__ Lbuf, float* __restrict__ wpk,
-                                                        int32_t* err, int wait_limit, int64_t rec_base) {
+                                                        int32_t* err, int wait_limit, int64_t rec_base,
+                                                        int nbuf) {
   using S = BlkShape<BMAX>;
   constexpr int TC = BMAX / 8, NCH = S::NCH, PS = S::PS, WPB = S::WPB;
   constexpr unsigned FULL = 0xffffffffu;
   static_assert(BMAX % 8 == 0 && BMAX <= 48, "window tier of the blocked sweeps");
   extern __shared__ __align__(128) float ssm[];
-  __shared__ __align__(8) uint64_t bars[WPB][NCH];
+  __shared__ __align__(8) uint64_t bars[WPB][S::NBUF_MAX];
   const int lane = threadIdx.x & 31, e = lane & 7, p = lane >> 3, wib = threadIdx.x >> 5;
   const int wglob = blockIdx.x * WPB + wib;
   const int wps = (k + 3) / 4;  // warps per subdomain
@@ -1777,90 +1788,109 @@ __global__ void __launch_bounds__(64) k_local_sweep_blk(int nsub, int k, const i
   const int64_t off = sub_ptr[l];
   const int nl = (int)(sub_ptr[l + 1] - off);
   const int32_t* dofs = sub_dofs + off;
-  float* buf = ssm + (size_t)wib * NCH * 4 * PS;  // [NCH][4][PS]
+  float* buf = ssm + (size_t)wib * nbuf * 4 * PS;  // [nbuf][4][PS]
   uint64_t* bar = bars[wib];
   const float* Lsub = Lbuf + (size_t)(off - rec_base) * k * BMAX;  // record of shift i at Lsub + i nl BMAX
   float* yp = wpk + off * k + ii;
   if (lane == 0) {
-    for (int b = 0; b < NCH; ++b) mbar_init(&bar[b], 1);
+    for (int b = 0; b < nbuf; ++b) mbar_init(&bar[b], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncwarp();
   const int nblk = (nl + 7) / 8;
-  // lane 0: copies issued and waited for, per buffer (for the drain on a timeout)
-  int uses[NCH], dones[NCH];
-#pragma unroll
-  for (int b = 0; b < NCH; ++b) uses[b] = dones[b] = 0;
-  // block ch = rows [8 ch, min(nl, 8 ch + 8)) of each served shift, into buffer ch % NCH
-  auto issue = [&](int ch, int b) {
-    if (ch < 0 || ch >= nblk) return;
+  // Blocks are copied and consumed in processing order: position q is block q
+  // (forward) or nblk - 1 - q (backward), in buffer q mod nbuf, whose wait has
+  // parity (q / nbuf) & 1.  Lane 0 issues the copies and counts the positions
+  // issued and waited for (for the drain on a timeout).
+  int n_issued = 0, n_done = 0;
+  // position q = rows [8 ch, min(nl, 8 ch + 8)) of each served shift, into buffer b
+  auto issue = [&](int q, int b) {
+    if (q >= nblk) return;
+    const int ch = FWD ? q : nblk - 1 - q;
     const int r0 = 8 * ch;
     const int rows = min(8, nl - r0);
     const uint32_t bytes = (uint32_t)rows * BMAX * sizeof(float);
     mbar_expect_tx(&bar[b], bytes * nact);
-    for (int q = 0; q < nact; ++q)
-      bulk_load(buf + (b * 4 + q) * PS, Lsub + ((size_t)(i0 + q) * nl + r0) * BMAX, bytes, &bar[b]);
-    ++uses[b];
+    for (int t = 0; t < nact; ++t)
+      bulk_load(buf + (b * 4 + t) * PS, Lsub + ((size_t)(i0 + t) * nl + r0) * BMAX, bytes, &bar[b]);
+    n_issued = q + 1;
   };
   auto rhs = [&](int row) -> float { return (row < nl) ? (float)rho[(int64_t)dofs[row] * k + ii] : 0.f; };
   float w[TC];  // backward: x of the window rows; forward: their pending right-hand sides
 #pragma unroll
   for (int t = 0; t < TC; ++t) w[t] = FWD ? rhs(e + 8 * t) : 0.f;
   // per block, lane e's row j0 + e: y (backward) or the entering row's right-hand
-  // side (forward), fetched one block ahead (the dof index two blocks ahead)
-  float vcur = 0.f, vnext = 0.f;
-  int dnext = -1;
+  // side (forward); ring slot b holds the value of the next block of window slot
+  // block b (NCH blocks ahead), dring[b] the dof index of the block after that
+  float vring[NCH];
+  int dring[NCH];
   auto row_of = [&](int ch) { return 8 * ch + e + (FWD ? BMAX : 0); };
+  auto dof_of = [&](int ch) -> int {
+    const int r = row_of(ch);
+    return (ch >= 0 && ch < nblk && r < nl) ? dofs[r] : -1;
+  };
   auto fetch = [&](int ch) -> float {
     const int r = row_of(ch);
     if (ch < 0 || ch >= nblk || r >= nl) return 0.f;
     return FWD ? 0.f : yp[(size_t)r * k];
   };
-  uint32_t phase = 0;  // bit b: parity of buffer b's next wait
+  int qpos = 0, qbuf = 0;   // processing position and its buffer
+  uint32_t qpar = 0;        // parity of its wait
+  int ibuf = nbuf - 1;      // buffer of position qpos + nbuf - 1, issued at position qpos
   bool timeout = false;
+  const int g0 = FWD ? 0 : (nblk - 1) / NCH, g1 = FWD ? (nblk - 1) / NCH : 0;
   if (FWD) {
     if (lane == 0)
-      for (int b = 0; b < NCH - 1; ++b) issue(b, b);
-    {
-      const int r0 = row_of(0), r1 = row_of(1);
-      vnext = (r0 < nl) ? (float)rho[(int64_t)dofs[r0] * k + ii] : 0.f;
-      dnext = (nblk > 1 && r1 < nl) ? dofs[r1] : -1;
+      for (int b = 0; b < nbuf - 1; ++b) issue(b, b);
+#pragma unroll
+    for (int b = 0; b < NCH; ++b) {
+      const int d = dof_of(b);
+      vring[b] = (d >= 0) ? (float)rho[(int64_t)d * k + ii] : 0.f;
+      dring[b] = dof_of(b + NCH);
     }
   } else {
     if (lane == 0)
-      for (int d = 0; d < NCH - 1; ++d) issue(nblk - 1 - d, (nblk - 1 - d) % NCH);
-    vnext = fetch(nblk - 1);
+      for (int b = 0; b < nbuf - 1; ++b) issue(b, b);
+#pragma unroll
+    for (int b = 0; b < NCH; ++b) {
+      // the first block processed in window slot block b
+      const int c0 = g0 * NCH + b;
+      vring[b] = fetch(c0 < nblk ? c0 : c0 - NCH);
+      dring[b] = -1;
+    }
   }
-  const int g0 = FWD ? 0 : (nblk - 1) / NCH, g1 = FWD ? (nblk - 1) / NCH : 0;
   for (int g = g0; FWD ? (g <= g1) : (g >= g1); g += FWD ? 1 : -1) {
 #pragma unroll
     for (int hq = 0; hq < NCH; ++hq) {
-      const int hc = FWD ? hq : NCH - 1 - hq;  // buffer and slot block of this block
+      const int hc = FWD ? hq : NCH - 1 - hq;  // window slot block of this block
       const int ch = g * NCH + hc;
       if (ch >= nblk) continue;
-      __syncwarp();  // the buffer of the previous block is no longer read
+      __syncwarp();  // the buffer of the previous position is no longer read
       if (lane == 0 && !timeout) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        // the previous block's buffer takes the block NCH - 1 ahead
-        const int nb = FWD ? ch + NCH - 1 : ch - (NCH - 1);
-        issue(nb, FWD ? (hc + NCH - 1) % NCH : (hc + 1) % NCH);
+        // the previous position's buffer takes the position nbuf - 1 ahead
+        issue(qpos + nbuf - 1, ibuf);
       }
-      vcur = vnext;
+      ibuf = (ibuf + 1 == nbuf) ? 0 : ibuf + 1;
+      const float vcur = vring[hc];
       if (FWD) {
-        vnext = (dnext >= 0) ? (float)rho[(int64_t)dnext * k + ii] : 0.f;
-        const int r2 = row_of(ch + 2);
-        dnext = (ch + 2 < nblk && r2 < nl) ? dofs[r2] : -1;
+        vring[hc] = (dring[hc] >= 0) ? (float)rho[(int64_t)dring[hc] * k + ii] : 0.f;
+        dring[hc] = dof_of(ch + 2 * NCH);
       } else {
-        vnext = fetch(ch - 1);
+        vring[hc] = fetch(ch - NCH);
       }
       if (!timeout) {
-        if (mbar_wait_bounded(&bar[hc], (phase >> hc) & 1u, wait_limit))
-          ++dones[hc];
+        if (mbar_wait_bounded(&bar[qbuf], qpar, wait_limit))
+          n_done = qpos + 1;
         else
           timeout = true;
       }
-      phase ^= 1u << hc;
-      const float* Lb = buf + (hc * 4 + p) * PS;  // records of rows 8 ch .. 8 ch + 7 (shift p)
+      const float* Lb = buf + (qbuf * 4 + p) * PS;  // records of rows 8 ch .. 8 ch + 7 (shift p)
+      ++qpos;
+      if (++qbuf == nbuf) {
+        qbuf = 0;
+        qpar ^= 1u;
+      }
       const int j0 = 8 * ch;
       const int nr = min(8, nl - j0);
       const int s0 = 8 * hc;  // slot of row j0
@@ -1939,13 +1969,11 @@ __global__ void __launch_bounds__(64) k_local_sweep_blk(int nsub, int k, const i
     }
   }
   if (timeout && lane == 0) atomicOr(err, kErrTimeout);
-  // lane 0 issued every copy of this warp: drain the ones it did not see complete
-  // (buffer b's phases complete in order; its last uses[b] - dones[b] are pending)
+  // lane 0 issued every copy of this warp: drain the positions it did not see
+  // complete (each buffer's phases complete in order)
   if (lane == 0)
-#pragma unroll
-    for (int b = 0; b < NCH; ++b)
-      for (int u = dones[b]; u < uses[b]; ++u)
-        if (!mbar_drain(&bar[b], (uint32_t)(u & 1))) atomicOr(err, kErrDrain);
+    for (int q = n_done; q < n_issued; ++q)
+      if (!mbar_drain(&bar[q % nbuf], (uint32_t)((q / nbuf) & 1))) atomicOr(err, kErrDrain);
 }
 
 // ---------------------------------------------------------------------------
@@ -2702,6 +2730,44 @@ int launch_combine_rows(Handle& h, int nin, const double* const* Win, const doub
   return (int)cudaGetLastError();
 }
 
+// Device facts for launch shapes, read once per device: SM count, shared memory
+// per SM and the share the driver reserves per block.
+struct SmFacts {
+  int sms = 0, smem_sm = 0, smem_reserved = 0, smem_block = 0;
+};
+SmFacts sm_facts() {
+  static std::mutex mu;
+  static std::map<int, SmFacts> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = cache.find(dev);
+  if (it != cache.end()) return it->second;
+  SmFacts f;
+  cudaDeviceGetAttribute(&f.sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&f.smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&f.smem_reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+  cudaDeviceGetAttribute(&f.smem_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (f.sms < 1) f.sms = 1;
+  cache[dev] = f;
+  return f;
+}
+
+// Ring depth of the blocked sweeps for a launch of `blocks` blocks: the deepest
+// ring (more copies in flight per warp) whose shared memory still lets every
+// block of the launch be resident at once (one wave), between 2 and NBUF_MAX.
+template <int BM>
+int sweep_ring_buffers(int64_t blocks) {
+  using S = BlkShape<BM>;
+  const SmFacts f = sm_facts();
+  const int64_t per_sm = std::max<int64_t>(1, (blocks + f.sms - 1) / f.sms);
+  const int64_t room = (int64_t)f.smem_sm / per_sm - f.smem_reserved - 1024;  // static part: the barriers
+  const int64_t per_buf = (int64_t)S::WPB * 4 * S::PS * sizeof(float);
+  int64_t nb = room / per_buf;
+  nb = std::min<int64_t>(nb, ((int64_t)f.smem_block - 1024) / per_buf);
+  return (int)std::max<int64_t>(2, std::min<int64_t>(S::NBUF_MAX, nb));
+}
+
 bool can_reuse_factors(const Handle& h) {
   if (!h.local_f32() || h.chunk_l0.size() != 2) return false;
   switch (h.Bpad) {
@@ -2730,16 +2796,19 @@ int launch_local(Handle& h, const double* rho, const double* lam, int mode) {
       constexpr int BM = decltype(bm)::value;
       if constexpr (BM <= 48) {
         // blocked sweeps, eight rows per step
-        const size_t ssm = sizeof(float) * BlkShape<BM>::smem_floats;
+        const int nbuf = sweep_ring_buffers<BM>(bwd_blocks);
+        const size_t ssm = sizeof(float) * BlkShape<BM>::smem_floats(nbuf);
         if (fwd) {
           allow_dynamic_smem((const void*)k_local_sweep_blk<BM, true>);
           k_local_sweep_blk<BM, true><<<bwd_blocks, 32 * BlkShape<BM>::WPB, ssm, h.stream>>>(
-              nsub, k, h.sub_ptr, h.sub_dofs, rho, (const float*)h.Lbuf, (float*)h.wpk, h.derr, h.wait_limit, 0);
+              nsub, k, h.sub_ptr, h.sub_dofs, rho, (const float*)h.Lbuf, (float*)h.wpk, h.derr, h.wait_limit, 0,
+              nbuf);
         }
         if (bwd) {
           allow_dynamic_smem((const void*)k_local_sweep_blk<BM, false>);
           k_local_sweep_blk<BM, false><<<bwd_blocks, 32 * BlkShape<BM>::WPB, ssm, h.stream>>>(
-              nsub, k, h.sub_ptr, h.sub_dofs, rho, (const float*)h.Lbuf, (float*)h.wpk, h.derr, h.wait_limit, 0);
+              nsub, k, h.sub_ptr, h.sub_dofs, rho, (const float*)h.Lbuf, (float*)h.wpk, h.derr, h.wait_limit, 0,
+              nbuf);
         }
         return;
       }
@@ -2797,10 +2866,12 @@ int launch_local(Handle& h, const double* rho, const double* lam, int mode) {
                                                                        (float*)h.wpk, h.derr, h.wait_limit,    \
                                                                        rec_base);                              \
     if (mode == kLocalFull) {                                                                                  \
-      const size_t ssm = sizeof(float) * BlkShape<BM>::smem_floats;                                            \
+      const int nbuf = sweep_ring_buffers<BM>(bwd_blocks);                                                     \
+      const size_t ssm = sizeof(float) * BlkShape<BM>::smem_floats(nbuf);                                      \
       allow_dynamic_smem((const void*)k_local_sweep_blk<BM, false>);                                           \
       k_local_sweep_blk<BM, false><<<bwd_blocks, 32 * BlkShape<BM>::WPB, ssm, h.stream>>>(                     \
-          nsub, k, sptr, h.sub_dofs, rho, (const float*)h.Lbuf, (float*)h.wpk, h.derr, h.wait_limit, rec_base); \
+          nsub, k, sptr, h.sub_dofs, rho, (const float*)h.Lbuf, (float*)h.wpk, h.derr, h.wait_limit, rec_base,  \
+          nbuf);                                                                                               \
     }                                                                                                          \
     break;                                                                                                     \
   }
