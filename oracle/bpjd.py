@@ -34,7 +34,12 @@ Algorithm 3.1:
   Step 3  Rayleigh-Ritz for the lowest s pairs in W^{k+1}; by Remark 3.1 the
           default search space is W^{k+1} = U^k + span{t_i} (dimension <= 2s);
           "3s" uses U^{k-1} + U^k + span{t_i} (the previous iterate is made
-          b-orthogonal to U^k first).
+          b-orthogonal to U^k first); "grow" is the space of Algorithm 3.1
+          itself, W^0 = U^0 and W^{k+1} = W^k + span{t_i}, kept as a
+          b-orthonormal basis (each new block b-orthogonalised against the
+          basis twice, then orthonormalised within itself, dependent
+          directions dropped), optionally restarted to U^k + U^{k-1} (the
+          choice V^k of Remark 3.1) when it would exceed max_dim.
   Step 4  stop: "dlambda" is the paper's rule sum_i |lambda_i^{k+1} - lambda_i^k|
           < tol; "residual" stops when every relative residual
           ||K x_i - lambda_i M x_i||_2 / (|lambda_i| ||M x_i||_2) <= tol.
@@ -214,6 +219,29 @@ class Result:
     history_lam: List[np.ndarray] = field(default_factory=list)
     history_res: List[float] = field(default_factory=list)
     history_dlam: List[float] = field(default_factory=list)
+    restarts: int = 0
+
+
+def extend_orthonormal(K, M, V, KV, MV, T, drop_tol: float = 1e-10):
+    """Append span(T) to the b-orthonormal basis V (growing space of Algorithm 3.1).
+
+    T is b-orthogonalised against V twice (classical Gram-Schmidt in the M-inner
+    product, repeated), then orthonormalised within itself through the eigen-
+    decomposition of its Gram matrix, directions below drop_tol * max dropped.
+    The products K V, M V of the new columns are formed from the columns
+    themselves (near convergence a new direction is a small difference of large
+    terms, whose products by linear combination would carry that cancellation).
+    Returns the extended (V, KV, MV) and the number of columns added.
+    """
+    for _ in range(2):
+        T = T - V @ (MV.T @ T)
+    MT = M @ T
+    G = T.T @ MT
+    G = 0.5 * (G + G.T)
+    g, Q = np.linalg.eigh(G)
+    keep = g > drop_tol * max(g.max(), 0.0) if g.max() > 0 else np.zeros_like(g, dtype=bool)
+    Tn = T @ (Q[:, keep] / np.sqrt(g[keep])[None, :])
+    return (np.hstack([V, Tn]), np.hstack([KV, K @ Tn]), np.hstack([MV, M @ Tn]), int(keep.sum()))
 
 
 def sign_normalise(X):
@@ -228,13 +256,20 @@ def sign_normalise(X):
 
 def solve(S: Setup, tol: float = 1e-8, max_iter: int = 200, stop: str = "residual",
           subspace: str = "2s", drop_tol: float = 1e-10, coarse: bool = True,
-          callback=None) -> Result:
-    """Algorithm 3.1 until the stop rule holds or max_iter Rayleigh-Ritz steps were taken."""
+          callback=None, max_dim: Optional[int] = None) -> Result:
+    """Algorithm 3.1 until the stop rule holds or max_iter Rayleigh-Ritz steps were taken.
+
+    max_dim (subspace "grow" only): restart the growing space to U^k + U^{k-1}
+    when appending the next block would make it larger than max_dim columns.
+    """
     k = S.k
     X, AX, MX, lam = initial_guess(S)
     res = Result(lam.copy(), X, 0, False)
     res.history_lam.append(lam.copy())
     Xprev = AXprev = MXprev = None
+    # growing space: b-orthonormal basis of W^k and its products (W^0 = U^0)
+    Vg, KVg, MVg = X, AX, MX
+    res.restarts = 0
     for it in range(max_iter + 1):
         rho, rel = residual(AX, MX, lam)
         res.history_res.append(float(rel.max()))
@@ -258,9 +293,23 @@ def solve(S: Setup, tol: float = 1e-8, max_iter: int = 200, stop: str = "residua
                 W = np.hstack([X, Pp, T])
                 AW = np.hstack([AX, S.K @ Pp, AT])
                 MW = np.hstack([MX, S.M @ Pp, MT])
+        elif subspace == "grow":
+            if max_dim is not None and Vg.shape[1] + k > max_dim:
+                # restart inside Remark 3.1: V^k = U^k + U^{k-1}
+                Vg, KVg, MVg = X, AX, MX
+                if Xprev is not None:
+                    Vg, KVg, MVg, _ = extend_orthonormal(S.K, S.M, Vg, KVg, MVg, Xprev, drop_tol)
+                res.restarts += 1
+            Vg, KVg, MVg, _ = extend_orthonormal(S.K, S.M, Vg, KVg, MVg, T, drop_tol)
+            Hg = Vg.T @ KVg
+            Hg = 0.5 * (Hg + Hg.T)
+            theta_all, Y = np.linalg.eigh(Hg)
+            theta, C = theta_all[:k], Y[:, :k]
+            W, AW, MW = Vg, KVg, MVg
         else:
             raise ValueError(subspace)
-        theta, C = rayleigh_ritz(W, AW, MW, k, k, drop_tol)
+        if subspace != "grow":
+            theta, C = rayleigh_ritz(W, AW, MW, k, k, drop_tol)
         Xprev, AXprev, MXprev = X, AX, MX
         X = W @ C
         AX = S.K @ X

@@ -17,6 +17,7 @@ import scipy.linalg as la
 import scipy.sparse as sp
 import scipy.sparse.linalg as sla
 
+from conftest import golden
 from oracle import bpjd, metrics, problem
 from workloads import ProblemSpec, config_c1, config_small_2d, config_small_3d, config_table1_col1
 
@@ -137,6 +138,64 @@ def test_subspace_variants_agree(c1):
     r3 = bpjd.solve(S, tol=1e-8, subspace="3s")
     assert r3.converged and r3.iterations < res.iterations
     np.testing.assert_allclose(r3.lam, res.lam, rtol=1e-10)
+
+
+def test_growing_space_is_nested_and_converges(c1):
+    """Algorithm 3.1's own search space, W^0 = U^0 and W^{k+1} = W^k + span{t_i}: the spaces are
+    nested, so by Courant-Fischer no Ritz value rises from one step to the next; the basis stays
+    b-orthonormal, and the result is the dense generalised eigensolve's.  The step count is
+    pinned against drift (the 2s and 3s spaces of Remark 3.1 take 54 and 21)."""
+    pb, S, res, w, V = c1
+    k = S.k
+    r = bpjd.solve(S, tol=1e-8, subspace="grow")
+    assert r.converged and r.restarts == 0
+    H = np.array(r.history_lam)
+    assert np.all(np.diff(H, axis=0) <= 1e-12 * np.abs(H[:-1])), np.diff(H, axis=0).max()
+    np.testing.assert_allclose(r.lam, w[:k], rtol=1e-10)
+    for a, b in metrics.clusters(w[:k]):
+        assert metrics.gap_b(r.X[:, a:b], V[:, a:b], pb.M) <= 1e-6
+    assert metrics.rel_residuals(pb.K, pb.M, r.lam, r.X).max() <= 1e-8
+    assert r.iterations == 18, r.iterations
+
+
+def test_growing_space_restarted_at_3s_is_the_3s_space(c1):
+    """Restarted whenever it would exceed 3s columns, the growing space is U^{k-1} + U^k +
+    span{t_i} at every step (step 1: W^1 = U^0 + span{t} contains U^1 and U^0; later steps restart
+    to U^k + U^{k-1} before the append), i.e. Remark 3.1's 3s space in another basis: the same
+    Ritz values at every step and the same step count."""
+    pb, S, res, w, V = c1
+    k = S.k
+    r3 = bpjd.solve(S, tol=1e-8, subspace="3s")
+    rg = bpjd.solve(S, tol=1e-8, subspace="grow", max_dim=3 * k)
+    assert rg.converged and rg.iterations == r3.iterations
+    assert rg.restarts == rg.iterations - 2
+    np.testing.assert_allclose(np.array(rg.history_lam), np.array(r3.history_lam), rtol=1e-9)
+
+
+@pytest.mark.slow
+def test_paper_iteration_count_with_the_growing_space():
+    """Table 1, first column, with the search space of Algorithm 3.1 as printed (W^{k+1} = W^k +
+    span{t}, up to 19 x 22 columns): on the paper's partition (2 and 3 rings of fine triangles)
+    the counts bracket the printed 21 as the 3s space's do (22 and 20), one step fewer with 3
+    rings; restarted at 5s columns it takes the 3s counts."""
+    from oracle import partition
+    spec = replace(config_table1_col1(), nsub=(16, 16), delta=2)
+    pb = problem.build(spec)
+    its, its5 = {}, {}
+    for layers in (2, 3):
+        ptr, dofs, col, nc = partition.triangle_partition(128, 16, layers)
+        S = bpjd.setup(pb.K, pb.M, pb.P, ptr, dofs, 19)
+        res = bpjd.solve(S, tol=1e-10, stop="dlambda", subspace="grow", max_iter=60)
+        assert res.converged and res.restarts == 0
+        its[layers] = res.iterations
+        if layers == 3:
+            want = np.array([r[0] for r in golden("table1.txt")])
+            np.testing.assert_allclose(res.lam, want, rtol=0, atol=6e-9)
+        res5 = bpjd.solve(S, tol=1e-10, stop="dlambda", subspace="grow", max_dim=5 * 19, max_iter=60)
+        its5[layers] = res5.iterations
+    assert its[3] <= 21 <= its[2], its
+    assert its == {2: 22, 3: 19}, its
+    assert its5 == {2: 22, 3: 20}, its5
 
 
 @pytest.mark.slow
