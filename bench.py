@@ -483,7 +483,13 @@ def run_serving(a, B):
         svc64.append(time.perf_counter() - t0)
     ktot = sum(r.spec.k for r in reqs)
     gap = 1.25 * float(np.mean(svc))
-    srv = B.Server(workers=a.serving_workers, precision=prec, subspace=B.W_3K, host_loop=not a.serving_graph)
+
+    def server(batch=True):
+        # batch: the local solves of the requests in flight share grouped launches
+        return B.Server(workers=a.serving_workers, precision=prec, subspace=B.W_3K, host_loop=not a.serving_graph,
+                        batch_local=batch and not a.serving_graph)
+
+    srv = server()
     lat, failed, tickets = [], 0, []
     t0 = time.perf_counter()
     for pb, r in zip(pbs, reqs):
@@ -497,19 +503,27 @@ def run_serving(a, B):
         lat.append(times[2])
     makespan = time.perf_counter() - t0
     srv.close()
-    # saturated: every request submitted at once (throughput of the served form)
-    srv = B.Server(workers=a.serving_workers, precision=prec, subspace=B.W_3K, host_loop=not a.serving_graph)
-    t0 = time.perf_counter()
-    tickets2 = [srv.submit(pb, r.spec.k) for pb, r in zip(pbs, reqs)]
-    for t in tickets2:
-        failed += int(srv.poll(t)[0] != B.OK)
-    sat = time.perf_counter() - t0
-    srv.close()
+    # saturated: every request submitted at once (throughput of the served form), with the
+    # local solves packed across requests and, for comparison, without
+    sat, groups = {}, (0, 0)
+    for batch in (True, False):
+        srv = server(batch)
+        t0 = time.perf_counter()
+        tickets2 = [srv.submit(pb, r.spec.k) for pb, r in zip(pbs, reqs)]
+        for t in tickets2:
+            failed += int(srv.poll(t)[0] != B.OK)
+        sat[batch] = time.perf_counter() - t0
+        if batch:
+            groups = srv.batch_stats()
+        srv.close()
     lat = np.array(lat)
     return {"requests": len(reqs), "workers": a.serving_workers, "offered_load": 0.8,
             "mean_interarrival_s": gap, "p50_latency_s": float(np.percentile(lat, 50)),
             "p99_latency_s": float(np.percentile(lat, 99)), "eigenpairs_per_s": ktot / makespan,
-            "saturated_eigenpairs_per_s": ktot / sat,
+            "saturated_eigenpairs_per_s": ktot / sat[True],
+            "saturated_unpacked_eigenpairs_per_s": ktot / sat[False],
+            "packed_local_solves": {"launch_groups": groups[0], "applications": groups[1],
+                                    "requests_per_group": groups[1] / groups[0] if groups[0] else None},
             "one_at_a_time_eigenpairs_per_s": ktot / float(np.sum(svc)),
             "fp64_one_at_a_time_eigenpairs_per_s": ktot / float(np.sum(svc64)) if svc64 else None,
             "one_at_a_time_p50_service_s": float(np.percentile(svc, 50)), "failed": failed,

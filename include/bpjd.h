@@ -45,7 +45,7 @@ extern "C" {
 #define BPJD_ERR_NOCONV           -8  /* max_iter reached before the stop rule held */
 #define BPJD_ERR_OOM              -9  /* device allocation failed */
 #define BPJD_ERR_CUDA            -10  /* a CUDA runtime call failed */
-#define BPJD_ERR_UNSUPPORTED     -11  /* option outside what this build implements, or a local
+#define BPJD_ERR_UNSUPPORTED     -11  /* option outside what the library implements, or a local
                                         band window the shared-memory kernel cannot hold
                                         (FP64 above 168, mixed above 240 on a 227 KB SM) */
 #define BPJD_ERR_TOO_LARGE       -12  /* request exceeds a fixed capacity (allocation-free entry point)
@@ -358,7 +358,13 @@ void bpjd_problem_free(bpjd_problem* p);
  * work first (dofs x k), except that a request waiting longer than
  * starvation_s seconds goes ahead of every younger one (oldest first), so that
  * small requests are not held up behind large ones and large ones still start;
- * BPJD_ADMIT_FIFO keeps arrival order.  This is the per-request workflow of
+ * BPJD_ADMIT_FIFO keeps arrival order.  With batch_local (the default) the
+ * local solves of the requests in flight share their launches: a request that
+ * reaches the local part of a preconditioner application waits (at most
+ * batch_wait_us) for the other requests in a solve to reach theirs, and all of
+ * them run as one grouped launch per kernel kind and window tier over every
+ * (request, subdomain, shift) pair, of uneven sizes; the rest of each step stays
+ * on the request's own stream.  This is the per-request workflow of
  * Algorithm 3.1 run many times; the paper itself solves one pencil at a time.
  */
 #define BPJD_ADMIT_SMALLEST 0  /* smallest estimated work first, with aging (default) */
@@ -378,11 +384,27 @@ typedef struct {
   double  starvation_s;     /* aging limit of BPJD_ADMIT_SMALLEST (default 1 s) */
   int32_t host_loop;        /* per-request loop mode, as in bpjd_opts; default 1, each
                                request's loop driven by its worker thread */
+  int32_t batch_local;      /* 1 (default): the local solves (Eq. (3.3), first term) of the
+                               requests in flight are packed into shared launches, one per
+                               kernel kind and window tier, whenever their preconditioner
+                               applications coincide (requests of other precisions, or whose
+                               factors are solved in chunks, keep their own launches);
+                               0: every request launches its own.  Needs host_loop = 1.
+                               Results are bitwise those of the request alone. */
+  int32_t batch_wait_us;    /* how long a request's local solves wait for those of the other
+                               requests in flight before they are launched (default 100) */
 } bpjd_server_opts;
 
 typedef struct bpjd_server bpjd_server;
 
 void bpjd_server_default_opts(bpjd_server_opts* o);
+
+/* Packing of the local solves (bpjd_server_opts.batch_local): *launches = how many
+   shared launch groups ran so far (each: one launch per kernel kind and window tier),
+   *solves = how many requests' preconditioner applications they carried (their ratio
+   is the mean number of requests per shared launch).  Zeros when packing is off.
+   Errors: BAD_ARG. */
+int bpjd_server_batch_stats(const bpjd_server* s, int64_t* launches, int64_t* solves);
 
 /* Starts the worker threads on the current device.  Errors: BAD_ARG, CUDA. */
 int bpjd_server_create(const bpjd_server_opts* opts, bpjd_server** out);

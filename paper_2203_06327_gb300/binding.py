@@ -78,7 +78,8 @@ class Stats(C.Structure):
 class ServerOpts(C.Structure):
     _fields_ = [("hbm_budget_bytes", C.c_size_t), ("workers", C.c_int32), ("precision", C.c_int32),
                 ("subspace", C.c_int32), ("stop_rule", C.c_int32), ("tol", C.c_double), ("max_iter", C.c_int32),
-                ("admission", C.c_int32), ("starvation_s", C.c_double), ("host_loop", C.c_int32)]
+                ("admission", C.c_int32), ("starvation_s", C.c_double), ("host_loop", C.c_int32),
+                ("batch_local", C.c_int32), ("batch_wait_us", C.c_int32)]
 
 
 class MeshS(C.Structure):
@@ -123,6 +124,7 @@ def _load():
                                      C.c_void_p]
     lib.bpjd_server_free.argtypes = [C.c_void_p]
     lib.bpjd_server_free.restype = None
+    lib.bpjd_server_batch_stats.argtypes = [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
     lib.bpjd_set_wait_limit.argtypes = [C.c_void_p, C.c_int32]
     lib.bpjd_profile.argtypes = [C.c_void_p, C.c_int32]
     lib.bpjd_profile_read.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
@@ -394,11 +396,13 @@ class Solver:
 class Server:
     """Many independent eigenproblems on one GPU (bpjd_server_*): requests are queued,
     admitted under a device-memory budget (smallest estimated work first with aging, or
-    first-in first-out) and solved by worker threads with one CUDA stream each."""
+    first-in first-out) and solved by worker threads with one CUDA stream each; with
+    batch_local the local solves of the requests in flight share grouped launches."""
 
     def __init__(self, workers: int = 8, hbm_budget_bytes: int = 0, precision: int = MIXED,
                  subspace: int = W_3K, stop_rule: int = STOP_RESIDUAL, tol: float = 1e-8, max_iter: int = 500,
-                 admission: int = 0, starvation_s: float = 1.0, host_loop: bool = True):
+                 admission: int = 0, starvation_s: float = 1.0, host_loop: bool = True,
+                 batch_local: bool = True, batch_wait_us: int = 100):
         o = ServerOpts()
         lib.bpjd_server_default_opts(C.byref(o))
         o.workers, o.hbm_budget_bytes = int(workers), int(hbm_budget_bytes)
@@ -406,6 +410,8 @@ class Server:
         o.tol, o.max_iter = float(tol), int(max_iter)
         o.admission, o.starvation_s = int(admission), float(starvation_s)
         o.host_loop = 1 if host_loop else 0
+        o.batch_local = 1 if batch_local else 0
+        o.batch_wait_us = int(batch_wait_us)
         h = C.c_void_p()
         _check(lib.bpjd_server_create(C.byref(o), C.byref(h)), "bpjd_server_create")
         self._h = h
@@ -438,6 +444,12 @@ class Server:
         del self._meta[ticket]
         stats = {f: getattr(st, f) for f, _ in Stats._fields_}
         return rc, lam, X, stats, tuple(float(x) for x in times)
+
+    def batch_stats(self):
+        """(shared launch groups so far, preconditioner applications they carried)."""
+        a, b = C.c_int64(), C.c_int64()
+        _check(lib.bpjd_server_batch_stats(self._h, C.byref(a), C.byref(b)), "bpjd_server_batch_stats")
+        return a.value, b.value
 
     def close(self):
         if self._h:

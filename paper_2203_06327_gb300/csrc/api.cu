@@ -250,6 +250,7 @@ extern "C" void bpjd_free(bpjd_handle* hh) {
     if (st) cudaStreamDestroy((cudaStream_t)st);
   for (void* p : h->allocs) cudaFree(p);
   for (void* e : h->ev_pool) cudaEventDestroy((cudaEvent_t)e);
+  if (h->batch_ev) cudaEventDestroy((cudaEvent_t)h->batch_ev);
   if (h->hstat) cudaFreeHost(h->hstat);
   delete h;
 }
@@ -365,6 +366,7 @@ extern "C" int bpjd_setup(const bpjd_csr* A, const bpjd_csr* M, const bpjd_csr* 
     if (h->dword()) {
       CK(dalloc(*h, &h->Asplit, (size_t)A->nnz));
       CK(dalloc(*h, &h->Msplit, (size_t)M->nnz));
+      CK(dalloc(*h, &h->xsplit, (size_t)n * k));
       CKI(launch_split_values(h->A.val, A->nnz, h->Asplit, h->stream));
       CKI(launch_split_values(h->M.val, M->nnz, h->Msplit, h->stream));
     }
@@ -809,9 +811,9 @@ int run_step(Handle& h, StepBufs& b, int nb, int it, bool reuse, const CaptureCt
     const double* Win[1] = {b.X};
     // double-word: the preconditioned residual is dominated by its component
     // along the iterate, so t is a small difference of large terms
-    CKI(launch_combine_rows(h, 1, Win, C1, k, k, h.Z, h.T, -1.0));
+    CKI(launch_combine_rows(h, 1, Win, C1, k, k, h.Z, h.T, -1.0, 0, h.xsplit));
   }
-  CKI(launch_spmm(h, h.T, h.AT, h.MT, k));
+  CKI(launch_spmm(h, h.T, h.AT, h.MT, k, h.xsplit));
   {
     // Step 3: Rayleigh-Ritz in W = U^k + span{t} (+ U^{k-1})
     const double *W[3], *AW[3], *MW[3];
@@ -840,16 +842,16 @@ int run_step(Handle& h, StepBufs& b, int nb, int it, bool reuse, const CaptureCt
       CKI(launch_inner(h, nb, W, nb, AW, Hm));
     }
     CKI(launch_rr(h, m, G, Hm, b.lam_cur, Crr, b.lam_nxt, it + 1, cap ? h.dctl + 3 : nullptr));
-    CKI(launch_combine_rows(h, nb, W, Crr, k, k, nullptr, b.Xn, 1.0));
-    CKI(launch_spmm(h, b.Xn, b.AXn, b.MXn, k));
+    CKI(launch_combine_rows(h, nb, W, Crr, k, k, nullptr, b.Xn, 1.0, 0, h.xsplit));
+    CKI(launch_spmm(h, b.Xn, b.AXn, b.MXn, k, h.xsplit));
     if (h.subspace == BPJD_W_3K) {
       // P_new = the non-iterate blocks of W times their rows of C, with K P_new and
       // M P_new by SpMM (no cancellation)
       if (mixed)
-        CKI(launch_combine_rows(h, nb - 1, W, Crr, k, k, nullptr, b.Pn, 1.0, 1));
+        CKI(launch_combine_rows(h, nb - 1, W, Crr, k, k, nullptr, b.Pn, 1.0, 1, h.xsplit));
       else
-        CKI(launch_combine_rows(h, nb - 1, W + 1, Crr + (size_t)k * k, k, k, nullptr, b.Pn, 1.0));
-      CKI(launch_spmm(h, b.Pn, b.APn, b.MPn, k));
+        CKI(launch_combine_rows(h, nb - 1, W + 1, Crr + (size_t)k * k, k, k, nullptr, b.Pn, 1.0, 0, h.xsplit));
+      CKI(launch_spmm(h, b.Pn, b.APn, b.MPn, k, h.xsplit));
     }
   }
   b.advance(h.subspace == BPJD_W_3K);
@@ -978,6 +980,17 @@ extern "C" int bpjd_solve(bpjd_handle* hh, double* eigvals, double* eigvecs, int
   const size_t vbytes = sizeof(double) * (size_t)n * k;
   int rc = BPJD_OK;
   const double t0 = now_s();
+  // a served solve whose local solves share launches with other requests'
+  // takes part in the batching for its whole duration
+  struct BatchMember {
+    LocalBatcher* b;
+    explicit BatchMember(LocalBatcher* bb) : b(bb) {
+      if (b) batch_enter(b);
+    }
+    ~BatchMember() {
+      if (b) batch_leave(b);
+    }
+  } member(h.batch && batch_eligible(h) ? h.batch : nullptr);
   int it = 0;
   bool converged = false;
   // every solve starts from the same buffer assignment (a captured loop refers to it)

@@ -34,6 +34,8 @@ struct CsrDev {
   double* val = nullptr;
 };
 
+struct LocalBatcher;
+
 struct Handle {
   // ---- sizes and options
   int32_t n = 0, nH = 0, nH0 = 0, k = 0, nsub = 0;
@@ -56,6 +58,7 @@ struct Handle {
   bool same_pattern = false;
   float2* Asplit = nullptr;  // (hi, lo) float pairs of K and M values (double-word SpMM)
   float2* Msplit = nullptr;
+  float2* xsplit = nullptr;  // n x k (hi, lo) split of the block the next double-word SpMM reads
   CsrDev P, PT;             // coarse interpolation and its transpose
   double* Phi = nullptr;    // n_H x n_H row-major, M_H-orthonormal eigenvectors
   double* lamH = nullptr;   // n_H ascending
@@ -111,6 +114,10 @@ struct Handle {
   DevStatus* hstat = nullptr;  // pinned host mirror
   int32_t* derr = nullptr;     // device error flags
 
+  // ---- serving: local solves packed with those of other handles (batch.cpp)
+  LocalBatcher* batch = nullptr;
+  void* batch_ev = nullptr;  // cudaEvent_t: this handle's work up to the local solves
+
   // ---- instrumentation
   bool profile = false;
   std::vector<void*> ev_pool;  // cudaEvent_t
@@ -159,7 +166,9 @@ int gen_eig_host(int n, const std::vector<double>& K, const std::vector<double>&
                  std::vector<double>& Phi, int nvec = -1);
 
 // kernels.cu launchers (all asynchronous on h.stream; return cudaError_t as int)
-int launch_spmm(Handle& h, const double* X, double* YA, double* YM, int ncols);
+// Xs (double-word path only): the (hi, lo) split of X written by the kernel
+// that produced it, read instead of splitting X per nonzero
+int launch_spmm(Handle& h, const double* X, double* YA, double* YM, int ncols, const float2* Xs = nullptr);
 int launch_csr_times_dense(const CsrDev& P, const double* D, int ldd, int ncols, double* Y, int ldy,
                            cudaStream_t s);
 int launch_residual(Handle& h, const double* AX, const double* MX, const double* lam, double* rho);
@@ -170,6 +179,25 @@ int launch_precond(Handle& h, const double* rho, const double* lam, double* Z, i
 enum { kLocalFull = 0, kLocalReuse = 1, kLocalFactorOnly = 2, kLocalForwardOnly = 3, kLocalBackwardOnly = 4 };
 int launch_local(Handle& h, const double* rho, const double* lam, int mode);
 int launch_coarse_prolong(Handle& h, const double* rho, const double* lam, double* Z);
+// Local solves of n handles of one window tier (Bpad) in grouped launches on
+// stream s: handles with refactor[j] = 1 factorise at their shifts (with the
+// fused forward sweep; the wide tiers 64, 96 and 152 in one launch per handle),
+// the others sweep forward on their stored factors, then every handle sweeps
+// backward.  Every handle satisfies can_reuse_factors; n <= kGroupedMax.
+constexpr int kGroupedMax = 16;
+int launch_local_grouped(Handle* const* hs, const double* const* rho, const double* const* lam,
+                         const int* refactor, int n, cudaStream_t s);
+// batch.cpp: the serving path's packing of local solves across handles.  A
+// handle with h.batch set (and the host-driven loop) hands its local solves to
+// batch_local, which returns once they are launched, with the handle's stream
+// ordered after them; batch_enter / batch_leave bracket every solve.
+LocalBatcher* batch_create(int wait_us);
+void batch_free(LocalBatcher* b);
+void batch_enter(LocalBatcher* b);
+void batch_leave(LocalBatcher* b);
+bool batch_eligible(const Handle& h);
+int batch_local(LocalBatcher* b, Handle& h, const double* rho, const double* lam, bool refactor);
+void batch_stats(const LocalBatcher* b, int64_t* flushes, int64_t* jobs);
 // whether this handle's local kernels can reuse stored factors (records of every pair resident)
 bool can_reuse_factors(const Handle& h);
 // sets the dynamic shared-memory limits of every kernel the handle's iterations launch
@@ -187,9 +215,11 @@ size_t gram_partial_doubles(int64_t n, int k, int nu, int nvb, int sym);
 int launch_gram_raw(int64_t n, int k, int nu, const double* const* U, int nvb, int nv, const double* const* V1,
                     const double* const* V2, int sym, double* out1, double* out2, double* partial,
                     size_t partial_capacity, cudaStream_t stream);
-// consistency_only (mixed precision): FP32 update, for the previous-update block P
+// consistency_only (mixed precision): FP32 update, for the previous-update block P;
+// split_out (double-word path only): also the (hi, lo) split of every output value
 int launch_combine_rows(Handle& h, int nin, const double* const* Win, const double* C, int ldc,
-                        int csub, const double* Zadd, double* out, double alpha, int consistency_only = 0);
+                        int csub, const double* Zadd, double* out, double alpha, int consistency_only = 0,
+                        float2* split_out = nullptr);
 // hist_row: history row of the Ritz values (host count), or d_row != NULL: the
 // device step counter + 1 (captured iterations)
 int launch_rr(Handle& h, int m, const double* G, const double* Hm, const double* lam_old, double* C,

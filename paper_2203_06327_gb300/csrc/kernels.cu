@@ -506,7 +506,7 @@ __global__ void __launch_bounds__(256) k_gram_reduce(int nblk, int nv, int mu, i
 constexpr int kCombRows = 64;
 __global__ void __launch_bounds__(256) k_combine_dw(int64_t n, int k, int nin, Ptrs6 W, const double* __restrict__ C,
                                                     int ldc, int csub, const double* __restrict__ Zadd,
-                                                    double* __restrict__ out, double sign) {
+                                                    double* __restrict__ out, double sign, float2* __restrict__ outs) {
   extern __shared__ __align__(16) float csm[];
   const int m = nin * k;
   float* Ch = csm;                       // m x csub
@@ -520,11 +520,26 @@ __global__ void __launch_bounds__(256) k_combine_dw(int64_t n, int k, int nin, P
   }
   const int64_t row0 = (int64_t)blockIdx.x * kCombRows;
   const int nr = (int)min((int64_t)kCombRows, n - row0);
-  for (int t = threadIdx.x; t < nr * m; t += blockDim.x) {
-    const int r = t / m, a = t % m;
-    const dw s = split_f64(W.p[a / k][(row0 + r) * k + (a % k)]);
-    Wh[t] = s.hi;
-    Wl[t] = s.lo;
+  // rows staged by warps, row entries by lanes: lane l holds entries a = l + 32 u
+  // (m <= 96: at most three), whose block and column are fixed
+  {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int ab[3], ac[3];
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      const int a = lane + 32 * u;
+      ab[u] = (a < m) ? a / k : -1;
+      ac[u] = (a < m) ? a - (a / k) * k : 0;
+    }
+    for (int r = wid; r < nr; r += nw) {
+#pragma unroll
+      for (int u = 0; u < 3; ++u)
+        if (ab[u] >= 0) {
+          const dw s = split_f64(W.p[ab[u]][(row0 + r) * k + ac[u]]);
+          Wh[r * m + lane + 32 * u] = s.hi;
+          Wl[r * m + lane + 32 * u] = s.lo;
+        }
+    }
   }
   __syncthreads();
   for (int t = threadIdx.x; t < nr * csub; t += blockDim.x) {
@@ -538,18 +553,25 @@ __global__ void __launch_bounds__(256) k_combine_dw(int64_t n, int k, int nin, P
     const int64_t o = (row0 + r) * csub + j;
     if (Zadd) v += Zadd[o];
     out[o] = v;
+    if (outs) {
+      const dw sp = split_f64(v);
+      outs[o] = make_float2(sp.hi, sp.lo);
+    }
   }
 }
 
 // CSR SpMM in double-word arithmetic with pre-split matrix values (hi/lo
 // float arrays of K and M): YA = K X, YM = M X.  LANES lanes serve one row;
 // lane j of the group owns columns j + LANES c, c < CPL.  The X entries are
-// split on the fly (integer operations only).
-template <int LANES, int CPL>
-__global__ void __launch_bounds__(256, 4) k_spmm_dw(int n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                                                 const float2* __restrict__ va, const float2* __restrict__ vm,
-                                                 const double* __restrict__ X, double* __restrict__ YA,
-                                                 double* __restrict__ YM, int ncols) {
+// split on the fly (integer operations only), or (XS) read as the (hi, lo)
+// pairs that the kernel producing X wrote beside it (split_f64 of the same
+// values: the same products).
+template <int LANES, int CPL, bool XS>
+__global__ void __launch_bounds__(256, 4) k_spmm_dw(int n, const int64_t* __restrict__ rp,
+                                                    const int32_t* __restrict__ ci,
+                                                    const float2* __restrict__ va, const float2* __restrict__ vm,
+                                                    const double* __restrict__ X, const float2* __restrict__ Xs,
+                                                    double* __restrict__ YA, double* __restrict__ YM, int ncols) {
   constexpr int RPW = 32 / LANES;
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -567,11 +589,19 @@ __global__ void __launch_bounds__(256, 4) k_spmm_dw(int n, const int64_t* __rest
     const float2 av = va[e];
     const float2 mv = vm ? vm[e] : make_float2(0.f, 0.f);
     const double* xr = X + col * ncols;
+    const float2* xsr = Xs + col * ncols;
 #pragma unroll
     for (int c = 0; c < CPL; ++c) {
       const int j = j0 + LANES * c;
       if (j < ncols) {
-        const dw x = split_f64(xr[j]);
+        dw x;
+        if (XS) {
+          const float2 p = xsr[j];
+          x.hi = p.x;
+          x.lo = p.y;
+        } else {
+          x = split_f64(xr[j]);
+        }
         a[c].mac(av.x, av.y, x.hi, x.lo);
         m[c].mac(mv.x, mv.y, x.hi, x.lo);
       }
@@ -595,7 +625,7 @@ __global__ void __launch_bounds__(256, 4) k_spmm_dw(int n, const int64_t* __rest
 // W and the coefficients.
 __global__ void __launch_bounds__(256) k_combine_f32(int64_t n, int k, int nin, Ptrs6 W, const double* __restrict__ C,
                                                      int ldc, int csub, const double* __restrict__ Zadd,
-                                                     double* __restrict__ out, float sign) {
+                                                     double* __restrict__ out, float sign, float2* __restrict__ outs) {
   extern __shared__ __align__(16) float csm[];
   const int m = nin * k;
   float* Cs = csm;              // m x csub
@@ -616,7 +646,12 @@ __global__ void __launch_bounds__(256) k_combine_f32(int64_t n, int k, int nin, 
     const int64_t o = (row0 + r) * csub + j;
     float v = sign * acc;
     if (Zadd) v += f64_hi(Zadd[o]);
-    out[o] = f32_to_f64_bits(v);
+    const double vd = f32_to_f64_bits(v);
+    out[o] = vd;
+    if (outs) {
+      const dw sp = split_f64(vd);
+      outs[o] = make_float2(sp.hi, sp.lo);
+    }
   }
 }
 
@@ -900,8 +935,18 @@ __device__ __forceinline__ void mma_tf32(float (&c)[4], const uint32_t (&a)[4], 
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-template <int BMAX>
-__global__ void __launch_bounds__(128, (BMAX <= 40) ? 3 : 2) k_local_factor_mma(
+// Block index of a local-solve kernel body: the launch's own (a launch of one
+// handle) or relative to the first block of the body's segment (grouped launch).
+struct BlockIdx {
+  __device__ __forceinline__ int operator()() const { return (int)blockIdx.x; }
+};
+struct SegBlockIdx {
+  int blk0;
+  __device__ __forceinline__ int operator()() const { return (int)blockIdx.x - blk0; }
+};
+
+template <int BMAX, class BID>
+__device__ __forceinline__ void k_local_factor_mma_body(BID bidf,
     int nsub, int k, const int64_t* __restrict__ sub_ptr, const int32_t* __restrict__ sub_dofs,
     const float* __restrict__ bandK, const float* __restrict__ bandM, const double* __restrict__ lam,
     const double* __restrict__ rho, float* __restrict__ Lbuf, float* __restrict__ wpk, int32_t* err,
@@ -916,8 +961,8 @@ __global__ void __launch_bounds__(128, (BMAX <= 40) ? 3 : 2) k_local_factor_mma(
   const int lane_id = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int lane_g = lane_id >> 2, lane_q = lane_id & 3;
   const int groups_per_sub = (k + kLocalWarps - 1) / kLocalWarps;
-  const int l = blockIdx.x / groups_per_sub;
-  const int i = (blockIdx.x % groups_per_sub) * kLocalWarps + wib;
+  const int l = bidf() / groups_per_sub;
+  const int i = (bidf() % groups_per_sub) * kLocalWarps + wib;
   const bool active = (i < k);
   const int ii = active ? i : 0;
   const int64_t off = sub_ptr[l];
@@ -1154,6 +1199,17 @@ __global__ void __launch_bounds__(128, (BMAX <= 40) ? 3 : 2) k_local_factor_mma(
   if (threadIdx.x == 0)
     for (int c = last_done + 1; c <= last_issued; ++c)
       if (!mbar_drain(&bars[c & 1], (uint32_t)((c >> 1) & 1))) atomicOr(err, kErrDrain);
+}
+
+template <int BMAX>
+__global__ void __launch_bounds__(128, (BMAX <= 40) ? 3 : 2) k_local_factor_mma(
+    int nsub, int k, const int64_t* __restrict__ sub_ptr, const int32_t* __restrict__ sub_dofs,
+    const float* __restrict__ bandK, const float* __restrict__ bandM, const double* __restrict__ lam,
+    const double* __restrict__ rho, float* __restrict__ Lbuf, float* __restrict__ wpk, int32_t* err,
+    int wait_limit, int64_t rec_base) {
+  k_local_factor_mma_body<BMAX, BlockIdx>(BlockIdx(), nsub, k, sub_ptr, sub_dofs, bandK, bandM, lam, rho, Lbuf, wpk,
+                                          err,
+                                wait_limit, rec_base);
 }
 
 // ---------------------------------------------------------------------------
@@ -1466,8 +1522,8 @@ struct BwdShape {
   static constexpr size_t smem_floats = (size_t)WPB * 2 * 4 * PS;
 };
 
-template <int BMAX>
-__global__ void __launch_bounds__(64, 1) k_local_backward(int nsub, int k, const int64_t* __restrict__ sub_ptr,
+template <int BMAX, class BID>
+__device__ __forceinline__ void k_local_backward_body(BID bidf, int nsub, int k, const int64_t* __restrict__ sub_ptr,
                                                        const float* __restrict__ Lbuf, float* __restrict__ wpk,
                                                        int32_t* err, int wait_limit, int64_t rec_base) {
   using S = BwdShape<BMAX>;
@@ -1478,7 +1534,7 @@ __global__ void __launch_bounds__(64, 1) k_local_backward(int nsub, int k, const
   extern __shared__ __align__(128) float bsm[];
   __shared__ __align__(8) uint64_t bars[WPB][2];
   const int lane = threadIdx.x & 31, e = lane & 7, p = lane >> 3, wib = threadIdx.x >> 5;
-  const int wglob = blockIdx.x * WPB + wib;
+  const int wglob = bidf() * WPB + wib;
   const int wps = (k + 3) / 4;  // warps per subdomain
   const int l = wglob / wps;
   if (l >= nsub) return;  // whole warps only; no block-wide barrier follows
@@ -1589,6 +1645,13 @@ __global__ void __launch_bounds__(64, 1) k_local_backward(int nsub, int k, const
       if (!mbar_drain(&bar[ch & 1], (uint32_t)(((chtop - ch) >> 1) & 1))) atomicOr(err, kErrDrain);
 }
 
+template <int BMAX>
+__global__ void __launch_bounds__(64, 1) k_local_backward(int nsub, int k, const int64_t* __restrict__ sub_ptr,
+                                                       const float* __restrict__ Lbuf, float* __restrict__ wpk,
+                                                       int32_t* err, int wait_limit, int64_t rec_base) {
+  k_local_backward_body<BMAX, BlockIdx>(BlockIdx(), nsub, k, sub_ptr, Lbuf, wpk, err, wait_limit, rec_base);
+}
+
 // ---------------------------------------------------------------------------
 // Local solves, forward substitution L y = R_l rho_i with stored band factors,
 // for the applications that reuse the factors of an earlier one (the
@@ -1601,8 +1664,8 @@ __global__ void __launch_bounds__(64, 1) k_local_backward(int nsub, int k, const
 // then r_r -= L(r, j) y_j for the rows r of column j's band, and row j + BMAX
 // enters the freed slot.
 // ---------------------------------------------------------------------------
-template <int BMAX>
-__global__ void __launch_bounds__(64, 1) k_local_forward(int nsub, int k, const int64_t* __restrict__ sub_ptr,
+template <int BMAX, class BID>
+__device__ __forceinline__ void k_local_forward_body(BID bidf, int nsub, int k, const int64_t* __restrict__ sub_ptr,
                                                       const int32_t* __restrict__ sub_dofs,
                                                       const double* __restrict__ rho, const float* __restrict__ Lbuf,
                                                       float* __restrict__ wpk, int32_t* err, int wait_limit,
@@ -1615,7 +1678,7 @@ __global__ void __launch_bounds__(64, 1) k_local_forward(int nsub, int k, const 
   extern __shared__ __align__(128) float fsm[];
   __shared__ __align__(8) uint64_t bars[WPB][2];
   const int lane = threadIdx.x & 31, e = lane & 7, p = lane >> 3, wib = threadIdx.x >> 5;
-  const int wglob = blockIdx.x * WPB + wib;
+  const int wglob = bidf() * WPB + wib;
   const int wps = (k + 3) / 4;  // warps per subdomain
   const int l = wglob / wps;
   if (l >= nsub) return;  // whole warps only; no block-wide barrier follows
@@ -1729,6 +1792,16 @@ __global__ void __launch_bounds__(64, 1) k_local_forward(int nsub, int k, const 
       if (!mbar_drain(&bar[ch & 1], (uint32_t)((ch >> 1) & 1))) atomicOr(err, kErrDrain);
 }
 
+template <int BMAX>
+__global__ void __launch_bounds__(64, 1) k_local_forward(int nsub, int k, const int64_t* __restrict__ sub_ptr,
+                                                      const int32_t* __restrict__ sub_dofs,
+                                                      const double* __restrict__ rho, const float* __restrict__ Lbuf,
+                                                      float* __restrict__ wpk, int32_t* err, int wait_limit,
+                                                      int64_t rec_base) {
+  k_local_forward_body<BMAX, BlockIdx>(BlockIdx(), nsub, k, sub_ptr, sub_dofs, rho, Lbuf, wpk, err, wait_limit,
+                                       rec_base);
+}
+
 
 // ---------------------------------------------------------------------------
 // Blocked sweeps with the stored band factors (window tiers up to 48): the
@@ -1763,8 +1836,8 @@ struct BlkShape {
   static size_t smem_floats(int nbuf) { return (size_t)WPB * nbuf * 4 * PS; }
 };
 
-template <int BMAX, bool FWD>
-__global__ void __launch_bounds__(64, 1) k_local_sweep_blk(int nsub, int k, const int64_t* __restrict__ sub_ptr,
+template <int BMAX, bool FWD, class BID>
+__device__ __forceinline__ void k_local_sweep_blk_body(BID bidf, int nsub, int k, const int64_t* __restrict__ sub_ptr,
                                                         const int32_t* __restrict__ sub_dofs,
                                                         const double* __restrict__ rho,
                                                         const float* __restrict__ Lbuf, float* __restrict__ wpk,
@@ -1777,7 +1850,7 @@ __global__ void __launch_bounds__(64, 1) k_local_sweep_blk(int nsub, int k, cons
   extern __shared__ __align__(128) float ssm[];
   __shared__ __align__(8) uint64_t bars[WPB][S::NBUF_MAX];
   const int lane = threadIdx.x & 31, e = lane & 7, p = lane >> 3, wib = threadIdx.x >> 5;
-  const int wglob = blockIdx.x * WPB + wib;
+  const int wglob = bidf() * WPB + wib;
   const int wps = (k + 3) / 4;  // warps per subdomain
   const int l = wglob / wps;
   if (l >= nsub) return;  // whole warps only; no block-wide barrier follows
@@ -1974,6 +2047,17 @@ __global__ void __launch_bounds__(64, 1) k_local_sweep_blk(int nsub, int k, cons
   if (lane == 0)
     for (int q = n_done; q < n_issued; ++q)
       if (!mbar_drain(&bar[q % nbuf], (uint32_t)((q / nbuf) & 1))) atomicOr(err, kErrDrain);
+}
+
+template <int BMAX, bool FWD>
+__global__ void __launch_bounds__(64, 1) k_local_sweep_blk(int nsub, int k, const int64_t* __restrict__ sub_ptr,
+                                                        const int32_t* __restrict__ sub_dofs,
+                                                        const double* __restrict__ rho,
+                                                        const float* __restrict__ Lbuf, float* __restrict__ wpk,
+                                                        int32_t* err, int wait_limit, int64_t rec_base,
+                                                        int nbuf) {
+  k_local_sweep_blk_body<BMAX, FWD, BlockIdx>(BlockIdx(), nsub, k, sub_ptr, sub_dofs, rho, Lbuf, wpk, err, wait_limit,
+                                    rec_base, nbuf);
 }
 
 // ---------------------------------------------------------------------------
@@ -2518,7 +2602,7 @@ void prof_flush(Handle& h) {
 // ===========================================================================
 // launchers
 // ===========================================================================
-int launch_spmm(Handle& h, const double* X, double* YA, double* YM, int ncols) {
+int launch_spmm(Handle& h, const double* X, double* YA, double* YM, int ncols, const float2* Xs) {
   ProfScope ps(h, BPJD_PROF_SPMM);
   const int n = h.n;
   auto go = [&](auto lanes_tag, const CsrDev& A, const double* vm, double* ya, double* ym) {
@@ -2538,7 +2622,12 @@ int launch_spmm(Handle& h, const double* X, double* YA, double* YM, int ncols) {
       constexpr int RPW = 32 / LANES;
       int64_t warps = (n + RPW - 1) / RPW;
       int64_t blocks = (warps * 32 + 255) / 256;
-      k_spmm_dw<LANES, CPL><<<(unsigned)blocks, 256, 0, h.stream>>>(n, A.row_ptr, A.col, va, vm, X, ya, ym, ncols);
+      if (Xs)
+        k_spmm_dw<LANES, CPL, true><<<(unsigned)blocks, 256, 0, h.stream>>>(n, A.row_ptr, A.col, va, vm, X, Xs, ya,
+                                                                           ym, ncols);
+      else
+        k_spmm_dw<LANES, CPL, false><<<(unsigned)blocks, 256, 0, h.stream>>>(n, A.row_ptr, A.col, va, vm, X, Xs, ya,
+                                                                            ym, ncols);
       h.launches += 1;
     };
     using I = std::integral_constant<int, 1>;
@@ -2702,9 +2791,10 @@ int launch_gram(Handle& h, int nu, const double* const* U, int nvb, int nv, cons
 }
 
 int launch_combine_rows(Handle& h, int nin, const double* const* Win, const double* C, int ldc, int csub,
-                        const double* Zadd, double* out, double sign, int consistency_only) {
+                        const double* Zadd, double* out, double sign, int consistency_only, float2* split_out) {
   ProfScope ps(h, BPJD_PROF_COMBINE);
   h.launches += 1;
+  if (nin < 1 || nin > 6 || nin * h.k > 96 || csub < 1 || csub > 256) return (int)cudaErrorInvalidValue;
   Ptrs6 w{};
   for (int b = 0; b < nin; ++b) w.p[b] = Win[b];
   if (h.dword() && consistency_only) {
@@ -2712,7 +2802,8 @@ int launch_combine_rows(Handle& h, int nin, const double* const* Win, const doub
     const size_t sm = (size_t)(m * csub + kCombRows * m) * sizeof(float);
     allow_dynamic_smem((const void*)k_combine_f32);
     const int64_t blocks = ((int64_t)h.n + kCombRows - 1) / kCombRows;
-    k_combine_f32<<<(unsigned)blocks, 256, sm, h.stream>>>(h.n, h.k, nin, w, C, ldc, csub, Zadd, out, (float)sign);
+    k_combine_f32<<<(unsigned)blocks, 256, sm, h.stream>>>(h.n, h.k, nin, w, C, ldc, csub, Zadd, out, (float)sign,
+                                                           split_out);
     return (int)cudaGetLastError();
   }
   if (h.dword()) {
@@ -2720,7 +2811,8 @@ int launch_combine_rows(Handle& h, int nin, const double* const* Win, const doub
     const size_t sm = (size_t)(2 * m * csub + 2 * kCombRows * m) * sizeof(float);
     allow_dynamic_smem((const void*)k_combine_dw);
     const int64_t blocks = ((int64_t)h.n + kCombRows - 1) / kCombRows;
-    k_combine_dw<<<(unsigned)blocks, 256, sm, h.stream>>>(h.n, h.k, nin, w, C, ldc, csub, Zadd, out, sign);
+    k_combine_dw<<<(unsigned)blocks, 256, sm, h.stream>>>(h.n, h.k, nin, w, C, ldc, csub, Zadd, out, sign,
+                                                          split_out);
     return (int)cudaGetLastError();
   }
   int64_t tot = (int64_t)h.n * csub;
@@ -2728,6 +2820,65 @@ int launch_combine_rows(Handle& h, int nin, const double* const* Win, const doub
   k_combine_rows<<<(unsigned)((tot + 255) / 256), 256, sm, h.stream>>>(h.n, h.k, nin, w, C, ldc, csub, Zadd, out,
                                                                         sign);
   return (int)cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Grouped local solves: the (subdomain, shift) work of several solver handles
+// of one window tier in one grid.  Segment j owns the blocks [blk0_j,
+// blk0_{j+1}); a block runs the same kernel body as a launch of its handle
+// alone would, on that handle's arrays, so every pair is computed exactly as
+// it is alone.  (The wide tiers' factorisations keep one launch per handle.)
+// ---------------------------------------------------------------------------
+constexpr int kMaxSegs = 16;
+struct LocalSeg {
+  const int64_t* sub_ptr;
+  const int32_t* sub_dofs;
+  const float* bandK;
+  const float* bandM;
+  const double* lam;
+  const double* rho;
+  float* Lbuf;
+  float* wpk;
+  int32_t* err;
+  int nsub, k, wait_limit, blk0;
+};
+struct LocalSegs {
+  int n;
+  LocalSeg s[kMaxSegs];
+};
+__device__ __forceinline__ int seg_of(const LocalSegs& g, int b) {
+  int j = 0;
+  while (j + 1 < g.n && b >= g.s[j + 1].blk0) ++j;
+  return j;
+}
+
+template <int BMAX>
+__global__ void __launch_bounds__(128, (BMAX <= 40) ? 3 : 2)
+    k_local_factor_mma_grp(const __grid_constant__ LocalSegs g) {
+  const LocalSeg& q = g.s[seg_of(g, blockIdx.x)];
+  k_local_factor_mma_body<BMAX, SegBlockIdx>(SegBlockIdx{q.blk0}, q.nsub, q.k, q.sub_ptr, q.sub_dofs, q.bandK,
+                                             q.bandM, q.lam,
+                                q.rho, q.Lbuf, q.wpk, q.err, q.wait_limit, 0);
+}
+template <int BMAX, bool FWD>
+__global__ void __launch_bounds__(64, 1) k_local_sweep_blk_grp(const __grid_constant__ LocalSegs g, int nbuf) {
+  const LocalSeg& q = g.s[seg_of(g, blockIdx.x)];
+  k_local_sweep_blk_body<BMAX, FWD, SegBlockIdx>(SegBlockIdx{q.blk0}, q.nsub, q.k, q.sub_ptr, q.sub_dofs, q.rho,
+                                                 q.Lbuf, q.wpk,
+                                    q.err, q.wait_limit, 0, nbuf);
+}
+template <int BMAX>
+__global__ void __launch_bounds__(64, 1) k_local_forward_grp(const __grid_constant__ LocalSegs g) {
+  const LocalSeg& q = g.s[seg_of(g, blockIdx.x)];
+  k_local_forward_body<BMAX, SegBlockIdx>(SegBlockIdx{q.blk0}, q.nsub, q.k, q.sub_ptr, q.sub_dofs, q.rho, q.Lbuf,
+                                          q.wpk, q.err,
+                             q.wait_limit, 0);
+}
+template <int BMAX>
+__global__ void __launch_bounds__(64, 1) k_local_backward_grp(const __grid_constant__ LocalSegs g) {
+  const LocalSeg& q = g.s[seg_of(g, blockIdx.x)];
+  k_local_backward_body<BMAX, SegBlockIdx>(SegBlockIdx{q.blk0}, q.nsub, q.k, q.sub_ptr, q.Lbuf, q.wpk, q.err,
+                                           q.wait_limit, 0);
 }
 
 // Device facts for launch shapes, read once per device: SM count, shared memory
@@ -2958,9 +3109,98 @@ int prime_kernel_attributes(Handle& h) {
 }
 
 int launch_precond(Handle& h, const double* rho, const double* lam, double* Z, int reuse) {
-  int e = launch_local(h, rho, lam, (reuse && can_reuse_factors(h)) ? kLocalReuse : kLocalFull);
+  const bool stored = reuse && can_reuse_factors(h);
+  int e;
+  if (h.batch && batch_eligible(h)) {
+    // served handle: the local solves go into a launch shared with other requests
+    e = batch_local(h.batch, h, rho, lam, !stored);
+    if (e == 0) {
+      h.launches += 2;
+      if (stored)
+        ++h.reuses;
+      else
+        ++h.refactorisations;
+    }
+  } else {
+    e = launch_local(h, rho, lam, stored ? kLocalReuse : kLocalFull);
+  }
   if (e) return e;
   return launch_coarse_prolong(h, rho, lam, Z);
+}
+
+int launch_local_grouped(Handle* const* hs, const double* const* rho, const double* const* lam,
+                         const int* refactor, int n, cudaStream_t s) {
+  if (n < 1 || n > kGroupedMax || n > kMaxSegs) return (int)cudaErrorInvalidValue;
+  const int BM = hs[0]->Bpad;
+  for (int j = 0; j < n; ++j)
+    if (!can_reuse_factors(*hs[j]) || hs[j]->Bpad != BM) return (int)cudaErrorInvalidValue;
+  auto run = [&](auto bm) -> int {
+    constexpr int B = decltype(bm)::value;
+    // segments: factorisations, forward sweeps on stored factors, backward sweeps
+    LocalSegs gf{}, gr{}, gb{};
+    int bf = 0, br = 0, bb = 0;
+    for (int j = 0; j < n; ++j) {
+      Handle& h = *hs[j];
+      LocalSeg q{h.sub_ptr, h.sub_dofs, h.bandKf, h.bandMf, lam[j], rho[j], (float*)h.Lbuf, (float*)h.wpk,
+                 h.derr, h.nsub, h.k, h.wait_limit, 0};
+      const int sweep_blocks = (h.nsub * ((h.k + 3) / 4) + 1) / 2;
+      if (refactor[j]) {
+        q.blk0 = bf;
+        gf.s[gf.n++] = q;
+        bf += (B <= 48) ? h.nsub * ((h.k + kLocalWarps - 1) / kLocalWarps) : h.nsub * h.k;
+      } else {
+        q.blk0 = br;
+        gr.s[gr.n++] = q;
+        br += sweep_blocks;
+      }
+      q.blk0 = bb;
+      gb.s[gb.n++] = q;
+      bb += sweep_blocks;
+    }
+    if constexpr (B <= 48) {
+      if (gf.n) {
+        allow_dynamic_smem((const void*)k_local_factor_mma_grp<B>);
+        k_local_factor_mma_grp<B><<<bf, 32 * kLocalWarps, sizeof(float) * MmaShape<B>::smem_floats, s>>>(gf);
+      }
+      if (gr.n) {
+        const int nbuf = sweep_ring_buffers<B>(br);
+        allow_dynamic_smem((const void*)k_local_sweep_blk_grp<B, true>);
+        k_local_sweep_blk_grp<B, true><<<br, 32 * BlkShape<B>::WPB, sizeof(float) * BlkShape<B>::smem_floats(nbuf),
+                                         s>>>(gr, nbuf);
+      }
+      const int nbuf = sweep_ring_buffers<B>(bb);
+      allow_dynamic_smem((const void*)k_local_sweep_blk_grp<B, false>);
+      k_local_sweep_blk_grp<B, false><<<bb, 32 * BlkShape<B>::WPB, sizeof(float) * BlkShape<B>::smem_floats(nbuf),
+                                        s>>>(gb, nbuf);
+    } else {
+      const size_t bsm = sizeof(float) * BwdShape<B>::smem_floats;
+      // wide tiers: each request's factorisation in a launch of its own (its register
+      // allocation is tuned for one subdomain-shift pair per CTA), on the shared stream
+      for (int j = 0; j < gf.n; ++j) {
+        const LocalSeg& q = gf.s[j];
+        k_local_factor_wide<B><<<q.nsub * q.k, 32 * WideShape<B>::NW, 0, s>>>(
+            q.nsub * q.k, q.k, q.sub_ptr, q.sub_dofs, q.bandK, q.bandM, q.lam, q.rho, q.Lbuf, q.wpk, q.err, 0);
+      }
+      if (gr.n) {
+        allow_dynamic_smem((const void*)k_local_forward_grp<B>);
+        k_local_forward_grp<B><<<br, 32 * BwdShape<B>::WPB, bsm, s>>>(gr);
+      }
+      allow_dynamic_smem((const void*)k_local_backward_grp<B>);
+      k_local_backward_grp<B><<<bb, 32 * BwdShape<B>::WPB, bsm, s>>>(gb);
+    }
+    return (int)cudaGetLastError();
+  };
+  switch (BM) {
+    case 16: return run(std::integral_constant<int, 16>());
+    case 24: return run(std::integral_constant<int, 24>());
+    case 32: return run(std::integral_constant<int, 32>());
+    case 40: return run(std::integral_constant<int, 40>());
+    case 48: return run(std::integral_constant<int, 48>());
+    case 64: return run(std::integral_constant<int, 64>());
+    case 96: return run(std::integral_constant<int, 96>());
+    case 152: return run(std::integral_constant<int, 152>());
+    default: return (int)cudaErrorInvalidValue;
+  }
 }
 
 int launch_coarse_prolong(Handle& h, const double* rho, const double* lam, double* Z) {

@@ -1,8 +1,10 @@
 // Serving many independent eigenproblems on one GPU (the bpjd_server_* entry
 // points of bpjd.h).  Worker threads, each with its own CUDA stream, run
-// bpjd_setup + bpjd_solve on requests taken first-in first-out from a queue;
-// the request at the head starts when its estimated device footprint fits in
-// the memory budget beside the requests in flight.
+// bpjd_setup + bpjd_solve on requests taken from a queue (smallest estimated
+// work first with aging, or first-in first-out); a request starts when its
+// estimated device footprint fits in the memory budget beside the requests in
+// flight.  With batch_local the local solves of the requests in flight share
+// grouped launches (batch.cpp).
 
 #include <cuda_runtime.h>
 
@@ -19,6 +21,7 @@
 #include <vector>
 
 #include "bpjd.h"
+#include "bpjd_internal.h"
 
 namespace {
 
@@ -134,6 +137,7 @@ struct bpjd_server {
   uint64_t next_id = 1;
   bool stop = false;
   std::vector<std::thread> threads;
+  bpjd::LocalBatcher* batch = nullptr;  // shared launches of the local solves (batch_local)
 };
 
 namespace {
@@ -158,6 +162,7 @@ void run_request(bpjd_server* s, Request& r, cudaStream_t stream) {
   bpjd_handle* h = nullptr;
   int rc = bpjd_setup(&A, &M, &P, r.has_p0 ? &P0 : nullptr, &part, &o, &h);
   if (rc == BPJD_OK) {
+    reinterpret_cast<bpjd::Handle*>(h)->batch = s->batch;
     r.lam.resize((size_t)r.k);
     r.X.resize((size_t)r.A.nr * r.k);
     rc = bpjd_solve(h, r.lam.data(), r.X.data(), 0, &r.st);
@@ -188,7 +193,8 @@ int pick_request(const bpjd_server* s, double now) {
 void worker(bpjd_server* s) {
   cudaSetDevice(s->device);
   cudaStream_t stream = nullptr;
-  if (cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) != cudaSuccess) stream = nullptr;  // requests fail with BPJD_ERR_CUDA
+  // without a stream the worker's requests fail with BPJD_ERR_CUDA
+  if (cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) != cudaSuccess) stream = nullptr;
   for (;;) {
     std::shared_ptr<Request> r;
     {
@@ -238,6 +244,8 @@ extern "C" void bpjd_server_default_opts(bpjd_server_opts* o) {
   o->admission = BPJD_ADMIT_SMALLEST;
   o->starvation_s = 1.0;
   o->host_loop = 1;
+  o->batch_local = 1;
+  o->batch_wait_us = 100;
 }
 
 extern "C" int bpjd_server_create(const bpjd_server_opts* opts, bpjd_server** out) {
@@ -245,11 +253,21 @@ extern "C" int bpjd_server_create(const bpjd_server_opts* opts, bpjd_server** ou
   *out = nullptr;
   if (opts->workers < 1 || opts->workers > 32) return BPJD_ERR_BAD_ARG;
   if (opts->admission != BPJD_ADMIT_SMALLEST && opts->admission != BPJD_ADMIT_FIFO) return BPJD_ERR_BAD_ARG;
+  if (opts->batch_local < 0 || opts->batch_local > 1 || opts->batch_wait_us < 0 ||
+      (opts->batch_local && !opts->host_loop))
+    return BPJD_ERR_BAD_ARG;
   auto* s = new bpjd_server;
   s->o = *opts;
   if (cudaGetDevice(&s->device) != cudaSuccess) {
     delete s;
     return BPJD_ERR_CUDA;
+  }
+  if (opts->batch_local) {
+    s->batch = bpjd::batch_create(opts->batch_wait_us);
+    if (!s->batch) {
+      delete s;
+      return BPJD_ERR_CUDA;
+    }
   }
   s->budget = opts->hbm_budget_bytes;
   if (s->budget == 0) {
@@ -346,5 +364,14 @@ extern "C" void bpjd_server_free(bpjd_server* s) {
   }
   s->cv_work.notify_all();
   for (auto& t : s->threads) t.join();
+  bpjd::batch_free(s->batch);
   delete s;
+}
+
+extern "C" int bpjd_server_batch_stats(const bpjd_server* s, int64_t* launches, int64_t* solves) {
+  if (!s) return BPJD_ERR_BAD_ARG;
+  if (launches) *launches = 0;
+  if (solves) *solves = 0;
+  if (s->batch) bpjd::batch_stats(s->batch, launches, solves);
+  return BPJD_OK;
 }

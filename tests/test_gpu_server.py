@@ -115,3 +115,35 @@ def test_budget_rejects_oversize_request():
         assert e.value.code == B.ERR_TOO_LARGE
     finally:
         srv.close()
+
+
+def test_local_solves_share_launches_across_requests():
+    """With batch_local (the default) the local solves of the requests in flight run in
+    shared grouped launches, one per kernel kind and window tier (here tiers 16, 24 and the
+    wide tier 64), so there are fewer launch groups than preconditioner applications; every
+    request's result is bitwise that of the same request served with packing off and of the
+    request solved alone."""
+    specs = [config_c1(), replace(config_c1(), k=5), config_small_2d(),
+             config_small_2d(nx=64, ny=64, nsx=4, nsy=4, delta=2, k=7),
+             config_small_2d(nx=64, ny=64, nsx=8, nsy=8, delta=2, k=4), config_small_3d(n=24, ns=4)]
+    pbs = [B.problem_from_spec(s) for s in specs]
+    out = {}
+    for batch in (True, False):
+        srv = B.Server(workers=len(specs), batch_local=batch, batch_wait_us=2000)
+        try:
+            tickets = [srv.submit(pb, s.k) for pb, s in zip(pbs, specs)]
+            results = [srv.poll(t) for t in tickets]
+            out[batch] = (results, srv.batch_stats())
+        finally:
+            srv.close()
+    (packed, (groups, apps)), (plain, stats_off) = out[True], out[False]
+    assert stats_off == (0, 0)
+    assert 0 < groups < apps, (groups, apps)
+    for pb, s, r1, r0 in zip(pbs, specs, packed, plain):
+        assert r1[0] == B.OK and r0[0] == B.OK, s.name
+        np.testing.assert_array_equal(r1[1], r0[1])
+        np.testing.assert_array_equal(r1[2], r0[2])
+        assert r1[3]["iters"] == r0[3]["iters"]
+        lam1, X1 = _alone(pb, s.k)
+        np.testing.assert_array_equal(r1[1], lam1)
+        np.testing.assert_array_equal(r1[2], X1)
