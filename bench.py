@@ -165,7 +165,7 @@ def spmm_bytes(nnz, n, k):
 # C2 solve (k_local_factor_mma<40>, k_local_sweep_blk<40, 0/1>: 7 factorisations, 39
 # backward and 32 forward sweeps), divided by its 39 applications; valid for the kernel
 # source it was measured on (sha256 of csrc/kernels.cu, first 16 hex digits), null otherwise
-LOCAL_TRAFFIC = {("c2_kappa_rect_p1_h512", "mixed"): ("c794f34af717b20d", 1.264e9)}
+LOCAL_TRAFFIC = {("c2_kappa_rect_p1_h512", "mixed"): ("c5a8e8fc55da6951", 1.2635e9)}
 
 
 def _kernel_source_hash():
@@ -644,15 +644,26 @@ def run_ours(a):
             h2d += sum(x.nbytes for x in (pb.P0.row_ptr, pb.P0.col_idx, pb.P0.val))
         h2d += pb.part.sub_ptr.nbytes + pb.part.sub_dofs.nbytes
         d2h = k * 8 + spec.n_dofs * k * 8
+        # the inputs and the eigenvector output in pinned host memory (copied once, before timing)
+        def pinned(x):
+            return None if x is None else torch.from_numpy(np.ascontiguousarray(x)).pin_memory().numpy()
+
+        def pin_csr(c):
+            return B.CsrArrays(c.n_rows, c.n_cols, pinned(c.row_ptr), pinned(c.col_idx), pinned(c.val))
+
+        hpb = B.Problem(pin_csr(pb.K), pin_csr(pb.M), pin_csr(pb.P), pin_csr(pb.P0),
+                        B.PartitionArrays(pinned(pb.part.sub_ptr), pinned(pb.part.sub_dofs),
+                                          pinned(pb.part.sub_color), pb.part.n_colors), pb.tau)
+        X_out = torch.empty((spec.n_dofs, k), dtype=torch.float64, pin_memory=True).numpy()
         et = []
         with torch.cuda.stream(stream):
             for s in range(1 + min(a.steps, 3)):
                 flush.fill_(1.0)
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
-                sv = B.Solver.from_problem(pb, k, device=None, precision=prec, subspace=sub, stream=stream,
+                sv = B.Solver.from_problem(hpb, k, device=None, precision=prec, subspace=sub, stream=stream,
                                            tol=a.tol, max_iter=a.max_iter)
-                lam_h, X_h, st_h = sv.solve(eigvecs="host")
+                lam_h, X_h, st_h = sv.solve(eigvecs="host", out=X_out)
                 t1 = time.perf_counter()
                 sv.close()
                 if s > 0:

@@ -331,12 +331,13 @@ class Solver:
             pass
 
     def solve(self, eigvecs: str = "host", out=None, raise_on_noconv: bool = True):
-        """Returns (eigenvalues, eigenvectors or None, stats dict).  eigvecs: "host" | "device" | None."""
+        """Returns (eigenvalues, eigenvectors or None, stats dict).  eigvecs: "host" | "device" | None;
+        out: the n x k float64 array (host) or CUDA tensor (device) that receives them."""
         lam = np.empty(self.k, dtype=np.float64)
         X = None
         on_dev = 0
         if eigvecs == "host":
-            X = np.empty((self.n, self.k), dtype=np.float64)
+            X = out if out is not None else np.empty((self.n, self.k), dtype=np.float64)
         elif eigvecs == "device":
             import torch
             X = out if out is not None else torch.empty((self.n, self.k), dtype=torch.float64, device="cuda")

@@ -13,6 +13,7 @@
 #include <string>
 #include <future>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "bpjd_internal.h"
@@ -125,16 +126,43 @@ int host_view(const bpjd_csr* c, bool on_dev, bool need_vals, HostCsr& out) {
   return BPJD_OK;
 }
 
-int validate_csr(const HostCsr& c) {
-  if (c.n_rows < 0 || c.n_cols < 0 || c.nnz < 0) return BPJD_ERR_BAD_ARG;
-  if (c.rp[0] != 0 || c.rp[c.n_rows] != c.nnz) return BPJD_ERR_CSR_INVALID;
-  for (int64_t r = 0; r < c.n_rows; ++r) {
-    if (c.rp[r + 1] < c.rp[r]) return BPJD_ERR_CSR_INVALID;
-    for (int64_t e = c.rp[r]; e < c.rp[r + 1]; ++e) {
-      if (c.ci[e] < 0 || c.ci[e] >= c.n_cols) return BPJD_ERR_CSR_INVALID;
-      if (e > c.rp[r] && c.ci[e] <= c.ci[e - 1]) return BPJD_ERR_CSR_INVALID;
-    }
+// Row pointers start at 0, end at nnz and never decrease; every row's columns
+// ascend strictly within [0, n_cols).  The matrices are checked together, in
+// row ranges on up to 16 host threads (a row range only reads its own rows).
+int validate_csrs(const std::vector<const HostCsr*>& cs) {
+  int64_t nnz = 0;
+  for (const HostCsr* c : cs) {
+    if (c->n_rows < 0 || c->n_cols < 0 || c->nnz < 0) return BPJD_ERR_BAD_ARG;
+    if (c->rp[0] != 0 || c->rp[c->n_rows] != c->nnz) return BPJD_ERR_CSR_INVALID;
+    // the row pointers first: every row range then indexes inside [0, nnz)
+    for (int64_t r = 0; r < c->n_rows; ++r)
+      if (c->rp[r + 1] < c->rp[r] || c->rp[r + 1] > c->nnz) return BPJD_ERR_CSR_INVALID;
+    nnz += c->nnz;
   }
+  auto rows = [](const HostCsr& c, int64_t r0, int64_t r1) -> bool {
+    for (int64_t r = r0; r < r1; ++r)
+      for (int64_t e = c.rp[r]; e < c.rp[r + 1]; ++e) {
+        if (c.ci[e] < 0 || c.ci[e] >= c.n_cols) return false;
+        if (e > c.rp[r] && c.ci[e] <= c.ci[e - 1]) return false;
+      }
+    return true;
+  };
+  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  const int T = (int)std::max<int64_t>(1, std::min<int64_t>(std::min<unsigned>(16, hw), nnz / 400000));
+  std::vector<char> ok((size_t)T, 1);
+  auto part = [&](int t) {
+    for (const HostCsr* c : cs) {
+      const int64_t per = (c->n_rows + T - 1) / T;
+      const int64_t r0 = std::min<int64_t>(c->n_rows, t * per), r1 = std::min<int64_t>(c->n_rows, r0 + per);
+      if (!rows(*c, r0, r1)) ok[t] = 0;
+    }
+  };
+  std::vector<std::thread> th;
+  for (int t = 1; t < T; ++t) th.emplace_back(part, t);
+  part(0);
+  for (auto& x : th) x.join();
+  for (char v : ok)
+    if (!v) return BPJD_ERR_CSR_INVALID;
   return BPJD_OK;
 }
 
@@ -319,13 +347,12 @@ extern "C" int bpjd_setup(const bpjd_csr* A, const bpjd_csr* M, const bpjd_csr* 
       host_view(A, false, false, vA);
       host_view(M, false, false, vM);
       host_view(P, false, false, vP);
-      if ((rc = validate_csr(vA)) != BPJD_OK) goto fail;
-      if ((rc = validate_csr(vM)) != BPJD_OK) goto fail;
-      if ((rc = validate_csr(vP)) != BPJD_OK) goto fail;
+      std::vector<const HostCsr*> cs{&vA, &vM, &vP};
       if (P0) {
         host_view(P0, false, false, vP0);
-        if ((rc = validate_csr(vP0)) != BPJD_OK) goto fail;
+        cs.push_back(&vP0);
       }
+      if ((rc = validate_csrs(cs)) != BPJD_OK) goto fail;
       if ((rc = validate_partition(nsub, n, part->sub_ptr, part->sub_dofs)) != BPJD_OK) goto fail;
     }
     h->nH = P->n_cols;

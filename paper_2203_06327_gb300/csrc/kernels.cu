@@ -520,25 +520,28 @@ __global__ void __launch_bounds__(256) k_combine_dw(int64_t n, int k, int nin, P
   }
   const int64_t row0 = (int64_t)blockIdx.x * kCombRows;
   const int nr = (int)min((int64_t)kCombRows, n - row0);
-  // rows staged by warps, row entries by lanes: lane l holds entries a = l + 32 u
-  // (m <= 96: at most three), whose block and column are fixed
+  // staged entries t = tid, tid + blockDim, ... of the nr x m row block: (row, entry)
+  // advanced incrementally, the block and column of entry a read from a table (no
+  // integer division per element)
+  __shared__ unsigned char eb[96], ec[96];
+  for (int a = threadIdx.x; a < m; a += blockDim.x) {
+    eb[a] = (unsigned char)(a / k);
+    ec[a] = (unsigned char)(a % k);
+  }
+  __syncthreads();
   {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    int ab[3], ac[3];
-#pragma unroll
-    for (int u = 0; u < 3; ++u) {
-      const int a = lane + 32 * u;
-      ab[u] = (a < m) ? a / k : -1;
-      ac[u] = (a < m) ? a - (a / k) * k : 0;
-    }
-    for (int r = wid; r < nr; r += nw) {
-#pragma unroll
-      for (int u = 0; u < 3; ++u)
-        if (ab[u] >= 0) {
-          const dw s = split_f64(W.p[ab[u]][(row0 + r) * k + ac[u]]);
-          Wh[r * m + lane + 32 * u] = s.hi;
-          Wl[r * m + lane + 32 * u] = s.lo;
-        }
+    int r = threadIdx.x / m, a = threadIdx.x % m;
+    const int dr = blockDim.x / m, da = blockDim.x % m;
+    while (r < nr) {
+      const dw s = split_f64(W.p[eb[a]][(row0 + r) * k + ec[a]]);
+      Wh[r * m + a] = s.hi;
+      Wl[r * m + a] = s.lo;
+      a += da;
+      r += dr;
+      if (a >= m) {
+        a -= m;
+        ++r;
+      }
     }
   }
   __syncthreads();

@@ -175,6 +175,23 @@ def test_setup_rejects_invalid_csr():
     assert e.value.code == B.ERR_CSR_INVALID
 
 
+def test_setup_rejects_invalid_csr_in_any_row_range():
+    """Host matrices with millions of entries are validated in row ranges on several threads:
+    a defect in the first, a middle or the last row is found, whichever range holds it."""
+    from workloads import config_c2
+    pb = B.problem_from_spec(config_c2())
+    K = pb.K
+    n = K.n_rows
+    for row in (0, n // 2 + 17, n - 1):
+        ci = K.col_idx.copy()
+        e = int(K.row_ptr[row])
+        ci[e] = K.n_cols if row != n // 2 + 17 else ci[e + 1]      # out of range, or a repeated column
+        bad = B.CsrArrays(n, K.n_cols, K.row_ptr, ci, K.val)
+        with pytest.raises(B.BpjdError) as err:
+            B.Solver(bad, pb.M, pb.P, pb.P0, pb.part, 12)
+        assert err.value.code == B.ERR_CSR_INVALID, row
+
+
 def test_setup_rejects_invalid_map_and_k():
     pb = _c1_arrays()
     dofs = pb.part.sub_dofs.copy()
