@@ -167,3 +167,45 @@ def test_table1_sixth_column_on_the_paper_partition():
           f"{st['iters']} iterations (paper, Table 2: 16)")
     assert st["converged"] == 1
     np.testing.assert_allclose(lam, want, rtol=0, atol=6e-9)
+
+
+def test_iterations_fall_with_the_number_of_subdomains_lshape():
+    """Table 4's experiment (iterations against N at delta / H = 1/4 fixed) on the L-shaped
+    domain, on Table 3's 784385-dof mesh: the boxes of the 16 x 16, 32 x 32 and 64 x 64 grids
+    over the square that lie in the domain (192, 768 and 3072 subdomains; the paper's N = 384,
+    1536 and 6144 triangles are the halves of such squares), delta = 16, 8 and 4 layers.  The
+    paper prints 21 / 18 / 16 at 12574721 dofs; here the counts must not grow with N, and the
+    eigenvalues are Table 3's fourth column to 8 decimals."""
+    want = np.array([r[3] for r in golden("table3.txt")])
+    its = []
+    for S in (16, 32, 64):
+        spec = replace(config_table3_col1(), n=(1024, 1024), nsub=(S, S), delta=1024 // (4 * S),
+                       name=f"table4_S{S}")
+        lam, st = _solve_paper_rule(spec, 32)
+        print(f"{S} x {S} boxes over the square, delta = {spec.delta}: {st['iters']} iterations")
+        assert st["converged"] == 1
+        np.testing.assert_allclose(lam, want, rtol=0, atol=6e-9)
+        its.append(st["iters"])
+    print(f"iterations for 192 / 768 / 3072 boxes: {its} (paper, 12574721 dofs, N = 384 / 1536 / 6144: 21 / 18 / 16)")
+    assert its[0] >= its[1] >= its[2], its
+
+
+def test_iterations_fall_with_the_number_of_subdomains_prism():
+    """Table 8's experiment (iterations against N) on the L-shaped prism, on Table 7's
+    758079-dof mesh: the paper's N = 1536 and 12288 cubes of sides pi/8 and pi/16, with
+    delta / H = 1/4 for both (2 and 1 layers; the paper's 1/2 would give the 1536 cubes local
+    bands beyond the kernel tiers).  The paper prints 18 / 15 at 6177407 dofs; here the count
+    must not grow with N, and the eigenvalues are Table 7's third column to 8 decimals."""
+    base = config_table7_col1()
+    want = np.array([r[2] for r in golden("table7.txt")])
+    its = []
+    for f, delta in ((1, 2), (2, 1)):
+        spec = replace(base, n=tuple(m * 4 for m in base.n), nsub=tuple(m * f for m in base.nsub), delta=delta,
+                       name=f"table8_N{1536 * f ** 3}")
+        lam, st = _solve_paper_rule(spec, 32)
+        print(f"N = {1536 * f ** 3} cubes, delta = {delta}: {st['iters']} iterations")
+        assert st["converged"] == 1
+        np.testing.assert_allclose(lam, want, rtol=0, atol=6e-9)
+        its.append(st["iters"])
+    print(f"iterations for N = 1536 / 12288: {its} (paper, 6177407 dofs, delta / H = 1/2: 18 / 15)")
+    assert its[0] >= its[1], its
