@@ -57,13 +57,14 @@ extern "C" {
 
 /* ---- option values ----------------------------------------------------- */
 #define BPJD_FP64        0  /* every step in FP64 */
-#define BPJD_MIXED       1  /* local band factorisations and solves in FP32 (tensor
-                               cores up to window 152); SpMM, projections, Gram
-                               matrices and the Ritz-vector update in double-word
-                               FP32 pairs (about 2^-46 relative, FP64-class);
-                               residuals and Rayleigh-Ritz in FP64 */
-#define BPJD_MIXED_LOCAL 2  /* local band factorisations and solves in FP32 as in
-                               BPJD_MIXED, every other step in native FP64: for
+#define BPJD_MIXED       1  /* the preconditioner in FP32: local band factorisations
+                               and solves (tensor cores up to window 152) and the
+                               prolongation-add (the coarse solve stays FP64); SpMM,
+                               projections, Gram matrices and the Ritz-vector update
+                               in double-word FP32 pairs (about 2^-46 relative,
+                               FP64-class); residuals and Rayleigh-Ritz in FP64 */
+#define BPJD_MIXED_LOCAL 2  /* the preconditioner in FP32 as in BPJD_MIXED, every
+                               other step in native FP64: for
                                operators whose residual amplifies product rounding
                                beyond the double-word floor (fourth-order problems on
                                fine meshes: |K||x| / |Kx| ~ 1e8) */
@@ -120,7 +121,7 @@ typedef struct {
                                anew only when some shift moved by more than this relative
                                amount since they were formed; otherwise the stored factors
                                are reused (forward and backward sweeps only).  0: default,
-                               1e-4 with FP32 local solves, exact shifts (a factorisation
+                               3e-4 with FP32 local solves, exact shifts (a factorisation
                                at every application, as in Eq. (3.3)) for BPJD_FP64;
                                < 0: exact shifts always.  Reuse needs every factor of one
                                application resident (one chunk) and a band window of at

@@ -318,10 +318,10 @@ extern "C" int bpjd_setup(const bpjd_csr* A, const bpjd_csr* M, const bpjd_csr* 
   h->max_iter = opts->max_iter > 0 ? opts->max_iter : 500;
   h->drop_tol = opts->drop_tol > 0 ? opts->drop_tol : 1e-10;
   // reuse of the local factors while the shifts stay within a relative tolerance
-  // (default 1e-4 with FP32 local solves; exact shifts for BPJD_FP64 or a negative value)
+  // (default 3e-4 with FP32 local solves; exact shifts for BPJD_FP64 or a negative value)
   h->refactor_tol = opts->local_refactor_tol > 0
                         ? opts->local_refactor_tol
-                        : ((opts->local_refactor_tol == 0 && opts->precision != BPJD_FP64) ? 1e-4 : 0.0);
+                        : ((opts->local_refactor_tol == 0 && opts->precision != BPJD_FP64) ? 3e-4 : 0.0);
   h->stream = (cudaStream_t)opts->stream;
   h->host_loop = opts->host_loop != 0;
 
@@ -405,6 +405,11 @@ extern "C" int bpjd_setup(const bpjd_csr* A, const bpjd_csr* M, const bpjd_csr* 
     CK(dalloc(*h, &h->PT.col, (size_t)P->nnz));
     CK(dalloc(*h, &h->PT.val, (size_t)P->nnz));
     CKI(launch_csr_transpose(h->P, h->PT.row_ptr, h->PT.col, h->PT.val, h->stream));
+    if (h->local_f32()) {
+      // FP32 preconditioners take the prolongation-add in FP32
+      CK(dalloc(*h, &h->Psplit, (size_t)std::max<int64_t>(P->nnz, 1)));
+      CKI(launch_split_values(h->P.val, P->nnz, h->Psplit, h->stream));
+    }
     // coarse pencils: Galerkin products on the device now, dense eigensolves on
     // host threads while the device-side setup below proceeds
     {

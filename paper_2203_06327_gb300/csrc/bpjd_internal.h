@@ -59,6 +59,7 @@ struct Handle {
   float2* Asplit = nullptr;  // (hi, lo) float pairs of K and M values (double-word SpMM)
   float2* Msplit = nullptr;
   float2* xsplit = nullptr;  // n x k (hi, lo) split of the block the next double-word SpMM reads
+  float2* Psplit = nullptr;  // (hi, lo) split of P's values (FP32 prolongation of FP32 preconditioners)
   CsrDev P, PT;             // coarse interpolation and its transpose
   double* Phi = nullptr;    // n_H x n_H row-major, M_H-orthonormal eigenvectors
   double* lamH = nullptr;   // n_H ascending

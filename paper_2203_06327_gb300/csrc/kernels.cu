@@ -2325,6 +2325,42 @@ __global__ void k_prolong_add(int64_t n, int k, const int64_t* __restrict__ prp,
   Z[t] = z;
 }
 
+// The prolongation-add in FP32 for the FP32 preconditioner: one thread per fine
+// row with its KC columns in registers, P values as the hi parts of their split,
+// w0 truncated to FP32 by integer operations, the FP32 local solutions added in
+// the inverse map's order (the order of k_prolong_add); Z stays FP64.
+template <int KC>
+__global__ void __launch_bounds__(256) k_prolong_add_f32(int64_t n, int k, const int64_t* __restrict__ prp,
+                                                         const int32_t* __restrict__ pci,
+                                                         const float2* __restrict__ pvs,
+                                                         const double* __restrict__ w0,
+                                                         const int32_t* __restrict__ rtp,
+                                                         const int32_t* __restrict__ rtpos,
+                                                         const float* __restrict__ wpk, double* __restrict__ Z) {
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= n) return;
+  float z[KC];
+#pragma unroll
+  for (int i = 0; i < KC; ++i) z[i] = 0.f;
+  for (int64_t e = prp[g]; e < prp[g + 1]; ++e) {
+    const float p = pvs[e].x;
+    const double* row = w0 + (int64_t)pci[e] * k;
+#pragma unroll
+    for (int i = 0; i < KC; ++i)
+      if (i < k) z[i] = fmaf(p, f64_hi(row[i]), z[i]);
+  }
+  for (int e = rtp[g]; e < rtp[g + 1]; ++e) {
+    const float* row = wpk + (int64_t)rtpos[e] * k;
+#pragma unroll
+    for (int i = 0; i < KC; ++i)
+      if (i < k) z[i] += row[i];
+  }
+  double* out = Z + g * k;
+#pragma unroll
+  for (int i = 0; i < KC; ++i)
+    if (i < k) out[i] = f32_to_f64_bits(z[i]);
+}
+
 // ---------------------------------------------------------------------------
 // Device-side setup: input validation, band structure of the local matrices.
 // ---------------------------------------------------------------------------
@@ -3230,7 +3266,18 @@ int launch_coarse_prolong(Handle& h, const double* rho, const double* lam, doubl
     ProfScope ps(h, BPJD_PROF_PROLONG);
     h.launches += 1;
     int64_t tot = (int64_t)h.n * k;
-    if (h.local_f32())
+    const unsigned rblocks = (unsigned)(((int64_t)h.n + 255) / 256);
+    if (h.local_f32() && h.Psplit) {
+      if (k <= 8)
+        k_prolong_add_f32<8><<<rblocks, 256, 0, h.stream>>>(h.n, k, h.P.row_ptr, h.P.col, h.Psplit, h.w0, h.rt_ptr,
+                                                           h.rt_pos, (const float*)h.wpk, Z);
+      else if (k <= 16)
+        k_prolong_add_f32<16><<<rblocks, 256, 0, h.stream>>>(h.n, k, h.P.row_ptr, h.P.col, h.Psplit, h.w0,
+                                                            h.rt_ptr, h.rt_pos, (const float*)h.wpk, Z);
+      else
+        k_prolong_add_f32<32><<<rblocks, 256, 0, h.stream>>>(h.n, k, h.P.row_ptr, h.P.col, h.Psplit, h.w0,
+                                                            h.rt_ptr, h.rt_pos, (const float*)h.wpk, Z);
+    } else if (h.local_f32())
       k_prolong_add<float><<<(unsigned)((tot + 255) / 256), 256, 0, h.stream>>>(
           h.n, k, h.P.row_ptr, h.P.col, h.P.val, h.w0, h.rt_ptr, h.rt_pos, (const float*)h.wpk, Z);
     else
