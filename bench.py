@@ -213,6 +213,7 @@ def oracle_sample(spec, iters_needed: int, n_local: int = 4, op=None):
         op = oracle_problem(spec)
     t_build = time.perf_counter() - t0
     N = len(op.sub_ptr) - 1
+    n_local = min(n_local, N)
     sel = np.linspace(0, N - 1, n_local).round().astype(int)
     ptr = [0]
     dofs = []
@@ -246,6 +247,23 @@ def oracle_sample(spec, iters_needed: int, n_local: int = 4, op=None):
               f"(all {spec.k} shifts) and the full-size coarse/projection/SpMM/Rayleigh-Ritz; local part scaled "
               f"x{scale:.0f}, iteration x{iters_needed} (GPU iteration count); measured {t_setup + t_local + t_rest:.1f} s")
     return spec.k / t_total, sample, {"t_iter_s": t_iter, "t_setup_s": t_setup * scale, "t_build_s": t_build}
+
+
+def oracle_complete_small():
+    """One complete, unextrapolated FP64 oracle solve of the small unit-square case
+    (961 dofs, k = 6: setup and every iteration to relative residual 1e-8), timed on
+    the host cores beside the extrapolated sample of the bench's workload."""
+    from oracle import bpjd as ob
+    from workloads import config_c1
+
+    spec = config_c1()
+    t0 = time.perf_counter()
+    op = oracle_problem(spec)
+    S = op.setup()
+    res = ob.solve(S, tol=1e-8, subspace="3s")
+    dt = time.perf_counter() - t0
+    return {"workload": spec.name, "eigenpairs_per_s": spec.k / dt, "seconds": dt, "iterations": res.iterations,
+            "converged": bool(res.converged), "kind": "oracle, complete solve (assembly, setup, all iterations)"}
 
 
 def _oracle_locals(spec, n):
@@ -447,7 +465,7 @@ def run_reference(a):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": spec.name, "n_dofs": spec.n_dofs, "k": spec.k},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle, extrapolated",
-                             "sample": sample},
+                             "sample": sample, "complete_small_solve": oracle_complete_small()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -685,7 +703,8 @@ def run_ours(a):
 
     if rank == 0 and not a.no_cpu_baseline:
         v, sample, info = oracle_sample(spec, int(round(statistics.mean(iters))), n_local=_oracle_locals(spec, 96))
-        cpu = {"value": v, "unit": UNIT, "cores": _blas_threads(), "kind": "oracle, extrapolated", "sample": sample}
+        cpu = {"value": v, "unit": UNIT, "cores": _blas_threads(), "kind": "oracle, extrapolated", "sample": sample,
+               "complete_small_solve": oracle_complete_small()}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
