@@ -295,26 +295,39 @@ bool tridiag_qr(int n, std::vector<double>& d, std::vector<double>& e, std::vect
   return true;
 }
 
-// The rotation sequence applied to nr rows (row stride ldz) starting at z0: each
-// row's pair of entries (k, k+1) is loaded for all rows first, then stored, so
-// that the rows proceed independently.  NR > 0 fixes the row count.
+// The rotation sequence applied to nr rows (row stride ldz) starting at z0.  A
+// QR sweep records rotations on consecutive column pairs (k, k+1), (k+1, k+2),
+// ...; along such a run the new entry k+1 of one rotation is the entry k of the
+// next, so every row carries it in a register (one load and one store per
+// rotation and row instead of two of each, the same arithmetic).  NR > 0 fixes
+// the row count.
 template <int NR>
 void rotate_rows(const std::vector<Rot>& rots, double* z0, int ldz, int nr) {
   constexpr int kMax = 8;
   const int cnt = NR > 0 ? NR : nr;
-  for (const Rot& g : rots) {
-    double* z = z0 + g.k;
-    double a[kMax], b[kMax];
+  const size_t nrot = rots.size();
+  for (size_t r0 = 0; r0 < nrot;) {
+    size_t r1 = r0 + 1;
+    while (r1 < nrot && rots[r1].k == rots[r1 - 1].k + 1) ++r1;
+    // the run r0 .. r1 - 1 acts on columns rots[r0].k .. rots[r1 - 1].k + 1
+    double carry[kMax];
+    const int k0 = rots[r0].k;
 #pragma GCC unroll 8
-    for (int i = 0; i < cnt; ++i) {
-      a[i] = z[(size_t)i * ldz];
-      b[i] = z[(size_t)i * ldz + 1];
-    }
+    for (int i = 0; i < cnt; ++i) carry[i] = z0[(size_t)i * ldz + k0];
+    for (size_t q = r0; q < r1; ++q) {
+      const Rot& g = rots[q];
+      double* z = z0 + g.k;
 #pragma GCC unroll 8
-    for (int i = 0; i < cnt; ++i) {
-      z[(size_t)i * ldz] = g.c * a[i] - g.s * b[i];
-      z[(size_t)i * ldz + 1] = g.s * a[i] + g.c * b[i];
+      for (int i = 0; i < cnt; ++i) {
+        const double a = carry[i], b = z[(size_t)i * ldz + 1];
+        z[(size_t)i * ldz] = g.c * a - g.s * b;
+        carry[i] = g.s * a + g.c * b;
+      }
     }
+    const int kl = rots[r1 - 1].k + 1;
+#pragma GCC unroll 8
+    for (int i = 0; i < cnt; ++i) z0[(size_t)i * ldz + kl] = carry[i];
+    r0 = r1;
   }
 }
 
